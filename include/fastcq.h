@@ -1,0 +1,164 @@
+/*
+ * fastcq — convolution-quadrature (CQ) history sums of the Riemann-Liouville
+ * derivative and the two-state fractional Fokker-Planck schemes of
+ * Sun, Nie & Deng, "Fast algorithms for convolution quadrature of
+ * Riemann-Liouville fractional derivative" (arXiv 1901.05128), on NVIDIA
+ * GB300 (sm_103a).
+ *
+ * C ABI. Every pointer named *_dev is CUDA device memory owned by the caller;
+ * *_host is host memory owned by the caller. The library never allocates
+ * device memory: entry points that need scratch take a caller workspace
+ * (ws_dev, ws_bytes). Passing ws_dev == NULL turns such a call into a size
+ * query: *ws_bytes receives the required size and nothing runs. Workspaces
+ * must be 256-byte aligned (cudaMalloc / torch allocations are).
+ *
+ * Unless stated otherwise a call only enqueues work on `stream` (a
+ * cudaStream_t; NULL = legacy default stream) and returns at once; argument
+ * errors are reported before anything is enqueued. Return values are CQ_OK
+ * or a negative CQ_E* status; cq_strerror() turns one into text. No entry
+ * point aborts, traps or exits.
+ *
+ * Notation (paper's): beta = 1 - alpha is the CQ order used for a state,
+ * tau = T/N the step, G^n the level at t_n, d_i the CQ weights,
+ * a = (1-m)/(2m-1) the coupling, A = -Laplacian (Dirichlet).
+ */
+#ifndef FASTCQ_H
+#define FASTCQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CQ_OK            0
+#define CQ_EINVAL       -1   /* invalid argument (range, size, pointer, order of calls) */
+#define CQ_ENOMEM       -2   /* caller workspace smaller than required */
+#define CQ_ECUDA        -3   /* a CUDA runtime call failed (launch, copy, sync) */
+#define CQ_ESINGULAR    -4   /* a 2x2 step matrix is singular to working precision */
+#define CQ_ENONFINITE   -5   /* the result contains Inf or NaN */
+#define CQ_ETIMEOUT     -6   /* a bounded device wait gave up */
+#define CQ_EUNSUPPORTED -7   /* valid request outside what this build implements */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define CQ_BE      1   /* backward Euler generating function (1 - zeta)/tau */
+#define CQ_BDF2    2   /* second-order backward difference ((1-zeta) + (1-zeta)^2/2)/tau */
+#define CQ_DIRECT  0   /* plain O(N^2) history (Eq. 3.8 / 4.1 / 4.7) */
+#define CQ_FAST    1   /* fast O(N Np) history (Eqs. 3.9-3.10, 3.17-3.18) */
+#define CQ_F64     0   /* FP64 end to end */
+
+/* Fast-form sizes. BE (Eqs. 3.6-3.10): np1 = Np Gauss-Jacobi points, np2
+ * ignored, ns ignored (the exact window of BE is d_1 alone).
+ * BDF2 (Eqs. 3.14-3.18): np1 = N_{p,1}, np2 = N_{p,2} points of the two
+ * families, ns = N_s >= 3 exact weights d_0..d_{Ns-1} (Remark 3.3).
+ * Limits: 1 <= np1 + np2 <= 256, ns <= 32. */
+typedef struct { int32_t np1, np2, ns; } cq_fast_cfg_t;
+
+/* ---- library information ----------------------------------------------- */
+const char *cq_strerror(int status);
+/* Number of CUDA kernels this library has launched since it was loaded. */
+int64_t cq_launch_count(void);
+/* When enabled (on != 0), fp2s_solve records CUDA events around its main
+ * time-stepping kernel on the caller's stream; cq_timing_last() returns that
+ * kernel's duration in milliseconds for the most recent fp2s_solve call. */
+int cq_timing_enable(int on);
+int cq_timing_last(double *ms_main_kernel);
+
+/* ---- CQ weights (Sec. 3, Eqs. 3.4 and 3.12) ---------------------------- */
+/* w_dev[i] = d^beta_{s,i}, i = 0..n: the Taylor coefficients of delta(zeta)^beta
+ * with delta = (1-zeta)/tau (CQ_BE, Eq. 3.4) or ((1-zeta)+(1-zeta)^2/2)/tau
+ * (CQ_BDF2, Eq. 3.12). 0 < beta < 1, tau > 0, 0 <= n <= 24000.
+ * Output: n+1 doubles in device memory. */
+int cq_weights(int32_t scheme, double beta, double tau, int64_t n, double *w_dev, void *stream);
+
+/* ---- Gauss-Jacobi rule (used by Eqs. 3.6 and 3.14) --------------------- */
+/* Nodes s_j (ascending) and weights lambda_j, j = 0..n-1, of the n-point
+ * Gauss rule for int_{-1}^{1} (1-s)^a (1+s)^b f(s) ds. 1 <= n <= 256,
+ * a, b > -1. Outputs: n doubles each, device memory. */
+int cq_gauss_jacobi(int32_t n, double a, double b, double *nodes_dev, double *weights_dev, void *stream);
+
+/* ---- fast-form coefficients (Eqs. 3.6-3.7, 3.14-3.16, Remark 3.2) ------ */
+/* For each Gauss-Jacobi point j (BE: j < np1; BDF2: the np1 points of family 1
+ * then the np2 points of family 2) the ratio r_j of its geometric sequence and
+ * the coefficient c_j such that the history part of the paper satisfies
+ *   Ghist_j(t_n) = c_j * Y_j(t_n),   Y_j(t_n) = r_j * Y_j(t_{n-1}) + G(t_{n-L}),
+ * with L = 2 for BE (c_j = w_j) and L = Ns for BDF2
+ * (c_j = w1_j (s+5)^-4 r1_j^(Ns-3), resp. w2_j Re((1+3s)^beta) r2_j^(Ns-3)).
+ * coef_dev: 2*np doubles, [r_0..r_{np-1}, c_0..c_{np-1}], np = np1 (BE) or
+ * np1+np2 (BDF2). ws_dev: scratch of *ws_bytes (size query when NULL). */
+int cq_fast_coeffs(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
+                   double *coef_dev, void *ws_dev, size_t *ws_bytes, void *stream);
+
+/* ---- direct history (Eq. 3.8; Eqs. 4.1 and 4.7 leave G^0 out) --------- */
+/* For every n in [n_lo, n_hi) and every DOF:
+ *     H_dev[(n - n_lo) * ldh + dof] = sum_{i=1}^{n-1} d_i G_dev[(n - i) * ldg + dof]
+ * i.e. the strictly lower-triangular Toeplitz product of the CQ weights with
+ * the levels G^1..G^{n-1} (row t of G_dev holds G^t; row 0 is never read).
+ * 1 <= n_lo <= n_hi, ndof >= 0, ldg, ldh >= ndof. The weights are computed
+ * into the workspace. prec must be CQ_F64. */
+int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof,
+                      int64_t n_lo, int64_t n_hi, const double *G_dev, int64_t ldg,
+                      double *H_dev, int64_t ldh, int32_t prec,
+                      void *ws_dev, size_t *ws_bytes, void *stream);
+
+/* ---- fast history, one step (Eqs. 3.9-3.10 / 3.17-3.18, Remarks 4.1, 4.7) */
+/* Forms h^n = sum_{i=1}^{min(L-1, n-1)} d_i G^{n-i} + sum_j Ghist_j(t_n) for all
+ * DOFs, L = 2 (BE) or Ns (BDF2), advancing the history parts from t_{n-1} to t_n.
+ * Must be called with n = 1, 2, 3, ... in order on the same workspace; the call
+ * with n = 1 (re)initialises the workspace (tables, zero state) and writes
+ * h^1 = 0. G_prev_dev = G^{n-1} (ndof doubles; ignored for n = 1, may be NULL).
+ * H_dev = h^n (ndof doubles). The workspace holds the Ghist state
+ * (np x ndof), the last L levels and the tables; its size depends on
+ * (scheme, cfg, ndof) only. prec must be CQ_F64. */
+int cq_history_fast(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
+                    int64_t ndof, int64_t n, const double *G_prev_dev, double *H_dev,
+                    int32_t prec, void *ws_dev, size_t *ws_bytes, void *stream);
+
+/* ---- two-state fractional Fokker-Planck system (Eqs. 1.1-1.3, 2.1) ----- */
+/* Problem on (0,1)^dim, dim in {1,2}, with M interior points per axis of the
+ * centred finite-difference Laplacian (h = 1/(M+1)); DOFs of one state are
+ * ordered dof = iy*M + ix and a two-state field is [2][M^dim] doubles.
+ * 0 < alpha1, alpha2 < 1; 0 <= m < 1, m != 1/2; T > 0; N >= 1.
+ * flags bit 0 (FP2S_ASYNC): fp2s_solve does not synchronise and does not
+ * report device status (CQ_ENONFINITE); use fp2s_status() later. */
+#define FP2S_ASYNC 1
+typedef struct {
+    double alpha1, alpha2, m, T;
+    int64_t N;
+    int32_t dim, M;
+    int32_t scheme;        /* CQ_BE or CQ_BDF2 */
+    int32_t form;          /* CQ_DIRECT or CQ_FAST */
+    cq_fast_cfg_t fast;    /* used when form == CQ_FAST */
+    int32_t prec;          /* CQ_F64 */
+    int32_t flags;
+} fp2s_problem_t;
+
+/* Whole solve, fused: G0_dev (physical [2][M^dim]) -> GN_dev (physical
+ * [2][M^dim], the level t_N of the BE scheme Eq. 4.1 / fast BE Eq. 4.3 /
+ * SBD Eq. 4.7 / fast SBD Eq. 4.8). Every sine mode is advanced through all N
+ * steps by one persistent kernel. Synchronises `stream` at the end to read
+ * the device status unless flags & FP2S_ASYNC. */
+int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double *GN_dev,
+               void *ws_dev, size_t *ws_bytes, void *stream);
+
+/* Step-by-step use of the same schemes: fp2s_init transforms G0 and sets up
+ * the tables and state in the workspace; fp2s_step(n) advances from t_{n-1}
+ * to t_n (n = 1..N in order) and, when G_out_dev != NULL, writes the physical
+ * level G^n ([2][M^dim]). */
+int fp2s_init(const fp2s_problem_t *p, const double *G0_dev, void *ws_dev, size_t *ws_bytes,
+              void *stream);
+int fp2s_step(const fp2s_problem_t *p, int64_t n, void *ws_dev, size_t ws_bytes,
+              double *G_out_dev, void *stream);
+/* Modal levels: g_dev receives the sine coefficients [2][M^dim] of the latest
+ * level computed by fp2s_step. */
+int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, double *g_dev,
+               void *stream);
+/* Device status of the last fp2s_* work on this workspace (synchronises the stream). */
+int fp2s_status(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTCQ_H */

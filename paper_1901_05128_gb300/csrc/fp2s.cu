@@ -1,0 +1,618 @@
+// Two-state fractional Fokker-Planck schemes (Eqs. 4.1, 4.3, 4.7, 4.8) in the
+// sine basis of the Dirichlet finite-difference Laplacian. Every mode k
+// (eigenvalue lambda_k) is an independent pair (g1, g2); with c = a + lambda_k:
+//
+//   BE, n >= 1:       [1/tau + c d1_0, -a d2_0; -a d1_0, 1/tau + c d2_0] g^n
+//                       = g^{n-1}/tau - c h_s + a h_o          (per state s, other o)
+//   SBD, n = 1:       [1/tau + 2/3 c d1_0, -2/3 a d2_0; ...] g^1
+//                       = g^0/tau - 1/3 c d_s0 g_s^0 + 1/3 a d_o0 g_o^0
+//   SBD, n >= 2:      [3/(2tau) + c d1_0, -a d2_0; ...] g^n
+//                       = (2 g^{n-1} - g^{n-2}/2)/tau - c e_s + a e_o,  e = h + d_{n-1} g^0 / 2
+//
+// h is the direct history sum_{i=1}^{n-1} d_i g^{n-i} or the fast one
+// (geometric history parts). The step matrix is the same for every n >= 2
+// (BE: n >= 1), so its inverse is formed once per mode.
+//
+// fp2s_solve runs all N steps of a mode inside one thread of one persistent
+// kernel: modes never interact, so there is no grid-wide synchronisation.
+#include "common.cuh"
+
+namespace fastcq {
+
+struct Fp2sParams {
+    double a, tau, inv_tau;
+    int64_t N, nmodes;
+    int scheme, form, np, L;     // np Gauss-Jacobi points per state, L exact window (2 for BE)
+};
+
+constexpr int kDirBT = 8;        // time block of the fused direct kernel
+
+struct Fp2sLayout {
+    int *status;
+    double *d1, *d2, *dz1, *dz2;
+    double *tab1, *tab2, *scr1, *scr2;
+    double *lam, *S, *tmp, *g0, *gN;
+    double *hist;                 // direct: (N+1) x 2 x nmodes
+    double *Y, *ring, *glast;     // step API, fast: 2 x np x nm, 2 x L x nm; both: 2 levels x 2 x nm
+    size_t bytes;
+};
+
+static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void *ws, bool stepper) {
+    Carve cv(ws);
+    Fp2sLayout l{};
+    const int64_t nm = P.nmodes;
+    l.status = cv.take<int>(64);
+    l.d1 = cv.take<double>(P.N + 1);
+    l.d2 = cv.take<double>(P.N + 1);
+    if (P.form == CQ_DIRECT) {
+        l.dz1 = cv.take<double>(P.N + 2 * kDirBT + 1);
+        l.dz2 = cv.take<double>(P.N + 2 * kDirBT + 1);
+    } else {
+        l.tab1 = cv.take<double>(2 * P.np);
+        l.tab2 = cv.take<double>(2 * P.np);
+        l.scr1 = cv.take<double>(2 * P.np);
+        l.scr2 = cv.take<double>(2 * P.np);
+    }
+    l.lam = cv.take<double>(nm);
+    l.S = cv.take<double>((size_t)p->M * p->M);
+    l.tmp = cv.take<double>(2 * nm);
+    l.g0 = cv.take<double>(2 * nm);
+    l.gN = cv.take<double>(2 * nm);
+    if (P.form == CQ_DIRECT) l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
+    if (stepper) {
+        if (P.form == CQ_FAST) {
+            l.Y = cv.take<double>((size_t)2 * P.np * nm);
+            l.ring = cv.take<double>((size_t)2 * P.L * nm);
+        }
+        l.glast = cv.take<double>((size_t)4 * nm);
+    }
+    l.bytes = cv.bytes();
+    return l;
+}
+
+static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
+    if (!p) return CQ_EINVAL;
+    if (!(p->alpha1 > 0.0 && p->alpha1 < 1.0 && p->alpha2 > 0.0 && p->alpha2 < 1.0)) return CQ_EINVAL;
+    if (!(p->m >= 0.0 && p->m < 1.0) || p->m == 0.5) return CQ_EINVAL;
+    if (!(p->T > 0.0) || p->N < 1 || p->N > kMaxWeights) return CQ_EINVAL;
+    if (p->dim != 1 && p->dim != 2) return CQ_EINVAL;
+    if (p->M < 1 || p->M > (p->dim == 1 ? (1 << 16) : 4096)) return CQ_EINVAL;
+    if (p->scheme != CQ_BE && p->scheme != CQ_BDF2) return CQ_EINVAL;
+    if (p->form != CQ_DIRECT && p->form != CQ_FAST) return CQ_EINVAL;
+    if (p->prec != CQ_F64) return CQ_EUNSUPPORTED;
+    P.a = (1.0 - p->m) / (2.0 * p->m - 1.0);
+    P.tau = p->T / (double)p->N;
+    P.inv_tau = 1.0 / P.tau;
+    P.N = p->N;
+    P.nmodes = (p->dim == 1) ? p->M : (int64_t)p->M * p->M;
+    P.scheme = p->scheme;
+    P.form = p->form;
+    np1 = p->fast.np1;
+    np2 = (p->scheme == CQ_BE) ? 0 : p->fast.np2;
+    P.L = (p->scheme == CQ_BE) ? 2 : p->fast.ns;
+    P.np = np1 + np2;
+    if (p->form == CQ_FAST) {
+        if (np1 < 1 || np2 < 0 || P.np > kMaxNp) return CQ_EINVAL;
+        if (p->scheme == CQ_BDF2 && (np2 < 1 || P.L < 3 || P.L > kMaxNs)) return CQ_EINVAL;
+    }
+    return CQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-mode step algebra
+// ---------------------------------------------------------------------------
+struct Inv2 {
+    double i11, i12, i21, i22;
+};
+
+__device__ inline bool invert2(double A11, double A12, double A21, double A22, Inv2 &m) {
+    const double det = A11 * A22 - A12 * A21;
+    const double sc = fmax(fabs(A11 * A22), fabs(A12 * A21));
+    const double id = 1.0 / det;
+    m.i11 = A22 * id;
+    m.i12 = -A12 * id;
+    m.i21 = -A21 * id;
+    m.i22 = A11 * id;
+    return fabs(det) > 1e-14 * sc;
+}
+
+struct ModeConst {
+    double c;                // a + lambda
+    Inv2 Mn;                 // n >= 2 (BE: n >= 1)
+    Inv2 M1;                 // SBD n = 1
+};
+
+__device__ inline bool mode_setup(const Fp2sParams &P, double lam, double d10, double d20, ModeConst &mc) {
+    const double c = P.a + lam;
+    mc.c = c;
+    const double lead = (P.scheme == CQ_BE) ? P.inv_tau : 1.5 * P.inv_tau;
+    bool ok = invert2(lead + c * d10, -P.a * d20, -P.a * d10, lead + c * d20, mc.Mn);
+    if (P.scheme == CQ_BDF2)
+        ok &= invert2(P.inv_tau + (2.0 / 3.0) * c * d10, -(2.0 / 3.0) * P.a * d20, -(2.0 / 3.0) * P.a * d10,
+                      P.inv_tau + (2.0 / 3.0) * c * d20, mc.M1);
+    return ok;
+}
+
+// One time step of one mode given its histories h1, h2. gm1 = g^{n-1}, gm2 = g^{n-2}, gz = g^0.
+__device__ inline void mode_step(const Fp2sParams &P, const ModeConst &mc, int64_t n, double h1, double h2,
+                                 double d10, double d20, double d1n, double d2n, double gm1_1, double gm1_2,
+                                 double gm2_1, double gm2_2, double gz1, double gz2, double &x1, double &x2) {
+    const double a = P.a, c = mc.c;
+    double b1, b2;
+    const Inv2 *M = &mc.Mn;
+    if (P.scheme == CQ_BE) {
+        b1 = gm1_1 * P.inv_tau - c * h1 + a * h2;
+        b2 = gm1_2 * P.inv_tau - c * h2 + a * h1;
+    } else if (n == 1) {
+        b1 = gz1 * P.inv_tau - c * d10 * gz1 * (1.0 / 3.0) + a * d20 * gz2 * (1.0 / 3.0);
+        b2 = gz2 * P.inv_tau - c * d20 * gz2 * (1.0 / 3.0) + a * d10 * gz1 * (1.0 / 3.0);
+        M = &mc.M1;
+    } else {
+        const double e1 = fma(0.5 * d1n, gz1, h1);
+        const double e2 = fma(0.5 * d2n, gz2, h2);
+        b1 = (2.0 * gm1_1 - 0.5 * gm2_1) * P.inv_tau - c * e1 + a * e2;
+        b2 = (2.0 * gm1_2 - 0.5 * gm2_2) * P.inv_tau - c * e2 + a * e1;
+    }
+    x1 = M->i11 * b1 + M->i12 * b2;
+    x2 = M->i21 * b1 + M->i22 * b2;
+}
+
+// ---------------------------------------------------------------------------
+// Fused fast solve: one thread per mode, all N steps. Shared memory holds the
+// tables, the history-part states Y[s][j][t] and the last L levels R[s][slot][t]
+// (level k in slot k % L) of the block's modes; consecutive threads touch
+// consecutive words, so every access is conflict-free.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fp2s_fast(Fp2sParams P, const double *__restrict__ lam,
+                                                   const double *__restrict__ g0, double *__restrict__ gN,
+                                                   int *__restrict__ status, const double *__restrict__ d1,
+                                                   const double *__restrict__ d2, const double *__restrict__ tab1,
+                                                   const double *__restrict__ tab2) {
+    extern __shared__ double sm[];
+    const int np = P.np, L = P.L, T = blockDim.x, t = threadIdx.x;
+    double *r1 = sm, *c1 = r1 + np, *r2 = c1 + np, *c2 = r2 + np;
+    double *w1 = c2 + np, *w2 = w1 + kMaxNs;
+    double *Y = w2 + kMaxNs;                  // [2][np][T]
+    double *R = Y + (size_t)2 * np * T;       // [2][L][T]
+    for (int i = t; i < np; i += T) {
+        r1[i] = tab1[i];
+        c1[i] = tab1[np + i];
+        r2[i] = tab2[i];
+        c2[i] = tab2[np + i];
+    }
+    for (int i = t; i < L; i += T) {
+        w1[i] = d1[i];
+        w2[i] = d2[i];
+    }
+    for (int j = 0; j < 2 * np; ++j) Y[(size_t)j * T + t] = 0.0;
+    for (int j = 0; j < 2 * L; ++j) R[(size_t)j * T + t] = 0.0;
+    __syncthreads();
+    const int64_t mode = (int64_t)blockIdx.x * T + t;
+    if (mode >= P.nmodes) return;
+    double *Y1 = Y + t, *Y2 = Y + (size_t)np * T + t;
+    double *R1 = R + t, *R2 = R + (size_t)L * T + t;
+
+    const double gz1 = g0[mode], gz2 = g0[P.nmodes + mode];
+    const double d10 = w1[0], d20 = w2[0];
+    ModeConst mc;
+    if (!mode_setup(P, lam[mode], d10, d20, mc)) atomicOr(status, ST_SINGULAR);
+    double gm1_1 = gz1, gm1_2 = gz2, gm2_1 = 0.0, gm2_2 = 0.0;
+    int slot = 0;                              // n % L
+    for (int64_t n = 1; n <= P.N; ++n) {
+        slot = (slot + 1 == L) ? 0 : slot + 1;
+        double h1 = 0.0, h2 = 0.0;
+        if (n - L >= 1) {
+            const double in1 = R1[(size_t)slot * T], in2 = R2[(size_t)slot * T];
+#pragma unroll 4
+            for (int j = 0; j < np; ++j) {
+                const double y1 = fma(r1[j], Y1[(size_t)j * T], in1);
+                const double y2 = fma(r2[j], Y2[(size_t)j * T], in2);
+                Y1[(size_t)j * T] = y1;
+                Y2[(size_t)j * T] = y2;
+                h1 = fma(c1[j], y1, h1);
+                h2 = fma(c2[j], y2, h2);
+            }
+        }
+        const int imax = (int)min((int64_t)(L - 1), n - 1);
+        int sl = slot;
+        for (int i = 1; i <= imax; ++i) {
+            sl = (sl == 0) ? L - 1 : sl - 1;   // slot of level n - i
+            h1 = fma(w1[i], R1[(size_t)sl * T], h1);
+            h2 = fma(w2[i], R2[(size_t)sl * T], h2);
+        }
+        double d1n = 0.0, d2n = 0.0;
+        if (P.scheme == CQ_BDF2 && n >= 2) {
+            d1n = __ldg(d1 + n - 1);
+            d2n = __ldg(d2 + n - 1);
+        }
+        double x1, x2;
+        mode_step(P, mc, n, h1, h2, d10, d20, d1n, d2n, gm1_1, gm1_2, gm2_1, gm2_2, gz1, gz2, x1, x2);
+        R1[(size_t)slot * T] = x1;
+        R2[(size_t)slot * T] = x2;
+        gm2_1 = gm1_1;
+        gm2_2 = gm1_2;
+        gm1_1 = x1;
+        gm1_2 = x2;
+    }
+    gN[mode] = gm1_1;
+    gN[P.nmodes + mode] = gm1_2;
+    if (!isfinite(gm1_1) || !isfinite(gm1_2)) atomicOr(status, ST_NONFINITE);
+}
+
+static size_t fast_smem_bytes(int np, int L, int T) {
+    return ((size_t)4 * np + 2 * kMaxNs + (size_t)2 * (np + L) * T) * sizeof(double);
+}
+
+static int fast_block_threads(int np, int L) {
+    for (int T = 256; T >= 32; T -= 32)
+        if (fast_smem_bytes(np, L, T) <= 220 * 1024) return T;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Fused direct solve: one thread per mode, time blocks of kDirBT steps. For a
+// block starting at n0 the contribution of the levels 1..n0-1 is accumulated
+// with a shifting register window of weights (one level load feeds 2*kDirBT
+// FMAs); the in-block terms follow step by step together with the solves.
+// hist[(k*2 + s)*nmodes + mode] holds level k of state s.
+// ---------------------------------------------------------------------------
+template <int BT>
+__global__ void __launch_bounds__(128) k_fp2s_direct(Fp2sParams P, const double *__restrict__ lam,
+                                                     const double *__restrict__ g0, double *__restrict__ gN,
+                                                     int *__restrict__ status, const double *__restrict__ d1,
+                                                     const double *__restrict__ d2,
+                                                     const double *__restrict__ dz1,
+                                                     const double *__restrict__ dz2, double *__restrict__ hist) {
+    const int64_t nm = P.nmodes;
+    const int64_t mode = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= nm) return;
+    const double gz1 = g0[mode], gz2 = g0[nm + mode];
+    hist[mode] = gz1;
+    hist[nm + mode] = gz2;
+    const double d10 = __ldg(d1), d20 = __ldg(d2);
+    ModeConst mc;
+    if (!mode_setup(P, lam[mode], d10, d20, mc)) atomicOr(status, ST_SINGULAR);
+    double gm1_1 = gz1, gm1_2 = gz2, gm2_1 = 0.0, gm2_2 = 0.0;
+    for (int64_t n0 = 1; n0 <= P.N; n0 += BT) {
+        double a1[BT], a2[BT], w1[BT], w2[BT], l1[BT] = {}, l2[BT] = {};
+#pragma unroll
+        for (int b = 0; b < BT; ++b) {
+            a1[b] = 0.0;
+            a2[b] = 0.0;
+            w1[b] = __ldg(dz1 + (n0 + b - 1) + BT);
+            w2[b] = __ldg(dz2 + (n0 + b - 1) + BT);
+        }
+        const double *hp = hist + 2 * nm + mode;          // level 1
+        for (int64_t k = 1; k < n0; ++k, hp += 2 * nm) {
+            const double x1 = hp[0], x2 = hp[nm];
+#pragma unroll
+            for (int b = 0; b < BT; ++b) {
+                a1[b] = fma(w1[b], x1, a1[b]);
+                a2[b] = fma(w2[b], x2, a2[b]);
+            }
+#pragma unroll
+            for (int b = BT - 1; b > 0; --b) {
+                w1[b] = w1[b - 1];
+                w2[b] = w2[b - 1];
+            }
+            w1[0] = __ldg(dz1 + (n0 - k - 1) + BT);
+            w2[0] = __ldg(dz2 + (n0 - k - 1) + BT);
+        }
+#pragma unroll
+        for (int b = 0; b < BT; ++b) {
+            const int64_t n = n0 + b;
+            if (n > P.N) break;
+            double h1 = a1[b], h2 = a2[b];
+#pragma unroll
+            for (int kk = 0; kk < b; ++kk) {
+                h1 = fma(__ldg(d1 + (b - kk)), l1[kk], h1);
+                h2 = fma(__ldg(d2 + (b - kk)), l2[kk], h2);
+            }
+            double d1n = 0.0, d2n = 0.0;
+            if (P.scheme == CQ_BDF2 && n >= 2) {
+                d1n = __ldg(d1 + n - 1);
+                d2n = __ldg(d2 + n - 1);
+            }
+            double x1, x2;
+            mode_step(P, mc, n, h1, h2, d10, d20, d1n, d2n, gm1_1, gm1_2, gm2_1, gm2_2, gz1, gz2, x1, x2);
+            l1[b] = x1;
+            l2[b] = x2;
+            hist[(n * 2) * nm + mode] = x1;
+            hist[(n * 2 + 1) * nm + mode] = x2;
+            gm2_1 = gm1_1;
+            gm2_2 = gm1_2;
+            gm1_1 = x1;
+            gm1_2 = x2;
+        }
+    }
+    gN[mode] = gm1_1;
+    gN[nm + mode] = gm1_2;
+    if (!isfinite(gm1_1) || !isfinite(gm1_2)) atomicOr(status, ST_NONFINITE);
+}
+
+__global__ void k_pad(const double *__restrict__ d, int64_t n, int BT, double *__restrict__ dz) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n + 2 * BT) return;
+    const int64_t idx = i - BT;
+    dz[i] = (idx >= 1 && idx <= n) ? d[idx] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Step API kernels (state in the workspace, one launch per time step).
+// glast[(lvl*2 + s)*nm + mode]: lvl 0 = g^{n-1}, lvl 1 = g^{n-2}.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fp2s_step_fast(Fp2sParams P, int64_t n, const double *__restrict__ lam,
+                                                        const double *__restrict__ g0, double *__restrict__ gout,
+                                                        int *__restrict__ status, const double *__restrict__ d1,
+                                                        const double *__restrict__ d2,
+                                                        const double *__restrict__ tab1,
+                                                        const double *__restrict__ tab2, double *__restrict__ Y,
+                                                        double *__restrict__ ring, double *__restrict__ glast) {
+    const int64_t nm = P.nmodes;
+    const int64_t mode = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= nm) return;
+    const int np = P.np, L = P.L;
+    double *Y1 = Y + mode, *Y2 = Y + (size_t)np * nm + mode;
+    double *R1 = ring + mode, *R2 = ring + (size_t)L * nm + mode;
+    const int slot = (int)(n % L);
+    double h1 = 0.0, h2 = 0.0;
+    if (n - L >= 1) {
+        const double in1 = R1[(size_t)slot * nm], in2 = R2[(size_t)slot * nm];
+        for (int j = 0; j < np; ++j) {
+            const double y1 = fma(__ldg(tab1 + j), Y1[(size_t)j * nm], in1);
+            const double y2 = fma(__ldg(tab2 + j), Y2[(size_t)j * nm], in2);
+            Y1[(size_t)j * nm] = y1;
+            Y2[(size_t)j * nm] = y2;
+            h1 = fma(__ldg(tab1 + np + j), y1, h1);
+            h2 = fma(__ldg(tab2 + np + j), y2, h2);
+        }
+    }
+    const int imax = (int)min((int64_t)(L - 1), n - 1);
+    for (int i = 1; i <= imax; ++i) {
+        const int sl = (int)((n - i) % L);
+        h1 = fma(__ldg(d1 + i), R1[(size_t)sl * nm], h1);
+        h2 = fma(__ldg(d2 + i), R2[(size_t)sl * nm], h2);
+    }
+    const double d10 = __ldg(d1), d20 = __ldg(d2);
+    ModeConst mc;
+    if (!mode_setup(P, lam[mode], d10, d20, mc)) atomicOr(status, ST_SINGULAR);
+    const double gz1 = g0[mode], gz2 = g0[nm + mode];
+    const double gm1_1 = glast[mode], gm1_2 = glast[nm + mode];
+    const double gm2_1 = glast[2 * nm + mode], gm2_2 = glast[3 * nm + mode];
+    double d1n = 0.0, d2n = 0.0;
+    if (P.scheme == CQ_BDF2 && n >= 2) {
+        d1n = __ldg(d1 + n - 1);
+        d2n = __ldg(d2 + n - 1);
+    }
+    double x1, x2;
+    mode_step(P, mc, n, h1, h2, d10, d20, d1n, d2n, gm1_1, gm1_2, gm2_1, gm2_2, gz1, gz2, x1, x2);
+    R1[(size_t)slot * nm] = x1;
+    R2[(size_t)slot * nm] = x2;
+    glast[2 * nm + mode] = gm1_1;
+    glast[3 * nm + mode] = gm1_2;
+    glast[mode] = x1;
+    glast[nm + mode] = x2;
+    gout[mode] = x1;
+    gout[nm + mode] = x2;
+    if (!isfinite(x1) || !isfinite(x2)) atomicOr(status, ST_NONFINITE);
+}
+
+__global__ void __launch_bounds__(256) k_fp2s_step_direct(Fp2sParams P, int64_t n, const double *__restrict__ lam,
+                                                          const double *__restrict__ g0, double *__restrict__ gout,
+                                                          int *__restrict__ status,
+                                                          const double *__restrict__ d1,
+                                                          const double *__restrict__ d2, double *__restrict__ hist,
+                                                          double *__restrict__ glast) {
+    const int64_t nm = P.nmodes;
+    const int64_t mode = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= nm) return;
+    double h1 = 0.0, h2 = 0.0;
+    for (int64_t i = 1; i <= n - 1; ++i) {
+        const double *lv = hist + ((n - i) * 2) * nm + mode;
+        h1 = fma(__ldg(d1 + i), lv[0], h1);
+        h2 = fma(__ldg(d2 + i), lv[nm], h2);
+    }
+    const double d10 = __ldg(d1), d20 = __ldg(d2);
+    ModeConst mc;
+    if (!mode_setup(P, lam[mode], d10, d20, mc)) atomicOr(status, ST_SINGULAR);
+    const double gz1 = g0[mode], gz2 = g0[nm + mode];
+    const double gm1_1 = glast[mode], gm1_2 = glast[nm + mode];
+    const double gm2_1 = glast[2 * nm + mode], gm2_2 = glast[3 * nm + mode];
+    double d1n = 0.0, d2n = 0.0;
+    if (P.scheme == CQ_BDF2 && n >= 2) {
+        d1n = __ldg(d1 + n - 1);
+        d2n = __ldg(d2 + n - 1);
+    }
+    double x1, x2;
+    mode_step(P, mc, n, h1, h2, d10, d20, d1n, d2n, gm1_1, gm1_2, gm2_1, gm2_2, gz1, gz2, x1, x2);
+    hist[(n * 2) * nm + mode] = x1;
+    hist[(n * 2 + 1) * nm + mode] = x2;
+    glast[2 * nm + mode] = gm1_1;
+    glast[3 * nm + mode] = gm1_2;
+    glast[mode] = x1;
+    glast[nm + mode] = x2;
+    gout[mode] = x1;
+    gout[nm + mode] = x2;
+    if (!isfinite(x1) || !isfinite(x2)) atomicOr(status, ST_NONFINITE);
+}
+
+__global__ void k_copy_levels(const double *__restrict__ g0, int64_t nm, double *__restrict__ hist,
+                              double *__restrict__ glast) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * nm) return;
+    if (hist) hist[i] = g0[i];
+    if (glast) {
+        glast[i] = g0[i];
+        glast[2 * nm + i] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int status_from_bits(int bits) {
+    if (bits & ST_TIMEOUT) return CQ_ETIMEOUT;
+    if (bits & ST_SINGULAR) return CQ_ESINGULAR;
+    if (bits & ST_NONFINITE) return CQ_ENONFINITE;
+    return CQ_OK;
+}
+
+static int read_status(const int *status_dev, cudaStream_t s) {
+    static int *host = nullptr;
+    if (!host && cudaMallocHost(&host, 64) != cudaSuccess) return CQ_ECUDA;
+    if (cudaMemcpyAsync(host, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CQ_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CQ_ECUDA;
+    return status_from_bits(host[0]);
+}
+
+// Common set-up of fp2s_solve and fp2s_init: status, weights, tables, spectrum, DST of G0.
+static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2, const Fp2sLayout &l,
+                 const double *G0, cudaStream_t s) {
+    int st;
+    const double b1 = 1.0 - p->alpha1, b2 = 1.0 - p->alpha2;
+    if ((st = cuda_status(cudaMemsetAsync(l.status, 0, 64 * sizeof(int), s)))) return st;
+    if ((st = launch_weights(P.scheme, b1, P.tau, P.N, l.d1, s))) return st;
+    if ((st = launch_weights(P.scheme, b2, P.tau, P.N, l.d2, s))) return st;
+    if (P.form == CQ_DIRECT) {
+        const unsigned g = (unsigned)((P.N + 2 * kDirBT + 256) / 256);
+        k_pad<<<g, 256, 0, s>>>(l.d1, P.N, kDirBT, l.dz1);
+        k_pad<<<g, 256, 0, s>>>(l.d2, P.N, kDirBT, l.dz2);
+        if ((st = launched(2))) return st;
+    } else {
+        if ((st = build_fast_coeffs(P.scheme, b1, P.tau, np1, np2, P.L, l.scr1, l.tab1, l.tab1 + P.np, s))) return st;
+        if ((st = build_fast_coeffs(P.scheme, b2, P.tau, np1, np2, P.L, l.scr2, l.tab2, l.tab2 + P.np, s))) return st;
+    }
+    if ((st = launch_mode_eigenvalues(p->M, p->dim, l.lam, s))) return st;
+    if ((st = launch_dst_matrix(p->M, l.S, s))) return st;
+    return launch_dst_field(p->M, p->dim, l.S, G0, l.g0, l.tmp, s);
+}
+
+static bool g_timing = false;
+static cudaEvent_t g_ev0 = nullptr, g_ev1 = nullptr;
+static bool g_timed = false;
+
+}  // namespace fastcq
+
+using namespace fastcq;
+
+extern "C" int cq_timing_enable(int on) {
+    if (on && !g_ev0) {
+        if (cudaEventCreate(&g_ev0) != cudaSuccess || cudaEventCreate(&g_ev1) != cudaSuccess) return CQ_ECUDA;
+    }
+    g_timing = on != 0;
+    return CQ_OK;
+}
+
+extern "C" int cq_timing_last(double *ms) {
+    if (!ms) return CQ_EINVAL;
+    if (!g_timed) return CQ_EINVAL;
+    float f = 0.0f;
+    if (cudaEventSynchronize(g_ev1) != cudaSuccess) return CQ_ECUDA;
+    if (cudaEventElapsedTime(&f, g_ev0, g_ev1) != cudaSuccess) return CQ_ECUDA;
+    *ms = f;
+    return CQ_OK;
+}
+
+extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double *GN_dev, void *ws_dev,
+                          size_t *ws_bytes, void *stream) {
+    Fp2sParams P;
+    int np1 = 0, np2 = 0;
+    int st = derive(p, P, np1, np2);
+    if (st) return st;
+    if (!ws_bytes) return CQ_EINVAL;
+    Fp2sLayout l = fp2s_layout(p, P, ws_dev, false);
+    if (!ws_dev) { *ws_bytes = l.bytes; return CQ_OK; }
+    if (*ws_bytes < l.bytes) return CQ_ENOMEM;
+    if (!G0_dev || !GN_dev || ((uintptr_t)ws_dev & 255)) return CQ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
+    if (g_timing && cudaEventRecord(g_ev0, s) != cudaSuccess) return CQ_ECUDA;
+    if (P.form == CQ_FAST) {
+        const int T = fast_block_threads(P.np, P.L);
+        if (T == 0) return CQ_EUNSUPPORTED;
+        const size_t smem = fast_smem_bytes(P.np, P.L, T);
+        cudaFuncSetAttribute(k_fp2s_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const unsigned blocks = (unsigned)((P.nmodes + T - 1) / T);
+        k_fp2s_fast<<<blocks, T, smem, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2);
+    } else {
+        const unsigned blocks = (unsigned)((P.nmodes + 127) / 128);
+        k_fp2s_direct<kDirBT><<<blocks, 128, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2,
+                                                     l.hist);
+    }
+    if ((st = launched())) return st;
+    if (g_timing) {
+        if (cudaEventRecord(g_ev1, s) != cudaSuccess) return CQ_ECUDA;
+        g_timed = true;
+    }
+    if ((st = launch_dst_field(p->M, p->dim, l.S, l.gN, GN_dev, l.tmp, s))) return st;
+    if (p->flags & FP2S_ASYNC) return CQ_OK;
+    return read_status(l.status, s);
+}
+
+extern "C" int fp2s_init(const fp2s_problem_t *p, const double *G0_dev, void *ws_dev, size_t *ws_bytes,
+                         void *stream) {
+    Fp2sParams P;
+    int np1 = 0, np2 = 0;
+    int st = derive(p, P, np1, np2);
+    if (st) return st;
+    if (!ws_bytes) return CQ_EINVAL;
+    Fp2sLayout l = fp2s_layout(p, P, ws_dev, true);
+    if (!ws_dev) { *ws_bytes = l.bytes; return CQ_OK; }
+    if (*ws_bytes < l.bytes) return CQ_ENOMEM;
+    if (!G0_dev || ((uintptr_t)ws_dev & 255)) return CQ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
+    if (P.form == CQ_FAST) {
+        if ((st = cuda_status(cudaMemsetAsync(l.Y, 0, (size_t)2 * P.np * P.nmodes * sizeof(double), s)))) return st;
+        if ((st = cuda_status(cudaMemsetAsync(l.ring, 0, (size_t)2 * P.L * P.nmodes * sizeof(double), s)))) return st;
+    }
+    const unsigned g = (unsigned)((2 * P.nmodes + 255) / 256);
+    k_copy_levels<<<g, 256, 0, s>>>(l.g0, P.nmodes, l.hist, l.glast);
+    if ((st = launched())) return st;
+    return cuda_status(cudaMemcpyAsync(l.gN, l.g0, 2 * P.nmodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+
+extern "C" int fp2s_step(const fp2s_problem_t *p, int64_t n, void *ws_dev, size_t ws_bytes, double *G_out_dev,
+                         void *stream) {
+    Fp2sParams P;
+    int np1 = 0, np2 = 0;
+    int st = derive(p, P, np1, np2);
+    if (st) return st;
+    if (!ws_dev || n < 1 || n > P.N) return CQ_EINVAL;
+    Fp2sLayout l = fp2s_layout(p, P, ws_dev, true);
+    if (ws_bytes < l.bytes) return CQ_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((P.nmodes + 255) / 256);
+    if (P.form == CQ_FAST)
+        k_fp2s_step_fast<<<blocks, 256, 0, s>>>(P, n, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.Y,
+                                                l.ring, l.glast);
+    else
+        k_fp2s_step_direct<<<blocks, 256, 0, s>>>(P, n, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.hist, l.glast);
+    if ((st = launched())) return st;
+    if (G_out_dev) return launch_dst_field(p->M, p->dim, l.S, l.gN, G_out_dev, l.tmp, s);
+    return CQ_OK;
+}
+
+extern "C" int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, double *g_dev,
+                          void *stream) {
+    Fp2sParams P;
+    int np1 = 0, np2 = 0;
+    int st = derive(p, P, np1, np2);
+    if (st) return st;
+    if (!ws_dev || !g_dev) return CQ_EINVAL;
+    Fp2sLayout l = fp2s_layout(p, P, const_cast<void *>(ws_dev), true);
+    if (ws_bytes < l.bytes) return CQ_ENOMEM;
+    return cuda_status(cudaMemcpyAsync(g_dev, l.gN, 2 * P.nmodes * sizeof(double), cudaMemcpyDeviceToDevice,
+                                       (cudaStream_t)stream));
+}
+
+extern "C" int fp2s_status(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, void *stream) {
+    Fp2sParams P;
+    int np1 = 0, np2 = 0;
+    int st = derive(p, P, np1, np2);
+    if (st) return st;
+    if (!ws_dev) return CQ_EINVAL;
+    Fp2sLayout l = fp2s_layout(p, P, const_cast<void *>(ws_dev), false);
+    (void)ws_bytes;
+    return read_status(l.status, (cudaStream_t)stream);
+}

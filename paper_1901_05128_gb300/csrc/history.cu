@@ -1,0 +1,233 @@
+// History sums over all DOFs: the direct strictly-lower-triangular Toeplitz
+// product (Eq. 3.8) and one step of the fast recurrences (Eqs. 3.9-3.10,
+// 3.17-3.18). FP64.
+#include "common.cuh"
+
+namespace fastcq {
+
+// ---------------------------------------------------------------------------
+// Direct history. Block (x: DOF tile, y: block of BT consecutive output steps).
+// Each thread owns VEC adjacent DOFs and BT outputs n0..n0+BT-1; it streams the
+// levels k = 1..n_last-1 once and keeps the BT weights d_{n0+b-k} in a register
+// window that shifts by one per level, so every level load feeds BT*VEC FMAs.
+// dz[i + BT] = d_i for i >= 1 and 0 for i <= 0 (this drops d_0 and the
+// non-causal terms).
+// ---------------------------------------------------------------------------
+template <int BT, int VEC>
+__global__ void __launch_bounds__(128) k_history_direct(int64_t ndof, int64_t n_lo, int64_t n_hi,
+                                                        const double *__restrict__ dz,
+                                                        const double *__restrict__ G, int64_t ldg,
+                                                        double *__restrict__ H, int64_t ldh) {
+    const int64_t dof = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * VEC;
+    if (dof >= ndof) return;
+    const int64_t n0 = n_lo + (int64_t)blockIdx.y * BT;
+    const int64_t n_last = min(n0 + BT - 1, n_hi - 1);
+    double acc[BT][VEC];
+    double w[BT];
+#pragma unroll
+    for (int b = 0; b < BT; ++b) {
+        w[b] = __ldg(dz + (n0 + b - 1) + BT);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[b][v] = 0.0;
+    }
+    const bool full = (dof + VEC <= ndof);
+    for (int64_t k = 1; k <= n_last - 1; ++k) {
+        double g[VEC];
+        const double *src = G + k * ldg + dof;
+        if (VEC == 2 && full) {
+            const double2 t = __ldg(reinterpret_cast<const double2 *>(src));
+            g[0] = t.x;
+            g[VEC - 1] = t.y;
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) g[v] = (dof + v < ndof) ? __ldg(src + v) : 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[b][v] = fma(w[b], g[v], acc[b][v]);
+#pragma unroll
+        for (int b = BT - 1; b > 0; --b) w[b] = w[b - 1];
+        w[0] = __ldg(dz + (n0 - k - 1) + BT);
+    }
+#pragma unroll
+    for (int b = 0; b < BT; ++b) {
+        const int64_t n = n0 + b;
+        if (n >= n_hi) break;
+        double *dst = H + (n - n_lo) * ldh + dof;
+        if (VEC == 2 && full) {
+            *reinterpret_cast<double2 *>(dst) = make_double2(acc[b][0], acc[b][VEC - 1]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v)
+                if (dof + v < ndof) dst[v] = acc[b][v];
+        }
+    }
+}
+
+constexpr int kDirectBT = 16;
+
+// Writes the zero-padded weight vector dz (see k_history_direct): entries
+// 0 .. n + 2*kDirectBT, i.e. every index a tail block may touch.
+__global__ void k_pad_weights(const double *__restrict__ d, int64_t n, double *__restrict__ dz) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n + 2 * kDirectBT) return;
+    const int64_t idx = i - kDirectBT;        // weight index
+    dz[i] = (idx >= 1 && idx <= n) ? d[idx] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Fast history, one step, for every DOF (2 DOFs per thread).
+// State Y[j][dof] (Ghist_j = c_j Y_j), ring[L][dof] with level k in slot k % L.
+// At step n: levels n-2..n-L are in the ring, level n-1 comes from G_prev.
+//   Y_j <- r_j Y_j + G^{n-L}               (only when n - L >= 1; G^0 is left out)
+//   h^n = sum_{i=1}^{min(L-1,n-1)} d_i G^{n-i} + sum_j c_j Y_j
+// then G^{n-1} is stored in slot (n-1) % L, which held level n-1-L.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_history_fast_step(int64_t ndof, int64_t n, int L, int np,
+                                                           const double *__restrict__ tab,
+                                                           double *__restrict__ ring, double *__restrict__ Y,
+                                                           const double *__restrict__ G_prev,
+                                                           double *__restrict__ H) {
+    __shared__ double r[kMaxNp], c[kMaxNp], d[kMaxNs];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        r[i] = tab[i];
+        c[i] = tab[np + i];
+    }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) d[i] = tab[2 * np + i];
+    __syncthreads();
+    const int64_t dof = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (dof >= ndof) return;
+    const bool pair = dof + 1 < ndof;
+    double h0 = 0.0, h1 = 0.0, gp0 = 0.0, gp1 = 0.0;
+    if (n >= 2) {
+        gp0 = G_prev[dof];
+        gp1 = pair ? G_prev[dof + 1] : 0.0;
+        h0 = d[1] * gp0;
+        h1 = d[1] * gp1;
+        const int64_t imax = min((int64_t)L - 1, n - 1);
+        for (int i = 2; i <= imax; ++i) {
+            const double *src = ring + (int64_t)((n - i) % L) * ndof + dof;
+            h0 = fma(d[i], src[0], h0);
+            if (pair) h1 = fma(d[i], src[1], h1);
+        }
+    }
+    if (n - L >= 1) {
+        const double *gin_p = ring + (int64_t)((n - L) % L) * ndof + dof;
+        const double g0 = gin_p[0], g1 = pair ? gin_p[1] : 0.0;
+        for (int j = 0; j < np; ++j) {
+            double *y = Y + (int64_t)j * ndof + dof;
+            const double y0 = fma(r[j], y[0], g0);
+            y[0] = y0;
+            h0 = fma(c[j], y0, h0);
+            if (pair) {
+                const double y1 = fma(r[j], y[1], g1);
+                y[1] = y1;
+                h1 = fma(c[j], y1, h1);
+            }
+        }
+    }
+    if (n >= 2) {
+        double *dst = ring + (int64_t)((n - 1) % L) * ndof + dof;
+        dst[0] = gp0;
+        if (pair) dst[1] = gp1;
+    }
+    H[dof] = h0;
+    if (pair) H[dof + 1] = h1;
+}
+
+struct FastHistLayout {
+    double *tab;       // r[np], c[np], d[L]
+    double *scratch;   // Gauss-Jacobi nodes / weights
+    double *dfull;     // weights d_0..d_{L-1} as produced by the weight kernel
+    double *ring;      // L x ndof
+    double *Y;         // np x ndof
+    size_t bytes;
+};
+
+static FastHistLayout fast_hist_layout(void *ws, int np1, int np2, int L, int64_t ndof) {
+    Carve cv(ws);
+    FastHistLayout l;
+    const int np = np1 + np2;
+    l.tab = cv.take<double>(2 * np + kMaxNs);
+    l.scratch = cv.take<double>(2 * (np1 + np2));
+    l.dfull = cv.take<double>(kMaxNs);
+    l.ring = cv.take<double>((size_t)L * ndof);
+    l.Y = cv.take<double>((size_t)np * ndof);
+    l.bytes = cv.bytes();
+    return l;
+}
+
+}  // namespace fastcq
+
+using namespace fastcq;
+
+extern "C" int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof, int64_t n_lo,
+                                 int64_t n_hi, const double *G_dev, int64_t ldg, double *H_dev, int64_t ldh,
+                                 int32_t prec, void *ws_dev, size_t *ws_bytes, void *stream) {
+    if (!ws_bytes || (scheme != CQ_BE && scheme != CQ_BDF2) || bad_order(beta) || !(tau > 0.0) || ndof < 0 ||
+        n_lo < 1 || n_hi < n_lo || n_hi > kMaxWeights || ldg < ndof || ldh < ndof)
+        return CQ_EINVAL;
+    if (prec != CQ_F64) return CQ_EUNSUPPORTED;
+    Carve cv(ws_dev);
+    double *d = cv.take<double>(n_hi + 1);
+    double *dz = cv.take<double>(n_hi + 2 * kDirectBT + 1);
+    if (!ws_dev) { *ws_bytes = cv.bytes(); return CQ_OK; }
+    if (*ws_bytes < cv.bytes()) return CQ_ENOMEM;
+    if (n_hi == n_lo || ndof == 0) return CQ_OK;
+    if (!G_dev || !H_dev) return CQ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = launch_weights(scheme, beta, tau, n_hi, d, s);
+    if (st) return st;
+    k_pad_weights<<<(unsigned)((n_hi + 2 * kDirectBT + 256) / 256), 256, 0, s>>>(d, n_hi, dz);
+    if ((st = launched())) return st;
+    const bool vec2 = (ldg % 2 == 0) && (ldh % 2 == 0) && ((uintptr_t)G_dev % 16 == 0) && ((uintptr_t)H_dev % 16 == 0);
+    const int64_t rows = n_hi - n_lo;
+    dim3 grid;
+    grid.y = (unsigned)((rows + kDirectBT - 1) / kDirectBT);
+    if (grid.y > 65535) return CQ_EUNSUPPORTED;
+    if (vec2) {
+        grid.x = (unsigned)((ndof + 2 * 128 - 1) / (2 * 128));
+        k_history_direct<kDirectBT, 2><<<grid, 128, 0, s>>>(ndof, n_lo, n_hi, dz, G_dev, ldg, H_dev, ldh);
+    } else {
+        grid.x = (unsigned)((ndof + 127) / 128);
+        k_history_direct<kDirectBT, 1><<<grid, 128, 0, s>>>(ndof, n_lo, n_hi, dz, G_dev, ldg, H_dev, ldh);
+    }
+    return launched();
+}
+
+extern "C" int cq_history_fast(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg, int64_t ndof,
+                               int64_t n, const double *G_prev_dev, double *H_dev, int32_t prec, void *ws_dev,
+                               size_t *ws_bytes, void *stream) {
+    if (!cfg || !ws_bytes || (scheme != CQ_BE && scheme != CQ_BDF2) || bad_order(beta) || !(tau > 0.0) ||
+        ndof < 0 || n < 1)
+        return CQ_EINVAL;
+    if (prec != CQ_F64) return CQ_EUNSUPPORTED;
+    const int np1 = cfg->np1, np2 = (scheme == CQ_BE) ? 0 : cfg->np2;
+    const int L = (scheme == CQ_BE) ? 2 : cfg->ns;
+    if (np1 < 1 || np2 < 0 || np1 + np2 > kMaxNp || (scheme == CQ_BDF2 && (np2 < 1 || L < 3 || L > kMaxNs)))
+        return CQ_EINVAL;
+    FastHistLayout lay = fast_hist_layout(ws_dev, np1, np2, L, ndof);
+    if (!ws_dev) { *ws_bytes = lay.bytes; return CQ_OK; }
+    if (*ws_bytes < lay.bytes) return CQ_ENOMEM;
+    if (!H_dev || (n >= 2 && !G_prev_dev)) return CQ_EINVAL;
+    if (ndof == 0) return CQ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = np1 + np2;
+    int st;
+    if (n == 1) {
+        if ((st = launch_weights(scheme, beta, tau, L - 1, lay.dfull, s))) return st;
+        if ((st = cuda_status(cudaMemcpyAsync(lay.tab + 2 * np, lay.dfull, L * sizeof(double),
+                                              cudaMemcpyDeviceToDevice, s))))
+            return st;
+        if ((st = build_fast_coeffs(scheme, beta, tau, np1, np2, L, lay.scratch, lay.tab, lay.tab + np, s)))
+            return st;
+        if ((st = cuda_status(cudaMemsetAsync(lay.Y, 0, (size_t)np * ndof * sizeof(double), s)))) return st;
+        if ((st = cuda_status(cudaMemsetAsync(lay.ring, 0, (size_t)L * ndof * sizeof(double), s)))) return st;
+        return cuda_status(cudaMemsetAsync(H_dev, 0, (size_t)ndof * sizeof(double), s));
+    }
+    const int64_t threads = (ndof + 1) / 2;
+    k_history_fast_step<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ndof, n, L, np, lay.tab, lay.ring, lay.Y,
+                                                                         G_prev_dev, H_dev);
+    return launched();
+}

@@ -1,0 +1,370 @@
+// Table builders: CQ weights, Gauss-Jacobi rules, fast-form coefficients,
+// sine-mode eigenvalues, the DST-I matrix and the small FP64 GEMM that applies it.
+// All run on the GPU in FP64 (FP32 only for the bracketing bisection of the
+// Gauss-Jacobi nodes, which is followed by FP64 Newton steps).
+#include "common.cuh"
+
+namespace fastcq {
+
+// ---------------------------------------------------------------------------
+// CQ weights (Sec. 3, Eqs. 3.4 and 3.12).
+// g_i = coefficients of (1 - zeta)^beta: g_0 = 1, g_i = g_{i-1} (i - 1 - beta)/i.
+// One block: each thread forms the product of the factors of its chunk, an
+// exclusive multiplicative block scan supplies the prefix, and each thread
+// then writes its chunk. BE: d_i = tau^-beta g_i.
+// BDF2: 3/2 - 2 zeta + zeta^2/2 = (3/2)(1 - zeta)(1 - zeta/3), so
+//   d_i = tau^-beta (3/2)^beta sum_k g_{i-k} g_k 3^-k;
+// terms with k > 64 are below 3^-64 relative and are left out.
+// ---------------------------------------------------------------------------
+constexpr int kWThreads = 1024;
+constexpr int kCauchyTerms = 64;
+
+__global__ void __launch_bounds__(kWThreads) k_weights(int scheme, double beta, double scale, int n,
+                                                       double *__restrict__ out) {
+    extern __shared__ double g[];                 // g[0..n]
+    __shared__ double part[kWThreads];
+    __shared__ double bk[kCauchyTerms + 1];
+    const int t = threadIdx.x;
+    const int T = blockDim.x;
+    const int chunk = (n + 1 + T - 1) / T;
+    const int lo = t * chunk;
+    const int hi = min(lo + chunk, n + 1);
+    double p = 1.0;
+    for (int i = max(lo, 1); i < hi; ++i) p *= (i - 1.0 - beta) / i;
+    part[t] = p;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        double x = (t >= off) ? part[t - off] : 1.0;
+        __syncthreads();
+        part[t] *= x;
+        __syncthreads();
+    }
+    double v = (t == 0) ? 1.0 : part[t - 1];
+    for (int i = lo; i < hi; ++i) {
+        if (i >= 1) v *= (i - 1.0 - beta) / i;
+        g[i] = v;
+    }
+    __syncthreads();
+    if (scheme == CQ_BE) {
+        for (int i = t; i <= n; i += T) out[i] = g[i] * scale;
+        return;
+    }
+    if (t <= kCauchyTerms && t <= n) {
+        bk[t] = g[t] / pow(3.0, (double)t);
+    }
+    __syncthreads();
+    const double c0 = pow(1.5, beta) * scale;
+    for (int i = t; i <= n; i += T) {
+        const int kmax = min(i, kCauchyTerms);
+        double acc = 0.0;
+        for (int k = kmax; k >= 0; --k) acc = fma(g[i - k], bk[k], acc);
+        out[i] = acc * c0;
+    }
+}
+
+int launch_weights(int scheme, double beta, double tau, int64_t n, double *out, cudaStream_t s) {
+    if (n < 0 || n > kMaxWeights) return CQ_EINVAL;
+    size_t smem = (size_t)(n + 1) * sizeof(double);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_weights, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((kMaxWeights + 1) * sizeof(double)));
+        attr_done = true;
+    }
+    k_weights<<<1, kWThreads, smem, s>>>(scheme, beta, pow(tau, -beta), (int)n, out);
+    return launched();
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Jacobi rule for (1-s)^a (1+s)^b on [-1,1].
+// Jacobi matrix of the monic Jacobi polynomials (three-term recurrence):
+//   alpha_0 = (b-a)/(a+b+2), alpha_k = (b^2-a^2)/((2k+a+b)(2k+a+b+2)),
+//   beta_k  = 4k(k+a)(k+b)(k+a+b)/((2k+a+b)^2 (2k+a+b+1)(2k+a+b-1)).
+// Each thread owns one node: FP32 Sturm-count bisection brackets the j-th
+// eigenvalue, FP64 Newton on the monic P_n (recurrence and its derivative)
+// converges it, and the weight is the Christoffel number
+//   lambda_j = 1 / sum_{k<n} phat_k(s_j)^2
+// with phat_k orthonormal (phat_0 = mu0^-1/2, mu0 = int (1-s)^a (1+s)^b ds).
+// ---------------------------------------------------------------------------
+constexpr int kGJThreads = 64;
+
+__global__ void __launch_bounds__(kGJThreads) k_gauss_jacobi(int n, double a, double b,
+                                                             double *__restrict__ nodes,
+                                                             double *__restrict__ wts) {
+    __shared__ double al[kMaxNp], be[kMaxNp], sq[kMaxNp];
+    __shared__ float fal[kMaxNp], fbe[kMaxNp];
+    const double ab = a + b;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double dk = (k == 0) ? (b - a) / (ab + 2.0) : (b * b - a * a) / ((2.0 * k + ab) * (2.0 * k + ab + 2.0));
+        al[k] = dk;
+        fal[k] = (float)dk;
+        double o2 = 0.0;
+        if (k >= 1) {
+            const double c = 2.0 * k + ab;
+            o2 = 4.0 * k * (k + a) * (k + b) * (k + ab) / (c * c * (c + 1.0) * (c - 1.0));
+        }
+        be[k] = o2;
+        sq[k] = sqrt(o2);
+        fbe[k] = (float)o2;
+    }
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float lo = -1.0f, hi = 1.0f;
+    for (int it = 0; it < 26; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        float q = fal[0] - mid;
+        int cnt = (q < 0.0f);
+        for (int k = 1; k < n; ++k) {
+            if (q == 0.0f) q = 1e-30f;
+            q = (fal[k] - mid) - fbe[k] / q;
+            cnt += (q < 0.0f);
+        }
+        if (cnt > j) hi = mid; else lo = mid;
+    }
+    double x = 0.5 * ((double)lo + (double)hi);
+    for (int it = 0; it < 6; ++it) {
+        double p0 = 1.0, p1 = x - al[0], d0 = 0.0, d1 = 1.0;
+        for (int k = 1; k < n; ++k) {
+            const double u = x - al[k];
+            const double p2 = u * p1 - be[k] * p0;
+            const double d2 = p1 + u * d1 - be[k] * d0;
+            p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+        }
+        x -= p1 / d1;
+    }
+    const double mu0 = exp2(ab + 1.0) * tgamma(a + 1.0) * tgamma(b + 1.0) / tgamma(ab + 2.0);
+    double pm = 0.0, pk = 1.0 / sqrt(mu0), sum = pk * pk;
+    for (int k = 0; k + 1 < n; ++k) {
+        const double pn = ((x - al[k]) * pk - sq[k] * pm) / sq[k + 1];
+        pm = pk;
+        pk = pn;
+        sum = fma(pk, pk, sum);
+    }
+    nodes[j] = x;
+    wts[j] = 1.0 / sum;
+}
+
+int launch_gauss_jacobi(int n, double a, double b, double *nodes, double *wts, cudaStream_t s) {
+    if (n < 1 || n > kMaxNp || !(a > -1.0) || !(b > -1.0)) return CQ_EINVAL;
+    k_gauss_jacobi<<<(n + kGJThreads - 1) / kGJThreads, kGJThreads, 0, s>>>(n, a, b, nodes, wts);
+    return launched();
+}
+
+// ---------------------------------------------------------------------------
+// Fast-form coefficients (Eqs. 3.6-3.7 for BE; Eqs. 3.14-3.16 with the real
+// parts of Remark 3.2 for BDF2). K = 1/(tau^beta Gamma(1-beta) Gamma(beta)).
+//   BE:    r = (s+1)/2,       c = w = -K lambda / 4
+//   fam 1: r = (s+1)/(s+5),   c = w1 (s+5)^-4 r^(Ns-3),  w1 = -2^(2+2beta) cos(pi beta) K lambda1
+//   fam 2: r = (s+1)/2,       c = w2 Re((1+3s)^beta) r^(Ns-3),  w2 = -2^(-beta-3) K lambda2
+// The history part of a point is c * Y with Y <- r Y + G(t_{n-L}).
+// ---------------------------------------------------------------------------
+__global__ void k_fast_coeffs(int scheme, double beta, double tau, int np1, int np2, int ns,
+                              const double *__restrict__ s1, const double *__restrict__ l1,
+                              const double *__restrict__ s2, const double *__restrict__ l2,
+                              double *__restrict__ r, double *__restrict__ c) {
+    const int np = (scheme == CQ_BE) ? np1 : np1 + np2;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const double K = 1.0 / (pow(tau, beta) * tgamma(1.0 - beta) * tgamma(beta));
+    if (scheme == CQ_BE) {
+        const double s = s1[j];
+        r[j] = 0.5 * (s + 1.0);
+        c[j] = -0.25 * K * l1[j];
+    } else if (j < np1) {
+        const double s = s1[j];
+        const double rr = (s + 1.0) / (s + 5.0);
+        const double w = -exp2(2.0 + 2.0 * beta) * cospi(beta) * K * l1[j];
+        const double s5 = s + 5.0;
+        r[j] = rr;
+        c[j] = w / (s5 * s5 * s5 * s5) * pow(rr, (double)(ns - 3));
+    } else {
+        const int k = j - np1;
+        const double s = s2[k];
+        const double rr = 0.5 * (s + 1.0);
+        const double w = -exp2(-beta - 3.0) * K * l2[k];
+        const double u = 1.0 + 3.0 * s;
+        const double re = (u >= 0.0) ? pow(u, beta) : pow(-u, beta) * cospi(beta);
+        r[j] = rr;
+        c[j] = w * re * pow(rr, (double)(ns - 3));
+    }
+}
+
+int launch_fast_coeffs(int scheme, double beta, double tau, int np1, int np2, int ns,
+                       const double *nodes1, const double *w1, const double *nodes2, const double *w2,
+                       double *r_out, double *c_out, cudaStream_t s) {
+    const int np = (scheme == CQ_BE) ? np1 : np1 + np2;
+    k_fast_coeffs<<<(np + 127) / 128, 128, 0, s>>>(scheme, beta, tau, np1, np2, ns, nodes1, w1, nodes2, w2,
+                                                    r_out, c_out);
+    return launched();
+}
+
+size_t fast_coeff_scratch_bytes(int np1, int np2) {
+    return align_up((size_t)2 * (np1 + np2) * sizeof(double));
+}
+
+int build_fast_coeffs(int scheme, double beta, double tau, int np1, int np2, int ns, double *scratch,
+                      double *r_out, double *c_out, cudaStream_t s) {
+    double *n1 = scratch, *w1 = scratch + np1;
+    double *n2 = scratch + 2 * np1, *w2 = n2 + np2;
+    int st;
+    if (scheme == CQ_BE) {
+        if ((st = launch_gauss_jacobi(np1, beta, 1.0 - beta, n1, w1, s))) return st;
+    } else {
+        if ((st = launch_gauss_jacobi(np1, beta, 2.0 - 2.0 * beta, n1, w1, s))) return st;
+        if ((st = launch_gauss_jacobi(np2, beta, 2.0 - 2.0 * beta, n2, w2, s))) return st;
+    }
+    return launch_fast_coeffs(scheme, beta, tau, np1, np2, ns, n1, w1, n2, w2, r_out, c_out, s);
+}
+
+// ---------------------------------------------------------------------------
+// Spatial operator: lambda_k = 4 (M+1)^2 sin^2(k pi / (2(M+1))), 2D sums over
+// (ky, kx) with mode = ky*M + kx; DST-I S_{jk} = sqrt(2/(M+1)) sin(j k pi/(M+1))
+// with the angle reduced exactly in integers before sinpi.
+// ---------------------------------------------------------------------------
+__global__ void k_mode_eigenvalues(int M, int dim, double *__restrict__ lam) {
+    const int64_t total = (dim == 1) ? M : (int64_t)M * M;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const double q = 2.0 * (M + 1);
+    const double f = 4.0 * (double)(M + 1) * (double)(M + 1);
+    if (dim == 1) {
+        const double sv = sinpi((double)(i + 1) / q);
+        lam[i] = f * sv * sv;
+    } else {
+        const int ky = (int)(i / M), kx = (int)(i % M);
+        const double sy = sinpi((double)(ky + 1) / q), sx = sinpi((double)(kx + 1) / q);
+        lam[i] = f * sy * sy + f * sx * sx;
+    }
+}
+
+int launch_mode_eigenvalues(int M, int dim, double *lam, cudaStream_t s) {
+    const int64_t total = (dim == 1) ? M : (int64_t)M * M;
+    k_mode_eigenvalues<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, dim, lam);
+    return launched();
+}
+
+__global__ void k_dst_matrix(int M, double *__restrict__ S) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * M) return;
+    const int64_t j = i / M + 1, k = i % M + 1;
+    const int64_t per = 2 * (int64_t)(M + 1);
+    const int64_t r = (j * k) % per;
+    S[i] = sqrt(2.0 / (M + 1)) * sinpi((double)r / (double)(M + 1));
+}
+
+int launch_dst_matrix(int M, double *S, cudaStream_t s) {
+    const int64_t total = (int64_t)M * M;
+    k_dst_matrix<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, S);
+    return launched();
+}
+
+// ---------------------------------------------------------------------------
+// Small FP64 GEMM C = A B (M x M, row-major), batched over blockIdx.z.
+// 64x64 tile per block, 16x16 threads with 4x4 register tiles, K step 16.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dgemm_square(int M, const double *__restrict__ A, int64_t sA,
+                                                      const double *__restrict__ B, int64_t sB,
+                                                      double *__restrict__ C, int64_t sC) {
+    __shared__ double As[16][64 + 1];
+    __shared__ double Bs[16][64 + 1];
+    A += blockIdx.z * sA;
+    B += blockIdx.z * sB;
+    C += blockIdx.z * sC;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < M; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int kk = e & 15, rr = e >> 4;          // A tile: rows row0.., cols k0..
+            const int r = row0 + rr, k = k0 + kk;
+            As[kk][rr] = (r < M && k < M) ? A[(int64_t)r * M + k] : 0.0;
+            const int cc = e & 63, kb = e >> 6;          // B tile: rows k0.., cols col0..
+            const int kb2 = k0 + kb, c = col0 + cc;
+            Bs[kb][cc] = (kb2 < M && c < M) ? B[(int64_t)kb2 * M + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b[i] = Bs[kk][tx + 16 * i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], b[jj], acc[i][jj]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * jj;
+            if (r < M && c < M) C[(int64_t)r * M + c] = acc[i][jj];
+        }
+}
+
+int launch_dgemm_square(int M, int batch, const double *A, int64_t sA, const double *B, int64_t sB, double *C,
+                        int64_t sC, cudaStream_t s) {
+    dim3 grid((M + 63) / 64, (M + 63) / 64, batch);
+    k_dgemm_square<<<grid, 256, 0, s>>>(M, A, sA, B, sB, C, sC);
+    return launched();
+}
+
+// 1D: out[s][k] = sum_j S[k][j] in[s][j]
+__global__ void k_dst_1d(int M, const double *__restrict__ S, const double *__restrict__ in,
+                         double *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int st = blockIdx.y;
+    if (k >= M) return;
+    double acc = 0.0;
+    for (int j = 0; j < M; ++j) acc = fma(S[(int64_t)k * M + j], in[(int64_t)st * M + j], acc);
+    out[(int64_t)st * M + k] = acc;
+}
+
+int launch_dst_field(int M, int dim, const double *S, const double *in, double *out, double *tmp, cudaStream_t s) {
+    if (dim == 1) {
+        k_dst_1d<<<dim3((M + 127) / 128, 2), 128, 0, s>>>(M, S, in, out);
+        return launched();
+    }
+    const int64_t mm = (int64_t)M * M;
+    int st = launch_dgemm_square(M, 2, S, 0, in, mm, tmp, mm, s);      // S F
+    if (st) return st;
+    return launch_dgemm_square(M, 2, tmp, mm, S, 0, out, mm, s);       // (S F) S
+}
+
+}  // namespace fastcq
+
+using namespace fastcq;
+
+extern "C" int cq_weights(int32_t scheme, double beta, double tau, int64_t n, double *w_dev, void *stream) {
+    if ((scheme != CQ_BE && scheme != CQ_BDF2) || bad_order(beta) || !(tau > 0.0) || n < 0 ||
+        n > kMaxWeights || !w_dev)
+        return CQ_EINVAL;
+    return launch_weights(scheme, beta, tau, n, w_dev, (cudaStream_t)stream);
+}
+
+extern "C" int cq_gauss_jacobi(int32_t n, double a, double b, double *nodes_dev, double *weights_dev,
+                               void *stream) {
+    if (!nodes_dev || !weights_dev) return CQ_EINVAL;
+    return launch_gauss_jacobi(n, a, b, nodes_dev, weights_dev, (cudaStream_t)stream);
+}
+
+extern "C" int cq_fast_coeffs(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
+                              double *coef_dev, void *ws_dev, size_t *ws_bytes, void *stream) {
+    if (!cfg || !ws_bytes || (scheme != CQ_BE && scheme != CQ_BDF2) || bad_order(beta) || !(tau > 0.0))
+        return CQ_EINVAL;
+    const int np1 = cfg->np1, np2 = (scheme == CQ_BE) ? 0 : cfg->np2, ns = cfg->ns;
+    if (np1 < 1 || np2 < 0 || np1 + np2 > kMaxNp || (scheme == CQ_BDF2 && (np2 < 1 || ns < 3 || ns > kMaxNs)))
+        return CQ_EINVAL;
+    const size_t need = fast_coeff_scratch_bytes(np1, np2);
+    if (!ws_dev) { *ws_bytes = need; return CQ_OK; }
+    if (*ws_bytes < need) return CQ_ENOMEM;
+    if (!coef_dev) return CQ_EINVAL;
+    const int np = np1 + np2;
+    return build_fast_coeffs(scheme, beta, tau, np1, np2, ns, (double *)ws_dev, coef_dev, coef_dev + np,
+                             (cudaStream_t)stream);
+}

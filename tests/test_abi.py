@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI: the library builds, loads, exports every
+function declared in include/fastcq.h, and rejects invalid arguments before
+touching the GPU (size queries and argument errors need no device)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_1901_05128_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fc():
+    pkg.build()
+    return pkg.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b((?:cq|fp2s)_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(fc):
+    decl = _declared()
+    assert {"cq_weights", "cq_history_direct", "cq_history_fast", "fp2s_step", "fp2s_solve"} <= decl
+    lib = C.CDLL(fc.LIB_PATH)
+    missing = [n for n in sorted(decl) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(fc.EXPORTS) == decl
+
+
+def test_strerror(fc):
+    assert fc.strerror(0) == "ok"
+    assert "workspace" in fc.strerror(-2)
+
+
+def test_invalid_arguments_rejected_on_host(fc):
+    lib = fc._lib
+    assert lib.cq_weights(1, 1.5, 0.1, 10, None, None) == fc.CQ_EINVAL
+    assert lib.cq_weights(3, 0.5, 0.1, 10, None, None) == fc.CQ_EINVAL
+    assert lib.cq_weights(1, 0.5, -0.1, 10, None, None) == fc.CQ_EINVAL
+    assert lib.cq_gauss_jacobi(0, 0.5, 0.5, None, None, None) == fc.CQ_EINVAL
+    assert lib.cq_gauss_jacobi(300, 0.5, 0.5, 8, 8, None) == fc.CQ_EINVAL
+    sz = C.c_size_t(0)
+    assert lib.cq_history_direct(1, 0.5, 0.1, 10, 0, 5, None, 10, None, 10, 0, None, C.byref(sz), None) == fc.CQ_EINVAL
+    assert lib.cq_history_direct(1, 0.5, 0.1, 10, 1, 5, None, 10, None, 10, 2, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
+    cfg = fc.FastCfg(8, 8, 2)
+    assert lib.cq_history_fast(2, 0.5, 0.1, C.byref(cfg), 10, 1, None, None, 0, None, C.byref(sz), None) == fc.CQ_EINVAL
+
+
+@pytest.mark.parametrize("m", [0.5, 1.0, -0.1])
+def test_problem_validation(fc, m):
+    p = fc.problem(0.3, 0.7, m, 1.0, 64, 1, 15)
+    sz = C.c_size_t(0)
+    assert fc._lib.fp2s_solve(C.byref(p), None, None, None, C.byref(sz), None) == fc.CQ_EINVAL
+
+
+def test_size_queries_need_no_device(fc):
+    p = fc.problem(0.4, 0.6, 0.49, 1.0, 4096, 2, 255, fc.CQ_BDF2, fc.CQ_FAST, 16, 64, 17)
+    n_fast = fc.fp2s_solve(p, None, None, None)
+    assert 0 < n_fast < 64 << 20            # tables and modal vectors only: the state lives on chip
+    pd = fc.problem(0.4, 0.6, 0.49, 1.0, 4096, 2, 255, fc.CQ_BDF2, fc.CQ_DIRECT)
+    n_dir = fc.fp2s_solve(pd, None, None, None)
+    assert n_dir >= 4097 * 2 * 255 * 255 * 8  # the full modal history
+    assert fc.fp2s_init(p, None, None) > n_fast
+    n_h = fc.cq_history_direct(1, 0.3, 1e-3, 1000, 1, 512, None, 1000, None, 1000)
+    assert n_h >= 512 * 8
+    n_f = fc.cq_history_fast(2, 0.3, 1e-3, 16, 64, 17, 1000, 1, None, None)
+    assert n_f >= (80 + 17) * 1000 * 8
+
+
+def test_workspace_too_small(fc):
+    import torch
+    p = fc.problem(0.4, 0.6, 0.3, 1.0, 64, 1, 15)
+    small = torch.empty(256, dtype=torch.uint8)
+    sz = C.c_size_t(256)
+    st = fc._lib.fp2s_solve(C.byref(p), 1 << 20, 1 << 20, small.data_ptr(), C.byref(sz), None)
+    assert st == fc.CQ_ENOMEM
