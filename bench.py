@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the CQ history hot path on GB300.
+
+Workload (one "step" = one whole fp2s_solve: CQ weights, Gauss-Jacobi fast
+coefficients, forward sine transform, all N time steps with the history sums
+and the per-mode 2x2 solves, inverse sine transform):
+  2D unit square, 255 x 255 interior finite-difference points (2 x 65025 DOF),
+  T = 1, N = 4096, BDF2 (SBD) scheme, alpha = (0.4, 0.6), m = 0.49, fast form
+  with N_p1 = 16, N_p2 = 64, N_s = 17, FP64; G0 = seeded U[0,1) on an 8x8
+  checkerboard, times 2^-1000 (the problem is linear; the factor keeps the mode
+  that grows like e^(1096 t) finite without changing the arithmetic).
+The same workload is also timed in the direct form ("direct" sub-object).
+
+value = DOF x N / (device time of one step), summed over ranks (weak scaling:
+every rank solves its own instance). L2 is flushed (256 MiB write) before
+every timed step, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CQ history DOF·steps/s (fast vs direct, FP64 vs mixed) at stated error; grad steps/s"
+UNIT = "DOF·steps/s"
+WORKLOAD = "bdf2_2d_m255"
+SCALE = 2.0 ** -1000
+FP64_PEAK_NOMINAL = 1.25e12       # FP64 FLOP/s of GB300 (2 DFMA / clock / SM x 152 SMs x ~2.07 GHz)
+FP64_PEAK_PROBE = 1.199e12        # own DFMA-chain probe on this machine's GB300 (independent FMA chains)
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def workload_config(p):
+    return {
+        "workload": "%s: 2D %dx%d FD grid (%d DOF), T=%g, N=%d, BDF2, alpha=(%g,%g), m=%g, fast np1=%d np2=%d Ns=%d, "
+                    "G0 = U[0,1) checkerboard x 2^-1000" % (WORKLOAD, p.M, p.M, p.ndof, p.T, p.N, p.alpha1,
+                                                           p.alpha2, p.m, p.np1, p.np2, p.ns),
+        "dof": p.ndof, "N": p.N, "scheme": "BDF2", "form": "fast", "precision": "FP64",
+        "l2": "flushed before every timed step (256 MiB write), outside the timed events",
+    }
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) legs
+def oracle_sample(p, G0, n_modes, seed):
+    """Time the oracle's plain per-mode scheme on a seeded sample of sine modes."""
+    import numpy as np
+    from oracle import scheme as OS
+    from oracle import spatial as OSP
+    import cq_inputs as ci
+
+    nm = p.M ** p.dim
+    sample = ci.sample_indices(nm, n_modes, seed)
+    lam = OSP.mode_eigenvalues(p.M, p.dim)[sample]
+    g0 = OSP.to_modal(G0, p.M, p.dim)[:, sample]
+    t = time.perf_counter()
+    g = OS.solve_modal(p, lam, g0)
+    dt = time.perf_counter() - t
+    return sample, g[p.N], dt
+
+
+def cpu_cores_used():
+    return 1        # the oracle's time loop is numpy element-wise work on one thread
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + SMI_FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    import cq_inputs as ci
+    import paper_1901_05128_gb300 as pkg
+
+    pkg.build()
+    fc = pkg.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p, G0 = ci.workload(WORKLOAD)
+    if rank:
+        G0 = ci.g0_checkerboard_uniform(p.M, ci.SEED_BASE + 1 + 1000 * rank)
+    G0 = G0 * SCALE
+    flags = fc.FP2S_ASYNC
+
+    def cproblem(q):
+        return fc.problem(q.alpha1, q.alpha2, q.m, q.T, q.N, q.dim, q.M, q.scheme, q.form, q.np1, q.np2, q.ns,
+                          flags=flags)
+
+    g0 = torch.tensor(G0, dtype=torch.float64, device=dev)
+    gN = torch.empty_like(g0)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > 2x L2
+    fc.cq_timing_enable(True)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(q, K, W):
+        cp = cproblem(q)
+        ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
+        for _ in range(W):
+            fc.fp2s_solve(cp, g0, gN, ws)
+        st = fc.fp2s_status(cp, ws)
+        if st not in (fc.CQ_OK,):
+            raise RuntimeError("warm-up solve failed: %s" % fc.strerror(st))
+        barrier()
+        torch.cuda.synchronize()
+        l0 = fc.cq_launch_count()
+        steps, mains = [], []
+        for _ in range(K):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fc.fp2s_solve(cp, g0, gN, ws)
+            e1.record()
+            e1.synchronize()
+            steps.append(e0.elapsed_time(e1))
+            mains.append(fc.cq_timing_last())
+        torch.cuda.synchronize()
+        barrier()
+        launches = fc.cq_launch_count() - l0
+        st = fc.fp2s_status(cp, ws)
+        return steps, mains, launches, st
+
+    K, W = args.steps, args.warmup
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        steps, mains, launches, st_fast = timed(p, K, W)
+        gN_fast = gN.cpu().numpy()
+        pd = p.replace(form=ci.DIRECT)
+        Kd, Wd = max(1, min(K, 4)), max(1, min(W, 1))
+        d_steps, d_mains, d_launches, st_dir = timed(pd, Kd, Wd)
+        gN_dir = gN.cpu().numpy()
+        # end to end through the public API with pinned host buffers
+        cp = cproblem(p)
+        ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
+        h_in = torch.tensor(G0, dtype=torch.float64).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        fc.fp2s_solve(cp, g0, gN, ws)
+        barrier()
+        torch.cuda.synchronize()
+        e2e = []
+        for _ in range(K):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g0.copy_(h_in, non_blocking=True)
+            fc.fp2s_solve(cp, g0, gN, ws)
+            h_out.copy_(gN, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            e2e.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        barrier()
+    clocks = clk.summary()
+
+    ms = statistics.mean(steps)
+    ms_main = statistics.mean(mains)
+    ms_dir = statistics.mean(d_steps)
+    ms_e2e = statistics.mean(e2e)
+    if dist is not None:
+        t = torch.tensor([ms, ms_dir, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_dir, ms_e2e = t.tolist()
+    units = p.ndof * p.N
+    value = world * units / (ms * 1e-3)
+    if rank != 0:
+        return None
+
+    # roofline of the dominant kernel (fused fast solve): FP64-pipe bound
+    hist_flops_per_dof_step = 4 * (p.np1 + p.np2) + 2 * (p.ns - 1)
+    flops_per_launch = hist_flops_per_dof_step * units
+    achieved = flops_per_launch / (ms_main * 1e-3)
+    roofline = {"kernel": "k_fp2s_fast", "bound": "alu", "unit": "TFLOP/s",
+                "achieved": achieved / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
+                "frac": achieved / FP64_PEAK_NOMINAL, "peak_source": "nominal FP64 rate (recipe); own DFMA probe "
+                "measured %.3f TFLOP/s" % (FP64_PEAK_PROBE / 1e12),
+                "traffic": None, "algorithmic_flops_per_launch": flops_per_launch,
+                "flops_per_dof_step": hist_flops_per_dof_step, "kernel_ms": ms_main,
+                "kernel_share_of_step": ms_main / ms}
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tr = json.load(open(prof)).get("k_fp2s_fast")
+            if tr and tr.get("source_hash") == _kernel_hash():
+                roofline["traffic"] = tr["dram_bytes_per_launch"]
+        except (OSError, ValueError):
+            pass
+
+    # oracle leg: bounded sample, also gives the error of this run
+    import numpy as np
+    from oracle import spatial as OSP
+    sample, ref_fast, t_fast = oracle_sample(p, G0, args.cpu_modes, ci.SEED_BASE + 21)
+    sample_d, ref_dir, t_dir = oracle_sample(p.replace(form=ci.DIRECT), G0, max(4, args.cpu_modes // 64),
+                                             ci.SEED_BASE + 22)
+
+    def rel_err(gN_phys, sample_idx, ref):
+        ghat = OSP.to_modal(gN_phys, p.M, p.dim)[:, sample_idx]
+        floor = 1e-13 * np.max(np.abs(ref))
+        return float(np.max(np.abs(ghat - ref) / (np.abs(ref) + floor)))
+
+    err_fast = rel_err(gN_fast, sample, ref_fast)
+    err_dir = rel_err(gN_dir, sample_d, ref_dir)
+    fd = OSP.to_modal(gN_fast, p.M, p.dim) - OSP.to_modal(gN_dir, p.M, p.dim)
+    fast_vs_direct = float(np.linalg.norm(fd) / np.linalg.norm(OSP.to_modal(gN_dir, p.M, p.dim)))
+    cpu_value = 2 * len(sample) * p.N / t_fast
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded; see config)", "config": workload_config(p),
+        "roofline": roofline,
+        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": "oracle fast SBD scheme, %d seeded sine modes x all %d steps (%.1f s)"
+                                   % (len(sample), p.N, t_fast)},
+        "e2e": {"value": world * units / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(G0.size * 8), "d2h_bytes_per_step": int(G0.size * 8),
+                "ms_per_step": ms_e2e},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "error": {"fast_vs_oracle_max_rel_modal": err_fast, "direct_vs_oracle_max_rel_modal": err_dir,
+                  "fast_vs_direct_rel_l2": fast_vs_direct, "status": fc.strerror(st_fast)},
+        "direct": {"value": world * units / (ms_dir * 1e-3), "unit": UNIT, "ms_per_step": ms_dir, "steps": Kd,
+                   "warmup": Wd, "kernel": "k_fp2s_direct<8>", "kernel_ms": statistics.mean(d_mains),
+                   "gpu_launches": int(d_launches), "status": fc.strerror(st_dir),
+                   "cpu_baseline": {"value": 2 * len(sample_d) * p.N / t_dir, "unit": UNIT, "cores": 1,
+                                    "kind": "oracle", "sample": "oracle direct SBD scheme, %d modes x %d steps "
+                                    "(%.1f s)" % (len(sample_d), p.N, t_dir)}},
+        "device": torch.cuda.get_device_name(),
+    }
+    return out
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fp2s.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1901_05128_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import cq_inputs as ci
+    p, G0 = ci.workload(WORKLOAD)
+    G0 = G0 * SCALE
+    n = args.ref_modes
+    for w in range(args.warmup):
+        oracle_sample(p.replace(N=64, T=p.T * 64 / p.N), G0, n, ci.SEED_BASE + 30 + w)
+    times = []
+    for k in range(args.steps):
+        _, _, dt = oracle_sample(p, G0, n, ci.SEED_BASE + 40 + k)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = 2 * n * p.N / (ms * 1e-3)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; see config)",
+            "config": workload_config(p),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                             "sample": "each step: oracle fast SBD scheme on %d seeded sine modes x all %d steps "
+                                       "(warm-up steps use N=64)" % (n, p.N)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-modes", type=int, default=1024, help="sine modes of the oracle's timed sample")
+    ap.add_argument("--ref-modes", type=int, default=256, help="sine modes per step of the reference arm")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "ours":
+        import torch
+        if world > 1:
+            import torch.distributed as tdist
+            local = int(os.environ.get("LOCAL_RANK", "0"))
+            torch.cuda.set_device(local)
+            tdist.init_process_group("nccl")
+            dist = tdist
+        out = run_ours(args, rank, world, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+    else:
+        out = run_reference(args, rank, world)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
