@@ -7,7 +7,8 @@
  *
  * C ABI. Every pointer named *_dev is CUDA device memory owned by the caller;
  * *_host is host memory owned by the caller. The library never allocates
- * device memory: entry points that need scratch take a caller workspace
+ * device memory at call time (cq_history_fast_noalloc uses one fixed array
+ * that exists from load): entry points that need scratch take a caller workspace
  * (ws_dev, ws_bytes). Passing ws_dev == NULL turns such a call into a size
  * query: *ws_bytes receives the required size and nothing runs. Workspaces
  * must be 256-byte aligned (cudaMalloc / torch allocations are).
@@ -115,6 +116,28 @@ int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof,
 int cq_history_fast(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
                     int64_t ndof, int64_t n, const double *G_prev_dev, double *H_dev,
                     int32_t prec, void *ws_dev, size_t *ws_bytes, void *stream);
+
+/* ---- allocation-free fast history (no counterpart in the paper) --------- */
+/* Same computation, arguments and call order as cq_history_fast, but with no
+ * workspace argument. It is meant for callers that cannot allocate device
+ * memory: a plug-in that is handed only its input and output arrays by a host
+ * application which owns all device memory; a program whose memory pool is
+ * fully reserved before its time loop; a loop that must not call cudaMalloc,
+ * which can synchronise the device and can fail at an arbitrary step.
+ * The state lives in one library-owned device array of
+ * CQ_NOALLOC_SCRATCH_BYTES (16 MiB) that every device loading the library
+ * keeps until the process exits. A request whose state does not fit
+ * ((np + L) * ndof doubles plus small tables; e.g. ndof <= ~21,600 for
+ * np = 80, L = 17) returns CQ_ENOMEM before any work is enqueued.
+ * The first call on a device (the current device) looks up the array's device
+ * address and caches it: make it before any stream capture. Every call shares
+ * the array, which keeps the last call's contents: the n = 1 call clears the
+ * state, and calls that overlap on the GPU (several problems or streams at
+ * once on one device) race on it. It calls no allocating routine. */
+#define CQ_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int cq_history_fast_noalloc(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
+                            int64_t ndof, int64_t n, const double *G_prev_dev, double *H_dev,
+                            int32_t prec, void *stream);
 
 /* ---- two-state fractional Fokker-Planck system (Eqs. 1.1-1.3, 2.1) ----- */
 /* Problem on (0,1)^dim, dim in {1,2}, with M interior points per axis of the

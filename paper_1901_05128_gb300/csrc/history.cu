@@ -1,6 +1,8 @@
 // History sums over all DOFs: the direct strictly-lower-triangular Toeplitz
 // product (Eq. 3.8) and one step of the fast recurrences (Eqs. 3.9-3.10,
 // 3.17-3.18). FP64.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace fastcq {
@@ -230,4 +232,61 @@ extern "C" int cq_history_fast(int32_t scheme, double beta, double tau, const cq
     k_history_fast_step<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ndof, n, L, np, lay.tab, lay.ring, lay.Y,
                                                                          G_prev_dev, H_dev);
     return launched();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of cq_history_fast.
+//
+// Some callers cannot hand this library a workspace: a plug-in that only
+// receives its input and output arrays from a host application which owns all
+// device memory and exposes no allocator; a program whose memory pool is
+// reserved in full before the time loop starts; a time loop that must not call
+// cudaMalloc because that call can synchronise the device and can fail at an
+// arbitrary step. For them the state of the fast history (Y, the last L levels
+// and the tables) lives in one file-scope device array of fixed size, which
+// every device that loads this library holds until the process exits.
+//
+// The first call on a device looks up the array's device address with
+// cudaGetSymbolAddress (a host-side name of a __device__ array is not a device
+// address) and caches it for that device; make that first call before any
+// stream capture. All calls share the one array and it keeps whatever the last
+// call left in it: the call with n = 1 clears the state before use, and calls
+// that overlap on the GPU (other streams, other threads, two problems at once
+// on one device) race on it.
+// ---------------------------------------------------------------------------
+namespace fastcq {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CQ_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+static int noalloc_scratch_address(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CQ_ECUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return CQ_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CQ_ECUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return CQ_OK;
+}
+
+}  // namespace fastcq
+
+extern "C" int cq_history_fast_noalloc(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
+                                       int64_t ndof, int64_t n, const double *G_prev_dev, double *H_dev,
+                                       int32_t prec, void *stream) {
+    size_t need = 0;
+    int st = cq_history_fast(scheme, beta, tau, cfg, ndof, n, G_prev_dev, H_dev, prec, nullptr, &need, stream);
+    if (st) return st;
+    if (need > CQ_NOALLOC_SCRATCH_BYTES) return CQ_ENOMEM;
+    void *scratch = nullptr;
+    if ((st = noalloc_scratch_address(&scratch))) return st;
+    size_t cap = CQ_NOALLOC_SCRATCH_BYTES;
+    return cq_history_fast(scheme, beta, tau, cfg, ndof, n, G_prev_dev, H_dev, prec, scratch, &cap, stream);
 }

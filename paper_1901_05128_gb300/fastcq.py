@@ -56,6 +56,7 @@ def _load():
         "cq_fast_coeffs": (C.c_int, [I32, D, D, C.POINTER(FastCfg), P, P, SZ, P]),
         "cq_history_direct": (C.c_int, [I32, D, D, I64, I64, I64, P, I64, P, I64, I32, P, SZ, P]),
         "cq_history_fast": (C.c_int, [I32, D, D, C.POINTER(FastCfg), I64, I64, P, P, I32, P, SZ, P]),
+        "cq_history_fast_noalloc": (C.c_int, [I32, D, D, C.POINTER(FastCfg), I64, I64, P, P, I32, P]),
         "fp2s_solve": (C.c_int, [C.POINTER(Problem), P, P, P, SZ, P]),
         "fp2s_init": (C.c_int, [C.POINTER(Problem), P, P, SZ, P]),
         "fp2s_step": (C.c_int, [C.POINTER(Problem), I64, P, C.c_size_t, P, P]),
@@ -71,7 +72,8 @@ def _load():
 
 _lib = _load()
 EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_weights",
-           "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_history_fast", "fp2s_solve",
+           "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_history_fast",
+           "cq_history_fast_noalloc", "fp2s_solve",
            "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status")
 
 
@@ -156,6 +158,15 @@ def cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, n, G_prev_dev, H_dev,
     _check(_lib.cq_history_fast(scheme, beta, tau, C.byref(cfg), ndof, n, _ptr(G_prev_dev), _ptr(H_dev), prec,
                                 _ptr(ws_dev), C.byref(sz), _stream(stream, ws_dev is None)), "cq_history_fast")
     return sz.value
+
+
+def cq_history_fast_noalloc(scheme, beta, tau, np1, np2, ns, ndof, n, G_prev_dev, H_dev, prec=CQ_F64,
+                            stream=None):
+    """cq_history_fast without a workspace: the state lives in the library's own
+    fixed-size device array (for callers that cannot allocate device memory)."""
+    cfg = FastCfg(np1, np2, ns)
+    _check(_lib.cq_history_fast_noalloc(scheme, beta, tau, C.byref(cfg), ndof, n, _ptr(G_prev_dev), _ptr(H_dev),
+                                        prec, _stream(stream)), "cq_history_fast_noalloc")
 
 
 def fp2s_solve(p: Problem, G0_dev, GN_dev, ws_dev=None, stream=None, check=True) -> int:
