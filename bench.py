@@ -62,7 +62,8 @@ def oracle_sample(p, G0, n_modes, seed):
     import cq_inputs as ci
 
     nm = p.M ** p.dim
-    sample = ci.sample_indices(nm, n_modes, seed)
+    lowest = [0, 1, p.M, p.M + 1] if p.dim == 2 else [0, 1]
+    sample = np.unique(np.concatenate([lowest, ci.sample_indices(nm, n_modes, seed)]))
     lam = OSP.mode_eigenvalues(p.M, p.dim)[sample]
     g0 = OSP.to_modal(G0, p.M, p.dim)[:, sample]
     t = time.perf_counter()
@@ -258,9 +259,11 @@ def run_ours(args, rank, world, dist):
         return np.ldexp(x, -e), np.ldexp(ref, -e)
 
     def rel_err(gN_phys, sample_idx, ref):
+        # max error over the sampled modes relative to the largest sampled mode: the
+        # comparison goes through one extra DST, which adds ~eps * max|g| to every mode
         ghat = OSP.to_modal(gN_phys, p.M, p.dim)[:, sample_idx]
         g, r = scaled(ghat, ref)
-        return float(np.max(np.abs(g - r) / (np.abs(r) + 1e-13)))
+        return float(np.max(np.abs(g - r)) / np.max(np.abs(r)))
 
     err_fast = rel_err(gN_fast, sample, ref_fast)
     err_dir = rel_err(gN_dir, sample_d, ref_dir)
@@ -281,7 +284,8 @@ def run_ours(args, rank, world, dist):
                 "ms_per_step": ms_e2e},
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "error": {"fast_vs_oracle_max_rel_modal": err_fast, "direct_vs_oracle_max_rel_modal": err_dir,
+        "error": {"fast_vs_oracle_max_err_rel_to_max_mode": err_fast,
+                  "direct_vs_oracle_max_err_rel_to_max_mode": err_dir,
                   "fast_vs_direct_rel_l2": fast_vs_direct, "status": fc.strerror(st_fast)},
         "direct": {"value": world * units / (ms_dir * 1e-3), "unit": UNIT, "ms_per_step": ms_dir, "steps": Kd,
                    "warmup": Wd, "kernel": "k_fp2s_direct<8>", "kernel_ms": statistics.mean(d_mains),

@@ -49,6 +49,8 @@ extern "C" {
 #define CQ_DIRECT  0   /* plain O(N^2) history (Eq. 3.8 / 4.1 / 4.7) */
 #define CQ_FAST    1   /* fast O(N Np) history (Eqs. 3.9-3.10, 3.17-3.18) */
 #define CQ_F64     0   /* FP64 end to end */
+#define CQ_F32     1   /* precision form of the fast solve: FP32 history state and sums, FP64 tables
+                        * and per-mode matrices, FP64 2x2 step when |a| > 10 (m near 1/2) */
 
 /* Fast-form sizes. BE (Eqs. 3.6-3.10): np1 = Np Gauss-Jacobi points, np2
  * ignored, ns ignored (the exact window of BE is d_1 alone).
@@ -154,7 +156,7 @@ typedef struct {
     int32_t scheme;        /* CQ_BE or CQ_BDF2 */
     int32_t form;          /* CQ_DIRECT or CQ_FAST */
     cq_fast_cfg_t fast;    /* used when form == CQ_FAST */
-    int32_t prec;          /* CQ_F64 */
+    int32_t prec;          /* CQ_F64; CQ_F32 with form == CQ_FAST in fp2s_solve (np1 + np2 <= 128) */
     int32_t flags;
 } fp2s_problem_t;
 

@@ -23,6 +23,7 @@ struct Fp2sParams {
     double a, tau, inv_tau;
     int64_t N, nmodes;
     int scheme, form, np, L;     // np Gauss-Jacobi points per state, L exact window (2 for BE)
+    int prec;                    // CQ_F64 or CQ_F32 (fast form only)
 };
 
 constexpr int kDirBT = 8;        // time block of the fused direct kernel
@@ -32,6 +33,7 @@ struct Fp2sLayout {
     double *d1, *d2, *dz1, *dz2;
     double *tab1, *tab2, *scr1, *scr2;
     double *lam, *S, *tmp, *g0, *gN;
+    float *hdf;                   // FP32 fast form: 0.5*d_i of both states as double-float, [4][N+1]
     double *hist;                 // direct: (N+1) x 2 x nmodes
     double *Y, *ring, *glast;     // step API, fast: 2 x np x nm, 2 x L x nm; both: 2 levels x 2 x nm
     size_t bytes;
@@ -59,6 +61,7 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.g0 = cv.take<double>(2 * nm);
     l.gN = cv.take<double>(2 * nm);
     if (P.form == CQ_DIRECT) l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
+    if (P.prec == CQ_F32) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
     if (stepper) {
         if (P.form == CQ_FAST) {
             l.Y = cv.take<double>((size_t)2 * P.np * nm);
@@ -79,7 +82,8 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     if (p->M < 1 || p->M > (p->dim == 1 ? (1 << 16) : 4096)) return CQ_EINVAL;
     if (p->scheme != CQ_BE && p->scheme != CQ_BDF2) return CQ_EINVAL;
     if (p->form != CQ_DIRECT && p->form != CQ_FAST) return CQ_EINVAL;
-    if (p->prec != CQ_F64) return CQ_EUNSUPPORTED;
+    if (p->prec != CQ_F64 && !(p->prec == CQ_F32 && p->form == CQ_FAST)) return CQ_EUNSUPPORTED;
+    P.prec = p->prec;
     P.a = (1.0 - p->m) / (2.0 * p->m - 1.0);
     P.tau = p->T / (double)p->N;
     P.inv_tau = 1.0 / P.tau;
@@ -158,95 +162,401 @@ __device__ inline void mode_step(const Fp2sParams &P, const ModeConst &mc, int64
 }
 
 // ---------------------------------------------------------------------------
-// Fused fast solve: one thread per mode, all N steps. Shared memory holds the
-// tables, the history-part states Y[s][j][t] and the last L levels R[s][slot][t]
-// (level k in slot k % L) of the block's modes; consecutive threads touch
-// consecutive words, so every access is conflict-free.
+// Fused fast solve. Each mode is carried by two lanes of one warp for all N
+// steps: lane l < 16 holds state 1 and lane l + 16 state 2 of the same mode,
+// so a warp advances 16 modes. A lane owns the history-part states
+// Y[j][tid] and the last L levels R[slot][tid] (level k in slot k % L) of its
+// state in shared memory (column tid: conflict-free); the two lanes of a mode
+// swap e = h (+ G^0 correction) and the right-hand side b with one shuffle
+// each to finish the 2x2 step. Tables are interleaved by state (word 2j + s)
+// so the two half-warps read different banks. Four partial sums break the
+// dependency chain of h = sum_j c_j Y_j.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_fp2s_fast(Fp2sParams P, const double *__restrict__ lam,
-                                                   const double *__restrict__ g0, double *__restrict__ gN,
-                                                   int *__restrict__ status, const double *__restrict__ d1,
-                                                   const double *__restrict__ d2, const double *__restrict__ tab1,
-                                                   const double *__restrict__ tab2) {
-    extern __shared__ double sm[];
-    const int np = P.np, L = P.L, T = blockDim.x, t = threadIdx.x;
-    double *r1 = sm, *c1 = r1 + np, *r2 = c1 + np, *c2 = r2 + np;
-    double *w1 = c2 + np, *w2 = w1 + kMaxNs;
-    double *Y = w2 + kMaxNs;                  // [2][np][T]
-    double *R = Y + (size_t)2 * np * T;       // [2][L][T]
-    for (int i = t; i < np; i += T) {
-        r1[i] = tab1[i];
-        c1[i] = tab1[np + i];
-        r2[i] = tab2[i];
-        c2[i] = tab2[np + i];
-    }
-    for (int i = t; i < L; i += T) {
-        w1[i] = d1[i];
-        w2[i] = d2[i];
-    }
-    for (int j = 0; j < 2 * np; ++j) Y[(size_t)j * T + t] = 0.0;
-    for (int j = 0; j < 2 * L; ++j) R[(size_t)j * T + t] = 0.0;
-    __syncthreads();
-    const int64_t mode = (int64_t)blockIdx.x * T + t;
-    if (mode >= P.nmodes) return;
-    double *Y1 = Y + t, *Y2 = Y + (size_t)np * T + t;
-    double *R1 = R + t, *R2 = R + (size_t)L * T + t;
+constexpr int kFastModesPerWarp = 16;
 
-    const double gz1 = g0[mode], gz2 = g0[P.nmodes + mode];
-    const double d10 = w1[0], d20 = w2[0];
+__global__ void __launch_bounds__(1024) k_fp2s_fast(Fp2sParams P, const double *__restrict__ lam,
+                                                    const double *__restrict__ g0, double *__restrict__ gN,
+                                                    int *__restrict__ status, const double *__restrict__ d1,
+                                                    const double *__restrict__ d2, const double *__restrict__ tab1,
+                                                    const double *__restrict__ tab2) {
+    extern __shared__ double sm[];
+    const int np = P.np, L = P.L, T = blockDim.x, tid = threadIdx.x;
+    double *rt = sm;                          // rt[2j + s] = r_j of state s
+    double *ct = rt + 2 * np;                 // ct[2j + s] = c_j of state s
+    double *wt = ct + 2 * np;                 // wt[2i + s] = d_i of state s, i < L
+    double *Y = wt + 2 * kMaxNs;              // [np][T]
+    double *R = Y + (size_t)np * T;           // [L][T]
+    for (int i = tid; i < np; i += T) {
+        rt[2 * i] = tab1[i];
+        rt[2 * i + 1] = tab2[i];
+        ct[2 * i] = tab1[np + i];
+        ct[2 * i + 1] = tab2[np + i];
+    }
+    for (int i = tid; i < L; i += T) {
+        wt[2 * i] = d1[i];
+        wt[2 * i + 1] = d2[i];
+    }
+    for (int j = 0; j < np; ++j) Y[(size_t)j * T + tid] = 0.0;
+    for (int j = 0; j < L; ++j) R[(size_t)j * T + tid] = 0.0;
+    __syncthreads();
+
+    const int lane = tid & 31, st = lane >> 4;            // st: 0 = state 1, 1 = state 2
+    const int64_t mode_raw = ((int64_t)blockIdx.x * (T >> 5) + (tid >> 5)) * kFastModesPerWarp + (lane & 15);
+    const bool active = mode_raw < P.nmodes;
+    const int64_t mode = active ? mode_raw : 0;           // idle lanes still take part in the shuffles
+    const double *rs = rt + st, *cs = ct + st, *ws = wt + st;
+    const double *dn = st ? d2 : d1;
+    double *Yc = Y + tid, *Rc = R + tid;
+
+    const double gz = g0[st * P.nmodes + mode];
+    const double d_s0 = ws[0], d_o0 = wt[1 - st];
     ModeConst mc;
-    if (!mode_setup(P, lam[mode], d10, d20, mc)) atomicOr(status, ST_SINGULAR);
-    double gm1_1 = gz1, gm1_2 = gz2, gm2_1 = 0.0, gm2_2 = 0.0;
-    int slot = 0;                              // n % L
+    const bool ok = mode_setup(P, lam[mode], st ? d_o0 : d_s0, st ? d_s0 : d_o0, mc);
+    if (active && st == 0 && !ok) atomicOr(status, ST_SINGULAR);
+    // own row of the inverse step matrices, ordered (own, other)
+    const double mn_oo = st ? mc.Mn.i22 : mc.Mn.i11, mn_ot = st ? mc.Mn.i21 : mc.Mn.i12;
+    const double m1_oo = st ? mc.M1.i22 : mc.M1.i11, m1_ot = st ? mc.M1.i21 : mc.M1.i12;
+    const double a = P.a, c = mc.c;
+    double gm1 = gz, gm2 = 0.0;
+    int slot = 0;                                           // n % L
     for (int64_t n = 1; n <= P.N; ++n) {
         slot = (slot + 1 == L) ? 0 : slot + 1;
-        double h1 = 0.0, h2 = 0.0;
+        double h0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0;
         if (n - L >= 1) {
-            const double in1 = R1[(size_t)slot * T], in2 = R2[(size_t)slot * T];
-#pragma unroll 4
-            for (int j = 0; j < np; ++j) {
-                const double y1 = fma(r1[j], Y1[(size_t)j * T], in1);
-                const double y2 = fma(r2[j], Y2[(size_t)j * T], in2);
-                Y1[(size_t)j * T] = y1;
-                Y2[(size_t)j * T] = y2;
-                h1 = fma(c1[j], y1, h1);
-                h2 = fma(c2[j], y2, h2);
+            const double in = Rc[(size_t)slot * T];
+            int j = 0;
+            for (; j + 4 <= np; j += 4) {
+                const double y0 = fma(rs[2 * j], Yc[(size_t)j * T], in);
+                const double y1 = fma(rs[2 * j + 2], Yc[(size_t)(j + 1) * T], in);
+                const double y2 = fma(rs[2 * j + 4], Yc[(size_t)(j + 2) * T], in);
+                const double y3 = fma(rs[2 * j + 6], Yc[(size_t)(j + 3) * T], in);
+                Yc[(size_t)j * T] = y0;
+                Yc[(size_t)(j + 1) * T] = y1;
+                Yc[(size_t)(j + 2) * T] = y2;
+                Yc[(size_t)(j + 3) * T] = y3;
+                h0 = fma(cs[2 * j], y0, h0);
+                h1 = fma(cs[2 * j + 2], y1, h1);
+                h2 = fma(cs[2 * j + 4], y2, h2);
+                h3 = fma(cs[2 * j + 6], y3, h3);
+            }
+            for (; j < np; ++j) {
+                const double y = fma(rs[2 * j], Yc[(size_t)j * T], in);
+                Yc[(size_t)j * T] = y;
+                h0 = fma(cs[2 * j], y, h0);
             }
         }
         const int imax = (int)min((int64_t)(L - 1), n - 1);
         int sl = slot;
         for (int i = 1; i <= imax; ++i) {
-            sl = (sl == 0) ? L - 1 : sl - 1;   // slot of level n - i
-            h1 = fma(w1[i], R1[(size_t)sl * T], h1);
-            h2 = fma(w2[i], R2[(size_t)sl * T], h2);
+            sl = (sl == 0) ? L - 1 : sl - 1;                // slot of level n - i
+            if (i & 1) h1 = fma(ws[2 * i], Rc[(size_t)sl * T], h1);
+            else h2 = fma(ws[2 * i], Rc[(size_t)sl * T], h2);
         }
-        double d1n = 0.0, d2n = 0.0;
-        if (P.scheme == CQ_BDF2 && n >= 2) {
-            d1n = __ldg(d1 + n - 1);
-            d2n = __ldg(d2 + n - 1);
+        const double h = (h0 + h1) + (h2 + h3);
+        double e, lead, m_oo = mn_oo, m_ot = mn_ot;
+        if (P.scheme == CQ_BE) {
+            e = h;
+            lead = gm1 * P.inv_tau;
+        } else if (n == 1) {
+            e = d_s0 * gz * (1.0 / 3.0);
+            lead = gz * P.inv_tau;
+            m_oo = m1_oo;
+            m_ot = m1_ot;
+        } else {
+            e = fma(0.5 * __ldg(dn + n - 1), gz, h);
+            lead = (2.0 * gm1 - 0.5 * gm2) * P.inv_tau;
         }
-        double x1, x2;
-        mode_step(P, mc, n, h1, h2, d10, d20, d1n, d2n, gm1_1, gm1_2, gm2_1, gm2_2, gz1, gz2, x1, x2);
-        R1[(size_t)slot * T] = x1;
-        R2[(size_t)slot * T] = x2;
-        gm2_1 = gm1_1;
-        gm2_2 = gm1_2;
-        gm1_1 = x1;
-        gm1_2 = x2;
+        const double e_o = __shfl_xor_sync(0xffffffffu, e, 16);
+        const double b = lead - c * e + a * e_o;
+        const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
+        const double x = m_oo * b + m_ot * b_o;
+        Rc[(size_t)slot * T] = x;
+        gm2 = gm1;
+        gm1 = x;
     }
-    gN[mode] = gm1_1;
-    gN[P.nmodes + mode] = gm1_2;
-    if (!isfinite(gm1_1) || !isfinite(gm1_2)) atomicOr(status, ST_NONFINITE);
+    if (active) {
+        gN[st * P.nmodes + mode] = gm1;
+        if (!isfinite(gm1)) atomicOr(status, ST_NONFINITE);
+    }
 }
 
 static size_t fast_smem_bytes(int np, int L, int T) {
-    return ((size_t)4 * np + 2 * kMaxNs + (size_t)2 * (np + L) * T) * sizeof(double);
+    return ((size_t)4 * np + 2 * kMaxNs + (size_t)(np + L) * T) * sizeof(double);
 }
 
-static int fast_block_threads(int np, int L) {
-    for (int T = 256; T >= 32; T -= 32)
-        if (fast_smem_bytes(np, L, T) <= 220 * 1024) return T;
-    return 0;
+static int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// Warps per block: the largest that fits shared memory among those whose grid
+// fills whole waves best (one block per SM).
+static int fast_block_threads(int np, int L, int64_t nmodes) {
+    const size_t limit = 227 * 1024;
+    const int sms = num_sms();
+    int best = 0;
+    double best_eff = -1.0;
+    for (int wb = 32; wb >= 1; --wb) {
+        if (fast_smem_bytes(np, L, 32 * wb) > limit) continue;
+        const int64_t blocks = (nmodes + (int64_t)kFastModesPerWarp * wb - 1) / ((int64_t)kFastModesPerWarp * wb);
+        const int64_t waves = (blocks + sms - 1) / sms;
+        const double eff = (double)nmodes / (double)(waves * sms * kFastModesPerWarp * wb);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = wb;
+        }
+    }
+    return best * 32;
+}
+
+// ---------------------------------------------------------------------------
+// Fused fast solve, FP32 precision form. Same mode/lane mapping and step
+// algebra as k_fp2s_fast, but the history-part states Y_j of a lane live in
+// FP32 registers (NP is a compile-time bound; the tables are zero-padded up to
+// it), the tables are FP32 pairs (r_j, c_j) read as float4 from shared memory
+// (state 2's table is offset by 4 words so the half-warps hit different banks),
+// and the history sums are formed in FP32. Weights, quadrature coefficients and
+// the per-mode step matrices are computed in FP64. The right-hand side and the
+// 2x2 step are evaluated from the FP32 history sums in double-float arithmetic
+// (FP32 pipe), or in FP64 when the coupling is strong (|a| > 10, i.e. m within
+// ~0.045 of 1/2).
+// Every mode is pre-scaled by an exact power of two (from its G^0) so that its
+// values sit near 1 in FP32 range; the factor is undone on output.
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (Dekker 1971, "A floating-point technique for extending the
+// available precision"; Knuth's TwoSum). Products use the FMA form of
+// Dekker's TwoProduct. About 44 significant bits, computed on the FP32 pipe.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_from(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ df df_fast_norm(float s, float e) {       // |s| >= |e|
+    const float t = s + e;
+    return {t, e - (t - s)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return df_fast_norm(s, e + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return df_fast_norm(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    const float p = a.hi * b;
+    const float e = fmaf(a.hi, b, -p);
+    return df_fast_norm(p, fmaf(a.lo, b, e));
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_shfl_xor16(df a) {
+    return {__shfl_xor_sync(0xffffffffu, a.hi, 16), __shfl_xor_sync(0xffffffffu, a.lo, 16)};
+}
+
+constexpr int kF32Threads = 128;
+
+template <int NP>
+__global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int solve64,
+                                                               const double *__restrict__ lam,
+                                                               const double *__restrict__ g0,
+                                                               double *__restrict__ gN, int *__restrict__ status,
+                                                               const double *__restrict__ d1,
+                                                               const double *__restrict__ d2,
+                                                               const double *__restrict__ tab1,
+                                                               const double *__restrict__ tab2,
+                                                               const float *__restrict__ hdf) {
+    extern __shared__ __align__(16) float smf[];
+    const int np = P.np, L = P.L, T = blockDim.x, tid = threadIdx.x;
+    float *rc0 = smf;                        // [NP] pairs (r_j, c_j), state 1
+    float *rc1 = smf + 2 * NP + 4;           // state 2
+    float *wt = smf + 4 * NP + 8;            // wt[2i + s] = d_i of state s, i < L
+    float *R = wt + 2 * kMaxNs;              // [L][T]
+    for (int j = tid; j < NP; j += T) {
+        const bool in = j < np;
+        rc0[2 * j] = in ? (float)tab1[j] : 0.0f;
+        rc0[2 * j + 1] = in ? (float)tab1[np + j] : 0.0f;
+        rc1[2 * j] = in ? (float)tab2[j] : 0.0f;
+        rc1[2 * j + 1] = in ? (float)tab2[np + j] : 0.0f;
+    }
+    for (int i = tid; i < L; i += T) {
+        wt[2 * i] = (float)d1[i];
+        wt[2 * i + 1] = (float)d2[i];
+    }
+    for (int j = 0; j < L; ++j) R[(size_t)j * T + tid] = 0.0f;
+    __syncthreads();
+
+    const int lane = tid & 31, st = lane >> 4;
+    const int64_t mode_raw = ((int64_t)blockIdx.x * (T >> 5) + (tid >> 5)) * kFastModesPerWarp + (lane & 15);
+    const bool active = mode_raw < P.nmodes;
+    const int64_t mode = active ? mode_raw : 0;
+    const float4 *rc4 = reinterpret_cast<const float4 *>(st ? rc1 : rc0);
+    const float *ws = wt + st;
+    const double *dn = st ? d2 : d1;
+    const float *hd_hi = hdf + (size_t)(2 * st) * (P.N + 1), *hd_lo = hd_hi + (P.N + 1);
+    float *Rc = R + tid;
+
+    // per-mode power-of-two scale from max(|g1^0|, |g2^0|)
+    const double gz64 = g0[st * P.nmodes + mode];
+    const double gmax = fmax(fabs(gz64), fabs(__shfl_xor_sync(0xffffffffu, gz64, 16)));
+    int ex = 0;
+    if (gmax > 0.0 && isfinite(gmax)) frexp(gmax, &ex);
+    const float gz = (float)ldexp(gz64, -ex);
+
+    const double d_s0 = dn[0];
+    const double d_o0 = st ? d1[0] : d2[0];
+    ModeConst mc;
+    const bool ok = mode_setup(P, lam[mode], st ? d_o0 : d_s0, st ? d_s0 : d_o0, mc);
+    if (active && st == 0 && !ok) atomicOr(status, ST_SINGULAR);
+    const double mn_oo = st ? mc.Mn.i22 : mc.Mn.i11, mn_ot = st ? mc.Mn.i21 : mc.Mn.i12;
+    const double m1_oo = st ? mc.M1.i22 : mc.M1.i11, m1_ot = st ? mc.M1.i21 : mc.M1.i12;
+    const df da = df_from(P.a), dc = df_from(mc.c), dinv_tau = df_from(P.inv_tau);
+    const df dmn_oo = df_from(mn_oo), dmn_ot = df_from(mn_ot), dm1_oo = df_from(m1_oo), dm1_ot = df_from(m1_ot);
+    const df dd_s0_3 = df_from(d_s0 * (1.0 / 3.0));
+
+    float Y[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) Y[j] = 0.0f;
+    float gm1 = gz, gm2 = 0.0f;
+    int slot = 0;
+    for (int64_t n = 1; n <= P.N; ++n) {
+        slot = (slot + 1 == L) ? 0 : slot + 1;
+        float h0 = 0.0f, h1 = 0.0f, h2 = 0.0f, h3 = 0.0f;
+        if (n - L >= 1) {
+            const float in = Rc[(size_t)slot * T];
+#pragma unroll
+            for (int j = 0; j < NP; j += 4) {
+                const float4 p = rc4[j / 2];
+                const float4 q = rc4[j / 2 + 1];
+                Y[j] = fmaf(p.x, Y[j], in);
+                Y[j + 1] = fmaf(p.z, Y[j + 1], in);
+                Y[j + 2] = fmaf(q.x, Y[j + 2], in);
+                Y[j + 3] = fmaf(q.z, Y[j + 3], in);
+                h0 = fmaf(p.y, Y[j], h0);
+                h1 = fmaf(p.w, Y[j + 1], h1);
+                h2 = fmaf(q.y, Y[j + 2], h2);
+                h3 = fmaf(q.w, Y[j + 3], h3);
+            }
+        }
+        const int imax = (int)min((int64_t)(L - 1), n - 1);
+        int sl = slot;
+        for (int i = 1; i <= imax; ++i) {
+            sl = (sl == 0) ? L - 1 : sl - 1;
+            if (i & 1) h1 = fmaf(ws[2 * i], Rc[(size_t)sl * T], h1);
+            else h2 = fmaf(ws[2 * i], Rc[(size_t)sl * T], h2);
+        }
+        const float h = (h0 + h1) + (h2 + h3);
+        float x;
+        if (solve64) {
+            double e, lead, m_oo = mn_oo, m_ot = mn_ot;
+            if (P.scheme == CQ_BE) {
+                e = h;
+                lead = (double)gm1 * P.inv_tau;
+            } else if (n == 1) {
+                e = d_s0 * (double)gz * (1.0 / 3.0);
+                lead = (double)gz * P.inv_tau;
+                m_oo = m1_oo;
+                m_ot = m1_ot;
+            } else {
+                e = fma(0.5 * __ldg(dn + n - 1), (double)gz, (double)h);
+                lead = (2.0 * (double)gm1 - 0.5 * (double)gm2) * P.inv_tau;
+            }
+            const double e_o = __shfl_xor_sync(0xffffffffu, e, 16);
+            const double b = lead - mc.c * e + P.a * e_o;
+            const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
+            x = (float)(m_oo * b + m_ot * b_o);
+        } else {
+            // double-float step: the FP32-rounded step coefficients would perturb the
+            // per-step amplification by ~1e-7, which compounds over the N steps
+            df e, lead;
+            df m_oo = dmn_oo, m_ot = dmn_ot;
+            if (P.scheme == CQ_BE) {
+                e = {h, 0.0f};
+                lead = df_mul_f(dinv_tau, gm1);
+            } else if (n == 1) {
+                e = df_mul_f(dd_s0_3, gz);
+                lead = df_mul_f(dinv_tau, gz);
+                m_oo = dm1_oo;
+                m_ot = dm1_ot;
+            } else {
+                e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
+                const df lin = df_add(df{2.0f * gm1, 0.0f}, df{-0.5f * gm2, 0.0f});
+                lead = df_mul(dinv_tau, lin);
+            }
+            const df e_o = df_shfl_xor16(e);
+            const df b = df_add(df_add(lead, df_neg(df_mul(dc, e))), df_mul(da, e_o));
+            const df b_o = df_shfl_xor16(b);
+            const df xx = df_add(df_mul(m_oo, b), df_mul(m_ot, b_o));
+            x = xx.hi + xx.lo;
+        }
+        Rc[(size_t)slot * T] = x;
+        gm2 = gm1;
+        gm1 = x;
+    }
+    if (active) {
+        const double out = ldexp((double)gm1, ex);
+        gN[st * P.nmodes + mode] = out;
+        if (!isfinite(out)) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+static size_t f32_smem_bytes(int NP, int L, int T) {
+    return ((size_t)4 * NP + 8 + 2 * kMaxNs + (size_t)L * T) * sizeof(float);
+}
+
+template <int NP>
+static void launch_f32(const Fp2sParams &P, int solve64, const Fp2sLayout &l, cudaStream_t s) {
+    const int T = kF32Threads;
+    const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
+    const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
+    k_fp2s_fast_f32<NP><<<blocks, T, f32_smem_bytes(NP, P.L, T), s>>>(P, solve64, l.lam, l.g0, l.gN, l.status,
+                                                                      l.d1, l.d2, l.tab1, l.tab2, l.hdf);
+}
+
+// hdf[(2s)(N+1) + i], hdf[(2s+1)(N+1) + i] = hi, lo of d^s_i / 2
+__global__ void k_half_weights_df(const double *__restrict__ d1, const double *__restrict__ d2, int64_t n,
+                                  float *__restrict__ hdf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    const double a = 0.5 * d1[i], b = 0.5 * d2[i];
+    const float ah = (float)a, bh = (float)b;
+    hdf[i] = ah;
+    hdf[(n + 1) + i] = (float)(a - (double)ah);
+    hdf[2 * (n + 1) + i] = bh;
+    hdf[3 * (n + 1) + i] = (float)(b - (double)bh);
+}
+
+static int fp2s_fast_f32(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
+    const int solve64 = fabs(P.a) > 10.0;
+    k_half_weights_df<<<(unsigned)((P.N + 256) / 256), 256, 0, s>>>(l.d1, l.d2, P.N, l.hdf);
+    int st = launched();
+    if (st) return st;
+    if (P.np <= 16) launch_f32<16>(P, solve64, l, s);
+    else if (P.np <= 32) launch_f32<32>(P, solve64, l, s);
+    else if (P.np <= 48) launch_f32<48>(P, solve64, l, s);
+    else if (P.np <= 64) launch_f32<64>(P, solve64, l, s);
+    else if (P.np <= 80) launch_f32<80>(P, solve64, l, s);
+    else if (P.np <= 96) launch_f32<96>(P, solve64, l, s);
+    else if (P.np <= 128) launch_f32<128>(P, solve64, l, s);
+    else return CQ_EUNSUPPORTED;
+    return CQ_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -257,7 +567,7 @@ static int fast_block_threads(int np, int L) {
 // hist[(k*2 + s)*nmodes + mode] holds level k of state s.
 // ---------------------------------------------------------------------------
 template <int BT>
-__global__ void __launch_bounds__(128) k_fp2s_direct(Fp2sParams P, const double *__restrict__ lam,
+__global__ void __launch_bounds__(32, 16) k_fp2s_direct(Fp2sParams P, const double *__restrict__ lam,
                                                      const double *__restrict__ g0, double *__restrict__ gN,
                                                      int *__restrict__ status, const double *__restrict__ d1,
                                                      const double *__restrict__ d2,
@@ -527,17 +837,22 @@ extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double 
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
     if (g_timing && cudaEventRecord(g_ev0, s) != cudaSuccess) return CQ_ECUDA;
-    if (P.form == CQ_FAST) {
-        const int T = fast_block_threads(P.np, P.L);
+    if (P.form == CQ_FAST && P.prec == CQ_F32) {
+        if ((st = fp2s_fast_f32(P, l, s))) return st;
+    } else if (P.form == CQ_FAST) {
+        const int T = fast_block_threads(P.np, P.L, P.nmodes);
         if (T == 0) return CQ_EUNSUPPORTED;
         const size_t smem = fast_smem_bytes(P.np, P.L, T);
         cudaFuncSetAttribute(k_fp2s_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const unsigned blocks = (unsigned)((P.nmodes + T - 1) / T);
+        const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
+        const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
         k_fp2s_fast<<<blocks, T, smem, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2);
     } else {
-        const unsigned blocks = (unsigned)((P.nmodes + 127) / 128);
-        k_fp2s_direct<kDirBT><<<blocks, 128, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2,
-                                                     l.hist);
+        // one-warp blocks: every block runs all N steps, so small blocks spread the
+        // modes evenly over the SMs (at most one warp of imbalance per SM)
+        const unsigned blocks = (unsigned)((P.nmodes + 31) / 32);
+        k_fp2s_direct<kDirBT><<<blocks, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2,
+                                                    l.hist);
     }
     if ((st = launched())) return st;
     if (g_timing) {
@@ -555,6 +870,7 @@ extern "C" int fp2s_init(const fp2s_problem_t *p, const double *G0_dev, void *ws
     int np1 = 0, np2 = 0;
     int st = derive(p, P, np1, np2);
     if (st) return st;
+    if (P.prec != CQ_F64) return CQ_EUNSUPPORTED;
     if (!ws_bytes) return CQ_EINVAL;
     Fp2sLayout l = fp2s_layout(p, P, ws_dev, true);
     if (!ws_dev) { *ws_bytes = l.bytes; return CQ_OK; }
@@ -578,6 +894,7 @@ extern "C" int fp2s_step(const fp2s_problem_t *p, int64_t n, void *ws_dev, size_
     int np1 = 0, np2 = 0;
     int st = derive(p, P, np1, np2);
     if (st) return st;
+    if (P.prec != CQ_F64) return CQ_EUNSUPPORTED;
     if (!ws_dev || n < 1 || n > P.N) return CQ_EINVAL;
     Fp2sLayout l = fp2s_layout(p, P, ws_dev, true);
     if (ws_bytes < l.bytes) return CQ_ENOMEM;

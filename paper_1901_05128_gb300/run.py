@@ -25,6 +25,7 @@ def main(argv=None):
     ap.add_argument("--N", type=int, default=None, help="override the number of steps")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--scale-exp", type=int, default=-1000, help="G0 is multiplied by 2**scale_exp")
+    ap.add_argument("--prec", choices=["f64", "f32"], default="f64")
     a = ap.parse_args(argv)
 
     import torch
@@ -41,7 +42,8 @@ def main(argv=None):
         p = p.replace(scheme=ci.BE if a.scheme == "be" else ci.BDF2)
     if a.N:
         p = p.replace(N=a.N, T=p.T * a.N / p.N)
-    cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns)
+    cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
+                    prec=fc.CQ_F32 if a.prec == "f32" else fc.CQ_F64)
     g0 = torch.tensor(G0 * 2.0 ** a.scale_exp, dtype=torch.float64, device="cuda")
     gN = torch.empty_like(g0)
     ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None))

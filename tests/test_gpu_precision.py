@@ -1,0 +1,75 @@
+"""GPU precision forms against the FP64 oracle (``-m gpu``).
+
+FP32 fast solve (prec = CQ_F32): FP32 history-part states and sums, FP64 tables and
+per-mode step matrices, FP64 2x2 step when |a| > 10. Tolerance, from the arithmetic:
+each history part Y_j = sum_k r_j^k G^{n-k} is advanced with one FP32 rounding per step
+(u = 2^-24); over its memory of ~1/(1-r_j) steps the random rounding errors add up to
+about u / sqrt(1 - r_j) relative to |Y_j| (~1e-6 for the slowest parts, 1 - r ~ 1e-4),
+and the weights c_j of those parts are small. The step is contractive for the stable
+problems used here, so the solution error stays at that level: relative L2 error
+<= 2e-5 per state (measured values are recorded in the design doc).
+"""
+import numpy as np
+import pytest
+
+import cq_inputs as ci
+from oracle import scheme as OS
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1901_05128_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+def _solve(fc, p, G0, prec):
+    cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
+                    prec=prec)
+    g0 = torch.tensor(G0, dtype=torch.float64, device="cuda")
+    gN = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), "cuda")
+    st = fc.fp2s_solve(cp, g0, gN, ws, check=False)
+    torch.cuda.synchronize()
+    return gN.cpu().numpy(), st
+
+
+F32_CASES = [
+    ("be_1d_m0.3", ci.Problem(0.3, 0.7, 0.3, 1.0, 1024, 1, 63, ci.BE, ci.FAST, 64, 0, 2)),
+    ("bdf2_1d_m0.45", ci.Problem(0.2, 0.8, 0.45, 1.0, 2000, 1, 127, ci.BDF2, ci.FAST, 16, 64, 17)),
+    ("bdf2_2d_m0.7", ci.Problem(0.4, 0.6, 0.7, 1.0, 600, 2, 23, ci.BDF2, ci.FAST, 12, 36, 15)),
+    ("bdf2_1d_m0.48_solve64", ci.Problem(0.5, 0.7, 0.48, 0.5, 800, 1, 31, ci.BDF2, ci.FAST, 16, 48, 17)),
+    ("be_2d_np128", ci.Problem(0.6, 0.3, 0.2, 1.0, 1500, 2, 15, ci.BE, ci.FAST, 128, 0, 2)),
+    ("bdf2_1d_np5", ci.Problem(0.7, 0.4, 0.6, 1.0, 300, 1, 9, ci.BDF2, ci.FAST, 2, 3, 5)),
+]
+
+
+@pytest.mark.parametrize("name,p", F32_CASES, ids=[c[0] for c in F32_CASES])
+def test_fast_f32_against_fp64_oracle(fc, name, p):
+    G0 = ci.g0_uniform(p.M, p.dim, 17) * 2.0 ** -200          # exercises the per-mode rescaling
+    got, st = _solve(fc, p, G0, fc.CQ_F32)
+    assert st == fc.CQ_OK
+    ref = OS.solve(p, G0)
+    errs = [np.linalg.norm(got[s] - ref[s]) / np.linalg.norm(ref[s]) for s in range(2)]
+    print("f32 %s rel L2 errors %.3e %.3e" % (name, errs[0], errs[1]))
+    assert max(errs) <= 2e-5
+
+
+def test_fast_f32_rejected_where_unsupported(fc):
+    p = ci.Problem(0.3, 0.7, 0.3, 1.0, 64, 1, 15, ci.BE, ci.FAST, 200, 0, 2)   # np > 128
+    cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
+                    prec=fc.CQ_F32)
+    g0 = torch.zeros((2, 15), dtype=torch.float64, device="cuda")
+    ws = fc.workspace(fc.fp2s_solve(cp, g0, g0, None), "cuda")
+    with pytest.raises(fc.CQError) as e:
+        fc.fp2s_solve(cp, g0, torch.empty_like(g0), ws)
+    assert e.value.status == fc.CQ_EUNSUPPORTED
+    cd = fc.problem(0.3, 0.7, 0.3, 1.0, 64, 1, 15, fc.CQ_BE, fc.CQ_DIRECT, prec=fc.CQ_F32)
+    with pytest.raises(fc.CQError):
+        fc.fp2s_solve(cd, g0, g0, None)
