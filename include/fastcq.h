@@ -50,7 +50,9 @@ extern "C" {
 #define CQ_FAST    1   /* fast O(N Np) history (Eqs. 3.9-3.10, 3.17-3.18) */
 #define CQ_F64     0   /* FP64 end to end */
 #define CQ_F32     1   /* precision form of the fast solve: FP32 history state and sums, FP64 tables
-                        * and per-mode matrices, FP64 2x2 step when |a| > 10 (m near 1/2) */
+                        * and per-mode matrices, double-float (FP64 when |a| > 10) 2x2 step */
+#define CQ_BF16X3  2   /* precision form of the direct history on tensor cores: operands split into
+                        * BF16 hi + lo, hi*hi + hi*lo + lo*hi accumulated in FP32 */
 
 /* Fast-form sizes. BE (Eqs. 3.6-3.10): np1 = Np Gauss-Jacobi points, np2
  * ignored, ns ignored (the exact window of BE is d_1 alone).
@@ -63,9 +65,10 @@ typedef struct { int32_t np1, np2, ns; } cq_fast_cfg_t;
 const char *cq_strerror(int status);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 int64_t cq_launch_count(void);
-/* When enabled (on != 0), fp2s_solve records CUDA events around its main
- * time-stepping kernel on the caller's stream; cq_timing_last() returns that
- * kernel's duration in milliseconds for the most recent fp2s_solve call. */
+/* When enabled (on != 0), fp2s_solve and the tensor-core cq_history_direct
+ * record CUDA events around their main kernel on the caller's stream;
+ * cq_timing_last() returns that kernel's duration in milliseconds for the most
+ * recent such call (it synchronises on the closing event). */
 int cq_timing_enable(int on);
 int cq_timing_last(double *ms_main_kernel);
 
@@ -100,7 +103,11 @@ int cq_fast_coeffs(int32_t scheme, double beta, double tau, const cq_fast_cfg_t 
  * i.e. the strictly lower-triangular Toeplitz product of the CQ weights with
  * the levels G^1..G^{n-1} (row t of G_dev holds G^t; row 0 is never read).
  * 1 <= n_lo <= n_hi, ndof >= 0, ldg, ldh >= ndof. The weights are computed
- * into the workspace. prec must be CQ_F64. */
+ * into the workspace. prec: CQ_F64 (FP64 FMAs) or CQ_BF16X3 (tcgen05 tensor
+ * cores; G and the Toeplitz tiles are split and staged in the workspace, which
+ * then holds about 4 * ndof * n_hi bytes; n_hi + 128 <= 24000). On a device
+ * fault or an expired internal wait the BF16X3 path writes NaN to the affected
+ * outputs. */
 int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof,
                       int64_t n_lo, int64_t n_hi, const double *G_dev, int64_t ldg,
                       double *H_dev, int64_t ldh, int32_t prec,

@@ -6,7 +6,43 @@
 namespace fastcq {
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Optional CUDA events around the main kernel of the latest fp2s_solve /
+// tensor-core cq_history_direct call, recorded on the caller's stream.
+static bool g_timing = false, g_timed = false;
+static cudaEvent_t g_ev0 = nullptr, g_ev1 = nullptr;
+
+int timing_begin(cudaStream_t s) {
+    if (!g_timing) return CQ_OK;
+    return cudaEventRecord(g_ev0, s) == cudaSuccess ? CQ_OK : CQ_ECUDA;
+}
+
+int timing_end(cudaStream_t s) {
+    if (!g_timing) return CQ_OK;
+    if (cudaEventRecord(g_ev1, s) != cudaSuccess) return CQ_ECUDA;
+    g_timed = true;
+    return CQ_OK;
+}
 }  // namespace fastcq
+
+extern "C" int cq_timing_enable(int on) {
+    using namespace fastcq;
+    if (on && !g_ev0) {
+        if (cudaEventCreate(&g_ev0) != cudaSuccess || cudaEventCreate(&g_ev1) != cudaSuccess) return CQ_ECUDA;
+    }
+    g_timing = on != 0;
+    return CQ_OK;
+}
+
+extern "C" int cq_timing_last(double *ms) {
+    using namespace fastcq;
+    if (!ms || !g_timed) return CQ_EINVAL;
+    float f = 0.0f;
+    if (cudaEventSynchronize(g_ev1) != cudaSuccess) return CQ_ECUDA;
+    if (cudaEventElapsedTime(&f, g_ev0, g_ev1) != cudaSuccess) return CQ_ECUDA;
+    *ms = f;
+    return CQ_OK;
+}
 
 extern "C" const char *cq_strerror(int status) {
     switch (status) {

@@ -12,6 +12,9 @@ namespace fastcq {
 
 // Kernels launched by this library since load (reported by cq_launch_count).
 void count_launches(int64_t k);
+// Events around a call's main kernel when timing is enabled (cq_timing_enable).
+int timing_begin(cudaStream_t s);
+int timing_end(cudaStream_t s);
 
 // Status bits written by kernels into a workspace status word.
 enum : int { ST_NONFINITE = 1, ST_SINGULAR = 2, ST_TIMEOUT = 4 };
@@ -70,5 +73,10 @@ int launch_dgemm_square(int M, int batch, const double *A, int64_t sA, const dou
 // Sine transform of a two-state field: out[s] = S in[s] (1D) or S in[s] S (2D); tmp: 2*M^dim doubles (2D).
 int launch_dst_field(int M, int dim, const double *S, const double *in, double *out, double *tmp,
                      cudaStream_t s);
+
+// Tensor-core (tcgen05, BF16x3) direct history (history_tc.cu).
+size_t history_tc_workspace(int64_t ndof, int64_t n_lo, int64_t n_hi);
+int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_lo, int64_t n_hi, const double *G,
+                   int64_t ldg, double *H, int64_t ldh, void *ws, cudaStream_t s);
 
 }  // namespace fastcq

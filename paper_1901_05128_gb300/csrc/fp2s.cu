@@ -797,31 +797,9 @@ static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2,
     return launch_dst_field(p->M, p->dim, l.S, G0, l.g0, l.tmp, s);
 }
 
-static bool g_timing = false;
-static cudaEvent_t g_ev0 = nullptr, g_ev1 = nullptr;
-static bool g_timed = false;
-
 }  // namespace fastcq
 
 using namespace fastcq;
-
-extern "C" int cq_timing_enable(int on) {
-    if (on && !g_ev0) {
-        if (cudaEventCreate(&g_ev0) != cudaSuccess || cudaEventCreate(&g_ev1) != cudaSuccess) return CQ_ECUDA;
-    }
-    g_timing = on != 0;
-    return CQ_OK;
-}
-
-extern "C" int cq_timing_last(double *ms) {
-    if (!ms) return CQ_EINVAL;
-    if (!g_timed) return CQ_EINVAL;
-    float f = 0.0f;
-    if (cudaEventSynchronize(g_ev1) != cudaSuccess) return CQ_ECUDA;
-    if (cudaEventElapsedTime(&f, g_ev0, g_ev1) != cudaSuccess) return CQ_ECUDA;
-    *ms = f;
-    return CQ_OK;
-}
 
 extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double *GN_dev, void *ws_dev,
                           size_t *ws_bytes, void *stream) {
@@ -836,7 +814,7 @@ extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double 
     if (!G0_dev || !GN_dev || ((uintptr_t)ws_dev & 255)) return CQ_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
-    if (g_timing && cudaEventRecord(g_ev0, s) != cudaSuccess) return CQ_ECUDA;
+    if ((st = timing_begin(s))) return st;
     if (P.form == CQ_FAST && P.prec == CQ_F32) {
         if ((st = fp2s_fast_f32(P, l, s))) return st;
     } else if (P.form == CQ_FAST) {
@@ -855,10 +833,7 @@ extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double 
                                                     l.hist);
     }
     if ((st = launched())) return st;
-    if (g_timing) {
-        if (cudaEventRecord(g_ev1, s) != cudaSuccess) return CQ_ECUDA;
-        g_timed = true;
-    }
+    if ((st = timing_end(s))) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, l.gN, GN_dev, l.tmp, s))) return st;
     if (p->flags & FP2S_ASYNC) return CQ_OK;
     return read_status(l.status, s);

@@ -1,0 +1,442 @@
+// Direct history on the 5th-generation tensor cores (tcgen05), split BF16
+// ("BF16x3") with FP32 accumulation in tensor memory.
+//
+// The direct history of Eq. 3.8 over a range of steps is the product of a
+// strictly lower-triangular Toeplitz matrix with the matrix of levels:
+//     H[n][dof] = sum_{k=1}^{n-1} d_{n-k} G[k][dof],   n in [n_lo, n_hi).
+// With k' = k - 1 (levels 1.. only) this is a GEMM with M = steps, N = DOFs,
+// K = levels:  A[m][k'] = d_{m-1-k'} (0 unless m-1-k' >= 1),  B[dof][k'] = G[k'+1][dof].
+// Each operand x is split as x = hi + lo with hi = bf16(x), lo = bf16(x - hi);
+// the product is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term,
+// <= 2^-16 relative, is dropped; the split itself leaves <= 2^-16 of x).
+//
+// A 128 x 64 tile of A at rows m0.. and columns k0'.. depends only on
+// delta = m0 - 1 - k0', so the distinct tiles are precomputed once per call
+// into a small bank (L2-resident) and streamed by TMA like any operand. G is
+// split and transposed once into K-major BF16 arrays.
+//
+// Kernel: one CTA per 128 x 256 output tile; warp 0 issues TMA loads into a
+// two-stage shared-memory ring, warp 1 issues tcgen05.mma (one thread) into a
+// 128 x 256 FP32 accumulator in tensor memory, warps 2-5 read the accumulator
+// back with tcgen05.ld and store FP64 results. Every mbarrier wait is bounded
+// by a global-timer deadline; on expiry the kernel records ST_TIMEOUT, writes
+// NaN to its tile, drains what it started and frees its tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace fastcq {
+namespace tc {
+
+constexpr int BM = 128;                     // steps per tile (UMMA M)
+constexpr int BN = 256;                     // DOFs per tile (UMMA N)
+constexpr int BK = 64;                      // levels per stage (one 128-byte swizzle row of BF16)
+constexpr int STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;        // 16 KiB
+constexpr int B_BYTES = BN * BK * 2;        // 32 KiB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 256;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the completion of the phase with the given parity. Gives up
+// after limit_ns, or at once when any CTA has already recorded a timeout (so a
+// failure ends the whole grid quickly instead of every CTA waiting in turn).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns,
+                                          const int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+        if (*(const volatile int *)status & ST_TIMEOUT) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator, both K-major, M = BM, N = BN.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcParams {
+    int64_t ndof, n_lo, rows, ldh;
+    int num_i;                 // tiles along the steps
+    int64_t delta0;            // delta of bank tile 0
+    int kprime;                // number of levels K' = n_hi - 2 (levels 1 .. n_hi - 2)
+};
+
+__global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_constant__ CUtensorMap tA_hi,
+                                                                 const __grid_constant__ CUtensorMap tA_lo,
+                                                                 const __grid_constant__ CUtensorMap tB_hi,
+                                                                 const __grid_constant__ CUtensorMap tB_lo,
+                                                                 TcParams P, double *__restrict__ H,
+                                                                 int *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accum = empty + STAGES;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(accum + 1);
+    int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);   // [0]: abort, [1]: always 0
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x;
+    const int nt = (int)(b / P.num_i);
+    const int it = P.num_i - 1 - (int)(b % P.num_i);          // longest K range first
+    const int64_t m0 = P.n_lo + (int64_t)it * BM;              // first step of the tile
+    const int64_t n0 = (int64_t)nt * BN;                       // first DOF of the tile
+    const int64_t m_last = min(m0 + BM - 1, P.n_lo + P.rows - 1);
+    // levels k' < m_last - 1 contribute (k = k' + 1 <= m_last - 1)
+    const int64_t k_end = min((int64_t)P.kprime, m_last - 1);
+    const int num_k = k_end > 0 ? (int)((k_end + BK - 1) / BK) : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        abort_flag[0] = (*(const volatile int *)status & ST_TIMEOUT) ? 1 : 0;   // an earlier CTA gave up
+        abort_flag[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    const bool aborted = *(volatile int *)abort_flag != 0;
+    if (warp == 0 && lane == 0 && num_k > 0 && !aborted) {
+        // ---------------- TMA producer
+        int armed[STAGES];
+        for (int i = 0; i < STAGES; ++i) armed[i] = -1;
+        for (int ks = 0; ks < num_k; ++ks) {
+            const int s = ks % STAGES;
+            const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u, WAIT_NS, status)) {
+                atomicOr(status, ST_TIMEOUT);
+                *(volatile int *)abort_flag = 1;
+                break;
+            }
+            if (*(volatile int *)abort_flag) break;
+            unsigned char *st = smem + s * STAGE_BYTES;
+            const int64_t delta = m0 - 1 - (int64_t)ks * BK;
+            const int arow = (int)((delta - P.delta0) / BK) * BM;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(st, &tA_hi, &full[s], 0, arow);
+            tma_load_2d(st + A_BYTES, &tA_lo, &full[s], 0, arow);
+            tma_load_2d(st + 2 * A_BYTES, &tB_hi, &full[s], ks * BK, (int)n0);
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tB_lo, &full[s], ks * BK, (int)n0);
+            armed[s] = ks;
+        }
+        if (*(volatile int *)abort_flag) {
+            // drain the loads this thread started before the CTA releases its shared memory
+            for (int i = 0; i < STAGES; ++i)
+                if (armed[i] >= 0) (void)mbar_wait(&full[i], (uint32_t)(armed[i] / STAGES) & 1u, WAIT_NS, abort_flag + 1);
+        }
+    } else if (warp == 1 && lane == 0 && num_k > 0 && !aborted) {
+        // ---------------- MMA issuer
+        for (int ks = 0; ks < num_k; ++ks) {
+            const int s = ks % STAGES;
+            const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, WAIT_NS, status) || *(volatile int *)abort_flag) {
+                atomicOr(status, ST_TIMEOUT);
+                *(volatile int *)abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t off = kk * 32;            // 16 BF16 = 32 bytes along K inside the swizzle row
+                const uint32_t acc0 = (ks > 0 || kk > 0) ? 1u : 0u;
+                umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
+                umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+                umma_bf16(tmem, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+            }
+            umma_commit(&empty[s]);                       // stage reusable once these MMAs are done
+        }
+        umma_commit(accum);                               // all issued MMAs complete -> accumulator ready
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> registers -> FP64 global
+        const int q = warp & 3;                           // TMEM lane quarter this warp may access
+        const int row = q * 32 + lane;
+        const int64_t m = m0 + row;
+        const bool row_ok = m < P.n_lo + P.rows;
+        bool have = !aborted;
+        if (num_k > 0 && !aborted) {
+            have = mbar_wait(accum, 0, WAIT_NS, status);
+            if (!have) atomicOr(status, ST_TIMEOUT);
+            tc_fence_after();
+        }
+        double *hrow = H + (m - P.n_lo) * P.ldh;
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            if (num_k > 0 && !aborted) {
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+            }
+            if (row_ok) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int64_t dof = n0 + c + i;
+                    if (dof < P.ndof) hrow[dof] = have ? (double)v[i] : __longlong_as_double(0x7ff8000000000000ll);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        if (num_k > 0 && *(volatile int *)abort_flag) {
+            // make sure nothing still writes the accumulator before it is freed
+            if (lane == 0) (void)mbar_wait(accum, 0, WAIT_NS, abort_flag + 1);
+        }
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// Bank of Toeplitz tiles: tile t, row r, column c holds d_{delta0 + 64 t + r - c} when
+// that index lies in [1, nw], else 0; split into BF16 hi + lo.
+__global__ void k_toeplitz_bank(const double *__restrict__ d, int64_t nw, int64_t delta0, int ntiles,
+                                __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)ntiles * BM * BK) return;
+    const int c = (int)(e % BK);
+    const int64_t rr = e / BK;                   // t * BM + r
+    const int r = (int)(rr % BM);
+    const int64_t t = rr / BM;
+    const int64_t q = delta0 + BK * t + r - c;
+    const double v = (q >= 1 && q <= nw) ? d[q] : 0.0;
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+}
+
+// Gt[dof][k'] = split(G[k' + 1][dof]) for k' < kprime, 0 for kprime <= k' < kpad.
+__global__ void k_split_transpose(const double *__restrict__ G, int64_t ldg, int64_t ndof, int kprime, int kpad,
+                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+    __shared__ double tile[32][33];
+    const int k0 = blockIdx.x * 32, d0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int k = k0 + j;
+        const int64_t dof = d0 + threadIdx.x;
+        tile[j][threadIdx.x] = (k < kprime && dof < ndof) ? G[(int64_t)(k + 1) * ldg + dof] : 0.0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int64_t dof = d0 + j;
+        const int k = k0 + threadIdx.x;
+        if (dof < ndof && k < kpad) {
+            const double v = tile[threadIdx.x][j];
+            const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+            hi[dof * kpad + k] = h;
+            lo[dof * kpad + k] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+        }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 2D BF16 tensor [rows][cols] (cols contiguous, pitch in elements), box {64, box_rows}, 128-byte swizzle.
+static int make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t pitch,
+                    uint32_t box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return CQ_ECUDA;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {pitch * 2};
+    const cuuint32_t box[2] = {64, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? CQ_OK : CQ_ECUDA;
+}
+
+struct TcLayout {
+    int *status;
+    double *d;
+    __nv_bfloat16 *a_hi, *a_lo, *g_hi, *g_lo;
+    int ntiles, kpad;
+    int64_t delta0;
+    size_t bytes;
+};
+
+static TcLayout tc_layout(void *ws, int64_t ndof, int64_t n_lo, int64_t n_hi) {
+    TcLayout l{};
+    const int64_t kprime = n_hi - 2 > 0 ? n_hi - 2 : 0;
+    l.kpad = (int)(((kprime + BK - 1) / BK) * BK);
+    if (l.kpad == 0) l.kpad = BK;
+    const int64_t rows = n_hi - n_lo;
+    const int64_t num_i = (rows + BM - 1) / BM;
+    // delta = m0 - 1 - 64 j over tiles i (m0 = n_lo + 128 i) and K-steps j; smallest at i = 0, largest j
+    const int64_t jmax0 = l.kpad / BK;
+    l.delta0 = n_lo - 1 - BK * jmax0;
+    const int64_t dmax = n_lo - 1 + BM * (num_i > 0 ? num_i - 1 : 0);
+    l.ntiles = (int)((dmax - l.delta0) / BK + 1);
+    Carve cv(ws);
+    l.status = cv.take<int>(64);
+    l.d = cv.take<double>(n_hi + BM + 2);
+    l.a_hi = cv.take<__nv_bfloat16>((size_t)l.ntiles * BM * BK);
+    l.a_lo = cv.take<__nv_bfloat16>((size_t)l.ntiles * BM * BK);
+    l.g_hi = cv.take<__nv_bfloat16>((size_t)ndof * l.kpad);
+    l.g_lo = cv.take<__nv_bfloat16>((size_t)ndof * l.kpad);
+    l.bytes = cv.bytes();
+    return l;
+}
+
+}  // namespace tc
+
+size_t history_tc_workspace(int64_t ndof, int64_t n_lo, int64_t n_hi) {
+    return tc::tc_layout(nullptr, ndof, n_lo, n_hi).bytes;
+}
+
+int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_lo, int64_t n_hi, const double *G,
+                   int64_t ldg, double *H, int64_t ldh, void *ws, cudaStream_t s) {
+    using namespace tc;
+    TcLayout l = tc_layout(ws, ndof, n_lo, n_hi);
+    const int64_t nw = n_hi + BM;
+    if (nw > kMaxWeights) return CQ_EUNSUPPORTED;
+    if (ndof > ((int64_t)1 << 31) - BN) return CQ_EUNSUPPORTED;
+    int st;
+    if ((st = cuda_status(cudaMemsetAsync(l.status, 0, 64 * sizeof(int), s)))) return st;
+    if ((st = launch_weights(scheme, beta, tau, nw, l.d, s))) return st;
+    const int64_t bank_elems = (int64_t)l.ntiles * BM * BK;
+    k_toeplitz_bank<<<(unsigned)((bank_elems + 255) / 256), 256, 0, s>>>(l.d, n_hi, l.delta0, l.ntiles, l.a_hi, l.a_lo);
+    if ((st = launched())) return st;
+    const int kprime = (int)(n_hi - 2 > 0 ? n_hi - 2 : 0);
+    dim3 tg((unsigned)(l.kpad / 32), (unsigned)((ndof + 31) / 32));
+    k_split_transpose<<<tg, dim3(32, 8), 0, s>>>(G, ldg, ndof, kprime, l.kpad, l.g_hi, l.g_lo);
+    if ((st = launched())) return st;
+    CUtensorMap mA_hi, mA_lo, mB_hi, mB_lo;
+    if ((st = make_map(&mA_hi, l.a_hi, BK, (uint64_t)l.ntiles * BM, BK, BM))) return st;
+    if ((st = make_map(&mA_lo, l.a_lo, BK, (uint64_t)l.ntiles * BM, BK, BM))) return st;
+    if ((st = make_map(&mB_hi, l.g_hi, l.kpad, ndof, l.kpad, BN))) return st;
+    if ((st = make_map(&mB_lo, l.g_lo, l.kpad, ndof, l.kpad, BN))) return st;
+    TcParams P;
+    P.ndof = ndof;
+    P.n_lo = n_lo;
+    P.rows = n_hi - n_lo;
+    P.ldh = ldh;
+    P.num_i = (int)((P.rows + BM - 1) / BM);
+    P.delta0 = l.delta0;
+    P.kprime = kprime;
+    const int64_t num_n = (ndof + BN - 1) / BN;
+    const int64_t blocks = num_n * P.num_i;
+    if (blocks > 0x7fffffffLL) return CQ_EUNSUPPORTED;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_history_tc_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) !=
+            cudaSuccess)
+            return CQ_ECUDA;
+        attr = true;
+    }
+    if ((st = timing_begin(s))) return st;
+    k_history_tc_bf16x3<<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(mA_hi, mA_lo, mB_hi, mB_lo, P, H, l.status);
+    if ((st = launched())) return st;
+    return timing_end(s);
+}
+
+}  // namespace fastcq

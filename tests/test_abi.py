@@ -51,7 +51,7 @@ def test_invalid_arguments_rejected_on_host(fc):
     assert lib.cq_gauss_jacobi(300, 0.5, 0.5, 8, 8, None) == fc.CQ_EINVAL
     sz = C.c_size_t(0)
     assert lib.cq_history_direct(1, 0.5, 0.1, 10, 0, 5, None, 10, None, 10, 0, None, C.byref(sz), None) == fc.CQ_EINVAL
-    assert lib.cq_history_direct(1, 0.5, 0.1, 10, 1, 5, None, 10, None, 10, 2, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
+    assert lib.cq_history_direct(1, 0.5, 0.1, 10, 1, 5, None, 10, None, 10, 7, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
     cfg = fc.FastCfg(8, 8, 2)
     assert lib.cq_history_fast(2, 0.5, 0.1, C.byref(cfg), 10, 1, None, None, 0, None, C.byref(sz), None) == fc.CQ_EINVAL
 

@@ -1,0 +1,69 @@
+"""Tensor-core direct history (prec = CQ_BF16X3) against the FP64 oracle (``-m gpu``).
+
+Error bound, from the arithmetic: BF16 keeps 8 significant bits (unit roundoff
+2^-8), so hi = bf16(x) and lo = bf16(x - hi) leave |x - hi - lo| <= 2^-16 |x|;
+products of BF16 numbers are exact in FP32; the dropped lo*lo term is <= 2^-16 |a||b|;
+the FP32 accumulation over K terms adds at most K * 2^-24 of the sum of absolute
+terms. So element by element
+    |H_tc - H| <= (3 * 2^-16 + K * 2^-24) * sum_i |d_i| |G^{n-i}|.
+The measured errors are far below the bound; both are printed.
+"""
+import numpy as np
+import pytest
+
+import cq_inputs as ci
+from oracle import history as OH
+from oracle import weights as OW
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1901_05128_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+def _bound(K):
+    return 3 * 2.0 ** -16 + K * 2.0 ** -24
+
+
+def _abs_scale(d, G, n):
+    if n < 2:
+        return np.zeros(G.shape[1])
+    return np.abs(d[n - 1:0:-1]) @ np.abs(G[1:n])
+
+
+CASES = [(1, 1, 2, 0), (1, 1, 3, 0), (100, 1, 65, 0), (300, 1, 130, 5), (257, 2, 300, 0),
+         (1000, 50, 200, 3), (513, 120, 400, 0), (2048, 1, 700, 0)]
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("ndof,n_lo,n_hi,ld_extra", CASES)
+def test_bf16x3_history_small(fc, scheme, ndof, n_lo, n_hi, ld_extra):
+    beta, tau = 0.45, 1.0 / 700
+    ld = ndof + ld_extra
+    G = np.zeros((n_hi, ld))
+    G[:, :ndof] = ci.rng(41).standard_normal((n_hi, ndof))
+    Gd = torch.tensor(G, dtype=torch.float64, device="cuda")
+    H = torch.full((n_hi - n_lo, ld), np.nan, dtype=torch.float64, device="cuda")
+    ws = fc.workspace(fc.cq_history_direct(scheme, beta, tau, ndof, n_lo, n_hi, None, ld, None, ld,
+                                           prec=fc.CQ_BF16X3), "cuda")
+    fc.cq_history_direct(scheme, beta, tau, ndof, n_lo, n_hi, Gd, ld, H, ld, ws, prec=fc.CQ_BF16X3)
+    torch.cuda.synchronize()
+    got = H.cpu().numpy()
+    d = OW.weights(scheme, beta, tau, n_hi)
+    ref = OH.history_direct_all(d, G[:, :ndof], n_lo, n_hi)
+    scale = np.stack([_abs_scale(d, G[:, :ndof], n) for n in range(n_lo, n_hi)])
+    err = np.abs(got[:, :ndof] - ref)
+    ratio = float(np.max(err / (scale + 1e-300)))
+    print("bf16x3 ndof=%d rows=[%d,%d): max |err| / sum|d||G| = %.3e (bound %.3e)"
+          % (ndof, n_lo, n_hi, ratio, _bound(n_hi)))
+    assert np.all(err <= _bound(n_hi) * scale + 1e-300)
+    if ld_extra:
+        assert np.all(np.isnan(got[:, ndof:]))
