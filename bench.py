@@ -38,6 +38,7 @@ WORKLOAD = "bdf2_2d_m255"
 SCALE = 2.0 ** -1000
 FP64_PEAK_NOMINAL = 1.25e12       # FP64 FLOP/s of GB300 (2 DFMA / clock / SM x 152 SMs x ~2.07 GHz)
 FP64_PEAK_PROBE = 1.199e12        # own DFMA-chain probe on this machine's GB300 (independent FMA chains)
+FP32_PEAK_PROBE = 73.2e12         # own FFMA-chain probe, same method
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -121,6 +122,162 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ----------------------------------------------------------------------------- precision forms
+PREC_WORKLOAD = "prec_2d_m511"
+PREC_COLS = 16
+
+
+def precision_leg(fc, torch, dev, K, W, flush):
+    """Tensor-core (BF16x3) direct history over the full 2D 511x511, N = 8192 contraction,
+    and the FP32 fast solve of the same grid. Returns timings plus the data the CPU leg
+    needs to state the error against the oracle."""
+    import cq_inputs as ci
+    p, G0 = ci.workload(PREC_WORKLOAD)
+    n_hi, ndof = p.N + 1, p.ndof
+    beta, tau = 1.0 - p.alpha1, p.T / p.N
+    out = {"problem": p}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(ci.SEED_BASE + 3)
+    G = torch.randn(n_hi, ndof, dtype=torch.float64, device=dev, generator=gen)   # synthetic levels
+    H = torch.empty(n_hi - 1, ndof, dtype=torch.float64, device=dev)
+    ws = fc.workspace(fc.cq_history_direct(ci.BE, beta, tau, ndof, 1, n_hi, None, ndof, None, ndof,
+                                           prec=fc.CQ_BF16X3), dev)
+    for _ in range(W):
+        fc.cq_history_direct(ci.BE, beta, tau, ndof, 1, n_hi, G, ndof, H, ndof, ws, prec=fc.CQ_BF16X3)
+    torch.cuda.synchronize()
+    l0 = fc.cq_launch_count()
+    calls, gemms = [], []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fc.cq_history_direct(ci.BE, beta, tau, ndof, 1, n_hi, G, ndof, H, ndof, ws, prec=fc.CQ_BF16X3)
+        e1.record()
+        e1.synchronize()
+        calls.append(e0.elapsed_time(e1))
+        gemms.append(fc.cq_timing_last())
+    out["tc_launches"] = fc.cq_launch_count() - l0
+    cols = ci.sample_indices(ndof, PREC_COLS, ci.SEED_BASE + 31)
+    ci_t = torch.tensor(cols, device=dev)
+    out["tc_cols"] = cols
+    out["tc_G"] = G[:, ci_t].cpu().numpy()
+    out["tc_H"] = H[:, ci_t].cpu().numpy()
+    out["tc_call_ms"], out["tc_gemm_ms"] = calls, gemms
+    out["tc_beta"], out["tc_tau"], out["tc_nhi"] = beta, tau, n_hi
+    del G, H, ws
+    torch.cuda.empty_cache()
+    # FP32 fast solve of the same grid
+    q = p.replace(form=ci.FAST)
+    cp = fc.problem(q.alpha1, q.alpha2, q.m, q.T, q.N, q.dim, q.M, q.scheme, q.form, q.np1, q.np2, q.ns,
+                    prec=fc.CQ_F32, flags=fc.FP2S_ASYNC)
+    g0 = torch.tensor(G0, dtype=torch.float64, device=dev)
+    gN = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
+    for _ in range(W):
+        fc.fp2s_solve(cp, g0, gN, ws)
+    torch.cuda.synchronize()
+    steps, kern = [], []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fc.fp2s_solve(cp, g0, gN, ws)
+        e1.record()
+        e1.synchronize()
+        steps.append(e0.elapsed_time(e1))
+        kern.append(fc.cq_timing_last())
+    out["f32_status"] = fc.strerror(fc.fp2s_status(cp, ws))
+    out["f32_ms"], out["f32_kernel_ms"] = steps, kern
+    out["f32_gN"] = gN.cpu().numpy()
+    out["f32_problem"], out["G0"] = q, G0
+    del ws, g0, gN
+    torch.cuda.empty_cache()
+    return out
+
+
+def precision_report(leg, cpu_modes):
+    """Oracle comparison and CPU baseline of the precision forms (CPU leg)."""
+    import numpy as np
+    import cq_inputs as ci
+    from oracle import history as OH
+    from oracle import spatial as OSP
+    from oracle import weights as OW
+    p = leg["problem"]
+    n_hi, ndof = leg["tc_nhi"], p.ndof
+    rows = n_hi - 1
+    # tensor-core contraction: the oracle recomputes PREC_COLS whole DOF columns
+    d = OW.weights(ci.BE, leg["tc_beta"], leg["tc_tau"], n_hi)
+    t = time.perf_counter()
+    ref = OH.history_direct_all(d, leg["tc_G"], 1, n_hi)
+    t_orc = time.perf_counter() - t
+    scale = np.stack([np.abs(d[n - 1:0:-1]) @ np.abs(leg["tc_G"][1:n]) if n >= 2 else np.zeros(PREC_COLS)
+                      for n in range(1, n_hi)])
+    tc_err = float(np.max(np.abs(leg["tc_H"] - ref) / (scale + 1e-300)))
+    gemm_ms = statistics.mean(leg["tc_gemm_ms"])
+    call_ms = statistics.mean(leg["tc_call_ms"])
+    useful = 3 * 2.0 * ndof * (rows * (rows - 1) / 2.0)
+    peaks = _measured_peaks()
+    bf16_peak = peaks.get("bf16_tflops", 1948.7)
+    tc = {
+        "workload": "%s: 2D %dx%d (%d DOF), levels 1..%d, BE weights beta=%g, tau=1/%d, synthetic N(0,1) levels"
+                    % (PREC_WORKLOAD, p.M, p.M, ndof, n_hi - 1, leg["tc_beta"], p.N),
+        "precision": "BF16x3 (hi*hi + hi*lo + lo*hi), FP32 accumulation, FP64 output",
+        "value": ndof * rows / (call_ms * 1e-3), "unit": UNIT, "ms_per_call": call_ms,
+        "gemm": {"value": ndof * rows / (gemm_ms * 1e-3), "ms": gemm_ms},
+        "roofline": {"kernel": "k_history_tc_bf16x3", "bound": "tensor", "unit": "TFLOP/s",
+                     "achieved": useful / (gemm_ms * 1e-3) / 1e12, "peak": bf16_peak,
+                     "frac": useful / (gemm_ms * 1e-3) / 1e12 / bf16_peak,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)",
+                     "algorithmic_flops_per_launch": useful,
+                     "flops_definition": "3 products x 2 x ndof x sum_n (n-1) (strictly lower-triangular Toeplitz)"},
+        "error_vs_oracle": {"max_abs_err_over_sum_abs_terms": tc_err, "bound": 3 * 2.0 ** -16 + rows * 2.0 ** -24,
+                            "sample": "%d whole DOF columns x %d steps" % (PREC_COLS, rows)},
+        "gpu_launches_per_call": leg["tc_launches"] / max(1, len(leg["tc_gemm_ms"])),
+        "cpu_baseline": {"value": PREC_COLS * rows / t_orc, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "oracle direct history of %d DOF columns x %d steps (%.1f s)"
+                                   % (PREC_COLS, rows, t_orc)},
+    }
+    # FP32 fast solve: oracle FP64 fast scheme on sampled modes
+    from oracle import scheme as OS
+    q, G0 = leg["f32_problem"], leg["G0"]
+    nm = q.M ** q.dim
+    sample = np.unique(np.concatenate([[0, 1, q.M, q.M + 1], ci.sample_indices(nm, cpu_modes, ci.SEED_BASE + 32)]))
+    lam = OSP.mode_eigenvalues(q.M, q.dim)[sample]
+    g0 = OSP.to_modal(G0, q.M, q.dim)[:, sample]
+    t = time.perf_counter()
+    refm = OS.solve_modal(q, lam, g0)[q.N]
+    t_f = time.perf_counter() - t
+    gm = OSP.to_modal(leg["f32_gN"], q.M, q.dim)[:, sample]
+    f32_err = float(np.linalg.norm(gm - refm) / np.linalg.norm(refm))
+    ms = statistics.mean(leg["f32_ms"])
+    kms = statistics.mean(leg["f32_kernel_ms"])
+    f32_flops = (4 * q.np1 + 2) * q.ndof * q.N
+    f32 = {
+        "workload": "%s fast form: 2D %dx%d (%d DOF), N=%d, BE, alpha=(%g,%g), m=%g, Np=%d"
+                    % (PREC_WORKLOAD, q.M, q.M, q.ndof, q.N, q.alpha1, q.alpha2, q.m, q.np1),
+        "precision": "FP32 history state and sums, FP64 tables, double-float 2x2 step",
+        "value": q.ndof * q.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+        "roofline": {"kernel": "k_fp2s_fast_f32", "bound": "alu", "unit": "TFLOP/s",
+                     "achieved": f32_flops / (kms * 1e-3) / 1e12, "peak": FP32_PEAK_PROBE / 1e12,
+                     "frac": f32_flops / (kms * 1e-3) / FP32_PEAK_PROBE,
+                     "peak_source": "own FFMA probe (FP32)", "kernel_ms": kms},
+        "error_vs_fp64_oracle_rel_l2_sampled_modes": f32_err, "status": leg["f32_status"],
+        "cpu_baseline": {"value": 2 * len(sample) * q.N / t_f, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "oracle FP64 fast BE scheme, %d modes x %d steps (%.1f s)"
+                                   % (len(sample), q.N, t_f)},
+    }
+    return {"tensor_core_direct_history": tc, "fp32_fast_solve": f32}
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -211,6 +368,9 @@ def run_ours(args, rank, world, dist):
             e2e.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
         barrier()
+        del ws
+        prec_leg = precision_leg(fc, torch, dev, max(1, min(K, 3)), 1, flush) if (args.precision and rank == 0) \
+            else None
     clocks = clk.summary()
 
     ms = statistics.mean(steps)
@@ -295,6 +455,8 @@ def run_ours(args, rank, world, dist):
                                     "(%.1f s)" % (len(sample_d), p.N, t_dir)}},
         "device": torch.cuda.get_device_name(),
     }
+    if prec_leg is not None:
+        out["precision"] = precision_report(prec_leg, max(16, args.cpu_modes // 64))
     return out
 
 
@@ -341,6 +503,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-modes", type=int, default=8192, help="sine modes of the oracle's timed sample")
     ap.add_argument("--ref-modes", type=int, default=2048, help="sine modes per step of the reference arm")
+    ap.add_argument("--no-precision", dest="precision", action="store_false",
+                    help="leave out the precision-form legs (2D 511x511 workload)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

@@ -147,8 +147,8 @@ def workload(name: str) -> tuple[Problem, np.ndarray]:
       BDF2, fast (np1=16, np2=64, ns=17); G0 = U[0,1) on an 8x8 checkerboard,
       seed SEED_BASE+1.
     * ``prec_2d_m511``: 2D 511x511, T=1, N=8192, alpha=(0.2,0.8), m=0.45,
-      BE, direct; G0 = N(0,1) times the disc of radius 1/4 about (1/2,1/2),
-      seed SEED_BASE+2.
+      BE, direct (fast-form size np1 = 128); G0 = N(0,1) times the disc of
+      radius 1/4 about (1/2,1/2), seed SEED_BASE+2.
     """
     if name == "be1d_m63":
         p = Problem(0.3, 0.7, 0.4, 1.0, 1024, 1, 63, BE, DIRECT, 32, 0, 2)
@@ -157,7 +157,7 @@ def workload(name: str) -> tuple[Problem, np.ndarray]:
         p = Problem(0.4, 0.6, 0.49, 1.0, 4096, 2, 255, BDF2, FAST, 16, 64, 17)
         return p, g0_checkerboard_uniform(255, SEED_BASE + 1)
     if name == "prec_2d_m511":
-        p = Problem(0.2, 0.8, 0.45, 1.0, 8192, 2, 511, BE, DIRECT, 64, 0, 2)
+        p = Problem(0.2, 0.8, 0.45, 1.0, 8192, 2, 511, BE, DIRECT, 128, 0, 2)
         return p, g0_disc_gaussian(511, SEED_BASE + 2)
     raise KeyError(name)
 
