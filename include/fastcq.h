@@ -105,7 +105,8 @@ int cq_fast_coeffs(int32_t scheme, double beta, double tau, const cq_fast_cfg_t 
  * 1 <= n_lo <= n_hi, ndof >= 0, ldg, ldh >= ndof. The weights are computed
  * into the workspace. prec: CQ_F64 (FP64 FMAs) or CQ_BF16X3 (tcgen05 tensor
  * cores; G and the Toeplitz tiles are split and staged in the workspace, which
- * then holds about 4 * ndof * n_hi bytes; n_hi + 128 <= 24000). On a device
+ * then holds about 4 * ndof * n_hi bytes; n_hi + 128 <= 24000; magnitudes
+ * below 2^-126 in the FP32 accumulator are returned as zero). On a device
  * fault or an expired internal wait the BF16X3 path writes NaN to the affected
  * outputs. */
 int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof,

@@ -6,7 +6,8 @@
 //     H[n][dof] = sum_{k=1}^{n-1} d_{n-k} G[k][dof],   n in [n_lo, n_hi).
 // With k' = k - 1 (levels 1.. only) this is a GEMM with M = steps, N = DOFs,
 // K = levels:  A[m][k'] = d_{m-1-k'} (0 unless m-1-k' >= 1),  B[dof][k'] = G[k'+1][dof].
-// Each operand x is split as x = hi + lo with hi = bf16(x), lo = bf16(x - hi);
+// Each operand x is split as x = hi + lo with hi = bf16(x), lo = bf16(x - hi)
+// (round to nearest even, computed with integer operations: bf16split.h);
 // the product is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term,
 // <= 2^-16 relative, is dropped; the split itself leaves <= 2^-16 of x).
 //
@@ -24,6 +25,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "bf16split.h"
 #include "common.cuh"
 
 namespace fastcq {
@@ -134,8 +136,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// FP32 -> FP64 by bit manipulation on the integer pipe (on GB300 the FP64 unit
+// that would otherwise convert is ~60x slower than FP32). FP32 subnormals
+// (|x| < 2^-126) become signed zero; Inf / NaN are kept.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    const uint64_t man = (uint64_t)(u & 0x7fffffu) << 29;
+    uint64_t bits;
+    if (e == 0u) bits = sign;
+    else if (e == 0xffu) bits = sign | (0x7ffull << 52) | man;
+    else bits = sign | ((uint64_t)(e + 896u) << 52) | man;
+    return __longlong_as_double((long long)bits);
+}
+
 struct TcParams {
     int64_t ndof, n_lo, rows, ldh;
+    int vec2;                  // H rows 16-byte aligned: store double2 pairs
     int num_i;                 // tiles along the steps
     int64_t delta0;            // delta of bank tile 0
     int kprime;                // number of levels K' = n_hi - 2 (levels 1 .. n_hi - 2)
@@ -262,10 +280,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
                 for (int i = 0; i < 16; ++i) v[i] = 0.0f;
             }
             if (row_ok) {
+                const double nan = __longlong_as_double(0x7ff8000000000000ll);
+                if (P.vec2 && n0 + c + 16 <= P.ndof) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int64_t dof = n0 + c + i;
-                    if (dof < P.ndof) hrow[dof] = have ? (double)v[i] : __longlong_as_double(0x7ff8000000000000ll);
+                    for (int i = 0; i < 16; i += 2) {
+                        const double2 pr = have ? make_double2(f32_to_f64_bits(v[i]), f32_to_f64_bits(v[i + 1]))
+                                                : make_double2(nan, nan);
+                        *reinterpret_cast<double2 *>(hrow + n0 + c + i) = pr;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int64_t dof = n0 + c + i;
+                        if (dof < P.ndof) hrow[dof] = have ? f32_to_f64_bits(v[i]) : nan;
+                    }
                 }
             }
         }
@@ -295,31 +323,37 @@ __global__ void k_toeplitz_bank(const double *__restrict__ d, int64_t nw, int64_
     const int64_t t = rr / BM;
     const int64_t q = delta0 + BK * t + r - c;
     const double v = (q >= 1 && q <= nw) ? d[q] : 0.0;
-    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-    hi[e] = h;
-    lo[e] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+    uint16_t h, l;
+    bf16_split(v, &h, &l);
+    hi[e] = __ushort_as_bfloat16(h);
+    lo[e] = __ushort_as_bfloat16(l);
 }
 
 // Gt[dof][k'] = split(G[k' + 1][dof]) for k' < kprime, 0 for kprime <= k' < kpad.
-__global__ void k_split_transpose(const double *__restrict__ G, int64_t ldg, int64_t ndof, int kprime, int kpad,
-                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
-    __shared__ double tile[32][33];
-    const int k0 = blockIdx.x * 32, d0 = blockIdx.y * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+// Tile of 64 levels x 32 DOFs: coalesced FP64 row reads, then every thread writes
+// a pair of BF16 values (a warp stores 128 contiguous bytes per array).
+__global__ void __launch_bounds__(256) k_split_transpose(const double *__restrict__ G, int64_t ldg, int64_t ndof,
+                                                         int kprime, int kpad, __nv_bfloat16 *__restrict__ hi,
+                                                         __nv_bfloat16 *__restrict__ lo) {
+    __shared__ double tile[32][65];                 // [dof][level]
+    const int k0 = blockIdx.x * 64;
+    const int64_t d0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int j = ty; j < 64; j += 8) {
         const int k = k0 + j;
-        const int64_t dof = d0 + threadIdx.x;
-        tile[j][threadIdx.x] = (k < kprime && dof < ndof) ? G[(int64_t)(k + 1) * ldg + dof] : 0.0;
+        const int64_t dof = d0 + tx;
+        tile[tx][j] = (k < kprime && dof < ndof) ? G[(int64_t)(k + 1) * ldg + dof] : 0.0;
     }
     __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int64_t dof = d0 + j;
-        const int k = k0 + threadIdx.x;
-        if (dof < ndof && k < kpad) {
-            const double v = tile[threadIdx.x][j];
-            const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-            hi[dof * kpad + k] = h;
-            lo[dof * kpad + k] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
-        }
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t dof = d0 + r;
+        if (dof >= ndof) break;
+        uint16_t h0, l0, h1, l1;
+        bf16_split(tile[r][2 * tx], &h0, &l0);        // integer ops only (no FP64 pipe)
+        bf16_split(tile[r][2 * tx + 1], &h1, &l1);
+        const int64_t o = dof * kpad + k0 + 2 * tx;
+        *reinterpret_cast<uint32_t *>(hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
+        *reinterpret_cast<uint32_t *>(lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
     }
 }
 
@@ -407,7 +441,7 @@ int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_
     k_toeplitz_bank<<<(unsigned)((bank_elems + 255) / 256), 256, 0, s>>>(l.d, n_hi, l.delta0, l.ntiles, l.a_hi, l.a_lo);
     if ((st = launched())) return st;
     const int kprime = (int)(n_hi - 2 > 0 ? n_hi - 2 : 0);
-    dim3 tg((unsigned)(l.kpad / 32), (unsigned)((ndof + 31) / 32));
+    dim3 tg((unsigned)(l.kpad / 64), (unsigned)((ndof + 31) / 32));
     k_split_transpose<<<tg, dim3(32, 8), 0, s>>>(G, ldg, ndof, kprime, l.kpad, l.g_hi, l.g_lo);
     if ((st = launched())) return st;
     CUtensorMap mA_hi, mA_lo, mB_hi, mB_lo;
@@ -420,6 +454,7 @@ int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_
     P.n_lo = n_lo;
     P.rows = n_hi - n_lo;
     P.ldh = ldh;
+    P.vec2 = (ldh % 2 == 0) && ((uintptr_t)H % 16 == 0);
     P.num_i = (int)((P.rows + BM - 1) / BM);
     P.delta0 = l.delta0;
     P.kprime = kprime;

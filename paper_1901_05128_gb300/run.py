@@ -25,7 +25,12 @@ def main(argv=None):
     ap.add_argument("--N", type=int, default=None, help="override the number of steps")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--scale-exp", type=int, default=-1000, help="G0 is multiplied by 2**scale_exp")
-    ap.add_argument("--prec", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--prec", choices=["f64", "f32", "bf16x3"], default="f64")
+    ap.add_argument("--history", action="store_true",
+                    help="run cq_history_direct alone on synthetic N(0,1) levels (--ndof, --n-lo, --n-hi)")
+    ap.add_argument("--ndof", type=int, default=65536)
+    ap.add_argument("--n-lo", type=int, default=1)
+    ap.add_argument("--n-hi", type=int, default=2049)
     a = ap.parse_args(argv)
 
     import torch
@@ -35,6 +40,8 @@ def main(argv=None):
 
     build()
     fc = load()
+    if a.history:
+        return run_history(fc, torch, a)
     p, G0 = ci.workload(a.workload)
     if a.form:
         p = p.replace(form=ci.FAST if a.form == "fast" else ci.DIRECT)
@@ -42,6 +49,8 @@ def main(argv=None):
         p = p.replace(scheme=ci.BE if a.scheme == "be" else ci.BDF2)
     if a.N:
         p = p.replace(N=a.N, T=p.T * a.N / p.N)
+    if a.prec == "bf16x3":
+        raise SystemExit("bf16x3 applies to --history")
     cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
                     prec=fc.CQ_F32 if a.prec == "f32" else fc.CQ_F64)
     g0 = torch.tensor(G0 * 2.0 ** a.scale_exp, dtype=torch.float64, device="cuda")
@@ -53,6 +62,29 @@ def main(argv=None):
         st = fc.fp2s_solve(cp, g0, gN, ws, check=False)
         torch.cuda.synchronize()
         print("solve %d: %.3f s status=%s" % (r, time.perf_counter() - t, fc.strerror(st)))
+
+
+def run_history(fc, torch, a):
+    """Direct history of synthetic levels: prints call and main-kernel times."""
+    import cq_inputs as ci
+    prec = {"f64": fc.CQ_F64, "bf16x3": fc.CQ_BF16X3}.get(a.prec)
+    if prec is None:
+        raise SystemExit("--history supports --prec f64 or bf16x3")
+    ndof, n_lo, n_hi = a.ndof, a.n_lo, a.n_hi
+    beta, tau = 0.8, 1.0 / max(n_hi - 1, 1)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(ci.SEED_BASE + 7)
+    G = torch.randn(n_hi, ndof, dtype=torch.float64, device="cuda", generator=gen)
+    H = torch.empty(n_hi - n_lo, ndof, dtype=torch.float64, device="cuda")
+    ws = fc.workspace(fc.cq_history_direct(1, beta, tau, ndof, n_lo, n_hi, None, ndof, None, ndof, prec=prec))
+    fc.cq_timing_enable(True)
+    for r in range(a.repeat):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fc.cq_history_direct(1, beta, tau, ndof, n_lo, n_hi, G, ndof, H, ndof, ws, prec=prec)
+        torch.cuda.synchronize()
+        k = fc.cq_timing_last() if prec == fc.CQ_BF16X3 else float("nan")
+        print("history %d: %.3f ms (main kernel %.3f ms)" % (r, (time.perf_counter() - t) * 1e3, k))
 
 
 if __name__ == "__main__":
