@@ -21,9 +21,11 @@ spatial     Dirichlet finite-difference Laplacian, its eigenvalues and the
             orthonormal DST-I (not specified by the paper).
 scheme      BE scheme (Eq. 4.1), fast BE (Eq. 4.3), SBD scheme (Eq. 4.7) and
             fast SBD (Eq. 4.8), solved per sine mode by 2x2 Cramer's rule.
+adjoint     gradients of a final-time misfit with respect to G^0 and alpha through
+            the direct schemes (discrete adjoint; pinned by finite differences).
 
 Pinning status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, library routines, brute force or the paper's printed
 properties; none is "parity unpinned".
 """
-from . import weights, quadrature, history, spatial, scheme  # noqa: F401
+from . import weights, quadrature, history, spatial, scheme, adjoint  # noqa: F401
