@@ -188,6 +188,17 @@ int fp2s_step(const fp2s_problem_t *p, int64_t n, void *ws_dev, size_t ws_bytes,
  * level computed by fp2s_step. */
 int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, double *g_dev,
                void *stream);
+/* Gradient of the final-time misfit J = 1/2 h^dim sum_{s,dof} (G_s^N - Gt_s)^2
+ * through the direct scheme (form == CQ_DIRECT, prec == CQ_F64; N <= 13000):
+ * the discrete adjoint of Eq. 4.1 / Eq. 4.7, i.e. the transposed 2x2 steps run
+ * backwards in time with the CQ convolution reversed in time (same weights), and
+ * the beta-derivatives of the weights for dJ/dalpha_i = -dJ/dbeta_i.
+ * Inputs G0_dev, Gt_dev: physical [2][M^dim]. Outputs: *J_host; dJdG0_dev
+ * [2][M^dim] (gradient with respect to the nodal values of G^0); dJdalpha_host[2].
+ * The workspace holds the forward history and the adjoint variables, two
+ * [N+1][2][M^dim] arrays. Synchronises `stream`. */
+int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, double *J_host,
+                  double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes, void *stream);
 /* Device status of the last fp2s_* work on this workspace (synchronises the stream). */
 int fp2s_status(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, void *stream);
 

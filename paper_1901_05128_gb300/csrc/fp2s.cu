@@ -908,3 +908,333 @@ extern "C" int fp2s_status(const fp2s_problem_t *p, const void *ws_dev, size_t w
     (void)ws_bytes;
     return read_status(l.status, (cudaStream_t)stream);
 }
+
+// ===========================================================================
+// Gradient of J = 1/2 h^dim sum (G^N - Gt)^2 through the direct schemes
+// (discrete adjoint). Per mode, with K = [[c, -a], [-a, c]], W_i = diag(d1_i, d2_i),
+// mu^n = K lambda^n, the adjoint runs backwards from m = N:
+//   BE:  (I/tau + W_0 K) lambda^m = -[m=N] r + [m<N] lambda^{m+1}/tau - sum_{n>m} W_{n-m} mu^n
+//   SBD: (c_m I + e_m W_0 K) lambda^m = -[m=N] r - sum_{n>m} W_{n-m} mu^n
+//                                       + (2/tau) lambda^{m+1} - lambda^{m+2}/(2 tau)
+//        ((c_1, e_1) = (1/tau, 2/3), (c_m, e_m) = (3/(2tau), 1) for m >= 2),
+// r = h^dim (x^N - t). The sum over n > m is the CQ convolution run backwards in
+// time with the same weights. dJ/dbeta_s = sum_m x_s^m sum_{n>=m} d'_{n-m} mu_s^n
+// (+ the SBD first-step and G^0 terms), dJ/dx^0 from lambda^1, lambda^2 and
+// sum_{n>=2} d_{n-1} mu^n. One backward sweep per mode (one thread), in blocks of
+// BT steps: one pass over the future mu^n feeds both running sums through two
+// shifting register windows of weights (d and d').
+// ===========================================================================
+
+// d(d_i)/d(beta), i = 0..n: with g_i the coefficients of (1-zeta)^beta,
+// g'_i = g_i S_i, S_i = -sum_{k=1}^{i} 1/(k-1-beta) (a block-wide sum scan), and
+//   BE:   d_i = tau^-beta g_i                          -> d'_i = tau^-beta (g'_i - ln(tau) g_i)
+//   BDF2: d_i = tau^-beta 1.5^beta sum_k g_{i-k} g_k 3^-k
+//         -> d'_i = tau^-beta 1.5^beta [ (ln 1.5 - ln tau) c_i + sum_k (g'_{i-k} g_k + g_{i-k} g'_k) 3^-k ].
+__global__ void __launch_bounds__(1024) k_dweights(int scheme, double beta, double tau, int n,
+                                                   double *__restrict__ out) {
+    extern __shared__ double smd[];
+    double *g = smd, *gp = smd + (n + 1);
+    __shared__ double part[1024], psum[1024];
+    __shared__ double bk[65], bpk[65];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int chunk = (n + 1 + T - 1) / T;
+    const int lo = t * chunk, hi = min(lo + chunk, n + 1);
+    double p = 1.0, q = 0.0;
+    for (int i = max(lo, 1); i < hi; ++i) {
+        p *= (i - 1.0 - beta) / i;
+        q -= 1.0 / (i - 1.0 - beta);
+    }
+    part[t] = p;
+    psum[t] = q;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        const double x = (t >= off) ? part[t - off] : 1.0;
+        const double y = (t >= off) ? psum[t - off] : 0.0;
+        __syncthreads();
+        part[t] *= x;
+        psum[t] += y;
+        __syncthreads();
+    }
+    double v = (t == 0) ? 1.0 : part[t - 1];
+    double S = (t == 0) ? 0.0 : psum[t - 1];
+    for (int i = lo; i < hi; ++i) {
+        if (i >= 1) {
+            v *= (i - 1.0 - beta) / i;
+            S -= 1.0 / (i - 1.0 - beta);
+        }
+        g[i] = v;
+        gp[i] = v * S;
+    }
+    __syncthreads();
+    const double tb = pow(tau, -beta), lt = log(tau);
+    if (scheme == CQ_BE) {
+        for (int i = t; i <= n; i += T) out[i] = tb * (gp[i] - lt * g[i]);
+        return;
+    }
+    if (t <= 64 && t <= n) {
+        const double s3 = pow(3.0, (double)t);
+        bk[t] = g[t] / s3;
+        bpk[t] = gp[t] / s3;
+    }
+    __syncthreads();
+    const double C = pow(1.5, beta), l15 = log(1.5);
+    for (int i = t; i <= n; i += T) {
+        const int kmax = min(i, 64);
+        double c = 0.0, cp = 0.0;
+        for (int k = kmax; k >= 0; --k) {
+            c = fma(g[i - k], bk[k], c);
+            cp = fma(gp[i - k], bk[k], fma(g[i - k], bpk[k], cp));
+        }
+        out[i] = tb * C * ((l15 - lt) * c + cp);
+    }
+}
+
+constexpr int kAdjBT = 4;
+
+template <int BT>
+__global__ void __launch_bounds__(32, 12) k_adjoint_direct(
+    Fp2sParams P, double wd, const double *__restrict__ lam, const double *__restrict__ d1,
+    const double *__restrict__ d2, const double *__restrict__ dz1, const double *__restrict__ dz2,
+    const double *__restrict__ q1, const double *__restrict__ q2, const double *__restrict__ qz1,
+    const double *__restrict__ qz2, const double *__restrict__ hist, const double *__restrict__ tgt,
+    double *__restrict__ mu, double *__restrict__ gx0, double *__restrict__ acc) {
+    const int64_t nm = P.nmodes;
+    const int64_t mode_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = mode_raw < nm;
+    const int64_t mode = active ? mode_raw : 0;
+    const int64_t N = P.N;
+    const double a = P.a, c = a + lam[mode], it = P.inv_tau;
+    const double d10 = __ldg(d1), d20 = __ldg(d2);
+    // transposed step matrices c0 I + e0 W_0 K and their inverses
+    Inv2 Mn, M1;
+    bool ok;
+    {
+        const double c0 = (P.scheme == CQ_BE) ? it : 1.5 * it;
+        ok = invert2(c0 + d10 * c, -d10 * a, -d20 * a, c0 + d20 * c, Mn);
+        if (P.scheme == CQ_BDF2)
+            ok &= invert2(it + (2.0 / 3.0) * d10 * c, -(2.0 / 3.0) * d10 * a, -(2.0 / 3.0) * d20 * a,
+                          it + (2.0 / 3.0) * d20 * c, M1);
+    }
+    const double xN1 = hist[(N * 2) * nm + mode], xN2 = hist[(N * 2 + 1) * nm + mode];
+    const double e1 = xN1 - tgt[mode], e2 = xN2 - tgt[nm + mode];
+    const double r1 = wd * e1, r2 = wd * e2;
+    double Jpart = active ? 0.5 * wd * (e1 * e1 + e2 * e2) : 0.0;
+    double lp1_1 = 0.0, lp1_2 = 0.0, lp2_1 = 0.0, lp2_2 = 0.0;      // lambda^{m+1}, lambda^{m+2}
+    double db1 = 0.0, db2 = 0.0, sg1 = 0.0, sg2 = 0.0, sx1 = 0.0, sx2 = 0.0;
+    double lam1_1 = 0.0, lam1_2 = 0.0, lam2_1 = 0.0, lam2_2 = 0.0, mu1_1 = 0.0, mu1_2 = 0.0;
+    for (int64_t mhi = N; mhi >= 1; mhi -= BT) {
+        double ar1[BT], ar2[BT], aq1[BT], aq2[BT], w1[BT], w2[BT], wq1[BT], wq2[BT], u1[BT] = {}, u2[BT] = {};
+#pragma unroll
+        for (int b = 0; b < BT; ++b) {
+            ar1[b] = ar2[b] = aq1[b] = aq2[b] = 0.0;
+            w1[b] = __ldg(dz1 + 1 + b + BT);
+            w2[b] = __ldg(dz2 + 1 + b + BT);
+            wq1[b] = __ldg(qz1 + 1 + b + BT);
+            wq2[b] = __ldg(qz2 + 1 + b + BT);
+        }
+        const double *mp = mu + ((mhi + 1) * 2) * nm + mode;
+        for (int64_t n = mhi + 1; n <= N; ++n, mp += 2 * nm) {
+            const double v1 = mp[0], v2 = mp[nm];
+#pragma unroll
+            for (int b = 0; b < BT; ++b) {
+                ar1[b] = fma(w1[b], v1, ar1[b]);
+                ar2[b] = fma(w2[b], v2, ar2[b]);
+                aq1[b] = fma(wq1[b], v1, aq1[b]);
+                aq2[b] = fma(wq2[b], v2, aq2[b]);
+            }
+#pragma unroll
+            for (int b = 0; b < BT - 1; ++b) {
+                w1[b] = w1[b + 1];
+                w2[b] = w2[b + 1];
+                wq1[b] = wq1[b + 1];
+                wq2[b] = wq2[b + 1];
+            }
+            const int64_t top = (n + 1 - mhi + BT - 1) + BT;
+            w1[BT - 1] = __ldg(dz1 + top);
+            w2[BT - 1] = __ldg(dz2 + top);
+            wq1[BT - 1] = __ldg(qz1 + top);
+            wq2[BT - 1] = __ldg(qz2 + top);
+        }
+#pragma unroll
+        for (int b = 0; b < BT; ++b) {
+            const int64_t m = mhi - b;
+            if (m < 1) break;
+            double h1 = ar1[b], h2 = ar2[b], hq1 = aq1[b], hq2 = aq2[b];
+#pragma unroll
+            for (int bb = 0; bb < b; ++bb) {
+                h1 = fma(__ldg(dz1 + (b - bb) + BT), u1[bb], h1);
+                h2 = fma(__ldg(dz2 + (b - bb) + BT), u2[bb], h2);
+                hq1 = fma(__ldg(qz1 + (b - bb) + BT), u1[bb], hq1);
+                hq2 = fma(__ldg(qz2 + (b - bb) + BT), u2[bb], hq2);
+            }
+            double b1 = -h1, b2 = -h2;
+            if (m == N) {
+                b1 -= r1;
+                b2 -= r2;
+            }
+            const bool first = (P.scheme == CQ_BDF2 && m == 1);
+            if (P.scheme == CQ_BE) {
+                if (m < N) {
+                    b1 += lp1_1 * it;
+                    b2 += lp1_2 * it;
+                }
+            } else {
+                if (m + 1 <= N) {
+                    b1 += 2.0 * it * lp1_1;
+                    b2 += 2.0 * it * lp1_2;
+                }
+                if (m + 2 <= N) {
+                    b1 -= 0.5 * it * lp2_1;
+                    b2 -= 0.5 * it * lp2_2;
+                }
+            }
+            const double i11 = first ? M1.i11 : Mn.i11, i12 = first ? M1.i12 : Mn.i12;
+            const double i21 = first ? M1.i21 : Mn.i21, i22 = first ? M1.i22 : Mn.i22;
+            const double l1 = i11 * b1 + i12 * b2;
+            const double l2 = i21 * b1 + i22 * b2;
+            const double v1 = c * l1 - a * l2, v2 = -a * l1 + c * l2;
+            u1[b] = v1;
+            u2[b] = v2;
+            mu[(m * 2) * nm + mode] = v1;
+            mu[(m * 2 + 1) * nm + mode] = v2;
+            hq1 = fma(__ldg(q1), v1, hq1);                      // n = m term, d'_0
+            hq2 = fma(__ldg(q2), v2, hq2);
+            db1 = fma(hist[(m * 2) * nm + mode], hq1, db1);
+            db2 = fma(hist[(m * 2 + 1) * nm + mode], hq2, db2);
+            if (m >= 2) {
+                sg1 = fma(__ldg(d1 + m - 1), v1, sg1);
+                sg2 = fma(__ldg(d2 + m - 1), v2, sg2);
+                sx1 = fma(__ldg(q1 + m - 1), v1, sx1);
+                sx2 = fma(__ldg(q2 + m - 1), v2, sx2);
+            }
+            if (m == 1) {
+                lam1_1 = l1;
+                lam1_2 = l2;
+                mu1_1 = v1;
+                mu1_2 = v2;
+            } else if (m == 2) {
+                lam2_1 = l1;
+                lam2_2 = l2;
+            }
+            lp2_1 = lp1_1;
+            lp2_2 = lp1_2;
+            lp1_1 = l1;
+            lp1_2 = l2;
+        }
+    }
+    const double x01 = hist[mode], x02 = hist[nm + mode];
+    double g1, g2;
+    if (P.scheme == CQ_BE) {
+        g1 = -lam1_1 * it;
+        g2 = -lam1_2 * it;
+    } else {
+        g1 = -lam1_1 * it + d10 * mu1_1 / 3.0 + 0.5 * it * lam2_1 + 0.5 * sg1;
+        g2 = -lam1_2 * it + d20 * mu1_2 / 3.0 + 0.5 * it * lam2_2 + 0.5 * sg2;
+        const double x11 = hist[2 * nm + mode], x12 = hist[3 * nm + mode];
+        db1 += mu1_1 * __ldg(q1) * (x01 - x11) / 3.0 + 0.5 * x01 * sx1;
+        db2 += mu1_2 * __ldg(q2) * (x02 - x12) / 3.0 + 0.5 * x02 * sx2;
+    }
+    if (active) {
+        gx0[mode] = g1;
+        gx0[nm + mode] = g2;
+    } else {
+        db1 = db2 = 0.0;
+    }
+    // warp sums, one atomic per warp and quantity
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        Jpart += __shfl_xor_sync(0xffffffffu, Jpart, off);
+        db1 += __shfl_xor_sync(0xffffffffu, db1, off);
+        db2 += __shfl_xor_sync(0xffffffffu, db2, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc + 0, Jpart);
+        atomicAdd(acc + 1, db1);
+        atomicAdd(acc + 2, db2);
+    }
+    if (active && !ok) atomicAdd(acc + 3, 1.0);
+}
+
+struct GradLayout {
+    double *tgt, *mu, *gx0, *q1, *q2, *qz1, *qz2, *dza1, *dza2, *acc;
+    size_t bytes;
+};
+
+static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void *ws) {
+    GradLayout g{};
+    Carve cv(ws);
+    cv.off = base.bytes;
+    const int64_t nm = P.nmodes;
+    g.acc = cv.take<double>(8);
+    g.tgt = cv.take<double>(2 * nm);
+    g.gx0 = cv.take<double>(2 * nm);
+    g.q1 = cv.take<double>(P.N + 1);
+    g.q2 = cv.take<double>(P.N + 1);
+    g.qz1 = cv.take<double>(P.N + 2 * kAdjBT + 1);
+    g.qz2 = cv.take<double>(P.N + 2 * kAdjBT + 1);
+    g.dza1 = cv.take<double>(P.N + 2 * kAdjBT + 1);
+    g.dza2 = cv.take<double>(P.N + 2 * kAdjBT + 1);
+    g.mu = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
+    g.bytes = cv.bytes();
+    return g;
+}
+
+extern "C" int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, double *J_host,
+                             double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes,
+                             void *stream) {
+    Fp2sParams P;
+    int np1 = 0, np2 = 0;
+    int st = derive(p, P, np1, np2);
+    if (st) return st;
+    if (!ws_bytes) return CQ_EINVAL;
+    if (P.form != CQ_DIRECT || P.prec != CQ_F64) return CQ_EUNSUPPORTED;
+    if (P.N > 13000) return CQ_EUNSUPPORTED;            // shared-memory bound of the weight derivatives
+    Fp2sLayout l = fp2s_layout(p, P, ws_dev, false);
+    GradLayout gl = grad_layout(P, l, ws_dev);
+    if (!ws_dev) { *ws_bytes = gl.bytes; return CQ_OK; }
+    if (*ws_bytes < gl.bytes) return CQ_ENOMEM;
+    if (!G0_dev || !Gt_dev || !J_host || !dJdG0_dev || !dJdalpha_host || ((uintptr_t)ws_dev & 255))
+        return CQ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
+    const unsigned fblocks = (unsigned)((P.nmodes + 31) / 32);
+    if ((st = timing_begin(s))) return st;
+    k_fp2s_direct<kDirBT><<<fblocks, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2, l.hist);
+    if ((st = launched())) return st;
+    if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, gl.tgt, l.tmp, s))) return st;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_dweights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * 13001 * sizeof(double)));
+        attr = true;
+    }
+    const size_t dsm = (size_t)2 * (P.N + 1) * sizeof(double);
+    k_dweights<<<1, 1024, dsm, s>>>(P.scheme, 1.0 - p->alpha1, P.tau, (int)P.N, gl.q1);
+    k_dweights<<<1, 1024, dsm, s>>>(P.scheme, 1.0 - p->alpha2, P.tau, (int)P.N, gl.q2);
+    const unsigned pg = (unsigned)((P.N + 2 * kAdjBT + 256) / 256);
+    k_pad<<<pg, 256, 0, s>>>(gl.q1, P.N, kAdjBT, gl.qz1);
+    k_pad<<<pg, 256, 0, s>>>(gl.q2, P.N, kAdjBT, gl.qz2);
+    if ((st = launched(4))) return st;
+    // the adjoint needs the weights padded for its own block size
+    double *dzA1 = gl.dza1, *dzA2 = gl.dza2;
+    k_pad<<<pg, 256, 0, s>>>(l.d1, P.N, kAdjBT, dzA1);
+    k_pad<<<pg, 256, 0, s>>>(l.d2, P.N, kAdjBT, dzA2);
+    if ((st = launched(2))) return st;
+    if ((st = cuda_status(cudaMemsetAsync(gl.acc, 0, 8 * sizeof(double), s)))) return st;
+    const double h = 1.0 / (p->M + 1);
+    const double wd = (p->dim == 1) ? h : h * h;
+    k_adjoint_direct<kAdjBT><<<fblocks, 32, 0, s>>>(P, wd, l.lam, l.d1, l.d2, dzA1, dzA2, gl.q1, gl.q2, gl.qz1,
+                                                    gl.qz2, l.hist, gl.tgt, gl.mu, gl.gx0, gl.acc);
+    if ((st = launched())) return st;
+    if ((st = timing_end(s))) return st;
+    if ((st = launch_dst_field(p->M, p->dim, l.S, gl.gx0, dJdG0_dev, l.tmp, s))) return st;
+    double host[4];
+    if (cudaMemcpyAsync(host, gl.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CQ_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CQ_ECUDA;
+    *J_host = host[0];
+    dJdalpha_host[0] = -host[1];
+    dJdalpha_host[1] = -host[2];
+    if (host[3] != 0.0) return CQ_ESINGULAR;
+    if ((st = read_status(l.status, s))) return st;
+    if (!isfinite(host[0]) || !isfinite(host[1]) || !isfinite(host[2])) return CQ_ENONFINITE;
+    return CQ_OK;
+}

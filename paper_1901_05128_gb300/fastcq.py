@@ -62,6 +62,8 @@ def _load():
         "fp2s_step": (C.c_int, [C.POINTER(Problem), I64, P, C.c_size_t, P, P]),
         "fp2s_modal": (C.c_int, [C.POINTER(Problem), P, C.c_size_t, P, P]),
         "fp2s_status": (C.c_int, [C.POINTER(Problem), P, C.c_size_t, P]),
+        "fp2s_gradient": (C.c_int, [C.POINTER(Problem), P, P, C.POINTER(C.c_double), P, C.POINTER(C.c_double), P,
+                                    SZ, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -74,7 +76,7 @@ _lib = _load()
 EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_weights",
            "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_history_fast",
            "cq_history_fast_noalloc", "fp2s_solve",
-           "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status")
+           "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient")
 
 
 def strerror(status: int) -> str:
@@ -194,6 +196,19 @@ def fp2s_step(p: Problem, n, ws_dev, G_out_dev=None, stream=None):
 
 def fp2s_modal(p: Problem, ws_dev, g_dev, stream=None):
     _check(_lib.fp2s_modal(C.byref(p), _ptr(ws_dev), _nbytes(ws_dev), _ptr(g_dev), _stream(stream)), "fp2s_modal")
+
+
+def fp2s_gradient(p: Problem, G0_dev, Gt_dev, dJdG0_dev, ws_dev=None, stream=None):
+    """Returns the workspace size when ws_dev is None, else (J, (dJ/dalpha1, dJ/dalpha2));
+    dJ/dG0 is written to dJdG0_dev."""
+    sz = C.c_size_t(0 if ws_dev is None else _nbytes(ws_dev))
+    J = C.c_double(0.0)
+    da = (C.c_double * 2)()
+    _check(_lib.fp2s_gradient(C.byref(p), _ptr(G0_dev), _ptr(Gt_dev), C.byref(J), _ptr(dJdG0_dev), da, _ptr(ws_dev),
+                              C.byref(sz), _stream(stream, ws_dev is None)), "fp2s_gradient")
+    if ws_dev is None:
+        return sz.value
+    return J.value, (da[0], da[1])
 
 
 def fp2s_status(p: Problem, ws_dev, stream=None) -> int:
