@@ -273,6 +273,70 @@ def precision_report(leg, cpu_modes):
     return {"tensor_core_direct_history": tc, "fp32_fast_solve": f32}
 
 
+GRAD_WORKLOAD = "grad_2d_m255"
+
+
+def gradient_leg(fc, torch, dev, K, flush):
+    """Gradient of 1/2 ||G^N - G_target||^2 with respect to G0 and (alpha1, alpha2) on the
+    2D 255x255 BDF2 workload (N = 4096), target = the same scheme with alpha + (0.05, -0.05);
+    dJ/dalpha checked against central differences of the forward solve."""
+    import numpy as np
+    import cq_inputs as ci
+    p, G0 = ci.workload(GRAD_WORKLOAD)
+
+    def cprob(q):
+        return fc.problem(q.alpha1, q.alpha2, q.m, q.T, q.N, q.dim, q.M, q.scheme, ci.DIRECT)
+
+    g0 = torch.tensor(G0, dtype=torch.float64, device=dev)
+    gt = torch.empty_like(g0)
+    wsf = fc.workspace(fc.fp2s_solve(cprob(p), g0, gt, None), dev)
+    fc.fp2s_solve(cprob(p.replace(alpha1=p.alpha1 + 0.05, alpha2=p.alpha2 - 0.05)), g0, gt, wsf)
+    Gt = gt.cpu().numpy()
+    h = 1.0 / (p.M + 1)
+
+    def J_of(q):
+        gN = torch.empty_like(g0)
+        fc.fp2s_solve(cprob(q), g0, gN, wsf)
+        return 0.5 * h ** p.dim * float(np.sum((gN.cpu().numpy() - Gt) ** 2))
+
+    dg = torch.empty_like(g0)
+    cp = cprob(p)
+    ws = fc.workspace(fc.fp2s_gradient(cp, g0, gt, dg, None), dev)
+    J, da = fc.fp2s_gradient(cp, g0, gt, dg, ws)              # warm-up
+    times, kern = [], []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        J, da = fc.fp2s_gradient(cp, g0, gt, dg, ws)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kern.append(fc.cq_timing_last())
+    del ws
+    eps = 1e-5
+    fd = []
+    for f in ("alpha1", "alpha2"):
+        v = getattr(p, f)
+        fd.append((J_of(p.replace(**{f: v + eps})) - J_of(p.replace(**{f: v - eps}))) / (2 * eps))
+    ms = statistics.mean(times)
+    rel = [abs(da[i] - fd[i]) / abs(fd[i]) for i in range(2)]
+    return {
+        "workload": "%s: 2D %dx%d (%d DOF), N=%d, BDF2 direct, alpha=(%g,%g), m=%g; target = same scheme with "
+                    "alpha + (0.05,-0.05); J = 1/2 h^2 ||G^N - G_target||^2" % (GRAD_WORKLOAD, p.M, p.M, p.ndof, p.N,
+                                                                              p.alpha1, p.alpha2, p.m),
+        "precision": "FP64 (forward history kept in full; adjoint of the direct scheme)",
+        "value": 1e3 / ms, "unit": "grad steps/s (gradient evaluations per second)", "ms_per_gradient": ms,
+        "dof_steps_per_s": p.ndof * p.N / (ms * 1e-3),
+        "kernels_ms": statistics.mean(kern), "J": J, "dJ_dalpha": list(da), "fd_dJ_dalpha": fd,
+        "rel_err_vs_central_differences": rel, "fd_step": eps,
+        "cpu_baseline": None,
+        "cpu_baseline_note": "the oracle adjoint is an O(N^2) Python loop; at N = 4096 it exceeds the bench's CPU "
+                             "budget, so it is timed only in the tests on small problems",
+    }
+
+
 def _measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -371,6 +435,7 @@ def run_ours(args, rank, world, dist):
         del ws
         prec_leg = precision_leg(fc, torch, dev, max(1, min(K, 3)), 1, flush) if (args.precision and rank == 0) \
             else None
+        grad = gradient_leg(fc, torch, dev, 2, flush) if (args.precision and rank == 0) else None
     clocks = clk.summary()
 
     ms = statistics.mean(steps)
@@ -457,6 +522,8 @@ def run_ours(args, rank, world, dist):
     }
     if prec_leg is not None:
         out["precision"] = precision_report(prec_leg, max(16, args.cpu_modes // 64))
+    if grad is not None:
+        out["gradient"] = grad
     return out
 
 
@@ -504,7 +571,7 @@ def main():
     ap.add_argument("--cpu-modes", type=int, default=8192, help="sine modes of the oracle's timed sample")
     ap.add_argument("--ref-modes", type=int, default=2048, help="sine modes per step of the reference arm")
     ap.add_argument("--no-precision", dest="precision", action="store_false",
-                    help="leave out the precision-form legs (2D 511x511 workload)")
+                    help="leave out the precision-form and gradient legs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

@@ -146,6 +146,9 @@ def workload(name: str) -> tuple[Problem, np.ndarray]:
     * ``bdf2_2d_m255``: 2D 255x255, T=1, N=4096, alpha=(0.4,0.6), m=0.49,
       BDF2, fast (np1=16, np2=64, ns=17); G0 = U[0,1) on an 8x8 checkerboard,
       seed SEED_BASE+1.
+    * ``grad_2d_m255``: the gradient workload: 2D 255x255, T=1, N=4096, BDF2,
+      direct, alpha=(0.4,0.6), m=0.4, G0 as for ``bdf2_2d_m255``; the target is
+      the same scheme's solution with alpha + (0.05, -0.05).
     * ``prec_2d_m511``: 2D 511x511, T=1, N=8192, alpha=(0.2,0.8), m=0.45,
       BE, direct (fast-form size np1 = 128); G0 = N(0,1) times the disc of
       radius 1/4 about (1/2,1/2), seed SEED_BASE+2.
@@ -155,6 +158,9 @@ def workload(name: str) -> tuple[Problem, np.ndarray]:
         return p, g0_indicator(63, 1)
     if name == "bdf2_2d_m255":
         p = Problem(0.4, 0.6, 0.49, 1.0, 4096, 2, 255, BDF2, FAST, 16, 64, 17)
+        return p, g0_checkerboard_uniform(255, SEED_BASE + 1)
+    if name == "grad_2d_m255":
+        p = Problem(0.4, 0.6, 0.4, 1.0, 4096, 2, 255, BDF2, DIRECT, 16, 64, 17)
         return p, g0_checkerboard_uniform(255, SEED_BASE + 1)
     if name == "prec_2d_m511":
         p = Problem(0.2, 0.8, 0.45, 1.0, 8192, 2, 511, BE, DIRECT, 128, 0, 2)
