@@ -168,6 +168,70 @@ def workload(name: str) -> tuple[Problem, np.ndarray]:
     raise KeyError(name)
 
 
+def lowest_eigenvalue(M: int, dim: int) -> float:
+    """Smallest eigenvalue of the centred FD Dirichlet Laplacian on (0,1)^dim (M points per axis)."""
+    h = 1.0 / (M + 1)
+    return dim * 4.0 / h ** 2 * math.sin(math.pi * h / 2.0) ** 2
+
+
+def growth_rate(alpha1: float, alpha2: float, m: float, lam: float) -> float:
+    """Largest real z > 0 with (z^a1 + a + lam)(z^a2 + a + lam) = a^2, a = (1-m)/(2m-1):
+    the growth rate of the mode with eigenvalue lam of the continuous problem (a pole of
+    H(z) in Eq. 2.2); 0 when there is none. Used only to screen random problem draws."""
+    a = (1.0 - m) / (2.0 * m - 1.0)
+    c = a + lam
+    f = lambda z: (z ** alpha1 + c) * (z ** alpha2 + c) - a * a
+    if f(0.0) >= 0.0:                      # both factors keep their sign: no positive root
+        return 0.0
+    lo, hi = 0.0, 1.0
+    while f(hi) < 0.0:
+        hi *= 2.0
+        if hi > 1e300:
+            return math.inf
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def batch_workload(n: int = 256, seed: int = SEED_BASE + 4, growth_limit: float = 600.0):
+    """Independent instances of uneven parameters (fast FP64 form), drawn from one seeded stream:
+    alpha_i ~ U(0.1, 0.9); m ~ U([0.30, 0.48]) or U([0.52, 0.70]) (50/50); 1D with M log-uniform
+    in [31, 1023] or 2D with M log-uniform in [31, 255] (50/50); N log-uniform in [512, 8192];
+    BE or BDF2 (50/50); T = 1. Fast sizes: BE Np = 64 (N <= 2048) or 128; BDF2 Np1 = 16,
+    Np2 = 64 (N <= 4096) or 96, Ns = 17. A draw whose lowest mode grows faster than
+    growth_limit / T (see growth_rate) is replaced by the next draw; the number of
+    replaced draws is returned. G0 = U[0,1) on the closed box [1/4, 3/4]^dim, both states.
+    Returns (problems, G0 list, redraws)."""
+    r = rng(seed)
+    probs, fields, redraws = [], [], 0
+    while len(probs) < n:
+        a1, a2 = r.uniform(0.1, 0.9, 2)
+        m = r.uniform(0.30, 0.48) if r.random() < 0.5 else r.uniform(0.52, 0.70)
+        dim = 1 if r.random() < 0.5 else 2
+        Mmax = 1023 if dim == 1 else 255
+        M = int(round(math.exp(r.uniform(math.log(31), math.log(Mmax)))))
+        N = int(round(math.exp(r.uniform(math.log(512), math.log(8192)))))
+        scheme = BE if r.random() < 0.5 else BDF2
+        if growth_rate(a1, a2, m, lowest_eigenvalue(M, dim)) * 1.0 > growth_limit:
+            redraws += 1
+            continue
+        if scheme == BE:
+            p = Problem(float(a1), float(a2), float(m), 1.0, N, dim, M, BE, FAST, 64 if N <= 2048 else 128, 0, 2)
+        else:
+            p = Problem(float(a1), float(a2), float(m), 1.0, N, dim, M, BDF2, FAST, 16, 64 if N <= 4096 else 96, 17)
+        pts = grid(M, dim)
+        box = np.ones(M ** dim, dtype=bool)
+        for c in pts:
+            box &= (c >= 0.25 - 1e-12) & (c <= 0.75 + 1e-12)
+        fields.append(r.random((2, M ** dim)) * box[None, :])
+        probs.append(p)
+    return probs, fields, redraws
+
+
 def sample_indices(n_total: int, n_sample: int, seed: int) -> np.ndarray:
     """A sorted seeded sample of distinct indices in [0, n_total)."""
     n_sample = min(n_sample, n_total)

@@ -199,6 +199,35 @@ int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, dou
  * [N+1][2][M^dim] arrays. Synchronises `stream`. */
 int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, double *J_host,
                   double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes, void *stream);
+/* ---- batches: many independent problems in one persistent launch ------- */
+/* Plan of a batch (host memory, filled by fp2s_batch_plan; treat as opaque
+ * apart from the documented fields). */
+typedef struct {
+    int32_t n_inst, n_units;        /* problems; work units of 16 * warps_per_block modes */
+    int32_t warps_per_block;        /* block width of the persistent kernel (autotuned or default) */
+    int32_t max_np, max_L, max_N, max_M, flags;   /* flags bit 0: width chosen by the autotuner */
+    int64_t max_modes, field_elems; /* field_elems: doubles of a packed [instance][2][M^dim] field */
+    int64_t ws_bytes;
+    int64_t off[16];                /* workspace regions (internal) */
+} fp2s_batch_t;
+
+/* Plans and prepares a batch of n problems (each with form == CQ_FAST,
+ * prec == CQ_F64; any mix of dim, M, N, scheme, alpha, m and fast sizes):
+ * builds every instance's tables in the workspace with batched kernels and
+ * orders the work units by decreasing cost. tune != 0 times the candidate
+ * block widths on a shortened run (96 steps) and keeps the fastest.
+ * Size query when ws_dev == NULL. Synchronises `stream`; the plan and the
+ * workspace stay valid for any number of fp2s_solve_batched calls. */
+int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t tune, fp2s_batch_t *plan, void *ws_dev,
+                    size_t *ws_bytes, void *stream);
+/* Solves every planned problem: G0_dev / GN_dev are packed fields, instance i
+ * occupying [2][M_i^dim] doubles in plan order. Enqueues five kernels and one
+ * memset on `stream` and does not synchronise (it can be captured in a CUDA
+ * graph); read the device status with fp2s_batch_status. Calls that overlap on
+ * the GPU must use different workspaces. */
+int fp2s_solve_batched(const fp2s_batch_t *plan, const double *G0_dev, double *GN_dev, void *ws_dev, void *stream);
+int fp2s_batch_status(const fp2s_batch_t *plan, const void *ws_dev, void *stream);
+
 /* Device status of the last fp2s_* work on this workspace (synchronises the stream). */
 int fp2s_status(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, void *stream);
 

@@ -3,6 +3,7 @@
 // All run on the GPU in FP64 (FP32 only for the bracketing bisection of the
 // Gauss-Jacobi nodes, which is followed by FP64 Newton steps).
 #include "common.cuh"
+#include "table_kernels.cuh"
 
 namespace fastcq {
 
@@ -16,50 +17,10 @@ namespace fastcq {
 //   d_i = tau^-beta (3/2)^beta sum_k g_{i-k} g_k 3^-k;
 // terms with k > 64 are below 3^-64 relative and are left out.
 // ---------------------------------------------------------------------------
-constexpr int kWThreads = 1024;
-constexpr int kCauchyTerms = 64;
-
 __global__ void __launch_bounds__(kWThreads) k_weights(int scheme, double beta, double scale, int n,
                                                        double *__restrict__ out) {
     extern __shared__ double g[];                 // g[0..n]
-    __shared__ double part[kWThreads];
-    __shared__ double bk[kCauchyTerms + 1];
-    const int t = threadIdx.x;
-    const int T = blockDim.x;
-    const int chunk = (n + 1 + T - 1) / T;
-    const int lo = t * chunk;
-    const int hi = min(lo + chunk, n + 1);
-    double p = 1.0;
-    for (int i = max(lo, 1); i < hi; ++i) p *= (i - 1.0 - beta) / i;
-    part[t] = p;
-    __syncthreads();
-    for (int off = 1; off < T; off <<= 1) {
-        double x = (t >= off) ? part[t - off] : 1.0;
-        __syncthreads();
-        part[t] *= x;
-        __syncthreads();
-    }
-    double v = (t == 0) ? 1.0 : part[t - 1];
-    for (int i = lo; i < hi; ++i) {
-        if (i >= 1) v *= (i - 1.0 - beta) / i;
-        g[i] = v;
-    }
-    __syncthreads();
-    if (scheme == CQ_BE) {
-        for (int i = t; i <= n; i += T) out[i] = g[i] * scale;
-        return;
-    }
-    if (t <= kCauchyTerms && t <= n) {
-        bk[t] = g[t] / pow(3.0, (double)t);
-    }
-    __syncthreads();
-    const double c0 = pow(1.5, beta) * scale;
-    for (int i = t; i <= n; i += T) {
-        const int kmax = min(i, kCauchyTerms);
-        double acc = 0.0;
-        for (int k = kmax; k >= 0; --k) acc = fma(g[i - k], bk[k], acc);
-        out[i] = acc * c0;
-    }
+    weights_block(scheme, beta, scale, n, out, g);
 }
 
 int launch_weights(int scheme, double beta, double tau, int64_t n, double *out, cudaStream_t s) {
@@ -86,63 +47,10 @@ int launch_weights(int scheme, double beta, double tau, int64_t n, double *out, 
 //   lambda_j = 1 / sum_{k<n} phat_k(s_j)^2
 // with phat_k orthonormal (phat_0 = mu0^-1/2, mu0 = int (1-s)^a (1+s)^b ds).
 // ---------------------------------------------------------------------------
-constexpr int kGJThreads = 64;
-
 __global__ void __launch_bounds__(kGJThreads) k_gauss_jacobi(int n, double a, double b,
                                                              double *__restrict__ nodes,
                                                              double *__restrict__ wts) {
-    __shared__ double al[kMaxNp], be[kMaxNp], sq[kMaxNp];
-    __shared__ float fal[kMaxNp], fbe[kMaxNp];
-    const double ab = a + b;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        double dk = (k == 0) ? (b - a) / (ab + 2.0) : (b * b - a * a) / ((2.0 * k + ab) * (2.0 * k + ab + 2.0));
-        al[k] = dk;
-        fal[k] = (float)dk;
-        double o2 = 0.0;
-        if (k >= 1) {
-            const double c = 2.0 * k + ab;
-            o2 = 4.0 * k * (k + a) * (k + b) * (k + ab) / (c * c * (c + 1.0) * (c - 1.0));
-        }
-        be[k] = o2;
-        sq[k] = sqrt(o2);
-        fbe[k] = (float)o2;
-    }
-    __syncthreads();
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    float lo = -1.0f, hi = 1.0f;
-    for (int it = 0; it < 26; ++it) {
-        const float mid = 0.5f * (lo + hi);
-        float q = fal[0] - mid;
-        int cnt = (q < 0.0f);
-        for (int k = 1; k < n; ++k) {
-            if (q == 0.0f) q = 1e-30f;
-            q = (fal[k] - mid) - fbe[k] / q;
-            cnt += (q < 0.0f);
-        }
-        if (cnt > j) hi = mid; else lo = mid;
-    }
-    double x = 0.5 * ((double)lo + (double)hi);
-    for (int it = 0; it < 6; ++it) {
-        double p0 = 1.0, p1 = x - al[0], d0 = 0.0, d1 = 1.0;
-        for (int k = 1; k < n; ++k) {
-            const double u = x - al[k];
-            const double p2 = u * p1 - be[k] * p0;
-            const double d2 = p1 + u * d1 - be[k] * d0;
-            p0 = p1; p1 = p2; d0 = d1; d1 = d2;
-        }
-        x -= p1 / d1;
-    }
-    const double mu0 = exp2(ab + 1.0) * tgamma(a + 1.0) * tgamma(b + 1.0) / tgamma(ab + 2.0);
-    double pm = 0.0, pk = 1.0 / sqrt(mu0), sum = pk * pk;
-    for (int k = 0; k + 1 < n; ++k) {
-        const double pn = ((x - al[k]) * pk - sq[k] * pm) / sq[k + 1];
-        pm = pk;
-        pk = pn;
-        sum = fma(pk, pk, sum);
-    }
-    nodes[j] = x;
-    wts[j] = 1.0 / sum;
+    gauss_jacobi_block(n, a, b, blockIdx.x * blockDim.x, nodes, wts);
 }
 
 int launch_gauss_jacobi(int n, double a, double b, double *nodes, double *wts, cudaStream_t s) {
@@ -166,28 +74,10 @@ __global__ void k_fast_coeffs(int scheme, double beta, double tau, int np1, int 
     const int np = (scheme == CQ_BE) ? np1 : np1 + np2;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= np) return;
-    const double K = 1.0 / (pow(tau, beta) * tgamma(1.0 - beta) * tgamma(beta));
-    if (scheme == CQ_BE) {
-        const double s = s1[j];
-        r[j] = 0.5 * (s + 1.0);
-        c[j] = -0.25 * K * l1[j];
-    } else if (j < np1) {
-        const double s = s1[j];
-        const double rr = (s + 1.0) / (s + 5.0);
-        const double w = -exp2(2.0 + 2.0 * beta) * cospi(beta) * K * l1[j];
-        const double s5 = s + 5.0;
-        r[j] = rr;
-        c[j] = w / (s5 * s5 * s5 * s5) * pow(rr, (double)(ns - 3));
-    } else {
-        const int k = j - np1;
-        const double s = s2[k];
-        const double rr = 0.5 * (s + 1.0);
-        const double w = -exp2(-beta - 3.0) * K * l2[k];
-        const double u = 1.0 + 3.0 * s;
-        const double re = (u >= 0.0) ? pow(u, beta) : pow(-u, beta) * cospi(beta);
-        r[j] = rr;
-        c[j] = w * re * pow(rr, (double)(ns - 3));
-    }
+    const bool fam1 = (scheme == CQ_BE) || j < np1;
+    const double s = fam1 ? s1[j] : s2[j - np1];
+    const double l = fam1 ? l1[j] : l2[j - np1];
+    fast_coeff_point(scheme, beta, tau, np1, ns, j, s, l, r + j, c + j);
 }
 
 int launch_fast_coeffs(int scheme, double beta, double tau, int np1, int np2, int ns,

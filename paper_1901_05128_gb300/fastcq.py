@@ -40,6 +40,14 @@ class Problem(C.Structure):
                 ("form", C.c_int32), ("fast", FastCfg), ("prec", C.c_int32), ("flags", C.c_int32)]
 
 
+class BatchPlan(C.Structure):
+    """fp2s_batch_t."""
+    _fields_ = [("n_inst", C.c_int32), ("n_units", C.c_int32), ("warps_per_block", C.c_int32),
+                ("max_np", C.c_int32), ("max_L", C.c_int32), ("max_N", C.c_int32), ("max_M", C.c_int32),
+                ("flags", C.c_int32), ("max_modes", C.c_int64), ("field_elems", C.c_int64),
+                ("ws_bytes", C.c_int64), ("off", C.c_int64 * 16)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("fastcq CUDA library not built (%s missing); run paper_1901_05128_gb300.build.build()"
@@ -64,6 +72,9 @@ def _load():
         "fp2s_status": (C.c_int, [C.POINTER(Problem), P, C.c_size_t, P]),
         "fp2s_gradient": (C.c_int, [C.POINTER(Problem), P, P, C.POINTER(C.c_double), P, C.POINTER(C.c_double), P,
                                     SZ, P]),
+        "fp2s_batch_plan": (C.c_int, [C.POINTER(Problem), I32, I32, C.POINTER(BatchPlan), P, SZ, P]),
+        "fp2s_solve_batched": (C.c_int, [C.POINTER(BatchPlan), P, P, P, P]),
+        "fp2s_batch_status": (C.c_int, [C.POINTER(BatchPlan), P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -76,7 +87,8 @@ _lib = _load()
 EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_weights",
            "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_history_fast",
            "cq_history_fast_noalloc", "fp2s_solve",
-           "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient")
+           "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient", "fp2s_batch_plan",
+           "fp2s_solve_batched", "fp2s_batch_status")
 
 
 def strerror(status: int) -> str:
@@ -209,6 +221,25 @@ def fp2s_gradient(p: Problem, G0_dev, Gt_dev, dJdG0_dev, ws_dev=None, stream=Non
     if ws_dev is None:
         return sz.value
     return J.value, (da[0], da[1])
+
+
+def fp2s_batch_plan(problems, ws_dev=None, tune=False, stream=None):
+    """Size query (ws_dev None) -> bytes; else -> BatchPlan."""
+    arr = (Problem * len(problems))(*problems)
+    plan = BatchPlan()
+    sz = C.c_size_t(0 if ws_dev is None else _nbytes(ws_dev))
+    _check(_lib.fp2s_batch_plan(arr, len(problems), 1 if tune else 0, C.byref(plan), _ptr(ws_dev), C.byref(sz),
+                                _stream(stream, ws_dev is None)), "fp2s_batch_plan")
+    return sz.value if ws_dev is None else plan
+
+
+def fp2s_solve_batched(plan: BatchPlan, G0_dev, GN_dev, ws_dev, stream=None):
+    _check(_lib.fp2s_solve_batched(C.byref(plan), _ptr(G0_dev), _ptr(GN_dev), _ptr(ws_dev), _stream(stream)),
+           "fp2s_solve_batched")
+
+
+def fp2s_batch_status(plan: BatchPlan, ws_dev, stream=None) -> int:
+    return int(_lib.fp2s_batch_status(C.byref(plan), _ptr(ws_dev), _stream(stream)))
 
 
 def fp2s_status(p: Problem, ws_dev, stream=None) -> int:

@@ -1,0 +1,123 @@
+"""Batched persistent solve (fp2s_batch_plan / fp2s_solve_batched) against single
+solves of the same problems and against the oracle (``-m gpu``). Also: autotuned block
+width, repeated solves, and capture of the batched solve in a CUDA graph."""
+import numpy as np
+import pytest
+
+import cq_inputs as ci
+from oracle import scheme as OS
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1901_05128_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+MIXED = [ci.Problem(0.3, 0.7, 0.4, 1.0, 300, 1, 63, ci.BE, ci.FAST, 64, 0, 2),
+         ci.Problem(0.4, 0.6, 0.3, 1.0, 257, 2, 19, ci.BDF2, ci.FAST, 9, 23, 7),
+         ci.Problem(0.5, 0.5, 0.6, 1.0, 3, 1, 1, ci.BDF2, ci.FAST, 2, 2, 3),
+         ci.Problem(0.25, 0.55, 0.7, 0.5, 333, 2, 21, ci.BE, ci.FAST, 40, 0, 2),
+         ci.Problem(0.8, 0.2, 0.45, 1.0, 700, 1, 45, ci.BDF2, ci.FAST, 16, 48, 17),
+         ci.Problem(0.6, 0.35, 0.0, 2.0, 111, 2, 40, ci.BDF2, ci.FAST, 12, 36, 15),
+         ci.Problem(0.2, 0.9, 0.52, 1.0, 64, 1, 300, ci.BE, ci.FAST, 33, 0, 2),
+         ci.Problem(0.45, 0.65, 0.35, 1.0, 1, 2, 3, ci.BE, ci.FAST, 4, 0, 2)]
+
+
+def _cp(fc, p):
+    return fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns)
+
+
+def _single(fc, p, G0):
+    cp = _cp(fc, p)
+    g0 = torch.tensor(G0, dtype=torch.float64, device="cuda")
+    gN = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), "cuda")
+    fc.fp2s_solve(cp, g0, gN, ws)
+    return gN.cpu().numpy()
+
+
+def _pack(fields):
+    return torch.tensor(np.concatenate([f.reshape(-1) for f in fields]), dtype=torch.float64, device="cuda")
+
+
+def _unpack(t, probs):
+    out, o, a = [], 0, t.cpu().numpy()
+    for p in probs:
+        n = 2 * p.M ** p.dim
+        out.append(a[o:o + n].reshape(2, -1))
+        o += n
+    return out
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_matches_single_solves_and_oracle(fc, tune):
+    fields = [ci.g0_uniform(p.M, p.dim, 100 + i) for i, p in enumerate(MIXED)]
+    cps = [_cp(fc, p) for p in MIXED]
+    ws = fc.workspace(fc.fp2s_batch_plan(cps), "cuda")
+    plan = fc.fp2s_batch_plan(cps, ws, tune=tune)
+    assert plan.n_inst == len(MIXED) and plan.n_units >= len(MIXED)
+    assert plan.field_elems == sum(2 * p.M ** p.dim for p in MIXED)
+    g0 = _pack(fields)
+    gN = torch.empty_like(g0)
+    fc.fp2s_solve_batched(plan, g0, gN, ws)
+    assert fc.fp2s_batch_status(plan, ws) == fc.CQ_OK
+    res = _unpack(gN, MIXED)
+    for i, (p, f) in enumerate(zip(MIXED, fields)):
+        single = _single(fc, p, f)
+        # same per-mode arithmetic; only the sine transforms sum in another order
+        assert np.max(np.abs(res[i] - single)) <= 1e-12 * np.max(np.abs(single)) + 1e-300, i
+        if i in (0, 1, 4, 7):
+            ref = OS.solve(p, f)
+            assert np.linalg.norm(res[i] - ref) <= 1e-12 * np.linalg.norm(ref), i
+    # a second solve on the same plan gives the same numbers (the work counter is reset)
+    gN2 = torch.empty_like(g0)
+    fc.fp2s_solve_batched(plan, g0, gN2, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(gN, gN2)
+
+
+def test_batch_in_cuda_graph(fc):
+    probs = MIXED[:5]
+    cps = [_cp(fc, p) for p in probs]
+    ws = fc.workspace(fc.fp2s_batch_plan(cps), "cuda")
+    plan = fc.fp2s_batch_plan(cps, ws)
+    f1 = [ci.g0_uniform(p.M, p.dim, 7 + i) for i, p in enumerate(probs)]
+    f2 = [ci.g0_uniform(p.M, p.dim, 70 + i) for i, p in enumerate(probs)]
+    g0 = _pack(f1)
+    gN = torch.empty_like(g0)
+    fc.fp2s_solve_batched(plan, g0, gN, ws)          # eager reference for f1
+    torch.cuda.synchronize()
+    ref1 = gN.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            fc.fp2s_solve_batched(plan, g0, gN, ws)
+    torch.cuda.synchronize()
+    gN.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(gN, ref1)
+    g0.copy_(_pack(f2))                              # new data, same graph
+    graph.replay()
+    torch.cuda.synchronize()
+    res = _unpack(gN, probs)
+    for i, (p, f) in enumerate(zip(probs, f2)):
+        single = _single(fc, p, f)
+        assert np.max(np.abs(res[i] - single)) <= 1e-12 * np.max(np.abs(single)) + 1e-300, i
+
+
+def test_batch_rejects_invalid(fc):
+    bad = [_cp(fc, MIXED[0]), fc.problem(0.3, 0.7, 0.4, 1.0, 64, 1, 15, fc.CQ_BE, fc.CQ_DIRECT)]
+    with pytest.raises(fc.CQError) as e:
+        fc.fp2s_batch_plan(bad)
+    assert e.value.status == fc.CQ_EUNSUPPORTED
