@@ -337,6 +337,73 @@ def gradient_leg(fc, torch, dev, K, flush):
     }
 
 
+def batch_leg(fc, torch, dev, K, flush):
+    """256 independent instances (uneven alpha, m, grid, N, scheme; FP64 fast form) in one
+    persistent launch; compared with the same instances solved one call at a time."""
+    import numpy as np
+    import cq_inputs as ci
+    probs, fields, redraws = ci.batch_workload()
+    fields = [f * SCALE for f in fields]
+    cps = [fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
+                      flags=fc.FP2S_ASYNC) for p in probs]
+    ws = fc.workspace(fc.fp2s_batch_plan(cps), dev)
+    t = time.perf_counter()
+    plan = fc.fp2s_batch_plan(cps, ws, tune=True)
+    plan_s = time.perf_counter() - t
+    g0 = torch.tensor(np.concatenate([f.reshape(-1) for f in fields]), dtype=torch.float64, device=dev)
+    gN = torch.empty_like(g0)
+    fc.fp2s_solve_batched(plan, g0, gN, ws)                       # warm-up
+    times, kern = [], []
+    l0 = fc.cq_launch_count()
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fc.fp2s_solve_batched(plan, g0, gN, ws)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kern.append(fc.cq_timing_last())
+    launches = (fc.cq_launch_count() - l0) / K
+    status = fc.strerror(fc.fp2s_batch_status(plan, ws))
+    batch = gN.cpu().numpy()
+    del ws
+    # the same instances, one fp2s_solve each (same arithmetic per mode)
+    singles, t_single, o = [], 0.0, 0
+    for cp, f in zip(cps, fields):
+        a = torch.tensor(f, dtype=torch.float64, device=dev)
+        b = torch.empty_like(a)
+        w = fc.workspace(fc.fp2s_solve(cp, a, b, None), dev)
+        fc.fp2s_solve(cp, a, b, w)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fc.fp2s_solve(cp, a, b, w)
+        e1.record()
+        e1.synchronize()
+        t_single += e0.elapsed_time(e1)
+        n = f.size
+        ref = b.cpu().numpy().reshape(-1)
+        got = batch[o:o + n]
+        o += n
+        sc = np.frexp(np.max(np.abs(ref)) if np.max(np.abs(ref)) > 0 else 1.0)[1]
+        singles.append(float(np.max(np.abs(np.ldexp(got - ref, -sc)))))
+    ms = statistics.mean(times)
+    dof_steps = sum(2 * p.M ** p.dim * p.N for p in probs)
+    return {
+        "workload": "256 seeded instances (alpha ~ U(0.1,0.9), m in [0.30,0.48]U[0.52,0.70], 1D M in [31,1023] "
+                    "or 2D M in [31,255] log-uniform, N in [512,8192] log-uniform, BE/BDF2), FP64 fast form, "
+                    "G0 = U[0,1) on [1/4,3/4]^d x 2^-1000; %d draws replaced by the growth screen" % redraws,
+        "value": dof_steps / (ms * 1e-3), "unit": UNIT, "ms_per_batch": ms, "kernel_ms": statistics.mean(kern),
+        "total_dof_steps": dof_steps, "warps_per_block": plan.warps_per_block, "autotuned": bool(plan.flags & 1),
+        "plan_s": plan_s, "gpu_launches_per_solve": launches, "status": status,
+        "sum_of_single_solves_ms": t_single, "persistent_launch_efficiency": t_single / ms,
+        "max_abs_diff_vs_single_solves_rel_to_instance_max": max(singles),
+    }
+
+
 def _measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -436,6 +503,7 @@ def run_ours(args, rank, world, dist):
         prec_leg = precision_leg(fc, torch, dev, max(1, min(K, 3)), 1, flush) if (args.precision and rank == 0) \
             else None
         grad = gradient_leg(fc, torch, dev, 2, flush) if (args.precision and rank == 0) else None
+        batch = batch_leg(fc, torch, dev, 2, flush) if (args.precision and rank == 0) else None
     clocks = clk.summary()
 
     ms = statistics.mean(steps)
@@ -524,6 +592,8 @@ def run_ours(args, rank, world, dist):
         out["precision"] = precision_report(prec_leg, max(16, args.cpu_modes // 64))
     if grad is not None:
         out["gradient"] = grad
+    if batch is not None:
+        out["batch"] = batch
     return out
 
 
@@ -571,7 +641,7 @@ def main():
     ap.add_argument("--cpu-modes", type=int, default=8192, help="sine modes of the oracle's timed sample")
     ap.add_argument("--ref-modes", type=int, default=2048, help="sine modes per step of the reference arm")
     ap.add_argument("--no-precision", dest="precision", action="store_false",
-                    help="leave out the precision-form and gradient legs")
+                    help="leave out the precision-form, gradient and batch legs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
