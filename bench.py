@@ -530,14 +530,10 @@ def run_ours(args, rank, world, dist):
                 "traffic": None, "algorithmic_flops_per_launch": flops_per_launch,
                 "flops_per_dof_step": hist_flops_per_dof_step, "kernel_ms": ms_main,
                 "kernel_share_of_step": ms_main / ms}
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            tr = json.load(open(prof)).get("k_fp2s_fast")
-            if tr and tr.get("source_hash") == _kernel_hash():
-                roofline["traffic"] = tr["dram_bytes_per_launch"]
-        except (OSError, ValueError):
-            pass
+    traffic = _profiled_traffic("k_fp2s_fast_bdf2_2d_m255.md")
+    if traffic is not None:
+        roofline["traffic"] = traffic
+        roofline["traffic_note"] = "ncu dram bytes per launch (independent of N: state stays on chip)"
 
     # oracle leg: bounded sample, also gives the error of this run
     import numpy as np
@@ -600,10 +596,23 @@ def run_ours(args, rank, world, dist):
 def _kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("fp2s.cu", "common.cuh"):
+    for f in ("fp2s.cu", "fp2s_core.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1901_05128_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def _profiled_traffic(name):
+    """DRAM bytes per launch recorded in a profiles/ summary, if it was taken on the current kernel source."""
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch: (\d+) \(source hash ([0-9a-f]+)\)", txt)
+    if not m or m.group(2) != _kernel_hash():
+        return None
+    return int(m.group(1))
 
 
 # ----------------------------------------------------------------------------- reference arm (the oracle)
