@@ -404,6 +404,59 @@ def batch_leg(fc, torch, dev, K, flush):
     }
 
 
+def stream_leg(fc, torch, dev, steps=24):
+    """Per-step fast history (cq_history_fast) streaming its state from HBM, FP32 and FP64,
+    on the 2D 511x511 DOF count with the BDF2 sizes of the main workload (np = 80, Ns = 17);
+    plus the FP32 form on 4 Mi DOFs (a longer kernel: the asymptotic bandwidth)."""
+    import cq_inputs as ci
+    p, _ = ci.workload(PREC_WORKLOAD)
+    out = _stream_case(fc, torch, dev, p.ndof, steps, (("f32", fc.CQ_F32), ("f64", fc.CQ_F64)))
+    out.update({k + "_4Mi_dof": v for k, v in _stream_case(fc, torch, dev, 4 << 20, steps, (("f32", fc.CQ_F32),)).items()
+                if k != "workload"})
+    return out
+
+
+def _stream_case(fc, torch, dev, ndof, steps, precs):
+    import cq_inputs as ci
+    np1, np2, ns, beta, tau = 16, 64, 17, 0.6, 1.0 / 4096
+    npt = np1 + np2
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(ci.SEED_BASE + 8)
+    G = torch.randn(2, ndof, dtype=torch.float64, device=dev, generator=gen)
+    H = torch.empty(ndof, dtype=torch.float64, device=dev)
+    out = {}
+    per_dofs = {"f32": 8 * npt + 4 * (ns - 2) + 4 + 4 + 8 + 8, "f64": 16 * npt + 8 * (ns - 2) + 8 + 8 + 8 + 8}
+    for name, prec in precs:
+        per_dof = per_dofs[name]
+        ws = fc.workspace(fc.cq_history_fast(2, beta, tau, np1, np2, ns, ndof, 1, None, None, prec=prec), dev)
+        n = 1
+        for _ in range(ns + 8):                                # past the exact window: full traffic
+            fc.cq_history_fast(2, beta, tau, np1, np2, ns, ndof, n, G[n % 2], H, ws, prec=prec)
+            n += 1
+        torch.cuda.synchronize()
+        kms = []
+        for _ in range(steps):
+            fc.cq_history_fast(2, beta, tau, np1, np2, ns, ndof, n, G[n % 2], H, ws, prec=prec)
+            kms.append(fc.cq_timing_last())
+            n += 1
+        ms = statistics.median(kms)
+        bytes_per_launch = per_dof * ndof
+        gbs = bytes_per_launch / (ms * 1e-3) / 1e9
+        hbm = _measured_peaks().get("hbm_gbs", 6790.0)
+        out[name] = {"value": ndof / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "roofline": {"kernel": "k_history_fast_step" + ("_f32" if name == "f32" else ""),
+                                  "bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": hbm, "frac": gbs / hbm,
+                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                                  "algorithmic_bytes_per_dof_step": per_dof,
+                                  "algorithmic_bytes_per_launch": bytes_per_launch}}
+        del ws
+    torch.cuda.empty_cache()
+    out["workload"] = ("cq_history_fast, one step over %d DOFs, BDF2 sizes np = %d, Ns = %d; "
+                       "state %.2f GB (FP32) / %.2f GB (FP64) streamed every step; median of %d steps"
+                       % (ndof, npt, ns, npt * ndof * 4 / 1e9, npt * ndof * 8 / 1e9, steps))
+    return out
+
+
 def _measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -504,6 +557,7 @@ def run_ours(args, rank, world, dist):
             else None
         grad = gradient_leg(fc, torch, dev, 2, flush) if (args.precision and rank == 0) else None
         batch = batch_leg(fc, torch, dev, 2, flush) if (args.precision and rank == 0) else None
+        stream = stream_leg(fc, torch, dev) if (args.precision and rank == 0) else None
     clocks = clk.summary()
 
     ms = statistics.mean(steps)
@@ -590,6 +644,8 @@ def run_ours(args, rank, world, dist):
         out["gradient"] = grad
     if batch is not None:
         out["batch"] = batch
+    if stream is not None:
+        out["fast_history_stream"] = stream
     return out
 
 

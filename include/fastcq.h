@@ -65,8 +65,9 @@ typedef struct { int32_t np1, np2, ns; } cq_fast_cfg_t;
 const char *cq_strerror(int status);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 int64_t cq_launch_count(void);
-/* When enabled (on != 0), fp2s_solve and the tensor-core cq_history_direct
- * record CUDA events around their main kernel on the caller's stream;
+/* When enabled (on != 0), fp2s_solve, fp2s_solve_batched, fp2s_gradient,
+ * cq_history_fast (n >= 2) and the tensor-core cq_history_direct record CUDA
+ * events around their main kernel on the caller's stream;
  * cq_timing_last() returns that kernel's duration in milliseconds for the most
  * recent such call (it synchronises on the closing event). */
 int cq_timing_enable(int on);
@@ -122,7 +123,8 @@ int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof,
  * h^1 = 0. G_prev_dev = G^{n-1} (ndof doubles; ignored for n = 1, may be NULL).
  * H_dev = h^n (ndof doubles). The workspace holds the Ghist state
  * (np x ndof), the last L levels and the tables; its size depends on
- * (scheme, cfg, ndof) only. prec must be CQ_F64. */
+ * (scheme, cfg, ndof, prec) only. prec: CQ_F64, or CQ_F32 (state, levels and
+ * sums in FP32, streamed with 16-byte accesses; tables computed in FP64). */
 int cq_history_fast(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
                     int64_t ndof, int64_t n, const double *G_prev_dev, double *H_dev,
                     int32_t prec, void *ws_dev, size_t *ws_bytes, void *stream);

@@ -138,6 +138,86 @@ __global__ void __launch_bounds__(256) k_history_fast_step(int64_t ndof, int64_t
     if (pair) H[dof + 1] = h1;
 }
 
+// ---------------------------------------------------------------------------
+// Fast history, one step, FP32 precision form, streaming from HBM: the state
+// Y[j][dof] and the last L levels ring[slot][dof] are FP32 rows with a pitch
+// rounded up to 4 floats, so every thread moves 4 DOFs with 16-byte loads and
+// stores (a warp touches 512 contiguous bytes per row). The tables (r_j, c_j,
+// d_i) are FP32 in shared memory; inputs G^{n-1} and outputs h^n stay FP64.
+// Per DOF-step the traffic is 8 np (state) + 4 L (window and recurrence input)
+// + 4 (ring store) + 8 (G^{n-1}) + 8 (h^n) bytes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(64) k_history_fast_step_f32(int64_t ndof, int64_t pitch, int64_t n, int L,
+                                                               int np, const float *__restrict__ tabf,
+                                                               float *__restrict__ ring, float *__restrict__ Y,
+                                                               const double *__restrict__ G_prev,
+                                                               double *__restrict__ H) {
+    __shared__ float r[kMaxNp], c[kMaxNp], d[kMaxNs];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        r[i] = tabf[i];
+        c[i] = tabf[np + i];
+    }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) d[i] = tabf[2 * np + i];
+    __syncthreads();
+    const int64_t dof = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (dof >= ndof) return;
+    const int cnt = (int)min((int64_t)4, ndof - dof);
+    float4 gp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float h[4] = {0.f, 0.f, 0.f, 0.f};
+    if (n >= 2) {
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int v = 0; v < cnt; ++v) g[v] = (float)G_prev[dof + v];
+        gp = make_float4(g[0], g[1], g[2], g[3]);
+        h[0] = d[1] * gp.x;
+        h[1] = d[1] * gp.y;
+        h[2] = d[1] * gp.z;
+        h[3] = d[1] * gp.w;
+        const int64_t imax = min((int64_t)L - 1, n - 1);
+        for (int i = 2; i <= imax; ++i) {
+            const float4 x = *reinterpret_cast<const float4 *>(ring + (int64_t)((n - i) % L) * pitch + dof);
+            h[0] = fmaf(d[i], x.x, h[0]);
+            h[1] = fmaf(d[i], x.y, h[1]);
+            h[2] = fmaf(d[i], x.z, h[2]);
+            h[3] = fmaf(d[i], x.w, h[3]);
+        }
+    }
+    if (n - L >= 1) {
+        const float4 in = *reinterpret_cast<const float4 *>(ring + (int64_t)((n - L) % L) * pitch + dof);
+        float4 *yp = reinterpret_cast<float4 *>(Y + dof);
+        const int64_t step = pitch / 4;
+        constexpr int B = 8;                       // rows in flight per thread
+        for (int j0 = 0; j0 < np; j0 += B) {
+            float4 y[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k)
+                if (j0 + k < np) y[k] = yp[(int64_t)(j0 + k) * step];
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                if (j0 + k >= np) break;
+                const float rj = r[j0 + k], cj = c[j0 + k];
+                y[k].x = fmaf(rj, y[k].x, in.x);
+                y[k].y = fmaf(rj, y[k].y, in.y);
+                y[k].z = fmaf(rj, y[k].z, in.z);
+                y[k].w = fmaf(rj, y[k].w, in.w);
+                h[0] = fmaf(cj, y[k].x, h[0]);
+                h[1] = fmaf(cj, y[k].y, h[1]);
+                h[2] = fmaf(cj, y[k].z, h[2]);
+                h[3] = fmaf(cj, y[k].w, h[3]);
+            }
+#pragma unroll
+            for (int k = 0; k < B; ++k)
+                if (j0 + k < np) yp[(int64_t)(j0 + k) * step] = y[k];
+        }
+    }
+    if (n >= 2) *reinterpret_cast<float4 *>(ring + (int64_t)((n - 1) % L) * pitch + dof) = gp;
+    for (int v = 0; v < cnt; ++v) H[dof + v] = (double)h[v];
+}
+
+__global__ void k_tab_to_f32(const double *__restrict__ t, int n, float *__restrict__ f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = (float)t[i];
+}
+
 struct FastHistLayout {
     double *tab;       // r[np], c[np], d[L]
     double *scratch;   // Gauss-Jacobi nodes / weights
@@ -156,6 +236,28 @@ static FastHistLayout fast_hist_layout(void *ws, int np1, int np2, int L, int64_
     l.dfull = cv.take<double>(kMaxNs);
     l.ring = cv.take<double>((size_t)L * ndof);
     l.Y = cv.take<double>((size_t)np * ndof);
+    l.bytes = cv.bytes();
+    return l;
+}
+
+struct FastHistLayoutF32 {
+    double *tab, *scratch, *dfull;
+    float *tabf, *ring, *Y;
+    int64_t pitch;
+    size_t bytes;
+};
+
+static FastHistLayoutF32 fast_hist_layout_f32(void *ws, int np1, int np2, int L, int64_t ndof) {
+    Carve cv(ws);
+    FastHistLayoutF32 l;
+    const int np = np1 + np2;
+    l.pitch = (ndof + 3) / 4 * 4;
+    l.tab = cv.take<double>(2 * np + kMaxNs);
+    l.scratch = cv.take<double>(2 * (np1 + np2));
+    l.dfull = cv.take<double>(kMaxNs);
+    l.tabf = cv.take<float>(2 * np + kMaxNs);
+    l.ring = cv.take<float>((size_t)L * l.pitch);
+    l.Y = cv.take<float>((size_t)np * l.pitch);
     l.bytes = cv.bytes();
     return l;
 }
@@ -213,11 +315,41 @@ extern "C" int cq_history_fast(int32_t scheme, double beta, double tau, const cq
     if (!cfg || !ws_bytes || (scheme != CQ_BE && scheme != CQ_BDF2) || bad_order(beta) || !(tau > 0.0) ||
         ndof < 0 || n < 1)
         return CQ_EINVAL;
-    if (prec != CQ_F64) return CQ_EUNSUPPORTED;
+    if (prec != CQ_F64 && prec != CQ_F32) return CQ_EUNSUPPORTED;
     const int np1 = cfg->np1, np2 = (scheme == CQ_BE) ? 0 : cfg->np2;
     const int L = (scheme == CQ_BE) ? 2 : cfg->ns;
     if (np1 < 1 || np2 < 0 || np1 + np2 > kMaxNp || (scheme == CQ_BDF2 && (np2 < 1 || L < 3 || L > kMaxNs)))
         return CQ_EINVAL;
+    if (prec == CQ_F32) {
+        FastHistLayoutF32 lf = fast_hist_layout_f32(ws_dev, np1, np2, L, ndof);
+        if (!ws_dev) { *ws_bytes = lf.bytes; return CQ_OK; }
+        if (*ws_bytes < lf.bytes) return CQ_ENOMEM;
+        if (!H_dev || (n >= 2 && !G_prev_dev)) return CQ_EINVAL;
+        if (ndof == 0) return CQ_OK;
+        cudaStream_t s = (cudaStream_t)stream;
+        const int np = np1 + np2;
+        int st;
+        if (n == 1) {
+            if ((st = launch_weights(scheme, beta, tau, L - 1, lf.dfull, s))) return st;
+            if ((st = cuda_status(cudaMemcpyAsync(lf.tab + 2 * np, lf.dfull, L * sizeof(double),
+                                                  cudaMemcpyDeviceToDevice, s))))
+                return st;
+            if ((st = build_fast_coeffs(scheme, beta, tau, np1, np2, L, lf.scratch, lf.tab, lf.tab + np, s)))
+                return st;
+            k_tab_to_f32<<<1, 512, 0, s>>>(lf.tab, 2 * np + L, lf.tabf);
+            if ((st = launched())) return st;
+            if ((st = cuda_status(cudaMemsetAsync(lf.Y, 0, (size_t)np * lf.pitch * sizeof(float), s)))) return st;
+            if ((st = cuda_status(cudaMemsetAsync(lf.ring, 0, (size_t)L * lf.pitch * sizeof(float), s)))) return st;
+            return cuda_status(cudaMemsetAsync(H_dev, 0, (size_t)ndof * sizeof(double), s));
+        }
+        // small blocks: a short streaming kernel, so whole-block granularity per SM matters
+        const int64_t threads = (ndof + 3) / 4;
+        if ((st = timing_begin(s))) return st;
+        k_history_fast_step_f32<<<(unsigned)((threads + 63) / 64), 64, 0, s>>>(ndof, lf.pitch, n, L, np, lf.tabf,
+                                                                              lf.ring, lf.Y, G_prev_dev, H_dev);
+        if ((st = launched())) return st;
+        return timing_end(s);
+    }
     FastHistLayout lay = fast_hist_layout(ws_dev, np1, np2, L, ndof);
     if (!ws_dev) { *ws_bytes = lay.bytes; return CQ_OK; }
     if (*ws_bytes < lay.bytes) return CQ_ENOMEM;
@@ -238,9 +370,11 @@ extern "C" int cq_history_fast(int32_t scheme, double beta, double tau, const cq
         return cuda_status(cudaMemsetAsync(H_dev, 0, (size_t)ndof * sizeof(double), s));
     }
     const int64_t threads = (ndof + 1) / 2;
+    if ((st = timing_begin(s))) return st;
     k_history_fast_step<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ndof, n, L, np, lay.tab, lay.ring, lay.Y,
                                                                          G_prev_dev, H_dev);
-    return launched();
+    if ((st = launched())) return st;
+    return timing_end(s);
 }
 
 // ---------------------------------------------------------------------------

@@ -73,3 +73,33 @@ def test_fast_f32_rejected_where_unsupported(fc):
     cd = fc.problem(0.3, 0.7, 0.3, 1.0, 64, 1, 15, fc.CQ_BE, fc.CQ_DIRECT, prec=fc.CQ_F32)
     with pytest.raises(fc.CQError):
         fc.fp2s_solve(cd, g0, g0, None)
+
+
+@pytest.mark.parametrize("scheme,beta,np1,np2,ns,ndof,N", [(2, 0.6, 16, 64, 17, 1001, 300), (1, 0.3, 64, 0, 2, 7, 250),
+                                                          (2, 0.45, 8, 12, 5, 4096, 120)])
+def test_history_fast_f32_stream(fc, scheme, beta, np1, np2, ns, ndof, N):
+    """Streaming FP32 fast history against the oracle's FP64 fast history. Per element the
+    error is bounded by 2e-5 of sum_i |d_i| |G^{n-i}| (FP32 levels, states and sums)."""
+    from oracle import history as OH
+    from oracle import weights as OW
+    tau = 1.0 / N
+    G = ci.rng(9).standard_normal((N + 1, ndof))
+    Gd = torch.tensor(G, dtype=torch.float64, device="cuda")
+    H = torch.empty(ndof, dtype=torch.float64, device="cuda")
+    ws = fc.workspace(fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, 1, None, None, prec=fc.CQ_F32),
+                      "cuda")
+    ref_h = OH.FastHistoryBE(beta, tau, np1, ndof) if scheme == 1 else OH.FastHistorySBD(beta, tau, np1, np2, ns,
+                                                                                          ndof)
+    d = OW.weights(scheme, beta, tau, N)
+    worst = 0.0
+    for n in range(1, N + 1):
+        fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, n, Gd[n - 1], H, ws, prec=fc.CQ_F32)
+        torch.cuda.synchronize()
+        got = H.cpu().numpy()
+        ref = ref_h(n, G)
+        scale = np.abs(d[n - 1:0:-1]) @ np.abs(G[1:n]) if n >= 2 else np.zeros(ndof)
+        err = np.abs(got - ref)
+        assert np.all(err <= 2e-5 * scale + 1e-300), n
+        if n >= 2:
+            worst = max(worst, float(np.max(err / (scale + 1e-300))))
+    print("f32 stream history: max |err| / sum|d||G| = %.3e" % worst)
