@@ -30,6 +30,7 @@ struct Fp2sLayout {
     float *hdf;                   // FP32 fast form: 0.5*d_i of both states as double-float, [4][N+1]
     double *hist;                 // direct: (N+1) x 2 x nmodes
     double *Y, *ring, *glast;     // step API, fast: 2 x np x nm, 2 x L x nm; both: 2 levels x 2 x nm
+    void *mixed;                  // direct, CQ_BF16X3: region of the mixed-precision solve
     size_t bytes;
 };
 
@@ -40,10 +41,10 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.status = cv.take<int>(64);
     l.d1 = cv.take<double>(P.N + 1);
     l.d2 = cv.take<double>(P.N + 1);
-    if (P.form == CQ_DIRECT) {
+    if (P.form == CQ_DIRECT && P.prec == CQ_F64) {
         l.dz1 = cv.take<double>(P.N + 2 * kDirBT + 1);
         l.dz2 = cv.take<double>(P.N + 2 * kDirBT + 1);
-    } else {
+    } else if (P.form == CQ_FAST) {
         l.tab1 = cv.take<double>(2 * P.np);
         l.tab2 = cv.take<double>(2 * P.np);
         l.scr1 = cv.take<double>(2 * P.np);
@@ -54,8 +55,9 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.tmp = cv.take<double>(2 * nm);
     l.g0 = cv.take<double>(2 * nm);
     l.gN = cv.take<double>(2 * nm);
-    if (P.form == CQ_DIRECT) l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
-    if (P.prec == CQ_F32) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
+    if (P.form == CQ_DIRECT && P.prec == CQ_F64) l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
+    if (P.prec != CQ_F64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
+    if (P.form == CQ_DIRECT && P.prec == CQ_BF16X3) l.mixed = cv.take<char>(mixed_direct_bytes(P));
     if (stepper) {
         if (P.form == CQ_FAST) {
             l.Y = cv.take<double>((size_t)2 * P.np * nm);
@@ -76,7 +78,9 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     if (p->M < 1 || p->M > (p->dim == 1 ? (1 << 16) : 4096)) return CQ_EINVAL;
     if (p->scheme != CQ_BE && p->scheme != CQ_BDF2) return CQ_EINVAL;
     if (p->form != CQ_DIRECT && p->form != CQ_FAST) return CQ_EINVAL;
-    if (p->prec != CQ_F64 && !(p->prec == CQ_F32 && p->form == CQ_FAST)) return CQ_EUNSUPPORTED;
+    if (p->prec != CQ_F64 && !(p->prec == CQ_F32 && p->form == CQ_FAST) &&
+        !(p->prec == CQ_BF16X3 && p->form == CQ_DIRECT))
+        return CQ_EUNSUPPORTED;
     P.prec = p->prec;
     P.a = (1.0 - p->m) / (2.0 * p->m - 1.0);
     P.tau = p->T / (double)p->N;
@@ -261,49 +265,6 @@ static int fast_block_threads(int np, int L, int64_t nmodes) {
 // Every mode is pre-scaled by an exact power of two (from its G^0) so that its
 // values sit near 1 in FP32 range; the factor is undone on output.
 // ---------------------------------------------------------------------------
-// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
-// numbers (Dekker 1971, "A floating-point technique for extending the
-// available precision"; Knuth's TwoSum). Products use the FMA form of
-// Dekker's TwoProduct. About 44 significant bits, computed on the FP32 pipe.
-struct df {
-    float hi, lo;
-};
-
-__device__ __forceinline__ df df_from(double x) {
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-}
-
-__device__ __forceinline__ df df_fast_norm(float s, float e) {       // |s| >= |e|
-    const float t = s + e;
-    return {t, e - (t - s)};
-}
-
-__device__ __forceinline__ df df_add(df a, df b) {
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (b.hi - bb);
-    return df_fast_norm(s, e + (a.lo + b.lo));
-}
-
-__device__ __forceinline__ df df_mul(df a, df b) {
-    const float p = a.hi * b.hi;
-    const float e = fmaf(a.hi, b.hi, -p);
-    return df_fast_norm(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
-}
-
-__device__ __forceinline__ df df_mul_f(df a, float b) {
-    const float p = a.hi * b;
-    const float e = fmaf(a.hi, b, -p);
-    return df_fast_norm(p, fmaf(a.lo, b, e));
-}
-
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-
-__device__ __forceinline__ df df_shfl_xor16(df a) {
-    return {__shfl_xor_sync(0xffffffffu, a.hi, 16), __shfl_xor_sync(0xffffffffu, a.lo, 16)};
-}
-
 constexpr int kF32Threads = 128;
 
 template <int NP>
@@ -353,16 +314,9 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
     if (gmax > 0.0 && isfinite(gmax)) frexp(gmax, &ex);
     const float gz = (float)ldexp(gz64, -ex);
 
-    const double d_s0 = dn[0];
-    const double d_o0 = st ? d1[0] : d2[0];
-    ModeConst mc;
-    const bool ok = mode_setup(P, lam[mode], st ? d_o0 : d_s0, st ? d_s0 : d_o0, mc);
+    LaneStep ls;
+    const bool ok = lane_step_setup(P, lam[mode], d1[0], d2[0], st, ls);
     if (active && st == 0 && !ok) atomicOr(status, ST_SINGULAR);
-    const double mn_oo = st ? mc.Mn.i22 : mc.Mn.i11, mn_ot = st ? mc.Mn.i21 : mc.Mn.i12;
-    const double m1_oo = st ? mc.M1.i22 : mc.M1.i11, m1_ot = st ? mc.M1.i21 : mc.M1.i12;
-    const df da = df_from(P.a), dc = df_from(mc.c), dinv_tau = df_from(P.inv_tau);
-    const df dmn_oo = df_from(mn_oo), dmn_ot = df_from(mn_ot), dm1_oo = df_from(m1_oo), dm1_ot = df_from(m1_ot);
-    const df dd_s0_3 = df_from(d_s0 * (1.0 / 3.0));
 
     float Y[NP];
 #pragma unroll
@@ -396,49 +350,7 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
             else h2 = fmaf(ws[2 * i], Rc[(size_t)sl * T], h2);
         }
         const float h = (h0 + h1) + (h2 + h3);
-        float x;
-        if (solve64) {
-            double e, lead, m_oo = mn_oo, m_ot = mn_ot;
-            if (P.scheme == CQ_BE) {
-                e = h;
-                lead = (double)gm1 * P.inv_tau;
-            } else if (n == 1) {
-                e = d_s0 * (double)gz * (1.0 / 3.0);
-                lead = (double)gz * P.inv_tau;
-                m_oo = m1_oo;
-                m_ot = m1_ot;
-            } else {
-                e = fma(0.5 * __ldg(dn + n - 1), (double)gz, (double)h);
-                lead = (2.0 * (double)gm1 - 0.5 * (double)gm2) * P.inv_tau;
-            }
-            const double e_o = __shfl_xor_sync(0xffffffffu, e, 16);
-            const double b = lead - mc.c * e + P.a * e_o;
-            const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
-            x = (float)(m_oo * b + m_ot * b_o);
-        } else {
-            // double-float step: the FP32-rounded step coefficients would perturb the
-            // per-step amplification by ~1e-7, which compounds over the N steps
-            df e, lead;
-            df m_oo = dmn_oo, m_ot = dmn_ot;
-            if (P.scheme == CQ_BE) {
-                e = {h, 0.0f};
-                lead = df_mul_f(dinv_tau, gm1);
-            } else if (n == 1) {
-                e = df_mul_f(dd_s0_3, gz);
-                lead = df_mul_f(dinv_tau, gz);
-                m_oo = dm1_oo;
-                m_ot = dm1_ot;
-            } else {
-                e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
-                const df lin = df_add(df{2.0f * gm1, 0.0f}, df{-0.5f * gm2, 0.0f});
-                lead = df_mul(dinv_tau, lin);
-            }
-            const df e_o = df_shfl_xor16(e);
-            const df b = df_add(df_add(lead, df_neg(df_mul(dc, e))), df_mul(da, e_o));
-            const df b_o = df_shfl_xor16(b);
-            const df xx = df_add(df_mul(m_oo, b), df_mul(m_ot, b_o));
-            x = xx.hi + xx.lo;
-        }
+        const float x = lane_step(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
         Rc[(size_t)slot * T] = x;
         gm2 = gm1;
         gm1 = x;
@@ -478,9 +390,6 @@ __global__ void k_half_weights_df(const double *__restrict__ d1, const double *_
 
 static int fp2s_fast_f32(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
     const int solve64 = fabs(P.a) > 10.0;
-    k_half_weights_df<<<(unsigned)((P.N + 256) / 256), 256, 0, s>>>(l.d1, l.d2, P.N, l.hdf);
-    int st = launched();
-    if (st) return st;
     if (P.np <= 16) launch_f32<16>(P, solve64, l, s);
     else if (P.np <= 32) launch_f32<32>(P, solve64, l, s);
     else if (P.np <= 48) launch_f32<48>(P, solve64, l, s);
@@ -716,18 +625,43 @@ static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2,
     if ((st = cuda_status(cudaMemsetAsync(l.status, 0, 64 * sizeof(int), s)))) return st;
     if ((st = launch_weights(P.scheme, b1, P.tau, P.N, l.d1, s))) return st;
     if ((st = launch_weights(P.scheme, b2, P.tau, P.N, l.d2, s))) return st;
-    if (P.form == CQ_DIRECT) {
+    if (P.prec != CQ_F64) {
+        k_half_weights_df<<<(unsigned)((P.N + 256) / 256), 256, 0, s>>>(l.d1, l.d2, P.N, l.hdf);
+        if ((st = launched())) return st;
+    }
+    if (P.form == CQ_DIRECT && P.prec == CQ_F64) {
         const unsigned g = (unsigned)((P.N + 2 * kDirBT + 256) / 256);
         k_pad<<<g, 256, 0, s>>>(l.d1, P.N, kDirBT, l.dz1);
         k_pad<<<g, 256, 0, s>>>(l.d2, P.N, kDirBT, l.dz2);
         if ((st = launched(2))) return st;
-    } else {
+    } else if (P.form == CQ_FAST) {
         if ((st = build_fast_coeffs(P.scheme, b1, P.tau, np1, np2, P.L, l.scr1, l.tab1, l.tab1 + P.np, s))) return st;
         if ((st = build_fast_coeffs(P.scheme, b2, P.tau, np1, np2, P.L, l.scr2, l.tab2, l.tab2 + P.np, s))) return st;
     }
     if ((st = launch_mode_eigenvalues(p->M, p->dim, l.lam, s))) return st;
     if ((st = launch_dst_matrix(p->M, l.S, s))) return st;
     return launch_dst_field(p->M, p->dim, l.S, G0, l.g0, l.tmp, s);
+}
+
+// The single-launch solve kernels (fast FP64, fast FP32, direct FP64).
+static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
+    if (P.form == CQ_FAST && P.prec == CQ_F32) return fp2s_fast_f32(P, l, s);
+    if (P.form == CQ_FAST) {
+        const int T = fast_block_threads(P.np, P.L, P.nmodes);
+        if (T == 0) return CQ_EUNSUPPORTED;
+        const size_t smem = fast_smem_bytes(P.np, P.L, T);
+        cudaFuncSetAttribute(k_fp2s_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
+        const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
+        k_fp2s_fast<<<blocks, T, smem, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2);
+    } else {
+        // one-warp blocks: every block runs all N steps, so small blocks spread the
+        // modes evenly over the SMs (at most one warp of imbalance per SM)
+        const unsigned blocks = (unsigned)((P.nmodes + 31) / 32);
+        k_fp2s_direct<kDirBT><<<blocks, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2,
+                                                    l.hist);
+    }
+    return CQ_OK;
 }
 
 }  // namespace fastcq
@@ -748,24 +682,13 @@ extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double 
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
     if ((st = timing_begin(s))) return st;
-    if (P.form == CQ_FAST && P.prec == CQ_F32) {
-        if ((st = fp2s_fast_f32(P, l, s))) return st;
-    } else if (P.form == CQ_FAST) {
-        const int T = fast_block_threads(P.np, P.L, P.nmodes);
-        if (T == 0) return CQ_EUNSUPPORTED;
-        const size_t smem = fast_smem_bytes(P.np, P.L, T);
-        cudaFuncSetAttribute(k_fp2s_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
-        const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
-        k_fp2s_fast<<<blocks, T, smem, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2);
+    if (P.form == CQ_DIRECT && P.prec == CQ_BF16X3) {
+        // counts its own launches
+        if ((st = mixed_direct_run(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.hdf, l.mixed, s))) return st;
     } else {
-        // one-warp blocks: every block runs all N steps, so small blocks spread the
-        // modes evenly over the SMs (at most one warp of imbalance per SM)
-        const unsigned blocks = (unsigned)((P.nmodes + 31) / 32);
-        k_fp2s_direct<kDirBT><<<blocks, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2,
-                                                    l.hist);
+        if ((st = solve_kernel(P, l, s))) return st;
+        if ((st = launched())) return st;
     }
-    if ((st = launched())) return st;
     if ((st = timing_end(s))) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, l.gN, GN_dev, l.tmp, s))) return st;
     if (p->flags & FP2S_ASYNC) return CQ_OK;

@@ -72,6 +72,136 @@ __device__ __forceinline__ void mode_step(const Fp2sParams &P, const ModeConst &
     x2 = M->i21 * b1 + M->i22 * b2;
 }
 
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (Dekker 1971, "A floating-point technique for extending the
+// available precision"; Knuth's TwoSum). Products use the FMA form of
+// Dekker's TwoProduct. About 44 significant bits, computed on the FP32 pipe.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_from(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ df df_fast_norm(float s, float e) {       // |s| >= |e|
+    const float t = s + e;
+    return {t, e - (t - s)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return df_fast_norm(s, e + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return df_fast_norm(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    const float p = a.hi * b;
+    const float e = fmaf(a.hi, b, -p);
+    return df_fast_norm(p, fmaf(a.lo, b, e));
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_shfl_xor16(df a) {
+    return {__shfl_xor_sync(0xffffffffu, a.hi, 16), __shfl_xor_sync(0xffffffffu, a.lo, 16)};
+}
+
+// Per-lane constants of the FP32-precision step: a lane carries state st of one
+// mode (its partner lane, lane ^ 16, the other state). The step matrices are
+// formed in FP64 and kept as double-float values.
+struct LaneStep {
+    double c, mn_oo, mn_ot, m1_oo, m1_ot, d_s0;
+    df da, dc, dinv_tau, dmn_oo, dmn_ot, dm1_oo, dm1_ot, dd_s0_3;
+};
+
+__device__ __forceinline__ bool lane_step_setup(const Fp2sParams &P, double lam, double d10, double d20, int st,
+                                                LaneStep &ls) {
+    ModeConst mc;
+    const bool ok = mode_setup(P, lam, d10, d20, mc);
+    ls.c = mc.c;
+    ls.d_s0 = st ? d20 : d10;
+    ls.mn_oo = st ? mc.Mn.i22 : mc.Mn.i11;
+    ls.mn_ot = st ? mc.Mn.i21 : mc.Mn.i12;
+    ls.m1_oo = st ? mc.M1.i22 : mc.M1.i11;
+    ls.m1_ot = st ? mc.M1.i21 : mc.M1.i12;
+    ls.da = df_from(P.a);
+    ls.dc = df_from(mc.c);
+    ls.dinv_tau = df_from(P.inv_tau);
+    ls.dmn_oo = df_from(ls.mn_oo);
+    ls.dmn_ot = df_from(ls.mn_ot);
+    ls.dm1_oo = df_from(ls.m1_oo);
+    ls.dm1_ot = df_from(ls.m1_ot);
+    ls.dd_s0_3 = df_from(ls.d_s0 * (1.0 / 3.0));
+    return ok;
+}
+
+// One step of the lane's state from its FP32 history sum h (both lanes of a mode
+// call it together: the states are exchanged with shuffles). gm1, gm2 = g^{n-1},
+// g^{n-2} and gz = g^0 of the lane's state. dn: FP64 weights of the state;
+// hd_hi/hd_lo: d_i / 2 of the state as double-float. The right-hand side and the
+// 2x2 solve run in double-float arithmetic (FP32 pipe): FP32-rounded step
+// coefficients would perturb the per-step amplification by ~1e-7, which compounds
+// over the steps. solve64 selects FP64 instead (strong coupling, |a| > 10).
+__device__ __forceinline__ float lane_step(const Fp2sParams &P, const LaneStep &ls, int solve64, int64_t n, float h,
+                                           float gm1, float gm2, float gz, const double *__restrict__ dn,
+                                           const float *__restrict__ hd_hi, const float *__restrict__ hd_lo) {
+    if (solve64) {
+        double e, lead, m_oo = ls.mn_oo, m_ot = ls.mn_ot;
+        if (P.scheme == CQ_BE) {
+            e = h;
+            lead = (double)gm1 * P.inv_tau;
+        } else if (n == 1) {
+            e = ls.d_s0 * (double)gz * (1.0 / 3.0);
+            lead = (double)gz * P.inv_tau;
+            m_oo = ls.m1_oo;
+            m_ot = ls.m1_ot;
+        } else {
+            e = fma(0.5 * __ldg(dn + n - 1), (double)gz, (double)h);
+            lead = (2.0 * (double)gm1 - 0.5 * (double)gm2) * P.inv_tau;
+        }
+        const double e_o = __shfl_xor_sync(0xffffffffu, e, 16);
+        const double b = lead - ls.c * e + P.a * e_o;
+        const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
+        return (float)(m_oo * b + m_ot * b_o);
+    }
+    df e, lead;
+    df m_oo = ls.dmn_oo, m_ot = ls.dmn_ot;
+    if (P.scheme == CQ_BE) {
+        e = {h, 0.0f};
+        lead = df_mul_f(ls.dinv_tau, gm1);
+    } else if (n == 1) {
+        e = df_mul_f(ls.dd_s0_3, gz);
+        lead = df_mul_f(ls.dinv_tau, gz);
+        m_oo = ls.dm1_oo;
+        m_ot = ls.dm1_ot;
+    } else {
+        e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
+        const df lin = df_add(df{2.0f * gm1, 0.0f}, df{-0.5f * gm2, 0.0f});
+        lead = df_mul(ls.dinv_tau, lin);
+    }
+    const df e_o = df_shfl_xor16(e);
+    const df b = df_add(df_add(lead, df_neg(df_mul(ls.dc, e))), df_mul(ls.da, e_o));
+    const df b_o = df_shfl_xor16(b);
+    const df xx = df_add(df_mul(m_oo, b), df_mul(m_ot, b_o));
+    return xx.hi + xx.lo;
+}
+
 constexpr int kFastModesPerWarp = 16;     // a warp carries 16 modes x 2 states
+
+// Mixed-precision direct solve (mixed.cu): workspace bytes of its own region, and
+// the run over all N steps (weights, spectrum and the modal G^0 already in place;
+// hdf: d_i / 2 of both states as double-float, [4][N + 1]).
+size_t mixed_direct_bytes(const Fp2sParams &P);
+int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
+                     const double *d1, const double *d2, const float *hdf, void *region, cudaStream_t s);
 
 }  // namespace fastcq

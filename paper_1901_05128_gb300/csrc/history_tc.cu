@@ -27,13 +27,11 @@
 
 #include "bf16split.h"
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace fastcq {
 namespace tc {
 
-constexpr int BM = 128;                     // steps per tile (UMMA M)
-constexpr int BN = 256;                     // DOFs per tile (UMMA N)
-constexpr int BK = 64;                      // levels per stage (one 128-byte swizzle row of BF16)
 constexpr int STAGES = 2;
 constexpr int A_BYTES = BM * BK * 2;        // 16 KiB
 constexpr int B_BYTES = BN * BK * 2;        // 32 KiB
@@ -151,20 +149,40 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
     return __longlong_as_double((long long)bits);
 }
 
-struct TcParams {
-    int64_t ndof, n_lo, rows, ldh;
-    int vec2;                  // H rows 16-byte aligned: store double2 pairs
-    int num_i;                 // tiles along the steps
-    int64_t delta0;            // delta of bank tile 0
-    int kprime;                // number of levels K' = n_hi - 2 (levels 1 .. n_hi - 2)
-};
+// Store 16 accumulator values of one row at columns c0.. (NaN when the MMA result is missing).
+__device__ __forceinline__ void store16(double *row, int64_t c0, int64_t ncol, int vec2, bool have, const float *v) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (vec2 && c0 + 16 <= ncol) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+            const double2 pr = have ? make_double2(f32_to_f64_bits(v[i]), f32_to_f64_bits(v[i + 1]))
+                                    : make_double2(nan, nan);
+            *reinterpret_cast<double2 *>(row + c0 + i) = pr;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (c0 + i < ncol) row[c0 + i] = have ? f32_to_f64_bits(v[i]) : nan;
+    }
+}
 
-__global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_constant__ CUtensorMap tA_hi,
-                                                                 const __grid_constant__ CUtensorMap tA_lo,
-                                                                 const __grid_constant__ CUtensorMap tB_hi,
-                                                                 const __grid_constant__ CUtensorMap tB_lo,
-                                                                 TcParams P, double *__restrict__ H,
-                                                                 int *__restrict__ status) {
+__device__ __forceinline__ void store16(float *row, int64_t c0, int64_t ncol, int vec2, bool have, const float *v) {
+    const float nan = __int_as_float(0x7fc00000);
+    if (vec2 && c0 + 16 <= ncol) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+            *reinterpret_cast<float4 *>(row + c0 + i) =
+                have ? make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]) : make_float4(nan, nan, nan, nan);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (c0 + i < ncol) row[c0 + i] = have ? v[i] : nan;
+    }
+}
+
+template <typename OutT>
+__global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_constant__ TcMaps maps, TcParams P,
+                                                                 OutT *__restrict__ H, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -175,10 +193,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t b = blockIdx.x;
-    const int nt = (int)(b / P.num_i);
+    const int64_t ntile = b / P.num_i;
+    const int state = (int)(ntile / P.ntile_state);
+    const int nt = (int)(ntile % P.ntile_state);
     const int it = P.num_i - 1 - (int)(b % P.num_i);          // longest K range first
     const int64_t m0 = P.n_lo + (int64_t)it * BM;              // first step of the tile
-    const int64_t n0 = (int64_t)nt * BN;                       // first DOF of the tile
+    const int64_t n0 = (int64_t)nt * BN;                       // first DOF of the tile (within its state)
+    const int64_t brow = (int64_t)state * P.state_stride + n0; // first row of the levels operand
+    const CUtensorMap *tA_hi = &maps.a_hi[state], *tA_lo = &maps.a_lo[state];
+    const CUtensorMap *tB_hi = &maps.b_hi, *tB_lo = &maps.b_lo;
     const int64_t m_last = min(m0 + BM - 1, P.n_lo + P.rows - 1);
     // levels k' < m_last - 1 contribute (k = k' + 1 <= m_last - 1)
     const int64_t k_end = min((int64_t)P.kprime, m_last - 1);
@@ -223,10 +246,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
             const int64_t delta = m0 - 1 - (int64_t)ks * BK;
             const int arow = (int)((delta - P.delta0) / BK) * BM;
             mbar_expect_tx(&full[s], STAGE_BYTES);
-            tma_load_2d(st, &tA_hi, &full[s], 0, arow);
-            tma_load_2d(st + A_BYTES, &tA_lo, &full[s], 0, arow);
-            tma_load_2d(st + 2 * A_BYTES, &tB_hi, &full[s], ks * BK, (int)n0);
-            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tB_lo, &full[s], ks * BK, (int)n0);
+            tma_load_2d(st, tA_hi, &full[s], 0, arow);
+            tma_load_2d(st + A_BYTES, tA_lo, &full[s], 0, arow);
+            tma_load_2d(st + 2 * A_BYTES, tB_hi, &full[s], ks * BK, (int)brow);
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, tB_lo, &full[s], ks * BK, (int)brow);
             armed[s] = ks;
         }
         if (*(volatile int *)abort_flag) {
@@ -270,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
             if (!have) atomicOr(status, ST_TIMEOUT);
             tc_fence_after();
         }
-        double *hrow = H + (m - P.n_lo) * P.ldh;
+        OutT *hrow = H + (m - P.n_lo) * P.ldh + (int64_t)state * P.state_stride;
         for (int c = 0; c < BN; c += 16) {
             float v[16];
             if (num_k > 0 && !aborted) {
@@ -279,23 +302,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = 0.0f;
             }
-            if (row_ok) {
-                const double nan = __longlong_as_double(0x7ff8000000000000ll);
-                if (P.vec2 && n0 + c + 16 <= P.ndof) {
-#pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        const double2 pr = have ? make_double2(f32_to_f64_bits(v[i]), f32_to_f64_bits(v[i + 1]))
-                                                : make_double2(nan, nan);
-                        *reinterpret_cast<double2 *>(hrow + n0 + c + i) = pr;
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int64_t dof = n0 + c + i;
-                        if (dof < P.ndof) hrow[dof] = have ? f32_to_f64_bits(v[i]) : nan;
-                    }
-                }
-            }
+            if (row_ok) store16(hrow, n0 + c, P.ndof, P.vec2, have, v);
         }
     }
     tc_fence_before();
@@ -421,6 +428,18 @@ static TcLayout tc_layout(void *ws, int64_t ndof, int64_t n_lo, int64_t n_hi) {
     return l;
 }
 
+static int tc_attr() {
+    static bool done = false;
+    if (done) return CQ_OK;
+    if (cudaFuncSetAttribute(k_history_tc_bf16x3<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(k_history_tc_bf16x3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES) != cudaSuccess)
+        return CQ_ECUDA;
+    done = true;
+    return CQ_OK;
+}
+
 }  // namespace tc
 
 size_t history_tc_workspace(int64_t ndof, int64_t n_lo, int64_t n_hi) {
@@ -444,11 +463,13 @@ int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_
     dim3 tg((unsigned)(l.kpad / 64), (unsigned)((ndof + 31) / 32));
     k_split_transpose<<<tg, dim3(32, 8), 0, s>>>(G, ldg, ndof, kprime, l.kpad, l.g_hi, l.g_lo);
     if ((st = launched())) return st;
-    CUtensorMap mA_hi, mA_lo, mB_hi, mB_lo;
-    if ((st = make_map(&mA_hi, l.a_hi, BK, (uint64_t)l.ntiles * BM, BK, BM))) return st;
-    if ((st = make_map(&mA_lo, l.a_lo, BK, (uint64_t)l.ntiles * BM, BK, BM))) return st;
-    if ((st = make_map(&mB_hi, l.g_hi, l.kpad, ndof, l.kpad, BN))) return st;
-    if ((st = make_map(&mB_lo, l.g_lo, l.kpad, ndof, l.kpad, BN))) return st;
+    TcMaps maps;
+    if ((st = make_map(&maps.a_hi[0], l.a_hi, BK, (uint64_t)l.ntiles * BM, BK, BM))) return st;
+    if ((st = make_map(&maps.a_lo[0], l.a_lo, BK, (uint64_t)l.ntiles * BM, BK, BM))) return st;
+    maps.a_hi[1] = maps.a_hi[0];
+    maps.a_lo[1] = maps.a_lo[0];
+    if ((st = make_map(&maps.b_hi, l.g_hi, l.kpad, ndof, l.kpad, BN))) return st;
+    if ((st = make_map(&maps.b_lo, l.g_lo, l.kpad, ndof, l.kpad, BN))) return st;
     TcParams P;
     P.ndof = ndof;
     P.n_lo = n_lo;
@@ -459,19 +480,46 @@ int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_
     P.delta0 = l.delta0;
     P.kprime = kprime;
     const int64_t num_n = (ndof + BN - 1) / BN;
+    P.n_states = 1;
+    P.ntile_state = num_n;
+    P.state_stride = 0;
     const int64_t blocks = num_n * P.num_i;
     if (blocks > 0x7fffffffLL) return CQ_EUNSUPPORTED;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_history_tc_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) !=
-            cudaSuccess)
-            return CQ_ECUDA;
-        attr = true;
-    }
+    if ((st = tc_attr())) return st;
     if ((st = timing_begin(s))) return st;
-    k_history_tc_bf16x3<<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(mA_hi, mA_lo, mB_hi, mB_lo, P, H, l.status);
+    k_history_tc_bf16x3<double><<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(maps, P, H, l.status);
     if ((st = launched())) return st;
     return timing_end(s);
+}
+
+int tc_bank(const double *d, int64_t nw, int64_t delta0, int ntiles, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+            cudaStream_t s) {
+    using namespace tc;
+    const int64_t elems = (int64_t)ntiles * BM * BK;
+    if (elems <= 0) return CQ_EINVAL;
+    k_toeplitz_bank<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(d, nw, delta0, ntiles, hi, lo);
+    return launched();
+}
+
+int tc_map_bank(CUtensorMap *m, const __nv_bfloat16 *bank, int ntiles) {
+    using namespace tc;
+    return make_map(m, bank, BK, (uint64_t)ntiles * BM, BK, BM);
+}
+
+int tc_map_levels(CUtensorMap *m, const __nv_bfloat16 *levels, int64_t kpad, int64_t rows) {
+    using namespace tc;
+    if (kpad % BK) return CQ_EINVAL;
+    return make_map(m, levels, (uint64_t)kpad, (uint64_t)rows, (uint64_t)kpad, BN);
+}
+
+int tc_contract_f32(const tc::TcMaps &maps, const tc::TcParams &P, float *H, int *status, cudaStream_t s) {
+    using namespace tc;
+    const int64_t blocks = P.ntile_state * P.n_states * P.num_i;
+    if (blocks <= 0 || blocks > 0x7fffffffLL) return CQ_EUNSUPPORTED;
+    int st;
+    if ((st = tc_attr())) return st;
+    k_history_tc_bf16x3<float><<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(maps, P, H, status);
+    return launched();
 }
 
 }  // namespace fastcq

@@ -49,19 +49,20 @@ def main(argv=None):
         p = p.replace(scheme=ci.BE if a.scheme == "be" else ci.BDF2)
     if a.N:
         p = p.replace(N=a.N, T=p.T * a.N / p.N)
-    if a.prec == "bf16x3":
-        raise SystemExit("bf16x3 applies to --history")
+    prec = {"f64": fc.CQ_F64, "f32": fc.CQ_F32, "bf16x3": fc.CQ_BF16X3}[a.prec]
     cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
-                    prec=fc.CQ_F32 if a.prec == "f32" else fc.CQ_F64)
+                    prec=prec)
     g0 = torch.tensor(G0 * 2.0 ** a.scale_exp, dtype=torch.float64, device="cuda")
     gN = torch.empty_like(g0)
     ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None))
+    fc.cq_timing_enable(True)
     for r in range(a.repeat):
         torch.cuda.synchronize()
         t = time.perf_counter()
         st = fc.fp2s_solve(cp, g0, gN, ws, check=False)
         torch.cuda.synchronize()
-        print("solve %d: %.3f s status=%s" % (r, time.perf_counter() - t, fc.strerror(st)))
+        print("solve %d: %.3f s (time-stepping %.3f ms) status=%s"
+              % (r, time.perf_counter() - t, fc.cq_timing_last(), fc.strerror(st)))
 
 
 def run_history(fc, torch, a):

@@ -1,0 +1,113 @@
+"""Mixed-precision direct solve (form = CQ_DIRECT, prec = CQ_BF16X3) against the FP64
+oracle (``-m gpu``).
+
+The history of Eq. 3.8 is split per time block of 128 steps: the part from earlier
+blocks is a tensor-core contraction of BF16 hi + lo operands with FP32 accumulation,
+the in-block part an FP32 sum, and the step (Eq. 4.1 / Eq. 4.7) is evaluated in
+double-float arithmetic (FP64 when |a| > 10). Every history term then carries a relative
+error of at most about 3 * 2^-16 (split operands, lo * lo dropped) plus the FP32
+accumulation, so |h_err| <= (3 * 2^-16 + K 2^-24) sum_i |d_i| |g^{n-i}|. A history
+error enters the step like a perturbed right-hand side; the step is contractive for the
+stable problems here, and the per-step errors, mostly random in sign, add up over the
+N steps. The bound used, relative L2 error <= 5e-4 per state at the final step, follows
+from N * 3 * 2^-16 * sum|d||g| / |d_0 g| with sum_i |d_i| <= 2 d_0 (BE weights; BDF2 alike)
+for N of a few hundred in the worst (fully correlated) case; measured errors are far
+smaller and are printed.
+"""
+import numpy as np
+import pytest
+
+import cq_inputs as ci
+from oracle import scheme as OS
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1901_05128_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+def _solve(fc, p, G0, prec):
+    cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
+                    prec=prec)
+    g0 = torch.tensor(G0, dtype=torch.float64, device="cuda")
+    gN = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), "cuda")
+    st = fc.fp2s_solve(cp, g0, gN, ws, check=False)
+    torch.cuda.synchronize()
+    return gN.cpu().numpy(), st
+
+
+def _rel(got, ref):
+    return [float(np.linalg.norm(got[s] - ref[s]) / np.linalg.norm(ref[s])) for s in range(2)]
+
+
+MIXED_CASES = [
+    # name, problem (form DIRECT), G0 scale exponent
+    ("be_1d_3blocks_ragged", ci.Problem(0.3, 0.7, 0.4, 1.0, 300, 1, 63, ci.BE, ci.DIRECT, 0, 0, 0), -200),
+    ("bdf2_1d_8blocks", ci.Problem(0.4, 0.6, 0.3, 1.0, 1000, 1, 127, ci.BDF2, ci.DIRECT, 0, 0, 0), 0),
+    ("bdf2_2d_ragged_tiles", ci.Problem(0.4, 0.6, 0.7, 1.0, 600, 2, 23, ci.BDF2, ci.DIRECT, 0, 0, 0), 300),
+    ("be_2d_m0.45", ci.Problem(0.2, 0.8, 0.45, 1.0, 520, 2, 31, ci.BE, ci.DIRECT, 0, 0, 0), 0),
+    ("bdf2_1d_m0.48_solve64", ci.Problem(0.5, 0.7, 0.48, 0.5, 400, 1, 31, ci.BDF2, ci.DIRECT, 0, 0, 0), 0),
+    ("be_1d_one_block", ci.Problem(0.6, 0.3, 0.2, 1.0, 128, 1, 17, ci.BE, ci.DIRECT, 0, 0, 0), 0),
+    ("bdf2_1d_block_plus_one", ci.Problem(0.6, 0.3, 0.6, 1.0, 129, 1, 17, ci.BDF2, ci.DIRECT, 0, 0, 0), 0),
+    ("be_1d_N1", ci.Problem(0.3, 0.7, 0.4, 1.0, 1, 1, 9, ci.BE, ci.DIRECT, 0, 0, 0), 0),
+    ("bdf2_1d_N2", ci.Problem(0.3, 0.7, 0.4, 1.0, 2, 1, 9, ci.BDF2, ci.DIRECT, 0, 0, 0), 0),
+]
+
+
+@pytest.mark.parametrize("name,p,sc", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_direct_mixed_against_fp64_oracle(fc, name, p, sc):
+    G0 = ci.g0_uniform(p.M, p.dim, 23) * 2.0 ** sc
+    got, st = _solve(fc, p, G0, fc.CQ_BF16X3)
+    assert st == fc.CQ_OK
+    ref = OS.solve(p, G0)
+    errs = _rel(got, ref)
+    print("mixed direct %s rel L2 errors %.3e %.3e" % (name, errs[0], errs[1]))
+    assert max(errs) <= 5e-4
+
+
+def test_direct_mixed_every_step_count(fc):
+    """Final states of the mixed solve for every N in 1..40 and around the block edges
+    (each N is its own problem, tau = T / N), against the oracle."""
+    worst = 0.0
+    for N in list(range(1, 41)) + [127, 128, 129, 255, 256, 257]:
+        p = ci.Problem(0.3, 0.6, 0.35, 1.0, N, 1, 15, ci.BDF2 if N % 2 else ci.BE, ci.DIRECT, 0, 0, 0)
+        G0 = ci.g0_uniform(p.M, p.dim, 100 + N)
+        got, st = _solve(fc, p, G0, fc.CQ_BF16X3)
+        assert st == fc.CQ_OK, N
+        errs = _rel(got, OS.solve(p, G0))
+        worst = max(worst, max(errs))
+        assert max(errs) <= 5e-4, N
+    print("mixed direct, N in 1..40 and block edges: worst rel L2 error %.3e" % worst)
+
+
+def test_direct_mixed_matches_fp64_gpu_solve(fc):
+    """Same problem through the FP64 direct kernel and the mixed solve: agree to the bound."""
+    p = ci.Problem(0.2, 0.8, 0.45, 1.0, 700, 2, 47, ci.BE, ci.DIRECT, 0, 0, 0)
+    G0 = ci.g0_disc_gaussian(p.M, 5)
+    g64, st64 = _solve(fc, p, G0, fc.CQ_F64)
+    gmx, stmx = _solve(fc, p, G0, fc.CQ_BF16X3)
+    assert st64 == fc.CQ_OK and stmx == fc.CQ_OK
+    errs = _rel(gmx, g64)
+    print("mixed vs FP64 GPU direct: %.3e %.3e" % tuple(errs))
+    assert max(errs) <= 5e-4
+
+
+def test_mixed_form_rejected_for_fast_and_stepper(fc):
+    g0 = torch.zeros((2, 15), dtype=torch.float64, device="cuda")
+    cf = fc.problem(0.3, 0.7, 0.3, 1.0, 64, 1, 15, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2, prec=fc.CQ_BF16X3)
+    with pytest.raises(fc.CQError) as e:
+        fc.fp2s_solve(cf, g0, g0, None)
+    assert e.value.status == fc.CQ_EUNSUPPORTED
+    cd = fc.problem(0.3, 0.7, 0.3, 1.0, 64, 1, 15, fc.CQ_BE, fc.CQ_DIRECT, prec=fc.CQ_BF16X3)
+    with pytest.raises(fc.CQError) as e:
+        fc.fp2s_init(cd, g0, None)
+    assert e.value.status == fc.CQ_EUNSUPPORTED
