@@ -6,8 +6,10 @@
 // Toeplitz contraction on the tensor cores (history_tc.cu: tcgen05, split BF16
 // operands, FP32 accumulation), with a separate weight bank per state; the rest,
 // from the levels n0 .. n-1 of the block itself, is formed step by step in FP32
-// by the kernel that also takes the steps (Eq. 4.1 / Eq. 4.7 in the sine basis),
-// evaluated in double-float arithmetic from the FP32 history sums (lane_step).
+// by the kernel that also takes the steps (Eq. 4.1 / Eq. 4.7 in the sine basis).
+// A step is evaluated from the FP32 history sums in the two-term form
+// x = A l + B e with a double-float A (lane_step2), or in FP64 when the coupling
+// is strong (|a| > 10); the first SBD step uses the double-float form (lane_step).
 //
 // Every mode is pre-scaled by an exact power of two from its G^0, as in the FP32
 // fast form, so its values sit near 1 in the FP32 / BF16 range; the contraction
@@ -22,15 +24,17 @@
 namespace fastcq {
 
 constexpr int kMxB = 128;      // steps per time block (= one tensor-core M tile)
-constexpr int kMxSB = 8;       // register window of the in-block sums
+constexpr int kMxSB = 8;       // sub-block / chunk of the in-block sums
 constexpr int kMxT = 128;      // threads per CTA: 64 modes x 2 states
-constexpr int kMxW = kMxB + kMxSB;
+constexpr int kMxWOff = 7;                 // weight table: entry i holds d_{i - 7}
+constexpr int kMxW = kMxB + 2 * kMxSB;     // entries per state (d_{-7} .. d_{kMxB + 8})
 
 struct MixedLayout {
     __nv_bfloat16 *a_hi[2], *a_lo[2];   // Toeplitz banks of d^1 and d^2
     __nv_bfloat16 *gt_hi, *gt_lo;       // levels, K-major: row s * nmp + mode, column k - 1
     float *acc;                         // contraction output [kMxB][2 * nmp]
     float *carry;                       // g^{n-1}, g^{n-2} at the end of a block: [2][2 * nmp]
+    float4 *coef;                       // per lane: (A row as double-float), (B row, scaled g^0, exponent)
     int nblk, ntiles;
     int64_t nmp, kpad;
     size_t bytes;
@@ -54,6 +58,7 @@ static MixedLayout mixed_layout(const Fp2sParams &P, void *base) {
     l.gt_lo = cv.take<__nv_bfloat16>(lev);
     l.acc = cv.take<float>(l.nblk > 1 ? (size_t)kMxB * 2 * l.nmp : 0);
     l.carry = cv.take<float>((size_t)4 * l.nmp);
+    l.coef = cv.take<float4>((size_t)4 * l.nmp);
     l.bytes = cv.bytes();
     return l;
 }
@@ -67,6 +72,7 @@ struct MixedArgs {
     const double *lam, *g0, *d1, *d2;
     const float *hdf, *acc;
     float *carry;
+    float4 *coef;
     __nv_bfloat16 *gt_hi, *gt_lo;
     double *gN;
     int *status;
@@ -83,19 +89,21 @@ __device__ __forceinline__ void split_f32(float x, uint32_t &h, uint32_t &l) {
 // Steps n0 .. min(n0 + kMxB - 1, N) of 64 modes per CTA. Lanes l < 16 of a warp
 // carry state 1 and lanes l + 16 state 2 of the same 16 modes. acc (absent for the
 // first block) holds the contribution of the earlier blocks' levels. The block's
-// levels stay in shared memory (column tid, conflict-free) for the in-block sums:
-// sub-blocks of kMxSB steps first take the earlier in-block levels with a
-// shifting register window of weights (one shared-memory load feeds kMxSB FMAs),
+// levels stay in shared memory for the in-block sums, four consecutive levels of a
+// thread in one 16-byte word (a warp's 16-byte loads cover 512 contiguous bytes).
+// Sub-blocks of kMxSB steps first take the earlier in-block levels in 8 x 8
+// Toeplitz chunks (15 weights and 8 levels, six 16-byte loads, feed 64 FMAs),
 // then their own triangle step by step.
 __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ MixedArgs A) {
     extern __shared__ __align__(16) float smx[];
-    float *xs = smx;                          // [kMxB][kMxT]
-    float *wsm = smx + kMxB * kMxT;           // [2][kMxW]: d_i of each state, i < kMxW
+    // levels of the block: level n0 + j of thread t at xs[((j / 4) * kMxT + t) * 4 + j % 4]
+    float *xs = smx;
+    float *wsm = smx + kMxB * kMxT;           // [2][kMxW]: entry i = d_{i - kMxWOff} of each state
     const Fp2sParams &P = A.P;
     const int tid = threadIdx.x, lane = tid & 31, st = lane >> 4;
     for (int i = tid; i < 2 * kMxW; i += kMxT) {
-        const int s = i / kMxW, ii = i % kMxW;
-        wsm[i] = ii <= P.N ? (float)(s ? A.d2 : A.d1)[ii] : 0.0f;
+        const int s = i / kMxW, ii = i % kMxW - kMxWOff;
+        wsm[i] = (ii >= 0 && ii <= P.N) ? (float)(s ? A.d2 : A.d1)[ii] : 0.0f;
     }
     __syncthreads();
 
@@ -104,15 +112,36 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     const int64_t mode = active ? mode_raw : 0;
     const int64_t col = st * A.nmp + mode;
 
-    const double gz64 = A.g0[st * P.nmodes + mode];
-    const double gmax = fmax(fabs(gz64), fabs(__shfl_xor_sync(0xffffffffu, gz64, 16)));
-    int ex = 0;
-    if (gmax > 0.0 && isfinite(gmax)) frexp(gmax, &ex);
-    const float gz = (float)ldexp(gz64, -ex);
-
+    // per-lane step coefficients: formed in FP64 by the first block (and by every block
+    // when the FP64 step is in use), read back from the table by the others
     LaneStep ls;
-    const bool ok = lane_step_setup(P, A.lam[mode], A.d1[0], A.d2[0], st, ls);
-    if (A.n0 == 1 && active && st == 0 && !ok) atomicOr(A.status, ST_SINGULAR);
+    LaneStep2 l2;
+    float gz;
+    int ex = 0;
+    const bool full_setup = A.n0 == 1 || A.solve64;
+    if (full_setup) {
+        const double gz64 = A.g0[st * P.nmodes + mode];
+        const double gmax = fmax(fabs(gz64), fabs(__shfl_xor_sync(0xffffffffu, gz64, 16)));
+        if (gmax > 0.0 && isfinite(gmax)) frexp(gmax, &ex);
+        gz = (float)ldexp(gz64, -ex);
+        const bool ok = lane_step_setup(P, A.lam[mode], A.d1[0], A.d2[0], st, ls);
+        if (A.n0 == 1 && active && st == 0 && !ok) atomicOr(A.status, ST_SINGULAR);
+        lane_step2_setup(P, ls, st, l2);
+        if (A.n0 == 1 && active) {
+            A.coef[col] = make_float4(l2.a_hi[0], l2.a_hi[1], l2.a_lo[0], l2.a_lo[1]);
+            A.coef[2 * A.nmp + col] = make_float4(l2.b[0], l2.b[1], gz, __int_as_float(ex));
+        }
+    } else {
+        const float4 c0 = A.coef[col], c1 = A.coef[2 * A.nmp + col];
+        l2.a_hi[0] = c0.x;
+        l2.a_hi[1] = c0.y;
+        l2.a_lo[0] = c0.z;
+        l2.a_lo[1] = c0.w;
+        l2.b[0] = c1.x;
+        l2.b[1] = c1.y;
+        gz = c1.z;
+        ex = __float_as_int(c1.w);
+    }
     const double *dn = st ? A.d2 : A.d1;
     const float *hd_hi = A.hdf + (size_t)(2 * st) * (P.N + 1), *hd_lo = hd_hi + (P.N + 1);
 
@@ -121,38 +150,70 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
         gm1 = A.carry[col];
         gm2 = A.carry[2 * A.nmp + col];
     }
-    const float *w = wsm + st * kMxW;
-    float *xc = xs + tid;
+    float gm1_o = __shfl_xor_sync(0xffffffffu, gm1, 16), gm2_o = __shfl_xor_sync(0xffffffffu, gm2, 16);
+    const float *w = wsm + st * kMxW + kMxWOff;     // w[i] = d_i, i >= -kMxWOff
+    float wt[kMxSB];                                 // d_1 .. d_7 of the lane's state
+#pragma unroll
+    for (int i = 1; i < kMxSB; ++i) wt[i] = w[i];
+    float *xc = xs + 4 * tid;
+    const float4 *xs4 = reinterpret_cast<const float4 *>(xs) + tid;
     const int64_t ldacc = 2 * A.nmp;
-    for (int j0 = 0; j0 < kMxB; j0 += kMxSB) {
-        if (A.n0 + j0 > P.N) break;
-        float a[kMxSB], wv[kMxSB];
+    const int jmax = (int)min((int64_t)kMxB, P.N - A.n0 + 1);      // steps in this block
+    float an[kMxSB];                                 // acc rows of the next sub-block (prefetched)
 #pragma unroll
-        for (int b = 0; b < kMxSB; ++b) {
-            a[b] = A.acc ? A.acc[(int64_t)(j0 + b) * ldacc + col] : 0.0f;
-            wv[b] = w[j0 + b];                      // d_{j0 + b - k} at k = 0
+    for (int b = 0; b < kMxSB; ++b) an[b] = A.acc ? A.acc[(int64_t)b * ldacc + col] : 0.0f;
+    for (int j0 = 0; j0 < jmax; j0 += kMxSB) {
+        float a[kMxSB];
+#pragma unroll
+        for (int b = 0; b < kMxSB; ++b) a[b] = an[b];
+        if (A.acc && j0 + kMxSB < jmax) {
+#pragma unroll
+            for (int b = 0; b < kMxSB; ++b) an[b] = A.acc[(int64_t)(j0 + kMxSB + b) * ldacc + col];
         }
-        for (int k = 0; k < j0; ++k) {
-            const float x = xc[k * kMxT];
+        // earlier in-block levels k in chunks of 8: a[b] += sum_kk d_{j0 + b - kc - kk} x^{n0 + kc + kk};
+        // the 15 weights of a chunk are d_{m-7} .. d_{m+7}, m = j0 - kc (four 16-byte loads)
+        for (int kc = 0; kc < j0; kc += kMxSB) {
+            const float4 *wp = reinterpret_cast<const float4 *>(w + (j0 - kc) - kMxWOff);
+            float W[16];
 #pragma unroll
-            for (int b = 0; b < kMxSB; ++b) a[b] = fmaf(wv[b], x, a[b]);
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = wp[q];
+                W[4 * q] = v.x;
+                W[4 * q + 1] = v.y;
+                W[4 * q + 2] = v.z;
+                W[4 * q + 3] = v.w;
+            }
+            const float4 x0 = xs4[(kc / 4) * kMxT], x1 = xs4[(kc / 4 + 1) * kMxT];
+            const float X[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-            for (int b = kMxSB - 1; b > 0; --b) wv[b] = wv[b - 1];
-            wv[0] = w[j0 - k - 1];
+            for (int kk = 0; kk < kMxSB; ++kk)
+#pragma unroll
+                for (int b = 0; b < kMxSB; ++b) a[b] = fmaf(W[b - kk + kMxWOff], X[kk], a[b]);
         }
-        float lv[kMxSB];
+        // the sub-block's own triangle: each new level is added forward into the later sums
 #pragma unroll
         for (int b = 0; b < kMxSB; ++b) {
             const int64_t n = A.n0 + j0 + b;
-            if (n > P.N) break;
-            float h = a[b];
+            if (j0 + b >= jmax) break;
+            const float h = a[b];
+            float x;
+            if (full_setup && (A.solve64 || (P.scheme == CQ_BDF2 && n == 1))) {
+                x = lane_step(P, ls, A.solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
+            } else if (P.scheme == CQ_BE) {
+                x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, __shfl_xor_sync(0xffffffffu, h, 16));
+            } else {
+                const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
+                const float e = fmaf(__ldg(hd_hi + n - 1), gz, h);
+                x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e, __shfl_xor_sync(0xffffffffu, e, 16));
+            }
 #pragma unroll
-            for (int kk = 0; kk < b; ++kk) h = fmaf(w[b - kk], lv[kk], h);
-            const float x = lane_step(P, ls, A.solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
-            lv[b] = x;
-            xc[(j0 + b) * kMxT] = x;
+            for (int bb = b + 1; bb < kMxSB; ++bb) a[bb] = fmaf(wt[bb - b], x, a[bb]);
+            const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);
+            xc[((j0 + b) / 4) * 4 * kMxT + (j0 + b) % 4] = x;
             gm2 = gm1;
             gm1 = x;
+            gm2_o = gm1_o;
+            gm1_o = x_o;
         }
     }
     if (!active) return;
@@ -163,7 +224,7 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
         for (int j = 0; j < kMxB; j += 8) {
             uint32_t h[8], l[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) split_f32(xc[(j + i) * kMxT], h[i], l[i]);
+            for (int i = 0; i < 8; ++i) split_f32(xc[((j + i) / 4) * 4 * kMxT + (j + i) % 4], h[i], l[i]);
             dh[j / 8] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
             dl[j / 8] = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16), l[6] | (l[7] << 16));
         }
@@ -211,6 +272,7 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
     A.d2 = d2;
     A.hdf = hdf;
     A.carry = l.carry;
+    A.coef = l.coef;
     A.gt_hi = l.gt_hi;
     A.gt_lo = l.gt_lo;
     A.gN = gN;
