@@ -196,7 +196,50 @@ def precision_leg(fc, torch, dev, K, W, flush):
     out["f32_problem"], out["G0"] = q, G0
     del ws, g0, gN
     torch.cuda.empty_cache()
+    out["mixed"] = mixed_direct_leg(fc, torch, dev, p, G0, K, W, flush)
     return out
+
+
+MIXED_ALPHAS = ((0.2, 0.8), (0.8, 0.2), (0.2, 0.2), (0.8, 0.8))
+
+
+def mixed_direct_leg(fc, torch, dev, p, G0, K, W, flush):
+    """Mixed-precision direct solve (tensor-core BF16x3 history, FP32 in-block sums and
+    steps) of the 2D 511x511, N = 8192 grid for BE and BDF2 and every (alpha1, alpha2) in
+    {0.2, 0.8}^2. The first case (BE, alpha = (0.2, 0.8)) is timed K times; the others once."""
+    import cq_inputs as ci
+    runs = []
+    g0 = torch.tensor(G0, dtype=torch.float64, device=dev)
+    gN = torch.empty_like(g0)
+    ws = None
+    for scheme in (ci.BE, ci.BDF2):
+        for al in MIXED_ALPHAS:
+            q = p.replace(form=ci.DIRECT, scheme=scheme, alpha1=al[0], alpha2=al[1])
+            cp = fc.problem(q.alpha1, q.alpha2, q.m, q.T, q.N, q.dim, q.M, q.scheme, q.form, 0, 0, 0,
+                            prec=fc.CQ_BF16X3, flags=fc.FP2S_ASYNC)
+            if ws is None:
+                ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
+            main = not runs
+            for _ in range(W if main else 1):
+                fc.fp2s_solve(cp, g0, gN, ws)
+            torch.cuda.synchronize()
+            l0 = fc.cq_launch_count()
+            ms, tc_ms = [], []
+            for _ in range(K if main else 1):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fc.fp2s_solve(cp, g0, gN, ws)
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                tc_ms.append(fc.cq_timing_part(1))
+            runs.append({"problem": q, "ms": ms, "tc_ms": tc_ms, "status": fc.strerror(fc.fp2s_status(cp, ws)),
+                         "launches": (fc.cq_launch_count() - l0) / len(ms), "gN": gN.cpu().numpy()})
+    del ws, g0, gN
+    torch.cuda.empty_cache()
+    return runs
 
 
 def precision_report(leg, cpu_modes):
@@ -270,7 +313,65 @@ def precision_report(leg, cpu_modes):
                          "sample": "oracle FP64 fast BE scheme, %d modes x %d steps (%.1f s)"
                                    % (len(sample), q.N, t_f)},
     }
-    return {"tensor_core_direct_history": tc, "fp32_fast_solve": f32}
+    return {"tensor_core_direct_history": tc, "fp32_fast_solve": f32,
+            "mixed_direct_solve": mixed_report(leg["mixed"], G0, cpu_modes)}
+
+
+def mixed_report(runs, G0, cpu_modes):
+    """Errors of the mixed-precision direct solves against the FP64 oracle direct scheme
+    on sampled modes (the lowest four and a seeded sample), and the main case's rates."""
+    import numpy as np
+    import cq_inputs as ci
+    from oracle import scheme as OS
+    from oracle import spatial as OSP
+    q0 = runs[0]["problem"]
+    nm = q0.M ** q0.dim
+    sample = np.unique(np.concatenate([[0, 1, q0.M, q0.M + 1],
+                                       ci.sample_indices(nm, max(4, cpu_modes // 8), ci.SEED_BASE + 33)]))
+    lam = OSP.mode_eigenvalues(q0.M, q0.dim)[sample]
+    g0 = OSP.to_modal(G0, q0.M, q0.dim)[:, sample]
+    cases, t_orc = [], None
+    for r in runs:
+        q = r["problem"]
+        t = time.perf_counter()
+        ref = OS.solve_modal(q, lam, g0)[q.N]
+        if t_orc is None:
+            t_orc = time.perf_counter() - t
+        gm = OSP.to_modal(r["gN"], q.M, q.dim)[:, sample]
+        err = [float(np.linalg.norm(gm[s] - ref[s]) / np.linalg.norm(ref[s])) for s in range(2)]
+        cases.append({"scheme": "BE" if q.scheme == ci.BE else "BDF2", "alpha": [q.alpha1, q.alpha2],
+                      "ms": statistics.mean(r["ms"]), "status": r["status"],
+                      "rel_l2_err_vs_fp64_oracle": err})
+    main = runs[0]
+    q = main["problem"]
+    ms = statistics.mean(main["ms"])
+    tc_ms = statistics.mean(main["tc_ms"])
+    B = 128
+    nblk = (q.N + B - 1) // B
+    # contraction flops: per block b >= 1, 3 products x 2 x 128 rows x 128 b levels x 2 nm columns
+    tc_flops = 3 * 2.0 * B * B * 2 * nm * sum(range(1, nblk))
+    peaks = _measured_peaks()
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1712.8)
+    return {
+        "workload": "%s direct form, 2D %dx%d (%d DOF), N=%d, m=%g; BE and BDF2 x alpha in {0.2,0.8}^2"
+                    % (PREC_WORKLOAD, q.M, q.M, q.ndof, q.N, q.m),
+        "precision": "tensor-core BF16x3 history of earlier 128-step blocks (FP32 accumulation), FP32 in-block "
+                     "sums, two-term FP32 step with a double-float amplification matrix",
+        "value": q.ndof * q.N / (ms * 1e-3), "unit": UNIT, "ms_per_solve": ms,
+        "gpu_launches_per_solve": main["launches"],
+        "roofline": {"kernel": "k_history_tc_bf16x3<float> (63 launches per solve)", "bound": "tensor",
+                     "unit": "TFLOP/s", "achieved": tc_flops / (tc_ms * 1e-3) / 1e12, "peak": bf16_peak,
+                     "frac": tc_flops / (tc_ms * 1e-3) / 1e12 / bf16_peak, "contraction_ms": tc_ms,
+                     "share_of_solve": tc_ms / ms,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel inside a long solve)",
+                     "algorithmic_flops_per_solve": tc_flops},
+        "whole_solve_tensor_equivalent_tflops": 3 * 2.0 * 2 * nm * q.N * (q.N - 1) / 2 / (ms * 1e-3) / 1e12,
+        "error_sample": "%d modes (4 lowest + seeded), final step N" % len(sample),
+        "cases": cases,
+        "cpu_baseline": {"value": 2 * len(sample) * q.N / t_orc, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "oracle FP64 direct BE scheme, %d modes x %d steps (%.1f s)"
+                                   % (len(sample), q.N, t_orc)},
+    }
 
 
 GRAD_WORKLOAD = "grad_2d_m255"

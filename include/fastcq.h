@@ -72,6 +72,12 @@ int64_t cq_launch_count(void);
  * recent such call (it synchronises on the closing event). */
 int cq_timing_enable(int on);
 int cq_timing_last(double *ms_main_kernel);
+/* Parts of the most recent timed call: part 0 = the same as cq_timing_last;
+ * part 1 = summed duration of the tensor-core contraction launches of the
+ * mixed-precision direct solve (fp2s_solve, CQ_DIRECT with CQ_BF16X3 or
+ * CQ_TF32X3; 0 for other calls). Synchronises on the recorded events.
+ * CQ_EINVAL for another part, a NULL pointer or no timed call yet. */
+int cq_timing_part(int part, double *ms);
 
 /* ---- CQ weights (Sec. 3, Eqs. 3.4 and 3.12) ---------------------------- */
 /* w_dev[i] = d^beta_{s,i}, i = 0..n: the Taylor coefficients of delta(zeta)^beta

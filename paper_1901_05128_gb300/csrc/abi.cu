@@ -12,9 +12,29 @@ void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relax
 static bool g_timing = false, g_timed = false;
 static cudaEvent_t g_ev0 = nullptr, g_ev1 = nullptr;
 
+// Event pairs around the sub-launches of one part (the tensor-core contractions of
+// the mixed-precision direct solve) inside the timed region; reset by timing_begin.
+static cudaEvent_t g_part_ev[2 * kMaxTimedParts];
+static int g_part_created = 0, g_part_used = 0;
+
 int timing_begin(cudaStream_t s) {
     if (!g_timing) return CQ_OK;
+    g_part_used = 0;
     return cudaEventRecord(g_ev0, s) == cudaSuccess ? CQ_OK : CQ_ECUDA;
+}
+
+int timing_part(cudaStream_t s, bool end) {
+    if (!g_timing) return CQ_OK;
+    if (!end && g_part_used >= kMaxTimedParts) return CQ_OK;     // beyond the pool: not timed
+    const int k = 2 * (end ? g_part_used - 1 : g_part_used) + (end ? 1 : 0);
+    if (k < 0) return CQ_OK;
+    while (g_part_created <= k) {
+        if (cudaEventCreate(&g_part_ev[g_part_created]) != cudaSuccess) return CQ_ECUDA;
+        ++g_part_created;
+    }
+    if (cudaEventRecord(g_part_ev[k], s) != cudaSuccess) return CQ_ECUDA;
+    if (!end) ++g_part_used;
+    return CQ_OK;
 }
 
 int timing_end(cudaStream_t s) {
@@ -41,6 +61,21 @@ extern "C" int cq_timing_last(double *ms) {
     if (cudaEventSynchronize(g_ev1) != cudaSuccess) return CQ_ECUDA;
     if (cudaEventElapsedTime(&f, g_ev0, g_ev1) != cudaSuccess) return CQ_ECUDA;
     *ms = f;
+    return CQ_OK;
+}
+
+extern "C" int cq_timing_part(int part, double *ms) {
+    using namespace fastcq;
+    if (!ms || !g_timed || part < 0 || part > 1) return CQ_EINVAL;
+    if (part == 0) return cq_timing_last(ms);
+    double tot = 0.0;
+    for (int i = 0; i < g_part_used; ++i) {
+        float f = 0.0f;
+        if (cudaEventSynchronize(g_part_ev[2 * i + 1]) != cudaSuccess) return CQ_ECUDA;
+        if (cudaEventElapsedTime(&f, g_part_ev[2 * i], g_part_ev[2 * i + 1]) != cudaSuccess) return CQ_ECUDA;
+        tot += f;
+    }
+    *ms = tot;
     return CQ_OK;
 }
 

@@ -15,6 +15,10 @@ void count_launches(int64_t k);
 // Events around a call's main kernel when timing is enabled (cq_timing_enable).
 int timing_begin(cudaStream_t s);
 int timing_end(cudaStream_t s);
+// Events around one sub-launch of the timed region (end = false before it, true after);
+// cq_timing_part(1) sums them. At most kMaxTimedParts sub-launches per call are timed.
+constexpr int kMaxTimedParts = 512;
+int timing_part(cudaStream_t s, bool end);
 
 // Status bits written by kernels into a workspace status word.
 enum : int { ST_NONFINITE = 1, ST_SINGULAR = 2, ST_TIMEOUT = 4 };

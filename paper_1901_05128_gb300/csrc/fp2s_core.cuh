@@ -205,46 +205,47 @@ __device__ __forceinline__ float lane_step(const Fp2sParams &P, const LaneStep &
 // (BE n >= 1; SBD n >= 2): with A = M^{-1} / tau and B = -M^{-1} K,
 //     x^n = A l + B e,   l = g^{n-1} (BE) or 2 g^{n-1} - g^{n-2} / 2 (SBD),
 //                        e = h (BE) or h + d_{n-1} g^0 / 2 (SBD).
-// Only A, whose eigenvalues lie near 1 for slowly varying modes (so that a
-// rounded A would compound over the steps), is kept as double-float; B e is a
-// plain FP32 term: its rounding error stays relative to |B e|, the per-step
-// change of a slowly varying mode, or is damped by a small A for the others.
+// A and B are kept as double-float values and the four products are summed with
+// error-free transformations: for slowly varying modes x^n differs from the terms
+// by far less than their size, so FP32-rounded coefficients would act like a
+// perturbed operator whose effect compounds over the steps.
 struct LaneStep2 {
     float a_hi[2], a_lo[2];   // row s of A: [own state, other state]
-    float b[2];               // row s of B
+    float b_hi[2], b_lo[2];   // row s of B
 };
 
-__device__ __forceinline__ void lane_step2_setup(const Fp2sParams &P, const LaneStep &ls, int st, LaneStep2 &l2) {
-    // row st of M^{-1}: (m_oo, m_ot) in the lane's own/other ordering
+__device__ __forceinline__ void lane_step2_setup(const Fp2sParams &P, const LaneStep &ls, LaneStep2 &l2) {
+    // row st of M^{-1}: (m_oo, m_ot) in the lane's own/other ordering; K = [[c, -a], [-a, c]]
+    // is symmetric with equal diagonal, so row st of M^{-1} K is (m_oo c - m_ot a, -m_oo a + m_ot c)
     const double a_oo = ls.mn_oo * P.inv_tau, a_ot = ls.mn_ot * P.inv_tau;
-    // K = [[c, -a], [-a, c]] is symmetric with equal diagonal, so row st of M^{-1} K in
-    // own/other ordering is (m_oo c - m_ot a, -m_oo a + m_ot c)
     const double b_oo = -(ls.mn_oo * ls.c - ls.mn_ot * P.a), b_ot = -(-ls.mn_oo * P.a + ls.mn_ot * ls.c);
-    const df x = df_from(a_oo), y = df_from(a_ot);
+    const df x = df_from(a_oo), y = df_from(a_ot), u = df_from(b_oo), v = df_from(b_ot);
     l2.a_hi[0] = x.hi;
     l2.a_lo[0] = x.lo;
     l2.a_hi[1] = y.hi;
     l2.a_lo[1] = y.lo;
-    l2.b[0] = (float)b_oo;
-    l2.b[1] = (float)b_ot;
-    (void)st;
+    l2.b_hi[0] = u.hi;
+    l2.b_lo[0] = u.lo;
+    l2.b_hi[1] = v.hi;
+    l2.b_lo[1] = v.lo;
 }
 
-// x = A l + B e for the lane's state: (l, lo) and (l_o, lo_o) the double-float l of
-// the lane's and the other state, e and e_o the history terms.
+// x = A l + B e for the lane's state: (l, l_lo) and (l_o, l_o_lo) the double-float l
+// of the lane's and the other state, e and e_o the history terms (FP32).
 __device__ __forceinline__ float lane_step2(const LaneStep2 &c, float l, float l_lo, float l_o, float l_o_lo, float e,
                                             float e_o) {
     const float p1 = c.a_hi[0] * l;
-    float r1 = fmaf(c.a_hi[0], l, -p1);
-    r1 = fmaf(c.a_hi[0], l_lo, fmaf(c.a_lo[0], l, r1));
+    float r = fmaf(c.a_hi[0], l, -p1);
+    r = fmaf(c.a_hi[0], l_lo, fmaf(c.a_lo[0], l, r));
     const float p2 = c.a_hi[1] * l_o;
-    float r2 = fmaf(c.a_hi[1], l_o, -p2);
-    r2 = fmaf(c.a_hi[1], l_o_lo, fmaf(c.a_lo[1], l_o, r2));
-    const float s = p1 + p2;                       // TwoSum(p1, p2)
-    const float bb = s - p1;
-    const float err = (p1 - (s - bb)) + (p2 - bb);
-    const float r = fmaf(c.b[0], e, fmaf(c.b[1], e_o, (r1 + r2) + err));
-    return s + r;
+    r += fmaf(c.a_hi[1], l_o_lo, fmaf(c.a_lo[1], l_o, fmaf(c.a_hi[1], l_o, -p2)));
+    const float p3 = c.b_hi[0] * e;
+    r += fmaf(c.b_lo[0], e, fmaf(c.b_hi[0], e, -p3));
+    const float p4 = c.b_hi[1] * e_o;
+    r += fmaf(c.b_lo[1], e_o, fmaf(c.b_hi[1], e_o, -p4));
+    const df s12 = two_sum(p1, p2), s34 = two_sum(p3, p4);
+    const df s = two_sum(s12.hi, s34.hi);
+    return s.hi + (s.lo + ((s12.lo + s34.lo) + r));
 }
 
 constexpr int kFastModesPerWarp = 16;     // a warp carries 16 modes x 2 states

@@ -8,8 +8,9 @@
 // from the levels n0 .. n-1 of the block itself, is formed step by step in FP32
 // by the kernel that also takes the steps (Eq. 4.1 / Eq. 4.7 in the sine basis).
 // A step is evaluated from the FP32 history sums in the two-term form
-// x = A l + B e with a double-float A (lane_step2), or in FP64 when the coupling
-// is strong (|a| > 10); the first SBD step uses the double-float form (lane_step).
+// x = A l + B e with double-float A and B (lane_step2), or in FP64 when the
+// coupling is strong (|a| > 10); the first SBD step uses the double-float form
+// (lane_step).
 //
 // Every mode is pre-scaled by an exact power of two from its G^0, as in the FP32
 // fast form, so its values sit near 1 in the FP32 / BF16 range; the contraction
@@ -34,7 +35,7 @@ struct MixedLayout {
     __nv_bfloat16 *gt_hi, *gt_lo;       // levels, K-major: row s * nmp + mode, column k - 1
     float *acc;                         // contraction output [kMxB][2 * nmp]
     float *carry;                       // g^{n-1}, g^{n-2} at the end of a block: [2][2 * nmp]
-    float4 *coef;                       // per lane: (A row as double-float), (B row, scaled g^0, exponent)
+    float4 *coef;                       // per lane: A row, B row (double-float), (scaled g^0, exponent)
     int nblk, ntiles;
     int64_t nmp, kpad;
     size_t bytes;
@@ -58,7 +59,7 @@ static MixedLayout mixed_layout(const Fp2sParams &P, void *base) {
     l.gt_lo = cv.take<__nv_bfloat16>(lev);
     l.acc = cv.take<float>(l.nblk > 1 ? (size_t)kMxB * 2 * l.nmp : 0);
     l.carry = cv.take<float>((size_t)4 * l.nmp);
-    l.coef = cv.take<float4>((size_t)4 * l.nmp);
+    l.coef = cv.take<float4>((size_t)6 * l.nmp);
     l.bytes = cv.bytes();
     return l;
 }
@@ -126,21 +127,24 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
         gz = (float)ldexp(gz64, -ex);
         const bool ok = lane_step_setup(P, A.lam[mode], A.d1[0], A.d2[0], st, ls);
         if (A.n0 == 1 && active && st == 0 && !ok) atomicOr(A.status, ST_SINGULAR);
-        lane_step2_setup(P, ls, st, l2);
+        lane_step2_setup(P, ls, l2);
         if (A.n0 == 1 && active) {
             A.coef[col] = make_float4(l2.a_hi[0], l2.a_hi[1], l2.a_lo[0], l2.a_lo[1]);
-            A.coef[2 * A.nmp + col] = make_float4(l2.b[0], l2.b[1], gz, __int_as_float(ex));
+            A.coef[2 * A.nmp + col] = make_float4(l2.b_hi[0], l2.b_hi[1], l2.b_lo[0], l2.b_lo[1]);
+            A.coef[4 * A.nmp + col] = make_float4(gz, __int_as_float(ex), 0.0f, 0.0f);
         }
     } else {
-        const float4 c0 = A.coef[col], c1 = A.coef[2 * A.nmp + col];
+        const float4 c0 = A.coef[col], c1 = A.coef[2 * A.nmp + col], c2 = A.coef[4 * A.nmp + col];
         l2.a_hi[0] = c0.x;
         l2.a_hi[1] = c0.y;
         l2.a_lo[0] = c0.z;
         l2.a_lo[1] = c0.w;
-        l2.b[0] = c1.x;
-        l2.b[1] = c1.y;
-        gz = c1.z;
-        ex = __float_as_int(c1.w);
+        l2.b_hi[0] = c1.x;
+        l2.b_hi[1] = c1.y;
+        l2.b_lo[0] = c1.z;
+        l2.b_lo[1] = c1.w;
+        gz = c2.x;
+        ex = __float_as_int(c2.y);
     }
     const double *dn = st ? A.d2 : A.d1;
     const float *hd_hi = A.hdf + (size_t)(2 * st) * (P.N + 1), *hd_lo = hd_hi + (P.N + 1);
@@ -294,7 +298,9 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
             T.n_lo = n0;
             T.rows = min((int64_t)kMxB, P.N - n0 + 1);
             T.kprime = (int)(n0 - 1);
+            if ((st = timing_part(s, false))) return st;
             if ((st = tc_contract_f32(maps, T, l.acc, status, s))) return st;
+            if ((st = timing_part(s, true))) return st;
         }
         A.n0 = n0;
         A.acc = b > 0 ? l.acc : nullptr;

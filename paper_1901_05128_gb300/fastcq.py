@@ -59,6 +59,7 @@ def _load():
         "cq_launch_count": (I64, []),
         "cq_timing_enable": (C.c_int, [C.c_int]),
         "cq_timing_last": (C.c_int, [C.POINTER(C.c_double)]),
+        "cq_timing_part": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
         "cq_weights": (C.c_int, [I32, D, D, I64, P, P]),
         "cq_gauss_jacobi": (C.c_int, [I32, D, D, P, P, P]),
         "cq_fast_coeffs": (C.c_int, [I32, D, D, C.POINTER(FastCfg), P, P, SZ, P]),
@@ -84,7 +85,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_weights",
+EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_timing_part", "cq_weights",
            "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_history_fast",
            "cq_history_fast_noalloc", "fp2s_solve",
            "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient", "fp2s_batch_plan",
@@ -137,6 +138,12 @@ def cq_timing_enable(on: bool):
 def cq_timing_last() -> float:
     ms = C.c_double()
     _check(_lib.cq_timing_last(C.byref(ms)), "cq_timing_last")
+    return ms.value
+
+
+def cq_timing_part(part: int) -> float:
+    ms = C.c_double()
+    _check(_lib.cq_timing_part(int(part), C.byref(ms)), "cq_timing_part")
     return ms.value
 
 

@@ -77,6 +77,33 @@ def test_size_queries_need_no_device(fc):
     assert n_f >= (80 + 17) * 1000 * 8
 
 
+def test_mixed_direct_size_query(fc):
+    """The mixed-precision direct solve sizes its BF16 hi/lo level matrix (K-major, levels
+    of all blocks but the last), the FP32 block accumulator and the Toeplitz banks; it
+    needs no FP64 history. The fast form and the step API reject the BF16x3 precision."""
+    M, N = 511, 8192
+    nm = M * M
+    nmp = (nm + 3) // 4 * 4
+    pm = fc.problem(0.2, 0.8, 0.45, 1.0, N, 2, M, fc.CQ_BE, fc.CQ_DIRECT, prec=fc.CQ_BF16X3)
+    n_mx = fc.fp2s_solve(pm, None, None, None)
+    levels = 2 * (2 * nmp) * (N - 128) * 2
+    assert levels + 128 * 2 * nmp * 4 <= n_mx <= levels + 128 * 2 * nmp * 4 + (64 << 20)
+    pd = fc.problem(0.2, 0.8, 0.45, 1.0, N, 2, M, fc.CQ_BE, fc.CQ_DIRECT)
+    assert fc.fp2s_solve(pd, None, None, None) > 1.9 * n_mx    # FP64 keeps (N + 1) x 2 x nm doubles
+    one = fc.problem(0.2, 0.8, 0.45, 1.0, 128, 1, 15, fc.CQ_BE, fc.CQ_DIRECT, prec=fc.CQ_BF16X3)
+    assert 0 < fc.fp2s_solve(one, None, None, None) < 1 << 20  # a single block: no levels, no accumulator
+    pf = fc.problem(0.2, 0.8, 0.45, 1.0, N, 2, M, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2, prec=fc.CQ_BF16X3)
+    sz = C.c_size_t(0)
+    assert fc._lib.fp2s_solve(C.byref(pf), None, None, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
+    assert fc._lib.fp2s_init(C.byref(pm), None, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
+
+
+def test_timing_part_needs_a_timed_call(fc):
+    ms = C.c_double(0.0)
+    assert fc._lib.cq_timing_part(3, C.byref(ms)) == fc.CQ_EINVAL
+    assert fc._lib.cq_timing_part(1, None) == fc.CQ_EINVAL
+
+
 def test_workspace_too_small(fc):
     import torch
     p = fc.problem(0.4, 0.6, 0.3, 1.0, 64, 1, 15)

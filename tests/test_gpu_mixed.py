@@ -111,3 +111,21 @@ def test_mixed_form_rejected_for_fast_and_stepper(fc):
     with pytest.raises(fc.CQError) as e:
         fc.fp2s_init(cd, g0, None)
     assert e.value.status == fc.CQ_EUNSUPPORTED
+
+
+def test_timing_parts_of_the_mixed_solve(fc):
+    """cq_timing_part(1) sums the contraction launches inside the timed region."""
+    p = ci.Problem(0.2, 0.8, 0.45, 1.0, 900, 2, 31, ci.BE, ci.DIRECT, 0, 0, 0)
+    G0 = ci.g0_uniform(p.M, p.dim, 3)
+    fc.cq_timing_enable(True)
+    try:
+        _solve(fc, p, G0, fc.CQ_BF16X3)
+        whole, part = fc.cq_timing_part(0), fc.cq_timing_part(1)
+        assert whole == fc.cq_timing_last()
+        assert 0.0 < part < whole
+        _solve(fc, p, G0, fc.CQ_F64)
+        assert fc.cq_timing_part(1) == 0.0
+        with pytest.raises(fc.CQError):
+            fc.cq_timing_part(2)
+    finally:
+        fc.cq_timing_enable(False)
