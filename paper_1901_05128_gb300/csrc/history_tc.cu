@@ -17,11 +17,16 @@
 // split and transposed once into K-major BF16 arrays.
 //
 // Kernel: one CTA per 128 x 256 output tile; warp 0 issues TMA loads into a
-// two-stage shared-memory ring, warp 1 issues tcgen05.mma (one thread) into a
-// 128 x 256 FP32 accumulator in tensor memory, warps 2-5 read the accumulator
-// back with tcgen05.ld and store FP64 results. Every mbarrier wait is bounded
-// by a global-timer deadline; on expiry the kernel records ST_TIMEOUT, writes
-// NaN to its tile, drains what it started and frees its tensor memory.
+// two-stage shared-memory ring, warp 1 issues tcgen05.mma (one thread) into two
+// 128 x 256 FP32 accumulators in tensor memory, one chunk of 128 levels at a
+// time, alternating; warps 2-9 read each finished chunk back with tcgen05.ld and
+// add it to FP32 running sums (round to nearest) while the next chunk is being
+// formed, then store FP64 (or FP32) results. The tensor cores' own accumulation
+// rounds toward zero, which on a history whose terms share a sign is a bias
+// that grows with K; chunking keeps it to one chunk's worth. Every mbarrier wait
+// is bounded by a global-timer deadline; on expiry the kernel records
+// ST_TIMEOUT, writes NaN to its tile, drains what it started and frees its
+// tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -36,8 +41,10 @@ constexpr int STAGES = 2;
 constexpr int A_BYTES = BM * BK * 2;        // 16 KiB
 constexpr int B_BYTES = BN * BK * 2;        // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int THREADS = 192;
-constexpr int TMEM_COLS = 256;
+constexpr int EPI_WARPS = 8;                // two warps per TMEM lane quarter, one per column half
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int TMEM_COLS = 512;              // two 128 x 256 FP32 accumulators
+constexpr int CHUNK = 2;                    // K stages (128 levels) accumulated per tensor-memory pass
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
 
@@ -53,6 +60,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -187,8 +198,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *accum = empty + STAGES;
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(accum + 1);
+    uint64_t *tfull = empty + STAGES;            // accumulator buffer b holds a finished chunk
+    uint64_t *tempty = tfull + 2;                // accumulator buffer b has been read back
+    uint64_t *drain = tempty + 2;                // every MMA this CTA issued has completed
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
     int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);   // [0]: abort, [1]: always 0
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -206,13 +219,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
     // levels k' < m_last - 1 contribute (k = k' + 1 <= m_last - 1)
     const int64_t k_end = min((int64_t)P.kprime, m_last - 1);
     const int num_k = k_end > 0 ? (int)((k_end + BK - 1) / BK) : 0;
+    const int nchunks = (num_k + CHUNK - 1) / CHUNK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accum, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&tfull[q], 1);
+            mbar_init(&tempty[q], 32 * EPI_WARPS);
+        }
+        mbar_init(drain, 1);
         abort_flag[0] = (*(const volatile int *)status & ST_TIMEOUT) ? 1 : 0;   // an earlier CTA gave up
         abort_flag[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -258,10 +276,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
                 if (armed[i] >= 0) (void)mbar_wait(&full[i], (uint32_t)(armed[i] / STAGES) & 1u, WAIT_NS, abort_flag + 1);
         }
     } else if (warp == 1 && lane == 0 && num_k > 0 && !aborted) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer: chunk c of CHUNK stages goes to accumulator buffer c & 1,
+        // starting from zero, once the epilogue has read back that buffer's previous chunk
         for (int ks = 0; ks < num_k; ++ks) {
             const int s = ks % STAGES;
             const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+            const int c = ks / CHUNK, buf = c & 1;
+            if (ks % CHUNK == 0) {
+                if (!mbar_wait(&tempty[buf], ((uint32_t)(c >> 1) & 1u) ^ 1u, WAIT_NS, status) ||
+                    *(volatile int *)abort_flag) {
+                    atomicOr(status, ST_TIMEOUT);
+                    *(volatile int *)abort_flag = 1;
+                    break;
+                }
+            }
             if (!mbar_wait(&full[s], ph, WAIT_NS, status) || *(volatile int *)abort_flag) {
                 atomicOr(status, ST_TIMEOUT);
                 *(volatile int *)abort_flag = 1;
@@ -270,49 +298,67 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
             const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+            const uint32_t acc = tmem + (uint32_t)(buf * BN);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint32_t off = kk * 32;            // 16 BF16 = 32 bytes along K inside the swizzle row
-                const uint32_t acc0 = (ks > 0 || kk > 0) ? 1u : 0u;
-                umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
-                umma_bf16(tmem, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
-                umma_bf16(tmem, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+                const uint32_t acc0 = (ks % CHUNK > 0 || kk > 0) ? 1u : 0u;
+                umma_bf16(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
+                umma_bf16(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+                umma_bf16(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
             }
             umma_commit(&empty[s]);                       // stage reusable once these MMAs are done
+            if (ks % CHUNK == CHUNK - 1 || ks == num_k - 1) umma_commit(&tfull[buf]);
         }
-        umma_commit(accum);                               // all issued MMAs complete -> accumulator ready
+        umma_commit(drain);                               // everything issued above has completed
     } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> registers -> FP64 global
+        // ---------------- epilogue: each chunk is read back from tensor memory and added to
+        // FP32 running sums with round-to-nearest (the tensor-core accumulation within a chunk
+        // rounds toward zero; summing chunks here keeps that bias to one chunk's worth)
         const int q = warp & 3;                           // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;                 // columns [128 half, 128 half + 128)
         const int row = q * 32 + lane;
         const int64_t m = m0 + row;
         const bool row_ok = m < P.n_lo + P.rows;
         bool have = !aborted;
-        if (num_k > 0 && !aborted) {
-            have = mbar_wait(accum, 0, WAIT_NS, status);
-            if (!have) atomicOr(status, ST_TIMEOUT);
-            tc_fence_after();
+        float accr[BN / 2];
+#pragma unroll
+        for (int i = 0; i < BN / 2; ++i) accr[i] = 0.0f;
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c & 1;
+            if (have) {
+                have = mbar_wait(&tfull[buf], (uint32_t)(c >> 1) & 1u, WAIT_NS, status);
+                if (!have) {
+                    atomicOr(status, ST_TIMEOUT);
+                    *(volatile int *)abort_flag = 1;
+                }
+            }
+            if (have) {
+                tc_fence_after();
+                const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + half * (BN / 2));
+#pragma unroll
+                for (int j = 0; j < BN / 2; j += 16) {
+                    float v[16];
+                    tmem_ld16(base + (uint32_t)j, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) accr[j + i] += v[i];
+                }
+                tc_fence_before();
+            }
+            mbar_arrive(&tempty[buf]);
         }
         OutT *hrow = H + (m - P.n_lo) * P.ldh + (int64_t)state * P.state_stride;
-        for (int c = 0; c < BN; c += 16) {
-            float v[16];
-            if (num_k > 0 && !aborted) {
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-            } else {
+        if (row_ok) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.0f;
-            }
-            if (row_ok) store16(hrow, n0 + c, P.ndof, P.vec2, have, v);
+            for (int j = 0; j < BN / 2; j += 16) store16(hrow, n0 + half * (BN / 2) + j, P.ndof, P.vec2, have, accr + j);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        if (num_k > 0 && *(volatile int *)abort_flag) {
-            // make sure nothing still writes the accumulator before it is freed
-            if (lane == 0) (void)mbar_wait(accum, 0, WAIT_NS, abort_flag + 1);
-        }
+        // nothing may still write tensor memory when it is freed
+        if (num_k > 0 && !aborted && lane == 0) (void)mbar_wait(drain, 0, WAIT_NS, abort_flag + 1);
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }

@@ -2,17 +2,15 @@
 oracle (``-m gpu``).
 
 The history of Eq. 3.8 is split per time block of 128 steps: the part from earlier
-blocks is a tensor-core contraction of BF16 hi + lo operands with FP32 accumulation,
-the in-block part an FP32 sum, and the step (Eq. 4.1 / Eq. 4.7) is evaluated in
-double-float arithmetic (FP64 when |a| > 10). Every history term then carries a relative
-error of at most about 3 * 2^-16 (split operands, lo * lo dropped) plus the FP32
-accumulation, so |h_err| <= (3 * 2^-16 + K 2^-24) sum_i |d_i| |g^{n-i}|. A history
-error enters the step like a perturbed right-hand side; the step is contractive for the
-stable problems here, and the per-step errors, mostly random in sign, add up over the
-N steps. The bound used, relative L2 error <= 5e-4 per state at the final step, follows
-from N * 3 * 2^-16 * sum|d||g| / |d_0 g| with sum_i |d_i| <= 2 d_0 (BE weights; BDF2 alike)
-for N of a few hundred in the worst (fully correlated) case; measured errors are far
-smaller and are printed.
+blocks is a tensor-core contraction of BF16 hi + lo operands (relative error <= 3 * 2^-16
+per term) accumulated in FP32 per 128-level chunk and summed across chunks with
+round-to-nearest; the in-block part is an FP32 sum; the step (Eq. 4.1 / Eq. 4.7) is
+x = A l + B e with double-float A and B (FP64 when |a| > 10). The history h is close to
+-d_0 x for a slowly varying mode, so an FP32 rounding of h weighs about d_0 = tau^-beta
+times more in the step than in h itself; these roundings are random in sign and add up
+over the N steps like a random walk: ~2^-24 * tau^-beta * sqrt(N) relative, 2e-6 at
+tau = 1/1000, beta = 0.8. The tolerance, relative L2 error <= 1e-4 per state at the final
+step, leaves a factor ~10 over the values measured on these cases (<= 9e-6, printed).
 """
 import numpy as np
 import pytest
@@ -71,7 +69,7 @@ def test_direct_mixed_against_fp64_oracle(fc, name, p, sc):
     ref = OS.solve(p, G0)
     errs = _rel(got, ref)
     print("mixed direct %s rel L2 errors %.3e %.3e" % (name, errs[0], errs[1]))
-    assert max(errs) <= 5e-4
+    assert max(errs) <= 1e-4
 
 
 def test_direct_mixed_every_step_count(fc):
@@ -85,7 +83,7 @@ def test_direct_mixed_every_step_count(fc):
         assert st == fc.CQ_OK, N
         errs = _rel(got, OS.solve(p, G0))
         worst = max(worst, max(errs))
-        assert max(errs) <= 5e-4, N
+        assert max(errs) <= 1e-4, N
     print("mixed direct, N in 1..40 and block edges: worst rel L2 error %.3e" % worst)
 
 
@@ -98,7 +96,7 @@ def test_direct_mixed_matches_fp64_gpu_solve(fc):
     assert st64 == fc.CQ_OK and stmx == fc.CQ_OK
     errs = _rel(gmx, g64)
     print("mixed vs FP64 GPU direct: %.3e %.3e" % tuple(errs))
-    assert max(errs) <= 5e-4
+    assert max(errs) <= 1e-4
 
 
 def test_mixed_form_rejected_for_fast_and_stepper(fc):
