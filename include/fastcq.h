@@ -207,6 +207,15 @@ int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, dou
  * [N+1][2][M^dim] arrays. Synchronises `stream`. */
 int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, double *J_host,
                   double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes, void *stream);
+/* Vector-Jacobian product of the direct solve G^N = fp2s_solve(G^0; alpha1, alpha2):
+ * the backward pass for an arbitrary upstream gradient dL/dG^N (physical
+ * [2][M^dim], device). Same adjoint sweep as fp2s_gradient with the terminal
+ * condition dL/dx^N = S dL/dG^N (S the orthonormal DST-I) instead of the misfit's.
+ * Outputs: dG0_dev [2][M^dim] = dL/dG^0 (device); dalpha_host[2] = dL/dalpha_i.
+ * Same restrictions, workspace size and errors as fp2s_gradient; synchronises
+ * `stream`. */
+int fp2s_vjp(const fp2s_problem_t *p, const double *G0_dev, const double *dGN_dev, double *dG0_dev,
+             double *dalpha_host, void *ws_dev, size_t *ws_bytes, void *stream);
 /* ---- batches: many independent problems in one persistent launch ------- */
 /* Plan of a batch (host memory, filled by fp2s_batch_plan; treat as opaque
  * apart from the documented fields). */

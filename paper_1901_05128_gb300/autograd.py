@@ -1,0 +1,51 @@
+"""torch.autograd binding of the direct two-state solve.
+
+``solve(G0, alpha, ...)`` returns G^N of the direct BE (Eq. 4.1) or SBD (Eq. 4.7)
+scheme on the GPU (``fp2s_solve``). Its backward pass is the discrete adjoint of the
+same scheme (``fp2s_vjp``): the transposed 2x2 steps run backwards in time with the CQ
+convolution reversed in time, plus the beta-derivatives of the weights for the
+gradient with respect to alpha_1, alpha_2 (d/dalpha_i = -d/dbeta_i, beta_i = 1 - alpha_i).
+The backward pass recomputes the forward history inside the library call, so nothing
+but G^0 and alpha is kept between forward and backward.
+
+Both passes run in FP64 on the device; arguments are marshalled only.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import fastcq as fc
+
+
+class _Solve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, G0, alpha, m, T, N, dim, M, scheme):
+        a1, a2 = (float(v) for v in alpha.detach().cpu().tolist())
+        p = fc.problem(a1, a2, m, T, N, dim, M, scheme, fc.CQ_DIRECT)
+        G0c = G0.detach().contiguous()
+        GN = torch.empty_like(G0c)
+        ws = fc.workspace(fc.fp2s_solve(p, G0c, GN, None), G0c.device)
+        fc.fp2s_solve(p, G0c, GN, ws)                   # on torch's current stream
+        ctx.save_for_backward(G0c, alpha)
+        ctx.p = p
+        return GN
+
+    @staticmethod
+    def backward(ctx, dGN):
+        G0, alpha = ctx.saved_tensors
+        dG0 = torch.empty_like(G0)
+        ws = fc.workspace(fc.fp2s_vjp(ctx.p, G0, dGN, dG0, None), G0.device)
+        da = fc.fp2s_vjp(ctx.p, G0, dGN.contiguous(), dG0, ws)
+        dalpha = torch.tensor(da, dtype=alpha.dtype, device=alpha.device)
+        return dG0, dalpha, None, None, None, None, None, None
+
+
+def solve(G0: torch.Tensor, alpha: torch.Tensor, *, m: float, T: float, N: int, dim: int, M: int,
+          scheme: int = fc.CQ_BDF2) -> torch.Tensor:
+    """G^N of the direct scheme for G0 (float64 CUDA tensor [2, M**dim]) and
+    alpha = (alpha_1, alpha_2) (float64 tensor [2]); differentiable in both."""
+    if G0.dtype != torch.float64 or not G0.is_cuda or tuple(G0.shape) != (2, M ** dim):
+        raise ValueError("G0 must be a float64 CUDA tensor of shape (2, M**dim)")
+    if alpha.numel() != 2:
+        raise ValueError("alpha must hold (alpha_1, alpha_2)")
+    return _Solve.apply(G0, alpha, m, T, N, dim, M, scheme)

@@ -852,7 +852,7 @@ __global__ void __launch_bounds__(32, 12) k_adjoint_direct(
     Fp2sParams P, double wd, const double *__restrict__ lam, const double *__restrict__ d1,
     const double *__restrict__ d2, const double *__restrict__ dz1, const double *__restrict__ dz2,
     const double *__restrict__ q1, const double *__restrict__ q2, const double *__restrict__ qz1,
-    const double *__restrict__ qz2, const double *__restrict__ hist, const double *__restrict__ tgt,
+    const double *__restrict__ qz2, const double *__restrict__ hist, const double *__restrict__ tgt, int vjp,
     double *__restrict__ mu, double *__restrict__ gx0, double *__restrict__ acc) {
     const int64_t nm = P.nmodes;
     const int64_t mode_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -872,9 +872,10 @@ __global__ void __launch_bounds__(32, 12) k_adjoint_direct(
                           it + (2.0 / 3.0) * d20 * c, M1);
     }
     const double xN1 = hist[(N * 2) * nm + mode], xN2 = hist[(N * 2 + 1) * nm + mode];
+    // terminal condition dJ/dx^N: the misfit's wd (x^N - t), or (vjp) the given modal gradient
     const double e1 = xN1 - tgt[mode], e2 = xN2 - tgt[nm + mode];
-    const double r1 = wd * e1, r2 = wd * e2;
-    double Jpart = active ? 0.5 * wd * (e1 * e1 + e2 * e2) : 0.0;
+    const double r1 = vjp ? tgt[mode] : wd * e1, r2 = vjp ? tgt[nm + mode] : wd * e2;
+    double Jpart = (active && !vjp) ? 0.5 * wd * (e1 * e1 + e2 * e2) : 0.0;
     double lp1_1 = 0.0, lp1_2 = 0.0, lp2_1 = 0.0, lp2_2 = 0.0;      // lambda^{m+1}, lambda^{m+2}
     double db1 = 0.0, db2 = 0.0, sg1 = 0.0, sg2 = 0.0, sx1 = 0.0, sx2 = 0.0;
     double lam1_1 = 0.0, lam1_2 = 0.0, lam2_1 = 0.0, lam2_2 = 0.0, mu1_1 = 0.0, mu1_2 = 0.0;
@@ -1035,9 +1036,11 @@ static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void 
     return g;
 }
 
-extern "C" int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, double *J_host,
-                             double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes,
-                             void *stream) {
+// Forward direct solve (history kept), then the adjoint sweep. vjp = 0: terminal condition
+// from the misfit against Gt; vjp = 1: Gt holds dL/dG^N and J is not formed.
+static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, int vjp,
+                         double *J_host, double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes,
+                         void *stream) {
     Fp2sParams P;
     int np1 = 0, np2 = 0;
     int st = derive(p, P, np1, np2);
@@ -1049,7 +1052,7 @@ extern "C" int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, cons
     GradLayout gl = grad_layout(P, l, ws_dev);
     if (!ws_dev) { *ws_bytes = gl.bytes; return CQ_OK; }
     if (*ws_bytes < gl.bytes) return CQ_ENOMEM;
-    if (!G0_dev || !Gt_dev || !J_host || !dJdG0_dev || !dJdalpha_host || ((uintptr_t)ws_dev & 255))
+    if (!G0_dev || !Gt_dev || (!vjp && !J_host) || !dJdG0_dev || !dJdalpha_host || ((uintptr_t)ws_dev & 255))
         return CQ_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
@@ -1079,18 +1082,29 @@ extern "C" int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, cons
     const double h = 1.0 / (p->M + 1);
     const double wd = (p->dim == 1) ? h : h * h;
     k_adjoint_direct<kAdjBT><<<fblocks, 32, 0, s>>>(P, wd, l.lam, l.d1, l.d2, dzA1, dzA2, gl.q1, gl.q2, gl.qz1,
-                                                    gl.qz2, l.hist, gl.tgt, gl.mu, gl.gx0, gl.acc);
+                                                    gl.qz2, l.hist, gl.tgt, vjp, gl.mu, gl.gx0, gl.acc);
     if ((st = launched())) return st;
     if ((st = timing_end(s))) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, gl.gx0, dJdG0_dev, l.tmp, s))) return st;
     double host[4];
     if (cudaMemcpyAsync(host, gl.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CQ_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CQ_ECUDA;
-    *J_host = host[0];
+    if (J_host) *J_host = host[0];
     dJdalpha_host[0] = -host[1];
     dJdalpha_host[1] = -host[2];
     if (host[3] != 0.0) return CQ_ESINGULAR;
     if ((st = read_status(l.status, s))) return st;
     if (!isfinite(host[0]) || !isfinite(host[1]) || !isfinite(host[2])) return CQ_ENONFINITE;
     return CQ_OK;
+}
+
+extern "C" int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, double *J_host,
+                             double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes,
+                             void *stream) {
+    return gradient_impl(p, G0_dev, Gt_dev, 0, J_host, dJdG0_dev, dJdalpha_host, ws_dev, ws_bytes, stream);
+}
+
+extern "C" int fp2s_vjp(const fp2s_problem_t *p, const double *G0_dev, const double *dGN_dev, double *dG0_dev,
+                        double *dalpha_host, void *ws_dev, size_t *ws_bytes, void *stream) {
+    return gradient_impl(p, G0_dev, dGN_dev, 1, nullptr, dG0_dev, dalpha_host, ws_dev, ws_bytes, stream);
 }

@@ -73,6 +73,7 @@ def _load():
         "fp2s_status": (C.c_int, [C.POINTER(Problem), P, C.c_size_t, P]),
         "fp2s_gradient": (C.c_int, [C.POINTER(Problem), P, P, C.POINTER(C.c_double), P, C.POINTER(C.c_double), P,
                                     SZ, P]),
+        "fp2s_vjp": (C.c_int, [C.POINTER(Problem), P, P, P, C.POINTER(C.c_double), P, SZ, P]),
         "fp2s_batch_plan": (C.c_int, [C.POINTER(Problem), I32, I32, C.POINTER(BatchPlan), P, SZ, P]),
         "fp2s_solve_batched": (C.c_int, [C.POINTER(BatchPlan), P, P, P, P]),
         "fp2s_batch_status": (C.c_int, [C.POINTER(BatchPlan), P, P]),
@@ -88,7 +89,7 @@ _lib = _load()
 EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_timing_part", "cq_weights",
            "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_history_fast",
            "cq_history_fast_noalloc", "fp2s_solve",
-           "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient", "fp2s_batch_plan",
+           "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient", "fp2s_vjp", "fp2s_batch_plan",
            "fp2s_solve_batched", "fp2s_batch_status")
 
 
@@ -228,6 +229,18 @@ def fp2s_gradient(p: Problem, G0_dev, Gt_dev, dJdG0_dev, ws_dev=None, stream=Non
     if ws_dev is None:
         return sz.value
     return J.value, (da[0], da[1])
+
+
+def fp2s_vjp(p: Problem, G0_dev, dGN_dev, dG0_dev, ws_dev=None, stream=None):
+    """Returns the workspace size when ws_dev is None, else (dL/dalpha1, dL/dalpha2);
+    dL/dG0 for the upstream gradient dGN_dev is written to dG0_dev."""
+    sz = C.c_size_t(0 if ws_dev is None else _nbytes(ws_dev))
+    da = (C.c_double * 2)()
+    _check(_lib.fp2s_vjp(C.byref(p), _ptr(G0_dev), _ptr(dGN_dev), _ptr(dG0_dev), da, _ptr(ws_dev), C.byref(sz),
+                         _stream(stream, ws_dev is None)), "fp2s_vjp")
+    if ws_dev is None:
+        return sz.value
+    return da[0], da[1]
 
 
 def fp2s_batch_plan(problems, ws_dev=None, tune=False, stream=None):

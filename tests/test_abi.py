@@ -98,6 +98,19 @@ def test_mixed_direct_size_query(fc):
     assert fc._lib.fp2s_init(C.byref(pm), None, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
 
 
+def test_vjp_host_checks(fc):
+    p = fc.problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, fc.CQ_BE, fc.CQ_DIRECT)
+    n_g = fc.fp2s_gradient(p, None, None, None, None)
+    assert fc.fp2s_vjp(p, None, None, None, None) == n_g
+    sz = C.c_size_t(0)
+    da = (C.c_double * 2)()
+    pf = fc.problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2)
+    assert fc._lib.fp2s_vjp(C.byref(pf), None, None, None, da, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
+    assert fc._lib.fp2s_vjp(C.byref(p), None, None, None, da, None, None, None) == fc.CQ_EINVAL
+    sz = C.c_size_t(n_g)
+    assert fc._lib.fp2s_vjp(C.byref(p), None, None, None, da, 1 << 20, C.byref(sz), None) == fc.CQ_EINVAL
+
+
 def test_timing_part_needs_a_timed_call(fc):
     ms = C.c_double(0.0)
     assert fc._lib.cq_timing_part(3, C.byref(ms)) == fc.CQ_EINVAL
