@@ -41,7 +41,8 @@ def grid_1d(M: int) -> np.ndarray:
 
 
 def grid(M: int, dim: int):
-    """Coordinates of the interior points, flattened with dof = iy*M + ix."""
+    """Coordinates of the interior points, flattened with dof = iy*M + ix (2D) or
+    (iz*M + iy)*M + ix (3D)."""
     x = grid_1d(M)
     if dim == 1:
         return (x,)
@@ -49,7 +50,12 @@ def grid(M: int, dim: int):
         X = np.tile(x, M)          # ix fastest
         Y = np.repeat(x, M)
         return (X, Y)
-    raise ValueError("dim must be 1 or 2")
+    if dim == 3:
+        X = np.tile(x, M * M)
+        Y = np.tile(np.repeat(x, M), M)
+        Z = np.repeat(x, M * M)
+        return (X, Y, Z)
+    raise ValueError("dim must be 1, 2 or 3")
 
 
 def g0_indicator(M: int, dim: int, lo: float = 0.25, hi: float = 0.75) -> np.ndarray:

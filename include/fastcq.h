@@ -158,9 +158,10 @@ int cq_history_fast_noalloc(int32_t scheme, double beta, double tau, const cq_fa
                             int32_t prec, void *stream);
 
 /* ---- two-state fractional Fokker-Planck system (Eqs. 1.1-1.3, 2.1) ----- */
-/* Problem on (0,1)^dim, dim in {1,2}, with M interior points per axis of the
- * centred finite-difference Laplacian (h = 1/(M+1)); DOFs of one state are
- * ordered dof = iy*M + ix and a two-state field is [2][M^dim] doubles.
+/* Problem on (0,1)^dim, dim in {1,2,3}, with M interior points per axis of the
+ * centred finite-difference Laplacian (h = 1/(M+1); M <= 65536, 4096, 1024 for
+ * dim 1, 2, 3); DOFs of one state are ordered dof = ix (1D), iy*M + ix (2D),
+ * (iz*M + iy)*M + ix (3D), and a two-state field is [2][M^dim] doubles.
  * 0 < alpha1, alpha2 < 1; 0 <= m < 1, m != 1/2; T > 0; N >= 1.
  * flags bit 0 (FP2S_ASYNC): fp2s_solve does not synchronise and does not
  * report device status (CQ_ENONFINITE); use fp2s_status() later. */
@@ -172,15 +173,22 @@ typedef struct {
     int32_t scheme;        /* CQ_BE or CQ_BDF2 */
     int32_t form;          /* CQ_DIRECT or CQ_FAST */
     cq_fast_cfg_t fast;    /* used when form == CQ_FAST */
-    int32_t prec;          /* CQ_F64; CQ_F32 with form == CQ_FAST in fp2s_solve (np1 + np2 <= 128) */
+    int32_t prec;          /* CQ_F64; in fp2s_solve also CQ_F32 with form == CQ_FAST (np1 + np2 <= 128)
+                              and CQ_BF16X3 with form == CQ_DIRECT (mixed-precision direct solve) */
     int32_t flags;
 } fp2s_problem_t;
 
 /* Whole solve, fused: G0_dev (physical [2][M^dim]) -> GN_dev (physical
  * [2][M^dim], the level t_N of the BE scheme Eq. 4.1 / fast BE Eq. 4.3 /
  * SBD Eq. 4.7 / fast SBD Eq. 4.8). Every sine mode is advanced through all N
- * steps by one persistent kernel. Synchronises `stream` at the end to read
- * the device status unless flags & FP2S_ASYNC. */
+ * steps by one persistent kernel (FP64, CQ_F32). The mixed-precision direct
+ * solve (CQ_DIRECT with CQ_BF16X3) runs in blocks of 128 steps: the history
+ * from earlier blocks is a tcgen05 BF16x3 contraction (FP32 accumulation per
+ * 128-level chunk, chunks summed with round-to-nearest), the in-block part and
+ * the steps run in FP32 / double-float (FP64 when |a| > 10); its workspace
+ * holds the levels as BF16 hi + lo (about 4 bytes per DOF-step).
+ * Synchronises `stream` at the end to read the device status unless
+ * flags & FP2S_ASYNC. */
 int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double *GN_dev,
                void *ws_dev, size_t *ws_bytes, void *stream);
 
@@ -229,7 +237,7 @@ typedef struct {
 } fp2s_batch_t;
 
 /* Plans and prepares a batch of n problems (each with form == CQ_FAST,
- * prec == CQ_F64; any mix of dim, M, N, scheme, alpha, m and fast sizes):
+ * prec == CQ_F64, dim 1 or 2; any mix of dim, M, N, scheme, alpha, m and fast sizes):
  * builds every instance's tables in the workspace with batched kernels and
  * orders the work units by decreasing cost. tune != 0 times the candidate
  * block widths on a shortened run (96 steps) and keeps the fastest.

@@ -67,14 +67,15 @@ int launch_fast_coeffs(int scheme, double beta, double tau, int np1, int np2, in
 size_t fast_coeff_scratch_bytes(int np1, int np2);
 int build_fast_coeffs(int scheme, double beta, double tau, int np1, int np2, int ns,
                       double *scratch, double *r_out, double *c_out, cudaStream_t s);
-// Sine-mode eigenvalues of the FD Laplacian (dim 1 or 2), M^dim values.
+// Sine-mode eigenvalues of the FD Laplacian (dim 1, 2 or 3), M^dim values.
 int launch_mode_eigenvalues(int M, int dim, double *lam, cudaStream_t s);
 // Orthonormal DST-I matrix S (M x M, row-major).
 int launch_dst_matrix(int M, double *S, cudaStream_t s);
 // C[batch] = A[batch] * B[batch] for M x M row-major matrices (FP64), batch strides in elements.
 int launch_dgemm_square(int M, int batch, const double *A, int64_t sA, const double *B, int64_t sB,
                         double *C, int64_t sC, cudaStream_t s);
-// Sine transform of a two-state field: out[s] = S in[s] (1D) or S in[s] S (2D); tmp: 2*M^dim doubles (2D).
+// Sine transform of a two-state field along every axis (1D: out[s] = S in[s]; 2D: S in[s] S;
+// 3D: along x, y, z); tmp: 2*M^dim doubles (2D, 3D); in and out must differ.
 int launch_dst_field(int M, int dim, const double *S, const double *in, double *out, double *tmp,
                      cudaStream_t s);
 

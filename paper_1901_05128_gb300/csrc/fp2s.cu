@@ -74,8 +74,8 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     if (!(p->alpha1 > 0.0 && p->alpha1 < 1.0 && p->alpha2 > 0.0 && p->alpha2 < 1.0)) return CQ_EINVAL;
     if (!(p->m >= 0.0 && p->m < 1.0) || p->m == 0.5) return CQ_EINVAL;
     if (!(p->T > 0.0) || p->N < 1 || p->N > kMaxWeights) return CQ_EINVAL;
-    if (p->dim != 1 && p->dim != 2) return CQ_EINVAL;
-    if (p->M < 1 || p->M > (p->dim == 1 ? (1 << 16) : 4096)) return CQ_EINVAL;
+    if (p->dim < 1 || p->dim > 3) return CQ_EINVAL;
+    if (p->M < 1 || p->M > (p->dim == 1 ? (1 << 16) : p->dim == 2 ? 4096 : 1024)) return CQ_EINVAL;
     if (p->scheme != CQ_BE && p->scheme != CQ_BDF2) return CQ_EINVAL;
     if (p->form != CQ_DIRECT && p->form != CQ_FAST) return CQ_EINVAL;
     if (p->prec != CQ_F64 && !(p->prec == CQ_F32 && p->form == CQ_FAST) &&
@@ -86,7 +86,7 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     P.tau = p->T / (double)p->N;
     P.inv_tau = 1.0 / P.tau;
     P.N = p->N;
-    P.nmodes = (p->dim == 1) ? p->M : (int64_t)p->M * p->M;
+    P.nmodes = (p->dim == 1) ? p->M : (p->dim == 2) ? (int64_t)p->M * p->M : (int64_t)p->M * p->M * p->M;
     P.scheme = p->scheme;
     P.form = p->form;
     np1 = p->fast.np1;
@@ -1080,7 +1080,7 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if ((st = launched(2))) return st;
     if ((st = cuda_status(cudaMemsetAsync(gl.acc, 0, 8 * sizeof(double), s)))) return st;
     const double h = 1.0 / (p->M + 1);
-    const double wd = (p->dim == 1) ? h : h * h;
+    const double wd = (p->dim == 1) ? h : (p->dim == 2) ? h * h : h * h * h;
     k_adjoint_direct<kAdjBT><<<fblocks, 32, 0, s>>>(P, wd, l.lam, l.d1, l.d2, dzA1, dzA2, gl.q1, gl.q2, gl.qz1,
                                                     gl.qz2, l.hist, gl.tgt, vjp, gl.mu, gl.gx0, gl.acc);
     if ((st = launched())) return st;

@@ -108,29 +108,35 @@ int build_fast_coeffs(int scheme, double beta, double tau, int np1, int np2, int
 }
 
 // ---------------------------------------------------------------------------
-// Spatial operator: lambda_k = 4 (M+1)^2 sin^2(k pi / (2(M+1))), 2D sums over
-// (ky, kx) with mode = ky*M + kx; DST-I S_{jk} = sqrt(2/(M+1)) sin(j k pi/(M+1))
+// Spatial operator: lambda_k = 4 (M+1)^2 sin^2(k pi / (2(M+1))), summed over the
+// axes in 2D / 3D with mode = ky*M + kx / (kz*M + ky)*M + kx; DST-I
+// S_{jk} = sqrt(2/(M+1)) sin(j k pi/(M+1))
 // with the angle reduced exactly in integers before sinpi.
 // ---------------------------------------------------------------------------
-__global__ void k_mode_eigenvalues(int M, int dim, double *__restrict__ lam) {
-    const int64_t total = (dim == 1) ? M : (int64_t)M * M;
+static int64_t field_size(int M, int dim) {
+    return dim == 1 ? (int64_t)M : dim == 2 ? (int64_t)M * M : (int64_t)M * M * M;
+}
+
+__global__ void k_mode_eigenvalues(int M, int dim, int64_t total, double *__restrict__ lam) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     const double q = 2.0 * (M + 1);
     const double f = 4.0 * (double)(M + 1) * (double)(M + 1);
-    if (dim == 1) {
-        const double sv = sinpi((double)(i + 1) / q);
-        lam[i] = f * sv * sv;
-    } else {
-        const int ky = (int)(i / M), kx = (int)(i % M);
-        const double sy = sinpi((double)(ky + 1) / q), sx = sinpi((double)(kx + 1) / q);
-        lam[i] = f * sy * sy + f * sx * sx;
+    // mode = (kz * M + ky) * M + kx: one sine factor per axis
+    int64_t r = i;
+    double acc = 0.0;
+    for (int ax = 0; ax < dim; ++ax) {
+        const int k = (int)(r % M);
+        r /= M;
+        const double sv = sinpi((double)(k + 1) / q);
+        acc += f * sv * sv;
     }
+    lam[i] = acc;
 }
 
 int launch_mode_eigenvalues(int M, int dim, double *lam, cudaStream_t s) {
-    const int64_t total = (dim == 1) ? M : (int64_t)M * M;
-    k_mode_eigenvalues<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, dim, lam);
+    const int64_t total = field_size(M, dim);
+    k_mode_eigenvalues<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, dim, total, lam);
     return launched();
 }
 
@@ -150,12 +156,13 @@ int launch_dst_matrix(int M, double *S, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Small FP64 GEMM C = A B (M x M, row-major), batched over blockIdx.z.
-// 64x64 tile per block, 16x16 threads with 4x4 register tiles, K step 16.
+// Small FP64 GEMM C = A B (M x M, row-major with row strides lda, ldb, ldc),
+// batched over blockIdx.z. 64x64 tile per block, 16x16 threads with 4x4
+// register tiles, K step 16.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_dgemm_square(int M, const double *__restrict__ A, int64_t sA,
-                                                      const double *__restrict__ B, int64_t sB,
-                                                      double *__restrict__ C, int64_t sC) {
+__global__ void __launch_bounds__(256) k_dgemm_square(int M, const double *__restrict__ A, int64_t sA, int64_t lda,
+                                                      const double *__restrict__ B, int64_t sB, int64_t ldb,
+                                                      double *__restrict__ C, int64_t sC, int64_t ldc) {
     __shared__ double As[16][64 + 1];
     __shared__ double Bs[16][64 + 1];
     A += blockIdx.z * sA;
@@ -168,10 +175,10 @@ __global__ void __launch_bounds__(256) k_dgemm_square(int M, const double *__res
         for (int e = threadIdx.x; e < 16 * 64; e += 256) {
             const int kk = e & 15, rr = e >> 4;          // A tile: rows row0.., cols k0..
             const int r = row0 + rr, k = k0 + kk;
-            As[kk][rr] = (r < M && k < M) ? A[(int64_t)r * M + k] : 0.0;
+            As[kk][rr] = (r < M && k < M) ? A[(int64_t)r * lda + k] : 0.0;
             const int cc = e & 63, kb = e >> 6;          // B tile: rows k0.., cols col0..
             const int kb2 = k0 + kb, c = col0 + cc;
-            Bs[kb][cc] = (kb2 < M && c < M) ? B[(int64_t)kb2 * M + c] : 0.0;
+            Bs[kb][cc] = (kb2 < M && c < M) ? B[(int64_t)kb2 * ldb + c] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -193,15 +200,21 @@ __global__ void __launch_bounds__(256) k_dgemm_square(int M, const double *__res
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
             const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * jj;
-            if (r < M && c < M) C[(int64_t)r * M + c] = acc[i][jj];
+            if (r < M && c < M) C[(int64_t)r * ldc + c] = acc[i][jj];
         }
+}
+
+static int dgemm_strided(int M, int batch, const double *A, int64_t sA, int64_t lda, const double *B, int64_t sB,
+                         int64_t ldb, double *C, int64_t sC, int64_t ldc, cudaStream_t s) {
+    if (batch < 1 || batch > 65535) return CQ_EUNSUPPORTED;
+    dim3 grid((M + 63) / 64, (M + 63) / 64, batch);
+    k_dgemm_square<<<grid, 256, 0, s>>>(M, A, sA, lda, B, sB, ldb, C, sC, ldc);
+    return launched();
 }
 
 int launch_dgemm_square(int M, int batch, const double *A, int64_t sA, const double *B, int64_t sB, double *C,
                         int64_t sC, cudaStream_t s) {
-    dim3 grid((M + 63) / 64, (M + 63) / 64, batch);
-    k_dgemm_square<<<grid, 256, 0, s>>>(M, A, sA, B, sB, C, sC);
-    return launched();
+    return dgemm_strided(M, batch, A, sA, M, B, sB, M, C, sC, M, s);
 }
 
 // 1D: out[s][k] = sum_j S[k][j] in[s][j]
@@ -221,9 +234,20 @@ int launch_dst_field(int M, int dim, const double *S, const double *in, double *
         return launched();
     }
     const int64_t mm = (int64_t)M * M;
-    int st = launch_dgemm_square(M, 2, S, 0, in, mm, tmp, mm, s);      // S F
-    if (st) return st;
-    return launch_dgemm_square(M, 2, tmp, mm, S, 0, out, mm, s);       // (S F) S
+    if (dim == 2) {
+        int st = launch_dgemm_square(M, 2, S, 0, in, mm, tmp, mm, s);      // S F
+        if (st) return st;
+        return launch_dgemm_square(M, 2, tmp, mm, S, 0, out, mm, s);       // (S F) S
+    }
+    // 3D, F[z][y][x] per state: along x (F[z] S, batched over z), along y (S F[z]), then along z:
+    // for each y the z-x plane (row stride M^2) is multiplied by S from the left
+    const int64_t m3 = mm * M;
+    int st;
+    if ((st = dgemm_strided(M, 2 * M, in, mm, M, S, 0, M, out, mm, M, s))) return st;
+    if ((st = dgemm_strided(M, 2 * M, S, 0, M, out, mm, M, tmp, mm, M, s))) return st;
+    for (int q = 0; q < 2; ++q)
+        if ((st = dgemm_strided(M, M, S, 0, M, tmp + q * m3, M, mm, out + q * m3, M, mm, s))) return st;
+    return CQ_OK;
 }
 
 }  // namespace fastcq

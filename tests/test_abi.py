@@ -98,6 +98,15 @@ def test_mixed_direct_size_query(fc):
     assert fc._lib.fp2s_init(C.byref(pm), None, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
 
 
+def test_dimension_limits(fc):
+    sz = C.c_size_t(0)
+    p3 = fc.problem(0.3, 0.7, 0.4, 1.0, 64, 3, 31)
+    assert fc.fp2s_solve(p3, None, None, None) >= 65 * 2 * 31 ** 3 * 8     # direct history of 31^3 modes
+    for dim, M in [(4, 5), (0, 5), (3, 1025), (2, 4097)]:
+        p = fc.problem(0.3, 0.7, 0.4, 1.0, 64, dim, M)
+        assert fc._lib.fp2s_solve(C.byref(p), None, None, None, C.byref(sz), None) == fc.CQ_EINVAL
+
+
 def test_vjp_host_checks(fc):
     p = fc.problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, fc.CQ_BE, fc.CQ_DIRECT)
     n_g = fc.fp2s_gradient(p, None, None, None, None)

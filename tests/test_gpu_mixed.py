@@ -57,6 +57,7 @@ MIXED_CASES = [
     ("be_1d_one_block", ci.Problem(0.6, 0.3, 0.2, 1.0, 128, 1, 17, ci.BE, ci.DIRECT, 0, 0, 0), 0),
     ("bdf2_1d_block_plus_one", ci.Problem(0.6, 0.3, 0.6, 1.0, 129, 1, 17, ci.BDF2, ci.DIRECT, 0, 0, 0), 0),
     ("be_1d_N1", ci.Problem(0.3, 0.7, 0.4, 1.0, 1, 1, 9, ci.BE, ci.DIRECT, 0, 0, 0), 0),
+    ("bdf2_3d", ci.Problem(0.35, 0.6, 0.4, 1.0, 300, 3, 15, ci.BDF2, ci.DIRECT, 0, 0, 0), 0),
     ("bdf2_1d_N2", ci.Problem(0.3, 0.7, 0.4, 1.0, 2, 1, 9, ci.BDF2, ci.DIRECT, 0, 0, 0), 0),
 ]
 

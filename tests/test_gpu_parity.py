@@ -165,6 +165,9 @@ SOLVES = [
     ("bdf2_2d_fast", ci.Problem(0.2, 0.8, 0.45, 1.0, 257, 2, 19, ci.BDF2, ci.FAST, 9, 23, 7)),
     ("tiny", ci.Problem(0.5, 0.5, 0.6, 1.0, 3, 1, 1, ci.BDF2, ci.FAST, 2, 2, 3)),
     ("one_step", ci.Problem(0.5, 0.5, 0.6, 1.0, 1, 2, 3, ci.BE, ci.DIRECT)),
+    ("be3d", ci.Problem(0.35, 0.7, 0.4, 1.0, 120, 3, 9, ci.BE, ci.DIRECT)),
+    ("bdf2_3d_fast", ci.Problem(0.3, 0.6, 0.65, 1.0, 150, 3, 11, ci.BDF2, ci.FAST, 12, 30, 9)),
+    ("be3d_fast_ragged", ci.Problem(0.6, 0.45, 0.3, 0.5, 77, 3, 13, ci.BE, ci.FAST, 40, 0, 2)),
 ]
 
 
@@ -183,7 +186,8 @@ def test_fp2s_solve(fc, name, p):
 
 
 @pytest.mark.parametrize("p", [ci.Problem(0.3, 0.6, 0.2, 1.0, 90, 1, 31, ci.BE, ci.DIRECT),
-                               ci.Problem(0.3, 0.6, 0.2, 1.0, 90, 2, 7, ci.BDF2, ci.FAST, 6, 10, 5)])
+                               ci.Problem(0.3, 0.6, 0.2, 1.0, 90, 2, 7, ci.BDF2, ci.FAST, 6, 10, 5),
+                               ci.Problem(0.3, 0.6, 0.2, 1.0, 40, 3, 5, ci.BDF2, ci.DIRECT)])
 def test_fp2s_step_levels(fc, p):
     G0 = ci.g0_uniform(p.M, p.dim, 3)
     _, g_ref = OS.solve(p, G0, all_levels=True)

@@ -47,6 +47,7 @@ F32_CASES = [
     ("bdf2_1d_m0.48_solve64", ci.Problem(0.5, 0.7, 0.48, 0.5, 800, 1, 31, ci.BDF2, ci.FAST, 16, 48, 17)),
     ("be_2d_np128", ci.Problem(0.6, 0.3, 0.2, 1.0, 1500, 2, 15, ci.BE, ci.FAST, 128, 0, 2)),
     ("bdf2_1d_np5", ci.Problem(0.7, 0.4, 0.6, 1.0, 300, 1, 9, ci.BDF2, ci.FAST, 2, 3, 5)),
+    ("be_3d", ci.Problem(0.4, 0.7, 0.3, 1.0, 400, 3, 11, ci.BE, ci.FAST, 64, 0, 2)),
 ]
 
 

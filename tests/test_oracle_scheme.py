@@ -98,6 +98,8 @@ CASES = [
     ci.Problem(0.3, 0.6, 0.6, 1.0, 12, 1, 4, ci.BE, ci.FAST, 3, 0, 2),
     ci.Problem(0.4, 0.7, 0.35, 1.0, 13, 1, 3, ci.BDF2, ci.FAST, 3, 5, 4),
     ci.Problem(0.5, 0.5, 0.8, 1.0, 11, 2, 2, ci.BDF2, ci.FAST, 2, 3, 3),
+    ci.Problem(0.35, 0.75, 0.4, 1.0, 6, 3, 2, ci.BE, ci.DIRECT),         # 3D (d <= 3, Sec. 1)
+    ci.Problem(0.55, 0.3, 0.65, 1.0, 5, 3, 3, ci.BDF2, ci.DIRECT),
 ]
 
 

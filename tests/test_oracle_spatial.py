@@ -13,7 +13,7 @@ def test_dst_is_orthogonal_involution(M):
     assert np.allclose(D, D.T, atol=0)
 
 
-@pytest.mark.parametrize("M,dim", [(5, 1), (9, 1), (3, 2), (6, 2)])
+@pytest.mark.parametrize("M,dim", [(5, 1), (9, 1), (3, 2), (6, 2), (2, 3), (4, 3)])
 def test_dst_diagonalises_laplacian(M, dim):
     A = S.laplacian_matrix(M, dim)
     lam = S.mode_eigenvalues(M, dim)
@@ -33,3 +33,19 @@ def test_eigenvalues_closed_form():
     h = 1.0 / 64
     assert abs(lam[0] - np.pi ** 2) < 1e-2 * np.pi ** 2
     assert np.isclose(lam[-1], 4.0 / h ** 2 * np.sin(63 * np.pi / 128) ** 2, rtol=1e-15)
+
+
+def test_3d_grid_and_mode_order():
+    """3D DOFs and modes run x fastest: the mode (kz, ky, kx) = (0, 0, 1) varies along x
+    only as sin(2 pi x), and its eigenvalue is lambda_1 + lambda_1 + lambda_2."""
+    import cq_inputs as ci
+    M = 5
+    X, Y, Z = ci.grid(M, 3)
+    e = np.zeros(M ** 3)
+    e[1] = 1.0
+    f = S.to_physical(e, M, 3)
+    c = np.sqrt(2.0 / (M + 1)) ** 3
+    expect = c * np.sin(np.pi * Z) * np.sin(np.pi * Y) * np.sin(2 * np.pi * X)
+    assert np.allclose(f, expect, atol=1e-14)
+    lam1 = S.eigenvalues_1d(M)
+    assert np.isclose(S.mode_eigenvalues(M, 3)[1], 2 * lam1[0] + lam1[1], rtol=1e-15)
