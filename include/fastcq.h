@@ -162,7 +162,8 @@ int cq_history_fast_noalloc(int32_t scheme, double beta, double tau, const cq_fa
  * centred finite-difference Laplacian (h = 1/(M+1); M <= 65536, 4096, 1024 for
  * dim 1, 2, 3); DOFs of one state are ordered dof = ix (1D), iy*M + ix (2D),
  * (iz*M + iy)*M + ix (3D), and a two-state field is [2][M^dim] doubles.
- * 0 < alpha1, alpha2 < 1; 0 <= m < 1, m != 1/2; T > 0; N >= 1.
+ * 0 < alpha1, alpha2 < 1; 0 <= m < 1, m != 1/2; T > 0; 1 <= N <= 2^20
+ * (N <= 24000 in the batch API, N <= 13000 for gradients).
  * flags bit 0 (FP2S_ASYNC): fp2s_solve does not synchronise and does not
  * report device status (CQ_ENONFINITE); use fp2s_status() later. */
 #define FP2S_ASYNC 1

@@ -25,7 +25,8 @@ enum : int { ST_NONFINITE = 1, ST_SINGULAR = 2, ST_TIMEOUT = 4 };
 
 constexpr int kMaxNp = 256;      // Gauss-Jacobi points per state (np1 + np2)
 constexpr int kMaxNs = 32;       // exact window of the fast BDF2 form
-constexpr int64_t kMaxWeights = 24000;
+constexpr int64_t kMaxWeights = 24000;       // weights built in shared memory (and per-call limit of the history APIs)
+constexpr int64_t kMaxSolveSteps = 1 << 20;  // fp2s_solve: longer weight tables go through a global scratch
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
@@ -55,8 +56,10 @@ inline int launched(int64_t k = 1) {
 inline bool bad_order(double beta) { return !(beta > 0.0 && beta < 1.0); }
 
 // ---- table builders (tables.cu), all enqueue on `s` -------------------------
-// weights d_i, i = 0..n, of scheme into out (device). Single block.
-int launch_weights(int scheme, double beta, double tau, int64_t n, double *out, cudaStream_t s);
+// weights d_i, i = 0..n, of scheme into out (device). Single block. n <= kMaxWeights, or
+// n <= kMaxSolveSteps with scratch (n + 1 doubles of device memory).
+int launch_weights(int scheme, double beta, double tau, int64_t n, double *out, cudaStream_t s,
+                   double *scratch = nullptr);
 // Gauss-Jacobi nodes / weights.
 int launch_gauss_jacobi(int n, double a, double b, double *nodes, double *wts, cudaStream_t s);
 // Fast-form (r_j, c_j) from Gauss-Jacobi rules already in nodes1/w1 (and nodes2/w2).

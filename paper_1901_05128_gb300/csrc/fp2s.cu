@@ -31,6 +31,7 @@ struct Fp2sLayout {
     double *hist;                 // direct: (N+1) x 2 x nmodes
     double *Y, *ring, *glast;     // step API, fast: 2 x np x nm, 2 x L x nm; both: 2 levels x 2 x nm
     void *mixed;                  // direct, CQ_BF16X3: region of the mixed-precision solve
+    double *wscr;                 // N > kMaxWeights: scratch of the weight builder
     size_t bytes;
 };
 
@@ -41,6 +42,7 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.status = cv.take<int>(64);
     l.d1 = cv.take<double>(P.N + 1);
     l.d2 = cv.take<double>(P.N + 1);
+    if (P.N > kMaxWeights) l.wscr = cv.take<double>(P.N + 1);
     if (P.form == CQ_DIRECT && P.prec == CQ_F64) {
         l.dz1 = cv.take<double>(P.N + 2 * kDirBT + 1);
         l.dz2 = cv.take<double>(P.N + 2 * kDirBT + 1);
@@ -73,7 +75,7 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     if (!p) return CQ_EINVAL;
     if (!(p->alpha1 > 0.0 && p->alpha1 < 1.0 && p->alpha2 > 0.0 && p->alpha2 < 1.0)) return CQ_EINVAL;
     if (!(p->m >= 0.0 && p->m < 1.0) || p->m == 0.5) return CQ_EINVAL;
-    if (!(p->T > 0.0) || p->N < 1 || p->N > kMaxWeights) return CQ_EINVAL;
+    if (!(p->T > 0.0) || p->N < 1 || p->N > kMaxSolveSteps) return CQ_EINVAL;
     if (p->dim < 1 || p->dim > 3) return CQ_EINVAL;
     if (p->M < 1 || p->M > (p->dim == 1 ? (1 << 16) : p->dim == 2 ? 4096 : 1024)) return CQ_EINVAL;
     if (p->scheme != CQ_BE && p->scheme != CQ_BDF2) return CQ_EINVAL;
@@ -623,8 +625,8 @@ static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2,
     int st;
     const double b1 = 1.0 - p->alpha1, b2 = 1.0 - p->alpha2;
     if ((st = cuda_status(cudaMemsetAsync(l.status, 0, 64 * sizeof(int), s)))) return st;
-    if ((st = launch_weights(P.scheme, b1, P.tau, P.N, l.d1, s))) return st;
-    if ((st = launch_weights(P.scheme, b2, P.tau, P.N, l.d2, s))) return st;
+    if ((st = launch_weights(P.scheme, b1, P.tau, P.N, l.d1, s, l.wscr))) return st;
+    if ((st = launch_weights(P.scheme, b2, P.tau, P.N, l.d2, s, l.wscr))) return st;
     if (P.prec != CQ_F64) {
         k_half_weights_df<<<(unsigned)((P.N + 256) / 256), 256, 0, s>>>(l.d1, l.d2, P.N, l.hdf);
         if ((st = launched())) return st;

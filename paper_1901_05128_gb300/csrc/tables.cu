@@ -18,21 +18,22 @@ namespace fastcq {
 // terms with k > 64 are below 3^-64 relative and are left out.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWThreads) k_weights(int scheme, double beta, double scale, int n,
-                                                       double *__restrict__ out) {
-    extern __shared__ double g[];                 // g[0..n]
-    weights_block(scheme, beta, scale, n, out, g);
+                                                       double *__restrict__ out, double *__restrict__ gscr) {
+    extern __shared__ double gsm[];               // g[0..n] in shared memory, or in gscr (longer runs)
+    weights_block(scheme, beta, scale, n, out, gscr ? gscr : gsm);
 }
 
-int launch_weights(int scheme, double beta, double tau, int64_t n, double *out, cudaStream_t s) {
-    if (n < 0 || n > kMaxWeights) return CQ_EINVAL;
-    size_t smem = (size_t)(n + 1) * sizeof(double);
+int launch_weights(int scheme, double beta, double tau, int64_t n, double *out, cudaStream_t s, double *scratch) {
+    if (n < 0 || n > (scratch ? kMaxSolveSteps : kMaxWeights)) return CQ_EINVAL;
+    const bool global = n > kMaxWeights;
+    size_t smem = global ? 0 : (size_t)(n + 1) * sizeof(double);
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncSetAttribute(k_weights, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((kMaxWeights + 1) * sizeof(double)));
         attr_done = true;
     }
-    k_weights<<<1, kWThreads, smem, s>>>(scheme, beta, pow(tau, -beta), (int)n, out);
+    k_weights<<<1, kWThreads, smem, s>>>(scheme, beta, pow(tau, -beta), (int)n, out, global ? scratch : nullptr);
     return launched();
 }
 
