@@ -484,6 +484,109 @@ __global__ void __launch_bounds__(32, 16) k_fp2s_direct(Fp2sParams P, const doub
     if (!isfinite(gm1_1) || !isfinite(gm1_2)) atomicOr(status, ST_NONFINITE);
 }
 
+// ---------------------------------------------------------------------------
+// Fused direct solve for problems with few modes (1D grids, small 2D grids):
+// LP lanes of a warp share one mode. Each lane takes every LP-th history level
+// of the block's sums (consecutive lanes read consecutive levels: coalesced
+// 16-byte loads from the mode-major history histm[mode][k][state]); the LP
+// partial sums are combined with xor shuffles inside the lane group, and every
+// lane of the group then takes the block's steps itself (one lane stores).
+// The FP64 pipe bounds the kernel, so the per-level weight loads (from L1) and
+// the shuffles cost little next to the FMAs they feed.
+// ---------------------------------------------------------------------------
+template <int LP, int BT>
+__global__ void __launch_bounds__(256) k_fp2s_direct_split(Fp2sParams P, const double *__restrict__ lam,
+                                                           const double *__restrict__ g0, double *__restrict__ gN,
+                                                           int *__restrict__ status, const double *__restrict__ d1,
+                                                           const double *__restrict__ d2, double *__restrict__ histm) {
+    const int64_t nm = P.nmodes;
+    const int lane = threadIdx.x & 31, sl = lane % LP;
+    const int64_t mode_raw = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / LP) + lane / LP;
+    const bool active = mode_raw < nm;
+    const int64_t mode = active ? mode_raw : 0;
+    double *hm = histm + (size_t)mode * 2 * (P.N + 1);          // level k of state s at hm[2k + s]
+    const double gz1 = g0[mode], gz2 = g0[nm + mode];
+    if (active && sl == 0) {
+        hm[0] = gz1;
+        hm[1] = gz2;
+    }
+    const double d10 = __ldg(d1), d20 = __ldg(d2);
+    ModeConst mc;
+    if (!mode_setup(P, lam[mode], d10, d20, mc) && active && sl == 0) atomicOr(status, ST_SINGULAR);
+    double gm1_1 = gz1, gm1_2 = gz2, gm2_1 = 0.0, gm2_2 = 0.0;
+    for (int64_t n0 = 1; n0 <= P.N; n0 += BT) {
+        double a1[BT], a2[BT], l1[BT] = {}, l2[BT] = {};
+#pragma unroll
+        for (int b = 0; b < BT; ++b) a1[b] = a2[b] = 0.0;
+        for (int64_t k = 1 + sl; k < n0; k += LP) {
+            const double2 x = *reinterpret_cast<const double2 *>(hm + 2 * k);
+            const int64_t i0 = n0 - k;                     // weight index of the block's first step
+#pragma unroll
+            for (int b = 0; b < BT; ++b) {
+                if (i0 + b <= P.N) {
+                    a1[b] = fma(__ldg(d1 + i0 + b), x.x, a1[b]);
+                    a2[b] = fma(__ldg(d2 + i0 + b), x.y, a2[b]);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = LP / 2; off > 0; off >>= 1) {
+#pragma unroll
+            for (int b = 0; b < BT; ++b) {
+                a1[b] += __shfl_xor_sync(0xffffffffu, a1[b], off);
+                a2[b] += __shfl_xor_sync(0xffffffffu, a2[b], off);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < BT; ++b) {
+            const int64_t n = n0 + b;
+            if (n > P.N) break;
+            double h1 = a1[b], h2 = a2[b];
+#pragma unroll
+            for (int kk = 0; kk < b; ++kk) {
+                h1 = fma(__ldg(d1 + (b - kk)), l1[kk], h1);
+                h2 = fma(__ldg(d2 + (b - kk)), l2[kk], h2);
+            }
+            double d1n = 0.0, d2n = 0.0;
+            if (P.scheme == CQ_BDF2 && n >= 2) {
+                d1n = __ldg(d1 + n - 1);
+                d2n = __ldg(d2 + n - 1);
+            }
+            double x1, x2;
+            mode_step(P, mc, n, h1, h2, d10, d20, d1n, d2n, gm1_1, gm1_2, gm2_1, gm2_2, gz1, gz2, x1, x2);
+            l1[b] = x1;
+            l2[b] = x2;
+            if (active && sl == 0) *reinterpret_cast<double2 *>(hm + 2 * n) = make_double2(x1, x2);
+            gm2_1 = gm1_1;
+            gm2_2 = gm1_2;
+            gm1_1 = x1;
+            gm1_2 = x2;
+        }
+        __syncwarp();                                      // the stored levels are read by the group next block
+    }
+    if (active && sl == 0) {
+        gN[mode] = gm1_1;
+        gN[nm + mode] = gm1_2;
+        if (!isfinite(gm1_1) || !isfinite(gm1_2)) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+// Lanes per mode of the direct solve: one lane per mode (the register-window kernel)
+// once that gives 8 warps per SM, else enough lanes per mode for about 16 warps per SM.
+static int direct_lanes_per_mode(int64_t nmodes) {
+    if (nmodes >= (int64_t)152 * 8 * 32) return 1;
+    int lp = 1;
+    while (lp < 32 && nmodes * lp < (int64_t)152 * 16 * 32) lp *= 2;
+    return lp;
+}
+
+template <int LP>
+static void launch_direct_split(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
+    const int64_t mpb = (256 / 32) * (32 / LP);
+    const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
+    k_fp2s_direct_split<LP, kDirBT><<<blocks, 256, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.hist);
+}
+
 __global__ void k_pad(const double *__restrict__ d, int64_t n, int BT, double *__restrict__ dz) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i > n + 2 * BT) return;
@@ -656,6 +759,14 @@ static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s
         const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
         const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
         k_fp2s_fast<<<blocks, T, smem, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2);
+    } else if (const int lp = direct_lanes_per_mode(P.nmodes); lp > 1) {
+        switch (lp) {
+            case 2: launch_direct_split<2>(P, l, s); break;
+            case 4: launch_direct_split<4>(P, l, s); break;
+            case 8: launch_direct_split<8>(P, l, s); break;
+            case 16: launch_direct_split<16>(P, l, s); break;
+            default: launch_direct_split<32>(P, l, s); break;
+        }
     } else {
         // one-warp blocks: every block runs all N steps, so small blocks spread the
         // modes evenly over the SMs (at most one warp of imbalance per SM)
