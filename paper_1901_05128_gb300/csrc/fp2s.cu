@@ -580,11 +580,13 @@ static int direct_lanes_per_mode(int64_t nmodes) {
     return lp;
 }
 
+// One-warp blocks: a warp or two per SM already keeps its FP64 pipe busy (16 independent
+// FMA chains per lane), so small grids are spread over every SM rather than packed.
 template <int LP>
 static void launch_direct_split(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
-    const int64_t mpb = (256 / 32) * (32 / LP);
-    const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
-    k_fp2s_direct_split<LP, kDirBT><<<blocks, 256, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.hist);
+    const int64_t mpw = 32 / LP;
+    const unsigned blocks = (unsigned)((P.nmodes + mpw - 1) / mpw);
+    k_fp2s_direct_split<LP, kDirBT><<<blocks, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.hist);
 }
 
 __global__ void k_pad(const double *__restrict__ d, int64_t n, int BT, double *__restrict__ dz) {
