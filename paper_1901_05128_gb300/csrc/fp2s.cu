@@ -260,10 +260,10 @@ static int fast_block_threads(int np, int L, int64_t nmodes) {
 // it), the tables are FP32 pairs (r_j, c_j) read as float4 from shared memory
 // (state 2's table is offset by 4 words so the half-warps hit different banks),
 // and the history sums are formed in FP32. Weights, quadrature coefficients and
-// the per-mode step matrices are computed in FP64. The right-hand side and the
-// 2x2 step are evaluated from the FP32 history sums in double-float arithmetic
-// (FP32 pipe), or in FP64 when the coupling is strong (|a| > 10, i.e. m within
-// ~0.045 of 1/2).
+// the per-mode step matrices are computed in FP64. The step is evaluated from the
+// FP32 history sums in the two-term form x = A l + B e with double-float A and B
+// (lane_step2; FP32 pipe), or in FP64 when the coupling is strong (|a| > 10, i.e.
+// m within ~0.045 of 1/2); the first SBD step uses the double-float form.
 // Every mode is pre-scaled by an exact power of two (from its G^0) so that its
 // values sit near 1 in FP32 range; the factor is undone on output.
 // ---------------------------------------------------------------------------
@@ -319,43 +319,63 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
     LaneStep ls;
     const bool ok = lane_step_setup(P, lam[mode], d1[0], d2[0], st, ls);
     if (active && st == 0 && !ok) atomicOr(status, ST_SINGULAR);
+    LaneStep2 l2;
+    lane_step2_setup(P, ls, l2);
 
     float Y[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) Y[j] = 0.0f;
-    float gm1 = gz, gm2 = 0.0f;
+    float gm1 = gz, gm2 = 0.0f, gm1_o = __shfl_xor_sync(0xffffffffu, gz, 16), gm2_o = 0.0f;
     int slot = 0;
-    for (int64_t n = 1; n <= P.N; ++n) {
+    const int N = (int)P.N;
+    for (int n = 1; n <= N; ++n) {
         slot = (slot + 1 == L) ? 0 : slot + 1;
-        float h0 = 0.0f, h1 = 0.0f, h2 = 0.0f, h3 = 0.0f;
+        float hp[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) hp[q] = 0.0f;
         if (n - L >= 1) {
-            const float in = Rc[(size_t)slot * T];
+            const float in = Rc[slot * T];
 #pragma unroll
             for (int j = 0; j < NP; j += 4) {
                 const float4 p = rc4[j / 2];
                 const float4 q = rc4[j / 2 + 1];
+                const int o = (j / 4) & 1;                    // eight partial sums: shorter chains
                 Y[j] = fmaf(p.x, Y[j], in);
                 Y[j + 1] = fmaf(p.z, Y[j + 1], in);
                 Y[j + 2] = fmaf(q.x, Y[j + 2], in);
                 Y[j + 3] = fmaf(q.z, Y[j + 3], in);
-                h0 = fmaf(p.y, Y[j], h0);
-                h1 = fmaf(p.w, Y[j + 1], h1);
-                h2 = fmaf(q.y, Y[j + 2], h2);
-                h3 = fmaf(q.w, Y[j + 3], h3);
+                hp[4 * o] = fmaf(p.y, Y[j], hp[4 * o]);
+                hp[4 * o + 1] = fmaf(p.w, Y[j + 1], hp[4 * o + 1]);
+                hp[4 * o + 2] = fmaf(q.y, Y[j + 2], hp[4 * o + 2]);
+                hp[4 * o + 3] = fmaf(q.w, Y[j + 3], hp[4 * o + 3]);
             }
         }
-        const int imax = (int)min((int64_t)(L - 1), n - 1);
+        const int imax = min(L - 1, n - 1);
         int sl = slot;
         for (int i = 1; i <= imax; ++i) {
             sl = (sl == 0) ? L - 1 : sl - 1;
-            if (i & 1) h1 = fmaf(ws[2 * i], Rc[(size_t)sl * T], h1);
-            else h2 = fmaf(ws[2 * i], Rc[(size_t)sl * T], h2);
+            if (i & 1) hp[1] = fmaf(ws[2 * i], Rc[sl * T], hp[1]);
+            else hp[2] = fmaf(ws[2 * i], Rc[sl * T], hp[2]);
         }
-        const float h = (h0 + h1) + (h2 + h3);
-        const float x = lane_step(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
-        Rc[(size_t)slot * T] = x;
+        const float h = ((hp[0] + hp[4]) + (hp[1] + hp[5])) + ((hp[2] + hp[6]) + (hp[3] + hp[7]));
+        float x;
+        if (solve64 || (P.scheme == CQ_BDF2 && n == 1)) {
+            x = lane_step(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
+        } else if (P.scheme == CQ_BE) {
+            x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, __shfl_xor_sync(0xffffffffu, h, 16), 0.0f);
+        } else {
+            const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
+            // e = h + d_{n-1} g^0 / 2 as a double-float pair
+            const df e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
+            x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, __shfl_xor_sync(0xffffffffu, e.hi, 16),
+                           __shfl_xor_sync(0xffffffffu, e.lo, 16));
+        }
+        const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);
+        Rc[slot * T] = x;
         gm2 = gm1;
         gm1 = x;
+        gm2_o = gm1_o;
+        gm1_o = x_o;
     }
     if (active) {
         const double out = ldexp((double)gm1, ex);

@@ -231,18 +231,18 @@ __device__ __forceinline__ void lane_step2_setup(const Fp2sParams &P, const Lane
 }
 
 // x = A l + B e for the lane's state: (l, l_lo) and (l_o, l_o_lo) the double-float l
-// of the lane's and the other state, e and e_o the history terms (FP32).
+// of the lane's and the other state, (e, e_lo) and (e_o, e_o_lo) the history terms.
 __device__ __forceinline__ float lane_step2(const LaneStep2 &c, float l, float l_lo, float l_o, float l_o_lo, float e,
-                                            float e_o) {
+                                            float e_lo, float e_o, float e_o_lo) {
     const float p1 = c.a_hi[0] * l;
     float r = fmaf(c.a_hi[0], l, -p1);
     r = fmaf(c.a_hi[0], l_lo, fmaf(c.a_lo[0], l, r));
     const float p2 = c.a_hi[1] * l_o;
     r += fmaf(c.a_hi[1], l_o_lo, fmaf(c.a_lo[1], l_o, fmaf(c.a_hi[1], l_o, -p2)));
     const float p3 = c.b_hi[0] * e;
-    r += fmaf(c.b_lo[0], e, fmaf(c.b_hi[0], e, -p3));
+    r += fmaf(c.b_hi[0], e_lo, fmaf(c.b_lo[0], e, fmaf(c.b_hi[0], e, -p3)));
     const float p4 = c.b_hi[1] * e_o;
-    r += fmaf(c.b_lo[1], e_o, fmaf(c.b_hi[1], e_o, -p4));
+    r += fmaf(c.b_hi[1], e_o_lo, fmaf(c.b_lo[1], e_o, fmaf(c.b_hi[1], e_o, -p4)));
     const df s12 = two_sum(p1, p2), s34 = two_sum(p3, p4);
     const df s = two_sum(s12.hi, s34.hi);
     return s.hi + (s.lo + ((s12.lo + s34.lo) + r));

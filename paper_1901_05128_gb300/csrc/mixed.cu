@@ -204,11 +204,13 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
             if (full_setup && (A.solve64 || (P.scheme == CQ_BDF2 && n == 1))) {
                 x = lane_step(P, ls, A.solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
             } else if (P.scheme == CQ_BE) {
-                x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, __shfl_xor_sync(0xffffffffu, h, 16));
+                x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, __shfl_xor_sync(0xffffffffu, h, 16), 0.0f);
             } else {
                 const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
-                const float e = fmaf(__ldg(hd_hi + n - 1), gz, h);
-                x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e, __shfl_xor_sync(0xffffffffu, e, 16));
+                // e = h + d_{n-1} g^0 / 2 as a double-float pair
+                const df e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
+                x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, __shfl_xor_sync(0xffffffffu, e.hi, 16),
+                               __shfl_xor_sync(0xffffffffu, e.lo, 16));
             }
 #pragma unroll
             for (int bb = b + 1; bb < kMxSB; ++bb) a[bb] = fmaf(wt[bb - b], x, a[bb]);
