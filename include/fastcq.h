@@ -53,6 +53,8 @@ extern "C" {
                         * and per-mode matrices, double-float (FP64 when |a| > 10) 2x2 step */
 #define CQ_BF16X3  2   /* precision form of the direct history on tensor cores: operands split into
                         * BF16 hi + lo, hi*hi + hi*lo + lo*hi accumulated in FP32 */
+#define CQ_TF32X3  3   /* the same with TF32 hi + lo (11 significant bits each; half the BF16
+                        * tensor rate, twice the operand bytes, ~2^6 times smaller split error) */
 
 /* Fast-form sizes. BE (Eqs. 3.6-3.10): np1 = Np Gauss-Jacobi points, np2
  * ignored, ns ignored (the exact window of BE is d_1 alone).
@@ -110,12 +112,13 @@ int cq_fast_coeffs(int32_t scheme, double beta, double tau, const cq_fast_cfg_t 
  * i.e. the strictly lower-triangular Toeplitz product of the CQ weights with
  * the levels G^1..G^{n-1} (row t of G_dev holds G^t; row 0 is never read).
  * 1 <= n_lo <= n_hi, ndof >= 0, ldg, ldh >= ndof. The weights are computed
- * into the workspace. prec: CQ_F64 (FP64 FMAs) or CQ_BF16X3 (tcgen05 tensor
- * cores; G and the Toeplitz tiles are split and staged in the workspace, which
- * then holds about 4 * ndof * n_hi bytes; n_hi + 128 <= 24000; magnitudes
- * below 2^-126 in the FP32 accumulator are returned as zero). On a device
- * fault or an expired internal wait the BF16X3 path writes NaN to the affected
- * outputs. */
+ * into the workspace. prec: CQ_F64 (FP64 FMAs), CQ_BF16X3 or CQ_TF32X3
+ * (tcgen05 tensor cores; G and the Toeplitz tiles are split and staged in the
+ * workspace, which then holds about 4 (BF16) or 8 (TF32) * ndof * n_hi bytes;
+ * n_hi + 128 <= 24000; the FP32 accumulation runs in chunks of 128 levels
+ * summed with round-to-nearest; magnitudes below 2^-126 in the FP32
+ * accumulator are returned as zero). On a device fault or an expired internal
+ * wait the tensor-core paths write NaN to the affected outputs. */
 int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof,
                       int64_t n_lo, int64_t n_hi, const double *G_dev, int64_t ldg,
                       double *H_dev, int64_t ldh, int32_t prec,

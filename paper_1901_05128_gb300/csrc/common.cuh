@@ -82,9 +82,9 @@ int launch_dgemm_square(int M, int batch, const double *A, int64_t sA, const dou
 int launch_dst_field(int M, int dim, const double *S, const double *in, double *out, double *tmp,
                      cudaStream_t s);
 
-// Tensor-core (tcgen05, BF16x3) direct history (history_tc.cu).
-size_t history_tc_workspace(int64_t ndof, int64_t n_lo, int64_t n_hi);
-int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_lo, int64_t n_hi, const double *G,
-                   int64_t ldg, double *H, int64_t ldh, void *ws, cudaStream_t s);
+// Tensor-core (tcgen05, BF16x3 or TF32x3: kind 0 / 1) direct history (history_tc.cu).
+size_t history_tc_workspace(int kind, int64_t ndof, int64_t n_lo, int64_t n_hi);
+int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, int64_t n_lo, int64_t n_hi,
+                   const double *G, int64_t ldg, double *H, int64_t ldh, void *ws, cudaStream_t s);
 
 }  // namespace fastcq

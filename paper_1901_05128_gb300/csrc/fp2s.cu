@@ -30,7 +30,7 @@ struct Fp2sLayout {
     float *hdf;                   // FP32 fast form: 0.5*d_i of both states as double-float, [4][N+1]
     double *hist;                 // direct: (N+1) x 2 x nmodes
     double *Y, *ring, *glast;     // step API, fast: 2 x np x nm, 2 x L x nm; both: 2 levels x 2 x nm
-    void *mixed;                  // direct, CQ_BF16X3: region of the mixed-precision solve
+    void *mixed;                  // direct, CQ_BF16X3 / CQ_TF32X3: region of the mixed-precision solve
     double *wscr;                 // N > kMaxWeights: scratch of the weight builder
     size_t bytes;
 };
@@ -59,7 +59,8 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.gN = cv.take<double>(2 * nm);
     if (P.form == CQ_DIRECT && P.prec == CQ_F64) l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
     if (P.prec != CQ_F64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
-    if (P.form == CQ_DIRECT && P.prec == CQ_BF16X3) l.mixed = cv.take<char>(mixed_direct_bytes(P));
+    if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3))
+        l.mixed = cv.take<char>(mixed_direct_bytes(P));
     if (stepper) {
         if (P.form == CQ_FAST) {
             l.Y = cv.take<double>((size_t)2 * P.np * nm);
@@ -81,7 +82,7 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     if (p->scheme != CQ_BE && p->scheme != CQ_BDF2) return CQ_EINVAL;
     if (p->form != CQ_DIRECT && p->form != CQ_FAST) return CQ_EINVAL;
     if (p->prec != CQ_F64 && !(p->prec == CQ_F32 && p->form == CQ_FAST) &&
-        !(p->prec == CQ_BF16X3 && p->form == CQ_DIRECT))
+        !((p->prec == CQ_BF16X3 || p->prec == CQ_TF32X3) && p->form == CQ_DIRECT))
         return CQ_EUNSUPPORTED;
     P.prec = p->prec;
     P.a = (1.0 - p->m) / (2.0 * p->m - 1.0);
@@ -817,7 +818,7 @@ extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double 
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
     if ((st = timing_begin(s))) return st;
-    if (P.form == CQ_DIRECT && P.prec == CQ_BF16X3) {
+    if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3)) {
         // counts its own launches
         if ((st = mixed_direct_run(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.hdf, l.mixed, s))) return st;
     } else {

@@ -272,13 +272,14 @@ extern "C" int cq_history_direct(int32_t scheme, double beta, double tau, int64_
     if (!ws_bytes || (scheme != CQ_BE && scheme != CQ_BDF2) || bad_order(beta) || !(tau > 0.0) || ndof < 0 ||
         n_lo < 1 || n_hi < n_lo || n_hi > kMaxWeights || ldg < ndof || ldh < ndof)
         return CQ_EINVAL;
-    if (prec == CQ_BF16X3) {
-        const size_t need = history_tc_workspace(ndof, n_lo, n_hi);
+    if (prec == CQ_BF16X3 || prec == CQ_TF32X3) {
+        const int kind = prec == CQ_TF32X3 ? 1 : 0;
+        const size_t need = history_tc_workspace(kind, ndof, n_lo, n_hi);
         if (!ws_dev) { *ws_bytes = need; return CQ_OK; }
         if (*ws_bytes < need) return CQ_ENOMEM;
         if (n_hi == n_lo || ndof == 0) return CQ_OK;
         if (!G_dev || !H_dev || ((uintptr_t)ws_dev & 255)) return CQ_EINVAL;
-        return history_tc_run(scheme, beta, tau, ndof, n_lo, n_hi, G_dev, ldg, H_dev, ldh, ws_dev,
+        return history_tc_run(kind, scheme, beta, tau, ndof, n_lo, n_hi, G_dev, ldg, H_dev, ldh, ws_dev,
                               (cudaStream_t)stream);
     }
     if (prec != CQ_F64) return CQ_EUNSUPPORTED;

@@ -1,15 +1,19 @@
 // Direct history on the 5th-generation tensor cores (tcgen05), split BF16
-// ("BF16x3") with FP32 accumulation in tensor memory.
+// ("BF16x3", kind::f16) or split TF32 ("TF32x3", kind::tf32) operands with FP32
+// accumulation in tensor memory.
 //
 // The direct history of Eq. 3.8 over a range of steps is the product of a
 // strictly lower-triangular Toeplitz matrix with the matrix of levels:
 //     H[n][dof] = sum_{k=1}^{n-1} d_{n-k} G[k][dof],   n in [n_lo, n_hi).
 // With k' = k - 1 (levels 1.. only) this is a GEMM with M = steps, N = DOFs,
 // K = levels:  A[m][k'] = d_{m-1-k'} (0 unless m-1-k' >= 1),  B[dof][k'] = G[k'+1][dof].
-// Each operand x is split as x = hi + lo with hi = bf16(x), lo = bf16(x - hi)
-// (round to nearest even, computed with integer operations: bf16split.h);
-// the product is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term,
-// <= 2^-16 relative, is dropped; the split itself leaves <= 2^-16 of x).
+// Each operand x is split as x = hi + lo with hi = rn(x), lo = rn(x - hi) to 8
+// (BF16) or 11 (TF32) significant bits (round to nearest even, computed with
+// integer operations: bf16split.h); the product is formed as
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term, <= 2^-16 resp. 2^-22
+// relative, is dropped; the split itself leaves <= 2^-16 resp. 2^-22 of x).
+// Both forms use the same shared-memory tiles: a 128-byte swizzle row holds 64
+// BF16 or 32 TF32 levels, and one MMA instruction consumes 32 bytes of K.
 //
 // A 128 x 64 tile of A at rows m0.. and columns k0'.. depends only on
 // delta = m0 - 1 - k0', so the distinct tiles are precomputed once per call
@@ -38,13 +42,14 @@ namespace fastcq {
 namespace tc {
 
 constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 2;        // 16 KiB
-constexpr int B_BYTES = BN * BK * 2;        // 32 KiB
+constexpr int ROW_BYTES = 128;              // one swizzle row of K per operand row and stage
+constexpr int A_BYTES = BM * ROW_BYTES;     // 16 KiB
+constexpr int B_BYTES = BN * ROW_BYTES;     // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int EPI_WARPS = 8;                // two warps per TMEM lane quarter, one per column half
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int TMEM_COLS = 512;              // two 128 x 256 FP32 accumulators
-constexpr int CHUNK = 2;                    // K stages (128 levels) accumulated per tensor-memory pass
+constexpr int CHUNK_LEVELS = 128;          // levels accumulated per tensor-memory pass
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
 
@@ -113,15 +118,26 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator, both K-major, M = BM, N = BN.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptors: FP32 accumulator (bits 4-5), A and B format (bits 7-9, 10-12:
+// BF16 = 1 under kind::f16, TF32 = 2 under kind::tf32), both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc(int fmt) {
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    if constexpr (KIND == TC_TF32X3) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc(2)), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc(1)), "r"(accumulate));
+    }
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -191,9 +207,11 @@ __device__ __forceinline__ void store16(float *row, int64_t c0, int64_t ncol, in
     }
 }
 
-template <typename OutT>
-__global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_constant__ TcMaps maps, TcParams P,
-                                                                 OutT *__restrict__ H, int *__restrict__ status) {
+template <typename OutT, int KIND>
+__global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant__ TcMaps maps, TcParams P,
+                                                          OutT *__restrict__ H, int *__restrict__ status) {
+    constexpr int BKK = kind_bk(KIND);                          // levels per stage
+    constexpr int CHUNK = CHUNK_LEVELS / BKK;                   // stages per accumulator chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -218,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
     const int64_t m_last = min(m0 + BM - 1, P.n_lo + P.rows - 1);
     // levels k' < m_last - 1 contribute (k = k' + 1 <= m_last - 1)
     const int64_t k_end = min((int64_t)P.kprime, m_last - 1);
-    const int num_k = k_end > 0 ? (int)((k_end + BK - 1) / BK) : 0;
+    const int num_k = k_end > 0 ? (int)((k_end + BKK - 1) / BKK) : 0;
     const int nchunks = (num_k + CHUNK - 1) / CHUNK;
 
     if (threadIdx.x == 0) {
@@ -261,13 +279,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
             }
             if (*(volatile int *)abort_flag) break;
             unsigned char *st = smem + s * STAGE_BYTES;
-            const int64_t delta = m0 - 1 - (int64_t)ks * BK;
-            const int arow = (int)((delta - P.delta0) / BK) * BM;
+            const int64_t delta = m0 - 1 - (int64_t)ks * BKK;
+            const int arow = (int)((delta - P.delta0) / BKK) * BM;
             mbar_expect_tx(&full[s], STAGE_BYTES);
             tma_load_2d(st, tA_hi, &full[s], 0, arow);
             tma_load_2d(st + A_BYTES, tA_lo, &full[s], 0, arow);
-            tma_load_2d(st + 2 * A_BYTES, tB_hi, &full[s], ks * BK, (int)brow);
-            tma_load_2d(st + 2 * A_BYTES + B_BYTES, tB_lo, &full[s], ks * BK, (int)brow);
+            tma_load_2d(st + 2 * A_BYTES, tB_hi, &full[s], ks * BKK, (int)brow);
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, tB_lo, &full[s], ks * BKK, (int)brow);
             armed[s] = ks;
         }
         if (*(volatile int *)abort_flag) {
@@ -300,12 +318,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
             const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
             const uint32_t acc = tmem + (uint32_t)(buf * BN);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t off = kk * 32;            // 16 BF16 = 32 bytes along K inside the swizzle row
+            for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
+                const uint32_t off = kk * 32;            // one MMA: 32 bytes along K (16 BF16 or 8 TF32)
                 const uint32_t acc0 = (ks % CHUNK > 0 || kk > 0) ? 1u : 0u;
-                umma_bf16(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
-                umma_bf16(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
-                umma_bf16(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+                umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
+                umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+                umma<KIND>(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
             }
             umma_commit(&empty[s]);                       // stage reusable once these MMAs are done
             if (ks % CHUNK == CHUNK - 1 || ks == num_k - 1) umma_commit(&tfull[buf]);
@@ -364,30 +382,45 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc_bf16x3(const __grid_c
     }
 }
 
-// Bank of Toeplitz tiles: tile t, row r, column c holds d_{delta0 + 64 t + r - c} when
-// that index lies in [1, nw], else 0; split into BF16 hi + lo.
+// Element of a hi / lo pair: BF16 bits or TF32 (FP32 bits with 13 low zero bits).
+template <int KIND> struct Elem;
+template <> struct Elem<TC_BF16X3> {
+    using T = uint16_t;
+    __device__ static void split(double v, T &h, T &l) { bf16_split(v, &h, &l); }
+};
+template <> struct Elem<TC_TF32X3> {
+    using T = uint32_t;
+    __device__ static void split(double v, T &h, T &l) { tf32_split(v, &h, &l); }
+};
+
+// Bank of Toeplitz tiles: tile t, row r, column c holds d_{delta0 + BK t + r - c} when
+// that index lies in [1, nw], else 0; split into hi + lo.
+template <int KIND>
 __global__ void k_toeplitz_bank(const double *__restrict__ d, int64_t nw, int64_t delta0, int ntiles,
-                                __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+                                typename Elem<KIND>::T *__restrict__ hi, typename Elem<KIND>::T *__restrict__ lo) {
+    constexpr int BKK = kind_bk(KIND);
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)ntiles * BM * BK) return;
-    const int c = (int)(e % BK);
-    const int64_t rr = e / BK;                   // t * BM + r
+    if (e >= (int64_t)ntiles * BM * BKK) return;
+    const int c = (int)(e % BKK);
+    const int64_t rr = e / BKK;                  // t * BM + r
     const int r = (int)(rr % BM);
     const int64_t t = rr / BM;
-    const int64_t q = delta0 + BK * t + r - c;
+    const int64_t q = delta0 + BKK * t + r - c;
     const double v = (q >= 1 && q <= nw) ? d[q] : 0.0;
-    uint16_t h, l;
-    bf16_split(v, &h, &l);
-    hi[e] = __ushort_as_bfloat16(h);
-    lo[e] = __ushort_as_bfloat16(l);
+    typename Elem<KIND>::T h, l;
+    Elem<KIND>::split(v, h, l);
+    hi[e] = h;
+    lo[e] = l;
 }
 
 // Gt[dof][k'] = split(G[k' + 1][dof]) for k' < kprime, 0 for kprime <= k' < kpad.
 // Tile of 64 levels x 32 DOFs: coalesced FP64 row reads, then every thread writes
-// a pair of BF16 values (a warp stores 128 contiguous bytes per array).
+// a pair of elements (a warp stores 128 or 256 contiguous bytes per array).
+template <int KIND>
 __global__ void __launch_bounds__(256) k_split_transpose(const double *__restrict__ G, int64_t ldg, int64_t ndof,
-                                                         int kprime, int kpad, __nv_bfloat16 *__restrict__ hi,
-                                                         __nv_bfloat16 *__restrict__ lo) {
+                                                         int kprime, int kpad, typename Elem<KIND>::T *__restrict__ hi,
+                                                         typename Elem<KIND>::T *__restrict__ lo) {
+    using T = typename Elem<KIND>::T;
     __shared__ double tile[32][65];                 // [dof][level]
     const int k0 = blockIdx.x * 64;
     const int64_t d0 = (int64_t)blockIdx.y * 32;
@@ -401,12 +434,17 @@ __global__ void __launch_bounds__(256) k_split_transpose(const double *__restric
     for (int r = ty; r < 32; r += 8) {
         const int64_t dof = d0 + r;
         if (dof >= ndof) break;
-        uint16_t h0, l0, h1, l1;
-        bf16_split(tile[r][2 * tx], &h0, &l0);        // integer ops only (no FP64 pipe)
-        bf16_split(tile[r][2 * tx + 1], &h1, &l1);
+        T h0, l0, h1, l1;
+        Elem<KIND>::split(tile[r][2 * tx], h0, l0);         // integer ops only (no FP64 pipe)
+        Elem<KIND>::split(tile[r][2 * tx + 1], h1, l1);
         const int64_t o = dof * kpad + k0 + 2 * tx;
-        *reinterpret_cast<uint32_t *>(hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
-        *reinterpret_cast<uint32_t *>(lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+        if constexpr (KIND == TC_TF32X3) {
+            *reinterpret_cast<uint2 *>(hi + o) = make_uint2(h0, h1);
+            *reinterpret_cast<uint2 *>(lo + o) = make_uint2(l0, l1);
+        } else {
+            *reinterpret_cast<uint32_t *>(hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            *reinterpret_cast<uint32_t *>(lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+        }
     }
 }
 
@@ -427,16 +465,19 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2D BF16 tensor [rows][cols] (cols contiguous, pitch in elements), box {64, box_rows}, 128-byte swizzle.
-static int make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t pitch,
+// 2D tensor [rows][cols] of the kind's elements (cols contiguous, pitch in elements),
+// box {128 bytes of columns, box_rows}, 128-byte swizzle.
+static int make_map(int kind, CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t pitch,
                     uint32_t box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return CQ_ECUDA;
+    const int es = kind_esize(kind);
     const cuuint64_t dims[2] = {cols, rows};
-    const cuuint64_t strides[1] = {pitch * 2};
-    const cuuint32_t box[2] = {64, box_rows};
+    const cuuint64_t strides[1] = {pitch * (uint64_t)es};
+    const cuuint32_t box[2] = {(cuuint32_t)kind_bk(kind), box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+    const CUtensorMapDataType dt = kind == TC_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUresult r = fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? CQ_OK : CQ_ECUDA;
@@ -445,31 +486,32 @@ static int make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t ro
 struct TcLayout {
     int *status;
     double *d;
-    __nv_bfloat16 *a_hi, *a_lo, *g_hi, *g_lo;
+    char *a_hi, *a_lo, *g_hi, *g_lo;
     int ntiles, kpad;
     int64_t delta0;
     size_t bytes;
 };
 
-static TcLayout tc_layout(void *ws, int64_t ndof, int64_t n_lo, int64_t n_hi) {
+static TcLayout tc_layout(int kind, void *ws, int64_t ndof, int64_t n_lo, int64_t n_hi) {
     TcLayout l{};
+    const int bk = kind_bk(kind), es = kind_esize(kind);
     const int64_t kprime = n_hi - 2 > 0 ? n_hi - 2 : 0;
-    l.kpad = (int)(((kprime + BK - 1) / BK) * BK);
-    if (l.kpad == 0) l.kpad = BK;
+    l.kpad = (int)(((kprime + 63) / 64) * 64);      // multiple of the split tile (64 levels)
+    if (l.kpad == 0) l.kpad = 64;
     const int64_t rows = n_hi - n_lo;
     const int64_t num_i = (rows + BM - 1) / BM;
-    // delta = m0 - 1 - 64 j over tiles i (m0 = n_lo + 128 i) and K-steps j; smallest at i = 0, largest j
-    const int64_t jmax0 = l.kpad / BK;
-    l.delta0 = n_lo - 1 - BK * jmax0;
+    // delta = m0 - 1 - bk j over tiles i (m0 = n_lo + 128 i) and K-steps j; smallest at i = 0, largest j
+    const int64_t jmax0 = l.kpad / bk;
+    l.delta0 = n_lo - 1 - bk * jmax0;
     const int64_t dmax = n_lo - 1 + BM * (num_i > 0 ? num_i - 1 : 0);
-    l.ntiles = (int)((dmax - l.delta0) / BK + 1);
+    l.ntiles = (int)((dmax - l.delta0) / bk + 1);
     Carve cv(ws);
     l.status = cv.take<int>(64);
     l.d = cv.take<double>(n_hi + BM + 2);
-    l.a_hi = cv.take<__nv_bfloat16>((size_t)l.ntiles * BM * BK);
-    l.a_lo = cv.take<__nv_bfloat16>((size_t)l.ntiles * BM * BK);
-    l.g_hi = cv.take<__nv_bfloat16>((size_t)ndof * l.kpad);
-    l.g_lo = cv.take<__nv_bfloat16>((size_t)ndof * l.kpad);
+    l.a_hi = cv.take<char>((size_t)l.ntiles * BM * bk * es);
+    l.a_lo = cv.take<char>((size_t)l.ntiles * BM * bk * es);
+    l.g_hi = cv.take<char>((size_t)ndof * l.kpad * es);
+    l.g_lo = cv.take<char>((size_t)ndof * l.kpad * es);
     l.bytes = cv.bytes();
     return l;
 }
@@ -477,45 +519,60 @@ static TcLayout tc_layout(void *ws, int64_t ndof, int64_t n_lo, int64_t n_hi) {
 static int tc_attr() {
     static bool done = false;
     if (done) return CQ_OK;
-    if (cudaFuncSetAttribute(k_history_tc_bf16x3<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES) != cudaSuccess ||
-        cudaFuncSetAttribute(k_history_tc_bf16x3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES) != cudaSuccess)
+    const int sm = (int)SMEM_BYTES;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(k_history_tc<double, TC_BF16X3>, a, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_history_tc<float, TC_BF16X3>, a, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_history_tc<double, TC_TF32X3>, a, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_history_tc<float, TC_TF32X3>, a, sm) != cudaSuccess)
         return CQ_ECUDA;
     done = true;
     return CQ_OK;
 }
 
-}  // namespace tc
-
-size_t history_tc_workspace(int64_t ndof, int64_t n_lo, int64_t n_hi) {
-    return tc::tc_layout(nullptr, ndof, n_lo, n_hi).bytes;
+template <int KIND>
+static void launch_bank(const double *d, int64_t nw, int64_t delta0, int ntiles, void *hi, void *lo, cudaStream_t s) {
+    using T = typename Elem<KIND>::T;
+    const int64_t elems = (int64_t)ntiles * BM * kind_bk(KIND);
+    k_toeplitz_bank<KIND><<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(d, nw, delta0, ntiles,
+                                                                           static_cast<T *>(hi), static_cast<T *>(lo));
 }
 
-int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_lo, int64_t n_hi, const double *G,
-                   int64_t ldg, double *H, int64_t ldh, void *ws, cudaStream_t s) {
+}  // namespace tc
+
+size_t history_tc_workspace(int kind, int64_t ndof, int64_t n_lo, int64_t n_hi) {
+    return tc::tc_layout(kind, nullptr, ndof, n_lo, n_hi).bytes;
+}
+
+int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, int64_t n_lo, int64_t n_hi,
+                   const double *G, int64_t ldg, double *H, int64_t ldh, void *ws, cudaStream_t s) {
     using namespace tc;
-    TcLayout l = tc_layout(ws, ndof, n_lo, n_hi);
+    TcLayout l = tc_layout(kind, ws, ndof, n_lo, n_hi);
     const int64_t nw = n_hi + BM;
     if (nw > kMaxWeights) return CQ_EUNSUPPORTED;
     if (ndof > ((int64_t)1 << 31) - BN) return CQ_EUNSUPPORTED;
     int st;
     if ((st = cuda_status(cudaMemsetAsync(l.status, 0, 64 * sizeof(int), s)))) return st;
     if ((st = launch_weights(scheme, beta, tau, nw, l.d, s))) return st;
-    const int64_t bank_elems = (int64_t)l.ntiles * BM * BK;
-    k_toeplitz_bank<<<(unsigned)((bank_elems + 255) / 256), 256, 0, s>>>(l.d, n_hi, l.delta0, l.ntiles, l.a_hi, l.a_lo);
-    if ((st = launched())) return st;
+    if ((st = tc_bank(kind, l.d, n_hi, l.delta0, l.ntiles, l.a_hi, l.a_lo, s))) return st;
     const int kprime = (int)(n_hi - 2 > 0 ? n_hi - 2 : 0);
     dim3 tg((unsigned)(l.kpad / 64), (unsigned)((ndof + 31) / 32));
-    k_split_transpose<<<tg, dim3(32, 8), 0, s>>>(G, ldg, ndof, kprime, l.kpad, l.g_hi, l.g_lo);
+    if (kind == TC_TF32X3)
+        k_split_transpose<TC_TF32X3><<<tg, dim3(32, 8), 0, s>>>(G, ldg, ndof, kprime, l.kpad,
+                                                                 reinterpret_cast<uint32_t *>(l.g_hi),
+                                                                 reinterpret_cast<uint32_t *>(l.g_lo));
+    else
+        k_split_transpose<TC_BF16X3><<<tg, dim3(32, 8), 0, s>>>(G, ldg, ndof, kprime, l.kpad,
+                                                                 reinterpret_cast<uint16_t *>(l.g_hi),
+                                                                 reinterpret_cast<uint16_t *>(l.g_lo));
     if ((st = launched())) return st;
     TcMaps maps;
-    if ((st = make_map(&maps.a_hi[0], l.a_hi, BK, (uint64_t)l.ntiles * BM, BK, BM))) return st;
-    if ((st = make_map(&maps.a_lo[0], l.a_lo, BK, (uint64_t)l.ntiles * BM, BK, BM))) return st;
+    if ((st = tc_map_bank(kind, &maps.a_hi[0], l.a_hi, l.ntiles))) return st;
+    if ((st = tc_map_bank(kind, &maps.a_lo[0], l.a_lo, l.ntiles))) return st;
     maps.a_hi[1] = maps.a_hi[0];
     maps.a_lo[1] = maps.a_lo[0];
-    if ((st = make_map(&maps.b_hi, l.g_hi, l.kpad, ndof, l.kpad, BN))) return st;
-    if ((st = make_map(&maps.b_lo, l.g_lo, l.kpad, ndof, l.kpad, BN))) return st;
+    if ((st = tc_map_levels(kind, &maps.b_hi, l.g_hi, l.kpad, ndof))) return st;
+    if ((st = tc_map_levels(kind, &maps.b_lo, l.g_lo, l.kpad, ndof))) return st;
     TcParams P;
     P.ndof = ndof;
     P.n_lo = n_lo;
@@ -533,38 +590,44 @@ int history_tc_run(int scheme, double beta, double tau, int64_t ndof, int64_t n_
     if (blocks > 0x7fffffffLL) return CQ_EUNSUPPORTED;
     if ((st = tc_attr())) return st;
     if ((st = timing_begin(s))) return st;
-    k_history_tc_bf16x3<double><<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(maps, P, H, l.status);
+    if (kind == TC_TF32X3)
+        k_history_tc<double, TC_TF32X3><<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(maps, P, H, l.status);
+    else
+        k_history_tc<double, TC_BF16X3><<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(maps, P, H, l.status);
     if ((st = launched())) return st;
     return timing_end(s);
 }
 
-int tc_bank(const double *d, int64_t nw, int64_t delta0, int ntiles, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-            cudaStream_t s) {
+int tc_bank(int kind, const double *d, int64_t nw, int64_t delta0, int ntiles, void *hi, void *lo, cudaStream_t s) {
     using namespace tc;
-    const int64_t elems = (int64_t)ntiles * BM * BK;
-    if (elems <= 0) return CQ_EINVAL;
-    k_toeplitz_bank<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(d, nw, delta0, ntiles, hi, lo);
+    if (ntiles <= 0) return CQ_EINVAL;
+    if (kind == TC_TF32X3) launch_bank<TC_TF32X3>(d, nw, delta0, ntiles, hi, lo, s);
+    else launch_bank<TC_BF16X3>(d, nw, delta0, ntiles, hi, lo, s);
     return launched();
 }
 
-int tc_map_bank(CUtensorMap *m, const __nv_bfloat16 *bank, int ntiles) {
+int tc_map_bank(int kind, CUtensorMap *m, const void *bank, int ntiles) {
     using namespace tc;
-    return make_map(m, bank, BK, (uint64_t)ntiles * BM, BK, BM);
+    const int bk = kind_bk(kind);
+    return make_map(kind, m, bank, bk, (uint64_t)ntiles * BM, bk, BM);
 }
 
-int tc_map_levels(CUtensorMap *m, const __nv_bfloat16 *levels, int64_t kpad, int64_t rows) {
+int tc_map_levels(int kind, CUtensorMap *m, const void *levels, int64_t kpad, int64_t rows) {
     using namespace tc;
-    if (kpad % BK) return CQ_EINVAL;
-    return make_map(m, levels, (uint64_t)kpad, (uint64_t)rows, (uint64_t)kpad, BN);
+    if (kpad % 64) return CQ_EINVAL;
+    return make_map(kind, m, levels, (uint64_t)kpad, (uint64_t)rows, (uint64_t)kpad, BN);
 }
 
-int tc_contract_f32(const tc::TcMaps &maps, const tc::TcParams &P, float *H, int *status, cudaStream_t s) {
+int tc_contract_f32(int kind, const tc::TcMaps &maps, const tc::TcParams &P, float *H, int *status, cudaStream_t s) {
     using namespace tc;
     const int64_t blocks = P.ntile_state * P.n_states * P.num_i;
     if (blocks <= 0 || blocks > 0x7fffffffLL) return CQ_EUNSUPPORTED;
     int st;
     if ((st = tc_attr())) return st;
-    k_history_tc_bf16x3<float><<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(maps, P, H, status);
+    if (kind == TC_TF32X3)
+        k_history_tc<float, TC_TF32X3><<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(maps, P, H, status);
+    else
+        k_history_tc<float, TC_BF16X3><<<(unsigned)blocks, THREADS, SMEM_BYTES, s>>>(maps, P, H, status);
     return launched();
 }
 

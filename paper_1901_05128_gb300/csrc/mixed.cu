@@ -1,10 +1,10 @@
-// Mixed-precision direct solve (precision form CQ_BF16X3 of the direct scheme).
+// Mixed-precision direct solve (precision forms CQ_BF16X3 and CQ_TF32X3 of the direct scheme).
 //
 // The direct history h^n = sum_{k=1}^{n-1} d_{n-k} g^k (Eq. 3.8) of all modes is
 // computed in time blocks of kMxB steps. For the block starting at n0 the part
 // from the levels of earlier blocks, sum_{k=1}^{n0-1} d_{n-k} g^k, is one causal
-// Toeplitz contraction on the tensor cores (history_tc.cu: tcgen05, split BF16
-// operands, FP32 accumulation), with a separate weight bank per state; the rest,
+// Toeplitz contraction on the tensor cores (history_tc.cu: tcgen05, split BF16 or
+// TF32 operands, FP32 accumulation), with a separate weight bank per state; the rest,
 // from the levels n0 .. n-1 of the block itself, is formed step by step in FP32
 // by the kernel that also takes the steps (Eq. 4.1 / Eq. 4.7 in the sine basis).
 // A step is evaluated from the FP32 history sums in the two-term form
@@ -31,32 +31,34 @@ constexpr int kMxWOff = 7;                 // weight table: entry i holds d_{i -
 constexpr int kMxW = kMxB + 2 * kMxSB;     // entries per state (d_{-7} .. d_{kMxB + 8})
 
 struct MixedLayout {
-    __nv_bfloat16 *a_hi[2], *a_lo[2];   // Toeplitz banks of d^1 and d^2
-    __nv_bfloat16 *gt_hi, *gt_lo;       // levels, K-major: row s * nmp + mode, column k - 1
+    char *a_hi[2], *a_lo[2];            // Toeplitz banks of d^1 and d^2
+    char *gt_hi, *gt_lo;                // levels (BF16 or TF32 hi / lo), K-major: row s * nmp + mode, column k - 1
     float *acc;                         // contraction output [kMxB][2 * nmp]
     float *carry;                       // g^{n-1}, g^{n-2} at the end of a block: [2][2 * nmp]
     float4 *coef;                       // per lane: A row, B row (double-float), (scaled g^0, exponent)
-    int nblk, ntiles;
+    int kind, nblk, ntiles;
     int64_t nmp, kpad;
     size_t bytes;
 };
 
 static MixedLayout mixed_layout(const Fp2sParams &P, void *base) {
     MixedLayout l{};
+    l.kind = P.prec == CQ_TF32X3 ? tc::TC_TF32X3 : tc::TC_BF16X3;
+    const int bk = tc::kind_bk(l.kind), es = tc::kind_esize(l.kind);
     l.nmp = (P.nmodes + 3) / 4 * 4;
     l.nblk = (int)((P.N + kMxB - 1) / kMxB);
     const int64_t klev = (int64_t)(l.nblk - 1) * kMxB;          // levels ever contracted
-    l.kpad = klev > 0 ? klev : tc::BK;
-    l.ntiles = klev > 0 ? (int)(klev / tc::BK) : 1;
+    l.kpad = klev > 0 ? klev : 64;
+    l.ntiles = klev > 0 ? (int)(klev / bk) : 1;
     Carve cv(base);
-    const size_t bank = (size_t)l.ntiles * tc::BM * tc::BK;
+    const size_t bank = (size_t)l.ntiles * tc::BM * bk * es;
     for (int s = 0; s < 2; ++s) {
-        l.a_hi[s] = cv.take<__nv_bfloat16>(bank);
-        l.a_lo[s] = cv.take<__nv_bfloat16>(bank);
+        l.a_hi[s] = cv.take<char>(bank);
+        l.a_lo[s] = cv.take<char>(bank);
     }
     const size_t lev = l.nblk > 1 ? (size_t)2 * l.nmp * l.kpad : 0;
-    l.gt_hi = cv.take<__nv_bfloat16>(lev);
-    l.gt_lo = cv.take<__nv_bfloat16>(lev);
+    l.gt_hi = cv.take<char>(lev * es);
+    l.gt_lo = cv.take<char>(lev * es);
     l.acc = cv.take<float>(l.nblk > 1 ? (size_t)kMxB * 2 * l.nmp : 0);
     l.carry = cv.take<float>((size_t)4 * l.nmp);
     l.coef = cv.take<float4>((size_t)6 * l.nmp);
@@ -69,12 +71,12 @@ size_t mixed_direct_bytes(const Fp2sParams &P) { return mixed_layout(P, nullptr)
 struct MixedArgs {
     Fp2sParams P;
     int64_t nmp, n0, kpad;
-    int solve64, write_levels;
+    int solve64, write_levels, kind;
     const double *lam, *g0, *d1, *d2;
     const float *hdf, *acc;
     float *carry;
     float4 *coef;
-    __nv_bfloat16 *gt_hi, *gt_lo;
+    char *gt_hi, *gt_lo;
     double *gN;
     int *status;
 };
@@ -85,6 +87,18 @@ __device__ __forceinline__ void split_f32(float x, uint32_t &h, uint32_t &l) {
     const __nv_bfloat16 lb = __float2bfloat16_rn(x - __bfloat162float(hb));
     h = __bfloat16_as_ushort(hb);
     l = __bfloat16_as_ushort(lb);
+}
+
+// x (finite) rounded to 11 significant bits, nearest-even: the TF32 value in FP32 bits.
+__device__ __forceinline__ uint32_t rn_tf32_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0xfffu + ((u >> 13) & 1u)) & 0xffffe000u;
+}
+
+// TF32 hi + lo of an FP32 value (x - hi is exact in FP32).
+__device__ __forceinline__ void split_f32_tf32(float x, uint32_t &h, uint32_t &l) {
+    h = rn_tf32_bits(x);
+    l = rn_tf32_bits(x - __uint_as_float(h));
 }
 
 // Steps n0 .. min(n0 + kMxB - 1, N) of 64 modes per CTA. Lanes l < 16 of a warp
@@ -224,15 +238,30 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     }
     if (!active) return;
     if (A.write_levels) {
-        // level n0 + j goes to column n0 + j - 1 of row col; 16 levels = two 16-byte stores per array
-        uint4 *dh = reinterpret_cast<uint4 *>(A.gt_hi + col * A.kpad + (A.n0 - 1));
-        uint4 *dl = reinterpret_cast<uint4 *>(A.gt_lo + col * A.kpad + (A.n0 - 1));
-        for (int j = 0; j < kMxB; j += 8) {
-            uint32_t h[8], l[8];
+        // level n0 + j goes to column n0 + j - 1 of row col, as 16-byte stores per array
+        const int64_t o = col * A.kpad + (A.n0 - 1);
+        if (A.kind == tc::TC_TF32X3) {
+            uint4 *dh = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(A.gt_hi) + o);
+            uint4 *dl = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(A.gt_lo) + o);
+            for (int j = 0; j < kMxB; j += 4) {
+                uint32_t h[4], l[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) split_f32(xc[((j + i) / 4) * 4 * kMxT + (j + i) % 4], h[i], l[i]);
-            dh[j / 8] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-            dl[j / 8] = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16), l[6] | (l[7] << 16));
+                for (int i = 0; i < 4; ++i) split_f32_tf32(xc[(j / 4) * 4 * kMxT + i], h[i], l[i]);
+                dh[j / 4] = make_uint4(h[0], h[1], h[2], h[3]);
+                dl[j / 4] = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+        } else {
+            uint4 *dh = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(A.gt_hi) + o);
+            uint4 *dl = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(A.gt_lo) + o);
+            for (int j = 0; j < kMxB; j += 8) {
+                uint32_t h[8], l[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) split_f32(xc[((j + i) / 4) * 4 * kMxT + (j + i) % 4], h[i], l[i]);
+                dh[j / 8] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                                       h[6] | (h[7] << 16));
+                dl[j / 8] = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16),
+                                       l[6] | (l[7] << 16));
+            }
         }
         A.carry[col] = gm1;
         A.carry[2 * A.nmp + col] = gm2;
@@ -253,12 +282,12 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
     if (l.nblk > 1) {
         const double *d[2] = {d1, d2};
         for (int q = 0; q < 2; ++q) {
-            if ((st = tc_bank(d[q], P.N, tc::BK, l.ntiles, l.a_hi[q], l.a_lo[q], s))) return st;
-            if ((st = tc_map_bank(&maps.a_hi[q], l.a_hi[q], l.ntiles))) return st;
-            if ((st = tc_map_bank(&maps.a_lo[q], l.a_lo[q], l.ntiles))) return st;
+            if ((st = tc_bank(l.kind, d[q], P.N, tc::kind_bk(l.kind), l.ntiles, l.a_hi[q], l.a_lo[q], s))) return st;
+            if ((st = tc_map_bank(l.kind, &maps.a_hi[q], l.a_hi[q], l.ntiles))) return st;
+            if ((st = tc_map_bank(l.kind, &maps.a_lo[q], l.a_lo[q], l.ntiles))) return st;
         }
-        if ((st = tc_map_levels(&maps.b_hi, l.gt_hi, l.kpad, 2 * l.nmp))) return st;
-        if ((st = tc_map_levels(&maps.b_lo, l.gt_lo, l.kpad, 2 * l.nmp))) return st;
+        if ((st = tc_map_levels(l.kind, &maps.b_hi, l.gt_hi, l.kpad, 2 * l.nmp))) return st;
+        if ((st = tc_map_levels(l.kind, &maps.b_lo, l.gt_lo, l.kpad, 2 * l.nmp))) return st;
     }
     static bool attr = false;
     if (!attr) {
@@ -272,6 +301,7 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
     A.nmp = l.nmp;
     A.kpad = l.kpad;
     A.solve64 = fabs(P.a) > 10.0;
+    A.kind = l.kind;
     A.lam = lam;
     A.g0 = g0;
     A.d1 = d1;
@@ -290,7 +320,7 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
     T.ldh = 2 * l.nmp;
     T.vec2 = 1;                         // ldh and the state offset are multiples of 4 floats
     T.num_i = 1;
-    T.delta0 = tc::BK;
+    T.delta0 = tc::kind_bk(l.kind);
     T.n_states = 2;
     T.ntile_state = (P.nmodes + tc::BN - 1) / tc::BN;
     T.state_stride = l.nmp;
@@ -301,7 +331,7 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
             T.rows = min((int64_t)kMxB, P.N - n0 + 1);
             T.kprime = (int)(n0 - 1);
             if ((st = timing_part(s, false))) return st;
-            if ((st = tc_contract_f32(maps, T, l.acc, status, s))) return st;
+            if ((st = tc_contract_f32(l.kind, maps, T, l.acc, status, s))) return st;
             if ((st = timing_part(s, true))) return st;
         }
         A.n0 = n0;

@@ -13,7 +13,14 @@ namespace tc {
 
 constexpr int BM = 128;                     // steps per tile (UMMA M)
 constexpr int BN = 256;                     // DOFs per tile (UMMA N)
-constexpr int BK = 64;                      // levels per stage (one 128-byte swizzle row of BF16)
+
+// Operand forms: BF16 hi + lo (kind::f16) or TF32 hi + lo (kind::tf32, FP32 containers
+// with the 13 low mantissa bits zero). A stage holds one 128-byte swizzle row per
+// operand row: 64 BF16 or 32 TF32 levels.
+enum : int { TC_BF16X3 = 0, TC_TF32X3 = 1 };
+__host__ __device__ constexpr int kind_bk(int kind) { return kind == TC_TF32X3 ? 32 : 64; }
+__host__ __device__ constexpr int kind_esize(int kind) { return kind == TC_TF32X3 ? 4 : 2; }
+constexpr int BK = 64;                      // BF16 levels per stage (kind_bk(TC_BF16X3))
 
 // Output rows are steps m in [n_lo, n_lo + rows); row m, column j of state s is
 //   sum over levels k = 1 .. kprime of  d^s_{m-k} * G[s * state_stride + j][k - 1]
@@ -37,14 +44,14 @@ struct TcMaps {
 }  // namespace tc
 
 // Bank of Toeplitz tiles of the weights d_1..d_nw (index 0 and > nw read as 0):
-// tile t, row r, column c = d_{delta0 + 64 t + r - c}, split into BF16 hi + lo.
-int tc_bank(const double *d, int64_t nw, int64_t delta0, int ntiles, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-            cudaStream_t s);
+// tile t, row r, column c = d_{delta0 + BK t + r - c} (BK = kind_bk(kind)), split into
+// hi + lo of the kind's element type (128 x BK elements per tile).
+int tc_bank(int kind, const double *d, int64_t nw, int64_t delta0, int ntiles, void *hi, void *lo, cudaStream_t s);
 // Tensor map of a bank of ntiles tiles.
-int tc_map_bank(CUtensorMap *m, const __nv_bfloat16 *bank, int ntiles);
+int tc_map_bank(int kind, CUtensorMap *m, const void *bank, int ntiles);
 // Tensor map of K-major levels [rows][kpad] (kpad a multiple of 64).
-int tc_map_levels(CUtensorMap *m, const __nv_bfloat16 *levels, int64_t kpad, int64_t rows);
+int tc_map_levels(int kind, CUtensorMap *m, const void *levels, int64_t kpad, int64_t rows);
 // Launch the contraction with FP32 output (timeouts recorded in *status).
-int tc_contract_f32(const tc::TcMaps &maps, const tc::TcParams &P, float *H, int *status, cudaStream_t s);
+int tc_contract_f32(int kind, const tc::TcMaps &maps, const tc::TcParams &P, float *H, int *status, cudaStream_t s);
 
 }  // namespace fastcq

@@ -25,7 +25,7 @@ def main(argv=None):
     ap.add_argument("--N", type=int, default=None, help="override the number of steps")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--scale-exp", type=int, default=-1000, help="G0 is multiplied by 2**scale_exp")
-    ap.add_argument("--prec", choices=["f64", "f32", "bf16x3"], default="f64")
+    ap.add_argument("--prec", choices=["f64", "f32", "bf16x3", "tf32x3"], default="f64")
     ap.add_argument("--history", action="store_true",
                     help="run cq_history_direct alone on synthetic N(0,1) levels (--ndof, --n-lo, --n-hi)")
     ap.add_argument("--ndof", type=int, default=65536)
@@ -49,7 +49,7 @@ def main(argv=None):
         p = p.replace(scheme=ci.BE if a.scheme == "be" else ci.BDF2)
     if a.N:
         p = p.replace(N=a.N, T=p.T * a.N / p.N)
-    prec = {"f64": fc.CQ_F64, "f32": fc.CQ_F32, "bf16x3": fc.CQ_BF16X3}[a.prec]
+    prec = {"f64": fc.CQ_F64, "f32": fc.CQ_F32, "bf16x3": fc.CQ_BF16X3, "tf32x3": fc.CQ_TF32X3}[a.prec]
     cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
                     prec=prec)
     g0 = torch.tensor(G0 * 2.0 ** a.scale_exp, dtype=torch.float64, device="cuda")
@@ -68,9 +68,9 @@ def main(argv=None):
 def run_history(fc, torch, a):
     """Direct history of synthetic levels: prints call and main-kernel times."""
     import cq_inputs as ci
-    prec = {"f64": fc.CQ_F64, "bf16x3": fc.CQ_BF16X3}.get(a.prec)
+    prec = {"f64": fc.CQ_F64, "bf16x3": fc.CQ_BF16X3, "tf32x3": fc.CQ_TF32X3}.get(a.prec)
     if prec is None:
-        raise SystemExit("--history supports --prec f64 or bf16x3")
+        raise SystemExit("--history supports --prec f64, bf16x3 or tf32x3")
     ndof, n_lo, n_hi = a.ndof, a.n_lo, a.n_hi
     beta, tau = 0.8, 1.0 / max(n_hi - 1, 1)
     gen = torch.Generator(device="cuda")
@@ -84,7 +84,7 @@ def run_history(fc, torch, a):
         t = time.perf_counter()
         fc.cq_history_direct(1, beta, tau, ndof, n_lo, n_hi, G, ndof, H, ndof, ws, prec=prec)
         torch.cuda.synchronize()
-        k = fc.cq_timing_last() if prec == fc.CQ_BF16X3 else float("nan")
+        k = fc.cq_timing_last() if prec in (fc.CQ_BF16X3, fc.CQ_TF32X3) else float("nan")
         print("history %d: %.3f ms (main kernel %.3f ms)" % (r, (time.perf_counter() - t) * 1e3, k))
 
 

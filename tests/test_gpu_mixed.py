@@ -73,6 +73,18 @@ def test_direct_mixed_against_fp64_oracle(fc, name, p, sc):
     assert max(errs) <= 1e-4
 
 
+@pytest.mark.parametrize("name,p,sc", MIXED_CASES[:6], ids=[c[0] for c in MIXED_CASES[:6]])
+def test_direct_mixed_tf32x3_against_fp64_oracle(fc, name, p, sc):
+    """The TF32x3 contraction in the same block algorithm: same bound (the FP32 in-block
+    sums and levels set the error level)."""
+    G0 = ci.g0_uniform(p.M, p.dim, 23) * 2.0 ** sc
+    got, st = _solve(fc, p, G0, fc.CQ_TF32X3)
+    assert st == fc.CQ_OK
+    errs = _rel(got, OS.solve(p, G0))
+    print("mixed direct tf32x3 %s rel L2 errors %.3e %.3e" % (name, errs[0], errs[1]))
+    assert max(errs) <= 1e-4
+
+
 def test_direct_mixed_every_step_count(fc):
     """Final states of the mixed solve for every N in 1..40 and around the block edges
     (each N is its own problem, tau = T / N), against the oracle."""

@@ -95,3 +95,54 @@ def test_bf16x3_history_full_size_sampled(fc):
     err = np.abs(Hc - ref)
     print("bf16x3 full size: max |err| / sum|d||G| = %.3e" % float(np.max(err / scale)))
     assert np.all(err <= _bound(n_hi) * scale)
+
+
+def _bound_tf32(K):
+    """TF32x3: each split operand keeps 22 bits (<= 2^-22 relative) and the dropped lo*lo
+    term is <= 2^-22, so the products carry <= 4 * 2^-22; the accumulator rounds toward
+    zero once per K = 8 instruction and product within a 128-level chunk (48 roundings,
+    <= 2^-23 each, relative to the chunk's sum of |terms|), and the chunks are summed in
+    FP32 with round-to-nearest (<= ceil(K / 128) roundings of 2^-24)."""
+    return 4 * 2.0 ** -22 + 48 * 2.0 ** -23 + (-(-K // 128)) * 2.0 ** -24
+
+
+def _run_history(fc, prec, scheme, beta, tau, G, ndof, n_lo, n_hi, ld):
+    Gd = torch.tensor(G, dtype=torch.float64, device="cuda")
+    H = torch.full((n_hi - n_lo, ld), np.nan, dtype=torch.float64, device="cuda")
+    ws = fc.workspace(fc.cq_history_direct(scheme, beta, tau, ndof, n_lo, n_hi, None, ld, None, ld, prec=prec), "cuda")
+    fc.cq_history_direct(scheme, beta, tau, ndof, n_lo, n_hi, Gd, ld, H, ld, ws, prec=prec)
+    torch.cuda.synchronize()
+    return H.cpu().numpy()
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("ndof,n_lo,n_hi,ld_extra", CASES)
+def test_tf32x3_history_small(fc, scheme, ndof, n_lo, n_hi, ld_extra):
+    beta, tau = 0.45, 1.0 / 700
+    ld = ndof + ld_extra
+    G = np.zeros((n_hi, ld))
+    G[:, :ndof] = ci.rng(41).standard_normal((n_hi, ndof))
+    got = _run_history(fc, fc.CQ_TF32X3, scheme, beta, tau, G, ndof, n_lo, n_hi, ld)
+    d = OW.weights(scheme, beta, tau, n_hi)
+    ref = OH.history_direct_all(d, G[:, :ndof], n_lo, n_hi)
+    scale = np.stack([_abs_scale(d, G[:, :ndof], n) for n in range(n_lo, n_hi)])
+    err = np.abs(got[:, :ndof] - ref)
+    ratio = float(np.max(err / (scale + 1e-300)))
+    print("tf32x3 ndof=%d rows=[%d,%d): max |err| / sum|d||G| = %.3e (bound %.3e)"
+          % (ndof, n_lo, n_hi, ratio, _bound_tf32(n_hi)))
+    assert np.all(err <= _bound_tf32(n_hi) * scale + 1e-300)
+    if ld_extra:
+        assert np.all(np.isnan(got[:, ndof:]))
+
+
+def test_tf32x3_more_accurate_than_bf16x3(fc):
+    """Same data through both forms: the TF32 split error is 2^6 times smaller, so the
+    TF32x3 history is at least 8x closer to the FP64 oracle in the max norm."""
+    ndof, n_lo, n_hi, beta, tau = 1500, 1, 900, 0.7, 1.0 / 900
+    G = ci.rng(43).standard_normal((n_hi, ndof))
+    d = OW.weights(1, beta, tau, n_hi)
+    ref = OH.history_direct_all(d, G, n_lo, n_hi)
+    e_b = np.max(np.abs(_run_history(fc, fc.CQ_BF16X3, 1, beta, tau, G, ndof, n_lo, n_hi, ndof) - ref))
+    e_t = np.max(np.abs(_run_history(fc, fc.CQ_TF32X3, 1, beta, tau, G, ndof, n_lo, n_hi, ndof) - ref))
+    print("max error: bf16x3 %.3e, tf32x3 %.3e" % (e_b, e_t))
+    assert e_t * 8 <= e_b
