@@ -167,6 +167,27 @@ def precision_leg(fc, torch, dev, K, W, flush):
     out["tc_H"] = H[:, ci_t].cpu().numpy()
     out["tc_call_ms"], out["tc_gemm_ms"] = calls, gemms
     out["tc_beta"], out["tc_tau"], out["tc_nhi"] = beta, tau, n_hi
+    # the same contraction in the TF32x3 form
+    del ws
+    torch.cuda.empty_cache()
+    ws = fc.workspace(fc.cq_history_direct(ci.BE, beta, tau, ndof, 1, n_hi, None, ndof, None, ndof,
+                                           prec=fc.CQ_TF32X3), dev)
+    for _ in range(W):
+        fc.cq_history_direct(ci.BE, beta, tau, ndof, 1, n_hi, G, ndof, H, ndof, ws, prec=fc.CQ_TF32X3)
+    torch.cuda.synchronize()
+    tcalls, tgemms = [], []
+    for _ in range(max(3, K // 3)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fc.cq_history_direct(ci.BE, beta, tau, ndof, 1, n_hi, G, ndof, H, ndof, ws, prec=fc.CQ_TF32X3)
+        e1.record()
+        e1.synchronize()
+        tcalls.append(e0.elapsed_time(e1))
+        tgemms.append(fc.cq_timing_last())
+    out["tf32_H"] = H[:, ci_t].cpu().numpy()
+    out["tf32_call_ms"], out["tf32_gemm_ms"] = tcalls, tgemms
     del G, H, ws
     torch.cuda.empty_cache()
     # FP32 fast solve of the same grid
@@ -206,37 +227,43 @@ MIXED_ALPHAS = ((0.2, 0.8), (0.8, 0.2), (0.2, 0.2), (0.8, 0.8))
 def mixed_direct_leg(fc, torch, dev, p, G0, K, W, flush):
     """Mixed-precision direct solve (tensor-core BF16x3 history, FP32 in-block sums and
     steps) of the 2D 511x511, N = 8192 grid for BE and BDF2 and every (alpha1, alpha2) in
-    {0.2, 0.8}^2. The first case (BE, alpha = (0.2, 0.8)) is timed K times; the others once."""
+    {0.2, 0.8}^2, and the BE (0.2, 0.8) case with the TF32x3 contraction. The first case
+    (BE, alpha = (0.2, 0.8), BF16x3) is timed K times; the others once."""
     import cq_inputs as ci
     runs = []
     g0 = torch.tensor(G0, dtype=torch.float64, device=dev)
     gN = torch.empty_like(g0)
     ws = None
-    for scheme in (ci.BE, ci.BDF2):
-        for al in MIXED_ALPHAS:
-            q = p.replace(form=ci.DIRECT, scheme=scheme, alpha1=al[0], alpha2=al[1])
-            cp = fc.problem(q.alpha1, q.alpha2, q.m, q.T, q.N, q.dim, q.M, q.scheme, q.form, 0, 0, 0,
-                            prec=fc.CQ_BF16X3, flags=fc.FP2S_ASYNC)
-            if ws is None:
-                ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
-            main = not runs
-            for _ in range(W if main else 1):
-                fc.fp2s_solve(cp, g0, gN, ws)
-            torch.cuda.synchronize()
-            l0 = fc.cq_launch_count()
-            ms, tc_ms = [], []
-            for _ in range(K if main else 1):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                fc.fp2s_solve(cp, g0, gN, ws)
-                e1.record()
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-                tc_ms.append(fc.cq_timing_part(1))
-            runs.append({"problem": q, "ms": ms, "tc_ms": tc_ms, "status": fc.strerror(fc.fp2s_status(cp, ws)),
-                         "launches": (fc.cq_launch_count() - l0) / len(ms), "gN": gN.cpu().numpy()})
+    cases = [(scheme, al, fc.CQ_BF16X3) for scheme in (ci.BE, ci.BDF2) for al in MIXED_ALPHAS]
+    cases.append((ci.BE, MIXED_ALPHAS[0], fc.CQ_TF32X3))
+    for scheme, al, prec in cases:
+        q = p.replace(form=ci.DIRECT, scheme=scheme, alpha1=al[0], alpha2=al[1])
+        cp = fc.problem(q.alpha1, q.alpha2, q.m, q.T, q.N, q.dim, q.M, q.scheme, q.form, 0, 0, 0,
+                        prec=prec, flags=fc.FP2S_ASYNC)
+        if prec == fc.CQ_TF32X3:          # twice the level bytes: a larger workspace
+            ws = None
+            torch.cuda.empty_cache()
+        if ws is None:
+            ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
+        main = not runs
+        for _ in range(W if main else 1):
+            fc.fp2s_solve(cp, g0, gN, ws)
+        torch.cuda.synchronize()
+        l0 = fc.cq_launch_count()
+        ms, tc_ms = [], []
+        for _ in range(K if main else 1):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fc.fp2s_solve(cp, g0, gN, ws)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            tc_ms.append(fc.cq_timing_part(1))
+        runs.append({"problem": q, "prec": "tf32x3" if prec == fc.CQ_TF32X3 else "bf16x3", "ms": ms,
+                     "tc_ms": tc_ms, "status": fc.strerror(fc.fp2s_status(cp, ws)),
+                     "launches": (fc.cq_launch_count() - l0) / len(ms), "gN": gN.cpu().numpy()})
     del ws, g0, gN
     torch.cuda.empty_cache()
     return runs
@@ -284,6 +311,23 @@ def precision_report(leg, cpu_modes):
                          "sample": "oracle direct history of %d DOF columns x %d steps (%.1f s)"
                                    % (PREC_COLS, rows, t_orc)},
     }
+    tf_gemm = statistics.mean(leg["tf32_gemm_ms"])
+    tf32_peak = bf16_peak * 1.1 / 2.25            # nominal TF32 : BF16 dense ratio
+    tf_err = float(np.max(np.abs(leg["tf32_H"] - ref) / (scale + 1e-300)))
+    tf32 = {
+        "workload": tc["workload"],
+        "precision": "TF32x3 (hi*hi + hi*lo + lo*hi, 11-bit parts), FP32 accumulation per 128-level chunk, "
+                     "FP64 output",
+        "value": ndof * rows / (statistics.mean(leg["tf32_call_ms"]) * 1e-3), "unit": UNIT,
+        "ms_per_call": statistics.mean(leg["tf32_call_ms"]),
+        "roofline": {"kernel": "k_history_tc<double, TF32X3>", "bound": "tensor", "unit": "TFLOP/s",
+                     "achieved": useful / (tf_gemm * 1e-3) / 1e12, "peak": tf32_peak,
+                     "frac": useful / (tf_gemm * 1e-3) / 1e12 / tf32_peak,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio 1.1/2.25",
+                     "kernel_ms": tf_gemm},
+        "error_vs_oracle": {"max_abs_err_over_sum_abs_terms": tf_err,
+                            "sample": "%d whole DOF columns x %d steps" % (PREC_COLS, rows)},
+    }
     # FP32 fast solve: oracle FP64 fast scheme on sampled modes
     from oracle import scheme as OS
     q, G0 = leg["f32_problem"], leg["G0"]
@@ -313,7 +357,7 @@ def precision_report(leg, cpu_modes):
                          "sample": "oracle FP64 fast BE scheme, %d modes x %d steps (%.1f s)"
                                    % (len(sample), q.N, t_f)},
     }
-    return {"tensor_core_direct_history": tc, "fp32_fast_solve": f32,
+    return {"tensor_core_direct_history": tc, "tensor_core_direct_history_tf32x3": tf32, "fp32_fast_solve": f32,
             "mixed_direct_solve": mixed_report(leg["mixed"], G0, cpu_modes)}
 
 
@@ -340,6 +384,7 @@ def mixed_report(runs, G0, cpu_modes):
         gm = OSP.to_modal(r["gN"], q.M, q.dim)[:, sample]
         err = [float(np.linalg.norm(gm[s] - ref[s]) / np.linalg.norm(ref[s])) for s in range(2)]
         cases.append({"scheme": "BE" if q.scheme == ci.BE else "BDF2", "alpha": [q.alpha1, q.alpha2],
+                      "contraction": r["prec"],
                       "ms": statistics.mean(r["ms"]), "status": r["status"],
                       "rel_l2_err_vs_fp64_oracle": err})
     main = runs[0]
