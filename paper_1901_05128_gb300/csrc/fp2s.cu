@@ -220,6 +220,120 @@ __global__ void __launch_bounds__(1024) k_fp2s_fast(Fp2sParams P, const double *
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused fast solve for problems with few modes (1D grids, small 2D grids): one
+// warp per mode, lanes l < 16 state 1 and l + 16 state 2 as above, and the
+// history nodes of a state split over its 16 lanes (node j on lane j % 16), so
+// a lane keeps only its NPL states Y_j and table entries in registers. The
+// partial sums meet through xor shuffles inside the half-warp; every lane then
+// takes the step itself and lane 0 of each half stores the new level into the
+// warp's ring of the last L levels in shared memory.
+// ---------------------------------------------------------------------------
+template <int NPL>
+__global__ void __launch_bounds__(32) k_fp2s_fast_split(Fp2sParams P, const double *__restrict__ lam,
+                                                        const double *__restrict__ g0, double *__restrict__ gN,
+                                                        int *__restrict__ status, const double *__restrict__ d1,
+                                                        const double *__restrict__ d2,
+                                                        const double *__restrict__ tab1,
+                                                        const double *__restrict__ tab2) {
+    __shared__ double ring[2][kMaxNs];
+    const int lane = threadIdx.x, st = lane >> 4, sub = lane & 15;
+    const int64_t mode = blockIdx.x;
+    const int np = P.np, L = P.L;
+    const double *tab = st ? tab2 : tab1;
+    double Y[NPL], r[NPL], c[NPL];
+#pragma unroll
+    for (int q = 0; q < NPL; ++q) {
+        const int j = sub + 16 * q;
+        r[q] = j < np ? tab[j] : 0.0;
+        c[q] = j < np ? tab[np + j] : 0.0;
+        Y[q] = 0.0;
+    }
+    for (int i = lane; i < 2 * kMaxNs; i += 32) ring[i / kMaxNs][i % kMaxNs] = 0.0;
+    __syncwarp();
+    double *rs = ring[st];
+    const double *dn = st ? d2 : d1;
+
+    const double gz = g0[st * P.nmodes + mode];
+    const double d_s0 = __ldg(dn), d_o0 = __ldg(st ? d1 : d2);
+    ModeConst mc;
+    const bool ok = mode_setup(P, lam[mode], st ? d_o0 : d_s0, st ? d_s0 : d_o0, mc);
+    if (lane == 0 && !ok) atomicOr(status, ST_SINGULAR);
+    const double mn_oo = st ? mc.Mn.i22 : mc.Mn.i11, mn_ot = st ? mc.Mn.i21 : mc.Mn.i12;
+    const double m1_oo = st ? mc.M1.i22 : mc.M1.i11, m1_ot = st ? mc.M1.i21 : mc.M1.i12;
+    const double a = P.a, cc = mc.c;
+    double gm1 = gz, gm2 = 0.0;
+    int slot = 0;
+    for (int64_t n = 1; n <= P.N; ++n) {
+        slot = (slot + 1 == L) ? 0 : slot + 1;
+        double ha = 0.0, hb = 0.0;
+        if (n - L >= 1) {
+            const double in = rs[slot];
+#pragma unroll
+            for (int q = 0; q < NPL; q += 2) {
+                Y[q] = fma(r[q], Y[q], in);
+                ha = fma(c[q], Y[q], ha);
+                if (q + 1 < NPL) {
+                    Y[q + 1] = fma(r[q + 1], Y[q + 1], in);
+                    hb = fma(c[q + 1], Y[q + 1], hb);
+                }
+            }
+        }
+        const int imax = (int)min((int64_t)(L - 1), n - 1);
+        for (int i = 1 + sub; i <= imax; i += 16) {         // this lane's terms of the exact window
+            const int sl = (slot - i + L) % L;                // slot of level n - i
+            ha = fma(__ldg(dn + i), rs[sl], ha);
+        }
+        double h = ha + hb;
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) h += __shfl_xor_sync(0xffffffffu, h, off);
+        double e, lead, m_oo = mn_oo, m_ot = mn_ot;
+        if (P.scheme == CQ_BE) {
+            e = h;
+            lead = gm1 * P.inv_tau;
+        } else if (n == 1) {
+            e = d_s0 * gz * (1.0 / 3.0);
+            lead = gz * P.inv_tau;
+            m_oo = m1_oo;
+            m_ot = m1_ot;
+        } else {
+            e = fma(0.5 * __ldg(dn + n - 1), gz, h);
+            lead = (2.0 * gm1 - 0.5 * gm2) * P.inv_tau;
+        }
+        const double e_o = __shfl_xor_sync(0xffffffffu, e, 16);
+        const double b = lead - cc * e + a * e_o;
+        const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
+        const double x = m_oo * b + m_ot * b_o;
+        __syncwarp();                                         // every lane has read the slot's old level
+        if (sub == 0) rs[slot] = x;
+        __syncwarp();
+        gm2 = gm1;
+        gm1 = x;
+    }
+    if (sub == 0) {
+        gN[st * P.nmodes + mode] = gm1;
+        if (!isfinite(gm1)) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+// Modes below which the fast solve gives each mode a whole warp (fewer than four
+// warps per SM with 16 modes per warp).
+static bool fast_use_split(int64_t nmodes) { return nmodes < (int64_t)152 * 4 * kFastModesPerWarp; }
+
+static int launch_fast_split(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
+    const int npl = (P.np + 15) / 16;
+    const unsigned grid = (unsigned)P.nmodes;
+#define CQ_FAST_SPLIT(NPLV) \
+    k_fp2s_fast_split<NPLV><<<grid, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2)
+    if (npl <= 2) CQ_FAST_SPLIT(2);
+    else if (npl <= 4) CQ_FAST_SPLIT(4);
+    else if (npl <= 8) CQ_FAST_SPLIT(8);
+    else if (npl <= 16) CQ_FAST_SPLIT(16);
+    else return CQ_EUNSUPPORTED;
+#undef CQ_FAST_SPLIT
+    return CQ_OK;
+}
+
 static size_t fast_smem_bytes(int np, int L, int T) {
     return ((size_t)4 * np + 2 * kMaxNs + (size_t)(np + L) * T) * sizeof(double);
 }
@@ -774,6 +888,7 @@ static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2,
 // The single-launch solve kernels (fast FP64, fast FP32, direct FP64).
 static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
     if (P.form == CQ_FAST && P.prec == CQ_F32) return fp2s_fast_f32(P, l, s);
+    if (P.form == CQ_FAST && fast_use_split(P.nmodes)) return launch_fast_split(P, l, s);
     if (P.form == CQ_FAST) {
         const int T = fast_block_threads(P.np, P.L, P.nmodes);
         if (T == 0) return CQ_EUNSUPPORTED;
