@@ -298,7 +298,7 @@ def precision_report(leg, cpu_modes):
         "precision": "BF16x3 (hi*hi + hi*lo + lo*hi), FP32 accumulation, FP64 output",
         "value": ndof * rows / (call_ms * 1e-3), "unit": UNIT, "ms_per_call": call_ms,
         "gemm": {"value": ndof * rows / (gemm_ms * 1e-3), "ms": gemm_ms},
-        "roofline": {"kernel": "k_history_tc_bf16x3", "bound": "tensor", "unit": "TFLOP/s",
+        "roofline": {"kernel": "k_history_tc<double, BF16X3>", "bound": "tensor", "unit": "TFLOP/s",
                      "achieved": useful / (gemm_ms * 1e-3) / 1e12, "peak": bf16_peak,
                      "frac": useful / (gemm_ms * 1e-3) / 1e12 / bf16_peak,
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)",
@@ -404,7 +404,7 @@ def mixed_report(runs, G0, cpu_modes):
                      "sums, two-term FP32 step with a double-float amplification matrix",
         "value": q.ndof * q.N / (ms * 1e-3), "unit": UNIT, "ms_per_solve": ms,
         "gpu_launches_per_solve": main["launches"],
-        "roofline": {"kernel": "k_history_tc_bf16x3<float> (63 launches per solve)", "bound": "tensor",
+        "roofline": {"kernel": "k_history_tc<float, BF16X3> (63 launches per solve)", "bound": "tensor",
                      "unit": "TFLOP/s", "achieved": tc_flops / (tc_ms * 1e-3) / 1e12, "peak": bf16_peak,
                      "frac": tc_flops / (tc_ms * 1e-3) / 1e12 / bf16_peak, "contraction_ms": tc_ms,
                      "share_of_solve": tc_ms / ms,
