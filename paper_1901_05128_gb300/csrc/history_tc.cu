@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
     const int64_t m_last = min(m0 + BM - 1, P.n_lo + P.rows - 1);
     // levels k' < m_last - 1 contribute (k = k' + 1 <= m_last - 1)
     const int64_t k_end = min((int64_t)P.kprime, m_last - 1);
-    const int num_k = k_end > 0 ? (int)((k_end + BKK - 1) / BKK) : 0;
+    const int num_k = k_end > P.k_lo ? (int)((k_end - P.k_lo + BKK - 1) / BKK) : 0;
     const int nchunks = (num_k + CHUNK - 1) / CHUNK;
 
     if (threadIdx.x == 0) {
@@ -279,13 +279,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
             }
             if (*(volatile int *)abort_flag) break;
             unsigned char *st = smem + s * STAGE_BYTES;
-            const int64_t delta = m0 - 1 - (int64_t)ks * BKK;
+            const int kc = P.k_lo + ks * BKK;                 // first level column of the stage
+            const int64_t delta = m0 - 1 - (int64_t)kc;
             const int arow = (int)((delta - P.delta0) / BKK) * BM;
             mbar_expect_tx(&full[s], STAGE_BYTES);
             tma_load_2d(st, tA_hi, &full[s], 0, arow);
             tma_load_2d(st + A_BYTES, tA_lo, &full[s], 0, arow);
-            tma_load_2d(st + 2 * A_BYTES, tB_hi, &full[s], ks * BKK, (int)brow);
-            tma_load_2d(st + 2 * A_BYTES + B_BYTES, tB_lo, &full[s], ks * BKK, (int)brow);
+            tma_load_2d(st + 2 * A_BYTES, tB_hi, &full[s], kc, (int)brow);
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, tB_lo, &full[s], kc, (int)brow);
             armed[s] = ks;
         }
         if (*(volatile int *)abort_flag) {
@@ -582,6 +583,7 @@ int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, 
     P.num_i = (int)((P.rows + BM - 1) / BM);
     P.delta0 = l.delta0;
     P.kprime = kprime;
+    P.k_lo = 0;
     const int64_t num_n = (ndof + BN - 1) / BN;
     P.n_states = 1;
     P.ntile_state = num_n;

@@ -16,8 +16,10 @@
 // fast form, so its values sit near 1 in the FP32 / BF16 range; the contraction
 // is linear per mode, so the scaled levels give the scaled history.
 //
-// Per block: one contraction launch (blocks after the first) and one step
-// launch, which appends the block's levels to the K-major BF16 level matrix.
+// Per pair of blocks: one contraction over the earlier pairs' levels for the rows
+// of both blocks (two row tiles share each level tile), one short contraction of
+// the first block's levels for the second block's rows, and one step launch per
+// block, which appends the block's levels to the K-major level matrix.
 #include "common.cuh"
 #include "fp2s_core.cuh"
 #include "tc.cuh"
@@ -33,7 +35,8 @@ constexpr int kMxW = kMxB + 2 * kMxSB;     // entries per state (d_{-7} .. d_{kM
 struct MixedLayout {
     char *a_hi[2], *a_lo[2];            // Toeplitz banks of d^1 and d^2
     char *gt_hi, *gt_lo;                // levels (BF16 or TF32 hi / lo), K-major: row s * nmp + mode, column k - 1
-    float *acc;                         // contraction output [kMxB][2 * nmp]
+    float *acc2b;                       // contraction of two blocks' rows [2 kMxB][2 * nmp]
+    float *acc1b;                       // contraction of one block's rows [kMxB][2 * nmp]
     float *carry;                       // g^{n-1}, g^{n-2} at the end of a block: [2][2 * nmp]
     float4 *coef;                       // per lane: A row, B row (double-float), (scaled g^0, exponent)
     int kind, nblk, ntiles;
@@ -59,7 +62,8 @@ static MixedLayout mixed_layout(const Fp2sParams &P, void *base) {
     const size_t lev = l.nblk > 1 ? (size_t)2 * l.nmp * l.kpad : 0;
     l.gt_hi = cv.take<char>(lev * es);
     l.gt_lo = cv.take<char>(lev * es);
-    l.acc = cv.take<float>(l.nblk > 1 ? (size_t)kMxB * 2 * l.nmp : 0);
+    l.acc2b = cv.take<float>(l.nblk > 2 ? (size_t)2 * kMxB * 2 * l.nmp : 0);
+    l.acc1b = cv.take<float>(l.nblk > 1 ? (size_t)kMxB * 2 * l.nmp : 0);
     l.carry = cv.take<float>((size_t)4 * l.nmp);
     l.coef = cv.take<float4>((size_t)6 * l.nmp);
     l.bytes = cv.bytes();
@@ -73,7 +77,7 @@ struct MixedArgs {
     int64_t nmp, n0, kpad;
     int solve64, write_levels, kind;
     const double *lam, *g0, *d1, *d2;
-    const float *hdf, *acc;
+    const float *hdf, *acc, *acc2;      // contraction rows of this block (each optional), summed
     float *carry;
     float4 *coef;
     char *gt_hi, *gt_lo;
@@ -179,14 +183,18 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     const int jmax = (int)min((int64_t)kMxB, P.N - A.n0 + 1);      // steps in this block
     float an[kMxSB];                                 // acc rows of the next sub-block (prefetched)
 #pragma unroll
-    for (int b = 0; b < kMxSB; ++b) an[b] = A.acc ? A.acc[(int64_t)b * ldacc + col] : 0.0f;
+    for (int b = 0; b < kMxSB; ++b)
+        an[b] = (A.acc ? A.acc[(int64_t)b * ldacc + col] : 0.0f) + (A.acc2 ? A.acc2[(int64_t)b * ldacc + col] : 0.0f);
     for (int j0 = 0; j0 < jmax; j0 += kMxSB) {
         float a[kMxSB];
 #pragma unroll
         for (int b = 0; b < kMxSB; ++b) a[b] = an[b];
-        if (A.acc && j0 + kMxSB < jmax) {
+        if (j0 + kMxSB < jmax) {
 #pragma unroll
-            for (int b = 0; b < kMxSB; ++b) an[b] = A.acc[(int64_t)(j0 + kMxSB + b) * ldacc + col];
+            for (int b = 0; b < kMxSB; ++b) {
+                const int64_t o = (int64_t)(j0 + kMxSB + b) * ldacc + col;
+                an[b] = (A.acc ? A.acc[o] : 0.0f) + (A.acc2 ? A.acc2[o] : 0.0f);
+            }
         }
         // earlier in-block levels k in chunks of 8: a[b] += sum_kk d_{j0 + b - kc - kk} x^{n0 + kc + kk};
         // the 15 weights of a chunk are d_{m-7} .. d_{m+7}, m = j0 - kc (four 16-byte loads)
@@ -324,18 +332,37 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
     T.n_states = 2;
     T.ntile_state = (P.nmodes + tc::BN - 1) / tc::BN;
     T.state_stride = l.nmp;
+    // Blocks in pairs (2p, 2p+1). Once both earlier pairs' levels exist, one contraction
+    // covers the rows of both blocks over the levels of blocks < 2p (two row tiles per
+    // column tile: the level matrix is streamed once for 256 rows); block 2p+1 then adds
+    // the levels of block 2p with a short contraction (K = 128) of its own.
+    auto contract = [&](int64_t n_lo, int64_t rows, int64_t k_lo, int64_t k_hi, float *out) -> int {
+        T.n_lo = n_lo;
+        T.rows = rows;
+        T.num_i = (int)((rows + kMxB - 1) / kMxB);
+        T.k_lo = (int)k_lo;
+        T.kprime = (int)k_hi;
+        int r;
+        if ((r = timing_part(s, false))) return r;
+        if ((r = tc_contract_f32(l.kind, maps, T, out, status, s))) return r;
+        return timing_part(s, true);
+    };
     for (int b = 0; b < l.nblk; ++b) {
         const int64_t n0 = 1 + (int64_t)b * kMxB;
-        if (b > 0) {
-            T.n_lo = n0;
-            T.rows = min((int64_t)kMxB, P.N - n0 + 1);
-            T.kprime = (int)(n0 - 1);
-            if ((st = timing_part(s, false))) return st;
-            if ((st = tc_contract_f32(l.kind, maps, T, l.acc, status, s))) return st;
-            if ((st = timing_part(s, true))) return st;
+        const int64_t left = P.N - n0 + 1;                 // steps from n0 to N
+        A.acc = nullptr;
+        A.acc2 = nullptr;
+        if (b % 2 == 0) {
+            if (b >= 2) {
+                if ((st = contract(n0, min((int64_t)2 * kMxB, left), 0, n0 - 1, l.acc2b))) return st;
+                A.acc = l.acc2b;
+            }
+        } else {
+            if ((st = contract(n0, min((int64_t)kMxB, left), n0 - 1 - kMxB, n0 - 1, l.acc1b))) return st;
+            A.acc2 = l.acc1b;
+            if (b >= 3) A.acc = l.acc2b + (size_t)kMxB * 2 * l.nmp;    // rows 128..255 of the pair
         }
         A.n0 = n0;
-        A.acc = b > 0 ? l.acc : nullptr;
         A.write_levels = b + 1 < l.nblk;
         k_mixed_block<<<grid, kMxT, kMxSmem, s>>>(A);
         if ((st = launched())) return st;

@@ -23,14 +23,16 @@ __host__ __device__ constexpr int kind_esize(int kind) { return kind == TC_TF32X
 constexpr int BK = 64;                      // BF16 levels per stage (kind_bk(TC_BF16X3))
 
 // Output rows are steps m in [n_lo, n_lo + rows); row m, column j of state s is
-//   sum over levels k = 1 .. kprime of  d^s_{m-k} * G[s * state_stride + j][k - 1]
+//   sum over levels k = k_lo + 1 .. kprime of  d^s_{m-k} * G[s * state_stride + j][k - 1]
 // (terms with m - k < 1 are absent), j < ndof, written to H[(m - n_lo) * ldh + s * state_stride + j].
+// k_lo is a multiple of 64.
 struct TcParams {
     int64_t ndof, n_lo, rows, ldh;
     int vec2;                  // output rows 16-byte aligned: vector stores
     int num_i;                 // tiles along the steps
     int64_t delta0;            // delta of bank tile 0
-    int kprime;                // levels 1 .. kprime contribute
+    int kprime;                // levels k_lo + 1 .. kprime contribute
+    int k_lo;
     int n_states;              // 1, or 2 (two weight sequences on two halves of the DOFs)
     int64_t ntile_state;       // DOF tiles per state
     int64_t state_stride;      // levels rows and output columns of state s start at s * state_stride
