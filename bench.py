@@ -550,6 +550,40 @@ def batch_leg(fc, torch, dev, K, flush):
     }
 
 
+# The paper's own CPU times (Tables 1 and 5; hardware not stated): context only.
+PAPER_TIMES = {"table1": {"BE": 78.53, "FBE": 23.95}, "table5": {"SBD": 870.13, "FSBD": 209.44}}
+
+
+def paper_leg(fc, torch):
+    """Two of the paper's timed runs on the GPU solver: Table 1 (BE / fast BE, h = 1/256,
+    1/tau = 1600, alpha = (0.3, 0.6)) and Table 5 (SBD / fast SBD, h = 1/1024, T = 10,
+    N = 20000, alpha = (0.3, 0.8)); errors against the plain-scheme reference as in the paper."""
+    from paper_1901_05128_gb300 import tables as TB
+    out = {}
+    for name, alpha, col in (("table1", (0.3, 0.6), -1), ("table5", (0.3, 0.8), 0)):
+        ex = dict(TB.EXPERIMENTS[name])
+        ex["alphas"] = [alpha]
+        ex["inv_tau"] = [ex["inv_tau"][col]]
+        key = name + "_bench"
+        TB.EXPERIMENTS[key] = ex
+        try:
+            res = TB.run(key, fc, torch)
+        finally:
+            del TB.EXPERIMENTS[key]
+        row = res["rows"][0]
+        labels = ("BE", "FBE") if name == "table1" else ("SBD", "FSBD")
+        ndof = 2 * ex["M"]
+        N = int(round(ex["inv_tau"][0] * ex["T"]))
+        entry = {"grid": "1D, h = 1/%d, N = %d, alpha = %s" % (ex["M"] + 1, N, alpha)}
+        for form, lab in zip(("direct", "fast"), labels):
+            t = row[form]["gpu_s"][0]
+            entry[lab] = {"gpu_s": t, "dof_steps_per_s": ndof * N / t,
+                          "E": [float(v) for v in row[form]["E"][0]],
+                          "paper_cpu_s": PAPER_TIMES[name][lab]}
+        out[name] = entry
+    return out
+
+
 def stream_leg(fc, torch, dev, steps=24):
     """Per-step fast history (cq_history_fast) streaming its state from HBM, FP32 and FP64,
     on the 2D 511x511 DOF count with the BDF2 sizes of the main workload (np = 80, Ns = 17);
@@ -704,6 +738,7 @@ def run_ours(args, rank, world, dist):
         grad = gradient_leg(fc, torch, dev, 2, flush) if (args.precision and rank == 0) else None
         batch = batch_leg(fc, torch, dev, 2, flush) if (args.precision and rank == 0) else None
         stream = stream_leg(fc, torch, dev) if (args.precision and rank == 0) else None
+        paper = paper_leg(fc, torch) if (args.precision and rank == 0) else None
     clocks = clk.summary()
 
     ms = statistics.mean(steps)
@@ -792,6 +827,8 @@ def run_ours(args, rank, world, dist):
         out["batch"] = batch
     if stream is not None:
         out["fast_history_stream"] = stream
+    if paper is not None:
+        out["paper_runs"] = {"note": "the paper's CPU times are on unstated hardware: context only", **paper}
     return out
 
 

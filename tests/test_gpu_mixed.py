@@ -86,10 +86,10 @@ def test_direct_mixed_tf32x3_against_fp64_oracle(fc, name, p, sc):
 
 
 def test_direct_mixed_every_step_count(fc):
-    """Final states of the mixed solve for every N in 1..40 and around the block edges
-    (each N is its own problem, tau = T / N), against the oracle."""
+    """Final states of the mixed solve for every N in 1..40 and around the block and pair
+    edges (each N is its own problem, tau = T / N), against the oracle."""
     worst = 0.0
-    for N in list(range(1, 41)) + [127, 128, 129, 255, 256, 257]:
+    for N in list(range(1, 41)) + [127, 128, 129, 255, 256, 257, 383, 384, 385, 511, 512, 513, 640, 641]:
         p = ci.Problem(0.3, 0.6, 0.35, 1.0, N, 1, 15, ci.BDF2 if N % 2 else ci.BE, ci.DIRECT, 0, 0, 0)
         G0 = ci.g0_uniform(p.M, p.dim, 100 + N)
         got, st = _solve(fc, p, G0, fc.CQ_BF16X3)
