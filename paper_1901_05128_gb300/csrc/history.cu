@@ -86,11 +86,13 @@ __global__ void k_pad_weights(const double *__restrict__ d, int64_t n, double *_
 //   h^n = sum_{i=1}^{min(L-1,n-1)} d_i G^{n-i} + sum_j c_j Y_j
 // then G^{n-1} is stored in slot (n-1) % L, which held level n-1-L.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_history_fast_step(int64_t ndof, int64_t n, int L, int np,
-                                                           const double *__restrict__ tab,
-                                                           double *__restrict__ ring, double *__restrict__ Y,
-                                                           const double *__restrict__ G_prev,
-                                                           double *__restrict__ H) {
+__global__ void __launch_bounds__(64) k_history_fast_step(int64_t ndof, int64_t n, int L, int np, int vec,
+                                                          const double *__restrict__ tab,
+                                                          double *__restrict__ ring, double *__restrict__ Y,
+                                                          const double *__restrict__ G_prev,
+                                                          double *__restrict__ H) {
+    // two DOFs per thread; rows are moved as 16-byte pairs when vec (ndof even, so the
+    // workspace rows stay 16-byte aligned, and G_prev, H 16-byte aligned), else element by element
     __shared__ double r[kMaxNp], c[kMaxNp], d[kMaxNs];
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
         r[i] = tab[i];
@@ -101,41 +103,44 @@ __global__ void __launch_bounds__(256) k_history_fast_step(int64_t ndof, int64_t
     const int64_t dof = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
     if (dof >= ndof) return;
     const bool pair = dof + 1 < ndof;
-    double h0 = 0.0, h1 = 0.0, gp0 = 0.0, gp1 = 0.0;
+    auto ld2 = [&](const double *p) -> double2 {
+        if (vec) return *reinterpret_cast<const double2 *>(p);
+        return make_double2(p[0], pair ? p[1] : 0.0);
+    };
+    auto st2 = [&](double *p, double2 v) {
+        if (vec) *reinterpret_cast<double2 *>(p) = v;
+        else {
+            p[0] = v.x;
+            if (pair) p[1] = v.y;
+        }
+    };
+    double h0 = 0.0, h1 = 0.0;
+    double2 gp = make_double2(0.0, 0.0);
     if (n >= 2) {
-        gp0 = G_prev[dof];
-        gp1 = pair ? G_prev[dof + 1] : 0.0;
-        h0 = d[1] * gp0;
-        h1 = d[1] * gp1;
+        gp = ld2(G_prev + dof);
+        h0 = d[1] * gp.x;
+        h1 = d[1] * gp.y;
         const int64_t imax = min((int64_t)L - 1, n - 1);
         for (int i = 2; i <= imax; ++i) {
-            const double *src = ring + (int64_t)((n - i) % L) * ndof + dof;
-            h0 = fma(d[i], src[0], h0);
-            if (pair) h1 = fma(d[i], src[1], h1);
+            const double2 g = ld2(ring + (int64_t)((n - i) % L) * ndof + dof);
+            h0 = fma(d[i], g.x, h0);
+            h1 = fma(d[i], g.y, h1);
         }
     }
     if (n - L >= 1) {
-        const double *gin_p = ring + (int64_t)((n - L) % L) * ndof + dof;
-        const double g0 = gin_p[0], g1 = pair ? gin_p[1] : 0.0;
-        for (int j = 0; j < np; ++j) {
-            double *y = Y + (int64_t)j * ndof + dof;
-            const double y0 = fma(r[j], y[0], g0);
-            y[0] = y0;
-            h0 = fma(c[j], y0, h0);
-            if (pair) {
-                const double y1 = fma(r[j], y[1], g1);
-                y[1] = y1;
-                h1 = fma(c[j], y1, h1);
-            }
+        const double2 gin = ld2(ring + (int64_t)((n - L) % L) * ndof + dof);
+        double *y = Y + dof;
+        for (int j = 0; j < np; ++j, y += ndof) {
+            double2 v = ld2(y);
+            v.x = fma(r[j], v.x, gin.x);
+            v.y = fma(r[j], v.y, gin.y);
+            st2(y, v);
+            h0 = fma(c[j], v.x, h0);
+            h1 = fma(c[j], v.y, h1);
         }
     }
-    if (n >= 2) {
-        double *dst = ring + (int64_t)((n - 1) % L) * ndof + dof;
-        dst[0] = gp0;
-        if (pair) dst[1] = gp1;
-    }
-    H[dof] = h0;
-    if (pair) H[dof + 1] = h1;
+    if (n >= 2) st2(ring + (int64_t)((n - 1) % L) * ndof + dof, gp);
+    st2(H + dof, make_double2(h0, h1));
 }
 
 // ---------------------------------------------------------------------------
@@ -372,8 +377,10 @@ extern "C" int cq_history_fast(int32_t scheme, double beta, double tau, const cq
     }
     const int64_t threads = (ndof + 1) / 2;
     if ((st = timing_begin(s))) return st;
-    k_history_fast_step<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ndof, n, L, np, lay.tab, lay.ring, lay.Y,
-                                                                         G_prev_dev, H_dev);
+    // 64-thread blocks: several per SM, so the last wave is short
+    const int vec = (ndof % 2 == 0) && ((uintptr_t)G_prev_dev % 16 == 0) && ((uintptr_t)H_dev % 16 == 0);
+    k_history_fast_step<<<(unsigned)((threads + 63) / 64), 64, 0, s>>>(ndof, n, L, np, vec, lay.tab, lay.ring,
+                                                                       lay.Y, G_prev_dev, H_dev);
     if ((st = launched())) return st;
     return timing_end(s);
 }

@@ -79,15 +79,16 @@ def test_size_queries_need_no_device(fc):
 
 def test_mixed_direct_size_query(fc):
     """The mixed-precision direct solve sizes its BF16 hi/lo level matrix (K-major, levels
-    of all blocks but the last), the FP32 block accumulator and the Toeplitz banks; it
-    needs no FP64 history. The fast form and the step API reject the BF16x3 precision."""
+    of all blocks but the last), the FP32 contraction rows of one block and of one pair of
+    blocks, and the Toeplitz banks; it needs no FP64 history. The fast form and the step API reject the BF16x3 precision."""
     M, N = 511, 8192
     nm = M * M
     nmp = (nm + 3) // 4 * 4
     pm = fc.problem(0.2, 0.8, 0.45, 1.0, N, 2, M, fc.CQ_BE, fc.CQ_DIRECT, prec=fc.CQ_BF16X3)
     n_mx = fc.fp2s_solve(pm, None, None, None)
     levels = 2 * (2 * nmp) * (N - 128) * 2
-    assert levels + 128 * 2 * nmp * 4 <= n_mx <= levels + 128 * 2 * nmp * 4 + (64 << 20)
+    accs = (128 + 256) * 2 * nmp * 4          # one block's and one pair's contraction rows (FP32)
+    assert levels + accs <= n_mx <= levels + accs + (64 << 20)
     pd = fc.problem(0.2, 0.8, 0.45, 1.0, N, 2, M, fc.CQ_BE, fc.CQ_DIRECT)
     assert fc.fp2s_solve(pd, None, None, None) > 1.9 * n_mx    # FP64 keeps (N + 1) x 2 x nm doubles
     one = fc.problem(0.2, 0.8, 0.45, 1.0, 128, 1, 15, fc.CQ_BE, fc.CQ_DIRECT, prec=fc.CQ_BF16X3)

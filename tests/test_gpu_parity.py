@@ -168,6 +168,15 @@ SOLVES = [
     ("be3d", ci.Problem(0.35, 0.7, 0.4, 1.0, 120, 3, 9, ci.BE, ci.DIRECT)),
     ("bdf2_3d_fast", ci.Problem(0.3, 0.6, 0.65, 1.0, 150, 3, 11, ci.BDF2, ci.FAST, 12, 30, 9)),
     ("be3d_fast_ragged", ci.Problem(0.6, 0.45, 0.3, 0.5, 77, 3, 13, ci.BE, ci.FAST, 40, 0, 2)),
+    # mode counts on both sides of the lane-split thresholds of the direct solve (32, 16, 8, 4
+    # lanes per mode below 4864, 9728, 19456, 38912 modes) and of the fast solve (a warp per
+    # mode below 9728 modes)
+    ("direct_lp16", ci.Problem(0.3, 0.7, 0.4, 1.0, 30, 2, 70, ci.BE, ci.DIRECT)),
+    ("direct_lp8", ci.Problem(0.5, 0.6, 0.6, 1.0, 25, 2, 100, ci.BDF2, ci.DIRECT)),
+    ("direct_lp4", ci.Problem(0.3, 0.7, 0.4, 1.0, 20, 2, 150, ci.BE, ci.DIRECT)),
+    ("direct_lp1", ci.Problem(0.3, 0.7, 0.4, 1.0, 12, 2, 200, ci.BDF2, ci.DIRECT)),
+    ("fast_warp_per_mode", ci.Problem(0.4, 0.6, 0.3, 1.0, 60, 2, 98, ci.BDF2, ci.FAST, 16, 64, 17)),
+    ("fast_16_per_warp", ci.Problem(0.4, 0.6, 0.3, 1.0, 60, 2, 99, ci.BDF2, ci.FAST, 16, 64, 17)),
 ]
 
 
