@@ -193,18 +193,31 @@ __device__ __forceinline__ void store16(double *row, int64_t c0, int64_t ncol, i
     }
 }
 
-__device__ __forceinline__ void store16(float *row, int64_t c0, int64_t ncol, int vec2, bool have, const float *v) {
+// FP32 output; add (the output already holds a partial sum) adds the row to it.
+__device__ __forceinline__ void store16(float *row, int64_t c0, int64_t ncol, int vec2, bool have, const float *v,
+                                        int add) {
     const float nan = __int_as_float(0x7fc00000);
     if (vec2 && c0 + 16 <= ncol) {
 #pragma unroll
-        for (int i = 0; i < 16; i += 4)
-            *reinterpret_cast<float4 *>(row + c0 + i) =
-                have ? make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]) : make_float4(nan, nan, nan, nan);
+        for (int i = 0; i < 16; i += 4) {
+            float4 *dst = reinterpret_cast<float4 *>(row + c0 + i);
+            float4 o = have ? make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]) : make_float4(nan, nan, nan, nan);
+            if (add) {
+                const float4 old = *dst;
+                o = make_float4(o.x + old.x, o.y + old.y, o.z + old.z, o.w + old.w);
+            }
+            *dst = o;
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-            if (c0 + i < ncol) row[c0 + i] = have ? v[i] : nan;
+            if (c0 + i < ncol) row[c0 + i] = (have ? v[i] : nan) + (add ? row[c0 + i] : 0.0f);
     }
+}
+
+__device__ __forceinline__ void store16(double *row, int64_t c0, int64_t ncol, int vec2, bool have, const float *v,
+                                        int) {
+    store16(row, c0, ncol, vec2, have, v);
 }
 
 template <typename OutT, int KIND>
@@ -369,7 +382,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
         OutT *hrow = H + (m - P.n_lo) * P.ldh + (int64_t)state * P.state_stride;
         if (row_ok) {
 #pragma unroll
-            for (int j = 0; j < BN / 2; j += 16) store16(hrow, n0 + half * (BN / 2) + j, P.ndof, P.vec2, have, accr + j);
+            for (int j = 0; j < BN / 2; j += 16)
+                store16(hrow, n0 + half * (BN / 2) + j, P.ndof, P.vec2, have, accr + j, P.add);
         }
     }
     tc_fence_before();
@@ -584,6 +598,7 @@ int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, 
     P.delta0 = l.delta0;
     P.kprime = kprime;
     P.k_lo = 0;
+    P.add = 0;
     const int64_t num_n = (ndof + BN - 1) / BN;
     P.n_states = 1;
     P.ntile_state = num_n;

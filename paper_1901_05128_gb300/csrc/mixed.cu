@@ -18,8 +18,8 @@
 //
 // Per pair of blocks: one contraction over the earlier pairs' levels for the rows
 // of both blocks (two row tiles share each level tile), one short contraction of
-// the first block's levels for the second block's rows, and one step launch per
-// block, which appends the block's levels to the K-major level matrix.
+// the first block's levels added onto the second block's rows, and one step
+// launch per block, which appends the block's levels to the K-major level matrix.
 #include "common.cuh"
 #include "fp2s_core.cuh"
 #include "tc.cuh"
@@ -77,7 +77,7 @@ struct MixedArgs {
     int64_t nmp, n0, kpad;
     int solve64, write_levels, kind;
     const double *lam, *g0, *d1, *d2;
-    const float *hdf, *acc, *acc2;      // contraction rows of this block (each optional), summed
+    const float *hdf, *acc;             // contraction rows of this block (absent for the first block)
     float *carry;
     float4 *coef;
     char *gt_hi, *gt_lo;
@@ -183,18 +183,14 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     const int jmax = (int)min((int64_t)kMxB, P.N - A.n0 + 1);      // steps in this block
     float an[kMxSB];                                 // acc rows of the next sub-block (prefetched)
 #pragma unroll
-    for (int b = 0; b < kMxSB; ++b)
-        an[b] = (A.acc ? A.acc[(int64_t)b * ldacc + col] : 0.0f) + (A.acc2 ? A.acc2[(int64_t)b * ldacc + col] : 0.0f);
+    for (int b = 0; b < kMxSB; ++b) an[b] = A.acc ? A.acc[(int64_t)b * ldacc + col] : 0.0f;
     for (int j0 = 0; j0 < jmax; j0 += kMxSB) {
         float a[kMxSB];
 #pragma unroll
         for (int b = 0; b < kMxSB; ++b) a[b] = an[b];
-        if (j0 + kMxSB < jmax) {
+        if (A.acc && j0 + kMxSB < jmax) {
 #pragma unroll
-            for (int b = 0; b < kMxSB; ++b) {
-                const int64_t o = (int64_t)(j0 + kMxSB + b) * ldacc + col;
-                an[b] = (A.acc ? A.acc[o] : 0.0f) + (A.acc2 ? A.acc2[o] : 0.0f);
-            }
+            for (int b = 0; b < kMxSB; ++b) an[b] = A.acc[(int64_t)(j0 + kMxSB + b) * ldacc + col];
         }
         // earlier in-block levels k in chunks of 8: a[b] += sum_kk d_{j0 + b - kc - kk} x^{n0 + kc + kk};
         // the 15 weights of a chunk are d_{m-7} .. d_{m+7}, m = j0 - kc (four 16-byte loads)
@@ -335,9 +331,10 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
     // Blocks in pairs (2p, 2p+1). Once both earlier pairs' levels exist, one contraction
     // covers the rows of both blocks over the levels of blocks < 2p (two row tiles per
     // column tile: the level matrix is streamed once for 256 rows); block 2p+1 then adds
-    // the levels of block 2p with a short contraction (K = 128) of its own.
-    auto contract = [&](int64_t n_lo, int64_t rows, int64_t k_lo, int64_t k_hi, float *out) -> int {
+    // the levels of block 2p with a short contraction (K = 128) added onto its rows.
+    auto contract = [&](int64_t n_lo, int64_t rows, int64_t k_lo, int64_t k_hi, float *out, int add) -> int {
         T.n_lo = n_lo;
+        T.add = add;
         T.rows = rows;
         T.num_i = (int)((rows + kMxB - 1) / kMxB);
         T.k_lo = (int)k_lo;
@@ -351,16 +348,16 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
         const int64_t n0 = 1 + (int64_t)b * kMxB;
         const int64_t left = P.N - n0 + 1;                 // steps from n0 to N
         A.acc = nullptr;
-        A.acc2 = nullptr;
         if (b % 2 == 0) {
             if (b >= 2) {
-                if ((st = contract(n0, min((int64_t)2 * kMxB, left), 0, n0 - 1, l.acc2b))) return st;
+                if ((st = contract(n0, min((int64_t)2 * kMxB, left), 0, n0 - 1, l.acc2b, 0))) return st;
                 A.acc = l.acc2b;
             }
         } else {
-            if ((st = contract(n0, min((int64_t)kMxB, left), n0 - 1 - kMxB, n0 - 1, l.acc1b))) return st;
-            A.acc2 = l.acc1b;
-            if (b >= 3) A.acc = l.acc2b + (size_t)kMxB * 2 * l.nmp;    // rows 128..255 of the pair
+            // block 2p+1: its rows of the pair's contraction (rows 128..255), or a fresh buffer
+            float *rows = b >= 3 ? l.acc2b + (size_t)kMxB * 2 * l.nmp : l.acc1b;
+            if ((st = contract(n0, min((int64_t)kMxB, left), n0 - 1 - kMxB, n0 - 1, rows, b >= 3))) return st;
+            A.acc = rows;
         }
         A.n0 = n0;
         A.write_levels = b + 1 < l.nblk;

@@ -33,6 +33,7 @@ struct TcParams {
     int64_t delta0;            // delta of bank tile 0
     int kprime;                // levels k_lo + 1 .. kprime contribute
     int k_lo;
+    int add;                   // FP32 output only: add to what H holds instead of overwriting
     int n_states;              // 1, or 2 (two weight sequences on two halves of the DOFs)
     int64_t ntile_state;       // DOF tiles per state
     int64_t state_stride;      // levels rows and output columns of state s start at s * state_stride
