@@ -146,3 +146,30 @@ def test_tf32x3_more_accurate_than_bf16x3(fc):
     e_t = np.max(np.abs(_run_history(fc, fc.CQ_TF32X3, 1, beta, tau, G, ndof, n_lo, n_hi, ndof) - ref))
     print("max error: bf16x3 %.3e, tf32x3 %.3e" % (e_b, e_t))
     assert e_t * 8 <= e_b
+
+
+def test_tf32x3_history_full_size_sampled(fc):
+    """The 2D 511x511 contraction at its full size in the TF32x3 form, last 193 steps, 24
+    whole DOF columns recomputed by the oracle."""
+    ndof, n_lo, n_hi = 2 * 511 * 511, 8000, 8193
+    beta, tau = 0.8, 1.0 / 8192
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(ci.SEED_BASE + 5)
+    G = torch.randn(n_hi, ndof, dtype=torch.float64, device="cuda", generator=gen)
+    H = torch.empty(n_hi - n_lo, ndof, dtype=torch.float64, device="cuda")
+    ws = fc.workspace(fc.cq_history_direct(1, beta, tau, ndof, n_lo, n_hi, None, ndof, None, ndof,
+                                           prec=fc.CQ_TF32X3), "cuda")
+    fc.cq_history_direct(1, beta, tau, ndof, n_lo, n_hi, G, ndof, H, ndof, ws, prec=fc.CQ_TF32X3)
+    torch.cuda.synchronize()
+    cols = np.concatenate([[0, ndof - 1], ci.sample_indices(ndof, 22, ci.SEED_BASE + 6)])
+    idx = torch.tensor(cols, device="cuda")
+    Gc = G[:, idx].cpu().numpy()
+    Hc = H[:, idx].cpu().numpy()
+    del G, H, ws
+    torch.cuda.empty_cache()
+    d = OW.weights(1, beta, tau, n_hi)
+    ref = OH.history_direct_all(d, Gc, n_lo, n_hi)
+    scale = np.stack([_abs_scale(d, Gc, n) for n in range(n_lo, n_hi)])
+    err = np.abs(Hc - ref)
+    print("tf32x3 full size: max |err| / sum|d||G| = %.3e" % float(np.max(err / scale)))
+    assert np.all(err <= _bound_tf32(n_hi) * scale)
