@@ -37,6 +37,28 @@ int timing_part(cudaStream_t s, bool end) {
     return CQ_OK;
 }
 
+int smem_attr_once(const void *func, int bytes, unsigned long long *done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CQ_ECUDA;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (__atomic_load_n(done, __ATOMIC_ACQUIRE) & bit)) return CQ_OK;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        return CQ_ECUDA;
+    if (bit) __atomic_fetch_or(done, bit, __ATOMIC_RELEASE);
+    return CQ_OK;
+}
+
+int device_sms() {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev < 64 && sms[dev] > 0) return sms[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    if (dev < 64) sms[dev] = n;
+    return n;
+}
+
 int timing_end(cudaStream_t s) {
     if (!g_timing) return CQ_OK;
     if (cudaEventRecord(g_ev1, s) != cudaSuccess) return CQ_ECUDA;

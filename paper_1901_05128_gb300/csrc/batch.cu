@@ -373,12 +373,7 @@ static void make_units(const std::vector<InstDesc> &descs, int wb, std::vector<U
     for (auto &t : tmp) units.push_back(t.second);
 }
 
-static int num_sms_b() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
-    return sms;
-}
+static int num_sms_b() { return device_sms(); }
 
 static int launch_main(const fp2s_batch_t *plan, const BatchLayout &l, int64_t step_cap, cudaStream_t s) {
     const int T = 32 * plan->warps_per_block;
@@ -485,13 +480,9 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
     if ((st = cuda_status(cudaMemsetAsync(l.status, 0, 64 * sizeof(int), s)))) return st;
     if ((st = cuda_status(cudaMemsetAsync(l.modal, 0, z.modal * sizeof(double), s)))) return st;
     // tables for the whole batch
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_b_weights, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((kMaxWeights + 1) * sizeof(double))) != cudaSuccess)
-            return CQ_ECUDA;
-        attr = true;
-    }
+    static unsigned long long attr = 0;
+    if ((st = smem_attr_once((const void *)k_b_weights, (int)((kMaxWeights + 1) * sizeof(double)), &attr)))
+        return st;
     k_b_weights<<<dim3(n, 2), kWThreads, (z.maxN + 1) * sizeof(double), s>>>(l.desc, l.W);
     k_b_gauss_jacobi<<<dim3(n, 4, (kMaxNp + kGJThreads - 1) / kGJThreads), kGJThreads, 0, s>>>(l.desc, l.scr);
     k_b_coeffs<<<dim3(n, 2), 256, 0, s>>>(l.desc, l.scr, l.tab);

@@ -55,6 +55,12 @@ inline int launched(int64_t k = 1) {
 
 inline bool bad_order(double beta) { return !(beta > 0.0 && beta < 1.0); }
 
+// Device-wide settings are per device: a kernel's dynamic shared-memory limit is set once
+// per device (bit d of *done marks device d; devices beyond 63 set it on every call).
+int smem_attr_once(const void *func, int bytes, unsigned long long *done);
+// Multiprocessor count of the current device.
+int device_sms();
+
 // ---- table builders (tables.cu), all enqueue on `s` -------------------------
 // weights d_i, i = 0..n, of scheme into out (device). Single block. n <= kMaxWeights, or
 // n <= kMaxSolveSteps with scratch (n + 1 doubles of device memory).

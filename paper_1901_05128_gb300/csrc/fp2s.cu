@@ -338,15 +338,7 @@ static size_t fast_smem_bytes(int np, int L, int T) {
     return ((size_t)4 * np + 2 * kMaxNs + (size_t)(np + L) * T) * sizeof(double);
 }
 
-static int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
-    }
-    return sms;
-}
+static int num_sms() { return device_sms(); }
 
 // Warps per block: the largest that fits shared memory among those whose grid
 // fills whole waves best (one block per SM).
@@ -893,7 +885,8 @@ static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s
         const int T = fast_block_threads(P.np, P.L, P.nmodes);
         if (T == 0) return CQ_EUNSUPPORTED;
         const size_t smem = fast_smem_bytes(P.np, P.L, T);
-        cudaFuncSetAttribute(k_fp2s_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaFuncSetAttribute(k_fp2s_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return CQ_ECUDA;
         const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
         const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
         k_fp2s_fast<<<blocks, T, smem, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2);
@@ -1312,11 +1305,8 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     k_fp2s_direct<kDirBT><<<fblocks, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2, l.hist);
     if ((st = launched())) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, gl.tgt, l.tmp, s))) return st;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_dweights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * 13001 * sizeof(double)));
-        attr = true;
-    }
+    static unsigned long long attr = 0;
+    if ((st = smem_attr_once((const void *)k_dweights, (int)(2 * 13001 * sizeof(double)), &attr))) return st;
     const size_t dsm = (size_t)2 * (P.N + 1) * sizeof(double);
     k_dweights<<<1, 1024, dsm, s>>>(P.scheme, 1.0 - p->alpha1, P.tau, (int)P.N, gl.q1);
     k_dweights<<<1, 1024, dsm, s>>>(P.scheme, 1.0 - p->alpha2, P.tau, (int)P.N, gl.q2);

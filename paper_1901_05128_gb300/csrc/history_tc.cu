@@ -532,16 +532,14 @@ static TcLayout tc_layout(int kind, void *ws, int64_t ndof, int64_t n_lo, int64_
 }
 
 static int tc_attr() {
-    static bool done = false;
-    if (done) return CQ_OK;
+    static unsigned long long done[4] = {};
     const int sm = (int)SMEM_BYTES;
-    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (cudaFuncSetAttribute(k_history_tc<double, TC_BF16X3>, a, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_history_tc<float, TC_BF16X3>, a, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_history_tc<double, TC_TF32X3>, a, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_history_tc<float, TC_TF32X3>, a, sm) != cudaSuccess)
-        return CQ_ECUDA;
-    done = true;
+    int st;
+    if ((st = smem_attr_once((const void *)k_history_tc<double, TC_BF16X3>, sm, &done[0])) ||
+        (st = smem_attr_once((const void *)k_history_tc<float, TC_BF16X3>, sm, &done[1])) ||
+        (st = smem_attr_once((const void *)k_history_tc<double, TC_TF32X3>, sm, &done[2])) ||
+        (st = smem_attr_once((const void *)k_history_tc<float, TC_TF32X3>, sm, &done[3])))
+        return st;
     return CQ_OK;
 }
 

@@ -293,13 +293,8 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
         if ((st = tc_map_levels(l.kind, &maps.b_hi, l.gt_hi, l.kpad, 2 * l.nmp))) return st;
         if ((st = tc_map_levels(l.kind, &maps.b_lo, l.gt_lo, l.kpad, 2 * l.nmp))) return st;
     }
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_mixed_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMxSmem) !=
-            cudaSuccess)
-            return CQ_ECUDA;
-        attr = true;
-    }
+    static unsigned long long attr = 0;
+    if ((st = smem_attr_once((const void *)k_mixed_block, (int)kMxSmem, &attr))) return st;
     MixedArgs A;
     A.P = P;
     A.nmp = l.nmp;

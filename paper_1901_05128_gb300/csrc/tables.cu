@@ -27,12 +27,9 @@ int launch_weights(int scheme, double beta, double tau, int64_t n, double *out, 
     if (n < 0 || n > (scratch ? kMaxSolveSteps : kMaxWeights)) return CQ_EINVAL;
     const bool global = n > kMaxWeights;
     size_t smem = global ? 0 : (size_t)(n + 1) * sizeof(double);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_weights, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((kMaxWeights + 1) * sizeof(double)));
-        attr_done = true;
-    }
+    static unsigned long long attr = 0;
+    int st;
+    if ((st = smem_attr_once((const void *)k_weights, (int)((kMaxWeights + 1) * sizeof(double)), &attr))) return st;
     k_weights<<<1, kWThreads, smem, s>>>(scheme, beta, pow(tau, -beta), (int)n, out, global ? scratch : nullptr);
     return launched();
 }
