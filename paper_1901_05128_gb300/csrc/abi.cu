@@ -20,12 +20,16 @@ static int g_part_created = 0, g_part_used = 0;
 int timing_begin(cudaStream_t s) {
     if (!g_timing) return CQ_OK;
     g_part_used = 0;
+    g_part_open = false;
     return cudaEventRecord(g_ev0, s) == cudaSuccess ? CQ_OK : CQ_ECUDA;
 }
+
+static bool g_part_open = false;          // a begin event of the current sub-launch was recorded
 
 int timing_part(cudaStream_t s, bool end) {
     if (!g_timing) return CQ_OK;
     if (!end && g_part_used >= kMaxTimedParts) return CQ_OK;     // beyond the pool: not timed
+    if (end && !g_part_open) return CQ_OK;                         // its begin was not recorded
     const int k = 2 * (end ? g_part_used - 1 : g_part_used) + (end ? 1 : 0);
     if (k < 0) return CQ_OK;
     while (g_part_created <= k) {
@@ -34,6 +38,7 @@ int timing_part(cudaStream_t s, bool end) {
     }
     if (cudaEventRecord(g_part_ev[k], s) != cudaSuccess) return CQ_ECUDA;
     if (!end) ++g_part_used;
+    g_part_open = !end;
     return CQ_OK;
 }
 
