@@ -16,6 +16,7 @@ static cudaEvent_t g_ev0 = nullptr, g_ev1 = nullptr;
 // the mixed-precision direct solve) inside the timed region; reset by timing_begin.
 static cudaEvent_t g_part_ev[2 * kMaxTimedParts];
 static int g_part_created = 0, g_part_used = 0;
+static bool g_part_open = false;          // a begin event of the current sub-launch was recorded
 
 int timing_begin(cudaStream_t s) {
     if (!g_timing) return CQ_OK;
@@ -23,8 +24,6 @@ int timing_begin(cudaStream_t s) {
     g_part_open = false;
     return cudaEventRecord(g_ev0, s) == cudaSuccess ? CQ_OK : CQ_ECUDA;
 }
-
-static bool g_part_open = false;          // a begin event of the current sub-launch was recorded
 
 int timing_part(cudaStream_t s, bool end) {
     if (!g_timing) return CQ_OK;
