@@ -468,6 +468,9 @@ def gradient_leg(fc, torch, dev, K, flush):
         fd.append((J_of(p.replace(**{f: v + eps})) - J_of(p.replace(**{f: v - eps}))) / (2 * eps))
     ms = statistics.mean(times)
     rel = [abs(da[i] - fd[i]) / abs(fd[i]) for i in range(2)]
+    dG64 = dg.clone()
+    mixed = [mixed_gradient_run(fc, torch, dev, p, g0, gt, prec, name, J, da, dG64, fd, ms, 3, flush)
+             for name, prec in (("BF16x3", fc.CQ_BF16X3), ("TF32x3", fc.CQ_TF32X3))]
     return {
         "workload": "%s: 2D %dx%d (%d DOF), N=%d, BDF2 direct, alpha=(%g,%g), m=%g; target = same scheme with "
                     "alpha + (0.05,-0.05); J = 1/2 h^2 ||G^N - G_target||^2" % (GRAD_WORKLOAD, p.M, p.M, p.ndof, p.N,
@@ -480,6 +483,66 @@ def gradient_leg(fc, torch, dev, K, flush):
         "cpu_baseline": None,
         "cpu_baseline_note": "the oracle adjoint is an O(N^2) Python loop; at N = 4096 it exceeds the bench's CPU "
                              "budget, so it is timed only in the tests on small problems",
+        "mixed_precision": mixed,
+    }
+
+
+def mixed_gradient_run(fc, torch, dev, p, g0, gt, prec, name, J64, da64, dG64, fd, ms64, K, flush):
+    """The same gradient through the mixed-precision direct solve (tensor-core histories on
+    FP32 levels): time, contraction roofline, and errors against the FP64 gradient and the
+    central differences of the FP64 forward solve."""
+    import cq_inputs as ci
+    cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, ci.DIRECT, prec=prec)
+    dg = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_gradient(cp, g0, gt, dg, None), dev)
+    Jm, dam = fc.fp2s_gradient(cp, g0, gt, dg, ws)            # warm-up
+    times, kern, tcs = [], [], []
+    l0 = fc.cq_launch_count()
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Jm, dam = fc.fp2s_gradient(cp, g0, gt, dg, ws)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kern.append(fc.cq_timing_last())
+        tcs.append(fc.cq_timing_part(1))
+    launches = (fc.cq_launch_count() - l0) / K
+    del ws
+    ms, tc_ms = statistics.mean(times), statistics.mean(tcs)
+    nm, N, B = p.M ** p.dim, p.N, 128
+    nblk = (N + B - 1) // B
+    # contractions: forward and adjoint sweeps (earlier blocks' levels for every block) and the
+    # weight-derivative history over all N rows; 3 products x 2 flops x 2 nm columns
+    sweep = 3 * 2.0 * B * B * 2 * nm * sum(range(1, nblk))
+    flops = 2 * sweep + 3 * 2.0 * 2 * nm * N * (N + 1) / 2
+    peaks = _measured_peaks()
+    if prec == fc.CQ_TF32X3:
+        peak = peaks.get("bf16_tflops_sustained", 1712.8) * 1.1 / 2.25
+        peak_src = "MEASURED_PEAKS.json bf16_tflops_sustained x nominal TF32/BF16 ratio 1.1/2.25"
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1712.8)
+        peak_src = "MEASURED_PEAKS.json bf16_tflops_sustained (kernels inside a long call)"
+    dgc, d64 = dg.double(), dG64.double()
+    return {
+        "precision": "%s contractions on FP32 levels (forward, weight-derivative history of the increments, "
+                     "reversed-time adjoint), FP64 weights and step coefficients" % name,
+        "value": 1e3 / ms, "unit": "grad steps/s (gradient evaluations per second)", "ms_per_gradient": ms,
+        "dof_steps_per_s": p.ndof * p.N / (ms * 1e-3), "kernels_ms": statistics.mean(kern),
+        "speedup_vs_fp64_gradient": ms64 / ms,
+        "gpu_launches_per_gradient": launches,
+        "roofline": {"kernel": "k_history_tc<float, %s> (all contractions of one gradient)" % name.upper(),
+                     "bound": "tensor", "unit": "TFLOP/s", "achieved": flops / (tc_ms * 1e-3) / 1e12, "peak": peak,
+                     "frac": flops / (tc_ms * 1e-3) / 1e12 / peak, "contraction_ms": tc_ms,
+                     "share_of_gradient": tc_ms / ms, "peak_source": peak_src, "algorithmic_flops": flops},
+        "J": Jm, "dJ_dalpha": list(dam),
+        "rel_err_vs_fp64_gradient": {
+            "J": abs(Jm - J64) / abs(J64),
+            "dJ_dalpha": [abs(dam[i] - da64[i]) / abs(da64[i]) for i in range(2)],
+            "dJ_dG0_rel_l2": float(torch.linalg.norm(dgc - d64) / torch.linalg.norm(d64))},
+        "rel_err_vs_central_differences": [abs(dam[i] - fd[i]) / abs(fd[i]) for i in range(2)],
     }
 
 

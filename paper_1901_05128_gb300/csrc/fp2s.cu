@@ -35,7 +35,8 @@ struct Fp2sLayout {
     size_t bytes;
 };
 
-static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void *ws, bool stepper) {
+static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void *ws, bool stepper,
+                              bool grad = false) {
     Carve cv(ws);
     Fp2sLayout l{};
     const int64_t nm = P.nmodes;
@@ -60,7 +61,7 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     if (P.form == CQ_DIRECT && P.prec == CQ_F64) l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
     if (P.prec != CQ_F64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
     if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3))
-        l.mixed = cv.take<char>(mixed_direct_bytes(P));
+        l.mixed = cv.take<char>(grad ? mixed_grad_bytes(P) : mixed_direct_bytes(P));
     if (stepper) {
         if (P.form == CQ_FAST) {
             l.Y = cv.take<double>((size_t)2 * P.np * nm);
@@ -1280,6 +1281,58 @@ static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void 
     return g;
 }
 
+static int weight_derivatives(const Fp2sParams &P, const fp2s_problem_t *p, double *q1, double *q2,
+                              cudaStream_t s) {
+    static unsigned long long attr = 0;
+    int st;
+    if ((st = smem_attr_once((const void *)k_dweights, (int)(2 * 13001 * sizeof(double)), &attr))) return st;
+    const size_t dsm = (size_t)2 * (P.N + 1) * sizeof(double);
+    k_dweights<<<1, 1024, dsm, s>>>(P.scheme, 1.0 - p->alpha1, P.tau, (int)P.N, q1);
+    k_dweights<<<1, 1024, dsm, s>>>(P.scheme, 1.0 - p->alpha2, P.tau, (int)P.N, q2);
+    return launched(2);
+}
+
+static double grid_weight(const fp2s_problem_t *p) {
+    const double h = 1.0 / (p->M + 1);
+    return (p->dim == 1) ? h : (p->dim == 2) ? h * h : h * h * h;
+}
+
+// Gradient through the mixed-precision direct solve (mixed.cu): same outputs as the
+// FP64 gradient, computed from FP32 levels and tensor-core histories.
+static int gradient_mixed(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2, const double *G0_dev,
+                          const double *Gt_dev, int vjp, double *J_host, double *dJdG0_dev, double *dJdalpha_host,
+                          void *ws_dev, size_t *ws_bytes, cudaStream_t s) {
+    const Fp2sLayout l = fp2s_layout(p, P, ws_dev, false, true);
+    Carve cv(ws_dev);
+    cv.off = l.bytes;
+    double *acc = cv.take<double>(8), *tgt = cv.take<double>(2 * P.nmodes), *gx0 = cv.take<double>(2 * P.nmodes);
+    double *q1 = cv.take<double>(P.N + 1), *q2 = cv.take<double>(P.N + 1);
+    if (!ws_dev) { *ws_bytes = cv.bytes(); return CQ_OK; }
+    if (*ws_bytes < cv.bytes()) return CQ_ENOMEM;
+    if (!G0_dev || !Gt_dev || (!vjp && !J_host) || !dJdG0_dev || !dJdalpha_host || ((uintptr_t)ws_dev & 255))
+        return CQ_EINVAL;
+    int st;
+    if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
+    if ((st = timing_begin(s))) return st;
+    if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, tgt, l.tmp, s))) return st;
+    if ((st = weight_derivatives(P, p, q1, q2, s))) return st;
+    if ((st = cuda_status(cudaMemsetAsync(acc, 0, 8 * sizeof(double), s)))) return st;
+    if ((st = mixed_grad_run(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, q1, q2, l.hdf, tgt, vjp, grid_weight(p),
+                             gx0, acc, l.mixed, s)))
+        return st;
+    if ((st = timing_end(s))) return st;
+    if ((st = launch_dst_field(p->M, p->dim, l.S, gx0, dJdG0_dev, l.tmp, s))) return st;
+    double host[4];
+    if (cudaMemcpyAsync(host, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CQ_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CQ_ECUDA;
+    if (J_host) *J_host = host[0];
+    dJdalpha_host[0] = -host[1];
+    dJdalpha_host[1] = -host[2];
+    if ((st = read_status(l.status, s))) return st;
+    if (!isfinite(host[0]) || !isfinite(host[1]) || !isfinite(host[2])) return CQ_ENONFINITE;
+    return CQ_OK;
+}
+
 // Forward direct solve (history kept), then the adjoint sweep. vjp = 0: terminal condition
 // from the misfit against Gt; vjp = 1: Gt holds dL/dG^N and J is not formed.
 static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, int vjp,
@@ -1290,8 +1343,12 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     int st = derive(p, P, np1, np2);
     if (st) return st;
     if (!ws_bytes) return CQ_EINVAL;
-    if (P.form != CQ_DIRECT || P.prec != CQ_F64) return CQ_EUNSUPPORTED;
+    const bool mixed = P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3;
+    if (P.form != CQ_DIRECT || !(P.prec == CQ_F64 || mixed)) return CQ_EUNSUPPORTED;
     if (P.N > 13000) return CQ_EUNSUPPORTED;            // shared-memory bound of the weight derivatives
+    if (mixed)
+        return gradient_mixed(p, P, np1, np2, G0_dev, Gt_dev, vjp, J_host, dJdG0_dev, dJdalpha_host, ws_dev,
+                              ws_bytes, (cudaStream_t)stream);
     Fp2sLayout l = fp2s_layout(p, P, ws_dev, false);
     GradLayout gl = grad_layout(P, l, ws_dev);
     if (!ws_dev) { *ws_bytes = gl.bytes; return CQ_OK; }
@@ -1305,23 +1362,18 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     k_fp2s_direct<kDirBT><<<fblocks, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2, l.hist);
     if ((st = launched())) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, gl.tgt, l.tmp, s))) return st;
-    static unsigned long long attr = 0;
-    if ((st = smem_attr_once((const void *)k_dweights, (int)(2 * 13001 * sizeof(double)), &attr))) return st;
-    const size_t dsm = (size_t)2 * (P.N + 1) * sizeof(double);
-    k_dweights<<<1, 1024, dsm, s>>>(P.scheme, 1.0 - p->alpha1, P.tau, (int)P.N, gl.q1);
-    k_dweights<<<1, 1024, dsm, s>>>(P.scheme, 1.0 - p->alpha2, P.tau, (int)P.N, gl.q2);
+    if ((st = weight_derivatives(P, p, gl.q1, gl.q2, s))) return st;
     const unsigned pg = (unsigned)((P.N + 2 * kAdjBT + 256) / 256);
     k_pad<<<pg, 256, 0, s>>>(gl.q1, P.N, kAdjBT, gl.qz1);
     k_pad<<<pg, 256, 0, s>>>(gl.q2, P.N, kAdjBT, gl.qz2);
-    if ((st = launched(4))) return st;
+    if ((st = launched(2))) return st;
     // the adjoint needs the weights padded for its own block size
     double *dzA1 = gl.dza1, *dzA2 = gl.dza2;
     k_pad<<<pg, 256, 0, s>>>(l.d1, P.N, kAdjBT, dzA1);
     k_pad<<<pg, 256, 0, s>>>(l.d2, P.N, kAdjBT, dzA2);
     if ((st = launched(2))) return st;
     if ((st = cuda_status(cudaMemsetAsync(gl.acc, 0, 8 * sizeof(double), s)))) return st;
-    const double h = 1.0 / (p->M + 1);
-    const double wd = (p->dim == 1) ? h : (p->dim == 2) ? h * h : h * h * h;
+    const double wd = grid_weight(p);
     k_adjoint_direct<kAdjBT><<<fblocks, 32, 0, s>>>(P, wd, l.lam, l.d1, l.d2, dzA1, dzA2, gl.q1, gl.q2, gl.qz1,
                                                     gl.qz2, l.hist, gl.tgt, vjp, gl.mu, gl.gx0, gl.acc);
     if ((st = launched())) return st;

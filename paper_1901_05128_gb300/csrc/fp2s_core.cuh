@@ -256,5 +256,13 @@ constexpr int kFastModesPerWarp = 16;     // a warp carries 16 modes x 2 states
 size_t mixed_direct_bytes(const Fp2sParams &P);
 int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
                      const double *d1, const double *d2, const float *hdf, void *region, cudaStream_t s);
+// Its gradient (discrete adjoint): the forward solve with every level kept, the
+// weight-derivative contraction and the reversed-time adjoint sweep. q1, q2: d(d_i)/d(beta);
+// tgt: the modal target (misfit) or dL/dx^N (vjp); writes the modal dJ/dx^0 to gx0 and
+// adds J, dJ/dbeta_1, dJ/dbeta_2 to acc[0..2].
+size_t mixed_grad_bytes(const Fp2sParams &P);
+int mixed_grad_run(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
+                   const double *d1, const double *d2, const double *q1, const double *q2, const float *hdf,
+                   const double *tgt, int vjp, double wd, double *gx0, double *acc, void *region, cudaStream_t s);
 
 }  // namespace fastcq

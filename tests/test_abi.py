@@ -121,6 +121,22 @@ def test_vjp_host_checks(fc):
     assert fc._lib.fp2s_vjp(C.byref(p), None, None, None, da, 1 << 20, C.byref(sz), None) == fc.CQ_EINVAL
 
 
+def test_mixed_gradient_size_query(fc):
+    """The mixed-precision gradient keeps every level and the weight-derivative history
+    (N x 2 x nmp FP32) beyond what the mixed solve needs; vjp shares the layout."""
+    N, M = 300, 15
+    p = fc.problem(0.3, 0.7, 0.4, 1.0, N, 1, M, fc.CQ_BDF2, fc.CQ_DIRECT, prec=fc.CQ_BF16X3)
+    n_g = fc.fp2s_gradient(p, None, None, None, None)
+    assert n_g >= fc.fp2s_solve(p, None, None, None) + N * 2 * 16 * 4
+    assert fc.fp2s_vjp(p, None, None, None, None) == n_g
+    pt = fc.problem(0.3, 0.7, 0.4, 1.0, N, 1, M, fc.CQ_BDF2, fc.CQ_DIRECT, prec=fc.CQ_TF32X3)
+    assert fc.fp2s_gradient(pt, None, None, None, None) > n_g          # 4-byte TF32 operands
+    sz = C.c_size_t(0)
+    da = (C.c_double * 2)()
+    p32 = fc.problem(0.3, 0.7, 0.4, 1.0, N, 1, M, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2, prec=fc.CQ_F32)
+    assert fc._lib.fp2s_vjp(C.byref(p32), None, None, None, da, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
+
+
 def test_timing_part_needs_a_timed_call(fc):
     ms = C.c_double(0.0)
     assert fc._lib.cq_timing_part(3, C.byref(ms)) == fc.CQ_EINVAL
