@@ -77,7 +77,8 @@ int cq_timing_last(double *ms_main_kernel);
 /* Parts of the most recent timed call: part 0 = the same as cq_timing_last;
  * part 1 = summed duration of the tensor-core contraction launches of the
  * mixed-precision direct solve (fp2s_solve, CQ_DIRECT with CQ_BF16X3 or
- * CQ_TF32X3; 0 for other calls). Synchronises on the recorded events.
+ * CQ_TF32X3) or of the mixed-precision gradient (0 for other calls).
+ * Synchronises on the recorded events.
  * CQ_EINVAL for another part, a NULL pointer or no timed call yet. */
 int cq_timing_part(int part, double *ms);
 
@@ -209,14 +210,20 @@ int fp2s_step(const fp2s_problem_t *p, int64_t n, void *ws_dev, size_t ws_bytes,
 int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, double *g_dev,
                void *stream);
 /* Gradient of the final-time misfit J = 1/2 h^dim sum_{s,dof} (G_s^N - Gt_s)^2
- * through the direct scheme (form == CQ_DIRECT, prec == CQ_F64; N <= 13000):
- * the discrete adjoint of Eq. 4.1 / Eq. 4.7, i.e. the transposed 2x2 steps run
- * backwards in time with the CQ convolution reversed in time (same weights), and
- * the beta-derivatives of the weights for dJ/dalpha_i = -dJ/dbeta_i.
+ * through the direct scheme (form == CQ_DIRECT; N <= 13000): the discrete adjoint
+ * of Eq. 4.1 / Eq. 4.7, i.e. the transposed 2x2 steps run backwards in time with
+ * the CQ convolution reversed in time (same weights), and the beta-derivatives
+ * of the weights for dJ/dalpha_i = -dJ/dbeta_i.
+ * prec == CQ_F64: FP64 throughout; the workspace holds the forward history and
+ * the adjoint variables, two [N+1][2][M^dim] FP64 arrays.
+ * prec == CQ_BF16X3 / CQ_TF32X3: forward and adjoint sweeps of the
+ * mixed-precision direct solve (FP32 levels, tensor-core histories), with the
+ * weight-derivative history as one more contraction; the workspace holds the
+ * split levels and increments (2 x 2 x N x 2 x M^dim operands) and an FP32
+ * [N][2][M^dim] history. Relative errors of order 1e-4 against the FP64 form.
  * Inputs G0_dev, Gt_dev: physical [2][M^dim]. Outputs: *J_host; dJdG0_dev
  * [2][M^dim] (gradient with respect to the nodal values of G^0); dJdalpha_host[2].
- * The workspace holds the forward history and the adjoint variables, two
- * [N+1][2][M^dim] arrays. Synchronises `stream`. */
+ * Synchronises `stream`. CQ_EUNSUPPORTED for other forms and precisions. */
 int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, double *J_host,
                   double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes, void *stream);
 /* Vector-Jacobian product of the direct solve G^N = fp2s_solve(G^0; alpha1, alpha2):

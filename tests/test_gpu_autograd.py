@@ -8,6 +8,9 @@ its torch.autograd binding (``-m gpu``).
 - dL/dalpha against central differences of the GPU forward solve (step 1e-5, FP64;
   accurate to ~1e-9 relative): 1e-6 relative.
 - torch.autograd.gradcheck on a tiny problem (every G0 entry and both alphas).
+- The mixed-precision binding (prec = CQ_BF16X3) against the FP64 one, within the mixed
+  gradient's bars; dL/dalpha relative to max(|dL/dalpha|, |L|), since a random W can make
+  dL/dalpha small against the terms it sums.
 """
 import numpy as np
 import pytest
@@ -109,3 +112,28 @@ def test_autograd_rejects_bad_input(pkg):
         ag.solve(torch.zeros(2, 7, dtype=torch.float32, device="cuda"), a, m=0.3, T=1.0, N=4, dim=1, M=7)
     with pytest.raises(ValueError):
         ag.solve(torch.zeros(2, 6, dtype=torch.float64, device="cuda"), a, m=0.3, T=1.0, N=4, dim=1, M=7)
+
+
+@pytest.mark.parametrize("p", CASES, ids=["be_1d", "bdf2_1d", "bdf2_2d"])
+def test_autograd_mixed_precision_against_fp64(pkg, p):
+    """prec = CQ_BF16X3: forward and backward through the mixed-precision form; the
+    gradients match the FP64 binding's within the mixed gradient's bars (test_gpu_mixed_gradient)."""
+    fc, ag = pkg
+    rng = ci.rng(78)
+    W = torch.tensor(rng.standard_normal((2, p.M ** p.dim)), dtype=torch.float64, device="cuda")
+    grads, Ls = [], []
+    for prec in (fc.CQ_F64, fc.CQ_BF16X3):
+        G0 = torch.tensor(ci.g0_uniform(p.M, p.dim, 8), dtype=torch.float64, device="cuda", requires_grad=True)
+        alpha = torch.tensor([p.alpha1, p.alpha2], dtype=torch.float64, device="cuda", requires_grad=True)
+        GN = ag.solve(G0, alpha, m=p.m, T=p.T, N=p.N, dim=p.dim, M=p.M, scheme=p.scheme, prec=prec)
+        L = torch.sum(W * GN)
+        L.backward()
+        Ls.append(abs(L.item()))
+        grads.append((GN.detach(), G0.grad, alpha.grad))
+    (g64, dg64, da64), (gmx, dgmx, damx) = grads
+    assert torch.linalg.norm(gmx - g64) <= 1e-4 * torch.linalg.norm(g64)
+    assert torch.linalg.norm(dgmx - dg64) <= 2e-4 * torch.linalg.norm(dg64)
+    assert torch.all(torch.abs(damx - da64) <= 5e-4 * torch.clamp(torch.abs(da64), min=Ls[0]))
+    with pytest.raises(ValueError):
+        ag.solve(torch.zeros(2, p.M ** p.dim, dtype=torch.float64, device="cuda"), torch.tensor([0.3, 0.6]), m=p.m,
+                 T=p.T, N=p.N, dim=p.dim, M=p.M, prec=fc.CQ_F32)
