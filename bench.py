@@ -909,10 +909,17 @@ def run_ours(args, rank, world, dist):
 
 
 def _kernel_hash():
+    """Hash of the source of k_fp2s_fast (its function text in fp2s.cu) and of the headers it
+    uses: a traffic figure recorded under another hash was taken on another kernel."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("fp2s.cu", "fp2s_core.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_1901_05128_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_1901_05128_gb300", "csrc")
+    with open(os.path.join(csrc, "fp2s.cu")) as fh:
+        src = fh.read()
+    i = src.index(" k_fp2s_fast(Fp2sParams P")
+    h.update(src[src.rindex("__global__", 0, i):src.index("\n}\n", i) + 3].encode())
+    for f in ("fp2s_core.cuh", "common.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -362,20 +362,35 @@ static int fast_block_threads(int np, int L, int64_t nmodes) {
 }
 
 // ---------------------------------------------------------------------------
-// Fused fast solve, FP32 precision form. Same mode/lane mapping and step
-// algebra as k_fp2s_fast, but the history-part states Y_j of a lane live in
-// FP32 registers (NP is a compile-time bound; the tables are zero-padded up to
-// it), the tables are FP32 pairs (r_j, c_j) read as float4 from shared memory
-// (state 2's table is offset by 4 words so the half-warps hit different banks),
-// and the history sums are formed in FP32. Weights, quadrature coefficients and
-// the per-mode step matrices are computed in FP64. The step is evaluated from the
-// FP32 history sums in the two-term form x = A l + B e with double-float A and B
-// (lane_step2; FP32 pipe), or in FP64 when the coupling is strong (|a| > 10, i.e.
-// m within ~0.045 of 1/2); the first SBD step uses the double-float form.
-// Every mode is pre-scaled by an exact power of two (from its G^0) so that its
-// values sit near 1 in FP32 range; the factor is undone on output.
+// Fused fast solve, FP32 precision form. Each lane carries one state of TWO
+// modes over HALF of the history-part nodes: lanes l = 16 s + 8 h + q hold state s
+// of the modes 2p, 2p + 1 of pair p = 8 w + q (w the warp) over the nodes of half h.
+// One 16-byte table word (r_j, c_j r_j, r_{j+1}, c_{j+1} r_{j+1}) then feeds both
+// modes (eight FMAs), and the four (half, state) words a load touches are adjacent.
+// The history sum is taken from the states before their update,
+//     h^n = sum_j c_j Y_j^n = sum_j (c_j r_j) Y_j^{n-1} + C G^{n-L},  C = sum_j c_j,
+// so the FMAs of a node do not wait on each other. Per step the two halves add their
+// partial sums with one shuffle per mode, lane h takes the 2x2 step of mode 2p + h with
+// its partner state (lane ^ 16), and the two new levels are exchanged with one shuffle;
+// the exact window (L - 1 terms) is split between the halves by parity. Each lane keeps
+// its own ring of the last L levels of its two modes (float2) in shared memory. The
+// states Y_j live in FP32 registers (NP is a compile-time bound; the tables are
+// zero-padded up to it). Weights, quadrature coefficients and the per-mode step
+// matrices are computed in FP64; the step is evaluated from the FP32 history sums in
+// the two-term form x = A l + B e with double-float A and B (lane_step2), or in FP64
+// when the coupling is strong (|a| > 10, i.e. m within ~0.045 of 1/2); the first SBD
+// step uses the double-float form. Every mode is pre-scaled by an exact power of two
+// (from its G^0) so that its values sit near 1 in FP32 range; the factor is undone on
+// output.
 // ---------------------------------------------------------------------------
 constexpr int kF32Threads = 128;
+
+// The FP64 / first-SBD step of the FP32 form, out of line (it runs on rare steps only).
+__device__ __noinline__ float lane_step_rare(const Fp2sParams P, const LaneStep ls, int solve64, int64_t n, float h,
+                                             float gm1, float gm2, float gz, const double *dn, const float *hd_hi,
+                                             const float *hd_lo) {
+    return lane_step(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
+}
 
 template <int NP>
 __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int solve64,
@@ -387,35 +402,47 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
                                                                const double *__restrict__ tab1,
                                                                const double *__restrict__ tab2,
                                                                const float *__restrict__ hdf) {
+    constexpr int NH = NP / 2;               // nodes per lane
+    constexpr int NQ = NP / 4;               // node pairs per lane
     extern __shared__ __align__(16) float smf[];
     const int np = P.np, L = P.L, T = blockDim.x, tid = threadIdx.x;
-    float *rc0 = smf;                        // [NP] pairs (r_j, c_j), state 1
-    float *rc1 = smf + 2 * NP + 4;           // state 2
-    float *wt = smf + 4 * NP + 8;            // wt[2i + s] = d_i of state s, i < L
-    float *R = wt + 2 * kMaxNs;              // [L][T]
-    for (int j = tid; j < NP; j += T) {
-        const bool in = j < np;
-        rc0[2 * j] = in ? (float)tab1[j] : 0.0f;
-        rc0[2 * j + 1] = in ? (float)tab1[np + j] : 0.0f;
-        rc1[2 * j] = in ? (float)tab2[j] : 0.0f;
-        rc1[2 * j + 1] = in ? (float)tab2[np + j] : 0.0f;
+    float4 *tab4 = reinterpret_cast<float4 *>(smf);                    // [NQ][half][state]
+    float *wt = smf + 4 * NP;                                           // wt[2i + s] = d_i of state s, i < L
+    float *csum = wt + 2 * kMaxNs;                                      // C of each state
+    float2 *R = reinterpret_cast<float2 *>(csum + 2);                  // [L][T]
+    for (int e = tid; e < 4 * NQ; e += T) {
+        const int kk = e >> 2, hf = (e >> 1) & 1, s = e & 1;
+        const int j = 2 * (hf * NQ + kk);
+        const double *tq = s ? tab2 : tab1;
+        tab4[e] = make_float4(j < np ? (float)tq[j] : 0.0f, j < np ? (float)(tq[np + j] * tq[j]) : 0.0f,
+                              j + 1 < np ? (float)tq[j + 1] : 0.0f,
+                              j + 1 < np ? (float)(tq[np + j + 1] * tq[j + 1]) : 0.0f);
     }
     for (int i = tid; i < L; i += T) {
         wt[2 * i] = (float)d1[i];
         wt[2 * i + 1] = (float)d2[i];
     }
-    for (int j = 0; j < L; ++j) R[(size_t)j * T + tid] = 0.0f;
+    if (tid < 2) {
+        const double *tq = tid ? tab2 : tab1;
+        double c = 0.0;
+        for (int j = 0; j < np; ++j) c += tq[np + j];
+        csum[tid] = (float)c;
+    }
+    for (int j = 0; j < L; ++j) R[(size_t)j * T + tid] = make_float2(0.0f, 0.0f);
     __syncthreads();
 
-    const int lane = tid & 31, st = lane >> 4;
-    const int64_t mode_raw = ((int64_t)blockIdx.x * (T >> 5) + (tid >> 5)) * kFastModesPerWarp + (lane & 15);
+    const int lane = tid & 31, st = lane >> 4, hf = (lane >> 3) & 1;
+    const int64_t pair = ((int64_t)blockIdx.x * (T >> 5) + (tid >> 5)) * 8 + (lane & 7);
+    const int64_t mode_raw = 2 * pair + hf;                             // the mode this lane steps
     const bool active = mode_raw < P.nmodes;
     const int64_t mode = active ? mode_raw : 0;
-    const float4 *rc4 = reinterpret_cast<const float4 *>(st ? rc1 : rc0);
+    const float4 *tb = tab4 + (2 * hf + st);
     const float *ws = wt + st;
+    float cs = hf ? 0.0f : csum[st];         // C G^{n-L} enters the sums of half 0 only
+    keep_reg(cs);
     const double *dn = st ? d2 : d1;
     const float *hd_hi = hdf + (size_t)(2 * st) * (P.N + 1), *hd_lo = hd_hi + (P.N + 1);
-    float *Rc = R + tid;
+    float2 *Rc = R + tid;
 
     // per-mode power-of-two scale from max(|g1^0|, |g2^0|)
     const double gz64 = g0[st * P.nmodes + mode];
@@ -429,46 +456,61 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
     if (active && st == 0 && !ok) atomicOr(status, ST_SINGULAR);
     LaneStep2 l2;
     lane_step2_setup(P, ls, l2);
+    keep_reg(l2);
 
-    float Y[NP];
+    float YA[NH], YB[NH];                    // the two modes' states over this lane's nodes
 #pragma unroll
-    for (int j = 0; j < NP; ++j) Y[j] = 0.0f;
+    for (int j = 0; j < NH; ++j) YA[j] = YB[j] = 0.0f;
     float gm1 = gz, gm2 = 0.0f, gm1_o = __shfl_xor_sync(0xffffffffu, gz, 16), gm2_o = 0.0f;
     int slot = 0;
     const int N = (int)P.N;
+    float2 in_next = Rc[(L == 1 ? 0 : 1) * T];          // G^{n-L} of the next step (L >= 2: written before)
     for (int n = 1; n <= N; ++n) {
         slot = (slot + 1 == L) ? 0 : slot + 1;
-        float hp[8];
+        const float2 in = in_next;
+        const int nslot = (slot + 1 == L) ? 0 : slot + 1;
+        in_next = Rc[nslot * T];
+        float hA[4], hB[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) hp[q] = 0.0f;
+        for (int q = 0; q < 4; ++q) hA[q] = hB[q] = 0.0f;
         if (n - L >= 1) {
-            const float in = Rc[slot * T];
+            hA[0] = cs * in.x;
+            hB[0] = cs * in.y;
 #pragma unroll
-            for (int j = 0; j < NP; j += 4) {
-                const float4 p = rc4[j / 2];
-                const float4 q = rc4[j / 2 + 1];
-                const int o = (j / 4) & 1;                    // eight partial sums: shorter chains
-                Y[j] = fmaf(p.x, Y[j], in);
-                Y[j + 1] = fmaf(p.z, Y[j + 1], in);
-                Y[j + 2] = fmaf(q.x, Y[j + 2], in);
-                Y[j + 3] = fmaf(q.z, Y[j + 3], in);
-                hp[4 * o] = fmaf(p.y, Y[j], hp[4 * o]);
-                hp[4 * o + 1] = fmaf(p.w, Y[j + 1], hp[4 * o + 1]);
-                hp[4 * o + 2] = fmaf(q.y, Y[j + 2], hp[4 * o + 2]);
-                hp[4 * o + 3] = fmaf(q.w, Y[j + 3], hp[4 * o + 3]);
+            for (int kk = 0; kk < NQ; ++kk) {
+                const float4 t = tb[4 * kk];
+                const int c = 2 * (kk & 1);                           // four partial sums per mode
+                hA[c] = fmaf(t.y, YA[2 * kk], hA[c]);
+                hB[c] = fmaf(t.y, YB[2 * kk], hB[c]);
+                hA[c + 1] = fmaf(t.w, YA[2 * kk + 1], hA[c + 1]);
+                hB[c + 1] = fmaf(t.w, YB[2 * kk + 1], hB[c + 1]);
+                YA[2 * kk] = fmaf(t.x, YA[2 * kk], in.x);
+                YB[2 * kk] = fmaf(t.x, YB[2 * kk], in.y);
+                YA[2 * kk + 1] = fmaf(t.z, YA[2 * kk + 1], in.x);
+                YB[2 * kk + 1] = fmaf(t.z, YB[2 * kk + 1], in.y);
             }
         }
+        // exact window d_i x^{n-i}, i = 1 .. min(L - 1, n - 1): odd i on half 0, even i on half
+        // 1 (same trip count on both halves; the last term of half 1 may be absent)
         const int imax = min(L - 1, n - 1);
-        int sl = slot;
-        for (int i = 1; i <= imax; ++i) {
-            sl = (sl == 0) ? L - 1 : sl - 1;
-            if (i & 1) hp[1] = fmaf(ws[2 * i], Rc[sl * T], hp[1]);
-            else hp[2] = fmaf(ws[2 * i], Rc[sl * T], hp[2]);
+        for (int q = 0; 2 * q < imax; ++q) {
+            const int i = 2 * q + 1 + hf;
+            int sl = slot - i;
+            if (sl < 0) sl += L;
+            const bool on = i <= imax;
+            const float2 v = Rc[(on ? sl : slot) * T];
+            const float w = on ? ws[2 * i] : 0.0f;
+            hA[3] = fmaf(w, v.x, hA[3]);
+            hB[3] = fmaf(w, v.y, hB[3]);
         }
-        const float h = ((hp[0] + hp[4]) + (hp[1] + hp[5])) + ((hp[2] + hp[6]) + (hp[3] + hp[7]));
+        float sA = (hA[0] + hA[1]) + (hA[2] + hA[3]);
+        float sB = (hB[0] + hB[1]) + (hB[2] + hB[3]);
+        sA += __shfl_xor_sync(0xffffffffu, sA, 8);                   // both halves: same sums
+        sB += __shfl_xor_sync(0xffffffffu, sB, 8);
+        const float h = hf ? sB : sA;
         float x;
         if (solve64 || (P.scheme == CQ_BDF2 && n == 1)) {
-            x = lane_step(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
+            x = lane_step_rare(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
         } else if (P.scheme == CQ_BE) {
             x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, __shfl_xor_sync(0xffffffffu, h, 16), 0.0f);
         } else {
@@ -478,8 +520,9 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
             x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, __shfl_xor_sync(0xffffffffu, e.hi, 16),
                            __shfl_xor_sync(0xffffffffu, e.lo, 16));
         }
-        const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);
-        Rc[slot * T] = x;
+        const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);       // partner state, same mode
+        const float x_p = __shfl_xor_sync(0xffffffffu, x, 8);        // same state, other mode of the pair
+        Rc[slot * T] = hf ? make_float2(x_p, x) : make_float2(x, x_p);
         gm2 = gm1;
         gm1 = x;
         gm2_o = gm1_o;
@@ -493,7 +536,7 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
 }
 
 static size_t f32_smem_bytes(int NP, int L, int T) {
-    return ((size_t)4 * NP + 8 + 2 * kMaxNs + (size_t)L * T) * sizeof(float);
+    return ((size_t)4 * NP + 2 * kMaxNs + 2) * sizeof(float) + (size_t)L * T * sizeof(float2);
 }
 
 template <int NP>

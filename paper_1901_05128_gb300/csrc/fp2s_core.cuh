@@ -248,6 +248,21 @@ __device__ __forceinline__ float lane_step2(const LaneStep2 &c, float l, float l
     return s.hi + (s.lo + ((s12.lo + s34.lo) + r));
 }
 
+// Opaque register barrier: the value is kept as computed. Step coefficients formed in
+// FP64 before a step loop pass through it; otherwise the compiler may recompute them
+// inside the loop to save registers, which puts FP64 work (1/64 of the FP32 rate on
+// this GPU) into every step.
+__device__ __forceinline__ void keep_reg(float &v) { asm volatile("" : "+f"(v)); }
+__device__ __forceinline__ void keep_reg(LaneStep2 &c) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        keep_reg(c.a_hi[i]);
+        keep_reg(c.a_lo[i]);
+        keep_reg(c.b_hi[i]);
+        keep_reg(c.b_lo[i]);
+    }
+}
+
 constexpr int kFastModesPerWarp = 16;     // a warp carries 16 modes x 2 states
 
 // Mixed-precision direct solve (mixed.cu): workspace bytes of its own region, and
