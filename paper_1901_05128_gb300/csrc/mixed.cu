@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     } else {
         coef_load(A.coef, A.nmp, col, l2, gz, ex);
     }
+    keep_reg(l2);
     const double *dn = st ? A.d2 : A.d1;
     const float *hd_hi = A.hdf + (size_t)(2 * st) * (P.N + 1), *hd_lo = hd_hi + (P.N + 1);
 
@@ -440,7 +441,13 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
         coef_load(A.coef, A.nmp, col, l2, rz, ey);
         l2f = l2;
     }
-    const df dc = df_from(P.a + A.lam[mode]), da = df_from(P.a);
+    df dc = df_from(P.a + A.lam[mode]), da = df_from(P.a);
+    keep_reg(dc.hi);
+    keep_reg(dc.lo);
+    keep_reg(da.hi);
+    keep_reg(da.lo);
+    keep_reg(l2);
+    keep_reg(l2f);
     const float *hd_hi = A.hdf + (size_t)(2 * st) * (N + 1);         // d_i / 2 (hi part)
     const float *dq = A.dqf + (size_t)st * (N + 1);                   // d'_i
     const float *cq = A.cqf + (size_t)st * (N + 1);                   // D'_i
