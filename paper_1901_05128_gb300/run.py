@@ -1,9 +1,10 @@
 """Command-line runner: solve one named synthetic workload on the GPU.
 
     python -m paper_1901_05128_gb300.run --workload bdf2_2d_m255 --form fast --repeat 2
+    python -m paper_1901_05128_gb300.run --workload grad_2d_m255 --gradient --prec bf16x3 --scale-exp 0
 
-Prints one line per solve with its wall time and the library status. Useful
-for profiling a single configuration (e.g. under ncu).
+Prints one line per solve (or gradient) with its wall time and the library status.
+Useful for profiling a single configuration (e.g. under ncu).
 """
 from __future__ import annotations
 
@@ -28,6 +29,9 @@ def main(argv=None):
     ap.add_argument("--prec", choices=["f64", "f32", "bf16x3", "tf32x3"], default="f64")
     ap.add_argument("--history", action="store_true",
                     help="run cq_history_direct alone on synthetic N(0,1) levels (--ndof, --n-lo, --n-hi)")
+    ap.add_argument("--gradient", action="store_true",
+                    help="run fp2s_gradient of the workload (direct form) against a target made with "
+                         "alpha + (0.05, -0.05)")
     ap.add_argument("--ndof", type=int, default=65536)
     ap.add_argument("--n-lo", type=int, default=1)
     ap.add_argument("--n-hi", type=int, default=2049)
@@ -54,6 +58,8 @@ def main(argv=None):
                     prec=prec)
     g0 = torch.tensor(G0 * 2.0 ** a.scale_exp, dtype=torch.float64, device="cuda")
     gN = torch.empty_like(g0)
+    if a.gradient:
+        return run_gradient(fc, torch, a, p, cp, g0)
     ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None))
     fc.cq_timing_enable(True)
     for r in range(a.repeat):
@@ -63,6 +69,27 @@ def main(argv=None):
         torch.cuda.synchronize()
         print("solve %d: %.3f s (time-stepping %.3f ms) status=%s"
               % (r, time.perf_counter() - t, fc.cq_timing_last(), fc.strerror(st)))
+
+
+def run_gradient(fc, torch, a, p, cp, g0):
+    """Gradient of 1/2 ||G^N - G_target||^2 (direct form, the run's precision); the target is
+    the FP64 direct solve with alpha + (0.05, -0.05). Prints the time per gradient."""
+    import cq_inputs as ci
+    if p.form != ci.DIRECT:
+        raise SystemExit("--gradient needs the direct form")
+    ct = fc.problem(p.alpha1 + 0.05, p.alpha2 - 0.05, p.m, p.T, p.N, p.dim, p.M, p.scheme, ci.DIRECT)
+    gt = torch.empty_like(g0)
+    fc.fp2s_solve(ct, g0, gt, fc.workspace(fc.fp2s_solve(ct, g0, gt, None)))
+    dg = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_gradient(cp, g0, gt, dg, None))
+    fc.cq_timing_enable(True)
+    for r in range(a.repeat):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        J, da = fc.fp2s_gradient(cp, g0, gt, dg, ws)
+        torch.cuda.synchronize()
+        print("gradient %d: %.3f ms (kernels %.3f ms, contractions %.3f ms) J=%.6e dJ/dalpha=(%.6e, %.6e)"
+              % (r, (time.perf_counter() - t) * 1e3, fc.cq_timing_last(), fc.cq_timing_part(1), J, da[0], da[1]))
 
 
 def run_history(fc, torch, a):
