@@ -264,6 +264,16 @@ def mixed_direct_leg(fc, torch, dev, p, G0, K, W, flush):
         runs.append({"problem": q, "prec": "tf32x3" if prec == fc.CQ_TF32X3 else "bf16x3", "ms": ms,
                      "tc_ms": tc_ms, "status": fc.strerror(fc.fp2s_status(cp, ws)),
                      "launches": (fc.cq_launch_count() - l0) / len(ms), "gN": gN.cpu().numpy()})
+    # the main case's levels at earlier steps n (same tau: N = n, T = n tau), for its per-step error
+    q0 = runs[0]["problem"]
+    partial = {}
+    for n in (q0.N // 8, q0.N // 4, q0.N // 2, 3 * q0.N // 4):
+        qn = q0.replace(N=n, T=q0.T * n / q0.N)
+        cpn = fc.problem(qn.alpha1, qn.alpha2, qn.m, qn.T, qn.N, qn.dim, qn.M, qn.scheme, qn.form, 0, 0, 0,
+                         prec=fc.CQ_BF16X3)
+        fc.fp2s_solve(cpn, g0, gN, ws)
+        partial[n] = gN.cpu().numpy()
+    runs[0]["partial"] = partial
     del ws, g0, gN
     torch.cuda.empty_cache()
     return runs
@@ -374,15 +384,23 @@ def mixed_report(runs, G0, cpu_modes):
                                        ci.sample_indices(nm, max(4, cpu_modes // 8), ci.SEED_BASE + 33)]))
     lam = OSP.mode_eigenvalues(q0.M, q0.dim)[sample]
     g0 = OSP.to_modal(G0, q0.M, q0.dim)[:, sample]
-    cases, t_orc = [], None
+    cases, t_orc, per_step = [], None, None
     for r in runs:
         q = r["problem"]
         t = time.perf_counter()
-        ref = OS.solve_modal(q, lam, g0)[q.N]
+        traj = OS.solve_modal(q, lam, g0)
+        ref = traj[q.N]
         if t_orc is None:
             t_orc = time.perf_counter() - t
         gm = OSP.to_modal(r["gN"], q.M, q.dim)[:, sample]
         err = [float(np.linalg.norm(gm[s] - ref[s]) / np.linalg.norm(ref[s])) for s in range(2)]
+        if "partial" in r:
+            per_step = {}
+            for n, G in sorted(r["partial"].items()):
+                gn = OSP.to_modal(G, q.M, q.dim)[:, sample]
+                per_step[str(n)] = [float(np.linalg.norm(gn[s] - traj[n][s]) / np.linalg.norm(traj[n][s]))
+                                    for s in range(2)]
+            per_step[str(q.N)] = err
         cases.append({"scheme": "BE" if q.scheme == ci.BE else "BDF2", "alpha": [q.alpha1, q.alpha2],
                       "contraction": r["prec"],
                       "ms": statistics.mean(r["ms"]), "status": r["status"],
@@ -412,6 +430,9 @@ def mixed_report(runs, G0, cpu_modes):
                      "algorithmic_flops_per_solve": tc_flops},
         "whole_solve_tensor_equivalent_tflops": 3 * 2.0 * 2 * nm * q.N * (q.N - 1) / 2 / (ms * 1e-3) / 1e12,
         "error_sample": "%d modes (4 lowest + seeded), final step N" % len(sample),
+        "rel_l2_err_vs_fp64_oracle_per_step": per_step,
+        "per_step_note": "main case (BE, alpha = (0.2, 0.8), BF16x3): level n of the N = 8192 run is the final "
+                         "level of the same scheme with N = n and T = n tau",
         "cases": cases,
         "cpu_baseline": {"value": 2 * len(sample) * q.N / t_orc, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "oracle FP64 direct BE scheme, %d modes x %d steps (%.1f s)"
