@@ -622,6 +622,12 @@ def batch_leg(fc, torch, dev, K, flush):
         singles.append(float(np.max(np.abs(np.ldexp(got - ref, -sc)))))
     ms = statistics.mean(times)
     dof_steps = sum(2 * p.M ** p.dim * p.N for p in probs)
+    # algorithmic FP64 flops: per DOF-step 4 np + 2 (L - 1) (node recurrences and sums, exact window)
+    flops = 0.0
+    for p in probs:
+        np_, L = (p.np1, 2) if p.scheme == ci.BE else (p.np1 + p.np2, p.ns)
+        flops += (4 * np_ + 2 * (L - 1)) * 2.0 * p.M ** p.dim * p.N
+    kms = statistics.mean(kern)
     return {
         "workload": "256 seeded instances (alpha ~ U(0.1,0.9), m in [0.30,0.48]U[0.52,0.70], 1D M in [31,1023] "
                     "or 2D M in [31,255] log-uniform, N in [512,8192] log-uniform, BE/BDF2), FP64 fast form, "
@@ -631,6 +637,11 @@ def batch_leg(fc, torch, dev, K, flush):
         "plan_s": plan_s, "gpu_launches_per_solve": launches, "status": status,
         "sum_of_single_solves_ms": t_single, "persistent_launch_efficiency": t_single / ms,
         "max_abs_diff_vs_single_solves_rel_to_instance_max": max(singles),
+        "roofline": {"kernel": "k_b_fast", "bound": "alu", "unit": "TFLOP/s",
+                     "achieved": flops / (kms * 1e-3) / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
+                     "frac": flops / (kms * 1e-3) / FP64_PEAK_NOMINAL, "peak_source": "nominal FP64 rate (recipe)",
+                     "algorithmic_flops_per_launch": flops,
+                     "flops_definition": "sum over instances of (4 np + 2 (L - 1)) x DOF x N"},
     }
 
 
