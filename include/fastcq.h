@@ -215,12 +215,21 @@ int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, dou
  * the CQ convolution reversed in time (same weights), and the beta-derivatives
  * of the weights for dJ/dalpha_i = -dJ/dbeta_i.
  * prec == CQ_F64: FP64 throughout; the workspace holds the forward history and
- * the adjoint variables, two [N+1][2][M^dim] FP64 arrays.
+ * the adjoint variables, two [N+1][2][M^dim] FP64 arrays. Sine modes are
+ * independent, so a smaller workspace is accepted: the forward and adjoint
+ * sweeps then run over slices of modes (the largest multiple of 32 modes whose
+ * two arrays fit), with the same results up to the summation order of J and
+ * dJ/dalpha. Size query (ws_dev == NULL): *ws_bytes == 0 on input returns the
+ * unsliced size; a nonzero *ws_bytes is taken as a cap and the size of the
+ * largest slicing within it is returned (CQ_ENOMEM when one 32-mode slice does
+ * not fit). The same rule picks the slice size from *ws_bytes at run time.
  * prec == CQ_BF16X3 / CQ_TF32X3: forward and adjoint sweeps of the
  * mixed-precision direct solve (FP32 levels, tensor-core histories), with the
  * weight-derivative history as one more contraction; the workspace holds the
  * split levels and increments (2 x 2 x N x 2 x M^dim operands) and an FP32
- * [N][2][M^dim] history. Relative errors of order 1e-4 against the FP64 form.
+ * [N][2][M^dim] history, for all modes (no slicing; a size query returns this
+ * size whatever *ws_bytes holds). Relative errors of order 1e-4 against the
+ * FP64 form.
  * Inputs G0_dev, Gt_dev: physical [2][M^dim]. Outputs: *J_host; dJdG0_dev
  * [2][M^dim] (gradient with respect to the nodal values of G^0); dJdalpha_host[2].
  * Synchronises `stream`. CQ_EUNSUPPORTED for other forms and precisions. */

@@ -35,8 +35,9 @@ struct Fp2sLayout {
     size_t bytes;
 };
 
+// hist_modes: modes of the direct FP64 history (all modes unless a gradient runs in slices).
 static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void *ws, bool stepper,
-                              bool grad = false) {
+                              bool grad = false, int64_t hist_modes = -1) {
     Carve cv(ws);
     Fp2sLayout l{};
     const int64_t nm = P.nmodes;
@@ -58,7 +59,8 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.tmp = cv.take<double>(2 * nm);
     l.g0 = cv.take<double>(2 * nm);
     l.gN = cv.take<double>(2 * nm);
-    if (P.form == CQ_DIRECT && P.prec == CQ_F64) l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
+    if (P.form == CQ_DIRECT && P.prec == CQ_F64)
+        l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
     if (P.prec != CQ_F64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
     if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3))
         l.mixed = cv.take<char>(grad ? mixed_grad_bytes(P) : mixed_direct_bytes(P));
@@ -1302,10 +1304,12 @@ __global__ void __launch_bounds__(32, 12) k_adjoint_direct(
 
 struct GradLayout {
     double *tgt, *mu, *gx0, *q1, *q2, *qz1, *qz2, *dza1, *dza2, *acc;
+    double *cg0, *ctgt, *cgx0, *cgN;     // compact [2][ns] copies of a slice (sliced runs only)
     size_t bytes;
 };
 
-static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void *ws) {
+// ns: modes per slice (the forward history and the adjoint variables hold ns modes).
+static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void *ws, int64_t ns) {
     GradLayout g{};
     Carve cv(ws);
     cv.off = base.bytes;
@@ -1319,9 +1323,45 @@ static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void 
     g.qz2 = cv.take<double>(P.N + 2 * kAdjBT + 1);
     g.dza1 = cv.take<double>(P.N + 2 * kAdjBT + 1);
     g.dza2 = cv.take<double>(P.N + 2 * kAdjBT + 1);
-    g.mu = cv.take<double>((size_t)(P.N + 1) * 2 * nm);
+    g.mu = cv.take<double>((size_t)(P.N + 1) * 2 * ns);
+    if (ns < nm) {
+        g.cg0 = cv.take<double>(2 * ns);
+        g.ctgt = cv.take<double>(2 * ns);
+        g.cgx0 = cv.take<double>(2 * ns);
+        g.cgN = cv.take<double>(2 * ns);
+    }
     g.bytes = cv.bytes();
     return g;
+}
+
+static size_t grad64_bytes(const fp2s_problem_t *p, const Fp2sParams &P, int64_t ns) {
+    const Fp2sLayout l = fp2s_layout(p, P, nullptr, false, false, ns);
+    return grad_layout(P, l, nullptr, ns).bytes;
+}
+
+constexpr int64_t kGradSliceQuantum = 32;    // modes per warp of the forward and adjoint kernels
+
+// Modes per slice of the FP64 gradient for a workspace of `cap` bytes: all modes when the
+// whole problem fits, else the largest multiple of 32 that fits (0: nothing fits).
+static int64_t grad64_slice(const fp2s_problem_t *p, const Fp2sParams &P, size_t cap) {
+    if (grad64_bytes(p, P, P.nmodes) <= cap) return P.nmodes;
+    int64_t lo = 0, hi = (P.nmodes - 1) / kGradSliceQuantum;           // in units of 32 modes
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (grad64_bytes(p, P, mid * kGradSliceQuantum) <= cap) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo * kGradSliceQuantum;
+}
+
+// [2][cnt] <-> rows s * nm + m0 .. + cnt of a [2][nm] array.
+static int copy_slice(double *dst, int64_t ldd, const double *src, int64_t lds, int64_t cnt, cudaStream_t s) {
+    for (int st = 0; st < 2; ++st) {
+        if (cudaMemcpyAsync(dst + st * ldd, src + st * lds, (size_t)cnt * sizeof(double), cudaMemcpyDeviceToDevice,
+                            s) != cudaSuccess)
+            return CQ_ECUDA;
+    }
+    return CQ_OK;
 }
 
 static int weight_derivatives(const Fp2sParams &P, const fp2s_problem_t *p, double *q1, double *q2,
@@ -1392,18 +1432,25 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if (mixed)
         return gradient_mixed(p, P, np1, np2, G0_dev, Gt_dev, vjp, J_host, dJdG0_dev, dJdalpha_host, ws_dev,
                               ws_bytes, (cudaStream_t)stream);
-    Fp2sLayout l = fp2s_layout(p, P, ws_dev, false);
-    GradLayout gl = grad_layout(P, l, ws_dev);
-    if (!ws_dev) { *ws_bytes = gl.bytes; return CQ_OK; }
-    if (*ws_bytes < gl.bytes) return CQ_ENOMEM;
+    // The forward history and the adjoint variables take (N + 1) x 2 x modes each. Modes are
+    // independent, so a workspace that cannot hold them for all modes runs the forward and
+    // adjoint sweeps over slices of modes; a nonzero *ws_bytes in a size query is such a cap.
+    if (!ws_dev) {
+        if (*ws_bytes == 0) { *ws_bytes = grad64_bytes(p, P, P.nmodes); return CQ_OK; }
+        const int64_t ns = grad64_slice(p, P, *ws_bytes);
+        if (ns == 0) return CQ_ENOMEM;
+        *ws_bytes = grad64_bytes(p, P, ns);
+        return CQ_OK;
+    }
+    const int64_t ns = grad64_slice(p, P, *ws_bytes);
+    if (ns == 0) return CQ_ENOMEM;
+    Fp2sLayout l = fp2s_layout(p, P, ws_dev, false, false, ns);
+    GradLayout gl = grad_layout(P, l, ws_dev, ns);
     if (!G0_dev || !Gt_dev || (!vjp && !J_host) || !dJdG0_dev || !dJdalpha_host || ((uintptr_t)ws_dev & 255))
         return CQ_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
-    const unsigned fblocks = (unsigned)((P.nmodes + 31) / 32);
     if ((st = timing_begin(s))) return st;
-    k_fp2s_direct<kDirBT><<<fblocks, 32, 0, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.dz1, l.dz2, l.hist);
-    if ((st = launched())) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, gl.tgt, l.tmp, s))) return st;
     if ((st = weight_derivatives(P, p, gl.q1, gl.q2, s))) return st;
     const unsigned pg = (unsigned)((P.N + 2 * kAdjBT + 256) / 256);
@@ -1417,9 +1464,29 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if ((st = launched(2))) return st;
     if ((st = cuda_status(cudaMemsetAsync(gl.acc, 0, 8 * sizeof(double), s)))) return st;
     const double wd = grid_weight(p);
-    k_adjoint_direct<kAdjBT><<<fblocks, 32, 0, s>>>(P, wd, l.lam, l.d1, l.d2, dzA1, dzA2, gl.q1, gl.q2, gl.qz1,
-                                                    gl.qz2, l.hist, gl.tgt, vjp, gl.mu, gl.gx0, gl.acc);
-    if ((st = launched())) return st;
+    const int64_t nm = P.nmodes;
+    for (int64_t m0 = 0; m0 < nm; m0 += ns) {
+        const int64_t cnt = min(ns, nm - m0);
+        Fp2sParams Ps = P;
+        Ps.nmodes = cnt;
+        const double *g0 = l.g0, *tgt = gl.tgt;
+        double *gN = l.gN, *gx0 = gl.gx0;
+        if (ns < nm) {                      // compact [2][cnt] copies of the slice
+            if ((st = copy_slice(gl.cg0, cnt, l.g0 + m0, nm, cnt, s))) return st;
+            if ((st = copy_slice(gl.ctgt, cnt, gl.tgt + m0, nm, cnt, s))) return st;
+            g0 = gl.cg0;
+            tgt = gl.ctgt;
+            gN = gl.cgN;
+            gx0 = gl.cgx0;
+        }
+        const unsigned fblocks = (unsigned)((cnt + 31) / 32);
+        k_fp2s_direct<kDirBT><<<fblocks, 32, 0, s>>>(Ps, l.lam + m0, g0, gN, l.status, l.d1, l.d2, l.dz1, l.dz2,
+                                                     l.hist);
+        k_adjoint_direct<kAdjBT><<<fblocks, 32, 0, s>>>(Ps, wd, l.lam + m0, l.d1, l.d2, dzA1, dzA2, gl.q1, gl.q2,
+                                                        gl.qz1, gl.qz2, l.hist, tgt, vjp, gl.mu, gx0, gl.acc);
+        if ((st = launched(2))) return st;
+        if (ns < nm && (st = copy_slice(gl.gx0 + m0, nm, gl.cgx0, cnt, cnt, s))) return st;
+    }
     if ((st = timing_end(s))) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, gl.gx0, dJdG0_dev, l.tmp, s))) return st;
     double host[4];

@@ -121,6 +121,27 @@ def test_vjp_host_checks(fc):
     assert fc._lib.fp2s_vjp(C.byref(p), None, None, None, da, 1 << 20, C.byref(sz), None) == fc.CQ_EINVAL
 
 
+def test_gradient_workspace_cap(fc):
+    """FP64 gradient: a nonzero *ws_bytes in the size query is a cap; the library sizes the
+    workspace for the largest slice of modes (a multiple of 32) that fits, or returns
+    CQ_ENOMEM below one slice."""
+    p = fc.problem(0.3, 0.7, 0.4, 1.0, 200, 2, 31, fc.CQ_BDF2, fc.CQ_DIRECT)
+    full = fc.fp2s_gradient(p, None, None, None, None)
+    J = C.c_double(0.0)
+    da = (C.c_double * 2)()
+    sz = C.c_size_t(full // 4)
+    assert fc._lib.fp2s_gradient(C.byref(p), None, None, C.byref(J), None, da, None, C.byref(sz), None) == fc.CQ_OK
+    assert 0 < sz.value <= full // 4
+    hist_slice = 2 * 201 * 2 * 32 * 8                 # forward history + adjoint variables of 32 modes
+    assert sz.value >= hist_slice
+    sz = C.c_size_t(full + 12345)                      # room for everything: the unsliced size
+    assert fc._lib.fp2s_gradient(C.byref(p), None, None, C.byref(J), None, da, None, C.byref(sz), None) == fc.CQ_OK
+    assert sz.value == full
+    sz = C.c_size_t(4096)
+    assert fc._lib.fp2s_gradient(C.byref(p), None, None, C.byref(J), None, da, None, C.byref(sz), None) == \
+        fc.CQ_ENOMEM
+
+
 def test_mixed_gradient_size_query(fc):
     """The mixed-precision gradient keeps every level and the weight-derivative history
     (N x 2 x nmp FP32) beyond what the mixed solve needs; vjp shares the layout."""

@@ -98,3 +98,27 @@ def test_gradient_against_finite_differences(fc, scheme):
         E[s, k] = 1e-4
         fd = (_J_gpu(fc, p, G0 + E, Gt) - _J_gpu(fc, p, G0 - E, Gt)) / 2e-4
         assert abs(dG0[s, k] - fd) <= 1e-6 * np.max(np.abs(dG0))
+
+
+def test_gradient_in_mode_slices(fc):
+    """A workspace too small for all modes: the forward and adjoint sweeps run over slices of
+    modes (independent in the sine basis); same per-mode arithmetic, so dJ/dG0 agrees to
+    rounding and J, dJ/dalpha differ only in the order of their sums."""
+    import ctypes as C
+    p = ci.Problem(0.35, 0.6, 0.4, 1.0, 300, 2, 31, ci.BDF2, ci.DIRECT)
+    G0 = ci.g0_uniform(p.M, p.dim, 41)
+    Gt = 0.5 * ci.g0_uniform(p.M, p.dim, 42)
+    J, dG0, da = _grad(fc, p, G0, Gt)
+    cp = _cp(fc, p)
+    full = fc.fp2s_gradient(cp, None, None, None, None)
+    Jc, dac = C.c_double(0.0), (C.c_double * 2)()
+    sz = C.c_size_t(full // 5)
+    assert fc._lib.fp2s_gradient(C.byref(cp), None, None, C.byref(Jc), None, dac, None, C.byref(sz), None) == fc.CQ_OK
+    ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    g0 = torch.tensor(G0, dtype=torch.float64, device="cuda")
+    gt = torch.tensor(Gt, dtype=torch.float64, device="cuda")
+    dg = torch.empty_like(g0)
+    Js, das = fc.fp2s_gradient(cp, g0, gt, dg, ws)
+    assert abs(Js - J) <= 1e-13 * abs(J)
+    assert np.all(np.abs(np.array(das) - da) <= 1e-12 * np.abs(da))
+    assert np.max(np.abs(dg.cpu().numpy() - dG0)) <= 1e-13 * np.max(np.abs(dG0))
