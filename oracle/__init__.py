@@ -18,7 +18,7 @@ quadrature  Gauss-Jacobi rules and the fast-form coefficients
 history     direct history (Eq. 3.8 / 4.1) and the fast BE / SBD history
             recurrences (Eqs. 3.9-3.10, 3.17-3.18, Remarks 4.1 and 4.7).
 spatial     Dirichlet finite-difference Laplacian, its eigenvalues and the
-            orthonormal DST-I (not specified by the paper).
+            orthonormal DST-I (the paper does not state its spatial discretisation).
 scheme      BE scheme (Eq. 4.1), fast BE (Eq. 4.3), SBD scheme (Eq. 4.7) and
             fast SBD (Eq. 4.8), solved per sine mode by 2x2 Cramer's rule.
 adjoint     gradients of a final-time misfit with respect to G^0 and alpha through

@@ -7,7 +7,7 @@ each history part Y_j = sum_k r_j^k G^{n-k} is advanced with one FP32 rounding p
 about u / sqrt(1 - r_j) relative to |Y_j| (~1e-6 for the slowest parts, 1 - r ~ 1e-4),
 and the weights c_j of those parts are small. The step is contractive for the stable
 problems used here, so the solution error stays at that level: relative L2 error
-<= 2e-5 per state (measured values are recorded in the design doc).
+<= 2e-5 per state (the measured values are printed).
 """
 import numpy as np
 import pytest
