@@ -394,7 +394,49 @@ __device__ __noinline__ float lane_step_rare(const Fp2sParams P, const LaneStep 
     return lane_step(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
 }
 
-template <int NP>
+// Node part of one step (two modes, this lane's half of the nodes): the partial history
+// sums sum_j (c_j r_j) Y_j^{n-1} + C G^{n-L} into hA / hB, then Y_j^n = r_j Y_j^{n-1} + G^{n-L}.
+template <int NQ>
+__device__ __forceinline__ void f32_node_part(const float4 *tb, float cs, float2 in, float (&YA)[2 * NQ],
+                                              float (&YB)[2 * NQ], float (&hA)[4], float (&hB)[4]) {
+    hA[0] = cs * in.x;
+    hB[0] = cs * in.y;
+#pragma unroll
+    for (int q = 1; q < 4; ++q) hA[q] = hB[q] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < NQ; ++kk) {
+        const float4 t = tb[4 * kk];
+        const int c = 2 * (kk & 1);                                   // four partial sums per mode
+        hA[c] = fmaf(t.y, YA[2 * kk], hA[c]);
+        hB[c] = fmaf(t.y, YB[2 * kk], hB[c]);
+        hA[c + 1] = fmaf(t.w, YA[2 * kk + 1], hA[c + 1]);
+        hB[c + 1] = fmaf(t.w, YB[2 * kk + 1], hB[c + 1]);
+        YA[2 * kk] = fmaf(t.x, YA[2 * kk], in.x);
+        YB[2 * kk] = fmaf(t.x, YB[2 * kk], in.y);
+        YA[2 * kk + 1] = fmaf(t.z, YA[2 * kk + 1], in.x);
+        YB[2 * kk + 1] = fmaf(t.z, YB[2 * kk + 1], in.y);
+    }
+}
+
+// Exact window d_i x^{n-i}, i = 1 .. min(L - 1, n - 1), of both modes into hA[3] / hB[3]: odd i
+// on half 0, even i on half 1 (same trip count on both halves; the last term of half 1 may be
+// absent). slot holds x^{n-L} .. and receives x^n.
+__device__ __forceinline__ void f32_window(const float2 *Rc, const float *ws, int T, int L, int slot, int n, int hf,
+                                           float (&hA)[4], float (&hB)[4]) {
+    const int imax = min(L - 1, n - 1);
+    for (int q = 0; 2 * q < imax; ++q) {
+        const int i = 2 * q + 1 + hf;
+        int sl = slot - i;
+        if (sl < 0) sl += L;
+        const bool on = i <= imax;
+        const float2 v = Rc[(on ? sl : slot) * T];
+        const float w = on ? ws[2 * i] : 0.0f;
+        hA[3] = fmaf(w, v.x, hA[3]);
+        hB[3] = fmaf(w, v.y, hB[3]);
+    }
+}
+
+template <int NP, bool BE>
 __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int solve64,
                                                                const double *__restrict__ lam,
                                                                const double *__restrict__ g0,
@@ -464,64 +506,10 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
 #pragma unroll
     for (int j = 0; j < NH; ++j) YA[j] = YB[j] = 0.0f;
     float gm1 = gz, gm2 = 0.0f, gm1_o = __shfl_xor_sync(0xffffffffu, gz, 16), gm2_o = 0.0f;
-    int slot = 0;
     const int N = (int)P.N;
-    float2 in_next = Rc[(L == 1 ? 0 : 1) * T];          // G^{n-L} of the next step (L >= 2: written before)
-    for (int n = 1; n <= N; ++n) {
-        slot = (slot + 1 == L) ? 0 : slot + 1;
-        const float2 in = in_next;
-        const int nslot = (slot + 1 == L) ? 0 : slot + 1;
-        in_next = Rc[nslot * T];
-        float hA[4], hB[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) hA[q] = hB[q] = 0.0f;
-        if (n - L >= 1) {
-            hA[0] = cs * in.x;
-            hB[0] = cs * in.y;
-#pragma unroll
-            for (int kk = 0; kk < NQ; ++kk) {
-                const float4 t = tb[4 * kk];
-                const int c = 2 * (kk & 1);                           // four partial sums per mode
-                hA[c] = fmaf(t.y, YA[2 * kk], hA[c]);
-                hB[c] = fmaf(t.y, YB[2 * kk], hB[c]);
-                hA[c + 1] = fmaf(t.w, YA[2 * kk + 1], hA[c + 1]);
-                hB[c + 1] = fmaf(t.w, YB[2 * kk + 1], hB[c + 1]);
-                YA[2 * kk] = fmaf(t.x, YA[2 * kk], in.x);
-                YB[2 * kk] = fmaf(t.x, YB[2 * kk], in.y);
-                YA[2 * kk + 1] = fmaf(t.z, YA[2 * kk + 1], in.x);
-                YB[2 * kk + 1] = fmaf(t.z, YB[2 * kk + 1], in.y);
-            }
-        }
-        // exact window d_i x^{n-i}, i = 1 .. min(L - 1, n - 1): odd i on half 0, even i on half
-        // 1 (same trip count on both halves; the last term of half 1 may be absent)
-        const int imax = min(L - 1, n - 1);
-        for (int q = 0; 2 * q < imax; ++q) {
-            const int i = 2 * q + 1 + hf;
-            int sl = slot - i;
-            if (sl < 0) sl += L;
-            const bool on = i <= imax;
-            const float2 v = Rc[(on ? sl : slot) * T];
-            const float w = on ? ws[2 * i] : 0.0f;
-            hA[3] = fmaf(w, v.x, hA[3]);
-            hB[3] = fmaf(w, v.y, hB[3]);
-        }
-        float sA = (hA[0] + hA[1]) + (hA[2] + hA[3]);
-        float sB = (hB[0] + hB[1]) + (hB[2] + hB[3]);
-        sA += __shfl_xor_sync(0xffffffffu, sA, 8);                   // both halves: same sums
-        sB += __shfl_xor_sync(0xffffffffu, sB, 8);
-        const float h = hf ? sB : sA;
-        float x;
-        if (solve64 || (P.scheme == CQ_BDF2 && n == 1)) {
-            x = lane_step_rare(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
-        } else if (P.scheme == CQ_BE) {
-            x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, __shfl_xor_sync(0xffffffffu, h, 16), 0.0f);
-        } else {
-            const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
-            // e = h + d_{n-1} g^0 / 2 as a double-float pair
-            const df e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
-            x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, __shfl_xor_sync(0xffffffffu, e.hi, 16),
-                           __shfl_xor_sync(0xffffffffu, e.lo, 16));
-        }
+    float hA[4], hB[4];                      // node part of the current step
+    // the new level x^n of the lane's mode: both halves' levels into the ring, shift the history
+    auto finish = [&](float x, int slot) {
         const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);       // partner state, same mode
         const float x_p = __shfl_xor_sync(0xffffffffu, x, 8);        // same state, other mode of the pair
         Rc[slot * T] = hf ? make_float2(x_p, x) : make_float2(x, x_p);
@@ -529,6 +517,60 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
         gm1 = x;
         gm2_o = gm1_o;
         gm1_o = x_o;
+    };
+    auto combine = [&]() -> float {
+        float sA = (hA[0] + hA[1]) + (hA[2] + hA[3]);
+        float sB = (hB[0] + hB[1]) + (hB[2] + hB[3]);
+        sA += __shfl_xor_sync(0xffffffffu, sA, 8);                   // both halves: same sums
+        sB += __shfl_xor_sync(0xffffffffu, sB, 8);
+        return hf ? sB : sA;
+    };
+    if (solve64) {
+        // strong coupling: every step in FP64 (not pipelined)
+        int slot = 0;
+        for (int n = 1; n <= N; ++n) {
+            slot = (slot + 1 == L) ? 0 : slot + 1;
+            f32_node_part<NQ>(tb, cs, Rc[slot * T], YA, YB, hA, hB);
+            f32_window(Rc, ws, T, L, slot, n, hf, hA, hB);
+            const float h = combine();
+            finish(lane_step_rare(P, ls, 1, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo), slot);
+        }
+    } else {
+        // Software-pipelined: the node part of step n + 1 needs G^{n+1-L} (L >= 2: written at
+        // step n - 1 or earlier) and not x^n, so it sits in the same iteration as the window and
+        // 2x2 step of step n and the two chains interleave.
+        int n = 1, slot = 1 % L;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) hA[q] = hB[q] = 0.0f;           // node part of step 1 (no input yet)
+        if (!BE) {                           // the first SBD step (its own matrix), out of line
+            finish(lane_step_rare(P, ls, 0, 1, combine(), gm1, gm2, gz, dn, hd_hi, hd_lo), slot);
+            n = 2;
+            slot = (slot + 1 == L) ? 0 : slot + 1;
+        }
+        for (; n <= N; ++n) {
+            const int next = (slot + 1 == L) ? 0 : slot + 1;
+            float nA[4], nB[4];
+            f32_node_part<NQ>(tb, cs, Rc[next * T], YA, YB, nA, nB);  // step n + 1
+            f32_window(Rc, ws, T, L, slot, n, hf, hA, hB);              // step n
+            const float h = combine();
+            float x;
+            if (BE) {
+                x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, __shfl_xor_sync(0xffffffffu, h, 16), 0.0f);
+            } else {
+                const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
+                // e = h + d_{n-1} g^0 / 2 as a double-float pair
+                const df e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
+                x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, __shfl_xor_sync(0xffffffffu, e.hi, 16),
+                               __shfl_xor_sync(0xffffffffu, e.lo, 16));
+            }
+            finish(x, slot);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                hA[q] = nA[q];
+                hB[q] = nB[q];
+            }
+            slot = next;
+        }
     }
     if (active) {
         const double out = ldexp((double)gm1, ex);
@@ -546,8 +588,12 @@ static void launch_f32(const Fp2sParams &P, int solve64, const Fp2sLayout &l, cu
     const int T = kF32Threads;
     const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
     const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
-    k_fp2s_fast_f32<NP><<<blocks, T, f32_smem_bytes(NP, P.L, T), s>>>(P, solve64, l.lam, l.g0, l.gN, l.status,
-                                                                      l.d1, l.d2, l.tab1, l.tab2, l.hdf);
+    if (P.scheme == CQ_BE)
+        k_fp2s_fast_f32<NP, true><<<blocks, T, f32_smem_bytes(NP, P.L, T), s>>>(
+            P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.hdf);
+    else
+        k_fp2s_fast_f32<NP, false><<<blocks, T, f32_smem_bytes(NP, P.L, T), s>>>(
+            P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.hdf);
 }
 
 // hdf[(2s)(N+1) + i], hdf[(2s+1)(N+1) + i] = hi, lo of d^s_i / 2
