@@ -104,3 +104,19 @@ def test_history_fast_f32_stream(fc, scheme, beta, np1, np2, ns, ndof, N):
         if n >= 2:
             worst = max(worst, float(np.max(err / (scale + 1e-300))))
     print("f32 stream history: max |err| / sum|d||G| = %.3e" % worst)
+
+
+def test_fp32_forms_report_range_overflow(fc):
+    """m = 0.49 (a = -25.5) on a 2D grid: the lowest mode grows by about 2^550 by t = 1/4, far
+    beyond the FP32 range after its single power-of-two prescale. The FP32 fast solve and the
+    mixed-precision direct solve report CQ_ENONFINITE; the FP64 solve stays finite."""
+    G0 = ci.g0_uniform(15, 2, 9)
+    fast = ci.Problem(0.4, 0.6, 0.49, 0.25, 256, 2, 15, ci.BDF2, ci.FAST, 16, 64, 17)
+    direct = fast.replace(form=ci.DIRECT)
+    g64, st64 = _solve(fc, fast, G0, fc.CQ_F64)
+    assert st64 == fc.CQ_OK and np.all(np.isfinite(g64))
+    assert np.log2(np.max(np.abs(g64))) > 300
+    _, st32 = _solve(fc, fast, G0, fc.CQ_F32)
+    assert st32 == fc.CQ_ENONFINITE
+    _, stmx = _solve(fc, direct, G0, fc.CQ_BF16X3)
+    assert stmx == fc.CQ_ENONFINITE
