@@ -649,6 +649,45 @@ def batch_leg(fc, torch, dev, K, flush):
 PAPER_TIMES = {"table1": {"BE": 78.53, "FBE": 23.95}, "table5": {"SBD": 870.13, "FSBD": 209.44}}
 
 
+def small_leg(fc, torch, dev, K):
+    """The 1D BE workload (63 interior points, N = 1024, FP64 direct): launch- and
+    latency-bound (126 DOF), so only its absolute rate is reported, with its error against
+    the oracle over all 63 modes and the oracle's own time."""
+    import numpy as np
+    import cq_inputs as ci
+    from oracle import scheme as OS
+    p, G0 = ci.workload("be1d_m63")
+    cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns)
+    g0 = torch.tensor(G0, dtype=torch.float64, device=dev)
+    gN = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
+    for _ in range(3):
+        fc.fp2s_solve(cp, g0, gN, ws)
+    times = []
+    for _ in range(K):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fc.fp2s_solve(cp, g0, gN, ws)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    got = gN.cpu().numpy()
+    t = time.perf_counter()
+    ref = OS.solve(p, G0)
+    t_orc = time.perf_counter() - t
+    ms = statistics.mean(times)
+    return {
+        "workload": "be1d_m63: 1D, 63 interior points (126 DOF), T=1, N=1024, BE direct FP64, alpha=(0.3,0.7), "
+                    "m=0.4, G0 = indicator of [1/4,3/4]",
+        "value": p.ndof * p.N / (ms * 1e-3), "unit": UNIT, "ms_per_solve": ms,
+        "note": "launch- and latency-bound (the whole history fits in L2); no roofline fraction",
+        "rel_l2_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+        "cpu_baseline": {"value": p.ndof * p.N / t_orc, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "oracle direct BE scheme, all 63 modes x 1024 steps (%.2f s)" % t_orc},
+    }
+
+
 def paper_leg(fc, torch):
     """Two of the paper's timed runs on the GPU solver: Table 1 (BE / fast BE, h = 1/256,
     1/tau = 1600, alpha = (0.3, 0.6)) and Table 5 (SBD / fast SBD, h = 1/1024, T = 10,
@@ -847,6 +886,7 @@ def run_ours(args, rank, world, dist):
         batch = batch_leg(fc, torch, dev, 2, flush) if (args.precision and rank == 0) else None
         stream = stream_leg(fc, torch, dev) if (args.precision and rank == 0) else None
         paper = paper_leg(fc, torch) if (args.precision and rank == 0) else None
+        small = small_leg(fc, torch, dev, 10) if (args.precision and rank == 0) else None
     clocks = clk.summary()
 
     ms = statistics.mean(steps)
@@ -937,6 +977,8 @@ def run_ours(args, rank, world, dist):
         out["fast_history_stream"] = stream
     if paper is not None:
         out["paper_runs"] = {"note": "the paper's CPU times are on unstated hardware: context only", **paper}
+    if small is not None:
+        out["small_1d"] = small
     return out
 
 
