@@ -220,6 +220,37 @@ __device__ __forceinline__ void store16(double *row, int64_t c0, int64_t ncol, i
     store16(row, c0, ncol, vec2, have, v);
 }
 
+// Geometry of output tile b (tiles of one column tile are consecutive, longest K first).
+struct TileGeom {
+    int state, num_k, nchunks;
+    int64_t m0, n0, brow;
+};
+
+template <int KIND>
+__device__ __forceinline__ TileGeom tile_geom(const TcParams &P, int64_t b) {
+    constexpr int BKK = kind_bk(KIND);
+    constexpr int CHUNK = CHUNK_LEVELS / BKK;
+    TileGeom g;
+    const int64_t ntile = b / P.num_i;
+    g.state = (int)(ntile / P.ntile_state);
+    const int nt = (int)(ntile % P.ntile_state);
+    const int it = P.num_i - 1 - (int)(b % P.num_i);
+    g.m0 = P.n_lo + (int64_t)it * BM;                      // first step of the tile
+    g.n0 = (int64_t)nt * BN;                               // first DOF of the tile (within its state)
+    g.brow = (int64_t)g.state * P.state_stride + g.n0;     // first row of the levels operand
+    const int64_t m_last = min(g.m0 + BM - 1, P.n_lo + P.rows - 1);
+    // levels k' < m_last - 1 contribute (k = k' + 1 <= m_last - 1)
+    const int64_t k_end = min((int64_t)P.kprime, m_last - 1);
+    g.num_k = k_end > P.k_lo ? (int)((k_end - P.k_lo + BKK - 1) / BKK) : 0;
+    g.nchunks = (g.num_k + CHUNK - 1) / CHUNK;
+    return g;
+}
+
+// A CTA takes the output tiles blockIdx.x, blockIdx.x + gridDim.x, ...: one tile when the
+// grid has a CTA per tile, several when the host launches fewer CTAs (tiles of equal K:
+// one CTA per SM, the next tile's loads and MMAs overlapping the previous tile's epilogue).
+// Stages and accumulator chunks are counted across the CTA's tiles, so the mbarrier phases
+// run on without a reset between tiles.
 template <typename OutT, int KIND>
 __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant__ TcMaps maps, TcParams P,
                                                           OutT *__restrict__ H, int *__restrict__ status) {
@@ -236,21 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
     int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);   // [0]: abort, [1]: always 0
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t b = blockIdx.x;
-    const int64_t ntile = b / P.num_i;
-    const int state = (int)(ntile / P.ntile_state);
-    const int nt = (int)(ntile % P.ntile_state);
-    const int it = P.num_i - 1 - (int)(b % P.num_i);          // longest K range first
-    const int64_t m0 = P.n_lo + (int64_t)it * BM;              // first step of the tile
-    const int64_t n0 = (int64_t)nt * BN;                       // first DOF of the tile (within its state)
-    const int64_t brow = (int64_t)state * P.state_stride + n0; // first row of the levels operand
-    const CUtensorMap *tA_hi = &maps.a_hi[state], *tA_lo = &maps.a_lo[state];
-    const CUtensorMap *tB_hi = &maps.b_hi, *tB_lo = &maps.b_lo;
-    const int64_t m_last = min(m0 + BM - 1, P.n_lo + P.rows - 1);
-    // levels k' < m_last - 1 contribute (k = k' + 1 <= m_last - 1)
-    const int64_t k_end = min((int64_t)P.kprime, m_last - 1);
-    const int num_k = k_end > P.k_lo ? (int)((k_end - P.k_lo + BKK - 1) / BKK) : 0;
-    const int nchunks = (num_k + CHUNK - 1) / CHUNK;
+    const int64_t total = P.ntile_state * P.n_states * P.num_i;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -278,69 +295,89 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
     const uint32_t tmem = *tmem_holder;
 
     const bool aborted = *(volatile int *)abort_flag != 0;
-    if (warp == 0 && lane == 0 && num_k > 0 && !aborted) {
+    if (warp == 0 && lane == 0 && !aborted) {
         // ---------------- TMA producer
-        int armed[STAGES];
+        int64_t armed[STAGES];
         for (int i = 0; i < STAGES; ++i) armed[i] = -1;
-        for (int ks = 0; ks < num_k; ++ks) {
-            const int s = ks % STAGES;
-            const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u, WAIT_NS, status)) {
-                atomicOr(status, ST_TIMEOUT);
-                *(volatile int *)abort_flag = 1;
-                break;
+        int64_t gks = 0;                                  // stages issued by this CTA so far
+        bool stop = false;
+        for (int64_t b = blockIdx.x; b < total && !stop; b += gridDim.x) {
+            const TileGeom g = tile_geom<KIND>(P, b);
+            const CUtensorMap *tA_hi = &maps.a_hi[g.state], *tA_lo = &maps.a_lo[g.state];
+            for (int ks = 0; ks < g.num_k; ++ks, ++gks) {
+                const int s = (int)(gks % STAGES);
+                const uint32_t ph = (uint32_t)(gks / STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u, WAIT_NS, status)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    *(volatile int *)abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                if (*(volatile int *)abort_flag) {
+                    stop = true;
+                    break;
+                }
+                unsigned char *st = smem + s * STAGE_BYTES;
+                const int kc = P.k_lo + ks * BKK;                 // first level column of the stage
+                const int64_t delta = g.m0 - 1 - (int64_t)kc;
+                const int arow = (int)((delta - P.delta0) / BKK) * BM;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                tma_load_2d(st, tA_hi, &full[s], 0, arow);
+                tma_load_2d(st + A_BYTES, tA_lo, &full[s], 0, arow);
+                tma_load_2d(st + 2 * A_BYTES, &maps.b_hi, &full[s], kc, (int)g.brow);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.b_lo, &full[s], kc, (int)g.brow);
+                armed[s] = gks;
             }
-            if (*(volatile int *)abort_flag) break;
-            unsigned char *st = smem + s * STAGE_BYTES;
-            const int kc = P.k_lo + ks * BKK;                 // first level column of the stage
-            const int64_t delta = m0 - 1 - (int64_t)kc;
-            const int arow = (int)((delta - P.delta0) / BKK) * BM;
-            mbar_expect_tx(&full[s], STAGE_BYTES);
-            tma_load_2d(st, tA_hi, &full[s], 0, arow);
-            tma_load_2d(st + A_BYTES, tA_lo, &full[s], 0, arow);
-            tma_load_2d(st + 2 * A_BYTES, tB_hi, &full[s], kc, (int)brow);
-            tma_load_2d(st + 2 * A_BYTES + B_BYTES, tB_lo, &full[s], kc, (int)brow);
-            armed[s] = ks;
         }
         if (*(volatile int *)abort_flag) {
             // drain the loads this thread started before the CTA releases its shared memory
             for (int i = 0; i < STAGES; ++i)
                 if (armed[i] >= 0) (void)mbar_wait(&full[i], (uint32_t)(armed[i] / STAGES) & 1u, WAIT_NS, abort_flag + 1);
         }
-    } else if (warp == 1 && lane == 0 && num_k > 0 && !aborted) {
-        // ---------------- MMA issuer: chunk c of CHUNK stages goes to accumulator buffer c & 1,
-        // starting from zero, once the epilogue has read back that buffer's previous chunk
-        for (int ks = 0; ks < num_k; ++ks) {
-            const int s = ks % STAGES;
-            const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
-            const int c = ks / CHUNK, buf = c & 1;
-            if (ks % CHUNK == 0) {
-                if (!mbar_wait(&tempty[buf], ((uint32_t)(c >> 1) & 1u) ^ 1u, WAIT_NS, status) ||
-                    *(volatile int *)abort_flag) {
+    } else if (warp == 1 && lane == 0 && !aborted) {
+        // ---------------- MMA issuer: chunk c (counted over the CTA's tiles) of CHUNK stages goes
+        // to accumulator buffer c & 1, starting from zero, once the epilogue has read back that
+        // buffer's previous chunk
+        int64_t gks = 0, gc = 0;
+        bool stop = false;
+        for (int64_t b = blockIdx.x; b < total && !stop; b += gridDim.x) {
+            const TileGeom g = tile_geom<KIND>(P, b);
+            for (int ks = 0; ks < g.num_k; ++ks, ++gks) {
+                const int s = (int)(gks % STAGES);
+                const uint32_t ph = (uint32_t)(gks / STAGES) & 1u;
+                const int64_t c = gc + ks / CHUNK;
+                const int buf = (int)(c & 1);
+                if (ks % CHUNK == 0) {
+                    if (!mbar_wait(&tempty[buf], ((uint32_t)(c >> 1) & 1u) ^ 1u, WAIT_NS, status) ||
+                        *(volatile int *)abort_flag) {
+                        atomicOr(status, ST_TIMEOUT);
+                        *(volatile int *)abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                }
+                if (!mbar_wait(&full[s], ph, WAIT_NS, status) || *(volatile int *)abort_flag) {
                     atomicOr(status, ST_TIMEOUT);
                     *(volatile int *)abort_flag = 1;
+                    stop = true;
                     break;
                 }
-            }
-            if (!mbar_wait(&full[s], ph, WAIT_NS, status) || *(volatile int *)abort_flag) {
-                atomicOr(status, ST_TIMEOUT);
-                *(volatile int *)abort_flag = 1;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
-            const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+                const uint32_t acc = tmem + (uint32_t)(buf * BN);
 #pragma unroll
-            for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
-                const uint32_t off = kk * 32;            // one MMA: 32 bytes along K (16 BF16 or 8 TF32)
-                const uint32_t acc0 = (ks % CHUNK > 0 || kk > 0) ? 1u : 0u;
-                umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
-                umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
-                umma<KIND>(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+                for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
+                    const uint32_t off = kk * 32;            // one MMA: 32 bytes along K (16 BF16 or 8 TF32)
+                    const uint32_t acc0 = (ks % CHUNK > 0 || kk > 0) ? 1u : 0u;
+                    umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
+                    umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+                    umma<KIND>(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+                }
+                umma_commit(&empty[s]);                       // stage reusable once these MMAs are done
+                if (ks % CHUNK == CHUNK - 1 || ks == g.num_k - 1) umma_commit(&tfull[buf]);
             }
-            umma_commit(&empty[s]);                       // stage reusable once these MMAs are done
-            if (ks % CHUNK == CHUNK - 1 || ks == num_k - 1) umma_commit(&tfull[buf]);
+            gc += g.nchunks;
         }
         umma_commit(drain);                               // everything issued above has completed
     } else if (warp >= 2) {
@@ -350,40 +387,48 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
         const int q = warp & 3;                           // TMEM lane quarter this warp may access
         const int half = (warp - 2) >> 2;                 // columns [128 half, 128 half + 128)
         const int row = q * 32 + lane;
-        const int64_t m = m0 + row;
-        const bool row_ok = m < P.n_lo + P.rows;
         bool have = !aborted;
-        float accr[BN / 2];
+        int64_t gc = 0;
+        for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+            const TileGeom g = tile_geom<KIND>(P, b);
+            const int64_t m = g.m0 + row;
+            const bool row_ok = m < P.n_lo + P.rows;
+            float accr[BN / 2];
 #pragma unroll
-        for (int i = 0; i < BN / 2; ++i) accr[i] = 0.0f;
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c & 1;
-            if (have) {
-                have = mbar_wait(&tfull[buf], (uint32_t)(c >> 1) & 1u, WAIT_NS, status);
-                if (!have) {
-                    atomicOr(status, ST_TIMEOUT);
-                    *(volatile int *)abort_flag = 1;
+            for (int i = 0; i < BN / 2; ++i) accr[i] = 0.0f;
+            for (int c = 0; c < g.nchunks; ++c) {
+                const int64_t cc = gc + c;
+                const int buf = (int)(cc & 1);
+                if (have) {
+                    have = mbar_wait(&tfull[buf], (uint32_t)(cc >> 1) & 1u, WAIT_NS, status);
+                    if (!have) {
+                        atomicOr(status, ST_TIMEOUT);
+                        *(volatile int *)abort_flag = 1;
+                    }
                 }
-            }
-            if (have) {
-                tc_fence_after();
-                const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + half * (BN / 2));
+                if (have) {
+                    tc_fence_after();
+                    const uint32_t base =
+                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + half * (BN / 2));
 #pragma unroll
-                for (int j = 0; j < BN / 2; j += 16) {
-                    float v[16];
-                    tmem_ld16(base + (uint32_t)j, v);
+                    for (int j = 0; j < BN / 2; j += 16) {
+                        float v[16];
+                        tmem_ld16(base + (uint32_t)j, v);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) accr[j + i] += v[i];
+                        for (int i = 0; i < 16; ++i) accr[j + i] += v[i];
+                    }
+                    tc_fence_before();
                 }
-                tc_fence_before();
+                mbar_arrive(&tempty[buf]);
             }
-            mbar_arrive(&tempty[buf]);
-        }
-        OutT *hrow = H + (m - P.n_lo) * P.ldh + (int64_t)state * P.state_stride;
-        if (row_ok) {
+            gc += g.nchunks;
+            OutT *hrow = H + (m - P.n_lo) * P.ldh + (int64_t)g.state * P.state_stride;
+            if (row_ok) {
 #pragma unroll
-            for (int j = 0; j < BN / 2; j += 16)
-                store16(hrow, n0 + half * (BN / 2) + j, P.ndof, P.vec2, have, accr + j, P.add);
+                for (int j = 0; j < BN / 2; j += 16)
+                    store16(hrow, g.n0 + half * (BN / 2) + j, P.ndof, P.vec2, have, accr + j, P.add);
+            }
+            if (!have) break;                             // this tile holds NaN; the grid is draining
         }
     }
     tc_fence_before();
@@ -391,7 +436,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
     if (warp == 1) {
         tc_fence_after();
         // nothing may still write tensor memory when it is freed
-        if (num_k > 0 && !aborted && lane == 0) (void)mbar_wait(drain, 0, WAIT_NS, abort_flag + 1);
+        if (!aborted && lane == 0) (void)mbar_wait(drain, 0, WAIT_NS, abort_flag + 1);
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
@@ -586,7 +631,7 @@ int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, 
     maps.a_lo[1] = maps.a_lo[0];
     if ((st = tc_map_levels(kind, &maps.b_hi, l.g_hi, l.kpad, ndof))) return st;
     if ((st = tc_map_levels(kind, &maps.b_lo, l.g_lo, l.kpad, ndof))) return st;
-    TcParams P;
+    TcParams P{};
     P.ndof = ndof;
     P.n_lo = n_lo;
     P.rows = n_hi - n_lo;
@@ -635,8 +680,9 @@ int tc_map_levels(int kind, CUtensorMap *m, const void *levels, int64_t kpad, in
 
 int tc_contract_f32(int kind, const tc::TcMaps &maps, const tc::TcParams &P, float *H, int *status, cudaStream_t s) {
     using namespace tc;
-    const int64_t blocks = P.ntile_state * P.n_states * P.num_i;
-    if (blocks <= 0 || blocks > 0x7fffffffLL) return CQ_EUNSUPPORTED;
+    const int64_t tiles = P.ntile_state * P.n_states * P.num_i;
+    if (tiles <= 0 || tiles > 0x7fffffffLL) return CQ_EUNSUPPORTED;
+    const int64_t blocks = P.max_ctas > 0 ? min(tiles, P.max_ctas) : tiles;
     int st;
     if ((st = tc_attr())) return st;
     if (kind == TC_TF32X3)

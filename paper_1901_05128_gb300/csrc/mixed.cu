@@ -690,6 +690,7 @@ static int mixed_sweep(const Fp2sParams &P, const MixedLayout &l, const tc::TcMa
     const int64_t mpb = (kMxT / 32) * kFastModesPerWarp;
     const unsigned grid = (unsigned)((P.nmodes + mpb - 1) / mpb);
     tc::TcParams T = mixed_tc_params(P, l);
+    T.max_ctas = device_sms();          // every tile of a launch has the same K: one CTA per SM
     auto contract = [&](int64_t n_lo, int64_t rows, int64_t k_lo, int64_t k_hi, float *out, int add) -> int {
         T.n_lo = n_lo;
         T.add = add;

@@ -37,6 +37,8 @@ struct TcParams {
     int n_states;              // 1, or 2 (two weight sequences on two halves of the DOFs)
     int64_t ntile_state;       // DOF tiles per state
     int64_t state_stride;      // levels rows and output columns of state s start at s * state_stride
+    int64_t max_ctas;          // 0: one CTA per output tile; else at most this many CTAs, each taking
+                               // every max_ctas-th tile (for launches whose tiles have equal K)
 };
 
 // Tensor maps of one contraction: per state the Toeplitz bank (hi, lo); the levels (hi, lo).
