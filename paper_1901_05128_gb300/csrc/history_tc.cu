@@ -50,7 +50,8 @@ constexpr int EPI_WARPS = 8;                // two warps per TMEM lane quarter, 
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int TMEM_COLS = 512;              // two 128 x 256 FP32 accumulators
 constexpr int CHUNK_LEVELS = 128;          // levels accumulated per tensor-memory pass
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int STG_FLOATS = 32 * 33;          // per epilogue warp: a 32 x 32 block, padded rows
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (size_t)EPI_WARPS * STG_FLOATS * 4;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -220,6 +221,15 @@ __device__ __forceinline__ void store16(double *row, int64_t c0, int64_t ncol, i
     store16(row, c0, ncol, vec2, have, v);
 }
 
+// One output element. Add mode (FP32 output only): a reduction without return value; each
+// element receives exactly one addition per launch, so the sum is that of a load-add-store,
+// without holding the old value or waiting for it.
+__device__ __forceinline__ void store1(float *dst, float v, int add) {
+    if (add) atomicAdd(dst, v);
+    else *dst = v;
+}
+__device__ __forceinline__ void store1(double *dst, float v, int) { *dst = f32_to_f64_bits(v); }
+
 // Geometry of output tile b (tiles of one column tile are consecutive, longest K first).
 struct TileGeom {
     int state, num_k, nchunks;
@@ -387,6 +397,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
         const int q = warp & 3;                           // TMEM lane quarter this warp may access
         const int half = (warp - 2) >> 2;                 // columns [128 half, 128 half + 128)
         const int row = q * 32 + lane;
+        float *stg = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * STG_FLOATS;
         bool have = !aborted;
         int64_t gc = 0;
         for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
@@ -422,11 +433,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
                 mbar_arrive(&tempty[buf]);
             }
             gc += g.nchunks;
-            OutT *hrow = H + (m - P.n_lo) * P.ldh + (int64_t)g.state * P.state_stride;
-            if (row_ok) {
+            (void)row_ok;
+            // the warp's 32 rows x 128 columns, in 32 x 32 blocks transposed through shared
+            // memory so that each store instruction writes 32 consecutive columns of one row
+            const int64_t row0 = g.m0 + q * 32;
+            OutT *hbase = H + (row0 - P.n_lo) * P.ldh + (int64_t)g.state * P.state_stride;
+            const float nanf_ = __int_as_float(0x7fc00000);
 #pragma unroll
-                for (int j = 0; j < BN / 2; j += 16)
-                    store16(hrow, g.n0 + half * (BN / 2) + j, P.ndof, P.vec2, have, accr + j, P.add);
+            for (int j = 0; j < BN / 2; j += 32) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = have ? accr[j + i] : nanf_;
+                __syncwarp();
+                const int64_t col = g.n0 + half * (BN / 2) + j + lane;
+                const int rmax = (int)min((int64_t)32, P.n_lo + P.rows - row0);
+                if (col < P.ndof) {
+#pragma unroll 8
+                    for (int r = 0; r < 32; ++r)
+                        if (r < rmax) store1(hbase + (int64_t)r * P.ldh + col, stg[r * 33 + lane], P.add);
+                }
+                __syncwarp();
             }
             if (!have) break;                             // this tile holds NaN; the grid is draining
         }
