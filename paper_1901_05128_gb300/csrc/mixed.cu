@@ -295,6 +295,8 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     keep_reg(l2);
     const double *dn = st ? A.d2 : A.d1;
     const float *hd_hi = A.hdf + (size_t)(2 * st) * (P.N + 1), *hd_lo = hd_hi + (P.N + 1);
+    const float *hdo_hi = A.hdf + (size_t)(2 * (1 - st)) * (P.N + 1), *hdo_lo = hdo_hi + (P.N + 1);
+    const float gz_o = __shfl_xor_sync(0xffffffffu, gz, 16);      // the partner state's scaled g^0
 
     float gm1 = gz, gm2 = 0.0f;
     if (A.n0 > 1) {
@@ -336,10 +338,13 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
                 x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, __shfl_xor_sync(0xffffffffu, h, 16), 0.0f);
             } else {
                 const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
-                // e = h + d_{n-1} g^0 / 2 as a double-float pair
-                const df e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
-                x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, __shfl_xor_sync(0xffffffffu, e.hi, 16),
-                               __shfl_xor_sync(0xffffffffu, e.lo, 16));
+                // e = h + d_{n-1} g^0 / 2 as a double-float pair, for this lane's state and (from the
+                // partner's h and g^0, with the same operations) for the partner's: one shuffle
+                const df ed = df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz);
+                const df edo = df_mul_f(df{__ldg(hdo_hi + n - 1), __ldg(hdo_lo + n - 1)}, gz_o);
+                const df e = df_add(ed, df{h, 0.0f});
+                const df e_o = df_add(edo, df{__shfl_xor_sync(0xffffffffu, h, 16), 0.0f});
+                x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, e_o.hi, e_o.lo);
             }
 #pragma unroll
             for (int bb = b + 1; bb < kMxSB; ++bb) a[bb] = fmaf(wt[bb - b], x, a[bb]);
