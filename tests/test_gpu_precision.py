@@ -48,6 +48,8 @@ F32_CASES = [
     ("be_2d_np128", ci.Problem(0.6, 0.3, 0.2, 1.0, 1500, 2, 15, ci.BE, ci.FAST, 128, 0, 2)),
     ("bdf2_1d_np5", ci.Problem(0.7, 0.4, 0.6, 1.0, 300, 1, 9, ci.BDF2, ci.FAST, 2, 3, 5)),
     ("be_3d", ci.Problem(0.4, 0.7, 0.3, 1.0, 400, 3, 11, ci.BE, ci.FAST, 64, 0, 2)),
+    ("bdf2_2d_ns32_max_window", ci.Problem(0.35, 0.55, 0.4, 1.0, 700, 2, 13, ci.BDF2, ci.FAST, 16, 48, 32)),
+    ("bdf2_1d_ns3_min_window", ci.Problem(0.45, 0.65, 0.35, 1.0, 500, 1, 33, ci.BDF2, ci.FAST, 8, 24, 3)),
 ]
 
 
