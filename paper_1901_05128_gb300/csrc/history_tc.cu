@@ -177,50 +177,6 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
     return __longlong_as_double((long long)bits);
 }
 
-// Store 16 accumulator values of one row at columns c0.. (NaN when the MMA result is missing).
-__device__ __forceinline__ void store16(double *row, int64_t c0, int64_t ncol, int vec2, bool have, const float *v) {
-    const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    if (vec2 && c0 + 16 <= ncol) {
-#pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-            const double2 pr = have ? make_double2(f32_to_f64_bits(v[i]), f32_to_f64_bits(v[i + 1]))
-                                    : make_double2(nan, nan);
-            *reinterpret_cast<double2 *>(row + c0 + i) = pr;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-            if (c0 + i < ncol) row[c0 + i] = have ? f32_to_f64_bits(v[i]) : nan;
-    }
-}
-
-// FP32 output; add (the output already holds a partial sum) adds the row to it.
-__device__ __forceinline__ void store16(float *row, int64_t c0, int64_t ncol, int vec2, bool have, const float *v,
-                                        int add) {
-    const float nan = __int_as_float(0x7fc00000);
-    if (vec2 && c0 + 16 <= ncol) {
-#pragma unroll
-        for (int i = 0; i < 16; i += 4) {
-            float4 *dst = reinterpret_cast<float4 *>(row + c0 + i);
-            float4 o = have ? make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]) : make_float4(nan, nan, nan, nan);
-            if (add) {
-                const float4 old = *dst;
-                o = make_float4(o.x + old.x, o.y + old.y, o.z + old.z, o.w + old.w);
-            }
-            *dst = o;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-            if (c0 + i < ncol) row[c0 + i] = (have ? v[i] : nan) + (add ? row[c0 + i] : 0.0f);
-    }
-}
-
-__device__ __forceinline__ void store16(double *row, int64_t c0, int64_t ncol, int vec2, bool have, const float *v,
-                                        int) {
-    store16(row, c0, ncol, vec2, have, v);
-}
-
 // One output element. Add mode (FP32 output only): a reduction without return value; each
 // element receives exactly one addition per launch, so the sum is that of a load-add-store,
 // without holding the old value or waiting for it.
@@ -396,14 +352,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
         // rounds toward zero; summing chunks here keeps that bias to one chunk's worth)
         const int q = warp & 3;                           // TMEM lane quarter this warp may access
         const int half = (warp - 2) >> 2;                 // columns [128 half, 128 half + 128)
-        const int row = q * 32 + lane;
         float *stg = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * STG_FLOATS;
         bool have = !aborted;
         int64_t gc = 0;
         for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
             const TileGeom g = tile_geom<KIND>(P, b);
-            const int64_t m = g.m0 + row;
-            const bool row_ok = m < P.n_lo + P.rows;
             float accr[BN / 2];
 #pragma unroll
             for (int i = 0; i < BN / 2; ++i) accr[i] = 0.0f;
@@ -433,7 +386,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
                 mbar_arrive(&tempty[buf]);
             }
             gc += g.nchunks;
-            (void)row_ok;
             // the warp's 32 rows x 128 columns, in 32 x 32 blocks transposed through shared
             // memory so that each store instruction writes 32 consecutive columns of one row
             const int64_t row0 = g.m0 + q * 32;
@@ -661,7 +613,6 @@ int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, 
     P.n_lo = n_lo;
     P.rows = n_hi - n_lo;
     P.ldh = ldh;
-    P.vec2 = (ldh % 2 == 0) && ((uintptr_t)H % 16 == 0);
     P.num_i = (int)((P.rows + BM - 1) / BM);
     P.delta0 = l.delta0;
     P.kprime = kprime;

@@ -672,7 +672,6 @@ static tc::TcParams mixed_tc_params(const Fp2sParams &P, const MixedLayout &l) {
     tc::TcParams T{};
     T.ndof = P.nmodes;
     T.ldh = 2 * l.nmp;
-    T.vec2 = 1;                         // ldh and the state offset are multiples of 4 floats
     T.num_i = 1;
     T.delta0 = tc::kind_bk(l.kind);
     T.n_states = 2;

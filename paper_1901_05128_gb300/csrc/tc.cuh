@@ -28,7 +28,6 @@ constexpr int BK = 64;                      // BF16 levels per stage (kind_bk(TC
 // k_lo is a multiple of 64.
 struct TcParams {
     int64_t ndof, n_lo, rows, ldh;
-    int vec2;                  // output rows 16-byte aligned: vector stores
     int num_i;                 // tiles along the steps
     int64_t delta0;            // delta of bank tile 0
     int kprime;                // levels k_lo + 1 .. kprime contribute
