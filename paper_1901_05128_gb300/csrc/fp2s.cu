@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
     for (int j = 0; j < NH; ++j) YA[j] = YB[j] = 0.0f;
     float gm1 = gz, gm2 = 0.0f, gm1_o = __shfl_xor_sync(0xffffffffu, gz, 16), gm2_o = 0.0f;
     const int N = (int)P.N;
-    float hA[4], hB[4];                      // node part of the current step
+    float hA[4] = {}, hB[4] = {};            // node part of the current step
     // the new level x^n of the lane's mode: both halves' levels into the ring, shift the history
     auto finish = [&](float x, int slot) {
         const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);       // partner state, same mode
