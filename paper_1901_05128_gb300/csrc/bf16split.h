@@ -18,47 +18,41 @@
 #define BF16SPLIT_FN static inline
 #endif
 
-BF16SPLIT_FN int bf16split_clz64(uint64_t a) {
+BF16SPLIT_FN int bf16split_clz32(uint32_t a) {
 #if defined(__CUDA_ARCH__)
-    return __clzll((long long)a);
+    return __clz((int)a);
 #else
-    return a ? __builtin_clzll(a) : 64;
+    return a ? __builtin_clz(a) : 32;
 #endif
 }
 
-// Round the magnitude a (> 0) times 2^scale to a BF16 with sign bit s.
-// a has at most 63 significant bits.
-BF16SPLIT_FN uint16_t bf16split_round(uint64_t a, int scale, uint32_t s) {
-    const int nb = 64 - bf16split_clz64(a);            // bit length of a
-    int shift = nb - 8;                                 // keep 8 significant bits
-    uint64_t q;
-    if (shift > 0) {
-        q = a >> shift;
-        const uint64_t rem = a & ((1ull << shift) - 1ull);
-        const uint64_t half = 1ull << (shift - 1);
-        if (rem > half || (rem == half && (q & 1ull))) ++q;
-        if (q == 256ull) {                              // carried into a new bit
-            q = 128ull;
-            ++shift;
-        }
-    } else {
-        q = a << (-shift);
+// BF16 bits with sign s of the value q * 2^(e - 127 - 7), q in [128, 256] (256 carries into the
+// exponent); zero below the normal range, Inf above it.
+BF16SPLIT_FN uint16_t bf16split_pack(uint32_t q, int e, uint32_t s) {
+    if (q == 256u) {
+        q = 128u;
+        ++e;
     }
-    // value = q * 2^(scale + shift), q in [128, 255]; BF16 exponent field = unbiased + 127
-    const int e = scale + shift + 7 + 127;
-    if (e <= 0) return (uint16_t)(s << 15);             // below the normal range
+    if (e <= 0) return (uint16_t)(s << 15);
     if (e >= 255) return (uint16_t)((s << 15) | 0x7f80u);
-    return (uint16_t)((s << 15) | ((uint32_t)e << 7) | (uint32_t)(q & 0x7full));
+    return (uint16_t)((s << 15) | ((uint32_t)e << 7) | (q & 0x7fu));
 }
 
+// The split with 32-bit integer operations only (64-bit integer operations cost several
+// instructions each on the GPU). With x = +-m 2^(ex - 1075), m = 2^52 + f:
+//   hi = m rounded to its 8 leading bits (nearest, ties to even);
+//   res = m - hi (|res| <= 2^44) held as a 45-bit magnitude (mh:ml) and a sign;
+//   lo = res rounded to 8 leading bits: normalise (mh:ml) so its leading bit is bit 63, keep
+//        the top 8 bits and round on the 56 below.
 BF16SPLIT_FN void bf16_split(double x, uint16_t *hi, uint16_t *lo) {
     uint64_t u;
     memcpy(&u, &x, sizeof u);
-    const uint32_t s = (uint32_t)(u >> 63);
-    const int ex = (int)((u >> 52) & 0x7ffull);
-    const uint64_t frac = u & 0xfffffffffffffull;
+    const uint32_t hw = (uint32_t)(u >> 32), lw = (uint32_t)u;
+    const uint32_t s = hw >> 31;
+    const int ex = (int)((hw >> 20) & 0x7ffu);
+    const uint32_t fh = hw & 0xfffffu;                  // fraction bits 51..32
     if (ex == 0x7ff) {                                  // Inf / NaN
-        *hi = (uint16_t)((s << 15) | 0x7f80u | (frac ? 0x40u : 0u));
+        *hi = (uint16_t)((s << 15) | 0x7f80u | ((fh | lw) ? 0x40u : 0u));
         *lo = 0;
         return;
     }
@@ -67,56 +61,62 @@ BF16SPLIT_FN void bf16_split(double x, uint16_t *hi, uint16_t *lo) {
         *lo = 0;
         return;
     }
-    const uint64_t m = frac | (1ull << 52);             // x = +-m * 2^(ex - 1075)
-    const int scale = ex - 1075;
-    // hi: 8 significant bits of m, round to nearest even
-    uint64_t q = m >> 45;
-    const uint64_t rem = m & ((1ull << 45) - 1ull);
-    if (rem > (1ull << 44) || (rem == (1ull << 44) && (q & 1ull))) ++q;
-    const int64_t res = (int64_t)m - (int64_t)(q << 45); // x - hi in units of 2^scale, |res| <= 2^44
-    *hi = bf16split_round(q << 45, scale, s);
-    if (((*hi) & 0x7f80u) == 0x7f80u || ((*hi) & 0x7fffu) == 0u || res == 0) {
+    const uint32_t q = 0x80u | (fh >> 13);              // m >> 45: the 8 leading bits
+    const uint32_t rh = fh & 0x1fffu;                   // m mod 2^45 = rh * 2^32 + lw
+    const uint32_t up = ((rh & 0x1000u) && (((rh & 0xfffu) | lw) != 0u || (q & 1u))) ? 1u : 0u;
+    *hi = bf16split_pack(q + up, ex - 896, s);
+    uint32_t mh, ml, sl = s;
+    if (up) {                                           // res = (m mod 2^45) - 2^45 < 0
+        ml = 0u - lw;
+        mh = 0x2000u - rh - (lw != 0u ? 1u : 0u);
+        sl ^= 1u;
+    } else {
+        ml = lw;
+        mh = rh;
+    }
+    if (((*hi) & 0x7f80u) == 0x7f80u || ((*hi) & 0x7fffu) == 0u || (mh | ml) == 0u) {
         *lo = 0;
         return;
     }
-    const uint32_t sl = s ^ (res < 0 ? 1u : 0u);
-    *lo = bf16split_round((uint64_t)(res < 0 ? -res : res), scale, sl);
+    const int c = mh ? bf16split_clz32(mh) : 32 + bf16split_clz32(ml);   // leading zeros of mh:ml
+    uint32_t top, bot;                                  // (mh:ml) << c
+    if (c >= 32) {
+        top = ml << (c - 32);
+        bot = 0u;
+    } else if (c > 0) {
+        top = (mh << c) | (ml >> (32 - c));
+        bot = ml << c;
+    } else {
+        top = mh;
+        bot = ml;
+    }
+    const uint32_t q8 = top >> 24;
+    const uint32_t up8 = ((top & 0x800000u) && (((top & 0x7fffffu) | bot) != 0u || (q8 & 1u))) ? 1u : 0u;
+    *lo = bf16split_pack(q8 + up8, ex - 885 - c, sl);
 }
 
-// Round the magnitude a (> 0, at most 63 significant bits) times 2^scale to nb
-// significant bits (nearest, ties to even); FP32 bit pattern with sign bit s.
-BF16SPLIT_FN uint32_t split_round_f32(uint64_t a, int scale, uint32_t s, int nb) {
-    const int bl = 64 - bf16split_clz64(a);
-    int shift = bl - nb;
-    uint64_t q;
-    if (shift > 0) {
-        q = a >> shift;
-        const uint64_t rem = a & ((1ull << shift) - 1ull);
-        const uint64_t half = 1ull << (shift - 1);
-        if (rem > half || (rem == half && (q & 1ull))) ++q;
-        if (q == (1ull << nb)) {                        // carried into a new bit
-            q >>= 1;
-            ++shift;
-        }
-    } else {
-        q = a << (-shift);
+// FP32 bits with sign s of the value q * 2^(e - 127 - 10), q in [1024, 2048] (2048 carries into
+// the exponent): a TF32 value (13 low mantissa bits zero); zero below the normal range, Inf above.
+BF16SPLIT_FN uint32_t tf32split_pack(uint32_t q, int e, uint32_t s) {
+    if (q == 2048u) {
+        q = 1024u;
+        ++e;
     }
-    // value = q * 2^(scale + shift), q in [2^(nb-1), 2^nb); FP32 exponent field = unbiased + 127
-    const int e = scale + shift + (nb - 1) + 127;
     if (e <= 0) return s << 31;
     if (e >= 255) return (s << 31) | 0x7f800000u;
-    return (s << 31) | ((uint32_t)e << 23) | ((uint32_t)(q & ((1ull << (nb - 1)) - 1ull)) << (24 - nb));
+    return (s << 31) | ((uint32_t)e << 23) | ((q & 0x3ffu) << 13);
 }
 
+// The TF32 split (11 significant bits) with 32-bit integer operations, as bf16_split.
 BF16SPLIT_FN void tf32_split(double x, uint32_t *hi, uint32_t *lo) {
-    const int nb = 11;
     uint64_t u;
     memcpy(&u, &x, sizeof u);
-    const uint32_t s = (uint32_t)(u >> 63);
-    const int ex = (int)((u >> 52) & 0x7ffull);
-    const uint64_t frac = u & 0xfffffffffffffull;
+    const uint32_t hw = (uint32_t)(u >> 32), lw = (uint32_t)u;
+    const uint32_t s = hw >> 31;
+    const int ex = (int)((hw >> 20) & 0x7ffu);
+    const uint32_t fh = hw & 0xfffffu;
     if (ex == 0x7ff) {                                  // Inf / NaN
-        *hi = (s << 31) | 0x7f800000u | (frac ? 0x00400000u : 0u);
+        *hi = (s << 31) | 0x7f800000u | ((fh | lw) ? 0x00400000u : 0u);
         *lo = 0;
         return;
     }
@@ -125,18 +125,36 @@ BF16SPLIT_FN void tf32_split(double x, uint32_t *hi, uint32_t *lo) {
         *lo = 0;
         return;
     }
-    const uint64_t m = frac | (1ull << 52);             // x = +-m * 2^(ex - 1075)
-    const int scale = ex - 1075;
-    const int drop = 53 - nb;
-    uint64_t q = m >> drop;
-    const uint64_t rem = m & ((1ull << drop) - 1ull);
-    if (rem > (1ull << (drop - 1)) || (rem == (1ull << (drop - 1)) && (q & 1ull))) ++q;
-    const int64_t res = (int64_t)m - (int64_t)(q << drop);   // x - hi in units of 2^scale
-    *hi = split_round_f32(q << drop, scale, s, nb);
-    if (((*hi) & 0x7f800000u) == 0x7f800000u || ((*hi) & 0x7fffffffu) == 0u || res == 0) {
+    const uint32_t q = 0x400u | (fh >> 10);             // m >> 42: the 11 leading bits
+    const uint32_t rh = fh & 0x3ffu;                    // m mod 2^42 = rh * 2^32 + lw
+    const uint32_t up = ((rh & 0x200u) && (((rh & 0x1ffu) | lw) != 0u || (q & 1u))) ? 1u : 0u;
+    *hi = tf32split_pack(q + up, ex - 896, s);
+    uint32_t mh, ml, sl = s;
+    if (up) {                                           // res = (m mod 2^42) - 2^42 < 0
+        ml = 0u - lw;
+        mh = 0x400u - rh - (lw != 0u ? 1u : 0u);
+        sl ^= 1u;
+    } else {
+        ml = lw;
+        mh = rh;
+    }
+    if (((*hi) & 0x7f800000u) == 0x7f800000u || ((*hi) & 0x7fffffffu) == 0u || (mh | ml) == 0u) {
         *lo = 0;
         return;
     }
-    const uint32_t sl = s ^ (res < 0 ? 1u : 0u);
-    *lo = split_round_f32((uint64_t)(res < 0 ? -res : res), scale, sl, nb);
+    const int c = mh ? bf16split_clz32(mh) : 32 + bf16split_clz32(ml);
+    uint32_t top, bot;
+    if (c >= 32) {
+        top = ml << (c - 32);
+        bot = 0u;
+    } else if (c > 0) {
+        top = (mh << c) | (ml >> (32 - c));
+        bot = ml << c;
+    } else {
+        top = mh;
+        bot = ml;
+    }
+    const uint32_t q11 = top >> 21;
+    const uint32_t up11 = ((top & 0x100000u) && (((top & 0xfffffu) | bot) != 0u || (q11 & 1u))) ? 1u : 0u;
+    *lo = tf32split_pack(q11 + up11, ex - 885 - c, sl);
 }
