@@ -211,12 +211,13 @@ __device__ __forceinline__ void inblock_chunks(float (&a)[kMxSB], const float *w
 // The block's levels of one lane (xc: level j at xc[(j / 4) * 4 * kMxT + j % 4]) as split
 // operands, row-contiguous at element offset o of the K-major level matrix; levels j >= jmax
 // (past step N) are stored as zeros. 16-byte stores per array.
-// With diff set, the increments x_j - x_{j-1} are stored instead (x_{-1} = prev).
-template <bool diff>
+// With diff set, the increments x_j - x_{j-1} are stored instead (x_{-1} = prev). full: every
+// level of the block exists (jmax == kMxB), so no level is tested.
+template <bool diff, bool full>
 __device__ __forceinline__ void store_levels(int kind, const float *xc, int jmax, char *gt_hi, char *gt_lo, int64_t o,
                                              float prev = 0.0f) {
     auto level = [&](int j) -> float {
-        if (j >= jmax) return 0.0f;
+        if (!full && j >= jmax) return 0.0f;
         const float x = xc[(j / 4) * 4 * kMxT + j % 4];
         if (!diff) return x;
         const float xp = j ? xc[((j - 1) / 4) * 4 * kMxT + (j - 1) % 4] : prev;
@@ -359,9 +360,10 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     if (!active) return;
     if (A.write_levels) {
         // level n0 + j goes to column n0 + j - 1 of row col
-        store_levels<false>(A.kind, xc, jmax, A.gt_hi, A.gt_lo, col * A.kpad + (A.n0 - 1));
+        if (jmax == kMxB) store_levels<false, true>(A.kind, xc, jmax, A.gt_hi, A.gt_lo, col * A.kpad + (A.n0 - 1));
+        else store_levels<false, false>(A.kind, xc, jmax, A.gt_hi, A.gt_lo, col * A.kpad + (A.n0 - 1));
         if (A.dt_hi)
-            store_levels<true>(A.kind, xc, jmax, A.dt_hi, A.dt_lo, col * A.kpad + (A.n0 - 1), x_before);
+            store_levels<true, false>(A.kind, xc, jmax, A.dt_hi, A.dt_lo, col * A.kpad + (A.n0 - 1), x_before);
         A.carry[col] = gm1;
         A.carry[2 * A.nmp + col] = gm2;
     }
@@ -544,7 +546,8 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
     }
     if (!active) return;
     if (A.write_levels) {
-        store_levels<false>(A.kind, xc, jmax, A.gt_hi, A.gt_lo, col * A.kpad + (A.n0 - 1));
+        if (jmax == kMxB) store_levels<false, true>(A.kind, xc, jmax, A.gt_hi, A.gt_lo, col * A.kpad + (A.n0 - 1));
+        else store_levels<false, false>(A.kind, xc, jmax, A.gt_hi, A.gt_lo, col * A.kpad + (A.n0 - 1));
         A.carry[col] = gm1;
         A.carry[2 * A.nmp + col] = gm2;
     }
