@@ -20,7 +20,7 @@
 // into a small bank (L2-resident) and streamed by TMA like any operand. G is
 // split and transposed once into K-major BF16 arrays.
 //
-// Kernel: one CTA per 128 x 256 output tile; warp 0 issues TMA loads into a
+// Kernel: one CTA per SM over 128 x 256 output tiles; warp 0 issues TMA loads into a
 // two-stage shared-memory ring, warp 1 issues tcgen05.mma (one thread) into two
 // 128 x 256 FP32 accumulators in tensor memory, one chunk of 128 levels at a
 // time, alternating; warps 2-9 read each finished chunk back with tcgen05.ld and
@@ -53,6 +53,7 @@ constexpr int CHUNK_LEVELS = 128;          // levels accumulated per tensor-memo
 constexpr int STG_FLOATS = 32 * 33;          // per epilogue warp: a 32 x 32 block, padded rows
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (size_t)EPI_WARPS * STG_FLOATS * 4;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
+constexpr int TQ = 4;                       // tile ring entries (claimed tiles in flight in a CTA)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -215,8 +216,12 @@ __device__ __forceinline__ TileGeom tile_geom(const TcParams &P, int64_t b) {
 // A CTA takes the output tiles blockIdx.x, blockIdx.x + gridDim.x, ...: one tile when the
 // grid has a CTA per tile, several when the host launches fewer CTAs (tiles of equal K:
 // one CTA per SM, the next tile's loads and MMAs overlapping the previous tile's epilogue).
-// Stages and accumulator chunks are counted across the CTA's tiles, so the mbarrier phases
-// run on without a reset between tiles.
+// With a tile counter (tiles of unequal K) the CTA's first tile is blockIdx.x and the
+// producer thread claims each further one from the counter, so a CTA that finishes early
+// takes the next tile in order; it hands the tile numbers to the MMA thread and the
+// epilogue warps through a ring of TQ entries in shared memory. Stages and accumulator
+// chunks are counted across the CTA's tiles, so the mbarrier phases run on without a
+// reset between tiles.
 template <typename OutT, int KIND>
 __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant__ TcMaps maps, TcParams P,
                                                           OutT *__restrict__ H, int *__restrict__ status) {
@@ -231,6 +236,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
     uint64_t *drain = tempty + 2;                // every MMA this CTA issued has completed
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drain + 1);
     int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);   // [0]: abort, [1]: always 0
+    uint64_t *tq_full = drain + 3;               // ring entry holds a claimed tile number
+    uint64_t *tq_empty = tq_full + TQ;           // ring entry read by the MMA thread and every epilogue warp
+    int64_t *tq = reinterpret_cast<int64_t *>(tq_empty + TQ);
+    const bool dyn = P.tile_counter != nullptr;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t total = P.ntile_state * P.n_states * P.num_i;
@@ -245,6 +254,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
             mbar_init(&tempty[q], 32 * EPI_WARPS);
         }
         mbar_init(drain, 1);
+        for (int i = 0; i < TQ; ++i) {
+            mbar_init(&tq_full[i], 1);
+            mbar_init(&tq_empty[i], 1 + EPI_WARPS);
+        }
         abort_flag[0] = (*(const volatile int *)status & ST_TIMEOUT) ? 1 : 0;   // an earlier CTA gave up
         abort_flag[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -267,7 +280,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
         for (int i = 0; i < STAGES; ++i) armed[i] = -1;
         int64_t gks = 0;                                  // stages issued by this CTA so far
         bool stop = false;
-        for (int64_t b = blockIdx.x; b < total && !stop; b += gridDim.x) {
+        for (int64_t t = 0; !stop; ++t) {
+            int64_t b = blockIdx.x + t * gridDim.x;
+            if (dyn) {
+                const int slot = (int)(t % TQ);
+                if (!mbar_wait(&tq_empty[slot], ((uint32_t)(t / TQ) & 1u) ^ 1u, WAIT_NS, status)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    *(volatile int *)abort_flag = 1;
+                    break;
+                }
+                b = t == 0 ? (int64_t)blockIdx.x : (int64_t)gridDim.x + atomicAdd(P.tile_counter, 1);
+                *(volatile int64_t *)&tq[slot] = b;
+                mbar_arrive(&tq_full[slot]);                  // b >= total tells the others to finish
+            }
+            if (b >= total) break;
             const TileGeom g = tile_geom<KIND>(P, b);
             const CUtensorMap *tA_hi = &maps.a_hi[g.state], *tA_lo = &maps.a_lo[g.state];
             for (int ks = 0; ks < g.num_k; ++ks, ++gks) {
@@ -306,7 +332,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
         // buffer's previous chunk
         int64_t gks = 0, gc = 0;
         bool stop = false;
-        for (int64_t b = blockIdx.x; b < total && !stop; b += gridDim.x) {
+        for (int64_t t = 0; !stop; ++t) {
+            int64_t b = blockIdx.x + t * gridDim.x;
+            if (dyn) {
+                const int slot = (int)(t % TQ);
+                if (!mbar_wait(&tq_full[slot], (uint32_t)(t / TQ) & 1u, WAIT_NS, status)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    *(volatile int *)abort_flag = 1;
+                    break;
+                }
+                b = *(volatile int64_t *)&tq[slot];
+                mbar_arrive(&tq_empty[slot]);
+            }
+            if (b >= total) break;
             const TileGeom g = tile_geom<KIND>(P, b);
             for (int ks = 0; ks < g.num_k; ++ks, ++gks) {
                 const int s = (int)(gks % STAGES);
@@ -355,7 +393,27 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
         float *stg = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * STG_FLOATS;
         bool have = !aborted;
         int64_t gc = 0;
-        for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+        for (int64_t t = 0;; ++t) {
+            int64_t b = blockIdx.x + t * gridDim.x;
+            if (dyn) {
+                // lane 0 takes the tile number from the ring and passes it to the warp
+                const int slot = (int)(t % TQ);
+                int ok = 0;
+                long long bb = 0;
+                if (lane == 0 && have) {
+                    ok = mbar_wait(&tq_full[slot], (uint32_t)(t / TQ) & 1u, WAIT_NS, status) ? 1 : 0;
+                    if (ok) {
+                        bb = *(volatile int64_t *)&tq[slot];
+                        mbar_arrive(&tq_empty[slot]);
+                    } else {
+                        atomicOr(status, ST_TIMEOUT);
+                        *(volatile int *)abort_flag = 1;
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+                b = __shfl_sync(0xffffffffu, bb, 0);
+            }
+            if (b >= total) break;
             const TileGeom g = tile_geom<KIND>(P, b);
             float accr[BN / 2];
 #pragma unroll
@@ -622,8 +680,13 @@ int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, 
     P.n_states = 1;
     P.ntile_state = num_n;
     P.state_stride = 0;
-    const int64_t blocks = num_n * P.num_i;
-    if (blocks > 0x7fffffffLL) return CQ_EUNSUPPORTED;
+    const int64_t tiles = num_n * P.num_i;
+    if (tiles > 0x7fffffffLL - 65536) return CQ_EUNSUPPORTED;
+    // one CTA per SM; tiles have unequal K (a causal triangle), so they are claimed in order
+    // from a counter (zeroed with the status words above)
+    P.max_ctas = device_sms();
+    P.tile_counter = l.status + 32;
+    const int64_t blocks = min(tiles, P.max_ctas);
     if ((st = tc_attr())) return st;
     if ((st = timing_begin(s))) return st;
     if (kind == TC_TF32X3)
@@ -657,7 +720,8 @@ int tc_map_levels(int kind, CUtensorMap *m, const void *levels, int64_t kpad, in
 int tc_contract_f32(int kind, const tc::TcMaps &maps, const tc::TcParams &P, float *H, int *status, cudaStream_t s) {
     using namespace tc;
     const int64_t tiles = P.ntile_state * P.n_states * P.num_i;
-    if (tiles <= 0 || tiles > 0x7fffffffLL) return CQ_EUNSUPPORTED;
+    if (tiles <= 0 || tiles > 0x7fffffffLL - 65536) return CQ_EUNSUPPORTED;
+    if (P.tile_counter && P.max_ctas <= 0) return CQ_EINVAL;
     const int64_t blocks = P.max_ctas > 0 ? min(tiles, P.max_ctas) : tiles;
     int st;
     if ((st = tc_attr())) return st;

@@ -62,6 +62,7 @@ struct MixedLayout {
     float *dqf;                         // [2][N + 1]: d' in FP32
     float *cqf;                         // [2][N + 1]: D' in FP32
     char *q_hi[2], *q_lo[2];            // Toeplitz banks of e
+    int *tcount;                        // tile counter of the weight-derivative contraction
     int kind, nblk, ntiles, qntiles;
     int64_t nmp, kpad, qdelta0;
     size_t bytes;
@@ -112,6 +113,7 @@ static MixedLayout mixed_layout(const Fp2sParams &P, void *base, bool grad) {
             l.q_hi[s] = cv.take<char>(qbank);
             l.q_lo[s] = cv.take<char>(qbank);
         }
+        l.tcount = cv.take<int>(1);
     }
     l.bytes = cv.bytes();
     return l;
@@ -800,6 +802,10 @@ int mixed_grad_run(const Fp2sParams &P, const double *lam, const double *g0, dou
     T.k_lo = 0;
     T.kprime = (int)P.N;
     T.add = 0;
+    // a full causal triangle: tiles of unequal K, claimed in order by one CTA per SM
+    T.max_ctas = device_sms();
+    T.tile_counter = l.tcount;
+    if ((st = cuda_status(cudaMemsetAsync(l.tcount, 0, sizeof(int), s)))) return st;
     if ((st = timing_part(s, false))) return st;
     if ((st = tc_contract_f32(l.kind, qm, T, l.ht, status, s))) return st;
     if ((st = timing_part(s, true))) return st;

@@ -38,6 +38,8 @@ struct TcParams {
     int64_t state_stride;      // levels rows and output columns of state s start at s * state_stride
     int64_t max_ctas;          // 0: one CTA per output tile; else at most this many CTAs, each taking
                                // every max_ctas-th tile (for launches whose tiles have equal K)
+    int *tile_counter;         // with max_ctas: a zeroed counter from which the CTAs claim tiles in
+                               // order instead (tiles of unequal K); nullptr: the fixed order above
 };
 
 // Tensor maps of one contraction: per state the Toeplitz bank (hi, lo); the levels (hi, lo).
