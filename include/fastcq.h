@@ -125,6 +125,18 @@ int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof,
                       double *H_dev, int64_t ldh, int32_t prec,
                       void *ws_dev, size_t *ws_bytes, void *stream);
 
+/* The operand split of the tensor-core forms, as cq_history_direct applies it
+ * to the levels and weights (exposed so that it can be checked against exact
+ * rounding): for i < n,
+ *     hi = x_dev[i] rounded to nearest-even with 8 (CQ_BF16X3) or 11
+ *          (CQ_TF32X3) significant bits, lo = (x_dev[i] - hi) rounded the same way,
+ * written as BF16 bit patterns (uint16_t, prec CQ_BF16X3) or FP32 bit patterns
+ * with the 13 low mantissa bits zero (uint32_t, CQ_TF32X3) to hi_dev[i] and
+ * lo_dev[i]. Parts below the normal FP32 range (2^-126) are signed zeros,
+ * parts above it +-Inf (lo = 0 then); NaN stays NaN. n >= 0; n = 0 does
+ * nothing. CQ_EUNSUPPORTED for other precisions. */
+int cq_split(int32_t prec, const double *x_dev, int64_t n, void *hi_dev, void *lo_dev, void *stream);
+
 /* ---- fast history, one step (Eqs. 3.9-3.10 / 3.17-3.18, Remarks 4.1, 4.7) */
 /* Forms h^n = sum_{i=1}^{min(L-1, n-1)} d_i G^{n-i} + sum_j Ghist_j(t_n) for all
  * DOFs, L = 2 (BE) or Ns (BDF2), advancing the history parts from t_{n-1} to t_n.

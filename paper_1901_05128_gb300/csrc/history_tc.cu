@@ -477,15 +477,64 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
     }
 }
 
+// Fast form of the split for FP64 exponents in [949, 1149] (2^-74 <= |x| < 2^127), bit-identical
+// to the integer-only split of bf16split.h, which serves every other value:
+//   t  = x rounded to odd at 24 significant bits, an FP32 bit pattern assembled from the FP64
+//        fields (truncate, then set the last bit when any dropped bit is set);
+//   hi = t rounded to nearest-even at 8 (BF16) or 11 (TF32) bits, which equals x rounded so
+//        directly (rounding to odd with at least two extra bits, then to nearest, rounds once);
+//   r  = x - hi, exact in FP64 (|r| <= 2^-8 |x| and both are multiples of x's last bit), so one
+//        FP64 subtraction; lo = r rounded the same way (r is 0 or at least 2^-126 here).
+__device__ __forceinline__ uint32_t ro24_bits(uint32_t hw, uint32_t lw) {
+    // (hw:lw) << 3 keeps the exponent's low 9 bits; rebiasing by 896 modulo 2^32 is exact for
+    // biased exponents 897 .. 1150
+    const uint32_t t = __funnelshift_l(lw, hw, 3) - (896u << 23);
+    return t | (hw & 0x80000000u) | ((lw & 0x1fffffffu) != 0u ? 1u : 0u);
+}
+__device__ __forceinline__ uint32_t rn_bf16_of_f32bits(uint32_t u) { return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16; }
+__device__ __forceinline__ uint32_t rn_tf32_of_f32bits(uint32_t u) {
+    return (u + 0xfffu + ((u >> 13) & 1u)) & 0xffffe000u;
+}
+__device__ __forceinline__ bool split_fast_range(uint32_t hw) {
+    const uint32_t ex = (hw >> 20) & 0x7ffu;
+    return ex >= 949u && ex <= 1149u;
+}
+__device__ __forceinline__ uint32_t dhi(double x) { return (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32); }
+__device__ __forceinline__ uint32_t dlo(double x) { return (uint32_t)__double_as_longlong(x); }
+
 // Element of a hi / lo pair: BF16 bits or TF32 (FP32 bits with 13 low zero bits).
 template <int KIND> struct Elem;
 template <> struct Elem<TC_BF16X3> {
     using T = uint16_t;
-    __device__ static void split(double v, T &h, T &l) { bf16_split(v, &h, &l); }
+    __device__ static void split(double v, T &h, T &l) {
+        const uint32_t hw = dhi(v), lw = dlo(v);
+        if (!split_fast_range(hw)) {
+            bf16_split(v, &h, &l);
+            return;
+        }
+        const uint32_t h16 = rn_bf16_of_f32bits(ro24_bits(hw, lw));
+        const uint32_t hh = (((h16 & 0x7fffu) << 13) + (896u << 20)) | ((h16 & 0x8000u) << 16);
+        const double r = __dsub_rn(v, __hiloint2double((int)hh, 0));
+        const uint32_t rw = dhi(r), rl = dlo(r);
+        h = (T)h16;
+        l = ((rw & 0x7fffffffu) | rl) ? (T)rn_bf16_of_f32bits(ro24_bits(rw, rl)) : (T)0;
+    }
 };
 template <> struct Elem<TC_TF32X3> {
     using T = uint32_t;
-    __device__ static void split(double v, T &h, T &l) { tf32_split(v, &h, &l); }
+    __device__ static void split(double v, T &h, T &l) {
+        const uint32_t hw = dhi(v), lw = dlo(v);
+        if (!split_fast_range(hw)) {
+            tf32_split(v, &h, &l);
+            return;
+        }
+        const uint32_t h32 = rn_tf32_of_f32bits(ro24_bits(hw, lw));
+        const uint32_t hh = (((h32 & 0x7fffffffu) >> 3) + (896u << 20)) | (h32 & 0x80000000u);
+        const double r = __dsub_rn(v, __hiloint2double((int)hh, 0));
+        const uint32_t rw = dhi(r), rl = dlo(r);
+        h = h32;
+        l = ((rw & 0x7fffffffu) | rl) ? rn_tf32_of_f32bits(ro24_bits(rw, rl)) : 0u;
+    }
 };
 
 // Bank of Toeplitz tiles: tile t, row r, column c holds d_{delta0 + BK t + r - c} when
@@ -530,7 +579,7 @@ __global__ void __launch_bounds__(256) k_split_transpose(const double *__restric
         const int64_t dof = d0 + r;
         if (dof >= ndof) break;
         T h0, l0, h1, l1;
-        Elem<KIND>::split(tile[r][2 * tx], h0, l0);         // integer ops only (no FP64 pipe)
+        Elem<KIND>::split(tile[r][2 * tx], h0, l0);
         Elem<KIND>::split(tile[r][2 * tx + 1], h1, l1);
         const int64_t o = dof * kpad + k0 + 2 * tx;
         if constexpr (KIND == TC_TF32X3) {
@@ -697,6 +746,19 @@ int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, 
     return timing_end(s);
 }
 
+namespace tc {
+template <int KIND>
+__global__ void k_split(const double *__restrict__ x, int64_t n, typename Elem<KIND>::T *__restrict__ hi,
+                        typename Elem<KIND>::T *__restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    typename Elem<KIND>::T h, l;
+    Elem<KIND>::split(x[i], h, l);
+    hi[i] = h;
+    lo[i] = l;
+}
+}  // namespace tc
+
 int tc_bank(int kind, const double *d, int64_t nw, int64_t delta0, int ntiles, void *hi, void *lo, cudaStream_t s) {
     using namespace tc;
     if (ntiles <= 0) return CQ_EINVAL;
@@ -733,3 +795,21 @@ int tc_contract_f32(int kind, const tc::TcMaps &maps, const tc::TcParams &P, flo
 }
 
 }  // namespace fastcq
+
+extern "C" int cq_split(int32_t prec, const double *x_dev, int64_t n, void *hi_dev, void *lo_dev, void *stream) {
+    using namespace fastcq;
+    if (n < 0) return CQ_EINVAL;
+    if (prec != CQ_BF16X3 && prec != CQ_TF32X3) return CQ_EUNSUPPORTED;
+    if (n == 0) return CQ_OK;
+    if (!x_dev || !hi_dev || !lo_dev) return CQ_EINVAL;
+    if (n > (int64_t)0x7fffffff * 256) return CQ_EUNSUPPORTED;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == CQ_TF32X3)
+        tc::k_split<tc::TC_TF32X3><<<blocks, 256, 0, s>>>(x_dev, n, static_cast<uint32_t *>(hi_dev),
+                                                         static_cast<uint32_t *>(lo_dev));
+    else
+        tc::k_split<tc::TC_BF16X3><<<blocks, 256, 0, s>>>(x_dev, n, static_cast<uint16_t *>(hi_dev),
+                                                         static_cast<uint16_t *>(lo_dev));
+    return launched();
+}

@@ -64,6 +64,7 @@ def _load():
         "cq_gauss_jacobi": (C.c_int, [I32, D, D, P, P, P]),
         "cq_fast_coeffs": (C.c_int, [I32, D, D, C.POINTER(FastCfg), P, P, SZ, P]),
         "cq_history_direct": (C.c_int, [I32, D, D, I64, I64, I64, P, I64, P, I64, I32, P, SZ, P]),
+        "cq_split": (C.c_int, [I32, P, I64, P, P, P]),
         "cq_history_fast": (C.c_int, [I32, D, D, C.POINTER(FastCfg), I64, I64, P, P, I32, P, SZ, P]),
         "cq_history_fast_noalloc": (C.c_int, [I32, D, D, C.POINTER(FastCfg), I64, I64, P, P, I32, P]),
         "fp2s_solve": (C.c_int, [C.POINTER(Problem), P, P, P, SZ, P]),
@@ -87,7 +88,7 @@ def _load():
 
 _lib = _load()
 EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_timing_part", "cq_weights",
-           "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_history_fast",
+           "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_split", "cq_history_fast",
            "cq_history_fast_noalloc", "fp2s_solve",
            "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient", "fp2s_vjp", "fp2s_batch_plan",
            "fp2s_solve_batched", "fp2s_batch_status")
@@ -171,6 +172,12 @@ def cq_history_direct(scheme, beta, tau, ndof, n_lo, n_hi, G_dev, ldg, H_dev, ld
     _check(_lib.cq_history_direct(scheme, beta, tau, ndof, n_lo, n_hi, _ptr(G_dev), ldg, _ptr(H_dev), ldh, prec,
                                   _ptr(ws_dev), C.byref(sz), _stream(stream, ws_dev is None)), "cq_history_direct")
     return sz.value
+
+
+def cq_split(prec, x_dev, hi_dev, lo_dev, stream=None):
+    """Operand split of the tensor-core forms: hi / lo bit patterns (uint16 BF16 or uint32
+    TF32-in-FP32) of every FP64 value of x_dev."""
+    _check(_lib.cq_split(prec, _ptr(x_dev), x_dev.numel(), _ptr(hi_dev), _ptr(lo_dev), _stream(stream)), "cq_split")
 
 
 def cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, n, G_prev_dev, H_dev, ws_dev=None, prec=CQ_F64,

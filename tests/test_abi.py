@@ -54,6 +54,10 @@ def test_invalid_arguments_rejected_on_host(fc):
     assert lib.cq_history_direct(1, 0.5, 0.1, 10, 1, 5, None, 10, None, 10, 7, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
     cfg = fc.FastCfg(8, 8, 2)
     assert lib.cq_history_fast(2, 0.5, 0.1, C.byref(cfg), 10, 1, None, None, 0, None, C.byref(sz), None) == fc.CQ_EINVAL
+    assert lib.cq_split(fc.CQ_F64, None, 0, None, None, None) == fc.CQ_EUNSUPPORTED
+    assert lib.cq_split(fc.CQ_BF16X3, None, -1, None, None, None) == fc.CQ_EINVAL
+    assert lib.cq_split(fc.CQ_TF32X3, None, 0, None, None, None) == fc.CQ_OK          # nothing to split
+    assert lib.cq_split(fc.CQ_BF16X3, None, 5, None, None, None) == fc.CQ_EINVAL
 
 
 @pytest.mark.parametrize("m", [0.5, 1.0, -0.1])
