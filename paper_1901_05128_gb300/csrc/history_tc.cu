@@ -558,8 +558,11 @@ __global__ void k_toeplitz_bank(const double *__restrict__ d, int64_t nw, int64_
 }
 
 // Gt[dof][k'] = split(G[k' + 1][dof]) for k' < kprime, 0 for kprime <= k' < kpad.
-// Tile of 64 levels x 32 DOFs: coalesced FP64 row reads, then every thread writes
-// a pair of elements (a warp stores 128 or 256 contiguous bytes per array).
+// Tile of 64 levels (blockIdx.x) x 32 DOFs (blockIdx.y, and every gridDim.y-th after it when
+// there are more DOF tiles than grid rows): coalesced FP64 row reads, then every thread writes
+// a pair of elements (a warp stores 128 or 256 contiguous bytes per array). One CTA per tile in
+// launch order keeps the CTAs in flight on neighbouring tiles (a persistent version whose
+// CTAs loop over tiles was slower on large inputs: they drift apart in memory).
 template <int KIND>
 __global__ void __launch_bounds__(256) k_split_transpose(const double *__restrict__ G, int64_t ldg, int64_t ndof,
                                                          int kprime, int kpad, typename Elem<KIND>::T *__restrict__ hi,
@@ -567,28 +570,30 @@ __global__ void __launch_bounds__(256) k_split_transpose(const double *__restric
     using T = typename Elem<KIND>::T;
     __shared__ double tile[32][65];                 // [dof][level]
     const int k0 = blockIdx.x * 64;
-    const int64_t d0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-    for (int j = ty; j < 64; j += 8) {
-        const int k = k0 + j;
-        const int64_t dof = d0 + tx;
-        tile[tx][j] = (k < kprime && dof < ndof) ? G[(int64_t)(k + 1) * ldg + dof] : 0.0;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t dof = d0 + r;
-        if (dof >= ndof) break;
-        T h0, l0, h1, l1;
-        Elem<KIND>::split(tile[r][2 * tx], h0, l0);
-        Elem<KIND>::split(tile[r][2 * tx + 1], h1, l1);
-        const int64_t o = dof * kpad + k0 + 2 * tx;
-        if constexpr (KIND == TC_TF32X3) {
-            *reinterpret_cast<uint2 *>(hi + o) = make_uint2(h0, h1);
-            *reinterpret_cast<uint2 *>(lo + o) = make_uint2(l0, l1);
-        } else {
-            *reinterpret_cast<uint32_t *>(hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
-            *reinterpret_cast<uint32_t *>(lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    for (int64_t d0 = (int64_t)blockIdx.y * 32; d0 < ndof; d0 += (int64_t)gridDim.y * 32) {
+        for (int j = ty; j < 64; j += 8) {
+            const int k = k0 + j;
+            const int64_t dof = d0 + tx;
+            tile[tx][j] = (k < kprime && dof < ndof) ? G[(int64_t)(k + 1) * ldg + dof] : 0.0;
         }
+        __syncthreads();
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t dof = d0 + r;
+            if (dof >= ndof) break;
+            T h0, l0, h1, l1;
+            Elem<KIND>::split(tile[r][2 * tx], h0, l0);
+            Elem<KIND>::split(tile[r][2 * tx + 1], h1, l1);
+            const int64_t o = dof * kpad + k0 + 2 * tx;
+            if constexpr (KIND == TC_TF32X3) {
+                *reinterpret_cast<uint2 *>(hi + o) = make_uint2(h0, h1);
+                *reinterpret_cast<uint2 *>(lo + o) = make_uint2(l0, l1);
+            } else {
+                *reinterpret_cast<uint32_t *>(hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                *reinterpret_cast<uint32_t *>(lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+        }
+        __syncthreads();                            // the tile is refilled for the next DOF tile
     }
 }
 
@@ -698,7 +703,8 @@ int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, 
     if ((st = launch_weights(scheme, beta, tau, nw, l.d, s))) return st;
     if ((st = tc_bank(kind, l.d, n_hi, l.delta0, l.ntiles, l.a_hi, l.a_lo, s))) return st;
     const int kprime = (int)(n_hi - 2 > 0 ? n_hi - 2 : 0);
-    dim3 tg((unsigned)(l.kpad / 64), (unsigned)((ndof + 31) / 32));
+    const int64_t ndt = (ndof + 31) / 32;
+    const dim3 tg((unsigned)(l.kpad / 64), (unsigned)min(ndt, (int64_t)65535));
     if (kind == TC_TF32X3)
         k_split_transpose<TC_TF32X3><<<tg, dim3(32, 8), 0, s>>>(G, ldg, ndof, kprime, l.kpad,
                                                                  reinterpret_cast<uint32_t *>(l.g_hi),
