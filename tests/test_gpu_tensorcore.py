@@ -97,6 +97,33 @@ def test_bf16x3_history_full_size_sampled(fc):
     assert np.all(err <= _bound(n_hi) * scale)
 
 
+def test_bf16x3_history_more_dof_tiles_than_grid_rows(fc):
+    """2.2 M DOFs: more 32-DOF tiles of the split-transpose than a grid has rows (65,535), so
+    its CTAs take further DOF tiles in turn; sampled columns from the first and the last
+    tiles are checked against the oracle."""
+    ndof, n_lo, n_hi = 2_200_000, 1, 70
+    beta, tau = 0.6, 1.0 / 64
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(ci.SEED_BASE + 8)
+    G = torch.randn(n_hi, ndof, dtype=torch.float64, device="cuda", generator=gen)
+    H = torch.empty(n_hi - n_lo, ndof, dtype=torch.float64, device="cuda")
+    ws = fc.workspace(fc.cq_history_direct(2, beta, tau, ndof, n_lo, n_hi, None, ndof, None, ndof,
+                                           prec=fc.CQ_BF16X3), "cuda")
+    fc.cq_history_direct(2, beta, tau, ndof, n_lo, n_hi, G, ndof, H, ndof, ws, prec=fc.CQ_BF16X3)
+    torch.cuda.synchronize()
+    cols = np.concatenate([[0, 31, 32 * 65535, 32 * 65535 + 7, ndof - 1],
+                           ci.sample_indices(ndof, 27, ci.SEED_BASE + 9)])
+    idx = torch.tensor(cols, device="cuda")
+    Gc = G[:, idx].cpu().numpy()
+    Hc = H[:, idx].cpu().numpy()
+    del G, H, ws
+    torch.cuda.empty_cache()
+    d = OW.weights(2, beta, tau, n_hi)
+    ref = OH.history_direct_all(d, Gc, n_lo, n_hi)
+    scale = np.stack([_abs_scale(d, Gc, n) for n in range(n_lo, n_hi)])
+    assert np.all(np.abs(Hc - ref) <= _bound(n_hi) * scale + 1e-300)
+
+
 def _bound_tf32(K):
     """TF32x3: each split operand keeps 22 bits (<= 2^-22 relative) and the dropped lo*lo
     term is <= 2^-22, so the products carry <= 4 * 2^-22; the accumulator rounds toward
