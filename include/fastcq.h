@@ -271,7 +271,8 @@ typedef struct {
 /* Plans and prepares a batch of n problems (each with form == CQ_FAST,
  * prec == CQ_F64, dim 1 or 2; any mix of dim, M, N, scheme, alpha, m and fast sizes):
  * builds every instance's tables in the workspace with batched kernels and
- * orders the work units by decreasing cost. tune != 0 times the candidate
+ * orders the work units by decreasing cost. 1 <= n <= 65535 (more: CQ_EUNSUPPORTED;
+ * split such a set into several batches). tune != 0 times the candidate
  * block widths on a shortened run (96 steps) and keeps the fastest.
  * Size query when ws_dev == NULL. Synchronises `stream`; the plan and the
  * workspace stay valid for any number of fp2s_solve_batched calls. */

@@ -21,6 +21,10 @@
 
 namespace fastcq {
 
+// Instances of one batch: the per-instance set-up and transform kernels put the instance
+// on the grid's y axis.
+constexpr int kMaxBatch = 65535;
+
 struct InstDesc {
     double a, tau, inv_tau, beta1, beta2;
     int64_t N, nmodes;
@@ -427,6 +431,7 @@ using namespace fastcq;
 extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t tune, fp2s_batch_t *plan,
                                void *ws_dev, size_t *ws_bytes, void *stream) {
     if (!probs || n < 1 || !plan || !ws_bytes) return CQ_EINVAL;
+    if (n > kMaxBatch) return CQ_EUNSUPPORTED;
     std::vector<InstDesc> descs(n);
     for (int i = 0; i < n; ++i) {
         const int st = validate(probs[i], descs[i]);

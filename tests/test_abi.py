@@ -60,6 +60,14 @@ def test_invalid_arguments_rejected_on_host(fc):
     assert lib.cq_split(fc.CQ_BF16X3, None, 5, None, None, None) == fc.CQ_EINVAL
 
 
+def test_batch_size_limit(fc):
+    probs = (fc.Problem * 65536)()
+    plan = fc.BatchPlan()
+    sz = C.c_size_t(0)
+    assert fc._lib.fp2s_batch_plan(probs, 65536, 0, C.byref(plan), None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
+    assert fc._lib.fp2s_batch_plan(probs, 3, 0, C.byref(plan), None, C.byref(sz), None) == fc.CQ_EINVAL  # zeroed
+
+
 @pytest.mark.parametrize("m", [0.5, 1.0, -0.1])
 def test_problem_validation(fc, m):
     p = fc.problem(0.3, 0.7, m, 1.0, 64, 1, 15)
