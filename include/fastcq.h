@@ -81,6 +81,17 @@ int cq_timing_last(double *ms_main_kernel);
  * Synchronises on the recorded events.
  * CQ_EINVAL for another part, a NULL pointer or no timed call yet. */
 int cq_timing_part(int part, double *ms);
+/* Test switch for the failure path of the tensor-core kernels (on != 0: on;
+ * process-wide; enqueued work is not affected). While on, every tensor-core
+ * launch (cq_history_direct with CQ_BF16X3 / CQ_TF32X3, the mixed-precision
+ * solve and gradient) withholds the first operand load of each CTA and bounds
+ * the waits between the CTA's producer, MMA and epilogue roles by 10 ms
+ * instead of 2 s. The MMA thread's wait for that load then expires: the kernel
+ * records the timeout, writes NaN to its tiles, drains its loads and frees its
+ * tensor memory; fp2s_solve / fp2s_gradient / fp2s_vjp return CQ_ETIMEOUT and
+ * cq_history_direct leaves NaN in the outputs it could not form. The device
+ * stays usable. For tests only; off when the library loads. Always CQ_OK. */
+int cq_test_expire_waits(int on);
 
 /* ---- CQ weights (Sec. 3, Eqs. 3.4 and 3.12) ---------------------------- */
 /* w_dev[i] = d^beta_{s,i}, i = 0..n: the Taylor coefficients of delta(zeta)^beta

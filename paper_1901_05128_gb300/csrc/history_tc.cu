@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
     uint64_t *tq_empty = tq_full + TQ;           // ring entry read by the MMA thread and every epilogue warp
     int64_t *tq = reinterpret_cast<int64_t *>(tq_empty + TQ);
     const bool dyn = P.tile_counter != nullptr;
+    const unsigned long long wlim = P.wait_ns ? P.wait_ns : WAIT_NS;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t total = P.ntile_state * P.n_states * P.num_i;
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
             int64_t b = blockIdx.x + t * gridDim.x;
             if (dyn) {
                 const int slot = (int)(t % TQ);
-                if (!mbar_wait(&tq_empty[slot], ((uint32_t)(t / TQ) & 1u) ^ 1u, WAIT_NS, status)) {
+                if (!mbar_wait(&tq_empty[slot], ((uint32_t)(t / TQ) & 1u) ^ 1u, wlim, status)) {
                     atomicOr(status, ST_TIMEOUT);
                     *(volatile int *)abort_flag = 1;
                     break;
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
             for (int ks = 0; ks < g.num_k; ++ks, ++gks) {
                 const int s = (int)(gks % STAGES);
                 const uint32_t ph = (uint32_t)(gks / STAGES) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u, WAIT_NS, status)) {
+                if (!mbar_wait(&empty[s], ph ^ 1u, wlim, status)) {
                     atomicOr(status, ST_TIMEOUT);
                     *(volatile int *)abort_flag = 1;
                     stop = true;
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
                     stop = true;
                     break;
                 }
+                if (P.test_stall && gks == 0) continue;           // never armed: the MMA thread's wait expires
                 unsigned char *st = smem + s * STAGE_BYTES;
                 const int kc = P.k_lo + ks * BKK;                 // first level column of the stage
                 const int64_t delta = g.m0 - 1 - (int64_t)kc;
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
             int64_t b = blockIdx.x + t * gridDim.x;
             if (dyn) {
                 const int slot = (int)(t % TQ);
-                if (!mbar_wait(&tq_full[slot], (uint32_t)(t / TQ) & 1u, WAIT_NS, status)) {
+                if (!mbar_wait(&tq_full[slot], (uint32_t)(t / TQ) & 1u, wlim, status)) {
                     atomicOr(status, ST_TIMEOUT);
                     *(volatile int *)abort_flag = 1;
                     break;
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
                 const int64_t c = gc + ks / CHUNK;
                 const int buf = (int)(c & 1);
                 if (ks % CHUNK == 0) {
-                    if (!mbar_wait(&tempty[buf], ((uint32_t)(c >> 1) & 1u) ^ 1u, WAIT_NS, status) ||
+                    if (!mbar_wait(&tempty[buf], ((uint32_t)(c >> 1) & 1u) ^ 1u, wlim, status) ||
                         *(volatile int *)abort_flag) {
                         atomicOr(status, ST_TIMEOUT);
                         *(volatile int *)abort_flag = 1;
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
                         break;
                     }
                 }
-                if (!mbar_wait(&full[s], ph, WAIT_NS, status) || *(volatile int *)abort_flag) {
+                if (!mbar_wait(&full[s], ph, wlim, status) || *(volatile int *)abort_flag) {
                     atomicOr(status, ST_TIMEOUT);
                     *(volatile int *)abort_flag = 1;
                     stop = true;
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
                 int ok = 0;
                 long long bb = 0;
                 if (lane == 0 && have) {
-                    ok = mbar_wait(&tq_full[slot], (uint32_t)(t / TQ) & 1u, WAIT_NS, status) ? 1 : 0;
+                    ok = mbar_wait(&tq_full[slot], (uint32_t)(t / TQ) & 1u, wlim, status) ? 1 : 0;
                     if (ok) {
                         bb = *(volatile int64_t *)&tq[slot];
                         mbar_arrive(&tq_empty[slot]);
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
                 const int64_t cc = gc + c;
                 const int buf = (int)(cc & 1);
                 if (have) {
-                    have = mbar_wait(&tfull[buf], (uint32_t)(cc >> 1) & 1u, WAIT_NS, status);
+                    have = mbar_wait(&tfull[buf], (uint32_t)(cc >> 1) & 1u, wlim, status);
                     if (!have) {
                         atomicOr(status, ST_TIMEOUT);
                         *(volatile int *)abort_flag = 1;
@@ -687,6 +689,16 @@ static void launch_bank(const double *d, int64_t nw, int64_t delta0, int ntiles,
 
 }  // namespace tc
 
+// Failure-path test switch (cq_test_expire_waits): launches withhold their first operand load
+// and wait at most 10 ms, so the bounded waits expire and the error path runs.
+static int g_test_expire = 0;
+static void apply_test_switch(tc::TcParams &P) {
+    if (g_test_expire) {
+        P.test_stall = 1;
+        P.wait_ns = 10000000ull;
+    }
+}
+
 size_t history_tc_workspace(int kind, int64_t ndof, int64_t n_lo, int64_t n_hi) {
     return tc::tc_layout(kind, nullptr, ndof, n_lo, n_hi).bytes;
 }
@@ -741,6 +753,7 @@ int history_tc_run(int kind, int scheme, double beta, double tau, int64_t ndof, 
     // from a counter (zeroed with the status words above)
     P.max_ctas = device_sms();
     P.tile_counter = l.status + 32;
+    apply_test_switch(P);
     const int64_t blocks = min(tiles, P.max_ctas);
     if ((st = tc_attr())) return st;
     if ((st = timing_begin(s))) return st;
@@ -785,8 +798,11 @@ int tc_map_levels(int kind, CUtensorMap *m, const void *levels, int64_t kpad, in
     return make_map(kind, m, levels, (uint64_t)kpad, (uint64_t)rows, (uint64_t)kpad, BN);
 }
 
-int tc_contract_f32(int kind, const tc::TcMaps &maps, const tc::TcParams &P, float *H, int *status, cudaStream_t s) {
+int tc_contract_f32(int kind, const tc::TcMaps &maps, const tc::TcParams &Pin, float *H, int *status,
+                    cudaStream_t s) {
     using namespace tc;
+    TcParams P = Pin;
+    apply_test_switch(P);
     const int64_t tiles = P.ntile_state * P.n_states * P.num_i;
     if (tiles <= 0 || tiles > 0x7fffffffLL - 65536) return CQ_EUNSUPPORTED;
     if (P.tile_counter && P.max_ctas <= 0) return CQ_EINVAL;
@@ -818,4 +834,9 @@ extern "C" int cq_split(int32_t prec, const double *x_dev, int64_t n, void *hi_d
         tc::k_split<tc::TC_BF16X3><<<blocks, 256, 0, s>>>(x_dev, n, static_cast<uint16_t *>(hi_dev),
                                                          static_cast<uint16_t *>(lo_dev));
     return launched();
+}
+
+extern "C" int cq_test_expire_waits(int on) {
+    fastcq::g_test_expire = on != 0;
+    return CQ_OK;
 }

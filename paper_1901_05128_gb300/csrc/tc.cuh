@@ -40,6 +40,8 @@ struct TcParams {
                                // every max_ctas-th tile (for launches whose tiles have equal K)
     int *tile_counter;         // with max_ctas: a zeroed counter from which the CTAs claim tiles in
                                // order instead (tiles of unequal K); nullptr: the fixed order above
+    int test_stall;            // failure-path test: each CTA withholds its first operand load
+    unsigned long long wait_ns;  // limit of each wait between the CTA's roles; 0: the default (2 s)
 };
 
 // Tensor maps of one contraction: per state the Toeplitz bank (hi, lo); the levels (hi, lo).

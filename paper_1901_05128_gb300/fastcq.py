@@ -60,6 +60,7 @@ def _load():
         "cq_timing_enable": (C.c_int, [C.c_int]),
         "cq_timing_last": (C.c_int, [C.POINTER(C.c_double)]),
         "cq_timing_part": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+        "cq_test_expire_waits": (C.c_int, [C.c_int]),
         "cq_weights": (C.c_int, [I32, D, D, I64, P, P]),
         "cq_gauss_jacobi": (C.c_int, [I32, D, D, P, P, P]),
         "cq_fast_coeffs": (C.c_int, [I32, D, D, C.POINTER(FastCfg), P, P, SZ, P]),
@@ -87,7 +88,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_timing_part", "cq_weights",
+EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_timing_part",
+           "cq_test_expire_waits", "cq_weights",
            "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_split", "cq_history_fast",
            "cq_history_fast_noalloc", "fp2s_solve",
            "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient", "fp2s_vjp", "fp2s_batch_plan",
@@ -147,6 +149,11 @@ def cq_timing_part(part: int) -> float:
     ms = C.c_double()
     _check(_lib.cq_timing_part(int(part), C.byref(ms)), "cq_timing_part")
     return ms.value
+
+
+def cq_test_expire_waits(on: bool):
+    """Failure-path test switch of the tensor-core kernels (see the C header)."""
+    _lib.cq_test_expire_waits(1 if on else 0)
 
 
 def cq_weights(scheme, beta, tau, n, w_dev, stream=None):

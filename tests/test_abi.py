@@ -60,6 +60,11 @@ def test_invalid_arguments_rejected_on_host(fc):
     assert lib.cq_split(fc.CQ_BF16X3, None, 5, None, None, None) == fc.CQ_EINVAL
 
 
+def test_test_switch_toggles(fc):
+    assert fc._lib.cq_test_expire_waits(1) == fc.CQ_OK
+    assert fc._lib.cq_test_expire_waits(0) == fc.CQ_OK
+
+
 def test_batch_size_limit(fc):
     probs = (fc.Problem * 65536)()
     plan = fc.BatchPlan()
