@@ -19,6 +19,12 @@
  * or a negative CQ_E* status; cq_strerror() turns one into text. No entry
  * point aborts, traps or exits.
  *
+ * Host threads: calls on different workspaces may run from several threads
+ * at once. Process-wide exceptions: the timing functions (cq_timing_*) and the
+ * test switch cq_test_expire_waits keep one state for the whole process, and
+ * every cq_history_fast_noalloc call uses the same device array (calls whose
+ * work overlaps on the GPU race).
+ *
  * Notation (paper's): beta = 1 - alpha is the CQ order used for a state,
  * tau = T/N the step, G^n the level at t_n, d_i the CQ weights,
  * a = (1-m)/(2m-1) the coupling, A = -Laplacian (Dirichlet).

@@ -935,12 +935,13 @@ static int status_from_bits(int bits) {
     return CQ_OK;
 }
 
+// The status word of one call (a buffer per call, so that calls from several host threads
+// do not share it).
 static int read_status(const int *status_dev, cudaStream_t s) {
-    static int *host = nullptr;
-    if (!host && cudaMallocHost(&host, 64) != cudaSuccess) return CQ_ECUDA;
-    if (cudaMemcpyAsync(host, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CQ_ECUDA;
+    int host = 0;
+    if (cudaMemcpyAsync(&host, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CQ_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CQ_ECUDA;
-    return status_from_bits(host[0]);
+    return status_from_bits(host);
 }
 
 // Common set-up of fp2s_solve and fp2s_init: status, weights, tables, spectrum, DST of G0.
