@@ -28,6 +28,12 @@ import sys
 import tempfile
 import time
 
+# The oracle legs run on one host thread and report cores = 1: their per-step numpy arithmetic is
+# element-wise, and the vector-matrix products of the direct history must not fan out to BLAS
+# threads either (set before numpy is first imported).
+for _var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ[_var] = "1"
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
