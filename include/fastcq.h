@@ -94,8 +94,9 @@ int cq_timing_part(int part, double *ms);
  * the waits between the CTA's producer, MMA and epilogue roles by 10 ms
  * instead of 2 s. The MMA thread's wait for that load then expires: the kernel
  * records the timeout, writes NaN to its tiles, drains its loads and frees its
- * tensor memory; fp2s_solve / fp2s_gradient / fp2s_vjp return CQ_ETIMEOUT and
- * cq_history_direct leaves NaN in the outputs it could not form. The device
+ * tensor memory; the mixed-precision fp2s_solve, fp2s_gradient and fp2s_vjp
+ * return CQ_ETIMEOUT and cq_history_direct leaves NaN in the outputs it could
+ * not form. The device
  * stays usable. For tests only; off when the library loads. Always CQ_OK. */
 int cq_test_expire_waits(int on);
 
