@@ -21,6 +21,7 @@
 namespace fastcq {
 
 constexpr int kDirBT = 8;        // time block of the fused direct kernel
+constexpr int kF32TabFloats = 1024;   // FP32 fast form: node tables (<= 4*128 + 8*8 + 2 floats)
 
 struct Fp2sLayout {
     int *status;
@@ -28,6 +29,7 @@ struct Fp2sLayout {
     double *tab1, *tab2, *scr1, *scr2;
     double *lam, *S, *tmp, *g0, *gN;
     float *hdf;                   // FP32 fast form: 0.5*d_i of both states as double-float, [4][N+1]
+    float *ftab;                  // FP32 fast form: node tables in the fused kernel's order (k_f32_tables)
     double *hist;                 // direct: (N+1) x 2 x nmodes
     double *Y, *ring, *glast;     // step API, fast: 2 x np x nm, 2 x L x nm; both: 2 levels x 2 x nm
     void *mixed;                  // direct, CQ_BF16X3 / CQ_TF32X3: region of the mixed-precision solve
@@ -62,6 +64,7 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     if (P.form == CQ_DIRECT && P.prec == CQ_F64)
         l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
     if (P.prec != CQ_F64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
+    if (P.form == CQ_FAST && P.prec == CQ_F32) l.ftab = cv.take<float>(kF32TabFloats);
     if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3))
         l.mixed = cv.take<char>(grad ? mixed_grad_bytes(P) : mixed_direct_bytes(P));
     if (stepper) {
@@ -387,18 +390,93 @@ static int fast_block_threads(int np, int L, int64_t nmodes) {
 // ---------------------------------------------------------------------------
 constexpr int kF32Threads = 128;
 
+// Node pairs per lane (NQ = NP / 4) of the FP32 fast form whose ratios r_j are kept as
+// double-float (r = fl(r) + r_lo): the top quarter of the slots, which hold the slowest
+// decaying nodes. A ratio near 1 rounded to FP32 changes 1 - r by up to 2^-25 / (1 - r)
+// relatively, and the geometric sum carries that error over ~1 / (1 - r) steps: with 128
+// points at tau = 1/8192 the slowest nodes have 1 - r ~ 2e-4, and the rounded ratios alone
+// put ~5e-5 into the solution. Faster nodes (1 - r > ~0.15) lose < 2e-7 this way.
+__host__ __device__ constexpr int f32_df_pairs(int NP) { return NP / 16 > 0 ? NP / 16 : 1; }
+
+// FP32 tables of the fused FP32 fast solve, in the order the kernel reads them
+// (ftab: [4 NP] float4-packed words, then [8 KD] floats, then 2 floats):
+//   per state s the np nodes are ranked by r (ascending, ties by index) and placed in the
+//   top np of the NP slots; slot t = 4 kk + 2 hf + e of state s is component pair e of word
+//   4 kk + 2 hf + s, holding (r, c r); the bottom NP - np slots are zero. The top 4 KD slots
+//   also get r - fl(r) in the float2 word 4 (kk - (NQ - KD)) + 2 hf + s, component e.
+//   The last two floats are C_s = sum_j c_j.
+// One block of 256 threads (2 np <= 256).
+__global__ void k_f32_tables(int NP, int KD, int np, const double *__restrict__ tab1, const double *__restrict__ tab2,
+                             float *__restrict__ out) {
+    const int NQ = NP / 4, tid = threadIdx.x;
+    float *tab = out, *tlo = out + 4 * NP, *csum = tlo + 8 * KD;
+    for (int i = tid; i < 4 * NP + 8 * KD; i += blockDim.x) out[i] = 0.0f;
+    __syncthreads();
+    for (int e = tid; e < 2 * np; e += blockDim.x) {
+        const int st = e / np, j = e - st * np;
+        const double *tq = st ? tab2 : tab1;
+        const double r = tq[j];
+        int rank = 0;
+        for (int k = 0; k < np; ++k) {
+            const double rk = tq[k];
+            rank += (rk < r || (rk == r && k < j)) ? 1 : 0;
+        }
+        const int t = NP - np + rank, kk = t >> 2, hf = (t >> 1) & 1, el = t & 1;
+        const float rf = (float)r;
+        float *w = tab + 4 * (4 * kk + 2 * hf + st) + 2 * el;
+        w[0] = rf;
+        w[1] = (float)(tq[np + j] * r);
+        if (kk >= NQ - KD) tlo[2 * (4 * (kk - (NQ - KD)) + 2 * hf + st) + el] = (float)(r - (double)rf);
+    }
+    if (tid < 2) {
+        const double *tq = tid ? tab2 : tab1;
+        double c = 0.0;
+        for (int j = 0; j < np; ++j) c += tq[np + j];
+        csum[tid] = (float)c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused fast solve, FP32 precision form. Each lane carries one state of TWO
+// modes over HALF of the history-part nodes: lanes l = 16 s + 8 h + q hold state s
+// of the modes 2p, 2p + 1 of pair p = 8 w + q (w the warp) over the node slots
+// 4 kk + 2 h, 4 kk + 2 h + 1 (kk < NP / 4), so both halves hold nodes of similar r at
+// the same kk. One 16-byte table word (r_j, c_j r_j, r_{j+1}, c_{j+1} r_{j+1}) then feeds
+// both modes (eight FMAs), and the four (half, state) words a load touches are adjacent.
+// The history sum is taken from the states before their update,
+//     h^n = sum_j c_j Y_j^n = sum_j (c_j r_j) Y_j^{n-1} + C G^{n-L},  C = sum_j c_j,
+// so the FMAs of a node do not wait on each other. The slowest quarter of the nodes
+// (the top slots) update with a double-float ratio, Y = fl(r) Y + (r_lo Y + G): one more
+// FMA per node. Per step the two halves add their partial sums with one shuffle per mode,
+// lane h takes the 2x2 step of mode 2p + h with its partner state (lane ^ 16), and the two
+// new levels are exchanged with one shuffle; the exact window (L - 1 terms) is split between
+// the halves by parity. Each lane keeps its own ring of the last L levels of its two modes
+// (float2) in shared memory. The states Y_j live in FP32 registers (NP is a compile-time
+// bound; the tables are zero-padded up to it). Weights, quadrature coefficients and the
+// per-mode step matrices are computed in FP64; the step is evaluated from the FP32 history
+// sums in the two-term form x = A l + B e with double-float A and B (lane_step2_df), or in
+// FP64 when the coupling is strong (|a| > 10, i.e. m within ~0.045 of 1/2); the first SBD
+// step uses the double-float form. The lane's own level is carried between steps as a
+// double-float pair: its low part enters l and, through d_1 x_lo^{n-1}, e (the term of the
+// window with the largest weight); the ring, the node inputs and the other window terms
+// use the FP32 part. Every mode is pre-scaled by an exact power of two (from its G^0) so
+// that its values sit near 1 in FP32 range; the factor is undone on output.
+// ---------------------------------------------------------------------------
+
 // The FP64 / first-SBD step of the FP32 form, out of line (it runs on rare steps only).
-__device__ __noinline__ float lane_step_rare(const Fp2sParams P, const LaneStep ls, int solve64, int64_t n, float h,
-                                             float gm1, float gm2, float gz, const double *dn, const float *hd_hi,
-                                             const float *hd_lo) {
-    return lane_step(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
+__device__ __noinline__ df lane_step_rare(const Fp2sParams P, const LaneStep ls, int solve64, int64_t n, float h,
+                                          float gm1, float gm2, float gz, const double *dn, const float *hd_hi,
+                                          const float *hd_lo) {
+    return lane_step_df(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
 }
 
 // Node part of one step (two modes, this lane's half of the nodes): the partial history
-// sums sum_j (c_j r_j) Y_j^{n-1} + C G^{n-L} into hA / hB, then Y_j^n = r_j Y_j^{n-1} + G^{n-L}.
-template <int NQ>
-__device__ __forceinline__ void f32_node_part(const float4 *tb, float cs, float2 in, float (&YA)[2 * NQ],
-                                              float (&YB)[2 * NQ], float (&hA)[4], float (&hB)[4]) {
+// sums sum_j (c_j r_j) Y_j^{n-1} + C G^{n-L} into hA / hB, then Y_j^n = r_j Y_j^{n-1} + G^{n-L}
+// (the last KD node pairs with the double-float ratio fl(r_j) + r_lo_j from tl).
+template <int NQ, int KD>
+__device__ __forceinline__ void f32_node_part(const float4 *tb, const float2 *tl, float cs, float2 in,
+                                              float (&YA)[2 * NQ], float (&YB)[2 * NQ], float (&hA)[4],
+                                              float (&hB)[4]) {
     hA[0] = cs * in.x;
     hB[0] = cs * in.y;
 #pragma unroll
@@ -411,18 +489,28 @@ __device__ __forceinline__ void f32_node_part(const float4 *tb, float cs, float2
         hB[c] = fmaf(t.y, YB[2 * kk], hB[c]);
         hA[c + 1] = fmaf(t.w, YA[2 * kk + 1], hA[c + 1]);
         hB[c + 1] = fmaf(t.w, YB[2 * kk + 1], hB[c + 1]);
-        YA[2 * kk] = fmaf(t.x, YA[2 * kk], in.x);
-        YB[2 * kk] = fmaf(t.x, YB[2 * kk], in.y);
-        YA[2 * kk + 1] = fmaf(t.z, YA[2 * kk + 1], in.x);
-        YB[2 * kk + 1] = fmaf(t.z, YB[2 * kk + 1], in.y);
+        if (kk >= NQ - KD) {
+            const float2 lo = tl[4 * (kk - (NQ - KD))];
+            YA[2 * kk] = fmaf(t.x, YA[2 * kk], fmaf(lo.x, YA[2 * kk], in.x));
+            YB[2 * kk] = fmaf(t.x, YB[2 * kk], fmaf(lo.x, YB[2 * kk], in.y));
+            YA[2 * kk + 1] = fmaf(t.z, YA[2 * kk + 1], fmaf(lo.y, YA[2 * kk + 1], in.x));
+            YB[2 * kk + 1] = fmaf(t.z, YB[2 * kk + 1], fmaf(lo.y, YB[2 * kk + 1], in.y));
+        } else {
+            YA[2 * kk] = fmaf(t.x, YA[2 * kk], in.x);
+            YB[2 * kk] = fmaf(t.x, YB[2 * kk], in.y);
+            YA[2 * kk + 1] = fmaf(t.z, YA[2 * kk + 1], in.x);
+            YB[2 * kk + 1] = fmaf(t.z, YB[2 * kk + 1], in.y);
+        }
     }
 }
 
 // Exact window d_i x^{n-i}, i = 1 .. min(L - 1, n - 1), of both modes into hA[3] / hB[3]: odd i
 // on half 0, even i on half 1 (same trip count on both halves; the last term of half 1 may be
-// absent). slot holds x^{n-L} .. and receives x^n.
-__device__ __forceinline__ void f32_window(const float2 *Rc, const float *ws, int T, int L, int slot, int n, int hf,
-                                           float (&hA)[4], float (&hB)[4]) {
+// absent). slot holds x^{n-L} .. and receives x^n. With LO, the same terms with the FP32
+// remainders of the weights (d_i - fl(d_i), wsl) go into wlA / wlB.
+template <bool LO>
+__device__ __forceinline__ void f32_window(const float2 *Rc, const float *ws, const float *wsl, int T, int L, int slot,
+                                           int n, int hf, float (&hA)[4], float (&hB)[4], float &wlA, float &wlB) {
     const int imax = min(L - 1, n - 1);
     for (int q = 0; 2 * q < imax; ++q) {
         const int i = 2 * q + 1 + hf;
@@ -433,6 +521,11 @@ __device__ __forceinline__ void f32_window(const float2 *Rc, const float *ws, in
         const float w = on ? ws[2 * i] : 0.0f;
         hA[3] = fmaf(w, v.x, hA[3]);
         hB[3] = fmaf(w, v.y, hB[3]);
+        if (LO) {
+            const float wl = on ? wsl[2 * i] : 0.0f;
+            wlA = fmaf(wl, v.x, wlA);
+            wlB = fmaf(wl, v.y, wlB);
+        }
     }
 }
 
@@ -443,34 +536,26 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
                                                                double *__restrict__ gN, int *__restrict__ status,
                                                                const double *__restrict__ d1,
                                                                const double *__restrict__ d2,
-                                                               const double *__restrict__ tab1,
-                                                               const double *__restrict__ tab2,
+                                                               const float *__restrict__ ftab,
                                                                const float *__restrict__ hdf) {
     constexpr int NH = NP / 2;               // nodes per lane
     constexpr int NQ = NP / 4;               // node pairs per lane
+    constexpr int KD = f32_df_pairs(NP);   // trailing node pairs with double-float ratios
     extern __shared__ __align__(16) float smf[];
-    const int np = P.np, L = P.L, T = blockDim.x, tid = threadIdx.x;
+    const int L = P.L, T = blockDim.x, tid = threadIdx.x;
     float4 *tab4 = reinterpret_cast<float4 *>(smf);                    // [NQ][half][state]
-    float *wt = smf + 4 * NP;                                           // wt[2i + s] = d_i of state s, i < L
-    float *csum = wt + 2 * kMaxNs;                                      // C of each state
-    float2 *R = reinterpret_cast<float2 *>(csum + 2);                  // [L][T]
-    for (int e = tid; e < 4 * NQ; e += T) {
-        const int kk = e >> 2, hf = (e >> 1) & 1, s = e & 1;
-        const int j = 2 * (hf * NQ + kk);
-        const double *tq = s ? tab2 : tab1;
-        tab4[e] = make_float4(j < np ? (float)tq[j] : 0.0f, j < np ? (float)(tq[np + j] * tq[j]) : 0.0f,
-                              j + 1 < np ? (float)tq[j + 1] : 0.0f,
-                              j + 1 < np ? (float)(tq[np + j + 1] * tq[j + 1]) : 0.0f);
-    }
+    float2 *tlo = reinterpret_cast<float2 *>(smf + 4 * NP);            // [KD][half][state]
+    float *csum = smf + 4 * NP + 8 * KD;                                // C of each state
+    float *wt = csum + 2;                                               // wt[2i + s] = fl(d_i) of state s, i < L
+    float *wlo = wt + 2 * kMaxNs;                                       // wlo[2i + s] = d_i - fl(d_i)
+    float2 *R = reinterpret_cast<float2 *>(wlo + 2 * kMaxNs);          // [L][T]
+    for (int e = tid; e < 4 * NP + 8 * KD + 2; e += T) smf[e] = ftab[e];
     for (int i = tid; i < L; i += T) {
-        wt[2 * i] = (float)d1[i];
-        wt[2 * i + 1] = (float)d2[i];
-    }
-    if (tid < 2) {
-        const double *tq = tid ? tab2 : tab1;
-        double c = 0.0;
-        for (int j = 0; j < np; ++j) c += tq[np + j];
-        csum[tid] = (float)c;
+        const float a = (float)d1[i], b = (float)d2[i];
+        wt[2 * i] = a;
+        wt[2 * i + 1] = b;
+        wlo[2 * i] = (float)(d1[i] - (double)a);
+        wlo[2 * i + 1] = (float)(d2[i] - (double)b);
     }
     for (int j = 0; j < L; ++j) R[(size_t)j * T + tid] = make_float2(0.0f, 0.0f);
     __syncthreads();
@@ -481,9 +566,16 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
     const bool active = mode_raw < P.nmodes;
     const int64_t mode = active ? mode_raw : 0;
     const float4 *tb = tab4 + (2 * hf + st);
-    const float *ws = wt + st;
+    const float2 *tl = tlo + (2 * hf + st);
+    const float *ws = wt + st, *wsl = wlo + st;
     float cs = hf ? 0.0f : csum[st];         // C G^{n-L} enters the sums of half 0 only
     keep_reg(cs);
+    // d_1 of the own / other state as double-float (the BE window is d_1 x^{n-1} alone)
+    float w1 = wt[2 + st], w1_lo = wlo[2 + st], w1_o = wt[3 - st], w1_o_lo = wlo[3 - st];
+    keep_reg(w1);
+    keep_reg(w1_lo);
+    keep_reg(w1_o);
+    keep_reg(w1_o_lo);
     const double *dn = st ? d2 : d1;
     const float *hd_hi = hdf + (size_t)(2 * st) * (P.N + 1), *hd_lo = hd_hi + (P.N + 1);
     float2 *Rc = R + tid;
@@ -493,7 +585,8 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
     const double gmax = fmax(fabs(gz64), fabs(__shfl_xor_sync(0xffffffffu, gz64, 16)));
     int ex = 0;
     if (gmax > 0.0 && isfinite(gmax)) frexp(gmax, &ex);
-    const float gz = (float)ldexp(gz64, -ex);
+    const df gzd = df_from(ldexp(gz64, -ex));
+    const float gz = gzd.hi;
 
     LaneStep ls;
     const bool ok = lane_step_setup(P, lam[mode], d1[0], d2[0], st, ls);
@@ -505,18 +598,26 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
     float YA[NH], YB[NH];                    // the two modes' states over this lane's nodes
 #pragma unroll
     for (int j = 0; j < NH; ++j) YA[j] = YB[j] = 0.0f;
-    float gm1 = gz, gm2 = 0.0f, gm1_o = __shfl_xor_sync(0xffffffffu, gz, 16), gm2_o = 0.0f;
+    // own (and partner state's) last two levels as double-float pairs
+    float gm1 = gz, gm1_lo = gzd.lo, gm2 = 0.0f, gm2_lo = 0.0f;
+    float gm1_o = __shfl_xor_sync(0xffffffffu, gz, 16), gm1_o_lo = __shfl_xor_sync(0xffffffffu, gzd.lo, 16);
+    float gm2_o = 0.0f, gm2_o_lo = 0.0f;
     const int N = (int)P.N;
     float hA[4] = {}, hB[4] = {};            // node part of the current step
     // the new level x^n of the lane's mode: both halves' levels into the ring, shift the history
-    auto finish = [&](float x, int slot) {
-        const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);       // partner state, same mode
-        const float x_p = __shfl_xor_sync(0xffffffffu, x, 8);        // same state, other mode of the pair
-        Rc[slot * T] = hf ? make_float2(x_p, x) : make_float2(x, x_p);
+    auto finish = [&](df x, int slot) {
+        const float x_o = __shfl_xor_sync(0xffffffffu, x.hi, 16);    // partner state, same mode
+        const float x_o_lo = __shfl_xor_sync(0xffffffffu, x.lo, 16);
+        const float x_p = __shfl_xor_sync(0xffffffffu, x.hi, 8);     // same state, other mode of the pair
+        Rc[slot * T] = hf ? make_float2(x_p, x.hi) : make_float2(x.hi, x_p);
         gm2 = gm1;
-        gm1 = x;
+        gm2_lo = gm1_lo;
+        gm1 = x.hi;
+        gm1_lo = x.lo;
         gm2_o = gm1_o;
+        gm2_o_lo = gm1_o_lo;
         gm1_o = x_o;
+        gm1_o_lo = x_o_lo;
     };
     auto combine = [&]() -> float {
         float sA = (hA[0] + hA[1]) + (hA[2] + hA[3]);
@@ -530,8 +631,9 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
         int slot = 0;
         for (int n = 1; n <= N; ++n) {
             slot = (slot + 1 == L) ? 0 : slot + 1;
-            f32_node_part<NQ>(tb, cs, Rc[slot * T], YA, YB, hA, hB);
-            f32_window(Rc, ws, T, L, slot, n, hf, hA, hB);
+            float wlA = 0.0f, wlB = 0.0f;
+            f32_node_part<NQ, KD>(tb, tl, cs, Rc[slot * T], YA, YB, hA, hB);
+            f32_window<false>(Rc, ws, wsl, T, L, slot, n, hf, hA, hB, wlA, wlB);
             const float h = combine();
             finish(lane_step_rare(P, ls, 1, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo), slot);
         }
@@ -550,18 +652,31 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
         for (; n <= N; ++n) {
             const int next = (slot + 1 == L) ? 0 : slot + 1;
             float nA[4], nB[4];
-            f32_node_part<NQ>(tb, cs, Rc[next * T], YA, YB, nA, nB);  // step n + 1
-            f32_window(Rc, ws, T, L, slot, n, hf, hA, hB);              // step n
+            f32_node_part<NQ, KD>(tb, tl, cs, Rc[next * T], YA, YB, nA, nB);  // step n + 1
+            float wlA = 0.0f, wlB = 0.0f;
+            f32_window<!BE>(Rc, ws, wsl, T, L, slot, n, hf, hA, hB, wlA, wlB);  // step n
             const float h = combine();
-            float x;
+            // The window took fl(d_i) fl(x^{n-i}); the FP32 remainders of the weights (a weight
+            // rounded to FP32 is a fixed relative error of up to 2^-25 that every step repeats,
+            // and d_1 is of size beta tau^-beta) and of the own level x^{n-1} go into e_lo.
+            // G^0 is not part of the history: nothing at n = 1.
+            df x;
             if (BE) {
-                x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, __shfl_xor_sync(0xffffffffu, h, 16), 0.0f);
+                const float e_lo = n > 1 ? fmaf(w1_lo, gm1, w1 * gm1_lo) : 0.0f;
+                const float e_o_lo = n > 1 ? fmaf(w1_o_lo, gm1_o, w1_o * gm1_o_lo) : 0.0f;
+                x = lane_step2_df(l2, gm1, gm1_lo, gm1_o, gm1_o_lo, h, e_lo, __shfl_xor_sync(0xffffffffu, h, 16),
+                                  e_o_lo);
             } else {
-                const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
-                // e = h + d_{n-1} g^0 / 2 as a double-float pair
-                const df e = df_add(df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz), df{h, 0.0f});
-                x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, __shfl_xor_sync(0xffffffffu, e.hi, 16),
-                               __shfl_xor_sync(0xffffffffu, e.lo, 16));
+                // window remainders of the own mode: this half's terms plus the other half's
+                const float wl = (hf ? wlB : wlA) + __shfl_xor_sync(0xffffffffu, hf ? wlA : wlB, 8);
+                const float e_lo = fmaf(w1, gm1_lo, wl);
+                df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
+                l.lo += fmaf(2.0f, gm1_lo, -0.5f * gm2_lo);
+                lo.lo += fmaf(2.0f, gm1_o_lo, -0.5f * gm2_o_lo);
+                // e = h + d_{n-1} g^0 / 2 (+ the low parts) as a double-float pair
+                const df e = df_add(df_mul(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gzd), df{h, e_lo});
+                x = lane_step2_df(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, __shfl_xor_sync(0xffffffffu, e.hi, 16),
+                                  __shfl_xor_sync(0xffffffffu, e.lo, 16));
             }
             finish(x, slot);
 #pragma unroll
@@ -573,14 +688,14 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
         }
     }
     if (active) {
-        const double out = ldexp((double)gm1, ex);
+        const double out = ldexp((double)gm1 + (double)gm1_lo, ex);
         gN[st * P.nmodes + mode] = out;
         if (!isfinite(out)) atomicOr(status, ST_NONFINITE);
     }
 }
 
 static size_t f32_smem_bytes(int NP, int L, int T) {
-    return ((size_t)4 * NP + 2 * kMaxNs + 2) * sizeof(float) + (size_t)L * T * sizeof(float2);
+    return ((size_t)4 * NP + 8 * f32_df_pairs(NP) + 2 + 4 * kMaxNs) * sizeof(float) + (size_t)L * T * sizeof(float2);
 }
 
 template <int NP>
@@ -590,10 +705,17 @@ static void launch_f32(const Fp2sParams &P, int solve64, const Fp2sLayout &l, cu
     const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
     if (P.scheme == CQ_BE)
         k_fp2s_fast_f32<NP, true><<<blocks, T, f32_smem_bytes(NP, P.L, T), s>>>(
-            P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.hdf);
+            P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.ftab, l.hdf);
     else
         k_fp2s_fast_f32<NP, false><<<blocks, T, f32_smem_bytes(NP, P.L, T), s>>>(
-            P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.hdf);
+            P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.ftab, l.hdf);
+}
+
+// The compile-time node bound NP of the FP32 fast kernel for np points per state (0: too many).
+static int f32_np_bound(int np) {
+    for (int b : {16, 32, 48, 64, 80, 96, 128})
+        if (np <= b) return b;
+    return 0;
 }
 
 // hdf[(2s)(N+1) + i], hdf[(2s+1)(N+1) + i] = hi, lo of d^s_i / 2
@@ -611,14 +733,16 @@ __global__ void k_half_weights_df(const double *__restrict__ d1, const double *_
 
 static int fp2s_fast_f32(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
     const int solve64 = fabs(P.a) > 10.0;
-    if (P.np <= 16) launch_f32<16>(P, solve64, l, s);
-    else if (P.np <= 32) launch_f32<32>(P, solve64, l, s);
-    else if (P.np <= 48) launch_f32<48>(P, solve64, l, s);
-    else if (P.np <= 64) launch_f32<64>(P, solve64, l, s);
-    else if (P.np <= 80) launch_f32<80>(P, solve64, l, s);
-    else if (P.np <= 96) launch_f32<96>(P, solve64, l, s);
-    else if (P.np <= 128) launch_f32<128>(P, solve64, l, s);
-    else return CQ_EUNSUPPORTED;
+    switch (f32_np_bound(P.np)) {
+        case 16: launch_f32<16>(P, solve64, l, s); break;
+        case 32: launch_f32<32>(P, solve64, l, s); break;
+        case 48: launch_f32<48>(P, solve64, l, s); break;
+        case 64: launch_f32<64>(P, solve64, l, s); break;
+        case 80: launch_f32<80>(P, solve64, l, s); break;
+        case 96: launch_f32<96>(P, solve64, l, s); break;
+        case 128: launch_f32<128>(P, solve64, l, s); break;
+        default: return CQ_EUNSUPPORTED;
+    }
     return CQ_OK;
 }
 
@@ -964,6 +1088,12 @@ static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2,
     } else if (P.form == CQ_FAST) {
         if ((st = build_fast_coeffs(P.scheme, b1, P.tau, np1, np2, P.L, l.scr1, l.tab1, l.tab1 + P.np, s))) return st;
         if ((st = build_fast_coeffs(P.scheme, b2, P.tau, np1, np2, P.L, l.scr2, l.tab2, l.tab2 + P.np, s))) return st;
+        if (P.prec == CQ_F32) {
+            const int NP = f32_np_bound(P.np);
+            if (NP == 0) return CQ_EUNSUPPORTED;
+            k_f32_tables<<<1, 256, 0, s>>>(NP, f32_df_pairs(NP), P.np, l.tab1, l.tab2, l.ftab);
+            if ((st = launched())) return st;
+        }
     }
     if ((st = launch_mode_eigenvalues(p->M, p->dim, l.lam, s))) return st;
     if ((st = launch_dst_matrix(p->M, l.S, s))) return st;

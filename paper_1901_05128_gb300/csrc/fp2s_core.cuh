@@ -157,7 +157,7 @@ __device__ __forceinline__ bool lane_step_setup(const Fp2sParams &P, double lam,
 // 2x2 solve run in double-float arithmetic (FP32 pipe): FP32-rounded step
 // coefficients would perturb the per-step amplification by ~1e-7, which compounds
 // over the steps. solve64 selects FP64 instead (strong coupling, |a| > 10).
-__device__ __forceinline__ float lane_step(const Fp2sParams &P, const LaneStep &ls, int solve64, int64_t n, float h,
+__device__ __forceinline__ df lane_step_df(const Fp2sParams &P, const LaneStep &ls, int solve64, int64_t n, float h,
                                            float gm1, float gm2, float gz, const double *__restrict__ dn,
                                            const float *__restrict__ hd_hi, const float *__restrict__ hd_lo) {
     if (solve64) {
@@ -177,7 +177,7 @@ __device__ __forceinline__ float lane_step(const Fp2sParams &P, const LaneStep &
         const double e_o = __shfl_xor_sync(0xffffffffu, e, 16);
         const double b = lead - ls.c * e + P.a * e_o;
         const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
-        return (float)(m_oo * b + m_ot * b_o);
+        return df_from(m_oo * b + m_ot * b_o);
     }
     df e, lead;
     df m_oo = ls.dmn_oo, m_ot = ls.dmn_ot;
@@ -197,8 +197,13 @@ __device__ __forceinline__ float lane_step(const Fp2sParams &P, const LaneStep &
     const df e_o = df_shfl_xor16(e);
     const df b = df_add(df_add(lead, df_neg(df_mul(ls.dc, e))), df_mul(ls.da, e_o));
     const df b_o = df_shfl_xor16(b);
-    const df xx = df_add(df_mul(m_oo, b), df_mul(m_ot, b_o));
-    return xx.hi + xx.lo;
+    return df_add(df_mul(m_oo, b), df_mul(m_ot, b_o));
+}
+// The same step rounded to one FP32 value.
+__device__ __forceinline__ float lane_step(const Fp2sParams &P, const LaneStep &ls, int solve64, int64_t n, float h,
+                                           float gm1, float gm2, float gz, const double *__restrict__ dn,
+                                           const float *__restrict__ hd_hi, const float *__restrict__ hd_lo) {
+    return lane_step_df(P, ls, solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo).hi;
 }
 
 // Two-term form of the FP32-precision step, for steps with the common matrix M
@@ -232,7 +237,8 @@ __device__ __forceinline__ void lane_step2_setup(const Fp2sParams &P, const Lane
 
 // x = A l + B e for the lane's state: (l, l_lo) and (l_o, l_o_lo) the double-float l
 // of the lane's and the other state, (e, e_lo) and (e_o, e_o_lo) the history terms.
-__device__ __forceinline__ float lane_step2(const LaneStep2 &c, float l, float l_lo, float l_o, float l_o_lo, float e,
+// The result as a normalised double-float pair (hi = its FP32 rounding).
+__device__ __forceinline__ df lane_step2_df(const LaneStep2 &c, float l, float l_lo, float l_o, float l_o_lo, float e,
                                             float e_lo, float e_o, float e_o_lo) {
     const float p1 = c.a_hi[0] * l;
     float r = fmaf(c.a_hi[0], l, -p1);
@@ -245,7 +251,11 @@ __device__ __forceinline__ float lane_step2(const LaneStep2 &c, float l, float l
     r += fmaf(c.b_hi[1], e_o_lo, fmaf(c.b_lo[1], e_o, fmaf(c.b_hi[1], e_o, -p4)));
     const df s12 = two_sum(p1, p2), s34 = two_sum(p3, p4);
     const df s = two_sum(s12.hi, s34.hi);
-    return s.hi + (s.lo + ((s12.lo + s34.lo) + r));
+    return df_fast_norm(s.hi, s.lo + ((s12.lo + s34.lo) + r));
+}
+__device__ __forceinline__ float lane_step2(const LaneStep2 &c, float l, float l_lo, float l_o, float l_o_lo, float e,
+                                            float e_lo, float e_o, float e_o_lo) {
+    return lane_step2_df(c, l, l_lo, l_o, l_o_lo, e, e_lo, e_o, e_o_lo).hi;
 }
 
 // Opaque register barrier: the value is kept as computed. Step coefficients formed in

@@ -1,13 +1,21 @@
 """GPU precision forms against the FP64 oracle (``-m gpu``).
 
 FP32 fast solve (prec = CQ_F32): FP32 history-part states and sums, FP64 tables and
-per-mode step matrices, FP64 2x2 step when |a| > 10. Tolerance, from the arithmetic:
-each history part Y_j = sum_k r_j^k G^{n-k} is advanced with one FP32 rounding per step
-(u = 2^-24); over its memory of ~1/(1-r_j) steps the random rounding errors add up to
-about u / sqrt(1 - r_j) relative to |Y_j| (~1e-6 for the slowest parts, 1 - r ~ 1e-4),
-and the weights c_j of those parts are small. The step is contractive for the stable
-problems used here, so the solution error stays at that level: relative L2 error
-<= 2e-5 per state (the measured values are printed).
+per-mode step matrices, FP64 2x2 step when |a| > 10. Error sources (u = 2^-24):
+- a weight rounded to FP32 is a fixed relative error that every step repeats; for the
+  window weights (d_1 ~ beta tau^-beta) this acts like an extra reaction term of size
+  (a + lambda) |d_1| u and was the largest error (5e-5 on the full workload), so the window
+  weights are double-float;
+- the ratios r_j of the slowest quarter of the nodes are double-float, the others FP32:
+  a rounded ratio near 1 perturbs the geometric weights by up to (u/2) / (1 - r_j) relative,
+  < 2e-7 for 1 - r_j > 0.15;
+- each history part Y_j is advanced with one FP32 rounding per step; over its memory of
+  ~1/(1 - r_j) steps these add up to about u / sqrt(1 - r_j) relative to |Y_j|;
+- the levels are FP32 in the ring (node inputs, window terms) and double-float in the
+  step and the d_1 term: u per level and step.
+These are random in sign and add up over the N steps like a random walk, to ~1e-6 at
+N = 8192. Bars: relative L2 error <= 5e-6 per state on the small cases and on the full
+2D 511x511, N = 8192 workload (measured <= 1.8e-6; printed).
 """
 import numpy as np
 import pytest
@@ -61,7 +69,27 @@ def test_fast_f32_against_fp64_oracle(fc, name, p):
     ref = OS.solve(p, G0)
     errs = [np.linalg.norm(got[s] - ref[s]) / np.linalg.norm(ref[s]) for s in range(2)]
     print("f32 %s rel L2 errors %.3e %.3e" % (name, errs[0], errs[1]))
-    assert max(errs) <= 2e-5
+    assert max(errs) <= 5e-6
+
+
+@pytest.mark.parametrize("alpha", [(0.2, 0.8), (0.8, 0.8)])
+def test_fast_f32_full_size_sampled(fc, alpha):
+    """The 2D 511x511, N = 8192 precision workload (BE, m = 0.45, Np = 128) in its fast form,
+    in the launch configuration the benchmark times; the four lowest and eight seeded sine
+    modes are recomputed by the oracle's FP64 fast scheme."""
+    from oracle import spatial as OSP
+    p, G0 = ci.workload("prec_2d_m511")
+    p = p.replace(form=ci.FAST, alpha1=alpha[0], alpha2=alpha[1])
+    got, st = _solve(fc, p, G0, fc.CQ_F32)
+    assert st == fc.CQ_OK
+    nm = p.M ** p.dim
+    sample = np.unique(np.concatenate([[0, 1, p.M, p.M + 1], ci.sample_indices(nm, 8, ci.SEED_BASE + 42)]))
+    lam = OSP.mode_eigenvalues(p.M, p.dim)[sample]
+    ref = OS.solve_modal(p, lam, OSP.to_modal(G0, p.M, p.dim)[:, sample])[p.N]
+    gm = OSP.to_modal(got, p.M, p.dim)[:, sample]
+    errs = [float(np.linalg.norm(gm[s] - ref[s]) / np.linalg.norm(ref[s])) for s in range(2)]
+    print("f32 fast full size %s: rel L2 errors over %d modes %.3e %.3e" % (alpha, len(sample), errs[0], errs[1]))
+    assert max(errs) <= 5e-6
 
 
 def test_fast_f32_rejected_where_unsupported(fc):
