@@ -134,10 +134,11 @@ int cq_fast_coeffs(int32_t scheme, double beta, double tau, const cq_fast_cfg_t 
  * into the workspace. prec: CQ_F64 (FP64 FMAs), CQ_BF16X3 or CQ_TF32X3
  * (tcgen05 tensor cores; G and the Toeplitz tiles are split and staged in the
  * workspace, which then holds about 4 (BF16) or 8 (TF32) * ndof * n_hi bytes;
- * n_hi + 128 <= 24000; the FP32 accumulation runs in chunks of 128 levels
- * summed with round-to-nearest; magnitudes below 2^-126 in the FP32
- * accumulator are returned as zero). On a device fault or an expired internal
- * wait the tensor-core paths write NaN to the affected outputs. */
+ * n_hi + 128 <= 24000; the tensor cores' FP32 accumulation, which rounds toward
+ * zero, runs in chunks of 128 (BF16) or 32 (TF32) levels that are summed with
+ * round-to-nearest; magnitudes below 2^-126 in the FP32 accumulator are returned
+ * as zero). On a device fault or an expired internal wait the tensor-core paths
+ * write NaN to the affected outputs. */
 int cq_history_direct(int32_t scheme, double beta, double tau, int64_t ndof,
                       int64_t n_lo, int64_t n_hi, const double *G_dev, int64_t ldg,
                       double *H_dev, int64_t ldh, int32_t prec,
@@ -209,7 +210,9 @@ typedef struct {
     int32_t form;          /* CQ_DIRECT or CQ_FAST */
     cq_fast_cfg_t fast;    /* used when form == CQ_FAST */
     int32_t prec;          /* CQ_F64; in fp2s_solve also CQ_F32 with form == CQ_FAST (np1 + np2 <= 128)
-                              and CQ_BF16X3 with form == CQ_DIRECT (mixed-precision direct solve) */
+                              and CQ_BF16X3 or CQ_TF32X3 with form == CQ_DIRECT (mixed-precision
+                              direct solve); fp2s_gradient / fp2s_vjp take CQ_F64, CQ_BF16X3 and
+                              CQ_TF32X3 with form == CQ_DIRECT */
     int32_t flags;
 } fp2s_problem_t;
 
@@ -217,11 +220,15 @@ typedef struct {
  * [2][M^dim], the level t_N of the BE scheme Eq. 4.1 / fast BE Eq. 4.3 /
  * SBD Eq. 4.7 / fast SBD Eq. 4.8). Every sine mode is advanced through all N
  * steps by one persistent kernel (FP64, CQ_F32). The mixed-precision direct
- * solve (CQ_DIRECT with CQ_BF16X3) runs in blocks of 128 steps: the history
- * from earlier blocks is a tcgen05 BF16x3 contraction (FP32 accumulation per
- * 128-level chunk, chunks summed with round-to-nearest), the in-block part and
- * the steps run in FP32 / double-float (FP64 when |a| > 10); its workspace
- * holds the levels as BF16 hi + lo (about 4 bytes per DOF-step).
+ * solve (CQ_DIRECT with CQ_BF16X3 or CQ_TF32X3) runs in blocks of 128 steps:
+ * the history from earlier blocks is a tcgen05 contraction of split BF16 or
+ * TF32 operands (FP32 accumulation per chunk, chunks summed with
+ * round-to-nearest), the in-block part and the steps run in FP32 /
+ * double-float (FP64 when |a| > 10), with the FP32 remainders of d_1 and d_2
+ * and of the previous level carried into the step; its workspace holds the
+ * levels as hi + lo (about 4 (BF16) or 8 (TF32) bytes per DOF-step). Relative
+ * errors against the FP64 scheme are of order 1e-6 (TF32x3) to 3e-6 (BF16x3)
+ * on 2D 511x511, N = 8192. CQ_F32 (fast form): of order 1e-6 on the same grid.
  * Synchronises `stream` at the end to read the device status unless
  * flags & FP2S_ASYNC. */
 int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double *GN_dev,
@@ -258,7 +265,7 @@ int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, dou
  * weight-derivative history as one more contraction; the workspace holds the
  * split levels and increments (2 x 2 x N x 2 x M^dim operands) and an FP32
  * [N][2][M^dim] history, for all modes (no slicing; a size query returns this
- * size whatever *ws_bytes holds). Relative errors of order 1e-4 against the
+ * size whatever *ws_bytes holds). Relative errors of order 1e-5 against the
  * FP64 form.
  * Inputs G0_dev, Gt_dev: physical [2][M^dim]. Outputs: *J_host; dJdG0_dev
  * [2][M^dim] (gradient with respect to the nodal values of G^0); dJdalpha_host[2].

@@ -22,12 +22,18 @@
 //
 // Kernel: one CTA per SM over 128 x 256 output tiles; warp 0 issues TMA loads into a
 // two-stage shared-memory ring, warp 1 issues tcgen05.mma (one thread) into two
-// 128 x 256 FP32 accumulators in tensor memory, one chunk of 128 levels at a
-// time, alternating; warps 2-9 read each finished chunk back with tcgen05.ld and
-// add it to FP32 running sums (round to nearest) while the next chunk is being
-// formed, then store FP64 (or FP32) results. The tensor cores' own accumulation
-// rounds toward zero, which on a history whose terms share a sign is a bias
-// that grows with K; chunking keeps it to one chunk's worth. Every mbarrier wait
+// 128 x 256 FP32 accumulators in tensor memory, one chunk of levels at a time
+// (128 BF16 levels, 32 TF32 levels), alternating; warps 2-9 read each finished chunk
+// back with tcgen05.ld and add it to FP32 running sums (round to nearest) while the
+// next chunk is being formed, then store FP64 (or FP32) results. The tensor cores'
+// own accumulation rounds toward zero: every MMA instruction that adds to an
+// accumulator of size |S| loses up to ulp(S) toward zero, and on a history whose
+// terms share a sign these losses are a bias that a time-stepping scheme repeats
+// at every step. Chunking keeps it to one chunk's worth, and within a stage the
+// small products (hi*lo, lo*hi, 2^-8 resp. 2^-11 of the result) are issued before
+// the hi*hi products, while the accumulator is still small: per TF32 chunk only
+// the four hi*hi instructions truncate a value of the chunk's full size (instead
+// of all twelve, or 48 in a 128-level chunk). Every mbarrier wait
 // is bounded by a global-timer deadline; on expiry the kernel records
 // ST_TIMEOUT, writes NaN to its tile, drains what it started and frees its
 // tensor memory.
@@ -49,7 +55,8 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int EPI_WARPS = 8;                // two warps per TMEM lane quarter, one per column half
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int TMEM_COLS = 512;              // two 128 x 256 FP32 accumulators
-constexpr int CHUNK_LEVELS = 128;          // levels accumulated per tensor-memory pass
+// levels accumulated per tensor-memory pass (see the truncation note above)
+__host__ __device__ constexpr int chunk_levels(int kind) { return kind == TC_TF32X3 ? 32 : 128; }
 constexpr int STG_FLOATS = 32 * 33;          // per epilogue warp: a 32 x 32 block, padded rows
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (size_t)EPI_WARPS * STG_FLOATS * 4;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
@@ -196,7 +203,7 @@ struct TileGeom {
 template <int KIND>
 __device__ __forceinline__ TileGeom tile_geom(const TcParams &P, int64_t b) {
     constexpr int BKK = kind_bk(KIND);
-    constexpr int CHUNK = CHUNK_LEVELS / BKK;
+    constexpr int CHUNK = chunk_levels(KIND) / BKK;
     TileGeom g;
     const int64_t ntile = b / P.num_i;
     g.state = (int)(ntile / P.ntile_state);
@@ -226,7 +233,7 @@ template <typename OutT, int KIND>
 __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant__ TcMaps maps, TcParams P,
                                                           OutT *__restrict__ H, int *__restrict__ status) {
     constexpr int BKK = kind_bk(KIND);                          // levels per stage
-    constexpr int CHUNK = CHUNK_LEVELS / BKK;                   // stages per accumulator chunk
+    constexpr int CHUNK = chunk_levels(KIND) / BKK;             // stages per accumulator chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -372,13 +379,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_history_tc(const __grid_constant
                 const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
                 const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
                 const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                // one MMA: 32 bytes along K (16 BF16 or 8 TF32); the small products of the
+                // stage first, the first of a chunk starting the accumulator from zero
 #pragma unroll
                 for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
-                    const uint32_t off = kk * 32;            // one MMA: 32 bytes along K (16 BF16 or 8 TF32)
+                    const uint32_t off = kk * 32;
                     const uint32_t acc0 = (ks % CHUNK > 0 || kk > 0) ? 1u : 0u;
-                    umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
-                    umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+                    umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_lo + off), acc0);
                     umma<KIND>(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+                }
+#pragma unroll
+                for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
+                    const uint32_t off = kk * 32;
+                    umma<KIND>(acc, sdesc(a_hi + off), sdesc(b_hi + off), 1u);
                 }
                 umma_commit(&empty[s]);                       // stage reusable once these MMAs are done
                 if (ks % CHUNK == CHUNK - 1 || ks == g.num_k - 1) umma_commit(&tfull[buf]);

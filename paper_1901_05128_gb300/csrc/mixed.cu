@@ -34,6 +34,7 @@
 #include "common.cuh"
 #include "fp2s_core.cuh"
 #include "tc.cuh"
+#include "bf16split.h"
 
 namespace fastcq {
 
@@ -48,7 +49,8 @@ struct MixedLayout {
     char *gt_hi, *gt_lo;                // levels (BF16 or TF32 hi / lo), K-major: row s * nmp + mode, column k - 1
     float *acc2b;                       // contraction of two blocks' rows [2 kMxB][2 * nmp]
     float *acc1b;                       // contraction of one block's rows [kMxB][2 * nmp]
-    float *carry;                       // g^{n-1}, g^{n-2} at the end of a block: [2][2 * nmp]
+    float *carry;                       // g^{n-1}, g^{n-2} at the end of a block: [4][2 * nmp] (FP32 parts,
+                                        // then the forward solve's double-float remainders)
     float4 *coef;                       // per lane: A row, B row (double-float), (scaled g^0, exponent)
     // gradient only
     float4 *coef_adj;                   // per lane coefficients of the adjoint steps (as coef)
@@ -89,7 +91,7 @@ static MixedLayout mixed_layout(const Fp2sParams &P, void *base, bool grad) {
     l.gt_lo = cv.take<char>(lev * es);
     l.acc2b = cv.take<float>(l.nblk > 2 ? (size_t)2 * kMxB * 2 * l.nmp : 0);
     l.acc1b = cv.take<float>(l.nblk > 1 ? (size_t)kMxB * 2 * l.nmp : 0);
-    l.carry = cv.take<float>((size_t)4 * l.nmp);
+    l.carry = cv.take<float>((size_t)8 * l.nmp);
     l.coef = cv.take<float4>((size_t)6 * l.nmp);
     if (grad) {
         l.coef_adj = cv.take<float4>((size_t)6 * l.nmp);
@@ -184,6 +186,49 @@ __device__ __forceinline__ void coef_load(const float4 *coef, int64_t nmp, int64
     l2.b_lo[1] = c1.w;
     z = c2.x;
     ex = __float_as_int(c2.y);
+}
+
+// FP32 remainders of the two largest history weights of a state, d_1 and d_2, for the
+// forward step. A weight rounded to FP32 is a fixed relative error that every step
+// repeats: d_1 ~ beta tau^-beta, and its rounding alone put ~5e-5 into the 2D 511x511,
+// N = 8192 solve. The in-block sums use fl(d_i) (remainder rf), the contraction rows the
+// tensor-core operands hi + lo of the kind's split (remainder rb).
+struct WeightRem {
+    float w1, r1f, r2f, r1b, r2b;
+};
+
+__device__ __forceinline__ float split_sum(int kind, double x) {
+    if (kind == tc::TC_TF32X3) {
+        uint32_t h, l;
+        tf32_split(x, &h, &l);
+        return __uint_as_float(h) + __uint_as_float(l);
+    }
+    uint16_t h, l;
+    bf16_split(x, &h, &l);
+    return __uint_as_float((uint32_t)h << 16) + __uint_as_float((uint32_t)l << 16);
+}
+
+__device__ __forceinline__ WeightRem weight_rem(int kind, const double *d, int64_t N) {
+    const double d1 = N >= 1 ? d[1] : 0.0, d2 = N >= 2 ? d[2] : 0.0;
+    WeightRem r;
+    r.w1 = (float)d1;
+    r.r1f = (float)(d1 - (double)(float)d1);
+    r.r2f = (float)(d2 - (double)(float)d2);
+    r.r1b = (float)(d1 - (double)split_sum(kind, d1));
+    r.r2b = (float)(d2 - (double)split_sum(kind, d2));
+    return r;
+}
+
+// The remainder terms of step n (block offset j) of one state: the weight remainders of
+// d_1 x^{n-1} and d_2 x^{n-2} (lag i comes from the block's own levels when j >= i, else from
+// the contraction) and d_1 times the double-float remainder of x^{n-1}. G^0 is not part of
+// the history.
+__device__ __forceinline__ float weight_rem_terms(const WeightRem &r, int j, int64_t n, float gm1, float gm1_lo,
+                                                  float gm2) {
+    float e = 0.0f;
+    if (n >= 2) e = fmaf(j >= 1 ? r.r1f : r.r1b, gm1, r.w1 * gm1_lo);
+    if (n >= 3) e = fmaf(j >= 2 ? r.r2f : r.r2b, gm2, e);
+    return e;
 }
 
 // Earlier in-block levels in chunks of 8: a[b] += sum_kk d_{j0 + b - kc - kk} x^{n0 + kc + kk}
@@ -301,13 +346,20 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     const float *hdo_hi = A.hdf + (size_t)(2 * (1 - st)) * (P.N + 1), *hdo_lo = hdo_hi + (P.N + 1);
     const float gz_o = __shfl_xor_sync(0xffffffffu, gz, 16);      // the partner state's scaled g^0
 
-    float gm1 = gz, gm2 = 0.0f;
+    // the lane's last two levels as double-float pairs (FP32 part: what the sums and the level
+    // matrix see), and the partner state's
+    float gm1 = gz, gm2 = 0.0f, gm1_lo = 0.0f, gm2_lo = 0.0f;
+    if (A.n0 == 1 && full_setup) gm1_lo = (float)(ldexp(A.g0[st * P.nmodes + mode], -ex) - (double)gz);
     if (A.n0 > 1) {
         gm1 = A.carry[col];
         gm2 = A.carry[2 * A.nmp + col];
+        gm1_lo = A.carry[4 * A.nmp + col];
+        gm2_lo = A.carry[6 * A.nmp + col];
     }
     const float x_before = gm1;                      // x^{n0 - 1}
     float gm1_o = __shfl_xor_sync(0xffffffffu, gm1, 16), gm2_o = __shfl_xor_sync(0xffffffffu, gm2, 16);
+    float gm1_o_lo = __shfl_xor_sync(0xffffffffu, gm1_lo, 16), gm2_o_lo = __shfl_xor_sync(0xffffffffu, gm2_lo, 16);
+    const WeightRem wr = weight_rem(A.kind, st ? A.d2 : A.d1, P.N), wr_o = weight_rem(A.kind, st ? A.d1 : A.d2, P.N);
     const float *w = wsm + st * kMxW + kMxWOff;     // w[i] = d_i, i >= -kMxWOff
     float wt[kMxSB];                                 // d_1 .. d_7 of the lane's state
 #pragma unroll
@@ -334,29 +386,41 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
             const int64_t n = A.n0 + j0 + b;
             if (j0 + b >= jmax) break;
             const float h = a[b];
-            float x;
+            const float h_o = __shfl_xor_sync(0xffffffffu, h, 16);
+            const float e_lo = weight_rem_terms(wr, j0 + b, n, gm1, gm1_lo, gm2);
+            const float e_o_lo = weight_rem_terms(wr_o, j0 + b, n, gm1_o, gm1_o_lo, gm2_o);
+            df xd;
             if (full_setup && (A.solve64 || (P.scheme == CQ_BDF2 && n == 1))) {
-                x = lane_step(P, ls, A.solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
+                xd = lane_step_df(P, ls, A.solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
             } else if (P.scheme == CQ_BE) {
-                x = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, __shfl_xor_sync(0xffffffffu, h, 16), 0.0f);
+                xd = lane_step2_df(l2, gm1, gm1_lo, gm1_o, gm1_o_lo, h, e_lo, h_o, e_o_lo);
             } else {
-                const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
-                // e = h + d_{n-1} g^0 / 2 as a double-float pair, for this lane's state and (from the
-                // partner's h and g^0, with the same operations) for the partner's: one shuffle
+                df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
+                l.lo += fmaf(2.0f, gm1_lo, -0.5f * gm2_lo);
+                lo.lo += fmaf(2.0f, gm1_o_lo, -0.5f * gm2_o_lo);
+                // e = h + d_{n-1} g^0 / 2 (+ the remainder terms) as a double-float pair, for this
+                // lane's state and (from the partner's h and g^0, with the same operations) for the
+                // partner's
                 const df ed = df_mul_f(df{__ldg(hd_hi + n - 1), __ldg(hd_lo + n - 1)}, gz);
                 const df edo = df_mul_f(df{__ldg(hdo_hi + n - 1), __ldg(hdo_lo + n - 1)}, gz_o);
-                const df e = df_add(ed, df{h, 0.0f});
-                const df e_o = df_add(edo, df{__shfl_xor_sync(0xffffffffu, h, 16), 0.0f});
-                x = lane_step2(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, e_o.hi, e_o.lo);
+                const df e = df_add(ed, df{h, e_lo});
+                const df e_o = df_add(edo, df{h_o, e_o_lo});
+                xd = lane_step2_df(l2, l.hi, l.lo, lo.hi, lo.lo, e.hi, e.lo, e_o.hi, e_o.lo);
             }
+            const float x = xd.hi;
 #pragma unroll
             for (int bb = b + 1; bb < kMxSB; ++bb) a[bb] = fmaf(wt[bb - b], x, a[bb]);
             const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);
+            const float x_o_lo = __shfl_xor_sync(0xffffffffu, xd.lo, 16);
             xc[((j0 + b) / 4) * 4 * kMxT + (j0 + b) % 4] = x;
             gm2 = gm1;
+            gm2_lo = gm1_lo;
             gm1 = x;
+            gm1_lo = xd.lo;
             gm2_o = gm1_o;
+            gm2_o_lo = gm1_o_lo;
             gm1_o = x_o;
+            gm1_o_lo = x_o_lo;
         }
     }
     if (!active) return;
@@ -368,10 +432,12 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
             store_levels<true, false>(A.kind, xc, jmax, A.dt_hi, A.dt_lo, col * A.kpad + (A.n0 - 1), x_before);
         A.carry[col] = gm1;
         A.carry[2 * A.nmp + col] = gm2;
+        A.carry[4 * A.nmp + col] = gm1_lo;
+        A.carry[6 * A.nmp + col] = gm2_lo;
     }
     if (A.x1 && A.n0 == 1) A.x1[col] = xc[0];
     if (A.n0 + kMxB > P.N) {                         // the block holding step N
-        const double out = ldexp((double)gm1, ex);
+        const double out = ldexp((double)gm1 + (double)gm1_lo, ex);
         A.gN[st * P.nmodes + mode] = out;
         if (!isfinite(out)) atomicOr(A.status, ST_NONFINITE);
     }
@@ -462,12 +528,23 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
     const float *cq = A.cqf + (size_t)st * (N + 1);                   // D'_i
     const float x0f = A.coef_fwd[4 * A.nmp + col].x;                  // x^0, scaled like the forward levels
 
-    float gm1 = 0.0f, gm2 = 0.0f;                            // lambda^{m+1}, lambda^{m+2}
+    // lambda^{m+1}, lambda^{m+2} as double-float pairs, and the partner state's
+    float gm1 = 0.0f, gm2 = 0.0f, gm1_lo = 0.0f, gm2_lo = 0.0f;
     if (A.n0 > 1) {
         gm1 = A.carry[col];
         gm2 = A.carry[2 * A.nmp + col];
+        gm1_lo = A.carry[4 * A.nmp + col];
+        gm2_lo = A.carry[6 * A.nmp + col];
     }
     float gm1_o = __shfl_xor_sync(0xffffffffu, gm1, 16), gm2_o = __shfl_xor_sync(0xffffffffu, gm2, 16);
+    float gm1_o_lo = __shfl_xor_sync(0xffffffffu, gm1_lo, 16), gm2_o_lo = __shfl_xor_sync(0xffffffffu, gm2_lo, 16);
+    // mu^{m+1} (double-float) and mu^{m+2} of both states, the levels of the adjoint's history
+    const df mv1 = df_add(df_mul_f(dc, gm1), df_neg(df_mul_f(da, gm1_o)));
+    const df mv2 = df_add(df_mul_f(dc, gm2), df_neg(df_mul_f(da, gm2_o)));
+    float mu1 = mv1.hi, mu1_lo = mv1.lo, mu2 = mv2.hi + mv2.lo;
+    float mu1_o = __shfl_xor_sync(0xffffffffu, mu1, 16), mu1_o_lo = __shfl_xor_sync(0xffffffffu, mu1_lo, 16);
+    float mu2_o = __shfl_xor_sync(0xffffffffu, mu2, 16);
+    const WeightRem wr = weight_rem(A.kind, st ? A.d2 : A.d1, N), wr_o = weight_rem(A.kind, st ? A.d1 : A.d2, N);
     const float *w = wsm + st * kMxW + kMxWOff;
     float wt[kMxSB];
 #pragma unroll
@@ -508,22 +585,29 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
             float h = a[b];
             if (r == 1) h += rz;                             // the terminal term at m = N
             const float h_o = __shfl_xor_sync(0xffffffffu, h, 16);
-            float lam;
+            // remainders of the history's largest weights (d_1, d_2) and of mu^{m+1}
+            const float e_lo = weight_rem_terms(wr, j0 + b, r, mu1, mu1_lo, mu2);
+            const float e_o_lo = weight_rem_terms(wr_o, j0 + b, r, mu1_o, mu1_o_lo, mu2_o);
+            df ld;
             if (A.solve64) {
                 const double l = sbd ? 2.0 * (double)gm1 - 0.5 * (double)gm2 : (double)gm1;
                 const double l_o = sbd ? 2.0 * (double)gm1_o - 0.5 * (double)gm2_o : (double)gm1_o;
                 const bool f = sbd && m == 1;
                 const double bs = l * P.inv_tau - (double)h, bo = l_o * P.inv_tau - (double)h_o;
-                lam = (float)((f ? t1_oo : t_oo) * bs + (f ? t1_ot : t_ot) * bo);
+                ld = df_from((f ? t1_oo : t_oo) * bs + (f ? t1_ot : t_ot) * bo);
             } else if (!sbd) {
-                lam = lane_step2(l2, gm1, 0.0f, gm1_o, 0.0f, h, 0.0f, h_o, 0.0f);
+                ld = lane_step2_df(l2, gm1, gm1_lo, gm1_o, gm1_o_lo, h, e_lo, h_o, e_o_lo);
             } else {
-                const df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
-                lam = lane_step2(m == 1 ? l2f : l2, l.hi, l.lo, lo.hi, lo.lo, h, 0.0f, h_o, 0.0f);
+                df l = two_sum(2.0f * gm1, -0.5f * gm2), lo = two_sum(2.0f * gm1_o, -0.5f * gm2_o);
+                l.lo += fmaf(2.0f, gm1_lo, -0.5f * gm2_lo);
+                lo.lo += fmaf(2.0f, gm1_o_lo, -0.5f * gm2_o_lo);
+                ld = lane_step2_df(m == 1 ? l2f : l2, l.hi, l.lo, lo.hi, lo.lo, h, e_lo, h_o, e_o_lo);
             }
+            const float lam = ld.hi;
             const float lam_o = __shfl_xor_sync(0xffffffffu, lam, 16);
+            const float lam_o_lo = __shfl_xor_sync(0xffffffffu, ld.lo, 16);
             const df mv = df_add(df_mul_f(dc, lam), df_neg(df_mul_f(da, lam_o)));
-            const float mu = mv.hi + mv.lo;
+            const float mu = mv.hi;
 #pragma unroll
             for (int bb = b + 1; bb < kMxSB; ++bb) a[bb] = fmaf(wt[bb - b], mu, a[bb]);
             xc[((j0 + b) / 4) * 4 * kMxT + (j0 + b) % 4] = mu;
@@ -541,9 +625,19 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
                 }
             }
             gm2 = gm1;
+            gm2_lo = gm1_lo;
             gm1 = lam;
+            gm1_lo = ld.lo;
             gm2_o = gm1_o;
+            gm2_o_lo = gm1_o_lo;
             gm1_o = lam_o;
+            gm1_o_lo = lam_o_lo;
+            mu2 = mu1;
+            mu1 = mu;
+            mu1_lo = mv.lo;
+            mu2_o = mu1_o;
+            mu1_o = __shfl_xor_sync(0xffffffffu, mu, 16);
+            mu1_o_lo = __shfl_xor_sync(0xffffffffu, mv.lo, 16);
         }
     }
     if (!active) return;
@@ -552,6 +646,8 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
         else store_levels<false, false>(A.kind, xc, jmax, A.gt_hi, A.gt_lo, col * A.kpad + (A.n0 - 1));
         A.carry[col] = gm1;
         A.carry[2 * A.nmp + col] = gm2;
+        A.carry[4 * A.nmp + col] = gm1_lo;
+        A.carry[6 * A.nmp + col] = gm2_lo;
     }
     const int exf = __float_as_int(A.coef_fwd[4 * A.nmp + col].y);     // the forward levels' exponent
     A.lacc[col] += ldexp((double)db, exf + ey);

@@ -4,10 +4,11 @@ gradient (``-m gpu``).
 
 The forward solve, the weight-derivative history sum_{k<=n} d'_{n-k} x^k and the
 reversed-time adjoint all run on FP32 levels with tensor-core histories, so each carries
-the error level of the mixed forward solve (relative 1e-6 .. 6e-5, see
+the error level of the mixed forward solve (relative ~1e-6 .. 3e-6, see
 test_gpu_mixed.py). The gradients are sums of products of the two sweeps and inherit
-that level. Bars: J and dJ/dG0 (relative L2) within 2e-4, dJ/dalpha within 5e-4
-relative (sums over all modes and steps, with partial cancellation between them).
+that level. Bars: J and dJ/dG0 (relative L2) within 5e-5 (measured <= 4.3e-6), dJ/dalpha
+within 5e-4 relative (sums over all modes and steps, with partial cancellation between
+them; measured <= 1.3e-4 on the one-step cases, where dJ/dalpha is smallest).
 The measured values are printed.
 """
 import numpy as np
@@ -72,7 +73,7 @@ def test_mixed_gradient_against_oracle_adjoint(fc, name, p):
     for prec in (fc.CQ_BF16X3, fc.CQ_TF32X3):
         eJ, eG, ea = _errs(*_grad(fc, p, G0, Gt, prec), Jr, dG0r, dar)
         print("mixed gradient %s prec %d: J %.2e dG0 %.2e dalpha %.2e %.2e" % (name, prec, eJ, eG, ea[0], ea[1]))
-        assert eJ <= 2e-4 and eG <= 2e-4
+        assert eJ <= 5e-5 and eG <= 5e-5
         assert np.all(ea <= 5e-4)
 
 
@@ -120,17 +121,16 @@ def test_mixed_vjp_dot_product(fc):
 def test_mixed_gradient_full_size(fc):
     """The 2D 255x255, N = 4096 gradient workload (BDF2, alpha = (0.4, 0.6), m = 0.4,
     target from alpha + (0.05, -0.05)): mixed against the FP64 GPU gradient, which the
-    oracle adjoint and central differences pin on smaller problems. At this length the
-    forward solve alone is within 2e-4 (test_gpu_mixed.py); the adjoint sweep adds its own
-    FP32 roundings of the same size, so J and dJ/dG0 are held to 4e-4 (measured 6e-5 ..
-    1.1e-4) and dJ/dalpha to 5e-4."""
+    oracle adjoint and central differences pin on smaller problems. The forward and the
+    adjoint sweep each carry the FP32 level of the mixed forward solve: J and dJ/dG0 are held
+    to 1e-4 (measured 6e-6 .. 2.4e-5) and dJ/dalpha to 1e-4 (measured 6e-6 .. 1.5e-5)."""
     p, G0, Gt = _grad_workload(fc)
     J64, dG64, da64 = _grad(fc, p, G0, Gt, fc.CQ_F64)
     for prec in (fc.CQ_BF16X3, fc.CQ_TF32X3):
         eJ, eG, ea = _errs(*_grad(fc, p, G0, Gt, prec), J64, dG64, da64)
         print("mixed gradient full size prec %d: J %.2e dG0 %.2e dalpha %.2e %.2e" % (prec, eJ, eG, ea[0], ea[1]))
-        assert eJ <= 4e-4 and eG <= 4e-4
-        assert np.all(ea <= 5e-4)
+        assert eJ <= 1e-4 and eG <= 1e-4
+        assert np.all(ea <= 1e-4)
 
 
 def _grad_workload(fc):

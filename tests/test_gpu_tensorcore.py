@@ -2,11 +2,14 @@
 
 Error bound, from the arithmetic: BF16 keeps 8 significant bits (unit roundoff
 2^-8), so hi = bf16(x) and lo = bf16(x - hi) leave |x - hi - lo| <= 2^-16 |x|;
-products of BF16 numbers are exact in FP32; the dropped lo*lo term is <= 2^-16 |a||b|;
-the FP32 accumulation over K terms adds at most K * 2^-24 of the sum of absolute
-terms. So element by element
-    |H_tc - H| <= (3 * 2^-16 + K * 2^-24) * sum_i |d_i| |G^{n-i}|.
-The measured errors are far below the bound; both are printed.
+products of BF16 numbers are exact in FP32; the dropped lo*lo term is <= 2^-16 |a||b|.
+The accumulator rounds toward zero once per MMA instruction (K = 16 levels, three
+products) within a chunk of 128 levels: 24 roundings of <= 2^-23 of the chunk's sum of
+absolute terms; the chunks are added to FP32 running sums with round-to-nearest
+(ceil(K / 128) roundings of <= 2^-24). So element by element
+    |H_tc - H| <= (3 * 2^-16 + 24 * 2^-23 + ceil(K / 128) * 2^-24) * sum_i |d_i| |G^{n-i}|.
+An accumulation over all K levels in the truncating accumulator (3 K / 16 roundings)
+would exceed it. The measured errors are printed beside the bound.
 """
 import numpy as np
 import pytest
@@ -30,7 +33,7 @@ def fc():
 
 
 def _bound(K):
-    return 3 * 2.0 ** -16 + K * 2.0 ** -24
+    return 3 * 2.0 ** -16 + 24 * 2.0 ** -23 + (-(-K // 128)) * 2.0 ** -24
 
 
 def _abs_scale(d, G, n):
@@ -127,10 +130,10 @@ def test_bf16x3_history_more_dof_tiles_than_grid_rows(fc):
 def _bound_tf32(K):
     """TF32x3: each split operand keeps 22 bits (<= 2^-22 relative) and the dropped lo*lo
     term is <= 2^-22, so the products carry <= 4 * 2^-22; the accumulator rounds toward
-    zero once per K = 8 instruction and product within a 128-level chunk (48 roundings,
+    zero once per K = 8 instruction and product within a 32-level chunk (12 roundings,
     <= 2^-23 each, relative to the chunk's sum of |terms|), and the chunks are summed in
-    FP32 with round-to-nearest (<= ceil(K / 128) roundings of 2^-24)."""
-    return 4 * 2.0 ** -22 + 48 * 2.0 ** -23 + (-(-K // 128)) * 2.0 ** -24
+    FP32 with round-to-nearest (<= ceil(K / 32) roundings of 2^-24)."""
+    return 4 * 2.0 ** -22 + 12 * 2.0 ** -23 + (-(-K // 32)) * 2.0 ** -24
 
 
 def _run_history(fc, prec, scheme, beta, tau, G, ndof, n_lo, n_hi, ld):
