@@ -234,6 +234,22 @@ typedef struct {
 int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double *GN_dev,
                void *ws_dev, size_t *ws_bytes, void *stream);
 
+/* The same schemes on the sine coefficients of a contiguous range of modes
+ * [mode_lo, mode_hi) of the grid (mode = ix-fastest index of the sine indices,
+ * like dof), with no transform: g0_dev holds [2][mode_hi - mode_lo] doubles, the
+ * coefficients of G^0 in the orthonormal DST-I basis of every axis (state 1 then
+ * state 2), and gN_dev receives those of G^N. In the sine basis of the Dirichlet
+ * Laplacian every mode is an independent 2x2 system (Eq. 2.1 with A diagonal), so a
+ * range is solved exactly as in fp2s_solve, mode by mode; ranges of one grid can be
+ * solved in separate calls (or on separate devices) and concatenated. The result for
+ * a mode equals fp2s_solve's before its inverse transform, bit for bit when both
+ * calls take the same kernel (the few-mode kernels serve problems with fewer than
+ * 9,728 (fast) or 38,912 (direct) modes). Same forms, precisions, flags, status and
+ * synchronisation as fp2s_solve; 0 <= mode_lo < mode_hi <= M^dim, else CQ_EINVAL.
+ * The workspace size depends on the range length (size query when ws_dev == NULL). */
+int fp2s_solve_modes(const fp2s_problem_t *p, int64_t mode_lo, int64_t mode_hi, const double *g0_dev,
+                     double *gN_dev, void *ws_dev, size_t *ws_bytes, void *stream);
+
 /* Step-by-step use of the same schemes: fp2s_init transforms G0 and sets up
  * the tables and state in the workspace; fp2s_step(n) advances from t_{n-1}
  * to t_n (n = 1..N in order) and, when G_out_dev != NULL, writes the physical

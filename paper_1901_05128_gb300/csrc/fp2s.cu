@@ -38,8 +38,9 @@ struct Fp2sLayout {
 };
 
 // hist_modes: modes of the direct FP64 history (all modes unless a gradient runs in slices).
+// lam_modes: eigenvalues computed (all modes of the grid when the solve covers a range of them).
 static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void *ws, bool stepper,
-                              bool grad = false, int64_t hist_modes = -1) {
+                              bool grad = false, int64_t hist_modes = -1, int64_t lam_modes = -1) {
     Carve cv(ws);
     Fp2sLayout l{};
     const int64_t nm = P.nmodes;
@@ -56,7 +57,7 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
         l.scr1 = cv.take<double>(2 * P.np);
         l.scr2 = cv.take<double>(2 * P.np);
     }
-    l.lam = cv.take<double>(nm);
+    l.lam = cv.take<double>(lam_modes < 0 ? nm : lam_modes);
     l.S = cv.take<double>((size_t)p->M * p->M);
     l.tmp = cv.take<double>(2 * nm);
     l.g0 = cv.take<double>(2 * nm);
@@ -1068,9 +1069,9 @@ static int read_status(const int *status_dev, cudaStream_t s) {
     return status_from_bits(host);
 }
 
-// Common set-up of fp2s_solve and fp2s_init: status, weights, tables, spectrum, DST of G0.
-static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2, const Fp2sLayout &l,
-                 const double *G0, cudaStream_t s) {
+// Status word, weights and the fast-form tables of a solve.
+static int setup_tables(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2, const Fp2sLayout &l,
+                        cudaStream_t s) {
     int st;
     const double b1 = 1.0 - p->alpha1, b2 = 1.0 - p->alpha2;
     if ((st = cuda_status(cudaMemsetAsync(l.status, 0, 64 * sizeof(int), s)))) return st;
@@ -1095,6 +1096,14 @@ static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2,
             if ((st = launched())) return st;
         }
     }
+    return CQ_OK;
+}
+
+// Common set-up of fp2s_solve and fp2s_init: status, weights, tables, spectrum, DST of G0.
+static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2, const Fp2sLayout &l,
+                 const double *G0, cudaStream_t s) {
+    int st;
+    if ((st = setup_tables(p, P, np1, np2, l, s))) return st;
     if ((st = launch_mode_eigenvalues(p->M, p->dim, l.lam, s))) return st;
     if ((st = launch_dst_matrix(p->M, l.S, s))) return st;
     return launch_dst_field(p->M, p->dim, l.S, G0, l.g0, l.tmp, s);
@@ -1135,6 +1144,21 @@ static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s
 
 using namespace fastcq;
 
+// The time loop of a solve on the modal G^0 in l.g0, writing the modal G^N to l.gN: the
+// fused kernel, or the block / contraction launches of the mixed-precision direct solve.
+static int run_modes(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
+    int st;
+    if ((st = timing_begin(s))) return st;
+    if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3)) {
+        // counts its own launches
+        if ((st = mixed_direct_run(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.hdf, l.mixed, s))) return st;
+    } else {
+        if ((st = solve_kernel(P, l, s))) return st;
+        if ((st = launched())) return st;
+    }
+    return timing_end(s);
+}
+
 extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double *GN_dev, void *ws_dev,
                           size_t *ws_bytes, void *stream) {
     Fp2sParams P;
@@ -1148,16 +1172,35 @@ extern "C" int fp2s_solve(const fp2s_problem_t *p, const double *G0_dev, double 
     if (!G0_dev || !GN_dev || ((uintptr_t)ws_dev & 255)) return CQ_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
-    if ((st = timing_begin(s))) return st;
-    if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3)) {
-        // counts its own launches
-        if ((st = mixed_direct_run(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.hdf, l.mixed, s))) return st;
-    } else {
-        if ((st = solve_kernel(P, l, s))) return st;
-        if ((st = launched())) return st;
-    }
-    if ((st = timing_end(s))) return st;
+    if ((st = run_modes(P, l, s))) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, l.gN, GN_dev, l.tmp, s))) return st;
+    if (p->flags & FP2S_ASYNC) return CQ_OK;
+    return read_status(l.status, s);
+}
+
+extern "C" int fp2s_solve_modes(const fp2s_problem_t *p, int64_t mode_lo, int64_t mode_hi, const double *g0_dev,
+                                double *gN_dev, void *ws_dev, size_t *ws_bytes, void *stream) {
+    Fp2sParams P;
+    int np1 = 0, np2 = 0;
+    int st = derive(p, P, np1, np2);
+    if (st) return st;
+    if (!ws_bytes) return CQ_EINVAL;
+    const int64_t all = P.nmodes;
+    if (mode_lo < 0 || mode_hi > all || mode_lo >= mode_hi) return CQ_EINVAL;
+    P.nmodes = mode_hi - mode_lo;
+    Fp2sLayout l = fp2s_layout(p, P, ws_dev, false, false, -1, all);
+    if (!ws_dev) { *ws_bytes = l.bytes; return CQ_OK; }
+    if (*ws_bytes < l.bytes) return CQ_ENOMEM;
+    if (!g0_dev || !gN_dev || ((uintptr_t)ws_dev & 255)) return CQ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = setup_tables(p, P, np1, np2, l, s))) return st;
+    if ((st = launch_mode_eigenvalues(p->M, p->dim, l.lam, s))) return st;
+    // the kernels see the range as a problem of its own: its spectrum, modal G^0 and G^N
+    Fp2sLayout lr = l;
+    lr.lam = l.lam + mode_lo;
+    lr.g0 = const_cast<double *>(g0_dev);
+    lr.gN = gN_dev;
+    if ((st = run_modes(P, lr, s))) return st;
     if (p->flags & FP2S_ASYNC) return CQ_OK;
     return read_status(l.status, s);
 }

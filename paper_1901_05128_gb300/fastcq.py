@@ -69,6 +69,7 @@ def _load():
         "cq_history_fast": (C.c_int, [I32, D, D, C.POINTER(FastCfg), I64, I64, P, P, I32, P, SZ, P]),
         "cq_history_fast_noalloc": (C.c_int, [I32, D, D, C.POINTER(FastCfg), I64, I64, P, P, I32, P]),
         "fp2s_solve": (C.c_int, [C.POINTER(Problem), P, P, P, SZ, P]),
+        "fp2s_solve_modes": (C.c_int, [C.POINTER(Problem), I64, I64, P, P, P, SZ, P]),
         "fp2s_init": (C.c_int, [C.POINTER(Problem), P, P, SZ, P]),
         "fp2s_step": (C.c_int, [C.POINTER(Problem), I64, P, C.c_size_t, P, P]),
         "fp2s_modal": (C.c_int, [C.POINTER(Problem), P, C.c_size_t, P, P]),
@@ -91,7 +92,7 @@ _lib = _load()
 EXPORTS = ("cq_strerror", "cq_launch_count", "cq_timing_enable", "cq_timing_last", "cq_timing_part",
            "cq_test_expire_waits", "cq_weights",
            "cq_gauss_jacobi", "cq_fast_coeffs", "cq_history_direct", "cq_split", "cq_history_fast",
-           "cq_history_fast_noalloc", "fp2s_solve",
+           "cq_history_fast_noalloc", "fp2s_solve", "fp2s_solve_modes",
            "fp2s_init", "fp2s_step", "fp2s_modal", "fp2s_status", "fp2s_gradient", "fp2s_vjp", "fp2s_batch_plan",
            "fp2s_solve_batched", "fp2s_batch_status")
 
@@ -213,6 +214,17 @@ def fp2s_solve(p: Problem, G0_dev, GN_dev, ws_dev=None, stream=None, check=True)
         _check(st, "fp2s_solve")
     elif st not in (CQ_OK, CQ_ENONFINITE):
         _check(st, "fp2s_solve")
+    return sz.value if ws_dev is None else st
+
+
+def fp2s_solve_modes(p: Problem, mode_lo, mode_hi, g0_dev, gN_dev, ws_dev=None, stream=None, check=True) -> int:
+    sz = C.c_size_t(0 if ws_dev is None else _nbytes(ws_dev))
+    st = _lib.fp2s_solve_modes(C.byref(p), int(mode_lo), int(mode_hi), _ptr(g0_dev), _ptr(gN_dev), _ptr(ws_dev),
+                               C.byref(sz), _stream(stream, ws_dev is None))
+    if check:
+        _check(st, "fp2s_solve_modes")
+    elif st not in (CQ_OK, CQ_ENONFINITE):
+        _check(st, "fp2s_solve_modes")
     return sz.value if ws_dev is None else st
 
 

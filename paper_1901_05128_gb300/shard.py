@@ -33,3 +33,26 @@ def gather_modal(local, nmodes: int, group=None):
     parts = [torch.empty_like(buf) for _ in range(world)]
     dist.all_gather(parts, buf, group=group)
     return torch.cat([p[:, : hi - lo] for p, (lo, hi) in zip(parts, shards)], dim=1)
+
+
+def solve_sharded(fc, problem, g0_modal, group=None, stream=None):
+    """This rank's contiguous shard of the sine modes solved with ``fp2s_solve_modes`` (no
+    exchange during the time loop), then the modal G^N of every rank all-gathered.
+
+    ``fc`` is the binding module, ``problem`` an ``fp2s_problem_t`` and ``g0_modal`` the
+    [2][M^dim] sine coefficients of G^0 on this rank's device (every rank holds them; only
+    its shard is read). Returns the [2][M^dim] modal G^N. A rank whose shard is empty (more
+    ranks than modes) solves nothing and contributes an empty shard."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    nm = g0_modal.shape[1]
+    lo, hi = mode_shards(nm, world)[rank]
+    if hi > lo:
+        g0 = g0_modal[:, lo:hi].contiguous()
+        gN = torch.empty_like(g0)
+        ws = fc.workspace(fc.fp2s_solve_modes(problem, lo, hi, g0, gN, None, stream=stream), g0.device)
+        fc.fp2s_solve_modes(problem, lo, hi, g0, gN, ws, stream=stream)
+    else:
+        gN = torch.empty((2, 0), dtype=g0_modal.dtype, device=g0_modal.device)
+    return gather_modal(gN, nm, group)

@@ -188,3 +188,16 @@ def test_workspace_too_small(fc):
     sz = C.c_size_t(256)
     st = fc._lib.fp2s_solve(C.byref(p), 1 << 20, 1 << 20, small.data_ptr(), C.byref(sz), None)
     assert st == fc.CQ_ENOMEM
+
+
+def test_mode_range_validation(fc):
+    """fp2s_solve_modes: 0 <= mode_lo < mode_hi <= M^dim; the workspace follows the range length."""
+    p = fc.problem(0.3, 0.7, 0.3, 1.0, 64, 2, 15, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2)
+    sz = C.c_size_t(0)
+    lib = fc._lib
+    for lo, hi in ((-1, 10), (0, 226), (5, 5), (7, 3)):
+        assert lib.fp2s_solve_modes(C.byref(p), lo, hi, None, None, None, C.byref(sz), None) == fc.CQ_EINVAL
+    assert lib.fp2s_solve_modes(C.byref(p), 0, 225, None, None, None, C.byref(sz), None) == fc.CQ_OK
+    whole = sz.value
+    assert lib.fp2s_solve_modes(C.byref(p), 100, 110, None, None, None, C.byref(sz), None) == fc.CQ_OK
+    assert 0 < sz.value < whole

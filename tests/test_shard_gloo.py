@@ -1,6 +1,8 @@
-"""World-size-2 test of the mode sharding on CPU (gloo): each rank advances its shard of
-sine modes (with the oracle as the CPU stand-in for the per-mode solve), the shards are
-all-gathered, and the result equals the unsharded solve."""
+"""World-size-2 tests of the mode sharding on CPU (gloo). ``solve_sharded`` (the product's
+sharded solve) runs with a CPU stand-in for the binding whose ``fp2s_solve_modes`` is the
+oracle's per-mode scheme (the CUDA entry point itself is tested on the GPU, shard by shard,
+in test_gpu_modes.py); the shards are all-gathered and the result equals the unsharded
+solve."""
 import os
 import socket
 
@@ -41,17 +43,45 @@ def _worker(rank, world, port, out_path):
     from oracle import spatial as OSP
     from paper_1901_05128_gb300.shard import gather_modal
 
+    from paper_1901_05128_gb300.shard import solve_sharded
+
     p = ci.Problem(0.35, 0.65, 0.4, 1.0, 120, 2, 9, ci.BDF2, ci.FAST, 8, 16, 9)
     G0 = ci.g0_uniform(p.M, p.dim, 5)
     nm = p.M ** p.dim
-    lo, hi = mode_shards(nm, world)[rank]
-    lam = OSP.mode_eigenvalues(p.M, p.dim)[lo:hi]
-    g0 = OSP.to_modal(G0, p.M, p.dim)[:, lo:hi]
-    local = OS.solve_modal(p, lam, g0)[p.N]
-    full = gather_modal(torch.tensor(local), nm).numpy()
+    g0m = torch.tensor(OSP.to_modal(G0, p.M, p.dim))
+    full = solve_sharded(_OracleBinding(p, rank), "problem", g0m).numpy()
     if rank == 0:
         np.save(out_path, OSP.to_physical(full, p.M, p.dim))
+    # more ranks than modes: the empty shards contribute nothing
+    tiny = ci.Problem(0.35, 0.65, 0.4, 1.0, 20, 1, 1, ci.BE, ci.FAST, 8, 0, 2)
+    one = solve_sharded(_OracleBinding(tiny, rank), "problem",
+                        torch.tensor([[1.0], [0.5]], dtype=torch.float64)).numpy()
+    if rank == 0:
+        np.save(out_path + ".tiny.npy", one)
     dist.destroy_process_group()
+
+
+class _OracleBinding:
+    """CPU stand-in for the binding module: fp2s_solve_modes runs the oracle's per-mode
+    scheme on the requested range; the size query returns a dummy size. Records the ranges
+    it was asked for."""
+
+    def __init__(self, p, rank):
+        self.p, self.rank, self.calls = p, rank, []
+
+    def workspace(self, nbytes, device):
+        return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+    def fp2s_solve_modes(self, problem, lo, hi, g0, gN, ws, stream=None):
+        from oracle import scheme as OS
+        from oracle import spatial as OSP
+        if ws is None:
+            return 256
+        assert g0.shape == (2, hi - lo)
+        self.calls.append((lo, hi))
+        lam = OSP.mode_eigenvalues(self.p.M, self.p.dim)[lo:hi]
+        gN.copy_(torch.tensor(OS.solve_modal(self.p, lam, g0.numpy())[self.p.N]))
+        return 0
 
 
 def test_sharded_solve_equals_unsharded(tmp_path):
@@ -63,3 +93,7 @@ def test_sharded_solve_equals_unsharded(tmp_path):
     ref = OS.solve(p, ci.g0_uniform(p.M, p.dim, 5))
     got = np.load(out)
     assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))
+    tiny = ci.Problem(0.35, 0.65, 0.4, 1.0, 20, 1, 1, ci.BE, ci.FAST, 8, 0, 2)
+    from oracle import spatial as OSP
+    ref1 = OS.solve_modal(tiny, OSP.mode_eigenvalues(1, 1), np.array([[1.0], [0.5]]))[tiny.N]
+    assert np.array_equal(np.load(out + ".tiny.npy"), ref1)
