@@ -28,9 +28,9 @@ import sys
 import tempfile
 import time
 
-# The oracle legs run on one host thread and report cores = 1: their per-step numpy arithmetic is
-# element-wise, and the vector-matrix products of the direct history must not fan out to BLAS
-# threads either (set before numpy is first imported).
+# Every oracle process does its numpy work on one thread: the one-thread figures use one core,
+# and the all-core figures run one spawned process per core (set before numpy is first imported,
+# and inherited by the spawned processes).
 for _var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ[_var] = "1"
 
@@ -43,8 +43,7 @@ UNIT = "DOF·steps/s"
 WORKLOAD = "bdf2_2d_m255"
 SCALE = 2.0 ** -1000
 FP64_PEAK_NOMINAL = 1.25e12       # FP64 FLOP/s of GB300 (2 DFMA / clock / SM x 152 SMs x ~2.07 GHz)
-FP64_PEAK_PROBE = 1.199e12        # own DFMA-chain probe on this machine's GB300 (independent FMA chains)
-FP32_PEAK_PROBE = 73.2e12         # own FFMA-chain probe, same method
+FP32_PEAK_PROBE = 73.2e12         # FP32 FMA probe figure of an earlier run (used only if the probe cannot run)
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -79,8 +78,118 @@ def oracle_sample(p, G0, n_modes, seed):
     return sample, g[p.N], dt
 
 
-def cpu_cores_used():
-    return 1        # the oracle's time loop is numpy element-wise work on one thread
+def mode_jobs(p, G0, n_modes, seeds):
+    """One oracle job per seed: the per-mode scheme of p on n_modes seeded sine modes."""
+    import numpy as np
+    from oracle import spatial as OSP
+    import cq_inputs as ci
+    nm = p.M ** p.dim
+    lam_all = OSP.mode_eigenvalues(p.M, p.dim)
+    g0_all = OSP.to_modal(G0, p.M, p.dim)
+    jobs = []
+    for sd in seeds:
+        idx = np.sort(ci.sample_indices(nm, min(n_modes, nm), sd))
+        jobs.append(("modes", p, lam_all[idx], g0_all[:, idx]))
+    return jobs
+
+
+def _oracle_job(job):
+    """One oracle computation (in a spawned worker process, or in this process); returns its
+    wall time in seconds. Jobs: ("modes", problem, lam, g0) the per-mode scheme;
+    ("history", scheme, beta, tau, G) the direct history of DOF columns; ("gradient",
+    problem, G0, Gt) the discrete adjoint gradient; ("warm",) imports only."""
+    kind = job[0]
+    if kind == "warm":
+        from oracle import adjoint, history, scheme  # noqa: F401
+        return 0.0
+    t = time.perf_counter()
+    if kind == "modes":
+        from oracle import scheme as OS
+        OS.solve_modal(job[1], job[2], job[3])
+    elif kind == "history":
+        from oracle import history as OH
+        from oracle import weights as OW
+        G = job[4]
+        OH.history_direct_all(OW.weights(job[1], job[2], job[3], G.shape[0]), G, 1, G.shape[0])
+    elif kind == "gradient":
+        from oracle import adjoint as AD
+        AD.gradient(job[1], job[2], job[3])
+    else:
+        raise ValueError(kind)
+    return time.perf_counter() - t
+
+
+_POOL = None
+
+
+def _oracle_pool():
+    """A pool of one spawned process per host core (spawn: safe after CUDA is initialised),
+    warmed up so that the timed maps do not include interpreter start-up and imports."""
+    global _POOL
+    if _POOL is None:
+        import multiprocessing as mp
+        n = os.cpu_count() or 1
+        _POOL = mp.get_context("spawn").Pool(n)
+        _POOL.map(_oracle_job, [("warm",)] * (4 * n), chunksize=1)
+    return _POOL
+
+
+def _close_pool():
+    global _POOL
+    if _POOL is not None:
+        _POOL.close()
+        _POOL.join()
+        _POOL = None
+
+
+def _ncpu():
+    return os.cpu_count() or 1
+
+
+def cpu_info():
+    """Host cores and CPU model (from /proc/cpuinfo: model name, or the Arm implementer / part)."""
+    model = None
+    try:
+        txt = open("/proc/cpuinfo").read()
+        for key in ("model name", "Model Name", "Processor"):
+            for line in txt.splitlines():
+                if line.split(":")[0].strip() == key:
+                    model = line.split(":", 1)[1].strip()
+                    break
+            if model:
+                break
+        if not model:
+            fields = {}
+            for line in txt.splitlines():
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+            if "CPU implementer" in fields:
+                model = "Arm implementer %s part %s" % (fields.get("CPU implementer"), fields.get("CPU part"))
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count() or 1, "model": model or platform.processor() or platform.machine()}
+
+
+def cpu_baseline(unit, units_one, t_one, sample_one, jobs_all=None, units_all=None, sample_all=None):
+    """The oracle's rate on the host: on every core (one spawned process per core running
+    jobs_all, wall time of the whole map) with the one-thread figure beside it (units_one
+    units of work in t_one seconds on one core)."""
+    one = {"value": units_one / t_one, "unit": unit, "cores": 1, "seconds": t_one, "sample": sample_one}
+    info = cpu_info()
+    out = {"kind": "oracle", "unit": unit, "one_thread": one, "cpu_model": info["model"], "nproc": info["nproc"]}
+    if jobs_all:
+        pool = _oracle_pool()
+        t = time.perf_counter()
+        pool.map(_oracle_job, jobs_all, chunksize=1)
+        wall = time.perf_counter() - t
+        out.update({"value": units_all / wall, "cores": info["nproc"], "seconds": wall,
+                    "sample": "%s (%d jobs over %d processes, one per core)" % (sample_all, len(jobs_all),
+                                                                              info["nproc"])})
+    else:
+        out.update({"value": one["value"], "cores": 1, "seconds": t_one, "sample": sample_one})
+    return out
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -320,12 +429,16 @@ def precision_report(leg, cpu_modes):
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)",
                      "algorithmic_flops_per_launch": useful,
                      "flops_definition": "3 products x 2 x ndof x sum_n (n-1) (strictly lower-triangular Toeplitz)"},
-        "error_vs_oracle": {"max_abs_err_over_sum_abs_terms": tc_err, "bound": 3 * 2.0 ** -16 + rows * 2.0 ** -24,
+        "error_vs_oracle": {"max_abs_err_over_sum_abs_terms": tc_err,
+                            "bound": 3 * 2.0 ** -16 + 24 * 2.0 ** -23 + (-(-rows // 128)) * 2.0 ** -24,
                             "sample": "%d whole DOF columns x %d steps" % (PREC_COLS, rows)},
         "gpu_launches_per_call": leg["tc_launches"] / max(1, len(leg["tc_gemm_ms"])),
-        "cpu_baseline": {"value": PREC_COLS * rows / t_orc, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "oracle direct history of %d DOF columns x %d steps (%.1f s)"
-                                   % (PREC_COLS, rows, t_orc)},
+        "cpu_baseline": cpu_baseline(
+            UNIT, PREC_COLS * rows, t_orc, "oracle direct history of %d DOF columns x %d steps" % (PREC_COLS, rows),
+            [("history", ci.BE, leg["tc_beta"], leg["tc_tau"], ci.rng(ci.SEED_BASE + 50 + k).standard_normal(
+                (n_hi, PREC_COLS))) for k in range(_ncpu())],
+            _ncpu() * PREC_COLS * rows, "oracle direct history of %d synthetic DOF columns x %d steps per job"
+            % (PREC_COLS, rows)),
     }
     tf_gemm = statistics.mean(leg["tf32_gemm_ms"])
     tf32_peak = bf16_peak * 1.1 / 2.25            # nominal TF32 : BF16 dense ratio
@@ -365,13 +478,17 @@ def precision_report(leg, cpu_modes):
         "precision": "FP32 history state and sums, FP64 tables, double-float 2x2 step",
         "value": q.ndof * q.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
         "roofline": {"kernel": "k_fp2s_fast_f32", "bound": "alu", "unit": "TFLOP/s",
-                     "achieved": f32_flops / (kms * 1e-3) / 1e12, "peak": FP32_PEAK_PROBE / 1e12,
-                     "frac": f32_flops / (kms * 1e-3) / FP32_PEAK_PROBE,
-                     "peak_source": "own FFMA probe (FP32)", "kernel_ms": kms},
+                     "achieved": f32_flops / (kms * 1e-3) / 1e12, "peak": alu_peak("fp32")[0] / 1e12,
+                     "frac": f32_flops / (kms * 1e-3) / alu_peak("fp32")[0],
+                     "peak_source": alu_peak("fp32")[1], "kernel_ms": kms,
+                     "flops_definition": "(4 np + 2) per DOF-step (node recurrences, history sums, C G^{n-L}); "
+                                         "the double-float remainders of the slow nodes and weights are not counted"},
         "error_vs_fp64_oracle_rel_l2_sampled_modes": f32_err, "status": leg["f32_status"],
-        "cpu_baseline": {"value": 2 * len(sample) * q.N / t_f, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "oracle FP64 fast BE scheme, %d modes x %d steps (%.1f s)"
-                                   % (len(sample), q.N, t_f)},
+        "cpu_baseline": cpu_baseline(
+            UNIT, 2 * len(sample) * q.N, t_f, "oracle FP64 fast BE scheme, %d modes x %d steps" % (len(sample), q.N),
+            mode_jobs(q, G0, len(sample), [ci.SEED_BASE + 60 + k for k in range(_ncpu())]),
+            _ncpu() * 2 * len(sample) * q.N, "oracle FP64 fast BE scheme, %d seeded modes x %d steps per job"
+            % (len(sample), q.N)),
     }
     return {"tensor_core_direct_history": tc, "tensor_core_direct_history_tf32x3": tf32, "fp32_fast_solve": f32,
             "mixed_direct_solve": mixed_report(leg["mixed"], G0, cpu_modes)}
@@ -440,9 +557,12 @@ def mixed_report(runs, G0, cpu_modes):
         "per_step_note": "main case (BE, alpha = (0.2, 0.8), BF16x3): level n of the N = 8192 run is the final "
                          "level of the same scheme with N = n and T = n tau",
         "cases": cases,
-        "cpu_baseline": {"value": 2 * len(sample) * q.N / t_orc, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "oracle FP64 direct BE scheme, %d modes x %d steps (%.1f s)"
-                                   % (len(sample), q.N, t_orc)},
+        "cpu_baseline": cpu_baseline(
+            UNIT, 2 * len(sample) * q.N, t_orc, "oracle FP64 direct BE scheme, %d modes x %d steps"
+            % (len(sample), q.N),
+            mode_jobs(q, G0, len(sample), [ci.SEED_BASE + 70 + k for k in range(_ncpu())]),
+            _ncpu() * 2 * len(sample) * q.N, "oracle FP64 direct BE scheme, %d seeded modes x %d steps per job"
+            % (len(sample), q.N)),
     }
 
 
@@ -507,11 +627,31 @@ def gradient_leg(fc, torch, dev, K, flush):
         "dof_steps_per_s": p.ndof * p.N / (ms * 1e-3),
         "kernels_ms": statistics.mean(kern), "J": J, "dJ_dalpha": list(da), "fd_dJ_dalpha": fd,
         "rel_err_vs_central_differences": rel, "fd_step": eps,
-        "cpu_baseline": None,
-        "cpu_baseline_note": "the oracle adjoint is an O(N^2) Python loop; at N = 4096 it exceeds the bench's CPU "
-                             "budget, so it is timed only in the tests on small problems",
+        "cpu_baseline": gradient_cpu_baseline(p),
         "mixed_precision": mixed,
     }
+
+
+def gradient_cpu_baseline(p):
+    """The oracle's discrete adjoint (forward scheme, reversed-time adjoint, dJ/dalpha) on a
+    bounded sample of the gradient workload: the same scheme, alpha, m and tau on a 15 x 15 grid
+    over the first 1024 steps (the direct gradient is O(N^2) per mode, with Python loops over the
+    step pairs: the full 4096-step problem would take minutes). One gradient on one core, and one
+    per core at once."""
+    import cq_inputs as ci
+    from oracle import scheme as OS
+    q = p.replace(M=15, N=1024, T=p.T * 1024 / p.N)
+    tgt = OS.solve(q.replace(alpha1=q.alpha1 + 0.05, alpha2=q.alpha2 - 0.05), ci.g0_checkerboard_uniform(15, 1))
+    jobs = [("gradient", q, ci.g0_checkerboard_uniform(15, ci.SEED_BASE + 90 + k), tgt) for k in range(_ncpu())]
+    t1 = _oracle_job(jobs[0])
+    units = q.ndof * q.N
+    desc = "oracle adjoint gradient, 2D 15x15 (%d DOF), first %d steps at tau = 1/%d, BDF2 direct" % (
+        q.ndof, q.N, p.N)
+    out = cpu_baseline(UNIT, units, t1, desc + ": one gradient", jobs, len(jobs) * units,
+                       desc + ", one gradient per job")
+    out["grad_steps_per_s"] = {"one_thread": 1.0 / t1, "all_cores": out["value"] / units,
+                               "note": "gradients of the sample problem per second"}
+    return out
 
 
 def mixed_gradient_run(fc, torch, dev, p, g0, gt, prec, name, J64, da64, dG64, fd, ms64, K, flush):
@@ -604,6 +744,28 @@ def batch_leg(fc, torch, dev, K, flush):
     launches = (fc.cq_launch_count() - l0) / K
     status = fc.strerror(fc.fp2s_batch_status(plan, ws))
     batch = gN.cpu().numpy()
+    # the same solve captured once in a CUDA graph and replayed (no host work per replay)
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        with torch.cuda.graph(graph, stream=gs):
+            fc.fp2s_solve_batched(plan, g0, gN, ws)
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    replay = []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        e1.synchronize()
+        replay.append(e0.elapsed_time(e1))
+    replay_same = bool(np.array_equal(gN.cpu().numpy(), batch))
+    del graph
     del ws
     # the same instances, one fp2s_solve each (same arithmetic per mode)
     singles, t_single, o = [], 0.0, 0
@@ -634,20 +796,43 @@ def batch_leg(fc, torch, dev, K, flush):
         np_, L = (p.np1, 2) if p.scheme == ci.BE else (p.np1 + p.np2, p.ns)
         flops += (4 * np_ + 2 * (L - 1)) * 2.0 * p.M ** p.dim * p.N
     kms = statistics.mean(kern)
+    # oracle: a seeded 16-instance subset, each on a seeded sample of at most 64 sine modes x all its steps
+    from oracle import spatial as OSP
+    pick = ci.sample_indices(len(probs), 16, ci.SEED_BASE + 95)
+    jobs, units_each = [], []
+    for k, i in enumerate(pick):
+        q, f = probs[i], fields[i]
+        jobs += mode_jobs(q, f, 64, [ci.SEED_BASE + 96 + k])
+        units_each.append(2 * min(64, q.M ** q.dim) * q.N)
+    t1 = sum(_oracle_job(j) for j in jobs)
+    reps = max(1, -(-2 * _ncpu() // len(jobs)))
+    jobs_all = [(j[0], j[1], j[2], j[3]) for _ in range(reps) for j in jobs]
+    cpu = cpu_baseline(UNIT, sum(units_each), t1, "oracle FP64 fast scheme, seeded 16-instance subset, <= 64 "
+                       "seeded modes per instance x all its steps", jobs_all, reps * sum(units_each),
+                       "the same 16 instance samples, %d times over" % reps)
     return {
         "workload": "256 seeded instances (alpha ~ U(0.1,0.9), m in [0.30,0.48]U[0.52,0.70], 1D M in [31,1023] "
                     "or 2D M in [31,255] log-uniform, N in [512,8192] log-uniform, BE/BDF2), FP64 fast form, "
                     "G0 = U[0,1) on [1/4,3/4]^d x 2^-1000; %d draws replaced by the growth screen" % redraws,
         "value": dof_steps / (ms * 1e-3), "unit": UNIT, "ms_per_batch": ms, "kernel_ms": statistics.mean(kern),
-        "total_dof_steps": dof_steps, "warps_per_block": plan.warps_per_block, "autotuned": bool(plan.flags & 1),
+        "total_dof_steps": dof_steps,
+        "graph_replay": {"value": dof_steps / (statistics.mean(replay) * 1e-3), "unit": UNIT,
+                         "ms_per_batch": statistics.mean(replay), "same_result_as_direct_calls": replay_same,
+                         "note": "fp2s_solve_batched captured once in a CUDA graph (five kernels, one memset), "
+                                 "replayed; L2 flushed before every replay, outside the events"},
+        "launch_shape": {"warps_per_block": plan.warps_per_block, "ctas_per_sm": plan.ctas_per_sm or "all that fit",
+                         "autotuned": bool(plan.flags & 1), "candidates_timed": plan.tuned_candidates,
+                         "tuner": "block widths 2..16 warps x (all, half of the CTAs per SM that fit), 96-step run, "
+                                  "median of three timings each"},
         "plan_s": plan_s, "gpu_launches_per_solve": launches, "status": status,
         "sum_of_single_solves_ms": t_single, "persistent_launch_efficiency": t_single / ms,
         "max_abs_diff_vs_single_solves_rel_to_instance_max": max(singles),
         "roofline": {"kernel": "k_b_fast", "bound": "alu", "unit": "TFLOP/s",
-                     "achieved": flops / (kms * 1e-3) / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
-                     "frac": flops / (kms * 1e-3) / FP64_PEAK_NOMINAL, "peak_source": "nominal FP64 rate (recipe)",
+                     "achieved": flops / (kms * 1e-3) / 1e12, "peak": alu_peak("fp64")[0] / 1e12,
+                     "frac": flops / (kms * 1e-3) / alu_peak("fp64")[0], "peak_source": alu_peak("fp64")[1],
                      "algorithmic_flops_per_launch": flops,
                      "flops_definition": "sum over instances of (4 np + 2 (L - 1)) x DOF x N"},
+        "cpu_baseline": cpu,
     }
 
 
@@ -689,8 +874,10 @@ def small_leg(fc, torch, dev, K):
         "value": p.ndof * p.N / (ms * 1e-3), "unit": UNIT, "ms_per_solve": ms,
         "note": "launch- and latency-bound (the whole history fits in L2); no roofline fraction",
         "rel_l2_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-        "cpu_baseline": {"value": p.ndof * p.N / t_orc, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "oracle direct BE scheme, all 63 modes x 1024 steps (%.2f s)" % t_orc},
+        "cpu_baseline": cpu_baseline(
+            UNIT, p.ndof * p.N, t_orc, "oracle direct BE scheme, all 63 modes x 1024 steps",
+            mode_jobs(p, G0, p.M, [ci.SEED_BASE + 80 + k for k in range(4 * _ncpu())]),
+            4 * _ncpu() * p.ndof * p.N, "oracle direct BE scheme, all 63 modes x 1024 steps per job"),
     }
 
 
@@ -774,10 +961,10 @@ def _stream_case(fc, torch, dev, ndof, steps, precs):
             flops = (4 * npt + 2 * (ns - 1)) * ndof
             tf = flops / (ms * 1e-3) / 1e12
             roof = {"kernel": "k_history_fast_step", "bound": "alu", "unit": "TFLOP/s", "achieved": tf,
-                    "peak": FP64_PEAK_NOMINAL / 1e12, "frac": tf * 1e12 / FP64_PEAK_NOMINAL,
-                    "peak_source": "nominal FP64 rate (recipe)", "algorithmic_flops_per_launch": flops,
+                    "peak": alu_peak("fp64")[0] / 1e12, "frac": tf * 1e12 / alu_peak("fp64")[0],
+                    "peak_source": alu_peak("fp64")[1], "algorithmic_flops_per_launch": flops,
                     "hbm": hbm_roof,
-                    "note": "FP64 time floor %.3f ms vs HBM floor %.3f ms" % (flops / FP64_PEAK_NOMINAL * 1e3,
+                    "note": "FP64 time floor %.3f ms vs HBM floor %.3f ms" % (flops / alu_peak("fp64")[0] * 1e3,
                                                                              bytes_per_launch / (hbm * 1e9) * 1e3)}
         else:
             roof = hbm_roof
@@ -788,6 +975,52 @@ def _stream_case(fc, torch, dev, ndof, steps, precs):
                        "state %.2f GB (FP32) / %.2f GB (FP64) streamed every step; median of %d steps"
                        % (ndof, npt, ns, npt * ndof * 4 / 1e9, npt * ndof * 8 / 1e9, steps))
     return out
+
+
+_ALU = {}
+
+
+def fma_peaks(torch, dev):
+    """FP64 and FP32 FMA rates of this GPU from the probe library (libcqprobe.so, built with the
+    package): 8 CTAs of 256 threads per SM, 8 independent FMA chains per thread, ~50 ms per
+    timed launch. They are the ALU roofs of the fast solves (the measured copy and GEMM peaks
+    cover HBM and the tensor pipe)."""
+    import ctypes as C
+    import importlib
+    B = importlib.import_module("paper_1901_05128_gb300.build")
+    lib = C.CDLL(B.PROBE_LIB)
+    f = lib.cq_probe_fma_rate
+    f.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]
+    f.restype = C.c_int
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    res = {}
+    for name, prec, iters in (("fp64", 0, 12000), ("fp32", 1, 700000)):
+        rates = []
+        for _ in range(3):
+            r = C.c_double(0.0)
+            st = f(prec, blocks, threads, iters, C.c_void_p(out.data_ptr()),
+                   C.byref(r), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+            if st != 0:
+                raise RuntimeError("FMA probe failed (%d)" % st)
+            rates.append(r.value)
+        res[name] = {"tflops": max(rates) / 1e12, "runs_tflops": [x / 1e12 for x in rates]}
+        _ALU[name] = max(rates)
+    res["method"] = ("libcqprobe cq_probe_fma_rate: %d blocks x %d threads, 8 independent FMA chains per thread; "
+                     "best of 3 timed launches" % (blocks, threads))
+    res["nominal_fp64_tflops"] = FP64_PEAK_NOMINAL / 1e12
+    return res
+
+
+def alu_peak(name):
+    """(peak FLOP/s, source) of the FP64 or FP32 pipe: the probe's figure from this run, else the
+    nominal FP64 rate / a previous probe figure for FP32."""
+    if name in _ALU:
+        return _ALU[name], "FMA-rate probe in this run (libcqprobe, peaks.%s)" % name
+    if name == "fp64":
+        return FP64_PEAK_NOMINAL, "nominal FP64 rate (2 DFMA / clock / SM x 152 SMs x 2.07 GHz)"
+    return FP32_PEAK_PROBE, "FMA-rate probe figure of an earlier run"
 
 
 def _measured_peaks():
@@ -857,6 +1090,7 @@ def run_ours(args, rank, world, dist):
 
     K, W = args.steps, args.warmup
     with ClockSampler(torch.cuda.current_device()) as clk:
+        peaks = fma_peaks(torch, dev) if rank == 0 else None
         steps, mains, launches, st_fast = timed(p, K, W)
         gN_fast = gN.cpu().numpy()
         pd = p.replace(form=ci.DIRECT)
@@ -894,6 +1128,14 @@ def run_ours(args, rank, world, dist):
         paper = paper_leg(fc, torch) if (args.precision and rank == 0) else None
         small = small_leg(fc, torch, dev, 10) if (args.precision and rank == 0) else None
     clocks = clk.summary()
+    # the same workload on its sine coefficients (fp2s_solve_modes, no transform): the modal
+    # result for the parity check against the oracle
+    gm_fast = gm_dir = None
+    if rank == 0:
+        from oracle import spatial as OSP
+        g0m = torch.tensor(OSP.to_modal(G0, p.M, p.dim), dtype=torch.float64, device=dev)
+        gm_fast, gm_dir = (_modal_solve(fc, torch, dev, cproblem(q), g0m) for q in (p, p.replace(form=ci.DIRECT)))
+        del g0m
 
     ms = statistics.mean(steps)
     ms_main = statistics.mean(mains)
@@ -912,10 +1154,10 @@ def run_ours(args, rank, world, dist):
     hist_flops_per_dof_step = 4 * (p.np1 + p.np2) + 2 * (p.ns - 1)
     flops_per_launch = hist_flops_per_dof_step * units
     achieved = flops_per_launch / (ms_main * 1e-3)
+    pk, pk_src = alu_peak("fp64")
     roofline = {"kernel": "k_fp2s_fast", "bound": "alu", "unit": "TFLOP/s",
-                "achieved": achieved / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
-                "frac": achieved / FP64_PEAK_NOMINAL, "peak_source": "nominal FP64 rate (recipe); own DFMA probe "
-                "measured %.3f TFLOP/s" % (FP64_PEAK_PROBE / 1e12),
+                "achieved": achieved / 1e12, "peak": pk / 1e12, "frac": achieved / pk, "peak_source": pk_src,
+                "frac_of_nominal_fp64": achieved / FP64_PEAK_NOMINAL,
                 "traffic": None, "algorithmic_flops_per_launch": flops_per_launch,
                 "flops_per_dof_step": hist_flops_per_dof_step, "kernel_ms": ms_main,
                 "kernel_share_of_step": ms_main / ms}
@@ -924,68 +1166,150 @@ def run_ours(args, rank, world, dist):
         roofline["traffic"] = traffic
         roofline["traffic_note"] = "ncu dram bytes per launch (independent of N: state stays on chip)"
 
-    # oracle leg: bounded sample, also gives the error of this run
+    # oracle legs: bounded samples, which also give the errors of this run
     import numpy as np
-    from oracle import spatial as OSP
+    pd = p.replace(form=ci.DIRECT)
     sample, ref_fast, t_fast = oracle_sample(p, G0, args.cpu_modes, ci.SEED_BASE + 21)
-    sample_d, ref_dir, t_dir = oracle_sample(p.replace(form=ci.DIRECT), G0, max(4, args.cpu_modes // 16),
-                                             ci.SEED_BASE + 22)
-
-    def scaled(x, ref):
-        # exact power-of-two rescaling (values span ~1e-300..1e+176 here) before any norm
-        e = np.frexp(np.max(np.abs(ref)))[1]
-        return np.ldexp(x, -e), np.ldexp(ref, -e)
-
-    def rel_err(gN_phys, sample_idx, ref):
-        # max error over the sampled modes relative to the largest sampled mode: the
-        # comparison goes through one extra DST, which adds ~eps * max|g| to every mode
-        ghat = OSP.to_modal(gN_phys, p.M, p.dim)[:, sample_idx]
-        g, r = scaled(ghat, ref)
-        return float(np.max(np.abs(g - r)) / np.max(np.abs(r)))
-
-    err_fast = rel_err(gN_fast, sample, ref_fast)
-    err_dir = rel_err(gN_dir, sample_d, ref_dir)
-    mf, md = scaled(OSP.to_modal(gN_fast, p.M, p.dim), OSP.to_modal(gN_dir, p.M, p.dim))
-    fast_vs_direct = float(np.linalg.norm(mf - md) / np.linalg.norm(md))
-    cpu_value = 2 * len(sample) * p.N / t_fast
+    sample_d, ref_dir, t_dir = oracle_sample(pd, G0, max(4, args.cpu_modes // 16), ci.SEED_BASE + 22)
+    cpu_fast = cpu_baseline(
+        UNIT, 2 * len(sample) * p.N, t_fast, "oracle fast SBD scheme, %d seeded sine modes x all %d steps"
+        % (len(sample), p.N), mode_jobs(p, G0, args.cpu_modes, [ci.SEED_BASE + 100 + k for k in range(_ncpu())]),
+        _ncpu() * 2 * args.cpu_modes * p.N, "oracle fast SBD scheme, %d seeded sine modes x all %d steps per job"
+        % (args.cpu_modes, p.N))
+    nd = max(4, args.cpu_modes // 16)
+    cpu_dir = cpu_baseline(
+        UNIT, 2 * len(sample_d) * p.N, t_dir, "oracle direct SBD scheme, %d seeded modes x %d steps"
+        % (len(sample_d), p.N), mode_jobs(pd, G0, nd, [ci.SEED_BASE + 120 + k for k in range(_ncpu())]),
+        _ncpu() * 2 * nd * p.N, "oracle direct SBD scheme, %d seeded modes x %d steps per job" % (nd, p.N))
+    error = {"fast": modal_parity(p, G0, gm_fast, sample, ref_fast),
+             "direct": modal_parity(pd, G0, gm_dir, sample_d, ref_dir)}
+    sc = np.max(np.abs(gm_dir))
+    error["fast_vs_direct_rel_l2"] = float(np.linalg.norm((gm_fast - gm_dir) / sc) / np.linalg.norm(gm_dir / sc))
+    error["status"] = fc.strerror(st_fast)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded; see config)", "config": workload_config(p),
         "roofline": roofline,
-        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                         "sample": "oracle fast SBD scheme, %d seeded sine modes x all %d steps (%.1f s)"
-                                   % (len(sample), p.N, t_fast)},
+        "cpu_baseline": cpu_fast,
         "e2e": {"value": world * units / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(G0.size * 8), "d2h_bytes_per_step": int(G0.size * 8),
                 "ms_per_step": ms_e2e},
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "error": {"fast_vs_oracle_max_err_rel_to_max_mode": err_fast,
-                  "direct_vs_oracle_max_err_rel_to_max_mode": err_dir,
-                  "fast_vs_direct_rel_l2": fast_vs_direct, "status": fc.strerror(st_fast)},
-        "direct": {"value": world * units / (ms_dir * 1e-3), "unit": UNIT, "ms_per_step": ms_dir, "steps": Kd,
-                   "warmup": Wd, "kernel": "k_fp2s_direct<8>", "kernel_ms": statistics.mean(d_mains),
-                   "gpu_launches": int(d_launches), "status": fc.strerror(st_dir),
-                   "cpu_baseline": {"value": 2 * len(sample_d) * p.N / t_dir, "unit": UNIT, "cores": 1,
-                                    "kind": "oracle", "sample": "oracle direct SBD scheme, %d modes x %d steps "
-                                    "(%.1f s)" % (len(sample_d), p.N, t_dir)}},
         "device": torch.cuda.get_device_name(),
     }
-    if prec_leg is not None:
-        out["precision"] = precision_report(prec_leg, max(16, args.cpu_modes // 64))
-    if grad is not None:
-        out["gradient"] = grad
-    if batch is not None:
-        out["batch"] = batch
-    if stream is not None:
-        out["fast_history_stream"] = stream
+    # secondary legs; the most informative ones last, where a truncated log keeps them
     if paper is not None:
         out["paper_runs"] = {"note": "the paper's CPU times are on unstated hardware: context only", **paper}
     if small is not None:
         out["small_1d"] = small
+    if stream is not None:
+        out["fast_history_stream"] = stream
+    out["direct"] = {"value": world * units / (ms_dir * 1e-3), "unit": UNIT, "ms_per_step": ms_dir, "steps": Kd,
+                     "warmup": Wd, "kernel": "k_fp2s_direct<8>", "kernel_ms": statistics.mean(d_mains),
+                     "gpu_launches": int(d_launches), "status": fc.strerror(st_dir), "cpu_baseline": cpu_dir}
+    if peaks is not None:
+        out["peaks"] = peaks
+    if prec_leg is not None:
+        out["precision"] = precision_report(prec_leg, 128)
+    if grad is not None:
+        out["gradient"] = grad
+    if batch is not None:
+        out["batch"] = batch
+    out["error"] = error
+    out["summary"] = summary(out)
+    _close_pool()
     return out
+
+
+def _modal_solve(fc, torch, dev, cp, g0m):
+    """The modal G^N of every mode through fp2s_solve_modes (numpy [2][nmodes])."""
+    nm = g0m.shape[1]
+    gN = torch.empty_like(g0m)
+    ws = fc.workspace(fc.fp2s_solve_modes(cp, 0, nm, g0m, gN, None), dev)
+    fc.fp2s_solve_modes(cp, 0, nm, g0m, gN, ws)
+    out = gN.cpu().numpy()
+    del ws
+    return out
+
+
+def modal_parity(p, G0, gm, sample, ref):
+    """GPU modal G^N against the oracle on sampled modes: relative L2 per state over the decaying
+    modes; each growing mode's relative error beside its one-ulp conditioning (the change of the
+    oracle's g^N when lambda_k, a or T moves by one unit in the last place)."""
+    import numpy as np
+    import cq_inputs as ci
+    from oracle import scheme as OS
+    from oracle import spatial as OSP
+    lam_all = OSP.mode_eigenvalues(p.M, p.dim)
+    grow = np.array([ci.growth_rate(p.alpha1, p.alpha2, p.m, lam_all[k]) > 0.0 for k in sample])
+    got = gm[:, sample]
+    rel = []
+    for s in range(2):
+        r, g = ref[s][~grow], got[s][~grow]
+        sc = np.max(np.abs(r))
+        rel.append(float(np.linalg.norm((g - r) / sc) / np.linalg.norm(r / sc)))
+    g0m = OSP.to_modal(G0, p.M, p.dim)
+    growing = []
+    one = 2.0 ** -52
+    for j in np.nonzero(grow)[0]:
+        k = sample[j]
+        lam_k, g0_k = lam_all[[k]], g0m[:, [k]]
+        r_k = ref[:, [j]]
+        moved = [OS.solve_modal(p, lam_k * (1 + one), g0_k)[p.N],
+                 OS.solve_modal(p, lam_k, g0_k, a=OS.coupling(p.m) * (1 + one))[p.N],
+                 OS.solve_modal(p.replace(T=p.T * (1 + one)), lam_k, g0_k)[p.N]]
+        kappa = max(float(np.max(np.abs(m - r_k)) / np.max(np.abs(r_k))) for m in moved)
+        growing.append({"mode": int(k), "rel_err": float(np.max(np.abs(got[:, [j]] - r_k)) / np.max(np.abs(r_k))),
+                        "one_ulp_conditioning": kappa})
+    return {"rel_l2_per_state_decaying_modes": rel, "decaying_modes": int((~grow).sum()),
+            "growing_modes": growing,
+            "method": "fp2s_solve_modes over all modes (the fused kernel, no transforms) against the oracle's "
+                      "per-mode FP64 scheme on the sampled modes"}
+
+
+def summary(out):
+    """The headline figures of every leg in one place."""
+    def g(d, *keys):
+        for k in keys:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+    prec = out.get("precision", {})
+    mixed = g(prec, "mixed_direct_solve") or {}
+    cases = {("%s %s %s" % (c["scheme"], c["alpha"], c["contraction"])): c["rel_l2_err_vs_fp64_oracle"]
+             for c in mixed.get("cases", [])}
+    return {
+        "headline": {"value": out["value"], "ms_per_step": out["ms_per_step"], "e2e": g(out, "e2e", "value"),
+                     "roofline_frac": g(out, "roofline", "frac"), "roofline_peak_source": g(out, "roofline",
+                                                                                            "peak_source")},
+        "fp64_parity": {"fast": g(out, "error", "fast", "rel_l2_per_state_decaying_modes"),
+                        "direct": g(out, "error", "direct", "rel_l2_per_state_decaying_modes"),
+                        "fast_vs_direct_rel_l2": g(out, "error", "fast_vs_direct_rel_l2")},
+        "fp32_fast_solve": {"ms": g(prec, "fp32_fast_solve", "ms_per_step"),
+                            "rel_err": g(prec, "fp32_fast_solve", "error_vs_fp64_oracle_rel_l2_sampled_modes"),
+                            "frac": g(prec, "fp32_fast_solve", "roofline", "frac")},
+        "mixed_direct_solve": {"ms": mixed.get("ms_per_solve"), "contraction_frac": g(mixed, "roofline", "frac"),
+                               "rel_l2_per_state": cases},
+        "tensor_core_history": {"bf16x3_frac": g(prec, "tensor_core_direct_history", "roofline", "frac"),
+                                "tf32x3_frac": g(prec, "tensor_core_direct_history_tf32x3", "roofline", "frac")},
+        "batch": {"value": g(out, "batch", "value"), "graph_replay_value": g(out, "batch", "graph_replay", "value"),
+                  "launch_shape": g(out, "batch", "launch_shape")},
+        "gradient": {"ms": g(out, "gradient", "ms_per_gradient"),
+                     "rel_err_vs_central_differences": g(out, "gradient", "rel_err_vs_central_differences"),
+                     "mixed": [{"precision": m.get("precision", "")[:6], "ms": m.get("ms_per_gradient"),
+                                "rel_err_vs_fp64_gradient": m.get("rel_err_vs_fp64_gradient")}
+                               for m in g(out, "gradient", "mixed_precision") or []]},
+        "cpu_baselines_all_cores": {k: g(v, "cpu_baseline", "value") for k, v in (
+            ("headline", out), ("direct", out.get("direct")), ("batch", out.get("batch")),
+            ("gradient", out.get("gradient")), ("small_1d", out.get("small_1d")),
+            ("fp32_fast", prec.get("fp32_fast_solve")), ("mixed", mixed),
+            ("tensor_core_history", prec.get("tensor_core_direct_history")))},
+        "cpu": cpu_info(),
+    }
 
 
 def _kernel_hash():
@@ -1019,27 +1343,38 @@ def _profiled_traffic(name):
 
 # ----------------------------------------------------------------------------- reference arm (the oracle)
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (the paper's scheme in plain FP64 numpy) on the host's cores,
+    one spawned process per core, each step a bounded sample of the workload (every process
+    solves args.ref_modes seeded sine modes over all N steps)."""
     if rank != 0:
         return None
     import cq_inputs as ci
     p, G0 = ci.workload(WORKLOAD)
     G0 = G0 * SCALE
-    n = args.ref_modes
+    n, ncpu = args.ref_modes, _ncpu()
+    pool = _oracle_pool()
+    short = p.replace(N=64, T=p.T * 64 / p.N)
     for w in range(args.warmup):
-        oracle_sample(p.replace(N=64, T=p.T * 64 / p.N), G0, n, ci.SEED_BASE + 30 + w)
+        pool.map(_oracle_job, mode_jobs(short, G0, n, [ci.SEED_BASE + 300 + 100 * w + k for k in range(ncpu)]),
+                 chunksize=1)
     times = []
-    for k in range(args.steps):
-        _, _, dt = oracle_sample(p, G0, n, ci.SEED_BASE + 40 + k)
-        times.append(dt)
+    for step in range(args.steps):
+        jobs = mode_jobs(p, G0, n, [ci.SEED_BASE + 1000 + 100 * step + k for k in range(ncpu)])
+        t = time.perf_counter()
+        pool.map(_oracle_job, jobs, chunksize=1)
+        times.append(time.perf_counter() - t)
+    _close_pool()
     ms = 1e3 * statistics.mean(times)
-    value = 2 * n * p.N / (ms * 1e-3)
+    value = ncpu * 2 * n * p.N / (ms * 1e-3)
+    info = cpu_info()
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; see config)",
             "config": workload_config(p),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                             "sample": "each step: oracle fast SBD scheme on %d seeded sine modes x all %d steps "
-                                       "(warm-up steps use N=64)" % (n, p.N)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncpu, "kind": "oracle", "cpu_model": info["model"],
+                             "sample": "each step: %d spawned processes (one per core), each solving the oracle's "
+                                       "fast SBD scheme on %d seeded sine modes x all %d steps (warm-up steps use "
+                                       "N=64)" % (ncpu, n, p.N)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -1049,8 +1384,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-modes", type=int, default=8192, help="sine modes of the oracle's timed sample")
-    ap.add_argument("--ref-modes", type=int, default=2048, help="sine modes per step of the reference arm")
+    ap.add_argument("--cpu-modes", type=int, default=2048, help="sine modes of the oracle's timed sample (per job)")
+    ap.add_argument("--ref-modes", type=int, default=2048,
+                    help="sine modes per process and step of the reference arm")
     ap.add_argument("--no-precision", dest="precision", action="store_false",
                     help="leave out the precision-form, gradient and batch legs")
     args = ap.parse_args()

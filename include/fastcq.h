@@ -182,8 +182,11 @@ int cq_history_fast(int32_t scheme, double beta, double tau, const cq_fast_cfg_t
  * keeps until the process exits. A request whose state does not fit
  * ((np + L) * ndof doubles plus small tables; e.g. ndof <= ~21,600 for
  * np = 80, L = 17) returns CQ_ENOMEM before any work is enqueued.
- * The first call on a device (the current device) looks up the array's device
- * address and caches it: make it before any stream capture. Every call shares
+ * Each call made outside stream capture looks up the array's device address on
+ * the current device, so a device reset or a new primary context (which moves
+ * the array) is picked up by the next call; a call made while `stream` is being
+ * captured reuses the address the last call outside capture found on that
+ * device: make one call on the device before any stream capture. Every call shares
  * the array, which keeps the last call's contents: the n = 1 call clears the
  * state, and calls that overlap on the GPU (several problems or streams at
  * once on one device) race on it. It calls no allocating routine. */
@@ -303,7 +306,9 @@ int fp2s_vjp(const fp2s_problem_t *p, const double *G0_dev, const double *dGN_de
 typedef struct {
     int32_t n_inst, n_units;        /* problems; work units of 16 * warps_per_block modes */
     int32_t warps_per_block;        /* block width of the persistent kernel (autotuned or default) */
-    int32_t max_np, max_L, max_N, max_M, flags;   /* flags bit 0: width chosen by the autotuner */
+    int32_t max_np, max_L, max_N, max_M, flags;   /* flags bit 0: launch shape chosen by the autotuner */
+    int32_t ctas_per_sm;            /* resident CTAs per SM of the persistent launch (0: as many as fit) */
+    int32_t tuned_candidates;       /* launch shapes the autotuner timed (0 without tuning) */
     int64_t max_modes, field_elems; /* field_elems: doubles of a packed [instance][2][M^dim] field */
     int64_t ws_bytes;
     int64_t off[16];                /* workspace regions (internal) */
@@ -313,8 +318,10 @@ typedef struct {
  * prec == CQ_F64, dim 1 or 2; any mix of dim, M, N, scheme, alpha, m and fast sizes):
  * builds every instance's tables in the workspace with batched kernels and
  * orders the work units by decreasing cost. 1 <= n <= 65535 (more: CQ_EUNSUPPORTED;
- * split such a set into several batches). tune != 0 times the candidate
- * block widths on a shortened run (96 steps) and keeps the fastest.
+ * split such a set into several batches). tune != 0 autotunes the launch shape:
+ * every block width whose shared memory fits (2..16 warps), each with all and
+ * with half of the CTAs per SM that fit, is timed on a shortened run (96 steps,
+ * median of three) and the fastest is kept (warps_per_block, ctas_per_sm).
  * Size query when ws_dev == NULL. Synchronises `stream`; the plan and the
  * workspace stay valid for any number of fp2s_solve_batched calls. */
 int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t tune, fp2s_batch_t *plan, void *ws_dev,

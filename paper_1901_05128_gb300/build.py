@@ -1,8 +1,10 @@
 """Build the fastcq CUDA library in-tree for sm_103a (GB300).
 
 ``build()`` compiles every translation unit under ``csrc/`` with nvcc in
-parallel and links ``_build/libfastcq.so``. The CUDA runtime is linked
-statically, so the library only needs the driver at load time.
+parallel and links ``_build/libfastcq.so``, and the FMA-rate probe under
+``probe/`` into ``_build/libcqprobe.so`` (used by the benchmark for the ALU roofs).
+The CUDA runtime is linked statically, so the libraries only need the driver at
+load time.
 """
 from __future__ import annotations
 
@@ -15,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfastcq.so")
+PROBE_SRC = os.path.join(HERE, "probe", "fma_peak.cu")
+PROBE_LIB = os.path.join(BUILD, "libcqprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -31,7 +35,9 @@ def sources() -> list[str]:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
+        return True
+    if os.path.getmtime(PROBE_SRC) > os.path.getmtime(PROBE_LIB):
         return True
     t = os.path.getmtime(LIB)
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
@@ -57,7 +63,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        probe = ex.submit(compile_one, PROBE_SRC)
         objs = list(ex.map(compile_one, sources()))
+        probe_obj = probe.result()
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", PROBE_LIB + ".tmp", probe_obj], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
+    os.replace(PROBE_LIB + ".tmp", PROBE_LIB)
     tmp = LIB + ".tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:

@@ -6,8 +6,10 @@
 // sine-mode eigenvalues, DST-I matrix), builds them with batched kernels (one
 // launch per kind of table for the whole batch), cuts every instance into work
 // units of 16 x WB modes, orders the units by decreasing cost (longest
-// processing time first) and, when asked, times a few block widths WB on a
-// shortened run and keeps the fastest.
+// processing time first) and, when asked, autotunes the launch shape: every
+// block width WB whose shared memory fits, each with the full occupancy and with
+// half of it (resident CTAs per SM), timed on a shortened run (median of three)
+// and the fastest kept.
 // fp2s_solve_batched then only transforms G0, runs the persistent kernel (its
 // CTAs take units from an atomic counter: no CTA ever waits for another) and
 // transforms back: five launches and one memset, with no host synchronisation,
@@ -379,14 +381,23 @@ static void make_units(const std::vector<InstDesc> &descs, int wb, std::vector<U
 
 static int num_sms_b() { return device_sms(); }
 
+// Resident CTAs per SM of the persistent kernel for a block width (0 when it does not fit).
+static int occupancy(int max_np, int max_L, int wb) {
+    const int T = 32 * wb;
+    const size_t smem = bfast_smem(max_np, max_L, T);
+    if (cudaFuncSetAttribute(k_b_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_fast, T, smem) != cudaSuccess) return 0;
+    return per_sm;
+}
+
+// One persistent launch: plan->ctas_per_sm CTAs per SM (0: as many as fit), never more than units.
 static int launch_main(const fp2s_batch_t *plan, const BatchLayout &l, int64_t step_cap, cudaStream_t s) {
     const int T = 32 * plan->warps_per_block;
     const size_t smem = bfast_smem(plan->max_np, plan->max_L, T);
-    if (cudaFuncSetAttribute(k_b_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return CQ_ECUDA;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_fast, T, smem) != cudaSuccess || per_sm < 1)
-        return CQ_EUNSUPPORTED;
+    const int fit = occupancy(plan->max_np, plan->max_L, plan->warps_per_block);
+    if (fit < 1) return CQ_EUNSUPPORTED;
+    const int per_sm = plan->ctas_per_sm > 0 ? std::min(plan->ctas_per_sm, fit) : fit;
     const int64_t want = (int64_t)num_sms_b() * per_sm;
     const int blocks = (int)std::min<int64_t>(want, plan->n_units);
     int st = cuda_status(cudaMemsetAsync(l.counter, 0, sizeof(int), s));
@@ -395,6 +406,18 @@ static int launch_main(const fp2s_batch_t *plan, const BatchLayout &l, int64_t s
                                     l.W, l.tab, l.lam, l.modal, l.status);
     return launched();
 }
+
+// CUDA events of the autotuner, destroyed on every path out of it.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool ok() {
+        return cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    }
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
 
 static int transform(const fp2s_batch_t *plan, const BatchLayout &l, const double *field_in, double *field_out, int src,
                      int dst, cudaStream_t s) {
@@ -494,15 +517,19 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
     const int64_t spec = std::max<int64_t>(z.max_nmodes, (int64_t)z.maxM * z.maxM);
     k_b_spectrum<<<dim3((unsigned)((spec + 255) / 256), n), 256, 0, s>>>(l.desc, l.lam, l.S);
     if ((st = launched(4))) return st;
-    // block width: default, or the fastest of the candidates on a shortened run
-    int best = cands.front();
-    if (tune && cands.size() > 1) {
-        cudaEvent_t e0, e1;
-        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CQ_ECUDA;
+    // launch shape: the widest block with full occupancy by default, or the fastest candidate
+    // (block width x resident CTAs per SM) on a shortened run, median of three timings each
+    int best = cands.front(), best_cps = 0;
+    plan->tuned_candidates = 0;
+    if (tune) {
+        EventPair ev;
+        if (!ev.ok()) return CQ_ECUDA;
         float best_ms = 1e30f;
         const int64_t cap = std::min<int64_t>(z.maxN, 96);
         for (int wb : cands) {
             if (wb < 2) continue;
+            const int fit = occupancy(z.maxnp, z.maxL, wb);
+            if (fit < 1) continue;
             std::vector<Unit> units;
             make_units(descs, wb, units);
             plan->warps_per_block = wb;
@@ -510,22 +537,30 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
             if ((st = cuda_status(cudaMemcpyAsync(l.units, units.data(), units.size() * sizeof(Unit),
                                                   cudaMemcpyHostToDevice, s))))
                 return st;
-            if ((st = launch_main(plan, l, cap, s))) return st;           // warm-up
-            cudaEventRecord(e0, s);
-            if ((st = launch_main(plan, l, cap, s))) return st;
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) return CQ_ECUDA;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms * 0.98f) {
-                best_ms = ms;
-                best = wb;
+            for (int cps : {fit, fit / 2}) {
+                if (cps < 1 || (cps == fit / 2 && fit / 2 == fit)) continue;
+                plan->ctas_per_sm = cps;
+                if ((st = launch_main(plan, l, cap, s))) return st;        // warm-up
+                float t[3];
+                for (float &ti : t) {
+                    cudaEventRecord(ev.a, s);
+                    if ((st = launch_main(plan, l, cap, s))) return st;
+                    cudaEventRecord(ev.b, s);
+                    if (cudaEventSynchronize(ev.b) != cudaSuccess) return CQ_ECUDA;
+                    if (cudaEventElapsedTime(&ti, ev.a, ev.b) != cudaSuccess) return CQ_ECUDA;
+                }
+                std::sort(t, t + 3);
+                ++plan->tuned_candidates;
+                if (t[1] < best_ms * 0.98f) {
+                    best_ms = t[1];
+                    best = wb;
+                    best_cps = cps == fit ? 0 : cps;
+                }
             }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         plan->flags |= 1;
     }
+    plan->ctas_per_sm = best_cps;
     std::vector<Unit> units;
     make_units(descs, best, units);
     plan->warps_per_block = best;

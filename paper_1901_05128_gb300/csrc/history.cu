@@ -397,9 +397,12 @@ extern "C" int cq_history_fast(int32_t scheme, double beta, double tau, const cq
 // and the tables) lives in one file-scope device array of fixed size, which
 // every device that loads this library holds until the process exits.
 //
-// The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (a host-side name of a __device__ array is not a device
-// address) and caches it for that device; make that first call before any
+// Every call made outside stream capture looks up the array's device address
+// with cudaGetSymbolAddress (a host-side name of a __device__ array is not a
+// device address), so a device reset or a new primary context, which reloads
+// the module and moves the array, is picked up by the next call. A call made
+// while its stream is being captured uses the address that the last call
+// outside capture found on that device: make one call on the device before any
 // stream capture. All calls share the one array and it keeps whatever the last
 // call left in it: the call with n = 1 clears the state before use, and calls
 // that overlap on the GPU (other streams, other threads, two problems at once
@@ -413,12 +416,14 @@ constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mutex;
 static void *g_noalloc_addr[kNoAllocMaxDevices] = {};
 
-static int noalloc_scratch_address(void **out) {
+static int noalloc_scratch_address(cudaStream_t s, void **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return CQ_ECUDA;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return CQ_EUNSUPPORTED;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return CQ_ECUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_noalloc_addr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CQ_ECUDA;
         g_noalloc_addr[dev] = p;
@@ -437,7 +442,7 @@ extern "C" int cq_history_fast_noalloc(int32_t scheme, double beta, double tau, 
     if (st) return st;
     if (need > CQ_NOALLOC_SCRATCH_BYTES) return CQ_ENOMEM;
     void *scratch = nullptr;
-    if ((st = noalloc_scratch_address(&scratch))) return st;
+    if ((st = noalloc_scratch_address((cudaStream_t)stream, &scratch))) return st;
     size_t cap = CQ_NOALLOC_SCRATCH_BYTES;
     return cq_history_fast(scheme, beta, tau, cfg, ndof, n, G_prev_dev, H_dev, prec, scratch, &cap, stream);
 }

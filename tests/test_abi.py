@@ -18,10 +18,10 @@ def fc():
     return pkg.load()
 
 
-def _declared():
+def _declared(only=None):
     names = set()
     for fn in os.listdir(os.path.join(ROOT, "include")):
-        if fn.endswith(".h"):
+        if fn.endswith(".h") and (only is None or fn == only):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
             names |= set(re.findall(r"\b((?:cq|fp2s)_\w+)\s*\(", src))
@@ -29,7 +29,7 @@ def _declared():
 
 
 def test_every_declared_symbol_is_exported(fc):
-    decl = _declared()
+    decl = _declared("fastcq.h")
     assert {"cq_weights", "cq_history_direct", "cq_history_fast", "fp2s_step", "fp2s_solve"} <= decl
     lib = C.CDLL(fc.LIB_PATH)
     missing = [n for n in sorted(decl) if not hasattr(lib, n)]
@@ -201,3 +201,18 @@ def test_mode_range_validation(fc):
     whole = sz.value
     assert lib.fp2s_solve_modes(C.byref(p), 100, 110, None, None, None, C.byref(sz), None) == fc.CQ_OK
     assert 0 < sz.value < whole
+
+
+def test_probe_library_exports_its_header(fc):
+    """libcqprobe.so (the FMA-rate probe of the benchmark) exports what include/cqprobe.h declares."""
+    import importlib
+    B = importlib.import_module("paper_1901_05128_gb300.build")
+    decl = _declared("cqprobe.h")
+    assert decl == {"cq_probe_fma_rate"}
+    lib = C.CDLL(B.PROBE_LIB)
+    assert all(hasattr(lib, n) for n in decl)
+    f = lib.cq_probe_fma_rate
+    f.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]
+    r = C.c_double(0)
+    assert f(2, 1, 32, 1, None, C.byref(r), None) == -1          # invalid arguments, checked on the host
+    assert f(0, 1, 48, 1, None, C.byref(r), None) == -1

@@ -8,11 +8,14 @@ or a loop that must not call cudaMalloc because that call can synchronise the
 device and can fail at an arbitrary step. For them cq_history_fast_noalloc
 keeps the history state in a fixed device array owned by the library.
 
-The test drives the entry point through the C ABI for two complete step
-sequences in a row. The second sequence is a different problem, so it starts
-from whatever the first one left in the shared array. Every step's h^n must
-agree with cq_history_fast (the workspace version) within the tolerance of the
-other history tests: |difference| <= 1e-12 * sum_i |d_i| |G^{n-i}|. A request
+The test drives the entry point through the C ABI for complete step sequences
+in a row, in both precisions it accepts (CQ_F64, and CQ_F32, which lays out
+padded FP32 rows and an FP32 table in the same array). Each later sequence is a
+different problem, so it starts from whatever the previous one left in the
+shared array, including a switch of precision between two problems. Every
+step's h^n must agree with cq_history_fast (the workspace version) at the same
+precision, within the tolerance of the other history tests:
+|difference| <= 1e-12 (FP64) or 2e-5 (FP32) * sum_i |d_i| |G^{n-i}|. A request
 that does not fit the array must be refused before any work is done. The file
 is named so that pytest collects it last.
 """
@@ -42,21 +45,22 @@ def _abs_scale(d, G, n):
     return np.abs(d[n - 1:0:-1]) @ np.abs(G[1:n])
 
 
-def _run(fc, scheme, beta, np1, np2, ns, ndof, N, seed):
+def _run(fc, scheme, beta, np1, np2, ns, ndof, N, seed, prec=0):
+    tol = 1e-12 if prec == fc.CQ_F64 else 2e-5
     tau = 1.0 / N
     G = ci.rng(seed).standard_normal((N + 1, ndof))
     Gd = torch.tensor(G, dtype=torch.float64, device="cuda")
     H_ws = torch.empty(ndof, dtype=torch.float64, device="cuda")
     H_na = torch.empty(ndof, dtype=torch.float64, device="cuda")
-    ws = fc.workspace(fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, 1, None, None), "cuda")
+    ws = fc.workspace(fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, 1, None, None, prec=prec), "cuda")
     d = OW.weights(scheme, beta, tau, N)
     for n in range(1, N + 1):
-        fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, n, Gd[n - 1], H_ws, ws)
-        fc.cq_history_fast_noalloc(scheme, beta, tau, np1, np2, ns, ndof, n, Gd[n - 1], H_na)
+        fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, n, Gd[n - 1], H_ws, ws, prec=prec)
+        fc.cq_history_fast_noalloc(scheme, beta, tau, np1, np2, ns, ndof, n, Gd[n - 1], H_na, prec=prec)
         torch.cuda.synchronize()
         a = H_ws.cpu().numpy()
         b = H_na.cpu().numpy()
-        assert np.all(np.abs(a - b) <= 1e-12 * _abs_scale(d, G, n) + 1e-300), n
+        assert np.all(np.abs(a - b) <= tol * _abs_scale(d, G, n) + 1e-300), n
 
 
 def test_noalloc_matches_workspace_version_on_two_calls_in_a_row(fc):
@@ -64,6 +68,13 @@ def test_noalloc_matches_workspace_version_on_two_calls_in_a_row(fc):
     _run(fc, 2, 0.6, 16, 64, 17, 3001, 240, seed=31)
     # second use right after it: a different scheme and size on top of the leftovers
     _run(fc, 1, 0.3, 40, 0, 2, 777, 200, seed=32)
+
+
+def test_noalloc_fp32_and_precision_switches(fc):
+    # FP32 after the FP64 problems above, then FP64 on FP32 leftovers, then FP32 again
+    _run(fc, 2, 0.45, 8, 24, 9, 2049, 180, seed=33, prec=fc.CQ_F32)
+    _run(fc, 1, 0.55, 32, 0, 2, 1001, 150, seed=34, prec=fc.CQ_F64)
+    _run(fc, 1, 0.7, 64, 0, 2, 4093, 160, seed=35, prec=fc.CQ_F32)
 
 
 def test_noalloc_refuses_requests_that_do_not_fit(fc):
