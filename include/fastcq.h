@@ -282,10 +282,10 @@ int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, dou
  * prec == CQ_BF16X3 / CQ_TF32X3: forward and adjoint sweeps of the
  * mixed-precision direct solve (FP32 levels, tensor-core histories), with the
  * weight-derivative history as one more contraction; the workspace holds the
- * split levels and increments (2 x 2 x N x 2 x M^dim operands) and an FP32
- * [N][2][M^dim] history, for all modes (no slicing; a size query returns this
- * size whatever *ws_bytes holds). Relative errors of order 1e-5 against the
- * FP64 form.
+ * split levels and increments (2 x 2 x N x 2 x modes operands) and an FP32
+ * [N][2][modes] history. With a smaller workspace the sweeps run over slices of
+ * modes (multiples of 64) by the same size-query rule as in FP64. Relative
+ * errors of order 1e-5 against the FP64 form.
  * Inputs G0_dev, Gt_dev: physical [2][M^dim]. Outputs: *J_host; dJdG0_dev
  * [2][M^dim] (gradient with respect to the nodal values of G^0); dJdalpha_host[2].
  * Synchronises `stream`. CQ_EUNSUPPORTED for other forms and precisions. */

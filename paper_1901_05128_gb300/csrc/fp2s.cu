@@ -66,8 +66,11 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
         l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
     if (P.prec != CQ_F64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
     if (P.form == CQ_FAST && P.prec == CQ_F32) l.ftab = cv.take<float>(kF32TabFloats);
-    if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3))
-        l.mixed = cv.take<char>(grad ? mixed_grad_bytes(P) : mixed_direct_bytes(P));
+    if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3)) {
+        Fp2sParams Pm = P;                 // a gradient may run over slices of hist_modes modes
+        if (grad && hist_modes >= 0) Pm.nmodes = hist_modes;
+        l.mixed = cv.take<char>(grad ? mixed_grad_bytes(Pm) : mixed_direct_bytes(Pm));
+    }
     if (stepper) {
         if (P.form == CQ_FAST) {
             l.Y = cv.take<double>((size_t)2 * P.np * nm);
@@ -1601,32 +1604,97 @@ static double grid_weight(const fp2s_problem_t *p) {
 }
 
 // Gradient through the mixed-precision direct solve (mixed.cu): same outputs as the
-// FP64 gradient, computed from FP32 levels and tensor-core histories.
+// FP64 gradient, computed from FP32 levels and tensor-core histories. The mixed region
+// holds the split levels and histories of ns modes: all modes, or (when the workspace is
+// capped) a slice, the slices running one after the other with compact [2][ns] copies of
+// their modal G^0, target and dJ/dx^0.
+struct MixedGradLayout {
+    Fp2sLayout l;
+    double *acc, *tgt, *gx0, *q1, *q2;
+    double *cg0, *ctgt, *cgx0, *cgN;
+    size_t bytes;
+};
+
+static MixedGradLayout mixed_grad_layout(const fp2s_problem_t *p, const Fp2sParams &P, void *ws, int64_t ns) {
+    MixedGradLayout g{};
+    g.l = fp2s_layout(p, P, ws, false, true, ns);
+    Carve cv(ws);
+    cv.off = g.l.bytes;
+    g.acc = cv.take<double>(8);
+    g.tgt = cv.take<double>(2 * P.nmodes);
+    g.gx0 = cv.take<double>(2 * P.nmodes);
+    g.q1 = cv.take<double>(P.N + 1);
+    g.q2 = cv.take<double>(P.N + 1);
+    if (ns < P.nmodes) {
+        g.cg0 = cv.take<double>(2 * ns);
+        g.ctgt = cv.take<double>(2 * ns);
+        g.cgx0 = cv.take<double>(2 * ns);
+        g.cgN = cv.take<double>(2 * ns);
+    }
+    g.bytes = cv.bytes();
+    return g;
+}
+
+constexpr int64_t kMixedSliceQuantum = 64;   // modes per CTA of the mixed block kernels
+
+// Modes per slice of the mixed gradient within `cap` bytes (all modes when they fit; 0: none fits).
+static int64_t mixed_grad_slice(const fp2s_problem_t *p, const Fp2sParams &P, size_t cap) {
+    if (mixed_grad_layout(p, P, nullptr, P.nmodes).bytes <= cap) return P.nmodes;
+    int64_t lo = 0, hi = (P.nmodes - 1) / kMixedSliceQuantum;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (mixed_grad_layout(p, P, nullptr, mid * kMixedSliceQuantum).bytes <= cap) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo * kMixedSliceQuantum;
+}
+
 static int gradient_mixed(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2, const double *G0_dev,
                           const double *Gt_dev, int vjp, double *J_host, double *dJdG0_dev, double *dJdalpha_host,
                           void *ws_dev, size_t *ws_bytes, cudaStream_t s) {
-    const Fp2sLayout l = fp2s_layout(p, P, ws_dev, false, true);
-    Carve cv(ws_dev);
-    cv.off = l.bytes;
-    double *acc = cv.take<double>(8), *tgt = cv.take<double>(2 * P.nmodes), *gx0 = cv.take<double>(2 * P.nmodes);
-    double *q1 = cv.take<double>(P.N + 1), *q2 = cv.take<double>(P.N + 1);
-    if (!ws_dev) { *ws_bytes = cv.bytes(); return CQ_OK; }
-    if (*ws_bytes < cv.bytes()) return CQ_ENOMEM;
+    if (!ws_dev) {
+        if (*ws_bytes == 0) { *ws_bytes = mixed_grad_layout(p, P, nullptr, P.nmodes).bytes; return CQ_OK; }
+        const int64_t ns = mixed_grad_slice(p, P, *ws_bytes);
+        if (ns == 0) return CQ_ENOMEM;
+        *ws_bytes = mixed_grad_layout(p, P, nullptr, ns).bytes;
+        return CQ_OK;
+    }
+    const int64_t ns = mixed_grad_slice(p, P, *ws_bytes);
+    if (ns == 0) return CQ_ENOMEM;
+    const MixedGradLayout g = mixed_grad_layout(p, P, ws_dev, ns);
+    const Fp2sLayout &l = g.l;
     if (!G0_dev || !Gt_dev || (!vjp && !J_host) || !dJdG0_dev || !dJdalpha_host || ((uintptr_t)ws_dev & 255))
         return CQ_EINVAL;
     int st;
     if ((st = setup(p, P, np1, np2, l, G0_dev, s))) return st;
     if ((st = timing_begin(s))) return st;
-    if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, tgt, l.tmp, s))) return st;
-    if ((st = weight_derivatives(P, p, q1, q2, s))) return st;
-    if ((st = cuda_status(cudaMemsetAsync(acc, 0, 8 * sizeof(double), s)))) return st;
-    if ((st = mixed_grad_run(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, q1, q2, l.hdf, tgt, vjp, grid_weight(p),
-                             gx0, acc, l.mixed, s)))
-        return st;
+    if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, g.tgt, l.tmp, s))) return st;
+    if ((st = weight_derivatives(P, p, g.q1, g.q2, s))) return st;
+    if ((st = cuda_status(cudaMemsetAsync(g.acc, 0, 8 * sizeof(double), s)))) return st;
+    const int64_t nm = P.nmodes;
+    for (int64_t m0 = 0; m0 < nm; m0 += ns) {
+        const int64_t cnt = min(ns, nm - m0);
+        Fp2sParams Ps = P;
+        Ps.nmodes = cnt;
+        const double *g0 = l.g0, *tgt = g.tgt;
+        double *gN = l.gN, *gx0 = g.gx0;
+        if (ns < nm) {
+            if ((st = copy_slice(g.cg0, cnt, l.g0 + m0, nm, cnt, s))) return st;
+            if ((st = copy_slice(g.ctgt, cnt, g.tgt + m0, nm, cnt, s))) return st;
+            g0 = g.cg0;
+            tgt = g.ctgt;
+            gN = g.cgN;
+            gx0 = g.cgx0;
+        }
+        if ((st = mixed_grad_run(Ps, l.lam + m0, g0, gN, l.status, l.d1, l.d2, g.q1, g.q2, l.hdf, tgt, vjp,
+                                 grid_weight(p), gx0, g.acc, l.mixed, s)))
+            return st;
+        if (ns < nm && (st = copy_slice(g.gx0 + m0, nm, g.cgx0, cnt, cnt, s))) return st;
+    }
     if ((st = timing_end(s))) return st;
-    if ((st = launch_dst_field(p->M, p->dim, l.S, gx0, dJdG0_dev, l.tmp, s))) return st;
+    if ((st = launch_dst_field(p->M, p->dim, l.S, g.gx0, dJdG0_dev, l.tmp, s))) return st;
     double host[4];
-    if (cudaMemcpyAsync(host, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CQ_ECUDA;
+    if (cudaMemcpyAsync(host, g.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CQ_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CQ_ECUDA;
     if (J_host) *J_host = host[0];
     dJdalpha_host[0] = -host[1];

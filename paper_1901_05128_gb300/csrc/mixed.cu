@@ -208,6 +208,16 @@ __device__ __forceinline__ float split_sum(int kind, double x) {
     return __uint_as_float((uint32_t)h << 16) + __uint_as_float((uint32_t)l << 16);
 }
 
+// Held in registers through the step loops: otherwise the compiler may recompute the
+// remainders from their FP64 sources inside the loop (FP64 work at 1/64 of the FP32 rate).
+__device__ __forceinline__ void keep_reg(WeightRem &r) {
+    keep_reg(r.w1);
+    keep_reg(r.r1f);
+    keep_reg(r.r2f);
+    keep_reg(r.r1b);
+    keep_reg(r.r2b);
+}
+
 __device__ __forceinline__ WeightRem weight_rem(int kind, const double *d, int64_t N) {
     const double d1 = N >= 1 ? d[1] : 0.0, d2 = N >= 2 ? d[2] : 0.0;
     WeightRem r;
@@ -359,7 +369,9 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     const float x_before = gm1;                      // x^{n0 - 1}
     float gm1_o = __shfl_xor_sync(0xffffffffu, gm1, 16), gm2_o = __shfl_xor_sync(0xffffffffu, gm2, 16);
     float gm1_o_lo = __shfl_xor_sync(0xffffffffu, gm1_lo, 16), gm2_o_lo = __shfl_xor_sync(0xffffffffu, gm2_lo, 16);
-    const WeightRem wr = weight_rem(A.kind, st ? A.d2 : A.d1, P.N), wr_o = weight_rem(A.kind, st ? A.d1 : A.d2, P.N);
+    WeightRem wr = weight_rem(A.kind, st ? A.d2 : A.d1, P.N), wr_o = weight_rem(A.kind, st ? A.d1 : A.d2, P.N);
+    keep_reg(wr);
+    keep_reg(wr_o);
     const float *w = wsm + st * kMxW + kMxWOff;     // w[i] = d_i, i >= -kMxWOff
     float wt[kMxSB];                                 // d_1 .. d_7 of the lane's state
 #pragma unroll
@@ -544,7 +556,9 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
     float mu1 = mv1.hi, mu1_lo = mv1.lo, mu2 = mv2.hi + mv2.lo;
     float mu1_o = __shfl_xor_sync(0xffffffffu, mu1, 16), mu1_o_lo = __shfl_xor_sync(0xffffffffu, mu1_lo, 16);
     float mu2_o = __shfl_xor_sync(0xffffffffu, mu2, 16);
-    const WeightRem wr = weight_rem(A.kind, st ? A.d2 : A.d1, N), wr_o = weight_rem(A.kind, st ? A.d1 : A.d2, N);
+    WeightRem wr = weight_rem(A.kind, st ? A.d2 : A.d1, N), wr_o = weight_rem(A.kind, st ? A.d1 : A.d2, N);
+    keep_reg(wr);
+    keep_reg(wr_o);
     const float *w = wsm + st * kMxW + kMxWOff;
     float wt[kMxSB];
 #pragma unroll

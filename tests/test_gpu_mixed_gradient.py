@@ -141,3 +141,36 @@ def _grad_workload(fc):
     ws = fc.workspace(fc.fp2s_solve(cp_t, g0, gt, None), "cuda")
     fc.fp2s_solve(cp_t, g0, gt, ws)
     return p, G0, gt.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_mixed_gradient_in_mode_slices(fc, prec):
+    """A workspace too small for all modes: the mixed-precision forward and adjoint sweeps run
+    over slices of modes (independent in the sine basis; multiples of 64 modes, the last one
+    ragged). Each mode takes the same arithmetic as in the unsliced run, so dJ/dG0 agrees to
+    rounding of its transform, and J, dJ/dalpha differ only in the order of their FP64 sums."""
+    import ctypes as C
+    p = ci.Problem(0.35, 0.6, 0.4, 1.0, 300, 2, 31, ci.BDF2, ci.DIRECT)
+    G0 = ci.g0_uniform(p.M, p.dim, 41)
+    Gt = 0.5 * ci.g0_uniform(p.M, p.dim, 42)
+    J, dG0, da = _grad(fc, p, G0, Gt, prec)
+    cp = _cp(fc, p, prec)
+    full = fc.fp2s_gradient(cp, None, None, None, None)
+    Jc, dac = C.c_double(0.0), (C.c_double * 2)()
+    sz = C.c_size_t(full // 4)
+    assert fc._lib.fp2s_gradient(C.byref(cp), None, None, C.byref(Jc), None, dac, None, C.byref(sz), None) == fc.CQ_OK
+    assert sz.value <= full // 4
+    ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    g0 = torch.tensor(G0, dtype=torch.float64, device="cuda")
+    gt = torch.tensor(Gt, dtype=torch.float64, device="cuda")
+    dg = torch.empty_like(g0)
+    Js, das = fc.fp2s_gradient(cp, g0, gt, dg, ws)
+    print("mixed gradient in slices (prec %d, %d of %d bytes): J %.2e dalpha %s" % (
+        prec, sz.value, full, abs(Js - J) / abs(J), np.abs(np.array(das) - da) / np.abs(da)))
+    assert abs(Js - J) <= 1e-12 * abs(J)
+    assert np.all(np.abs(np.array(das) - da) <= 1e-12 * np.abs(da))
+    assert np.max(np.abs(dg.cpu().numpy() - dG0)) <= 1e-13 * np.max(np.abs(dG0))
+    # a cap below one slice of 64 modes is refused
+    sz = C.c_size_t(4096)
+    assert fc._lib.fp2s_gradient(C.byref(cp), None, None, C.byref(Jc), None, dac, None, C.byref(sz),
+                                 None) == fc.CQ_ENOMEM
