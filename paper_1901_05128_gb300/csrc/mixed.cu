@@ -52,6 +52,7 @@ struct MixedLayout {
     float *carry;                       // g^{n-1}, g^{n-2} at the end of a block: [4][2 * nmp] (FP32 parts,
                                         // then the forward solve's double-float remainders)
     float4 *coef;                       // per lane: A row, B row (double-float), (scaled g^0, exponent)
+    float *wrem;                        // [2][5]: WeightRem of each state (k_weight_rem)
     // gradient only
     float4 *coef_adj;                   // per lane coefficients of the adjoint steps (as coef)
     float *ht;                          // [N][2 * nmp]: row n - 1 = sum_{j=1}^{n} D'_{n-j} delta^j (scaled levels)
@@ -93,6 +94,7 @@ static MixedLayout mixed_layout(const Fp2sParams &P, void *base, bool grad) {
     l.acc1b = cv.take<float>(l.nblk > 1 ? (size_t)kMxB * 2 * l.nmp : 0);
     l.carry = cv.take<float>((size_t)8 * l.nmp);
     l.coef = cv.take<float4>((size_t)6 * l.nmp);
+    l.wrem = cv.take<float>(16);
     if (grad) {
         l.coef_adj = cv.take<float4>((size_t)6 * l.nmp);
         l.ht = cv.take<float>((size_t)P.N * 2 * l.nmp);
@@ -132,6 +134,7 @@ struct MixedArgs {
     const float *hdf, *acc;             // contraction rows of this block (absent for the first block)
     float *carry;
     float4 *coef;
+    const float *wrem;                  // [2][5] weight remainders (k_weight_rem)
     char *gt_hi, *gt_lo;
     double *gN;
     int *status;
@@ -229,6 +232,25 @@ __device__ __forceinline__ WeightRem weight_rem(int kind, const double *d, int64
     return r;
 }
 
+// WeightRem of both states, once per run: wrem[5 s + (w1, r1f, r2f, r1b, r2b)].
+__global__ void k_weight_rem(int kind, const double *__restrict__ d1, const double *__restrict__ d2, int64_t N,
+                             float *__restrict__ wrem) {
+    const int s = threadIdx.x;
+    if (s > 1) return;
+    const WeightRem r = weight_rem(kind, s ? d2 : d1, N);
+    float *o = wrem + 5 * s;
+    o[0] = r.w1;
+    o[1] = r.r1f;
+    o[2] = r.r2f;
+    o[3] = r.r1b;
+    o[4] = r.r2b;
+}
+
+__device__ __forceinline__ WeightRem load_weight_rem(const float *wrem, int s) {
+    const float *o = wrem + 5 * s;
+    return WeightRem{o[0], o[1], o[2], o[3], o[4]};
+}
+
 // The remainder terms of step n (block offset j) of one state: the weight remainders of
 // d_1 x^{n-1} and d_2 x^{n-2} (lag i comes from the block's own levels when j >= i, else from
 // the contraction) and d_1 times the double-float remainder of x^{n-1}. G^0 is not part of
@@ -273,20 +295,38 @@ __device__ __forceinline__ void inblock_chunks(float (&a)[kMxSB], const float *w
 template <bool diff, bool full>
 __device__ __forceinline__ void store_levels(int kind, const float *xc, int jmax, char *gt_hi, char *gt_lo, int64_t o,
                                              float prev = 0.0f) {
-    auto level = [&](int j) -> float {
-        if (!full && j >= jmax) return 0.0f;
-        const float x = xc[(j / 4) * 4 * kMxT + j % 4];
-        if (!diff) return x;
-        const float xp = j ? xc[((j - 1) / 4) * 4 * kMxT + (j - 1) % 4] : prev;
-        return x - xp;
+    // levels j .. j + 3 (j a multiple of 4) in one 16-byte shared-memory load; increments and
+    // the zeros past jmax applied in registers
+    const float4 *xq = reinterpret_cast<const float4 *>(xc);
+    auto quad = [&](int j, float (&v)[4]) {
+        const float4 q = xq[(j / 4) * kMxT];
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+        if (diff) {
+            const float p0 = prev;
+            prev = v[3];
+            v[3] -= v[2];
+            v[2] -= v[1];
+            v[1] -= v[0];
+            v[0] -= p0;
+        }
+        if (!full) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (j + i >= jmax) v[i] = 0.0f;
+        }
     };
     if (kind == tc::TC_TF32X3) {
         uint4 *dh = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(gt_hi) + o);
         uint4 *dl = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(gt_lo) + o);
         for (int j = 0; j < kMxB; j += 4) {
+            float v[4];
+            quad(j, v);
             uint32_t h[4], l[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) split_f32_tf32(level(j + i), h[i], l[i]);
+            for (int i = 0; i < 4; ++i) split_f32_tf32(v[i], h[i], l[i]);
             dh[j / 4] = make_uint4(h[0], h[1], h[2], h[3]);
             dl[j / 4] = make_uint4(l[0], l[1], l[2], l[3]);
         }
@@ -294,9 +334,12 @@ __device__ __forceinline__ void store_levels(int kind, const float *xc, int jmax
         uint4 *dh = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(gt_hi) + o);
         uint4 *dl = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(gt_lo) + o);
         for (int j = 0; j < kMxB; j += 8) {
+            float v[8];
+            quad(j, *reinterpret_cast<float(*)[4]>(v));
+            quad(j + 4, *reinterpret_cast<float(*)[4]>(v + 4));
             uint32_t h[8], l[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) split_f32(level(j + i), h[i], l[i]);
+            for (int i = 0; i < 8; ++i) split_f32(v[i], h[i], l[i]);
             dh[j / 8] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
                                    h[6] | (h[7] << 16));
             dl[j / 8] = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16), l[4] | (l[5] << 16),
@@ -369,9 +412,8 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
     const float x_before = gm1;                      // x^{n0 - 1}
     float gm1_o = __shfl_xor_sync(0xffffffffu, gm1, 16), gm2_o = __shfl_xor_sync(0xffffffffu, gm2, 16);
     float gm1_o_lo = __shfl_xor_sync(0xffffffffu, gm1_lo, 16), gm2_o_lo = __shfl_xor_sync(0xffffffffu, gm2_lo, 16);
-    WeightRem wr = weight_rem(A.kind, st ? A.d2 : A.d1, P.N), wr_o = weight_rem(A.kind, st ? A.d1 : A.d2, P.N);
+    WeightRem wr = load_weight_rem(A.wrem, st);
     keep_reg(wr);
-    keep_reg(wr_o);
     const float *w = wsm + st * kMxW + kMxWOff;     // w[i] = d_i, i >= -kMxWOff
     float wt[kMxSB];                                 // d_1 .. d_7 of the lane's state
 #pragma unroll
@@ -392,6 +434,7 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
             for (int b = 0; b < kMxSB; ++b) an[b] = A.acc[(int64_t)(j0 + kMxSB + b) * ldacc + col];
         }
         inblock_chunks(a, w, xs4, j0);
+        float xb[kMxSB] = {};                         // the sub-block's levels, stored as two float4
         // the sub-block's own triangle: each new level is added forward into the later sums
 #pragma unroll
         for (int b = 0; b < kMxSB; ++b) {
@@ -400,7 +443,7 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
             const float h = a[b];
             const float h_o = __shfl_xor_sync(0xffffffffu, h, 16);
             const float e_lo = weight_rem_terms(wr, j0 + b, n, gm1, gm1_lo, gm2);
-            const float e_o_lo = weight_rem_terms(wr_o, j0 + b, n, gm1_o, gm1_o_lo, gm2_o);
+            const float e_o_lo = __shfl_xor_sync(0xffffffffu, e_lo, 16);     // the partner state's
             df xd;
             if (full_setup && (A.solve64 || (P.scheme == CQ_BDF2 && n == 1))) {
                 xd = lane_step_df(P, ls, A.solve64, n, h, gm1, gm2, gz, dn, hd_hi, hd_lo);
@@ -424,7 +467,7 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
             for (int bb = b + 1; bb < kMxSB; ++bb) a[bb] = fmaf(wt[bb - b], x, a[bb]);
             const float x_o = __shfl_xor_sync(0xffffffffu, x, 16);
             const float x_o_lo = __shfl_xor_sync(0xffffffffu, xd.lo, 16);
-            xc[((j0 + b) / 4) * 4 * kMxT + (j0 + b) % 4] = x;
+            xb[b] = x;
             gm2 = gm1;
             gm2_lo = gm1_lo;
             gm1 = x;
@@ -434,6 +477,10 @@ __global__ void __launch_bounds__(kMxT) k_mixed_block(const __grid_constant__ Mi
             gm1_o = x_o;
             gm1_o_lo = x_o_lo;
         }
+        // 16-byte stores: a warp's 32 lanes write 512 contiguous bytes (no bank conflicts)
+        float4 *xw = reinterpret_cast<float4 *>(xs) + (j0 / 4) * kMxT + tid;
+        xw[0] = make_float4(xb[0], xb[1], xb[2], xb[3]);
+        xw[kMxT] = make_float4(xb[4], xb[5], xb[6], xb[7]);
     }
     if (!active) return;
     if (A.write_levels) {
@@ -550,15 +597,12 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
     }
     float gm1_o = __shfl_xor_sync(0xffffffffu, gm1, 16), gm2_o = __shfl_xor_sync(0xffffffffu, gm2, 16);
     float gm1_o_lo = __shfl_xor_sync(0xffffffffu, gm1_lo, 16), gm2_o_lo = __shfl_xor_sync(0xffffffffu, gm2_lo, 16);
-    // mu^{m+1} (double-float) and mu^{m+2} of both states, the levels of the adjoint's history
+    // mu^{m+1} (double-float) and mu^{m+2} of the lane's state, the levels of the adjoint's history
     const df mv1 = df_add(df_mul_f(dc, gm1), df_neg(df_mul_f(da, gm1_o)));
     const df mv2 = df_add(df_mul_f(dc, gm2), df_neg(df_mul_f(da, gm2_o)));
     float mu1 = mv1.hi, mu1_lo = mv1.lo, mu2 = mv2.hi + mv2.lo;
-    float mu1_o = __shfl_xor_sync(0xffffffffu, mu1, 16), mu1_o_lo = __shfl_xor_sync(0xffffffffu, mu1_lo, 16);
-    float mu2_o = __shfl_xor_sync(0xffffffffu, mu2, 16);
-    WeightRem wr = weight_rem(A.kind, st ? A.d2 : A.d1, N), wr_o = weight_rem(A.kind, st ? A.d1 : A.d2, N);
+    WeightRem wr = load_weight_rem(A.wrem, st);
     keep_reg(wr);
-    keep_reg(wr_o);
     const float *w = wsm + st * kMxW + kMxWOff;
     float wt[kMxSB];
 #pragma unroll
@@ -591,6 +635,7 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
             }
         }
         inblock_chunks(a, w, xs4, j0);
+        float xb[kMxSB] = {};                         // the sub-block's levels, stored as two float4
 #pragma unroll
         for (int b = 0; b < kMxSB; ++b) {
             const int64_t r = A.n0 + j0 + b;
@@ -601,7 +646,7 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
             const float h_o = __shfl_xor_sync(0xffffffffu, h, 16);
             // remainders of the history's largest weights (d_1, d_2) and of mu^{m+1}
             const float e_lo = weight_rem_terms(wr, j0 + b, r, mu1, mu1_lo, mu2);
-            const float e_o_lo = weight_rem_terms(wr_o, j0 + b, r, mu1_o, mu1_o_lo, mu2_o);
+            const float e_o_lo = __shfl_xor_sync(0xffffffffu, e_lo, 16);     // the partner state's
             df ld;
             if (A.solve64) {
                 const double l = sbd ? 2.0 * (double)gm1 - 0.5 * (double)gm2 : (double)gm1;
@@ -624,7 +669,7 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
             const float mu = mv.hi;
 #pragma unroll
             for (int bb = b + 1; bb < kMxSB; ++bb) a[bb] = fmaf(wt[bb - b], mu, a[bb]);
-            xc[((j0 + b) / 4) * 4 * kMxT + (j0 + b) % 4] = mu;
+            xb[b] = mu;
             db = fmaf(mu, fmaf(x0f, __ldg(cq + m - 1), hv[b]), db);      // mu^m hp^m
             if (sbd && m >= 2) {
                 sg = fmaf(2.0f * __ldg(hd_hi + m - 1), mu, sg);
@@ -649,10 +694,10 @@ __global__ void __launch_bounds__(kMxT) k_mixed_adjoint(const __grid_constant__ 
             mu2 = mu1;
             mu1 = mu;
             mu1_lo = mv.lo;
-            mu2_o = mu1_o;
-            mu1_o = __shfl_xor_sync(0xffffffffu, mu, 16);
-            mu1_o_lo = __shfl_xor_sync(0xffffffffu, mv.lo, 16);
         }
+        float4 *xw = reinterpret_cast<float4 *>(xs) + (j0 / 4) * kMxT + tid;
+        xw[0] = make_float4(xb[0], xb[1], xb[2], xb[3]);
+        xw[kMxT] = make_float4(xb[4], xb[5], xb[6], xb[7]);
     }
     if (!active) return;
     if (A.write_levels) {
@@ -860,6 +905,7 @@ static MixedArgs mixed_args(const Fp2sParams &P, const MixedLayout &l, const dou
     A.hdf = hdf;
     A.carry = l.carry;
     A.coef = l.coef;
+    A.wrem = l.wrem;
     A.gt_hi = l.gt_hi;
     A.gt_lo = l.gt_lo;
     A.status = status;
@@ -872,6 +918,8 @@ int mixed_direct_run(const Fp2sParams &P, const double *lam, const double *g0, d
     int st;
     tc::TcMaps maps;
     if ((st = mixed_maps(l, P, d1, d2, false, maps, s))) return st;
+    k_weight_rem<<<1, 32, 0, s>>>(l.kind, d1, d2, P.N, l.wrem);
+    if ((st = launched())) return st;
     MixedArgs A = mixed_args(P, l, lam, d1, d2, hdf, status);
     A.g0 = g0;
     A.gN = gN;
@@ -885,6 +933,8 @@ int mixed_grad_run(const Fp2sParams &P, const double *lam, const double *g0, dou
     int st;
     tc::TcMaps maps;
     if ((st = mixed_maps(l, P, d1, d2, true, maps, s))) return st;
+    k_weight_rem<<<1, 32, 0, s>>>(l.kind, d1, d2, P.N, l.wrem);
+    if ((st = launched())) return st;
     // forward solve, every level kept
     MixedArgs A = mixed_args(P, l, lam, d1, d2, hdf, status);
     A.g0 = g0;
