@@ -1047,9 +1047,9 @@ def run_ours(args, rank, world, dist):
     G0 = G0 * SCALE
     flags = fc.FP2S_ASYNC
 
-    def cproblem(q):
+    def cproblem(q, prec=0):
         return fc.problem(q.alpha1, q.alpha2, q.m, q.T, q.N, q.dim, q.M, q.scheme, q.form, q.np1, q.np2, q.ns,
-                          flags=flags)
+                          prec=prec, flags=flags)
 
     g0 = torch.tensor(G0, dtype=torch.float64, device=dev)
     gN = torch.empty_like(g0)
@@ -1060,8 +1060,8 @@ def run_ours(args, rank, world, dist):
         if dist is not None:
             dist.barrier()
 
-    def timed(q, K, W):
-        cp = cproblem(q)
+    def timed(q, K, W, prec=0):
+        cp = cproblem(q, prec)
         ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
         for _ in range(W):
             fc.fp2s_solve(cp, g0, gN, ws)
@@ -1097,6 +1097,8 @@ def run_ours(args, rank, world, dist):
         Kd, Wd = max(1, min(K, 4)), max(1, min(W, 1))
         d_steps, d_mains, d_launches, st_dir = timed(pd, Kd, Wd)
         gN_dir = gN.cpu().numpy()
+        # the same fast solve in the double-float form (FP64-class accuracy on the FP32 pipe)
+        df_steps, df_mains, df_launches, st_df = timed(p, K, W, fc.CQ_DF64)
         # end to end through the public API with pinned host buffers
         cp = cproblem(p)
         ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
@@ -1135,16 +1137,18 @@ def run_ours(args, rank, world, dist):
         from oracle import spatial as OSP
         g0m = torch.tensor(OSP.to_modal(G0, p.M, p.dim), dtype=torch.float64, device=dev)
         gm_fast, gm_dir = (_modal_solve(fc, torch, dev, cproblem(q), g0m) for q in (p, p.replace(form=ci.DIRECT)))
+        gm_df = _modal_solve(fc, torch, dev, cproblem(p, fc.CQ_DF64), g0m)
         del g0m
 
     ms = statistics.mean(steps)
     ms_main = statistics.mean(mains)
     ms_dir = statistics.mean(d_steps)
     ms_e2e = statistics.mean(e2e)
+    ms_df = statistics.mean(df_steps)
     if dist is not None:
-        t = torch.tensor([ms, ms_dir, ms_e2e], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms, ms_dir, ms_e2e, ms_df], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_dir, ms_e2e = t.tolist()
+        ms, ms_dir, ms_e2e, ms_df = t.tolist()
     units = p.ndof * p.N
     value = world * units / (ms * 1e-3)
     if rank != 0:
@@ -1183,6 +1187,7 @@ def run_ours(args, rank, world, dist):
         _ncpu() * 2 * nd * p.N, "oracle direct SBD scheme, %d seeded modes x %d steps per job" % (nd, p.N))
     error = {"fast": modal_parity(p, G0, gm_fast, sample, ref_fast),
              "direct": modal_parity(pd, G0, gm_dir, sample_d, ref_dir)}
+    error["fast_df64"] = modal_parity(p, G0, gm_df, sample, ref_fast)
     sc = np.max(np.abs(gm_dir))
     error["fast_vs_direct_rel_l2"] = float(np.linalg.norm((gm_fast - gm_dir) / sc) / np.linalg.norm(gm_dir / sc))
     error["status"] = fc.strerror(st_fast)
@@ -1210,6 +1215,8 @@ def run_ours(args, rank, world, dist):
     out["direct"] = {"value": world * units / (ms_dir * 1e-3), "unit": UNIT, "ms_per_step": ms_dir, "steps": Kd,
                      "warmup": Wd, "kernel": "k_fp2s_direct<8>", "kernel_ms": statistics.mean(d_mains),
                      "gpu_launches": int(d_launches), "status": fc.strerror(st_dir), "cpu_baseline": cpu_dir}
+    out["df64"] = df64_report(p, units, world, ms_df, statistics.mean(df_mains), ms, df_launches,
+                              fc.strerror(st_df), error["fast_df64"], K, W)
     if peaks is not None:
         out["peaks"] = peaks
     if prec_leg is not None:
@@ -1222,6 +1229,37 @@ def run_ours(args, rank, world, dist):
     out["summary"] = summary(out)
     _close_pool()
     return out
+
+
+def df64_fp32_ops_per_dof_step(p):
+    """FP32-pipe operations of the double-float fast solve per DOF and step: per node 15 (update
+    Y = r Y + G: TwoProduct with an FMA and TwoSum) or 23 (the slowest quarter of the node slots:
+    Y = Y - u Y + G, two TwoSums) plus 12 (adding c Y to the sum), and 12 per window term."""
+    npt = p.np1 + p.np2
+    NP = next(b for b in (16, 32, 48, 64, 80) if npt <= b)
+    ku = NP // 4
+    return 27 * (NP - ku) + 35 * ku + 12 * (p.ns - 1)
+
+
+def df64_report(p, units, world, ms, ms_main, ms_fp64, launches, status, error, K, W):
+    """The headline workload in the double-float form (CQ_DF64): FP64-class accuracy from pairs
+    of FP32 numbers on the FP32 pipe, the 2x2 step in FP64."""
+    ops = df64_fp32_ops_per_dof_step(p)
+    achieved = ops * units / (ms_main * 1e-3)
+    pk, pk_src = alu_peak("fp32")
+    flops64 = (4 * (p.np1 + p.np2) + 2 * (p.ns - 1)) * units
+    return {
+        "value": world * units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": K, "warmup": W,
+        "speedup_vs_fp64_form": ms_fp64 / ms, "gpu_launches": int(launches), "status": status,
+        "precision": "double-float (hi + lo FP32 pairs) node states, tables and history sums; FP64 2x2 step",
+        "roofline": {"kernel": "k_fp2s_fast_df<80, SBD, 17>", "bound": "alu", "unit": "T FP32-op/s",
+                     "achieved": achieved / 1e12, "peak": pk / 2e12, "frac": achieved / (pk / 2),
+                     "peak_source": pk_src + " / 2 (one FMA = 2 flops = 1 FP32-pipe operation)",
+                     "fp32_ops_per_dof_step": ops, "kernel_ms": ms_main,
+                     "fp64_equivalent_tflops": flops64 / (ms_main * 1e-3) / 1e12},
+        "error_vs_oracle": error,
+        "cpu_baseline": "the headline's (the same oracle fast scheme)",
+    }
 
 
 def _modal_solve(fc, torch, dev, cp, g0m):
@@ -1286,6 +1324,10 @@ def summary(out):
         "headline": {"value": out["value"], "ms_per_step": out["ms_per_step"], "e2e": g(out, "e2e", "value"),
                      "roofline_frac": g(out, "roofline", "frac"), "roofline_peak_source": g(out, "roofline",
                                                                                             "peak_source")},
+        "df64_fast_solve": {"value": g(out, "df64", "value"), "ms": g(out, "df64", "ms_per_step"),
+                            "speedup_vs_fp64_form": g(out, "df64", "speedup_vs_fp64_form"),
+                            "frac_fp32_pipe": g(out, "df64", "roofline", "frac"),
+                            "rel_l2_per_state": g(out, "error", "fast_df64", "rel_l2_per_state_decaying_modes")},
         "fp64_parity": {"fast": g(out, "error", "fast", "rel_l2_per_state_decaying_modes"),
                         "direct": g(out, "error", "direct", "rel_l2_per_state_decaying_modes"),
                         "fast_vs_direct_rel_l2": g(out, "error", "fast_vs_direct_rel_l2")},

@@ -64,8 +64,9 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.gN = cv.take<double>(2 * nm);
     if (P.form == CQ_DIRECT && P.prec == CQ_F64)
         l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
-    if (P.prec != CQ_F64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
+    if (P.prec != CQ_F64 && P.prec != CQ_DF64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
     if (P.form == CQ_FAST && P.prec == CQ_F32) l.ftab = cv.take<float>(kF32TabFloats);
+    if (P.form == CQ_FAST && P.prec == CQ_DF64) l.ftab = cv.take<float>(kDfTabFloats);
     if (P.form == CQ_DIRECT && (P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3)) {
         Fp2sParams Pm = P;                 // a gradient may run over slices of hist_modes modes
         if (grad && hist_modes >= 0) Pm.nmodes = hist_modes;
@@ -91,7 +92,7 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     if (p->M < 1 || p->M > (p->dim == 1 ? (1 << 16) : p->dim == 2 ? 4096 : 1024)) return CQ_EINVAL;
     if (p->scheme != CQ_BE && p->scheme != CQ_BDF2) return CQ_EINVAL;
     if (p->form != CQ_DIRECT && p->form != CQ_FAST) return CQ_EINVAL;
-    if (p->prec != CQ_F64 && !(p->prec == CQ_F32 && p->form == CQ_FAST) &&
+    if (p->prec != CQ_F64 && !((p->prec == CQ_F32 || p->prec == CQ_DF64) && p->form == CQ_FAST) &&
         !((p->prec == CQ_BF16X3 || p->prec == CQ_TF32X3) && p->form == CQ_DIRECT))
         return CQ_EUNSUPPORTED;
     P.prec = p->prec;
@@ -109,6 +110,7 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     if (p->form == CQ_FAST) {
         if (np1 < 1 || np2 < 0 || P.np > kMaxNp) return CQ_EINVAL;
         if (p->scheme == CQ_BDF2 && (np2 < 1 || P.L < 3 || P.L > kMaxNs)) return CQ_EINVAL;
+        if (P.prec == CQ_DF64 && df_np_bound(P.np) == 0) return CQ_EUNSUPPORTED;
     }
     return CQ_OK;
 }
@@ -1080,7 +1082,7 @@ static int setup_tables(const fp2s_problem_t *p, const Fp2sParams &P, int np1, i
     if ((st = cuda_status(cudaMemsetAsync(l.status, 0, 64 * sizeof(int), s)))) return st;
     if ((st = launch_weights(P.scheme, b1, P.tau, P.N, l.d1, s, l.wscr))) return st;
     if ((st = launch_weights(P.scheme, b2, P.tau, P.N, l.d2, s, l.wscr))) return st;
-    if (P.prec != CQ_F64) {
+    if (P.prec != CQ_F64 && P.prec != CQ_DF64) {
         k_half_weights_df<<<(unsigned)((P.N + 256) / 256), 256, 0, s>>>(l.d1, l.d2, P.N, l.hdf);
         if ((st = launched())) return st;
     }
@@ -1097,6 +1099,8 @@ static int setup_tables(const fp2s_problem_t *p, const Fp2sParams &P, int np1, i
             if (NP == 0) return CQ_EUNSUPPORTED;
             k_f32_tables<<<1, 256, 0, s>>>(NP, f32_df_pairs(NP), P.np, l.tab1, l.tab2, l.ftab);
             if ((st = launched())) return st;
+        } else if (P.prec == CQ_DF64) {
+            if ((st = fast_df_tables(P, l.tab1, l.tab2, l.d1, l.d2, l.ftab, s))) return st;
         }
     }
     return CQ_OK;
@@ -1115,6 +1119,8 @@ static int setup(const fp2s_problem_t *p, const Fp2sParams &P, int np1, int np2,
 // The single-launch solve kernels (fast FP64, fast FP32, direct FP64).
 static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s) {
     if (P.form == CQ_FAST && P.prec == CQ_F32) return fp2s_fast_f32(P, l, s);
+    if (P.form == CQ_FAST && P.prec == CQ_DF64)
+        return fast_df_solve(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.ftab, s);
     if (P.form == CQ_FAST && fast_use_split(P.nmodes)) return launch_fast_split(P, l, s);
     if (P.form == CQ_FAST) {
         const int T = fast_block_threads(P.np, P.L, P.nmodes);

@@ -10,7 +10,7 @@ struct Fp2sParams {
     double a, tau, inv_tau;
     int64_t N, nmodes;
     int scheme, form, np, L;     // np Gauss-Jacobi points per state, L exact window (2 for BE)
-    int prec;                    // CQ_F64 or CQ_F32 (fast form only)
+    int prec;                    // CQ_F64; CQ_F32 or CQ_DF64 (fast form); CQ_BF16X3 or CQ_TF32X3 (direct)
 };
 
 // ---------------------------------------------------------------------------
@@ -274,6 +274,16 @@ __device__ __forceinline__ void keep_reg(LaneStep2 &c) {
 }
 
 constexpr int kFastModesPerWarp = 16;     // a warp carries 16 modes x 2 states
+
+// Fast solve in double-float (CQ_DF64, fastdf.cu): node bound for np points per state (0: more
+// than it supports), its tables (from the FP64 tables r, c and the weights; kDfTabFloats floats)
+// and the solve over all N steps.
+constexpr int kDfTabFloats = 1024;
+int df_np_bound(int np);
+int fast_df_tables(const Fp2sParams &P, const double *tab1, const double *tab2, const double *d1, const double *d2,
+                   float *out, cudaStream_t s);
+int fast_df_solve(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
+                  const double *d1, const double *d2, const float *dftab, cudaStream_t s);
 
 // Mixed-precision direct solve (mixed.cu): workspace bytes of its own region, and
 // the run over all N steps (weights, spectrum and the modal G^0 already in place;

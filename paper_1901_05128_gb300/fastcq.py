@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libfastcq.so")
 CQ_OK, CQ_EINVAL, CQ_ENOMEM, CQ_ECUDA, CQ_ESINGULAR, CQ_ENONFINITE, CQ_ETIMEOUT, CQ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 CQ_BE, CQ_BDF2 = 1, 2
 CQ_DIRECT, CQ_FAST = 0, 1
-CQ_F64, CQ_F32, CQ_BF16X3, CQ_TF32X3 = 0, 1, 2, 3
+CQ_F64, CQ_F32, CQ_BF16X3, CQ_TF32X3, CQ_DF64 = 0, 1, 2, 3, 4
 FP2S_ASYNC = 1
 
 

@@ -26,7 +26,7 @@ def main(argv=None):
     ap.add_argument("--N", type=int, default=None, help="override the number of steps")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--scale-exp", type=int, default=-1000, help="G0 is multiplied by 2**scale_exp")
-    ap.add_argument("--prec", choices=["f64", "f32", "bf16x3", "tf32x3"], default="f64")
+    ap.add_argument("--prec", choices=["f64", "f32", "bf16x3", "tf32x3", "df64"], default="f64")
     ap.add_argument("--history", action="store_true",
                     help="run cq_history_direct alone on synthetic N(0,1) levels (--ndof, --n-lo, --n-hi)")
     ap.add_argument("--gradient", action="store_true",
@@ -53,7 +53,8 @@ def main(argv=None):
         p = p.replace(scheme=ci.BE if a.scheme == "be" else ci.BDF2)
     if a.N:
         p = p.replace(N=a.N, T=p.T * a.N / p.N)
-    prec = {"f64": fc.CQ_F64, "f32": fc.CQ_F32, "bf16x3": fc.CQ_BF16X3, "tf32x3": fc.CQ_TF32X3}[a.prec]
+    prec = {"f64": fc.CQ_F64, "f32": fc.CQ_F32, "bf16x3": fc.CQ_BF16X3, "tf32x3": fc.CQ_TF32X3,
+            "df64": fc.CQ_DF64}[a.prec]
     cp = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
                     prec=prec)
     g0 = torch.tensor(G0 * 2.0 ** a.scale_exp, dtype=torch.float64, device="cuda")

@@ -51,8 +51,9 @@ def _rel_per_state(got, ref):
     return out
 
 
-@pytest.mark.parametrize("form", [ci.FAST, ci.DIRECT])
-def test_bdf2_2d_m255_modal_parity(fc, form):
+@pytest.mark.parametrize("form,prec", [(ci.FAST, 0), (ci.DIRECT, 0), (ci.FAST, 4)],
+                         ids=["fast_f64", "direct_f64", "fast_df64"])
+def test_bdf2_2d_m255_modal_parity(fc, form, prec):
     """The 2D 255x255 BDF2 workload (N = 4096, m = 0.49, G0 x 2^-1000) over all 65,025 modes
     in the launch configuration of the benchmark, compared in the sine basis with the oracle's
     FP64 scheme (same form, same tables) on the 4 lowest and 60 seeded modes, with no
@@ -62,12 +63,13 @@ def test_bdf2_2d_m255_modal_parity(fc, form):
     from FP64 coefficients, so a relative error of one unit in the last place of a
     coefficient becomes many units in g^N. The test measures that conditioning with the
     oracle itself (the largest change of g^N when lambda_k, a or T moves by one ulp) and
-    bounds the GPU's error on each growing mode by 4 x it."""
+    bounds the GPU's error on each growing mode by 4 x it. The double-float fast form
+    (CQ_DF64) is held to the same bars."""
     p, G0 = ci.workload("bdf2_2d_m255")
     p = p.replace(form=form)
     g0m = OSP.to_modal(G0 * 2.0 ** -1000, p.M, p.dim)
     nm = p.M ** p.dim
-    got, st = _modes(fc, _cp(fc, p), g0m, 0, nm)
+    got, st = _modes(fc, _cp(fc, p, prec), g0m, 0, nm)
     assert st == fc.CQ_OK
     sample = np.unique(np.concatenate([[0, 1, p.M, p.M + 1], ci.sample_indices(nm, 60, ci.SEED_BASE + 12)]))
     lam_all = OSP.mode_eigenvalues(p.M, p.dim)
@@ -76,8 +78,8 @@ def test_bdf2_2d_m255_modal_parity(fc, form):
     calm = sample[~growing]
     ref = OS.solve_modal(p, lam_all[calm], g0m[:, calm])[p.N]
     errs = _rel_per_state(got[:, calm], ref)
-    print("modal parity %s: rel L2 per state %.3e %.3e over %d decaying modes"
-          % ("fast" if form == ci.FAST else "direct", errs[0], errs[1], len(calm)))
+    print("modal parity %s%s: rel L2 per state %.3e %.3e over %d decaying modes"
+          % ("fast" if form == ci.FAST else "direct", " df64" if prec == 4 else "", errs[0], errs[1], len(calm)))
     assert max(errs) <= 1e-12
     one_ulp = 2.0 ** -52
     for k in sample[growing]:
@@ -96,6 +98,7 @@ SHARD_CASES = [
     ("fast_f64_2d", ci.Problem(0.4, 0.6, 0.3, 1.0, 300, 2, 255, ci.BDF2, ci.FAST, 16, 48, 17), 0),
     ("direct_f64_2d", ci.Problem(0.3, 0.7, 0.4, 1.0, 200, 2, 283, ci.BE, ci.DIRECT, 0, 0, 0), 0),
     ("fast_f32_2d", ci.Problem(0.2, 0.8, 0.45, 1.0, 400, 2, 127, ci.BE, ci.FAST, 64, 0, 2), 1),
+    ("fast_df64_2d", ci.Problem(0.4, 0.6, 0.3, 1.0, 300, 2, 255, ci.BDF2, ci.FAST, 16, 48, 17), 4),
     ("mixed_bf16x3_2d", ci.Problem(0.4, 0.6, 0.3, 1.0, 300, 2, 255, ci.BDF2, ci.DIRECT, 0, 0, 0), 2),
     ("mixed_tf32x3_2d", ci.Problem(0.3, 0.7, 0.4, 1.0, 260, 2, 255, ci.BE, ci.DIRECT, 0, 0, 0), 3),
 ]
@@ -121,7 +124,7 @@ def test_two_shards_equal_whole(fc, name, p, prec):
     ref = OS.solve_modal(p, OSP.mode_eigenvalues(p.M, p.dim)[sample], g0m[:, sample])[p.N]
     errs = _rel_per_state(whole[:, sample], ref)
     print("shards %s: rel L2 per state vs oracle %.3e %.3e" % (name, *errs))
-    assert max(errs) <= (1e-12 if prec == 0 else 2e-5)
+    assert max(errs) <= (1e-12 if prec in (0, 4) else 2e-5)
 
 
 def test_single_mode_range(fc):
