@@ -535,7 +535,33 @@ __device__ __forceinline__ void f32_window(const float2 *Rc, const float *ws, co
     }
 }
 
-template <int NP, bool BE>
+// The same window unrolled to a compile-time bound WL >= L, with no branch: terms i >= L have
+// zero weight, and levels before level 1 sit in ring slots that are still zero. In the
+// pipelined loop this keeps the node part, the window and the step in one basic block, so
+// the compiler can interleave the step's dependency chain with the node work.
+template <bool LO, int WL>
+__device__ __forceinline__ void f32_window_u(const float2 *Rc, const float *ws, const float *wsl, int T, int L,
+                                             int slot, int hf, float (&hA)[4], float (&hB)[4], float &wlA,
+                                             float &wlB) {
+#pragma unroll
+    for (int q = 0; 2 * q < WL - 1; ++q) {
+        const int i = 2 * q + 1 + hf;
+        const bool on = i < L;
+        int sl = slot - i;
+        if (sl < 0) sl += L;
+        const float2 v = Rc[(on ? sl : slot) * T];
+        const float w = on ? ws[2 * i] : 0.0f;
+        hA[3] = fmaf(w, v.x, hA[3]);
+        hB[3] = fmaf(w, v.y, hB[3]);
+        if (LO) {
+            const float wl = on ? wsl[2 * i] : 0.0f;
+            wlA = fmaf(wl, v.x, wlA);
+            wlB = fmaf(wl, v.y, wlB);
+        }
+    }
+}
+
+template <int NP, bool BE, int WL>
 __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int solve64,
                                                                const double *__restrict__ lam,
                                                                const double *__restrict__ g0,
@@ -660,7 +686,7 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
             float nA[4], nB[4];
             f32_node_part<NQ, KD>(tb, tl, cs, Rc[next * T], YA, YB, nA, nB);  // step n + 1
             float wlA = 0.0f, wlB = 0.0f;
-            f32_window<!BE>(Rc, ws, wsl, T, L, slot, n, hf, hA, hB, wlA, wlB);  // step n
+            f32_window_u<!BE, WL>(Rc, ws, wsl, T, L, slot, hf, hA, hB, wlA, wlB);  // step n
             const float h = combine();
             // The window took fl(d_i) fl(x^{n-i}); the FP32 remainders of the weights (a weight
             // rounded to FP32 is a fixed relative error of up to 2^-25 that every step repeats,
@@ -709,12 +735,14 @@ static void launch_f32(const Fp2sParams &P, int solve64, const Fp2sLayout &l, cu
     const int T = kF32Threads;
     const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
     const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
-    if (P.scheme == CQ_BE)
-        k_fp2s_fast_f32<NP, true><<<blocks, T, f32_smem_bytes(NP, P.L, T), s>>>(
-            P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.ftab, l.hdf);
-    else
-        k_fp2s_fast_f32<NP, false><<<blocks, T, f32_smem_bytes(NP, P.L, T), s>>>(
-            P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.ftab, l.hdf);
+    const size_t smem = f32_smem_bytes(NP, P.L, T);
+#define CQ_F32_LAUNCH(BEV, WLV)                                                                              \
+    k_fp2s_fast_f32<NP, BEV, WLV><<<blocks, T, smem, s>>>(P, solve64, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, \
+                                                          l.ftab, l.hdf)
+    if (P.scheme == CQ_BE) CQ_F32_LAUNCH(true, 2);
+    else if (P.L <= 17) CQ_F32_LAUNCH(false, 17);
+    else CQ_F32_LAUNCH(false, kMaxNs);
+#undef CQ_F32_LAUNCH
 }
 
 // The compile-time node bound NP of the FP32 fast kernel for np points per state (0: too many).
