@@ -821,9 +821,10 @@ def batch_leg(fc, torch, dev, K, flush):
                          "note": "fp2s_solve_batched captured once in a CUDA graph (five kernels, one memset), "
                                  "replayed; L2 flushed before every replay, outside the events"},
         "launch_shape": {"warps_per_block": plan.warps_per_block, "ctas_per_sm": plan.ctas_per_sm or "all that fit",
+                         "node_unroll": plan.node_unroll,
                          "autotuned": bool(plan.flags & 1), "candidates_timed": plan.tuned_candidates,
-                         "tuner": "block widths 2..16 warps x (all, half of the CTAs per SM that fit), 96-step run, "
-                                  "median of three timings each"},
+                         "tuner": "block widths 2..16 warps x (all, half of the CTAs per SM that fit) x node-loop "
+                                  "width (2, 4, 8 partial sums), 96-step run, median of three timings each"},
         "plan_s": plan_s, "gpu_launches_per_solve": launches, "status": status,
         "sum_of_single_solves_ms": t_single, "persistent_launch_efficiency": t_single / ms,
         "max_abs_diff_vs_single_solves_rel_to_instance_max": max(singles),

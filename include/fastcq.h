@@ -313,6 +313,7 @@ typedef struct {
     int32_t max_np, max_L, max_N, max_M, flags;   /* flags bit 0: launch shape chosen by the autotuner */
     int32_t ctas_per_sm;            /* resident CTAs per SM of the persistent launch (0: as many as fit) */
     int32_t tuned_candidates;       /* launch shapes the autotuner timed (0 without tuning) */
+    int32_t node_unroll;            /* partial sums of the node loop: 2, 4 or 8 (autotuned or 4) */
     int64_t max_modes, field_elems; /* field_elems: doubles of a packed [instance][2][M^dim] field */
     int64_t ws_bytes;
     int64_t off[16];                /* workspace regions (internal) */
@@ -324,8 +325,9 @@ typedef struct {
  * orders the work units by decreasing cost. 1 <= n <= 65535 (more: CQ_EUNSUPPORTED;
  * split such a set into several batches). tune != 0 autotunes the launch shape:
  * every block width whose shared memory fits (2..16 warps), each with all and
- * with half of the CTAs per SM that fit, is timed on a shortened run (96 steps,
- * median of three) and the fastest is kept (warps_per_block, ctas_per_sm).
+ * with half of the CTAs per SM that fit and with 2, 4 or 8 partial sums in the
+ * node loop, is timed on a shortened run (96 steps, median of three) and the
+ * fastest is kept (warps_per_block, ctas_per_sm, node_unroll).
  * Size query when ws_dev == NULL. Synchronises `stream`; the plan and the
  * workspace stay valid for any number of fp2s_solve_batched calls. */
 int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t tune, fp2s_batch_t *plan, void *ws_dev,

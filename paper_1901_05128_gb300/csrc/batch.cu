@@ -8,8 +8,8 @@
 // units of 16 x WB modes, orders the units by decreasing cost (longest
 // processing time first) and, when asked, autotunes the launch shape: every
 // block width WB whose shared memory fits, each with the full occupancy and with
-// half of it (resident CTAs per SM), timed on a shortened run (median of three)
-// and the fastest kept.
+// half of it (resident CTAs per SM), and each node-loop width (2, 4 or 8 partial
+// sums), timed on a shortened run (median of three) and the fastest kept.
 // fp2s_solve_batched then only transforms G0, runs the persistent kernel (its
 // CTAs take units from an atomic counter: no CTA ever waits for another) and
 // transforms back: five launches and one memset, with no host synchronisation,
@@ -198,6 +198,8 @@ __global__ void k_b_dst_pass(const InstDesc *__restrict__ D, const double *__res
 // ---------------------------------------------------------------------------
 // persistent fast solve over work units (same per-mode arithmetic as k_fp2s_fast)
 // ---------------------------------------------------------------------------
+// NU: partial sums of the node loop (nodes processed NU at a time; a tuning knob).
+template <int NU>
 __global__ void __launch_bounds__(1024) k_b_fast(const InstDesc *__restrict__ D, const Unit *__restrict__ U,
                                                  int n_units, int *__restrict__ counter, int maxnp, int maxL,
                                                  int64_t step_cap, const double *__restrict__ W,
@@ -266,38 +268,41 @@ __global__ void __launch_bounds__(1024) k_b_fast(const InstDesc *__restrict__ D,
         int slot = 0;
         for (int64_t n = 1; n <= P.N; ++n) {
             slot = (slot + 1 == L) ? 0 : slot + 1;
-            double h0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0;
+            double hp[NU];
+#pragma unroll
+            for (int u = 0; u < NU; ++u) hp[u] = 0.0;
             if (n - L >= 1) {
                 const double in = Rc[(size_t)slot * T];
                 int j = 0;
-                for (; j + 4 <= np; j += 4) {
-                    const double y0 = fma(rs[2 * j], Yc[(size_t)j * T], in);
-                    const double y1 = fma(rs[2 * j + 2], Yc[(size_t)(j + 1) * T], in);
-                    const double y2 = fma(rs[2 * j + 4], Yc[(size_t)(j + 2) * T], in);
-                    const double y3 = fma(rs[2 * j + 6], Yc[(size_t)(j + 3) * T], in);
-                    Yc[(size_t)j * T] = y0;
-                    Yc[(size_t)(j + 1) * T] = y1;
-                    Yc[(size_t)(j + 2) * T] = y2;
-                    Yc[(size_t)(j + 3) * T] = y3;
-                    h0 = fma(cs[2 * j], y0, h0);
-                    h1 = fma(cs[2 * j + 2], y1, h1);
-                    h2 = fma(cs[2 * j + 4], y2, h2);
-                    h3 = fma(cs[2 * j + 6], y3, h3);
+                for (; j + NU <= np; j += NU) {
+                    double y[NU];
+#pragma unroll
+                    for (int u = 0; u < NU; ++u) y[u] = fma(rs[2 * (j + u)], Yc[(size_t)(j + u) * T], in);
+#pragma unroll
+                    for (int u = 0; u < NU; ++u) {
+                        Yc[(size_t)(j + u) * T] = y[u];
+                        hp[u] = fma(cs[2 * (j + u)], y[u], hp[u]);
+                    }
                 }
                 for (; j < np; ++j) {
                     const double y = fma(rs[2 * j], Yc[(size_t)j * T], in);
                     Yc[(size_t)j * T] = y;
-                    h0 = fma(cs[2 * j], y, h0);
+                    hp[0] = fma(cs[2 * j], y, hp[0]);
                 }
             }
             const int imax = (int)min((int64_t)(L - 1), n - 1);
             int sl = slot;
             for (int i = 1; i <= imax; ++i) {
                 sl = (sl == 0) ? L - 1 : sl - 1;
-                if (i & 1) h1 = fma(ws[2 * i], Rc[(size_t)sl * T], h1);
-                else h2 = fma(ws[2 * i], Rc[(size_t)sl * T], h2);
+                if (i & 1) hp[1] = fma(ws[2 * i], Rc[(size_t)sl * T], hp[1]);
+                else hp[NU > 2 ? 2 : 0] = fma(ws[2 * i], Rc[(size_t)sl * T], hp[NU > 2 ? 2 : 0]);
             }
-            const double h = (h0 + h1) + (h2 + h3);
+            double h = 0.0;
+#pragma unroll
+            for (int w = 1; w < NU; w *= 2)
+#pragma unroll
+                for (int u = 0; u + w < NU; u += 2 * w) hp[u] += hp[u + w];
+            h = hp[0];
             double e, lead, m_oo = mn_oo, m_ot = mn_ot;
             if (P.scheme == CQ_BE) {
                 e = h;
@@ -381,13 +386,23 @@ static void make_units(const std::vector<InstDesc> &descs, int wb, std::vector<U
 
 static int num_sms_b() { return device_sms(); }
 
+// The persistent kernel for a node-loop width (2, 4 or 8 partial sums; 0 = the default 4).
+using BFastKernel = void (*)(const InstDesc *, const Unit *, int, int *, int, int, int64_t, const double *,
+                             const double *, const double *, double *, int *);
+static BFastKernel bfast_kernel(int node_unroll) {
+    if (node_unroll == 2) return k_b_fast<2>;
+    if (node_unroll == 8) return k_b_fast<8>;
+    return k_b_fast<4>;
+}
+
 // Resident CTAs per SM of the persistent kernel for a block width (0 when it does not fit).
-static int occupancy(int max_np, int max_L, int wb) {
+static int occupancy(int max_np, int max_L, int wb, int node_unroll) {
     const int T = 32 * wb;
     const size_t smem = bfast_smem(max_np, max_L, T);
-    if (cudaFuncSetAttribute(k_b_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    const BFastKernel k = bfast_kernel(node_unroll);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_fast, T, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem) != cudaSuccess) return 0;
     return per_sm;
 }
 
@@ -395,15 +410,16 @@ static int occupancy(int max_np, int max_L, int wb) {
 static int launch_main(const fp2s_batch_t *plan, const BatchLayout &l, int64_t step_cap, cudaStream_t s) {
     const int T = 32 * plan->warps_per_block;
     const size_t smem = bfast_smem(plan->max_np, plan->max_L, T);
-    const int fit = occupancy(plan->max_np, plan->max_L, plan->warps_per_block);
+    const int fit = occupancy(plan->max_np, plan->max_L, plan->warps_per_block, plan->node_unroll);
     if (fit < 1) return CQ_EUNSUPPORTED;
     const int per_sm = plan->ctas_per_sm > 0 ? std::min(plan->ctas_per_sm, fit) : fit;
     const int64_t want = (int64_t)num_sms_b() * per_sm;
     const int blocks = (int)std::min<int64_t>(want, plan->n_units);
     int st = cuda_status(cudaMemsetAsync(l.counter, 0, sizeof(int), s));
     if (st) return st;
-    k_b_fast<<<blocks, T, smem, s>>>(l.desc, l.units, plan->n_units, l.counter, plan->max_np, plan->max_L, step_cap,
-                                    l.W, l.tab, l.lam, l.modal, l.status);
+    bfast_kernel(plan->node_unroll)<<<blocks, T, smem, s>>>(l.desc, l.units, plan->n_units, l.counter, plan->max_np,
+                                                           plan->max_L, step_cap, l.W, l.tab, l.lam, l.modal,
+                                                           l.status);
     return launched();
 }
 
@@ -517,10 +533,12 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
     const int64_t spec = std::max<int64_t>(z.max_nmodes, (int64_t)z.maxM * z.maxM);
     k_b_spectrum<<<dim3((unsigned)((spec + 255) / 256), n), 256, 0, s>>>(l.desc, l.lam, l.S);
     if ((st = launched(4))) return st;
-    // launch shape: the widest block with full occupancy by default, or the fastest candidate
-    // (block width x resident CTAs per SM) on a shortened run, median of three timings each
-    int best = cands.front(), best_cps = 0;
+    // launch shape: the widest block with full occupancy and 4 partial sums by default, or the
+    // fastest candidate (block width x resident CTAs per SM x node-loop width) on a shortened
+    // run, median of three timings each
+    int best = cands.front(), best_cps = 0, best_nu = 4;
     plan->tuned_candidates = 0;
+    plan->node_unroll = 4;
     if (tune) {
         EventPair ev;
         if (!ev.ok()) return CQ_ECUDA;
@@ -528,8 +546,6 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
         const int64_t cap = std::min<int64_t>(z.maxN, 96);
         for (int wb : cands) {
             if (wb < 2) continue;
-            const int fit = occupancy(z.maxnp, z.maxL, wb);
-            if (fit < 1) continue;
             std::vector<Unit> units;
             make_units(descs, wb, units);
             plan->warps_per_block = wb;
@@ -537,29 +553,36 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
             if ((st = cuda_status(cudaMemcpyAsync(l.units, units.data(), units.size() * sizeof(Unit),
                                                   cudaMemcpyHostToDevice, s))))
                 return st;
-            for (int cps : {fit, fit / 2}) {
-                if (cps < 1 || (cps == fit / 2 && fit / 2 == fit)) continue;
-                plan->ctas_per_sm = cps;
-                if ((st = launch_main(plan, l, cap, s))) return st;        // warm-up
-                float t[3];
-                for (float &ti : t) {
-                    cudaEventRecord(ev.a, s);
-                    if ((st = launch_main(plan, l, cap, s))) return st;
-                    cudaEventRecord(ev.b, s);
-                    if (cudaEventSynchronize(ev.b) != cudaSuccess) return CQ_ECUDA;
-                    if (cudaEventElapsedTime(&ti, ev.a, ev.b) != cudaSuccess) return CQ_ECUDA;
-                }
-                std::sort(t, t + 3);
-                ++plan->tuned_candidates;
-                if (t[1] < best_ms * 0.98f) {
-                    best_ms = t[1];
-                    best = wb;
-                    best_cps = cps == fit ? 0 : cps;
+            for (int nu : {4, 2, 8}) {
+                const int fit = occupancy(z.maxnp, z.maxL, wb, nu);
+                if (fit < 1) continue;
+                plan->node_unroll = nu;
+                for (int cps : {fit, fit / 2}) {
+                    if (cps < 1 || (cps == fit / 2 && fit / 2 == fit)) continue;
+                    plan->ctas_per_sm = cps;
+                    if ((st = launch_main(plan, l, cap, s))) return st;        // warm-up
+                    float t[3];
+                    for (float &ti : t) {
+                        cudaEventRecord(ev.a, s);
+                        if ((st = launch_main(plan, l, cap, s))) return st;
+                        cudaEventRecord(ev.b, s);
+                        if (cudaEventSynchronize(ev.b) != cudaSuccess) return CQ_ECUDA;
+                        if (cudaEventElapsedTime(&ti, ev.a, ev.b) != cudaSuccess) return CQ_ECUDA;
+                    }
+                    std::sort(t, t + 3);
+                    ++plan->tuned_candidates;
+                    if (t[1] < best_ms * 0.98f) {
+                        best_ms = t[1];
+                        best = wb;
+                        best_cps = cps == fit ? 0 : cps;
+                        best_nu = nu;
+                    }
                 }
             }
         }
         plan->flags |= 1;
     }
+    plan->node_unroll = best_nu;
     plan->ctas_per_sm = best_cps;
     std::vector<Unit> units;
     make_units(descs, best, units);

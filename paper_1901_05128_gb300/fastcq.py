@@ -45,6 +45,7 @@ class BatchPlan(C.Structure):
     _fields_ = [("n_inst", C.c_int32), ("n_units", C.c_int32), ("warps_per_block", C.c_int32),
                 ("max_np", C.c_int32), ("max_L", C.c_int32), ("max_N", C.c_int32), ("max_M", C.c_int32),
                 ("flags", C.c_int32), ("ctas_per_sm", C.c_int32), ("tuned_candidates", C.c_int32),
+                ("node_unroll", C.c_int32),
                 ("max_modes", C.c_int64), ("field_elems", C.c_int64),
                 ("ws_bytes", C.c_int64), ("off", C.c_int64 * 16)]
 

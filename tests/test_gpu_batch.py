@@ -65,11 +65,12 @@ def test_batch_matches_single_solves_and_oracle(fc, tune):
     plan = fc.fp2s_batch_plan(cps, ws, tune=tune)
     assert plan.n_inst == len(MIXED) and plan.n_units >= len(MIXED)
     if tune:
-        # block widths x (all, half of the CTAs per SM that fit), each timed three times
-        assert plan.flags & 1 and plan.tuned_candidates >= 2
-        assert 2 <= plan.warps_per_block <= 16 and plan.ctas_per_sm >= 0
+        # block widths x (all, half of the CTAs per SM that fit) x node-loop widths, each timed
+        # three times
+        assert plan.flags & 1 and plan.tuned_candidates >= 6
+        assert 2 <= plan.warps_per_block <= 16 and plan.ctas_per_sm >= 0 and plan.node_unroll in (2, 4, 8)
     else:
-        assert plan.tuned_candidates == 0 and plan.ctas_per_sm == 0
+        assert plan.tuned_candidates == 0 and plan.ctas_per_sm == 0 and plan.node_unroll == 4
     assert plan.field_elems == sum(2 * p.M ** p.dim for p in MIXED)
     g0 = _pack(fields)
     gN = torch.empty_like(g0)
