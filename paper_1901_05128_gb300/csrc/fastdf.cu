@@ -26,8 +26,9 @@
 // exponent range is never reached; the exponent is carried in an integer and
 // applied on output. Layout and lane roles as the FP64 kernel: lane l < 16 of a warp
 // carries state 1 and lane l + 16 state 2 of the same mode; the node states of a
-// lane live in registers (NP, a compile-time bound, is at most 80: 160 registers), the
-// last L levels in a per-lane ring in shared memory. Measured on the 2D 255 x 255 grid
+// lane live in registers (the top 80 slots: 160 registers; for NP > 80, a compile-time bound
+// of at most 128, the fastest-decaying NP - 80 slots in shared memory, column tid), the last L
+// levels in a per-lane ring in shared memory. Measured on the 2D 255 x 255 grid
 // (80 points, N = 4096): holding half of the node states in shared memory to fit three
 // warps per scheduler was slower (80 against 58 ms), as was a loop body with the node
 // part and the window behind branches (76 ms): the FP64 step is a long dependency chain
@@ -44,6 +45,11 @@ constexpr int kDfMinBlocks = 2;       // two CTAs per SM: two warps per schedule
 
 // Slots of the u form (the slowest-decaying nodes): the top quarter.
 __host__ __device__ constexpr int df_u_slots(int NP) { return NP / 4; }
+
+// Node slots held in registers (the top ones: the slowest nodes, u form included); the bottom
+// NP - kDfRegSlots slots (fast-decaying, r form) live in shared memory, column tid.
+constexpr int kDfRegSlots = 80;
+__host__ __device__ constexpr int df_smem_slots(int NP) { return NP > kDfRegSlots ? NP - kDfRegSlots : 0; }
 
 // Floats of the kernel's table: [NP][2] float4 (a_hi, a_lo, c_hi, c_lo) with a = r or
 // a = 1 - r, then [kMaxNs][2] float2 window weights d_i.
@@ -160,13 +166,17 @@ __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
                    double *__restrict__ gN, int *__restrict__ status, const double *__restrict__ d1,
                    const double *__restrict__ d2, const float *__restrict__ dftab) {
     constexpr int KR = NP - df_u_slots(NP);       // slots of the r form
+    constexpr int KS = df_smem_slots(NP);         // slots in shared memory (all of the r form)
+    static_assert(KS <= KR, "shared-memory slots take the r form");
     extern __shared__ __align__(16) float smd[];
     const int L = P.L, T = blockDim.x, tid = threadIdx.x;
     const float4 *tab = reinterpret_cast<const float4 *>(smd);
     const float2 *wdf = reinterpret_cast<const float2 *>(smd + 8 * NP);
     float2 *R = reinterpret_cast<float2 *>(smd + df_table_floats(NP));      // [L][T]
+    float2 *Ys = R + (size_t)L * T;                                          // [KS][T]
     for (int e = tid; e < df_table_floats(NP); e += T) smd[e] = dftab[e];
     for (int j = 0; j < L; ++j) R[(size_t)j * T + tid] = make_float2(0.0f, 0.0f);
+    for (int j = 0; j < KS; ++j) Ys[(size_t)j * T + tid] = make_float2(0.0f, 0.0f);
     __syncthreads();
 
     const int lane = tid & 31, st = lane >> 4;
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
     const int64_t mode = active ? mode_raw : 0;
     const float4 *tb = tab + st;
     const float2 *ws = wdf + st;
-    float2 *Rc = R + tid;
+    float2 *Rc = R + tid, *Yc = Ys + tid;
     const double *dn = st ? d2 : d1;
 
     // per-mode power-of-two scale from max(|g1^0|, |g2^0|)
@@ -192,9 +202,9 @@ __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
     const double mn_oo = st ? mc.Mn.i22 : mc.Mn.i11, mn_ot = st ? mc.Mn.i21 : mc.Mn.i12;
     const double a = P.a, c = mc.c, inv_tau = P.inv_tau;
 
-    float yh[NP], yl[NP];
+    float yh[NP - KS], yl[NP - KS];              // slot j >= KS in register j - KS
 #pragma unroll
-    for (int j = 0; j < NP; ++j) yh[j] = yl[j] = 0.0f;
+    for (int j = 0; j < NP - KS; ++j) yh[j] = yl[j] = 0.0f;
     double gm1 = gz, gm2 = 0.0;
     const int64_t N = P.N;
     int slot = 1 % L;                            // n % L
@@ -221,12 +231,22 @@ __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
         float nh0 = 0.0f, nl0 = 0.0f, nh1 = 0.0f, nl1 = 0.0f;
         const float2 g = Rc[(size_t)next * T];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
+        for (int j = 0; j < KS; ++j) {
             const float4 t = tb[2 * j];
-            if (j < KR) node_r(t.x, t.y, g.x, g.y, yh[j], yl[j]);
-            else node_u(t.x, t.y, g.x, g.y, yh[j], yl[j]);
-            if (j & 1) acc_prod(t.z, t.w, yh[j], yl[j], nh1, nl1);
-            else acc_prod(t.z, t.w, yh[j], yl[j], nh0, nl0);
+            float2 y = Yc[(size_t)j * T];
+            node_r(t.x, t.y, g.x, g.y, y.x, y.y);
+            Yc[(size_t)j * T] = y;
+            if (j & 1) acc_prod(t.z, t.w, y.x, y.y, nh1, nl1);
+            else acc_prod(t.z, t.w, y.x, y.y, nh0, nl0);
+        }
+#pragma unroll
+        for (int j = KS; j < NP; ++j) {
+            const float4 t = tb[2 * j];
+            float &ya = yh[j - KS], &yb = yl[j - KS];
+            if (j < KR) node_r(t.x, t.y, g.x, g.y, ya, yb);
+            else node_u(t.x, t.y, g.x, g.y, ya, yb);
+            if (j & 1) acc_prod(t.z, t.w, ya, yb, nh1, nl1);
+            else acc_prod(t.z, t.w, ya, yb, nh0, nl0);
         }
         // exact window of step n: d_i x^{n-i}, i = 1 .. L - 1 (levels before 1 are zero slots;
         // terms i >= L have zero weights)
@@ -265,9 +285,13 @@ __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
             const float f = ldexpf(1.0f, -k);
             const double fd = ldexp(1.0, -k);
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
+            for (int j = 0; j < NP - KS; ++j) {
                 yh[j] *= f;
                 yl[j] *= f;
+            }
+            for (int j = 0; j < KS; ++j) {
+                const float2 v = Yc[(size_t)j * T];
+                Yc[(size_t)j * T] = make_float2(v.x * f, v.y * f);
             }
             for (int j = 0; j < L; ++j) {
                 const float2 v = Rc[(size_t)j * T];
@@ -301,11 +325,11 @@ __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 }
 
 static size_t df_smem_bytes(int NP, int L) {
-    return (size_t)df_table_floats(NP) * sizeof(float) + (size_t)L * kDfThreads * sizeof(float2);
+    return (size_t)df_table_floats(NP) * sizeof(float) + (size_t)(L + df_smem_slots(NP)) * kDfThreads * sizeof(float2);
 }
 
 int df_np_bound(int np) {
-    for (int b : {16, 32, 48, 64, 80})
+    for (int b : {16, 32, 48, 64, 80, 96, 112, 128})
         if (np <= b) return b;
     return 0;
 }
@@ -369,7 +393,6 @@ template <int NP>
 static int launch_df(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
                      const double *d1, const double *d2, const float *dftab, cudaStream_t s) {
     if (P.scheme == CQ_BE) return launch_df_kernel<NP, true, 2>(P, lam, g0, gN, status, d1, d2, dftab, s);
-    if (P.L <= 9) return launch_df_kernel<NP, false, 9>(P, lam, g0, gN, status, d1, d2, dftab, s);
     if (P.L <= 17) return launch_df_kernel<NP, false, 17>(P, lam, g0, gN, status, d1, d2, dftab, s);
     return launch_df_kernel<NP, false, kMaxNs>(P, lam, g0, gN, status, d1, d2, dftab, s);
 }
@@ -382,6 +405,9 @@ int fast_df_solve(const Fp2sParams &P, const double *lam, const double *g0, doub
         case 48: return launch_df<48>(P, lam, g0, gN, status, d1, d2, dftab, s);
         case 64: return launch_df<64>(P, lam, g0, gN, status, d1, d2, dftab, s);
         case 80: return launch_df<80>(P, lam, g0, gN, status, d1, d2, dftab, s);
+        case 96: return launch_df<96>(P, lam, g0, gN, status, d1, d2, dftab, s);
+        case 112: return launch_df<112>(P, lam, g0, gN, status, d1, d2, dftab, s);
+        case 128: return launch_df<128>(P, lam, g0, gN, status, d1, d2, dftab, s);
         default: return CQ_EUNSUPPORTED;
     }
 }

@@ -278,7 +278,7 @@ constexpr int kFastModesPerWarp = 16;     // a warp carries 16 modes x 2 states
 // Fast solve in double-float (CQ_DF64, fastdf.cu): node bound for np points per state (0: more
 // than it supports), its tables (from the FP64 tables r, c and the weights; kDfTabFloats floats)
 // and the solve over all N steps.
-constexpr int kDfTabFloats = 1024;
+constexpr int kDfTabFloats = 8 * 128 + 4 * kMaxNs;
 int df_np_bound(int np);
 int fast_df_tables(const Fp2sParams &P, const double *tab1, const double *tab2, const double *d1, const double *d2,
                    float *out, cudaStream_t s);

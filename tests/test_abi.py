@@ -118,13 +118,15 @@ def test_mixed_direct_size_query(fc):
 
 def test_df64_form_host_checks(fc):
     """The double-float fast solve (CQ_DF64) needs no more workspace than the FP64 fast
-    solve's tables and modal vectors; it takes the fast form with up to 80 points per state,
+    solve's tables and modal vectors; it takes the fast form with up to 128 points per state,
     and rejects the direct form and larger node counts before touching the device."""
     sz = C.c_size_t(0)
     p = fc.problem(0.4, 0.6, 0.49, 1.0, 4096, 2, 255, fc.CQ_BDF2, fc.CQ_FAST, 16, 64, 17, prec=fc.CQ_DF64)
     n_df = fc.fp2s_solve(p, None, None, None)
     assert 0 < n_df < 64 << 20
-    big = fc.problem(0.4, 0.6, 0.49, 1.0, 4096, 2, 255, fc.CQ_BDF2, fc.CQ_FAST, 16, 65, 17, prec=fc.CQ_DF64)
+    ok = fc.problem(0.2, 0.8, 0.45, 1.0, 8192, 2, 511, fc.CQ_BE, fc.CQ_FAST, 128, 0, 2, prec=fc.CQ_DF64)
+    assert 0 < fc.fp2s_solve(ok, None, None, None) < 64 << 20
+    big = fc.problem(0.4, 0.6, 0.49, 1.0, 4096, 2, 255, fc.CQ_BDF2, fc.CQ_FAST, 16, 113, 17, prec=fc.CQ_DF64)
     assert fc._lib.fp2s_solve(C.byref(big), None, None, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
     dr = fc.problem(0.4, 0.6, 0.49, 1.0, 4096, 2, 255, fc.CQ_BDF2, fc.CQ_DIRECT, prec=fc.CQ_DF64)
     assert fc._lib.fp2s_solve(C.byref(dr), None, None, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED

@@ -5,7 +5,8 @@ significant bits) on the FP32 pipe, the 2x2 step is FP64. It is held to the FP64
 of the fast form: against the oracle's FP64 fast scheme (same tables), relative L2
 error <= 1e-12 per state and max element error <= 1e-11 * max|ref|, and against the
 GPU's FP64 fast solve the same. The cases cover both schemes, 1D/2D/3D grids, every
-compile-time node bound (16 .. 80 points per state, ragged counts), the few-mode sizes,
+compile-time node bound (16 .. 128 points per state, ragged counts; above 80 the
+fastest-decaying slots live in shared memory), the few-mode sizes,
 and the power-of-two rescaling that keeps every mode inside the FP32 exponent range
 (fields near 2^+-900 and a growing mode).
 """
@@ -67,6 +68,10 @@ CASES = [
     ("tiny", ci.Problem(0.5, 0.5, 0.6, 1.0, 3, 1, 1, ci.BDF2, ci.FAST, 2, 2, 3)),
     ("bdf2_ns32", ci.Problem(0.45, 0.55, 0.35, 1.0, 400, 2, 33, ci.BDF2, ci.FAST, 20, 40, 32)),
     ("m0_coupled", ci.Problem(0.3, 0.8, 0.0, 1.0, 400, 2, 47, ci.BDF2, ci.FAST, 16, 48, 15)),
+    # more than 80 points: the fastest-decaying slots in shared memory
+    ("be2d_np128", ci.Problem(0.2, 0.8, 0.45, 1.0, 700, 2, 63, ci.BE, ci.FAST, 128, 0, 2)),
+    ("bdf2_2d_np112", ci.Problem(0.35, 0.55, 0.6, 1.0, 500, 2, 63, ci.BDF2, ci.FAST, 16, 96, 17)),
+    ("bdf2_1d_np90_ns20", ci.Problem(0.6, 0.25, 0.35, 1.0, 600, 1, 255, ci.BDF2, ci.FAST, 30, 60, 20)),
 ]
 
 
