@@ -767,6 +767,7 @@ def batch_leg(fc, torch, dev, K, flush):
     replay_same = bool(np.array_equal(gN.cpu().numpy(), batch))
     del graph
     del ws
+    df64 = batch_df64(fc, torch, dev, K, flush, probs, g0, batch, ms_fp64=statistics.mean(times))
     # the same instances, one fp2s_solve each (same arithmetic per mode)
     singles, t_single, o = [], 0.0, 0
     for cp, f in zip(cps, fields):
@@ -834,7 +835,49 @@ def batch_leg(fc, torch, dev, K, flush):
                      "algorithmic_flops_per_launch": flops,
                      "flops_definition": "sum over instances of (4 np + 2 (L - 1)) x DOF x N"},
         "cpu_baseline": cpu,
+        "df64": df64,
     }
+
+
+def batch_df64(fc, torch, dev, K, flush, probs, g0, batch_fp64, ms_fp64):
+    """The same 256 instances as one double-float batch (CQ_DF64 for every instance): time per
+    batch and the largest difference from the FP64 batch per instance, relative to the instance's
+    largest value."""
+    import numpy as np
+    cps = [fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
+                      prec=fc.CQ_DF64, flags=fc.FP2S_ASYNC) for p in probs]
+    ws = fc.workspace(fc.fp2s_batch_plan(cps), dev)
+    plan = fc.fp2s_batch_plan(cps, ws)
+    gN = torch.empty_like(g0)
+    fc.fp2s_solve_batched(plan, g0, gN, ws)                       # warm-up
+    times, kern = [], []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fc.fp2s_solve_batched(plan, g0, gN, ws)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kern.append(fc.cq_timing_last())
+    status = fc.strerror(fc.fp2s_batch_status(plan, ws))
+    got = gN.cpu().numpy()
+    del ws
+    worst, o = 0.0, 0
+    for p in probs:
+        n = 2 * p.M ** p.dim
+        a, b = got[o:o + n], batch_fp64[o:o + n]
+        o += n
+        sc = np.max(np.abs(b))
+        if sc > 0:
+            worst = max(worst, float(np.max(np.abs(a - b)) / sc))
+    ms = statistics.mean(times)
+    dof_steps = sum(2 * p.M ** p.dim * p.N for p in probs)
+    return {"value": dof_steps / (ms * 1e-3), "unit": UNIT, "ms_per_batch": ms, "kernel_ms": statistics.mean(kern),
+            "speedup_vs_fp64_batch": ms_fp64 / ms, "status": status,
+            "max_abs_diff_vs_fp64_batch_rel_to_instance_max": worst,
+            "kernel": "k_b_df (double-float node states and sums, FP64 step; 64-mode units)"}
 
 
 # The paper's own CPU times (Tables 1 and 5; hardware not stated): context only.
@@ -1340,6 +1383,8 @@ def summary(out):
         "tensor_core_history": {"bf16x3_frac": g(prec, "tensor_core_direct_history", "roofline", "frac"),
                                 "tf32x3_frac": g(prec, "tensor_core_direct_history_tf32x3", "roofline", "frac")},
         "batch": {"value": g(out, "batch", "value"), "graph_replay_value": g(out, "batch", "graph_replay", "value"),
+                  "df64_value": g(out, "batch", "df64", "value"),
+                  "df64_max_diff_vs_fp64": g(out, "batch", "df64", "max_abs_diff_vs_fp64_batch_rel_to_instance_max"),
                   "launch_shape": g(out, "batch", "launch_shape")},
         "gradient": {"ms": g(out, "gradient", "ms_per_gradient"),
                      "rel_err_vs_central_differences": g(out, "gradient", "rel_err_vs_central_differences"),

@@ -310,20 +310,24 @@ int fp2s_vjp(const fp2s_problem_t *p, const double *G0_dev, const double *dGN_de
 typedef struct {
     int32_t n_inst, n_units;        /* problems; work units of 16 * warps_per_block modes */
     int32_t warps_per_block;        /* block width of the persistent kernel (autotuned or default) */
-    int32_t max_np, max_L, max_N, max_M, flags;   /* flags bit 0: launch shape chosen by the autotuner */
+    int32_t max_np, max_L, max_N, max_M, flags;   /* flags bit 0: launch shape chosen by the autotuner;
+                                                     bit 1: double-float batch (CQ_DF64) */
     int32_t ctas_per_sm;            /* resident CTAs per SM of the persistent launch (0: as many as fit) */
     int32_t tuned_candidates;       /* launch shapes the autotuner timed (0 without tuning) */
-    int32_t node_unroll;            /* partial sums of the node loop: 2, 4 or 8 (autotuned or 4) */
+    int32_t node_unroll;            /* partial sums of the node loop: 2, 4 or 8 (autotuned or 4; 0 for CQ_DF64) */
     int64_t max_modes, field_elems; /* field_elems: doubles of a packed [instance][2][M^dim] field */
     int64_t ws_bytes;
     int64_t off[16];                /* workspace regions (internal) */
 } fp2s_batch_t;
 
 /* Plans and prepares a batch of n problems (each with form == CQ_FAST,
- * prec == CQ_F64, dim 1 or 2; any mix of dim, M, N, scheme, alpha, m and fast sizes):
- * builds every instance's tables in the workspace with batched kernels and
- * orders the work units by decreasing cost. 1 <= n <= 65535 (more: CQ_EUNSUPPORTED;
- * split such a set into several batches). tune != 0 autotunes the launch shape:
+ * dim 1 or 2; any mix of dim, M, N, scheme, alpha, m and fast sizes; one precision
+ * for the whole batch: CQ_F64, or CQ_DF64 with np1 + np2 <= 128, else
+ * CQ_EUNSUPPORTED): builds every instance's tables in the workspace with batched
+ * kernels and orders the work units by decreasing cost. 1 <= n <= 65535 (more:
+ * CQ_EUNSUPPORTED; split such a set into several batches). A CQ_DF64 batch runs the
+ * double-float kernel of fp2s_solve over units of 64 modes (flags bit 1 set,
+ * warps_per_block 4, no tuning). For CQ_F64, tune != 0 autotunes the launch shape:
  * every block width whose shared memory fits (2..16 warps), each with all and
  * with half of the CTAs per SM that fit and with 2, 4 or 8 partial sums in the
  * node loop, is timed on a shortened run (96 steps, median of three) and the

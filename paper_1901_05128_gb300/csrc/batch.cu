@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fastdf.cuh"
 #include "fp2s_core.cuh"
 #include "table_kernels.cuh"
 
@@ -44,16 +45,17 @@ struct BatchLayout {
     InstDesc *desc;
     Unit *units;
     double *W, *tab, *scr, *lam, *S, *modal;
+    float *dftab;                        // double-float batches: [instance][kDfTabFloats]
     size_t bytes;
 };
 
 struct BatchSizes {
-    int64_t w = 0, tab = 0, scr = 0, lam = 0, S = 0, modal = 0, field = 0;
+    int64_t w = 0, tab = 0, scr = 0, lam = 0, S = 0, modal = 0, field = 0, dftab = 0;
     int maxnp = 1, maxL = 2, maxM = 1;
     int64_t maxN = 1, max_nmodes = 1;
 };
 
-enum { R_STATUS, R_COUNTER, R_DESC, R_UNITS, R_W, R_TAB, R_SCR, R_LAM, R_S, R_MODAL, R_END };
+enum { R_STATUS, R_COUNTER, R_DESC, R_UNITS, R_W, R_TAB, R_SCR, R_LAM, R_S, R_MODAL, R_DFTAB, R_END };
 
 static BatchLayout batch_layout(void *ws, int n_inst, int64_t n_units, const BatchSizes &z, int64_t *off) {
     Carve cv(ws);
@@ -79,6 +81,8 @@ static BatchLayout batch_layout(void *ws, int n_inst, int64_t n_units, const Bat
     l.S = cv.take<double>(z.S);
     mark(R_MODAL);
     l.modal = cv.take<double>(z.modal);
+    mark(R_DFTAB);
+    l.dftab = cv.take<float>(z.dftab);
     l.bytes = cv.bytes();
     if (off) off[R_END] = (int64_t)l.bytes;
     return l;
@@ -97,6 +101,7 @@ static BatchLayout layout_from_plan(const fp2s_batch_t *plan, void *ws) {
     l.lam = reinterpret_cast<double *>(b + plan->off[R_LAM]);
     l.S = reinterpret_cast<double *>(b + plan->off[R_S]);
     l.modal = reinterpret_cast<double *>(b + plan->off[R_MODAL]);
+    l.dftab = reinterpret_cast<float *>(b + plan->off[R_DFTAB]);
     l.bytes = (size_t)plan->off[R_END];
     return l;
 }
@@ -332,6 +337,90 @@ __global__ void __launch_bounds__(1024) k_b_fast(const InstDesc *__restrict__ D,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float batches (every instance CQ_DF64): the per-lane solve of the single-problem
+// double-float kernel (fastdf.cuh) over work units of 64 modes, taken from the same atomic
+// counter. Tables per instance in double-float (ranked nodes, u form for the slowest quarter)
+// are built once by the plan; a unit copies its instance's table into shared memory and
+// dispatches on its node class and scheme.
+// ---------------------------------------------------------------------------
+__global__ void k_b_df_tables(const InstDesc *__restrict__ D, const double *__restrict__ W,
+                              const double *__restrict__ tab, float *__restrict__ dftab) {
+    const InstDesc d = D[blockIdx.x];
+    const double *t1 = tab + d.o_tab, *t2 = t1 + 2 * d.np, *d1 = W + d.o_w, *d2 = d1 + d.N + 1;
+    df_tables_fill(df_np_class(d.np), d.np, d.L, d.N, t1, t2, d1, d2, dftab + (size_t)blockIdx.x * kDfTabFloats,
+                   threadIdx.x, blockDim.x);
+}
+
+template <int WL>
+__global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
+    k_b_df(const InstDesc *__restrict__ D, const Unit *__restrict__ U, int n_units, int *__restrict__ counter,
+           int maxL, int maxKS, int64_t step_cap, const double *__restrict__ W, const float *__restrict__ dftab,
+           const double *__restrict__ lamp, double *__restrict__ modal, int *__restrict__ status) {
+    extern __shared__ __align__(16) float smd[];
+    __shared__ int s_unit;
+    const int T = blockDim.x, tid = threadIdx.x;
+    float2 *R = reinterpret_cast<float2 *>(smd + kDfTabFloats);      // [maxL][T]
+    float2 *Ys = R + (size_t)maxL * T;                                // [maxKS][T]
+    const int modes_per_unit = (T >> 5) * kFastModesPerWarp;
+    for (;;) {
+        if (tid == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= n_units) break;
+        const Unit un = U[u];
+        const InstDesc d = D[un.inst];
+        const int NP = df_np_class(d.np);
+        const float *src = dftab + (size_t)un.inst * kDfTabFloats;
+        for (int e = tid; e < df_table_floats(NP); e += T) smd[e] = src[e];
+        for (int j = 0; j < d.L; ++j) R[(size_t)j * T + tid] = make_float2(0.0f, 0.0f);
+        for (int j = 0; j < df_smem_slots(NP); ++j) Ys[(size_t)j * T + tid] = make_float2(0.0f, 0.0f);
+        __syncthreads();
+        Fp2sParams P;
+        P.a = d.a;
+        P.tau = d.tau;
+        P.inv_tau = d.inv_tau;
+        P.N = d.N < step_cap ? d.N : step_cap;
+        P.nmodes = d.nmodes;
+        P.scheme = d.scheme;
+        P.form = CQ_FAST;
+        P.np = d.np;
+        P.L = d.L;
+        P.prec = CQ_DF64;
+        const double *lam = lamp + d.o_lam, *d1 = W + d.o_w, *d2 = d1 + d.N + 1;
+        const double *g0 = modal + d.o_modal;
+        double *gN = modal + d.o_modal + 2 * d.nmodes;
+        const int64_t mode_raw = (int64_t)un.first_mode + (tid >> 5) * kFastModesPerWarp + (tid & 15);
+        const int64_t mode_end = min(d.nmodes, (int64_t)un.first_mode + modes_per_unit);
+        const float4 *tb = reinterpret_cast<const float4 *>(smd);
+        const float2 *wd = reinterpret_cast<const float2 *>(smd + 8 * NP);
+#define CQ_B_DF(NPV)                                                                                            \
+    case NPV:                                                                                                   \
+        if (d.scheme == CQ_BE)                                                                                  \
+            df_solve_lane<NPV, true, 2>(P, lam, g0, gN, status, d1, d2, tb, wd, R, Ys, T, tid, mode_raw, mode_end); \
+        else                                                                                                    \
+            df_solve_lane<NPV, false, WL>(P, lam, g0, gN, status, d1, d2, tb, wd, R, Ys, T, tid, mode_raw, mode_end); \
+        break;
+        switch (NP) {
+            CQ_B_DF(16)
+            CQ_B_DF(32)
+            CQ_B_DF(48)
+            CQ_B_DF(64)
+            CQ_B_DF(80)
+            CQ_B_DF(96)
+            CQ_B_DF(112)
+            CQ_B_DF(128)
+            default: break;
+        }
+#undef CQ_B_DF
+        __syncthreads();
+    }
+}
+
+static size_t bdf_smem(int maxL, int maxKS) {
+    return (size_t)kDfTabFloats * sizeof(float) + (size_t)(maxL + maxKS) * kDfThreads * sizeof(float2);
+}
+
 static size_t bfast_smem(int maxnp, int maxL, int T) {
     return ((size_t)4 * maxnp + 2 * kMaxNs + (size_t)(maxnp + maxL) * T) * sizeof(double);
 }
@@ -343,11 +432,12 @@ static int validate(const fp2s_problem_t &p, InstDesc &d) {
     if (p.dim != 1 && p.dim != 2) return CQ_EINVAL;
     if (p.M < 1 || p.M > (p.dim == 1 ? (1 << 16) : 4096)) return CQ_EINVAL;
     if (p.scheme != CQ_BE && p.scheme != CQ_BDF2) return CQ_EINVAL;
-    if (p.form != CQ_FAST || p.prec != CQ_F64) return CQ_EUNSUPPORTED;
+    if (p.form != CQ_FAST || (p.prec != CQ_F64 && p.prec != CQ_DF64)) return CQ_EUNSUPPORTED;
     const int np1 = p.fast.np1, np2 = (p.scheme == CQ_BE) ? 0 : p.fast.np2;
     const int L = (p.scheme == CQ_BE) ? 2 : p.fast.ns;
     if (np1 < 1 || np2 < 0 || np1 + np2 > kMaxNp) return CQ_EINVAL;
     if (p.scheme == CQ_BDF2 && (np2 < 1 || L < 3 || L > kMaxNs)) return CQ_EINVAL;
+    if (p.prec == CQ_DF64 && df_np_class(np1 + np2) == 0) return CQ_EUNSUPPORTED;
     d = InstDesc{};
     d.a = (1.0 - p.m) / (2.0 * p.m - 1.0);
     d.tau = p.T / (double)p.N;
@@ -406,8 +496,27 @@ static int occupancy(int max_np, int max_L, int wb, int node_unroll) {
     return per_sm;
 }
 
+// Double-float batch: one persistent launch with every CTA that fits per SM.
+static int launch_df_batch(const fp2s_batch_t *plan, const BatchLayout &l, int64_t step_cap, cudaStream_t s) {
+    const int maxKS = df_smem_slots(df_np_class(plan->max_np));
+    const size_t smem = bdf_smem(plan->max_L, maxKS);
+    auto kern = plan->max_L <= 17 ? k_b_df<17> : k_b_df<kMaxNs>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return CQ_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDfThreads, smem) != cudaSuccess || per_sm < 1)
+        return CQ_EUNSUPPORTED;
+    const int blocks = (int)std::min<int64_t>((int64_t)num_sms_b() * per_sm, plan->n_units);
+    int st = cuda_status(cudaMemsetAsync(l.counter, 0, sizeof(int), s));
+    if (st) return st;
+    kern<<<blocks, kDfThreads, smem, s>>>(l.desc, l.units, plan->n_units, l.counter, plan->max_L, maxKS, step_cap,
+                                          l.W, l.dftab, l.lam, l.modal, l.status);
+    return launched();
+}
+
 // One persistent launch: plan->ctas_per_sm CTAs per SM (0: as many as fit), never more than units.
 static int launch_main(const fp2s_batch_t *plan, const BatchLayout &l, int64_t step_cap, cudaStream_t s) {
+    if (plan->flags & 2) return launch_df_batch(plan, l, step_cap, s);
     const int T = 32 * plan->warps_per_block;
     const size_t smem = bfast_smem(plan->max_np, plan->max_L, T);
     const int fit = occupancy(plan->max_np, plan->max_L, plan->warps_per_block, plan->node_unroll);
@@ -475,7 +584,9 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
     for (int i = 0; i < n; ++i) {
         const int st = validate(probs[i], descs[i]);
         if (st) return st;
+        if (probs[i].prec != probs[0].prec) return CQ_EUNSUPPORTED;      // one precision per batch
     }
+    const bool df = probs[0].prec == CQ_DF64;
     // offsets
     int64_t ow = 0, otab = 0, oscr = 0, olam = 0, oS = 0, omod = 0, ofield = 0;
     for (InstDesc &d : descs) {
@@ -494,11 +605,15 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
         d.o_field = ofield;
         ofield += 2 * d.nmodes;
     }
-    const BatchSizes z = sizes_of(descs);
-    // block widths that fit shared memory; the largest is the default
+    BatchSizes z = sizes_of(descs);
+    if (df) z.dftab = (int64_t)n * kDfTabFloats;
+    // block widths that fit shared memory; the largest is the default (double-float batches:
+    // the fixed width of their kernel)
     std::vector<int> cands;
-    for (int wb = 16; wb >= 1; --wb)
-        if (bfast_smem(z.maxnp, z.maxL, 32 * wb) <= 227 * 1024) cands.push_back(wb);
+    if (df) cands.push_back(kDfThreads / 32);
+    else
+        for (int wb = 16; wb >= 1; --wb)
+            if (bfast_smem(z.maxnp, z.maxL, 32 * wb) <= 227 * 1024) cands.push_back(wb);
     if (cands.empty()) return CQ_EUNSUPPORTED;
     // the unit list is largest for the smallest width: size the workspace for it
     std::vector<Unit> units_max;
@@ -516,7 +631,7 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
     plan->max_modes = z.max_nmodes;
     plan->field_elems = z.field;
     plan->ws_bytes = (int64_t)l.bytes;
-    plan->flags = 0;
+    plan->flags = df ? 2 : 0;
     for (int r = 0; r <= R_END; ++r) plan->off[r] = off[r];
     int st;
     if ((st = cuda_status(cudaMemcpyAsync(l.desc, descs.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, s))))
@@ -533,13 +648,19 @@ extern "C" int fp2s_batch_plan(const fp2s_problem_t *probs, int32_t n, int32_t t
     const int64_t spec = std::max<int64_t>(z.max_nmodes, (int64_t)z.maxM * z.maxM);
     k_b_spectrum<<<dim3((unsigned)((spec + 255) / 256), n), 256, 0, s>>>(l.desc, l.lam, l.S);
     if ((st = launched(4))) return st;
+    if (df) {
+        k_b_df_tables<<<n, 256, 0, s>>>(l.desc, l.W, l.tab, l.dftab);
+        if ((st = launched())) return st;
+    }
     // launch shape: the widest block with full occupancy and 4 partial sums by default, or the
     // fastest candidate (block width x resident CTAs per SM x node-loop width) on a shortened
     // run, median of three timings each
     int best = cands.front(), best_cps = 0, best_nu = 4;
     plan->tuned_candidates = 0;
     plan->node_unroll = 4;
-    if (tune) {
+    if (df) {
+        best_nu = 0;                         // the double-float kernel has no tuned knob
+    } else if (tune) {
         EventPair ev;
         if (!ev.ok()) return CQ_ECUDA;
         float best_ms = 1e30f;

@@ -1,6 +1,7 @@
 """Batched persistent solve (fp2s_batch_plan / fp2s_solve_batched) against single
 solves of the same problems and against the oracle (``-m gpu``). Also: autotuned block
-width, repeated solves, and capture of the batched solve in a CUDA graph."""
+width, repeated solves, capture of the batched solve in a CUDA graph, and batches in the
+double-float form (CQ_DF64) at the FP64 bar."""
 import numpy as np
 import pytest
 
@@ -31,8 +32,9 @@ MIXED = [ci.Problem(0.3, 0.7, 0.4, 1.0, 300, 1, 63, ci.BE, ci.FAST, 64, 0, 2),
          ci.Problem(0.45, 0.65, 0.35, 1.0, 1, 2, 3, ci.BE, ci.FAST, 4, 0, 2)]
 
 
-def _cp(fc, p):
-    return fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns)
+def _cp(fc, p, prec=0):
+    return fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, p.form, p.np1, p.np2, p.ns,
+                      prec=prec)
 
 
 def _single(fc, p, G0):
@@ -127,4 +129,42 @@ def test_batch_rejects_invalid(fc):
     bad = [_cp(fc, MIXED[0]), fc.problem(0.3, 0.7, 0.4, 1.0, 64, 1, 15, fc.CQ_BE, fc.CQ_DIRECT)]
     with pytest.raises(fc.CQError) as e:
         fc.fp2s_batch_plan(bad)
+    assert e.value.status == fc.CQ_EUNSUPPORTED
+
+
+# node classes 16 .. 128 (above 80 the fastest slots in shared memory), both schemes, windows
+# up to 17, and instances smaller than one 64-mode unit
+DF_BATCH = MIXED + [ci.Problem(0.2, 0.8, 0.45, 1.0, 400, 2, 31, ci.BE, ci.FAST, 128, 0, 2),
+                    ci.Problem(0.35, 0.55, 0.6, 1.0, 300, 1, 127, ci.BDF2, ci.FAST, 16, 96, 17),
+                    ci.Problem(0.6, 0.25, 0.35, 1.0, 350, 2, 23, ci.BDF2, ci.FAST, 30, 60, 12)]
+
+
+def test_df64_batch_matches_fp64_batch_and_oracle(fc):
+    fields = [ci.g0_uniform(p.M, p.dim, 300 + i) for i, p in enumerate(DF_BATCH)]
+    g0 = _pack(fields)
+    res = {}
+    for prec in (fc.CQ_F64, fc.CQ_DF64):
+        cps = [_cp(fc, p, prec) for p in DF_BATCH]
+        ws = fc.workspace(fc.fp2s_batch_plan(cps), "cuda")
+        plan = fc.fp2s_batch_plan(cps, ws, tune=False)
+        if prec == fc.CQ_DF64:
+            assert plan.flags & 2 and plan.warps_per_block == 4 and plan.node_unroll == 0
+        gN = torch.empty_like(g0)
+        fc.fp2s_solve_batched(plan, g0, gN, ws)
+        assert fc.fp2s_batch_status(plan, ws) == fc.CQ_OK
+        res[prec] = _unpack(gN, DF_BATCH)
+    for i, (p, f) in enumerate(zip(DF_BATCH, fields)):
+        a, b = res[fc.CQ_DF64][i], res[fc.CQ_F64][i]
+        for s_ in range(2):
+            assert np.linalg.norm(a[s_] - b[s_]) <= 1e-12 * np.linalg.norm(b[s_]) + 1e-300, (i, s_)
+        if i in (0, 4, 8, 9, 10):
+            ref = OS.solve(p, f)
+            for s_ in range(2):
+                assert np.linalg.norm(a[s_] - ref[s_]) <= 1e-12 * np.linalg.norm(ref[s_]), (i, s_)
+
+
+def test_batch_one_precision_per_plan(fc):
+    mixed = [_cp(fc, MIXED[0]), _cp(fc, MIXED[1], fc.CQ_DF64)]
+    with pytest.raises(fc.CQError) as e:
+        fc.fp2s_batch_plan(mixed)
     assert e.value.status == fc.CQ_EUNSUPPORTED
