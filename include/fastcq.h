@@ -61,9 +61,10 @@ extern "C" {
                         * BF16 hi + lo, hi*hi + hi*lo + lo*hi accumulated in FP32 */
 #define CQ_TF32X3  3   /* the same with TF32 hi + lo (11 significant bits each; half the BF16
                         * tensor rate, twice the operand bytes, ~2^6 times smaller split error) */
-#define CQ_DF64    4   /* FP64-class form of the fast solve: history state, tables and sums as
-                        * double-float pairs (hi + lo of two FP32 numbers) on the FP32 pipe, the
-                        * 2x2 step in FP64 (np1 + np2 <= 128) */
+#define CQ_DF64    4   /* FP64-class form of the solves: history state (fast form) or stored levels
+                        * (direct form), weights, tables and sums as double-float pairs (hi + lo of
+                        * two FP32 numbers) on the FP32 pipe, the 2x2 step in FP64
+                        * (fast: np1 + np2 <= 128) */
 
 /* Fast-form sizes. BE (Eqs. 3.6-3.10): np1 = Np Gauss-Jacobi points, np2
  * ignored, ns ignored (the exact window of BE is d_1 alone).
@@ -216,7 +217,7 @@ typedef struct {
     int32_t form;          /* CQ_DIRECT or CQ_FAST */
     cq_fast_cfg_t fast;    /* used when form == CQ_FAST */
     int32_t prec;          /* CQ_F64; in fp2s_solve also CQ_F32 with form == CQ_FAST (np1 + np2 <= 128),
-                              CQ_DF64 with form == CQ_FAST (np1 + np2 <= 128)
+                              CQ_DF64 with either form (fast: np1 + np2 <= 128)
                               and CQ_BF16X3 or CQ_TF32X3 with form == CQ_DIRECT (mixed-precision
                               direct solve); fp2s_gradient / fp2s_vjp take CQ_F64, CQ_BF16X3 and
                               CQ_TF32X3 with form == CQ_DIRECT */

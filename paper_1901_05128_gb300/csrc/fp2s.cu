@@ -31,6 +31,7 @@ struct Fp2sLayout {
     float *hdf;                   // FP32 fast form: 0.5*d_i of both states as double-float, [4][N+1]
     float *ftab;                  // FP32 fast form: node tables in the fused kernel's order (k_f32_tables)
     double *hist;                 // direct: (N+1) x 2 x nmodes
+    float2 *wz1, *wz2, *hist2;    // direct, CQ_DF64: padded double-float weights; levels [N+1][nmodes][2]
     double *Y, *ring, *glast;     // step API, fast: 2 x np x nm, 2 x L x nm; both: 2 levels x 2 x nm
     void *mixed;                  // direct, CQ_BF16X3 / CQ_TF32X3: region of the mixed-precision solve
     double *wscr;                 // N > kMaxWeights: scratch of the weight builder
@@ -64,6 +65,11 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.gN = cv.take<double>(2 * nm);
     if (P.form == CQ_DIRECT && P.prec == CQ_F64)
         l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
+    if (P.form == CQ_DIRECT && P.prec == CQ_DF64) {
+        l.wz1 = cv.take<float2>(P.N + 2 * kDirDfBT + 1);
+        l.wz2 = cv.take<float2>(P.N + 2 * kDirDfBT + 1);
+        l.hist2 = cv.take<float2>((size_t)(P.N + 1) * 2 * nm);
+    }
     if (P.prec != CQ_F64 && P.prec != CQ_DF64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
     if (P.form == CQ_FAST && P.prec == CQ_F32) l.ftab = cv.take<float>(kF32TabFloats);
     if (P.form == CQ_FAST && P.prec == CQ_DF64) l.ftab = cv.take<float>(kDfTabFloats);
@@ -92,7 +98,7 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
     if (p->M < 1 || p->M > (p->dim == 1 ? (1 << 16) : p->dim == 2 ? 4096 : 1024)) return CQ_EINVAL;
     if (p->scheme != CQ_BE && p->scheme != CQ_BDF2) return CQ_EINVAL;
     if (p->form != CQ_DIRECT && p->form != CQ_FAST) return CQ_EINVAL;
-    if (p->prec != CQ_F64 && !((p->prec == CQ_F32 || p->prec == CQ_DF64) && p->form == CQ_FAST) &&
+    if (p->prec != CQ_F64 && p->prec != CQ_DF64 && !(p->prec == CQ_F32 && p->form == CQ_FAST) &&
         !((p->prec == CQ_BF16X3 || p->prec == CQ_TF32X3) && p->form == CQ_DIRECT))
         return CQ_EUNSUPPORTED;
     P.prec = p->prec;
@@ -1114,7 +1120,9 @@ static int setup_tables(const fp2s_problem_t *p, const Fp2sParams &P, int np1, i
         k_half_weights_df<<<(unsigned)((P.N + 256) / 256), 256, 0, s>>>(l.d1, l.d2, P.N, l.hdf);
         if ((st = launched())) return st;
     }
-    if (P.form == CQ_DIRECT && P.prec == CQ_F64) {
+    if (P.form == CQ_DIRECT && P.prec == CQ_DF64) {
+        if ((st = direct_df_tables(P, l.d1, l.d2, l.wz1, l.wz2, s))) return st;
+    } else if (P.form == CQ_DIRECT && P.prec == CQ_F64) {
         const unsigned g = (unsigned)((P.N + 2 * kDirBT + 256) / 256);
         k_pad<<<g, 256, 0, s>>>(l.d1, P.N, kDirBT, l.dz1);
         k_pad<<<g, 256, 0, s>>>(l.d2, P.N, kDirBT, l.dz2);
@@ -1149,6 +1157,8 @@ static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s
     if (P.form == CQ_FAST && P.prec == CQ_F32) return fp2s_fast_f32(P, l, s);
     if (P.form == CQ_FAST && P.prec == CQ_DF64)
         return fast_df_solve(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.ftab, s);
+    if (P.form == CQ_DIRECT && P.prec == CQ_DF64)
+        return direct_df_solve(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.wz1, l.wz2, l.hist2, s);
     if (P.form == CQ_FAST && fast_use_split(P.nmodes)) return launch_fast_split(P, l, s);
     if (P.form == CQ_FAST) {
         const int T = fast_block_threads(P.np, P.L, P.nmodes);

@@ -285,6 +285,16 @@ int fast_df_tables(const Fp2sParams &P, const double *tab1, const double *tab2, 
 int fast_df_solve(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
                   const double *d1, const double *d2, const float *dftab, cudaStream_t s);
 
+// Direct solve in double-float (CQ_DIRECT with CQ_DF64, directdf.cu): time block, the padded
+// double-float weights (wz: n + 2 kDirDfBT + 1 pairs per state) and the solve over all N steps
+// (hist: (N + 1) x 2 x nmodes pairs).
+constexpr int kDirDfBT = 8;
+int direct_df_tables(const Fp2sParams &P, const double *d1, const double *d2, float2 *wz1, float2 *wz2,
+                     cudaStream_t s);
+int direct_df_solve(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
+                    const double *d1, const double *d2, const float2 *wz1, const float2 *wz2, float2 *hist,
+                    cudaStream_t s);
+
 // Mixed-precision direct solve (mixed.cu): workspace bytes of its own region, and
 // the run over all N steps (weights, spectrum and the modal G^0 already in place;
 // hdf: d_i / 2 of both states as double-float, [4][N + 1]).

@@ -1,4 +1,4 @@
-"""GPU parity of the double-float fast solve (precision form CQ_DF64, ``-m gpu``).
+"""GPU parity of the double-float solves (precision form CQ_DF64, fast and direct, ``-m gpu``).
 
 The fast history's node states, tables and sums are pairs of FP32 numbers (about 48
 significant bits) on the FP32 pipe, the 2x2 step is FP64. It is held to the FP64 bar
@@ -132,3 +132,49 @@ def test_df64_growing_mode_rescaled(fc):
         assert err <= 4.0 * kappa
     calm = np.arange(8, p.M)
     _assert_close(got[:, calm], ref[:, calm], "decaying modes")
+
+
+DIRECT_CASES = [
+    ("be1d_m63", ci.Problem(0.3, 0.7, 0.4, 1.0, 1024, 1, 63, ci.BE, ci.DIRECT)),
+    ("bdf2_1d", ci.Problem(0.4, 0.6, 0.3, 1.0, 700, 1, 45, ci.BDF2, ci.DIRECT)),
+    ("bdf2_2d_m0", ci.Problem(0.2, 0.8, 0.0, 1.0, 257, 2, 19, ci.BDF2, ci.DIRECT)),
+    ("be2d_ragged_N", ci.Problem(0.25, 0.55, 0.7, 0.5, 333, 2, 41, ci.BE, ci.DIRECT)),
+    ("be3d", ci.Problem(0.35, 0.7, 0.4, 1.0, 120, 3, 9, ci.BE, ci.DIRECT)),
+    ("tiny", ci.Problem(0.5, 0.5, 0.6, 1.0, 3, 1, 1, ci.BDF2, ci.DIRECT)),
+    ("one_step", ci.Problem(0.5, 0.5, 0.6, 1.0, 1, 2, 3, ci.BE, ci.DIRECT)),
+    ("bdf2_2d_many", ci.Problem(0.45, 0.65, 0.35, 1.0, 600, 2, 127, ci.BDF2, ci.DIRECT)),
+]
+
+
+@pytest.mark.parametrize("name,p", DIRECT_CASES, ids=[c[0] for c in DIRECT_CASES])
+def test_df64_direct_matches_oracle_and_fp64(fc, name, p):
+    """The direct scheme with double-float weights, levels and history sums (FP64 step)."""
+    G0 = ci.g0_uniform(p.M, p.dim, 81)
+    got, st = _solve(fc, p, G0, fc.CQ_DF64)
+    assert st == fc.CQ_OK
+    _assert_close(got, OS.solve(p, G0), name + " direct vs oracle")
+    f64, st64 = _solve(fc, p, G0, fc.CQ_F64)
+    assert st64 == fc.CQ_OK
+    _assert_close(got, f64, name + " direct vs FP64 kernel")
+
+
+def test_df64_direct_full_size_decaying_modes(fc):
+    """The 2D 255x255 BDF2 workload (N = 4096, m = 0.49) in the direct double-float form over
+    the modes past the second row of the spectrum (the three growing modes, whose growth of
+    up to e^1096 leaves the FP32 exponent range, lie before it), in the sine basis against
+    the oracle's FP64 direct scheme on seeded sampled modes: relative L2 per state <= 1e-12."""
+    p, G0 = ci.workload("bdf2_2d_m255")
+    p = p.replace(form=ci.DIRECT)
+    nm = p.M ** p.dim
+    lo = p.M + 1
+    g0m = OSP.to_modal(G0, p.M, p.dim)
+    cp = _cp(fc, p, fc.CQ_DF64)
+    g0 = torch.tensor(np.ascontiguousarray(g0m[:, lo:]), dtype=torch.float64, device="cuda")
+    gN = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_solve_modes(cp, lo, nm, g0, gN, None), "cuda")
+    assert fc.fp2s_solve_modes(cp, lo, nm, g0, gN, ws, check=False) == fc.CQ_OK
+    got = gN.cpu().numpy()
+    sample = np.unique(np.concatenate([[0, 1, 2], ci.sample_indices(nm - lo, 40, ci.SEED_BASE + 14)]))
+    lam = OSP.mode_eigenvalues(p.M, p.dim)[lo + sample]
+    ref = OS.solve_modal(p, lam, g0m[:, lo + sample])[p.N]
+    _assert_close(got[:, sample], ref, "direct df64 full size")
