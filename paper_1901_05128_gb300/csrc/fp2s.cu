@@ -68,7 +68,7 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     if (P.form == CQ_DIRECT && P.prec == CQ_DF64) {
         l.wz1 = cv.take<float2>(P.N + 2 * kDirDfBT + 1);
         l.wz2 = cv.take<float2>(P.N + 2 * kDirDfBT + 1);
-        l.hist2 = cv.take<float2>((size_t)(P.N + 1) * 2 * nm);
+        l.hist2 = cv.take<float2>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
     }
     if (P.prec != CQ_F64 && P.prec != CQ_DF64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
     if (P.form == CQ_FAST && P.prec == CQ_F32) l.ftab = cv.take<float>(kF32TabFloats);
@@ -1571,6 +1571,7 @@ __global__ void __launch_bounds__(32, 12) k_adjoint_direct(
 
 struct GradLayout {
     double *tgt, *mu, *gx0, *q1, *q2, *qz1, *qz2, *dza1, *dza2, *acc;
+    float2 *wa1, *wa2, *qa1, *qa2;       // CQ_DF64: d and d' padded for the double-float adjoint
     double *cg0, *ctgt, *cgx0, *cgN;     // compact [2][ns] copies of a slice (sliced runs only)
     size_t bytes;
 };
@@ -1590,7 +1591,15 @@ static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void 
     g.qz2 = cv.take<double>(P.N + 2 * kAdjBT + 1);
     g.dza1 = cv.take<double>(P.N + 2 * kAdjBT + 1);
     g.dza2 = cv.take<double>(P.N + 2 * kAdjBT + 1);
-    g.mu = cv.take<double>((size_t)(P.N + 1) * 2 * ns);
+    const bool df = P.prec == CQ_DF64;
+    if (df) {
+        g.wa1 = cv.take<float2>(P.N + 4 * kAdjDfBT);
+        g.wa2 = cv.take<float2>(P.N + 4 * kAdjDfBT);
+        g.qa1 = cv.take<float2>(P.N + 4 * kAdjDfBT);
+        g.qa2 = cv.take<float2>(P.N + 4 * kAdjDfBT);
+    }
+    // FP64: [N + 1][2][ns] doubles; CQ_DF64: [N + 1 + kAdjDfBT][ns][2] pairs (zero levels past N)
+    g.mu = cv.take<double>((size_t)(P.N + 1 + (df ? kAdjDfBT : 0)) * 2 * ns);
     if (ns < nm) {
         g.cg0 = cv.take<double>(2 * ns);
         g.ctgt = cv.take<double>(2 * ns);
@@ -1759,7 +1768,7 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if (st) return st;
     if (!ws_bytes) return CQ_EINVAL;
     const bool mixed = P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3;
-    if (P.form != CQ_DIRECT || !(P.prec == CQ_F64 || mixed)) return CQ_EUNSUPPORTED;
+    if (P.form != CQ_DIRECT || !(P.prec == CQ_F64 || P.prec == CQ_DF64 || mixed)) return CQ_EUNSUPPORTED;
     if (P.N > 13000) return CQ_EUNSUPPORTED;            // shared-memory bound of the weight derivatives
     if (mixed)
         return gradient_mixed(p, P, np1, np2, G0_dev, Gt_dev, vjp, J_host, dJdG0_dev, dJdalpha_host, ws_dev,
@@ -1785,6 +1794,9 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if ((st = timing_begin(s))) return st;
     if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, gl.tgt, l.tmp, s))) return st;
     if ((st = weight_derivatives(P, p, gl.q1, gl.q2, s))) return st;
+    const bool df = P.prec == CQ_DF64;
+    if (df && (st = direct_df_grad_tables(P.N, l.d1, l.d2, gl.q1, gl.q2, gl.wa1, gl.wa2, gl.qa1, gl.qa2, s)))
+        return st;
     const unsigned pg = (unsigned)((P.N + 2 * kAdjBT + 256) / 256);
     k_pad<<<pg, 256, 0, s>>>(gl.q1, P.N, kAdjBT, gl.qz1);
     k_pad<<<pg, 256, 0, s>>>(gl.q2, P.N, kAdjBT, gl.qz2);
@@ -1810,6 +1822,14 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
             tgt = gl.ctgt;
             gN = gl.cgN;
             gx0 = gl.cgx0;
+        }
+        if (df) {
+            if ((st = direct_df_gradient_slice(Ps, wd, l.lam + m0, g0, gN, l.status, l.d1, l.d2, gl.q1, gl.q2, l.wz1,
+                                               l.wz2, gl.wa1, gl.wa2, gl.qa1, gl.qa2, l.hist2, tgt, vjp,
+                                               reinterpret_cast<float2 *>(gl.mu), gx0, gl.acc, s)))
+                return st;
+            if (ns < nm && (st = copy_slice(gl.gx0 + m0, nm, gl.cgx0, cnt, cnt, s))) return st;
+            continue;
         }
         const unsigned fblocks = (unsigned)((cnt + 31) / 32);
         k_fp2s_direct<kDirBT><<<fblocks, 32, 0, s>>>(Ps, l.lam + m0, g0, gN, l.status, l.d1, l.d2, l.dz1, l.dz2,

@@ -28,12 +28,12 @@ def fc():
     return pkg.load()
 
 
-def _cp(fc, p):
-    return fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, ci.DIRECT)
+def _cp(fc, p, prec=0):
+    return fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, ci.DIRECT, prec=prec)
 
 
-def _grad(fc, p, G0, Gt):
-    cp = _cp(fc, p)
+def _grad(fc, p, G0, Gt, prec=0):
+    cp = _cp(fc, p, prec)
     g0 = torch.tensor(G0, dtype=torch.float64, device="cuda")
     gt = torch.tensor(Gt, dtype=torch.float64, device="cuda")
     dg = torch.empty_like(g0)
@@ -42,8 +42,8 @@ def _grad(fc, p, G0, Gt):
     return J, dg.cpu().numpy(), np.array(da)
 
 
-def _J_gpu(fc, p, G0, Gt):
-    cp = _cp(fc, p)
+def _J_gpu(fc, p, G0, Gt, prec=0):
+    cp = _cp(fc, p, prec)
     g0 = torch.tensor(G0, dtype=torch.float64, device="cuda")
     gN = torch.empty_like(g0)
     ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), "cuda")
@@ -61,21 +61,24 @@ CASES = [ci.Problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, ci.BE, ci.DIRECT),
          ci.Problem(0.6, 0.3, 0.3, 1.0, 1, 1, 3, ci.BE, ci.DIRECT)]
 
 
+@pytest.mark.parametrize("prec", [0, 4], ids=["f64", "df64"])
 @pytest.mark.parametrize("p", CASES)
-def test_gradient_against_oracle_adjoint(fc, p):
+def test_gradient_against_oracle_adjoint(fc, p, prec):
+    """FP64 and double-float (CQ_DF64: double-float histories, FP64 steps) gradients."""
     G0 = ci.g0_uniform(p.M, p.dim, 31)
     Gt = 0.5 * ci.g0_uniform(p.M, p.dim, 32)
-    J, dG0, da = _grad(fc, p, G0, Gt)
+    J, dG0, da = _grad(fc, p, G0, Gt, prec)
     Jr, dG0r, dar = AD.gradient(p, G0, Gt)
     assert abs(J - Jr) <= 1e-12 * abs(Jr)
     assert np.all(np.abs(da - dar) <= 1e-9 * np.abs(dar) + 1e-14 * abs(Jr))
     assert np.max(np.abs(dG0 - dG0r)) <= 1e-10 * np.max(np.abs(dG0r))
 
 
+@pytest.mark.parametrize("prec", [0, 4], ids=["f64", "df64"])
 @pytest.mark.parametrize("scheme", [ci.BE, ci.BDF2])
-def test_gradient_against_finite_differences(fc, scheme):
+def test_gradient_against_finite_differences(fc, scheme, prec):
     """Misfit against a target made by the same scheme with perturbed orders,
-    alpha + (0.05, -0.05), on a 2D grid."""
+    alpha + (0.05, -0.05), on a 2D grid; the finite differences of the FP64 forward solve."""
     p = ci.Problem(0.4, 0.6, 0.4, 1.0, 256, 2, 31, scheme, ci.DIRECT)
     G0 = ci.g0_checkerboard_uniform(p.M, ci.SEED_BASE + 9)
     cp_t = _cp(fc, p.replace(alpha1=0.45, alpha2=0.55))
@@ -84,7 +87,7 @@ def test_gradient_against_finite_differences(fc, scheme):
     ws = fc.workspace(fc.fp2s_solve(cp_t, g0, gt, None), "cuda")
     fc.fp2s_solve(cp_t, g0, gt, ws)
     Gt = gt.cpu().numpy()
-    J, dG0, da = _grad(fc, p, G0, Gt)
+    J, dG0, da = _grad(fc, p, G0, Gt, prec)
     eps = 1e-5
     for s, f in ((0, "alpha1"), (1, "alpha2")):
         v = getattr(p, f)
@@ -100,7 +103,8 @@ def test_gradient_against_finite_differences(fc, scheme):
         assert abs(dG0[s, k] - fd) <= 1e-6 * np.max(np.abs(dG0))
 
 
-def test_gradient_in_mode_slices(fc):
+@pytest.mark.parametrize("prec", [0, 4], ids=["f64", "df64"])
+def test_gradient_in_mode_slices(fc, prec):
     """A workspace too small for all modes: the forward and adjoint sweeps run over slices of
     modes (independent in the sine basis); same per-mode arithmetic, so dJ/dG0 agrees to
     rounding and J, dJ/dalpha differ only in the order of their sums."""
@@ -108,8 +112,8 @@ def test_gradient_in_mode_slices(fc):
     p = ci.Problem(0.35, 0.6, 0.4, 1.0, 300, 2, 31, ci.BDF2, ci.DIRECT)
     G0 = ci.g0_uniform(p.M, p.dim, 41)
     Gt = 0.5 * ci.g0_uniform(p.M, p.dim, 42)
-    J, dG0, da = _grad(fc, p, G0, Gt)
-    cp = _cp(fc, p)
+    J, dG0, da = _grad(fc, p, G0, Gt, prec)
+    cp = _cp(fc, p, prec)
     full = fc.fp2s_gradient(cp, None, None, None, None)
     Jc, dac = C.c_double(0.0), (C.c_double * 2)()
     sz = C.c_size_t(full // 5)
