@@ -618,6 +618,9 @@ def gradient_leg(fc, torch, dev, K, flush):
     dG64 = dg.clone()
     mixed = [mixed_gradient_run(fc, torch, dev, p, g0, gt, prec, name, J, da, dG64, fd, ms, 3, flush)
              for name, prec in (("BF16x3", fc.CQ_BF16X3), ("TF32x3", fc.CQ_TF32X3))]
+    df = mixed_gradient_run(fc, torch, dev, p, g0, gt, fc.CQ_DF64, "DF64", J, da, dG64, fd, ms, K, flush)
+    df["precision"] = ("double-float (FP32 pairs) weights, stored levels and histories of the forward and "
+                       "adjoint sweeps; FP64 2x2 steps")
     return {
         "workload": "%s: 2D %dx%d (%d DOF), N=%d, BDF2 direct, alpha=(%g,%g), m=%g; target = same scheme with "
                     "alpha + (0.05,-0.05); J = 1/2 h^2 ||G^N - G_target||^2" % (GRAD_WORKLOAD, p.M, p.M, p.ndof, p.N,
@@ -629,6 +632,7 @@ def gradient_leg(fc, torch, dev, K, flush):
         "rel_err_vs_central_differences": rel, "fd_step": eps,
         "cpu_baseline": gradient_cpu_baseline(p),
         "mixed_precision": mixed,
+        "df64": df,
     }
 
 
@@ -693,6 +697,20 @@ def mixed_gradient_run(fc, torch, dev, p, g0, gt, prec, name, J64, da64, dG64, f
         peak = peaks.get("bf16_tflops_sustained", 1712.8)
         peak_src = "MEASURED_PEAKS.json bf16_tflops_sustained (kernels inside a long call)"
     dgc, d64 = dg.double(), dG64.double()
+    if prec == fc.CQ_DF64:
+        # double-float histories on the FP32 pipe: 12 operations per term; forward N^2 / 2 terms per
+        # mode and state, adjoint twice that (the d and d' histories)
+        ops = 12.0 * 2 * nm * N * N / 2 * 3
+        pk, pk_src = alu_peak("fp32")
+        roof = {"kernel": "k_fp2s_direct_df<8> + k_adjoint_direct_df<4>", "bound": "alu", "unit": "T FP32-op/s",
+                "achieved": ops / (statistics.mean(kern) * 1e-3) / 1e12, "peak": pk / 2e12,
+                "frac": ops / (statistics.mean(kern) * 1e-3) / (pk / 2), "peak_source": pk_src + " / 2",
+                "fp32_ops": ops}
+    else:
+        roof = {"kernel": "k_history_tc<float, %s> (all contractions of one gradient)" % name.upper(),
+                "bound": "tensor", "unit": "TFLOP/s", "achieved": flops / (tc_ms * 1e-3) / 1e12, "peak": peak,
+                "frac": flops / (tc_ms * 1e-3) / 1e12 / peak, "contraction_ms": tc_ms,
+                "share_of_gradient": tc_ms / ms, "peak_source": peak_src, "algorithmic_flops": flops}
     return {
         "precision": "%s contractions on FP32 levels (forward, weight-derivative history of the increments, "
                      "reversed-time adjoint), FP64 weights and step coefficients" % name,
@@ -700,10 +718,7 @@ def mixed_gradient_run(fc, torch, dev, p, g0, gt, prec, name, J64, da64, dG64, f
         "dof_steps_per_s": p.ndof * p.N / (ms * 1e-3), "kernels_ms": statistics.mean(kern),
         "speedup_vs_fp64_gradient": ms64 / ms,
         "gpu_launches_per_gradient": launches,
-        "roofline": {"kernel": "k_history_tc<float, %s> (all contractions of one gradient)" % name.upper(),
-                     "bound": "tensor", "unit": "TFLOP/s", "achieved": flops / (tc_ms * 1e-3) / 1e12, "peak": peak,
-                     "frac": flops / (tc_ms * 1e-3) / 1e12 / peak, "contraction_ms": tc_ms,
-                     "share_of_gradient": tc_ms / ms, "peak_source": peak_src, "algorithmic_flops": flops},
+        "roofline": roof,
         "J": Jm, "dJ_dalpha": list(dam),
         "rel_err_vs_fp64_gradient": {
             "J": abs(Jm - J64) / abs(J64),
@@ -1104,13 +1119,13 @@ def run_ours(args, rank, world, dist):
         if dist is not None:
             dist.barrier()
 
-    def timed(q, K, W, prec=0):
+    def timed(q, K, W, prec=0, accept=()):
         cp = cproblem(q, prec)
         ws = fc.workspace(fc.fp2s_solve(cp, g0, gN, None), dev)
         for _ in range(W):
             fc.fp2s_solve(cp, g0, gN, ws)
         st = fc.fp2s_status(cp, ws)
-        if st not in (fc.CQ_OK,):
+        if st not in (fc.CQ_OK,) + tuple(accept):
             raise RuntimeError("warm-up solve failed: %s" % fc.strerror(st))
         barrier()
         torch.cuda.synchronize()
@@ -1140,6 +1155,9 @@ def run_ours(args, rank, world, dist):
         pd = p.replace(form=ci.DIRECT)
         Kd, Wd = max(1, min(K, 4)), max(1, min(W, 1))
         d_steps, d_mains, d_launches, st_dir = timed(pd, Kd, Wd)
+        # the direct form in double-float: the (1,1) mode's growth (e^1096) leaves the FP32
+        # exponent range, so its run ends non-finite; the timing does not depend on the values
+        dd_steps, dd_mains, dd_launches, st_ddf = timed(pd, Kd, Wd, fc.CQ_DF64, accept=(fc.CQ_ENONFINITE,))
         gN_dir = gN.cpu().numpy()
         # the same fast solve in the double-float form (FP64-class accuracy on the FP32 pipe)
         df_steps, df_mains, df_launches, st_df = timed(p, K, W, fc.CQ_DF64)
@@ -1182,6 +1200,7 @@ def run_ours(args, rank, world, dist):
         g0m = torch.tensor(OSP.to_modal(G0, p.M, p.dim), dtype=torch.float64, device=dev)
         gm_fast, gm_dir = (_modal_solve(fc, torch, dev, cproblem(q), g0m) for q in (p, p.replace(form=ci.DIRECT)))
         gm_df = _modal_solve(fc, torch, dev, cproblem(p, fc.CQ_DF64), g0m)
+        gm_ddf = _modal_solve(fc, torch, dev, cproblem(p.replace(form=ci.DIRECT), fc.CQ_DF64), g0m, lo=p.M + 1)
         del g0m
 
     ms = statistics.mean(steps)
@@ -1259,6 +1278,29 @@ def run_ours(args, rank, world, dist):
     out["direct"] = {"value": world * units / (ms_dir * 1e-3), "unit": UNIT, "ms_per_step": ms_dir, "steps": Kd,
                      "warmup": Wd, "kernel": "k_fp2s_direct<8>", "kernel_ms": statistics.mean(d_mains),
                      "gpu_launches": int(d_launches), "status": fc.strerror(st_dir), "cpu_baseline": cpu_dir}
+    ms_ddf = statistics.mean(dd_steps)
+    kms_ddf = statistics.mean(dd_mains)
+    ops_ddf = 12.0 * 2 * (p.ndof // 2) * p.N * (p.N - 1) / 2          # double-float history terms
+    dec = np.array([k for k in sample_d if k > p.M])
+    ref_dec = ref_dir[:, np.isin(sample_d, dec)]
+    err_ddf = []
+    for s_ in range(2):
+        r_, g_ = ref_dec[s_], gm_ddf[s_, dec]
+        sc = np.max(np.abs(r_))
+        err_ddf.append(float(np.linalg.norm((g_ - r_) / sc) / np.linalg.norm(r_ / sc)))
+    out["direct"]["df64"] = {
+        "value": world * units / (ms_ddf * 1e-3), "unit": UNIT, "ms_per_step": ms_ddf,
+        "kernel": "k_fp2s_direct_df<8>", "kernel_ms": kms_ddf, "speedup_vs_fp64_direct": ms_dir / ms_ddf,
+        "gpu_launches": int(dd_launches), "status": fc.strerror(st_ddf),
+        "status_note": "the (1,1) mode grows like e^(1096 t), past the FP32 exponent range the double-float "
+                       "form keeps each mode in; the other modes are unaffected",
+        "rel_l2_per_state_vs_oracle_decaying_modes": err_ddf, "decaying_modes_compared": int(len(dec)),
+        "roofline": {"kernel": "k_fp2s_direct_df<8>", "bound": "alu", "unit": "T FP32-op/s",
+                     "achieved": ops_ddf / (kms_ddf * 1e-3) / 1e12, "peak": alu_peak("fp32")[0] / 2e12,
+                     "frac": ops_ddf / (kms_ddf * 1e-3) / (alu_peak("fp32")[0] / 2),
+                     "fp32_ops_per_launch": ops_ddf,
+                     "ops_definition": "12 FP32 operations per double-float history term, 2 states x nmodes x "
+                                       "N (N - 1) / 2 terms"}}
     out["df64"] = df64_report(p, units, world, ms_df, statistics.mean(df_mains), ms, df_launches,
                               fc.strerror(st_df), error["fast_df64"], K, W)
     if peaks is not None:
@@ -1306,13 +1348,17 @@ def df64_report(p, units, world, ms, ms_main, ms_fp64, launches, status, error, 
     }
 
 
-def _modal_solve(fc, torch, dev, cp, g0m):
-    """The modal G^N of every mode through fp2s_solve_modes (numpy [2][nmodes])."""
+def _modal_solve(fc, torch, dev, cp, g0m, lo=0):
+    """The modal G^N of the modes lo .. nmodes - 1 through fp2s_solve_modes (numpy [2][nmodes];
+    the columns before lo are NaN)."""
+    import numpy as np
     nm = g0m.shape[1]
-    gN = torch.empty_like(g0m)
-    ws = fc.workspace(fc.fp2s_solve_modes(cp, 0, nm, g0m, gN, None), dev)
-    fc.fp2s_solve_modes(cp, 0, nm, g0m, gN, ws)
-    out = gN.cpu().numpy()
+    src = g0m[:, lo:].contiguous()
+    gN = torch.empty_like(src)
+    ws = fc.workspace(fc.fp2s_solve_modes(cp, lo, nm, src, gN, None), dev)
+    fc.fp2s_solve_modes(cp, lo, nm, src, gN, ws)
+    out = np.full((2, nm), np.nan)
+    out[:, lo:] = gN.cpu().numpy()
     del ws
     return out
 
@@ -1372,6 +1418,10 @@ def summary(out):
                             "speedup_vs_fp64_form": g(out, "df64", "speedup_vs_fp64_form"),
                             "frac_fp32_pipe": g(out, "df64", "roofline", "frac"),
                             "rel_l2_per_state": g(out, "error", "fast_df64", "rel_l2_per_state_decaying_modes")},
+        "direct_df64": {"ms": g(out, "direct", "df64", "ms_per_step"),
+                        "speedup_vs_fp64_direct": g(out, "direct", "df64", "speedup_vs_fp64_direct"),
+                        "rel_l2_per_state_decaying_modes": g(out, "direct", "df64",
+                                                             "rel_l2_per_state_vs_oracle_decaying_modes")},
         "fp64_parity": {"fast": g(out, "error", "fast", "rel_l2_per_state_decaying_modes"),
                         "direct": g(out, "error", "direct", "rel_l2_per_state_decaying_modes"),
                         "fast_vs_direct_rel_l2": g(out, "error", "fast_vs_direct_rel_l2")},
@@ -1388,6 +1438,10 @@ def summary(out):
                   "launch_shape": g(out, "batch", "launch_shape")},
         "gradient": {"ms": g(out, "gradient", "ms_per_gradient"),
                      "rel_err_vs_central_differences": g(out, "gradient", "rel_err_vs_central_differences"),
+                     "df64": {"ms": g(out, "gradient", "df64", "ms_per_gradient"),
+                              "rel_err_vs_central_differences": g(out, "gradient", "df64",
+                                                                  "rel_err_vs_central_differences"),
+                              "rel_err_vs_fp64_gradient": g(out, "gradient", "df64", "rel_err_vs_fp64_gradient")},
                      "mixed": [{"precision": m.get("precision", "")[:6], "ms": m.get("ms_per_gradient"),
                                 "rel_err_vs_fp64_gradient": m.get("rel_err_vs_fp64_gradient")}
                                for m in g(out, "gradient", "mixed_precision") or []]},
