@@ -971,13 +971,14 @@ def paper_leg(fc, torch):
 
 
 def stream_leg(fc, torch, dev, steps=24):
-    """Per-step fast history (cq_history_fast) streaming its state from HBM, FP32 and FP64,
+    """Per-step fast history (cq_history_fast) streaming its state from HBM, FP32, FP64 and double-float,
     on the 2D 511x511 DOF count with the BDF2 sizes of the main workload (np = 80, Ns = 17);
-    plus the FP32 form on 4 Mi DOFs (a longer kernel: the asymptotic bandwidth)."""
+    plus the FP32 and double-float forms on 4 Mi DOFs (a longer kernel: the asymptotic bandwidth)."""
     import cq_inputs as ci
     p, _ = ci.workload(PREC_WORKLOAD)
-    out = _stream_case(fc, torch, dev, p.ndof, steps, (("f32", fc.CQ_F32), ("f64", fc.CQ_F64)))
-    out.update({k + "_4Mi_dof": v for k, v in _stream_case(fc, torch, dev, 4 << 20, steps, (("f32", fc.CQ_F32),)).items()
+    out = _stream_case(fc, torch, dev, p.ndof, steps, (("f32", fc.CQ_F32), ("f64", fc.CQ_F64), ("df64", fc.CQ_DF64)))
+    out.update({k + "_4Mi_dof": v for k, v in _stream_case(fc, torch, dev, 4 << 20, steps,
+                                                          (("f32", fc.CQ_F32), ("df64", fc.CQ_DF64))).items()
                 if k != "workload"})
     return out
 
@@ -991,7 +992,8 @@ def _stream_case(fc, torch, dev, ndof, steps, precs):
     G = torch.randn(2, ndof, dtype=torch.float64, device=dev, generator=gen)
     H = torch.empty(ndof, dtype=torch.float64, device=dev)
     out = {}
-    per_dofs = {"f32": 8 * npt + 4 * (ns - 2) + 4 + 4 + 8 + 8, "f64": 16 * npt + 8 * (ns - 2) + 8 + 8 + 8 + 8}
+    per_dofs = {"f32": 8 * npt + 4 * (ns - 2) + 4 + 4 + 8 + 8, "f64": 16 * npt + 8 * (ns - 2) + 8 + 8 + 8 + 8,
+                "df64": 16 * npt + 8 * (ns - 2) + 8 + 8 + 8 + 8}
     for name, prec in precs:
         per_dof = per_dofs[name]
         ws = fc.workspace(fc.cq_history_fast(2, beta, tau, np1, np2, ns, ndof, 1, None, None, prec=prec), dev)
@@ -1009,7 +1011,7 @@ def _stream_case(fc, torch, dev, ndof, steps, precs):
         bytes_per_launch = per_dof * ndof
         gbs = bytes_per_launch / (ms * 1e-3) / 1e9
         hbm = _measured_peaks().get("hbm_gbs", 6790.0)
-        hbm_roof = {"kernel": "k_history_fast_step" + ("_f32" if name == "f32" else ""),
+        hbm_roof = {"kernel": "k_history_fast_step" + {"f32": "_f32", "df64": "_df"}.get(name, ""),
                     "bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": hbm, "frac": gbs / hbm,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                     "algorithmic_bytes_per_dof_step": per_dof,

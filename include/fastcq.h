@@ -168,8 +168,10 @@ int cq_split(int32_t prec, const double *x_dev, int64_t n, void *hi_dev, void *l
  * h^1 = 0. G_prev_dev = G^{n-1} (ndof doubles; ignored for n = 1, may be NULL).
  * H_dev = h^n (ndof doubles). The workspace holds the Ghist state
  * (np x ndof), the last L levels and the tables; its size depends on
- * (scheme, cfg, ndof, prec) only. prec: CQ_F64, or CQ_F32 (state, levels and
- * sums in FP32, streamed with 16-byte accesses; tables computed in FP64). */
+ * (scheme, cfg, ndof, prec) only. prec: CQ_F64, CQ_F32 (state, levels and
+ * sums in FP32, streamed with 16-byte accesses; tables computed in FP64), or
+ * CQ_DF64 (state, levels, tables and sums as double-float pairs on the FP32
+ * pipe, 8 bytes per value as in FP64; the FP64 error bar at HBM-bound speed). */
 int cq_history_fast(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
                     int64_t ndof, int64_t n, const double *G_prev_dev, double *H_dev,
                     int32_t prec, void *ws_dev, size_t *ws_bytes, void *stream);

@@ -1,9 +1,10 @@
 // History sums over all DOFs: the direct strictly-lower-triangular Toeplitz
 // product (Eq. 3.8) and one step of the fast recurrences (Eqs. 3.9-3.10,
-// 3.17-3.18). FP64.
+// 3.17-3.18). FP64, FP32 and double-float (FP64-class on the FP32 pipe).
 #include <mutex>
 
 #include "common.cuh"
+#include "fastdf.cuh"
 
 namespace fastcq {
 
@@ -218,6 +219,109 @@ __global__ void __launch_bounds__(64) k_history_fast_step_f32(int64_t ndof, int6
     for (int v = 0; v < cnt; ++v) H[dof + v] = (double)h[v];
 }
 
+// ---------------------------------------------------------------------------
+// Fast history, one step, double-float form (CQ_DF64): the state Y[j][dof] and the last L
+// levels ring[slot][dof] are hi + lo pairs of FP32 numbers (8 bytes per DOF, as in FP64),
+// rows with an even pitch so that a thread moves its 2 DOFs with one 16-byte access; the node
+// update and the sums are error-free FP32 sequences (fastdf.cuh). The table holds the nodes
+// with r_j <= 1/2 first (entry (r_hi, r_lo, c_hi, c_lo)), then the others with u_j = 1 - r_j in
+// place of r_j (their update runs as Y - u Y + G, which keeps the relative accuracy of 1 - r for
+// ratios near 1); the state rows follow that order. Rows are moved DF_ROWS at a time so that
+// several loads are in flight per thread. G^{n-1} comes in and h^n goes out in FP64. Per
+// DOF-step the traffic is that of the FP64 kernel, 16 np + 8 L + 16 bytes, but the arithmetic
+// runs on the FP32 pipe: the step is bound by HBM rather than by the FP64 pipe.
+// ---------------------------------------------------------------------------
+constexpr int kDfRows = 4;
+
+template <bool U>
+__device__ __forceinline__ void df_step_rows(const float4 *t, int j0, int j1, const float4 gin, float2 *Y,
+                                             int64_t pitch, int64_t dof, float &h0, float &l0, float &h1, float &l1) {
+    for (int j = j0; j < j1; j += kDfRows) {
+        float4 v[kDfRows];
+#pragma unroll
+        for (int k = 0; k < kDfRows; ++k)
+            if (j + k < j1) v[k] = *reinterpret_cast<const float4 *>(Y + (int64_t)(j + k) * pitch + dof);
+#pragma unroll
+        for (int k = 0; k < kDfRows; ++k) {
+            if (j + k >= j1) break;
+            const float4 tj = t[j + k];
+            if (U) {
+                node_u(tj.x, tj.y, gin.x, gin.y, v[k].x, v[k].y);
+                node_u(tj.x, tj.y, gin.z, gin.w, v[k].z, v[k].w);
+            } else {
+                node_r(tj.x, tj.y, gin.x, gin.y, v[k].x, v[k].y);
+                node_r(tj.x, tj.y, gin.z, gin.w, v[k].z, v[k].w);
+            }
+            acc_prod(tj.z, tj.w, v[k].x, v[k].y, h0, l0);
+            acc_prod(tj.z, tj.w, v[k].z, v[k].w, h1, l1);
+        }
+#pragma unroll
+        for (int k = 0; k < kDfRows; ++k)
+            if (j + k < j1) *reinterpret_cast<float4 *>(Y + (int64_t)(j + k) * pitch + dof) = v[k];
+    }
+}
+
+__global__ void __launch_bounds__(64) k_history_fast_step_df(int64_t ndof, int64_t pitch, int64_t n, int L, int np,
+                                                             const float4 *__restrict__ tabdf,
+                                                             const float2 *__restrict__ wdf,
+                                                             const int *__restrict__ nr_dev,
+                                                             float2 *__restrict__ ring, float2 *__restrict__ Y,
+                                                             const double *__restrict__ G_prev,
+                                                             double *__restrict__ H) {
+    __shared__ float4 t[kMaxNp];
+    __shared__ float2 w[kMaxNs];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) t[i] = tabdf[i];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) w[i] = wdf[i];
+    __syncthreads();
+    const int nr = *nr_dev;                    // nodes of the r form (the first nr rows)
+    const int64_t dof = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (dof >= ndof) return;
+    const bool pair = dof + 1 < ndof;
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+    float4 gp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    auto row = [&](float2 *base, int64_t r) { return reinterpret_cast<float4 *>(base + r * pitch + dof); };
+    if (n >= 2) {
+        const float2 a = df_of(G_prev[dof]), b = pair ? df_of(G_prev[dof + 1]) : make_float2(0.0f, 0.0f);
+        gp = make_float4(a.x, a.y, b.x, b.y);
+        acc_prod(w[1].x, w[1].y, gp.x, gp.y, h0, l0);
+        acc_prod(w[1].x, w[1].y, gp.z, gp.w, h1, l1);
+        const int64_t imax = min((int64_t)L - 1, n - 1);
+        for (int i = 2; i <= imax; ++i) {
+            const float4 x = *row(ring, (n - i) % L);
+            acc_prod(w[i].x, w[i].y, x.x, x.y, h0, l0);
+            acc_prod(w[i].x, w[i].y, x.z, x.w, h1, l1);
+        }
+    }
+    if (n - L >= 1) {
+        const float4 gin = *row(ring, (n - L) % L);
+        df_step_rows<false>(t, 0, nr, gin, Y, pitch, dof, h0, l0, h1, l1);
+        df_step_rows<true>(t, nr, np, gin, Y, pitch, dof, h0, l0, h1, l1);
+    }
+    if (n >= 2) *row(ring, (n - 1) % L) = gp;
+    H[dof] = (double)h0 + (double)l0;
+    if (pair) H[dof + 1] = (double)h1 + (double)l1;
+}
+
+// Double-float tables of the per-step form (one block): the nodes with r <= 1/2 first as
+// (r_hi, r_lo, c_hi, c_lo), then the others as (u_hi, u_lo, c_hi, c_lo), u = 1 - r, each class
+// in its original order; *nr = the size of the first class; then the weights d_i, i < L, as
+// pairs. tab: r[np], c[np], d[L].
+__global__ void k_tab_to_df(const double *__restrict__ tab, int np, int L, float4 *__restrict__ tabdf,
+                            float2 *__restrict__ wdf, int *__restrict__ nr) {
+    int total_r = 0;
+    for (int k = 0; k < np; ++k) total_r += tab[k] <= 0.5 ? 1 : 0;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const double r = tab[j];
+        const bool u = r > 0.5;
+        int before = 0;
+        for (int k = 0; k < j; ++k) before += ((tab[k] > 0.5) == u) ? 1 : 0;
+        const float2 a = u ? df_of(1.0 - r) : df_of(r), c = df_of(tab[np + j]);
+        tabdf[u ? total_r + before : before] = make_float4(a.x, a.y, c.x, c.y);
+    }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) wdf[i] = df_of(tab[2 * np + i]);
+    if (threadIdx.x == 0) *nr = total_r;
+}
+
 __global__ void k_tab_to_f32(const double *__restrict__ t, int n, float *__restrict__ f) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) f[i] = (float)t[i];
@@ -241,6 +345,32 @@ static FastHistLayout fast_hist_layout(void *ws, int np1, int np2, int L, int64_
     l.dfull = cv.take<double>(kMaxNs);
     l.ring = cv.take<double>((size_t)L * ndof);
     l.Y = cv.take<double>((size_t)np * ndof);
+    l.bytes = cv.bytes();
+    return l;
+}
+
+struct FastHistLayoutDF {
+    double *tab, *scratch, *dfull;
+    float4 *tabdf;
+    float2 *wdf, *ring, *Y;
+    int *nr;
+    int64_t pitch;
+    size_t bytes;
+};
+
+static FastHistLayoutDF fast_hist_layout_df(void *ws, int np1, int np2, int L, int64_t ndof) {
+    Carve cv(ws);
+    FastHistLayoutDF l;
+    const int np = np1 + np2;
+    l.pitch = (ndof + 1) / 2 * 2;
+    l.tab = cv.take<double>(2 * np + kMaxNs);
+    l.scratch = cv.take<double>(2 * (np1 + np2));
+    l.dfull = cv.take<double>(kMaxNs);
+    l.tabdf = cv.take<float4>(np);
+    l.wdf = cv.take<float2>(kMaxNs);
+    l.nr = cv.take<int>(1);
+    l.ring = cv.take<float2>((size_t)L * l.pitch);
+    l.Y = cv.take<float2>((size_t)np * l.pitch);
     l.bytes = cv.bytes();
     return l;
 }
@@ -321,11 +451,40 @@ extern "C" int cq_history_fast(int32_t scheme, double beta, double tau, const cq
     if (!cfg || !ws_bytes || (scheme != CQ_BE && scheme != CQ_BDF2) || bad_order(beta) || !(tau > 0.0) ||
         ndof < 0 || n < 1)
         return CQ_EINVAL;
-    if (prec != CQ_F64 && prec != CQ_F32) return CQ_EUNSUPPORTED;
+    if (prec != CQ_F64 && prec != CQ_F32 && prec != CQ_DF64) return CQ_EUNSUPPORTED;
     const int np1 = cfg->np1, np2 = (scheme == CQ_BE) ? 0 : cfg->np2;
     const int L = (scheme == CQ_BE) ? 2 : cfg->ns;
     if (np1 < 1 || np2 < 0 || np1 + np2 > kMaxNp || (scheme == CQ_BDF2 && (np2 < 1 || L < 3 || L > kMaxNs)))
         return CQ_EINVAL;
+    if (prec == CQ_DF64) {
+        FastHistLayoutDF ld = fast_hist_layout_df(ws_dev, np1, np2, L, ndof);
+        if (!ws_dev) { *ws_bytes = ld.bytes; return CQ_OK; }
+        if (*ws_bytes < ld.bytes) return CQ_ENOMEM;
+        if (!H_dev || (n >= 2 && !G_prev_dev)) return CQ_EINVAL;
+        if (ndof == 0) return CQ_OK;
+        cudaStream_t s = (cudaStream_t)stream;
+        const int np = np1 + np2;
+        int st;
+        if (n == 1) {
+            if ((st = launch_weights(scheme, beta, tau, L - 1, ld.dfull, s))) return st;
+            if ((st = cuda_status(cudaMemcpyAsync(ld.tab + 2 * np, ld.dfull, L * sizeof(double),
+                                                  cudaMemcpyDeviceToDevice, s))))
+                return st;
+            if ((st = build_fast_coeffs(scheme, beta, tau, np1, np2, L, ld.scratch, ld.tab, ld.tab + np, s)))
+                return st;
+            k_tab_to_df<<<1, 256, 0, s>>>(ld.tab, np, L, ld.tabdf, ld.wdf, ld.nr);
+            if ((st = launched())) return st;
+            if ((st = cuda_status(cudaMemsetAsync(ld.Y, 0, (size_t)np * ld.pitch * sizeof(float2), s)))) return st;
+            if ((st = cuda_status(cudaMemsetAsync(ld.ring, 0, (size_t)L * ld.pitch * sizeof(float2), s)))) return st;
+            return cuda_status(cudaMemsetAsync(H_dev, 0, (size_t)ndof * sizeof(double), s));
+        }
+        const int64_t threads = (ndof + 1) / 2;
+        if ((st = timing_begin(s))) return st;
+        k_history_fast_step_df<<<(unsigned)((threads + 63) / 64), 64, 0, s>>>(
+            ndof, ld.pitch, n, L, np, ld.tabdf, ld.wdf, ld.nr, ld.ring, ld.Y, G_prev_dev, H_dev);
+        if ((st = launched())) return st;
+        return timing_end(s);
+    }
     if (prec == CQ_F32) {
         FastHistLayoutF32 lf = fast_hist_layout_f32(ws_dev, np1, np2, L, ndof);
         if (!ws_dev) { *ws_bytes = lf.bytes; return CQ_OK; }

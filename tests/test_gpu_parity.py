@@ -118,14 +118,16 @@ def test_history_direct(fc, scheme, ndof, n_lo, n_hi, ld_extra):
         assert np.all(np.isnan(_np(H)[:, ndof:]))
 
 
+@pytest.mark.parametrize("prec", [0, 4], ids=["f64", "df64"])
 @pytest.mark.parametrize("scheme,beta,np1,np2,ns,ndof,N", [(1, 0.7, 24, 0, 2, 131, 400), (1, 0.3, 64, 0, 2, 2, 300),
                                                           (2, 0.6, 16, 64, 17, 257, 300), (2, 0.4, 8, 12, 5, 1, 120),
                                                           (2, 0.8, 31, 31, 15, 64, 250)])
-def test_history_fast(fc, scheme, beta, np1, np2, ns, ndof, N):
+def test_history_fast(fc, scheme, beta, np1, np2, ns, ndof, N, prec):
+    """FP64 and the double-float form (CQ_DF64) against the oracle at the FP64 bar."""
     tau = 1.0 / N
     G = ci.rng(7).standard_normal((N + 1, ndof))
     H = torch.empty(ndof, dtype=torch.float64, device=DEV)
-    ws = fc.workspace(fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, 1, None, None), DEV)
+    ws = fc.workspace(fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, 1, None, None, prec=prec), DEV)
     if scheme == 1:
         ref_h = OH.FastHistoryBE(beta, tau, np1, ndof)
     else:
@@ -133,7 +135,7 @@ def test_history_fast(fc, scheme, beta, np1, np2, ns, ndof, N):
     d = OW.weights(scheme, beta, tau, N)
     Gd = _t(G)
     for n in range(1, N + 1):
-        fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, n, Gd[n - 1], H, ws)
+        fc.cq_history_fast(scheme, beta, tau, np1, np2, ns, ndof, n, Gd[n - 1], H, ws, prec=prec)
         got = _np(H)
         ref = ref_h(n, G)
         scale = _abs_scale(d, G, n)
