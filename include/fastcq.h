@@ -171,7 +171,13 @@ int cq_split(int32_t prec, const double *x_dev, int64_t n, void *hi_dev, void *l
  * (scheme, cfg, ndof, prec) only. prec: CQ_F64, CQ_F32 (state, levels and
  * sums in FP32, streamed with 16-byte accesses; tables computed in FP64), or
  * CQ_DF64 (state, levels, tables and sums as double-float pairs on the FP32
- * pipe, 8 bytes per value as in FP64; the FP64 error bar at HBM-bound speed). */
+ * pipe, 8 bytes per value as in FP64; the FP64 error bar at HBM-bound speed).
+ * CQ_F32 and CQ_DF64 hold every value in FP32's exponent range and, unlike the
+ * solves, apply no scaling of their own: levels or states of magnitude below
+ * about 2^-126 lose their low bits (down to zero below 2^-149), and above
+ * about 2^127 become infinite. The history is linear in G, so a caller whose
+ * levels lie outside that range scales them by a power of two (exact) and
+ * scales h^n back. */
 int cq_history_fast(int32_t scheme, double beta, double tau, const cq_fast_cfg_t *cfg,
                     int64_t ndof, int64_t n, const double *G_prev_dev, double *H_dev,
                     int32_t prec, void *ws_dev, size_t *ws_bytes, void *stream);

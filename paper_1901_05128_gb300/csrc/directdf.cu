@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(32, 16)
     constexpr int kStages = 3;
     __shared__ float4 sxs[kStages * BT * 32];
     float4 *sx = sxs + (threadIdx.x & 31);
-    for (int64_t mhi = N; mhi >= 1; mhi -= BT) {
+    // idle lanes (past the last mode) skip the sweep: they take part in the warp sums only
+    for (int64_t mhi = active ? N : 0; mhi >= 1; mhi -= BT) {
         float ar1[BT], er1[BT], ar2[BT], er2[BT], aq1[BT], eq1[BT], aq2[BT], eq2[BT];
 #pragma unroll
         for (int b = 0; b < BT; ++b) ar1[b] = er1[b] = ar2[b] = er2[b] = aq1[b] = eq1[b] = aq2[b] = eq2[b] = 0.0f;

@@ -1436,7 +1436,8 @@ __global__ void __launch_bounds__(32, 12) k_adjoint_direct(
     double lp1_1 = 0.0, lp1_2 = 0.0, lp2_1 = 0.0, lp2_2 = 0.0;      // lambda^{m+1}, lambda^{m+2}
     double db1 = 0.0, db2 = 0.0, sg1 = 0.0, sg2 = 0.0, sx1 = 0.0, sx2 = 0.0;
     double lam1_1 = 0.0, lam1_2 = 0.0, lam2_1 = 0.0, lam2_2 = 0.0, mu1_1 = 0.0, mu1_2 = 0.0;
-    for (int64_t mhi = N; mhi >= 1; mhi -= BT) {
+    // idle lanes (past the last mode) skip the sweep: they take part in the warp sums only
+    for (int64_t mhi = active ? N : 0; mhi >= 1; mhi -= BT) {
         double ar1[BT], ar2[BT], aq1[BT], aq2[BT], w1[BT], w2[BT], wq1[BT], wq2[BT], u1[BT] = {}, u2[BT] = {};
 #pragma unroll
         for (int b = 0; b < BT; ++b) {

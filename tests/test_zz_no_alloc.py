@@ -9,13 +9,14 @@ device and can fail at an arbitrary step. For them cq_history_fast_noalloc
 keeps the history state in a fixed device array owned by the library.
 
 The test drives the entry point through the C ABI for complete step sequences
-in a row, in both precisions it accepts (CQ_F64, and CQ_F32, which lays out
-padded FP32 rows and an FP32 table in the same array). Each later sequence is a
+in a row, in the three precisions it accepts (CQ_F64; CQ_F32, which lays out
+padded FP32 rows and an FP32 table in the same array; CQ_DF64, double-float
+rows and tables). Each later sequence is a
 different problem, so it starts from whatever the previous one left in the
 shared array, including a switch of precision between two problems. Every
 step's h^n must agree with cq_history_fast (the workspace version) at the same
 precision, within the tolerance of the other history tests:
-|difference| <= 1e-12 (FP64) or 2e-5 (FP32) * sum_i |d_i| |G^{n-i}|. A request
+|difference| <= 1e-12 (FP64, double-float) or 2e-5 (FP32) * sum_i |d_i| |G^{n-i}|. A request
 that does not fit the array must be refused before any work is done. The file
 is named so that pytest collects it last.
 """
@@ -46,7 +47,7 @@ def _abs_scale(d, G, n):
 
 
 def _run(fc, scheme, beta, np1, np2, ns, ndof, N, seed, prec=0):
-    tol = 1e-12 if prec == fc.CQ_F64 else 2e-5
+    tol = 2e-5 if prec == fc.CQ_F32 else 1e-12
     tau = 1.0 / N
     G = ci.rng(seed).standard_normal((N + 1, ndof))
     Gd = torch.tensor(G, dtype=torch.float64, device="cuda")
@@ -75,6 +76,14 @@ def test_noalloc_fp32_and_precision_switches(fc):
     _run(fc, 2, 0.45, 8, 24, 9, 2049, 180, seed=33, prec=fc.CQ_F32)
     _run(fc, 1, 0.55, 32, 0, 2, 1001, 150, seed=34, prec=fc.CQ_F64)
     _run(fc, 1, 0.7, 64, 0, 2, 4093, 160, seed=35, prec=fc.CQ_F32)
+
+
+def test_noalloc_double_float_and_precision_switches(fc):
+    # double-float on the leftovers of the problems above, FP32 on double-float leftovers,
+    # then double-float again with the BE window
+    _run(fc, 2, 0.6, 16, 64, 17, 2047, 200, seed=36, prec=fc.CQ_DF64)
+    _run(fc, 2, 0.35, 8, 24, 9, 1500, 120, seed=37, prec=fc.CQ_F32)
+    _run(fc, 1, 0.8, 48, 0, 2, 3001, 150, seed=38, prec=fc.CQ_DF64)
 
 
 def test_noalloc_refuses_requests_that_do_not_fit(fc):
