@@ -66,6 +66,8 @@ CASES = [
     ("bdf2_3d_np42", ci.Problem(0.3, 0.6, 0.65, 1.0, 150, 3, 11, ci.BDF2, ci.FAST, 12, 30, 9)),
     ("be3d_ragged", ci.Problem(0.6, 0.45, 0.3, 0.5, 77, 3, 13, ci.BE, ci.FAST, 37, 0, 2)),
     ("tiny", ci.Problem(0.5, 0.5, 0.6, 1.0, 3, 1, 1, ci.BDF2, ci.FAST, 2, 2, 3)),
+    ("one_step_bdf2", ci.Problem(0.5, 0.5, 0.6, 1.0, 1, 2, 3, ci.BDF2, ci.FAST, 4, 4, 3)),
+    ("two_steps_be", ci.Problem(0.3, 0.7, 0.4, 1.0, 2, 1, 5, ci.BE, ci.FAST, 8, 0, 2)),
     ("bdf2_ns32", ci.Problem(0.45, 0.55, 0.35, 1.0, 400, 2, 33, ci.BDF2, ci.FAST, 20, 40, 32)),
     ("m0_coupled", ci.Problem(0.3, 0.8, 0.0, 1.0, 400, 2, 47, ci.BDF2, ci.FAST, 16, 48, 15)),
     # more than 80 points: the fastest-decaying slots in shared memory
@@ -142,6 +144,8 @@ DIRECT_CASES = [
     ("be3d", ci.Problem(0.35, 0.7, 0.4, 1.0, 120, 3, 9, ci.BE, ci.DIRECT)),
     ("tiny", ci.Problem(0.5, 0.5, 0.6, 1.0, 3, 1, 1, ci.BDF2, ci.DIRECT)),
     ("one_step", ci.Problem(0.5, 0.5, 0.6, 1.0, 1, 2, 3, ci.BE, ci.DIRECT)),
+    ("two_steps_bdf2", ci.Problem(0.4, 0.6, 0.3, 1.0, 2, 1, 7, ci.BDF2, ci.DIRECT)),
+    ("one_step_bdf2", ci.Problem(0.4, 0.6, 0.3, 1.0, 1, 2, 5, ci.BDF2, ci.DIRECT)),
     ("bdf2_2d_many", ci.Problem(0.45, 0.65, 0.35, 1.0, 600, 2, 127, ci.BDF2, ci.DIRECT)),
 ]
 
