@@ -413,8 +413,9 @@ __host__ __device__ constexpr int f32_df_pairs(int NP) { return NP / 16 > 0 ? NP
 // FP32 tables of the fused FP32 fast solve, in the order the kernel reads them
 // (ftab: [4 NP] float4-packed words, then [8 KD] floats, then 2 floats):
 //   per state s the np nodes are ranked by r (ascending, ties by index) and placed in the
-//   top np of the NP slots; slot t = 4 kk + 2 hf + e of state s is component pair e of word
-//   4 kk + 2 hf + s, holding (r, c r); the bottom NP - np slots are zero. The top 4 KD slots
+//   top np of the NP slots; slot t = 4 kk + 2 hf + e of state s sits in word 4 kk + 2 hf + s,
+//   which holds (r_t0, r_t1, c r_t0, c r_t1) for its two slots e = 0, 1 (so that each pair
+//   feeds one packed two-wide FMA); the bottom NP - np slots are zero. The top 4 KD slots
 //   also get r - fl(r) in the float2 word 4 (kk - (NQ - KD)) + 2 hf + s, component e.
 //   The last two floats are C_s = sum_j c_j.
 // One block of 256 threads (2 np <= 256).
@@ -435,9 +436,9 @@ __global__ void k_f32_tables(int NP, int KD, int np, const double *__restrict__ 
         }
         const int t = NP - np + rank, kk = t >> 2, hf = (t >> 1) & 1, el = t & 1;
         const float rf = (float)r;
-        float *w = tab + 4 * (4 * kk + 2 * hf + st) + 2 * el;
-        w[0] = rf;
-        w[1] = (float)(tq[np + j] * r);
+        float *w = tab + 4 * (4 * kk + 2 * hf + st);
+        w[el] = rf;
+        w[2 + el] = (float)(tq[np + j] * r);
         if (kk >= NQ - KD) tlo[2 * (4 * (kk - (NQ - KD)) + 2 * hf + st) + el] = (float)(r - (double)rf);
     }
     if (tid < 2) {
@@ -453,8 +454,10 @@ __global__ void k_f32_tables(int NP, int KD, int np, const double *__restrict__ 
 // modes over HALF of the history-part nodes: lanes l = 16 s + 8 h + q hold state s
 // of the modes 2p, 2p + 1 of pair p = 8 w + q (w the warp) over the node slots
 // 4 kk + 2 h, 4 kk + 2 h + 1 (kk < NP / 4), so both halves hold nodes of similar r at
-// the same kk. One 16-byte table word (r_j, c_j r_j, r_{j+1}, c_{j+1} r_{j+1}) then feeds
-// both modes (eight FMAs), and the four (half, state) words a load touches are adjacent.
+// the same kk. One 16-byte table word (r_j, r_{j+1}, c_j r_j, c_{j+1} r_{j+1}) then feeds
+// both modes (eight FMAs, issued as four packed two-wide FMAs: Blackwell's FFMA2 halves the
+// instructions of the node work, which bounds this kernel by issue rather than by the FMA
+// pipe), and the four (half, state) words a load touches are adjacent.
 // The history sum is taken from the states before their update,
 //     h^n = sum_j c_j Y_j^n = sum_j (c_j r_j) Y_j^{n-1} + C G^{n-L},  C = sum_j c_j,
 // so the FMAs of a node do not wait on each other. The slowest quarter of the nodes
@@ -484,36 +487,41 @@ __device__ __noinline__ df lane_step_rare(const Fp2sParams P, const LaneStep ls,
 
 // Node part of one step (two modes, this lane's half of the nodes): the partial history
 // sums sum_j (c_j r_j) Y_j^{n-1} + C G^{n-L} into hA / hB, then Y_j^n = r_j Y_j^{n-1} + G^{n-L}
-// (the last KD node pairs with the double-float ratio fl(r_j) + r_lo_j from tl).
+// (the last KD node pairs with the double-float ratio fl(r_j) + r_lo_j from tl). YA[kk] holds the
+// states of the node pair kk of mode A; every FMA is a packed two-wide one over such a pair
+// (each component rounded as a scalar FMA). Partial sum q of a mode: pair parity q >> 1, pair
+// element q & 1.
 template <int NQ, int KD>
 __device__ __forceinline__ void f32_node_part(const float4 *tb, const float2 *tl, float cs, float2 in,
-                                              float (&YA)[2 * NQ], float (&YB)[2 * NQ], float (&hA)[4],
+                                              float2 (&YA)[NQ], float2 (&YB)[NQ], float (&hA)[4],
                                               float (&hB)[4]) {
-    hA[0] = cs * in.x;
-    hB[0] = cs * in.y;
-#pragma unroll
-    for (int q = 1; q < 4; ++q) hA[q] = hB[q] = 0.0f;
+    float2 pA[2] = {make_float2(cs * in.x, 0.0f), make_float2(0.0f, 0.0f)};
+    float2 pB[2] = {make_float2(cs * in.y, 0.0f), make_float2(0.0f, 0.0f)};
+    const float2 gA = make_float2(in.x, in.x), gB = make_float2(in.y, in.y);
 #pragma unroll
     for (int kk = 0; kk < NQ; ++kk) {
         const float4 t = tb[4 * kk];
-        const int c = 2 * (kk & 1);                                   // four partial sums per mode
-        hA[c] = fmaf(t.y, YA[2 * kk], hA[c]);
-        hB[c] = fmaf(t.y, YB[2 * kk], hB[c]);
-        hA[c + 1] = fmaf(t.w, YA[2 * kk + 1], hA[c + 1]);
-        hB[c + 1] = fmaf(t.w, YB[2 * kk + 1], hB[c + 1]);
+        const float2 r = make_float2(t.x, t.y), cr = make_float2(t.z, t.w);
+        const int c = kk & 1;
+        pA[c] = __ffma2_rn(cr, YA[kk], pA[c]);
+        pB[c] = __ffma2_rn(cr, YB[kk], pB[c]);
         if (kk >= NQ - KD) {
             const float2 lo = tl[4 * (kk - (NQ - KD))];
-            YA[2 * kk] = fmaf(t.x, YA[2 * kk], fmaf(lo.x, YA[2 * kk], in.x));
-            YB[2 * kk] = fmaf(t.x, YB[2 * kk], fmaf(lo.x, YB[2 * kk], in.y));
-            YA[2 * kk + 1] = fmaf(t.z, YA[2 * kk + 1], fmaf(lo.y, YA[2 * kk + 1], in.x));
-            YB[2 * kk + 1] = fmaf(t.z, YB[2 * kk + 1], fmaf(lo.y, YB[2 * kk + 1], in.y));
+            YA[kk] = __ffma2_rn(r, YA[kk], __ffma2_rn(lo, YA[kk], gA));
+            YB[kk] = __ffma2_rn(r, YB[kk], __ffma2_rn(lo, YB[kk], gB));
         } else {
-            YA[2 * kk] = fmaf(t.x, YA[2 * kk], in.x);
-            YB[2 * kk] = fmaf(t.x, YB[2 * kk], in.y);
-            YA[2 * kk + 1] = fmaf(t.z, YA[2 * kk + 1], in.x);
-            YB[2 * kk + 1] = fmaf(t.z, YB[2 * kk + 1], in.y);
+            YA[kk] = __ffma2_rn(r, YA[kk], gA);
+            YB[kk] = __ffma2_rn(r, YB[kk], gB);
         }
     }
+    hA[0] = pA[0].x;
+    hA[1] = pA[0].y;
+    hA[2] = pA[1].x;
+    hA[3] = pA[1].y;
+    hB[0] = pB[0].x;
+    hB[1] = pB[0].y;
+    hB[2] = pB[1].x;
+    hB[3] = pB[1].y;
 }
 
 // Exact window d_i x^{n-i}, i = 1 .. min(L - 1, n - 1), of both modes into hA[3] / hB[3]: odd i
@@ -576,7 +584,6 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
                                                                const double *__restrict__ d2,
                                                                const float *__restrict__ ftab,
                                                                const float *__restrict__ hdf) {
-    constexpr int NH = NP / 2;               // nodes per lane
     constexpr int NQ = NP / 4;               // node pairs per lane
     constexpr int KD = f32_df_pairs(NP);   // trailing node pairs with double-float ratios
     extern __shared__ __align__(16) float smf[];
@@ -633,9 +640,9 @@ __global__ void __launch_bounds__(kF32Threads) k_fp2s_fast_f32(Fp2sParams P, int
     lane_step2_setup(P, ls, l2);
     keep_reg(l2);
 
-    float YA[NH], YB[NH];                    // the two modes' states over this lane's nodes
+    float2 YA[NQ], YB[NQ];                   // the two modes' states over this lane's node pairs
 #pragma unroll
-    for (int j = 0; j < NH; ++j) YA[j] = YB[j] = 0.0f;
+    for (int j = 0; j < NQ; ++j) YA[j] = YB[j] = make_float2(0.0f, 0.0f);
     // own (and partner state's) last two levels as double-float pairs
     float gm1 = gz, gm1_lo = gzd.lo, gm2 = 0.0f, gm2_lo = 0.0f;
     float gm1_o = __shfl_xor_sync(0xffffffffu, gz, 16), gm1_o_lo = __shfl_xor_sync(0xffffffffu, gzd.lo, 16);
