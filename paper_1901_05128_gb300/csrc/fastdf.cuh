@@ -25,8 +25,9 @@ __host__ __device__ inline int df_np_class(int np) {
                           : np <= 112 ? 112 : np <= 128 ? 128 : 0;
 }
 
-// Floats of the kernel's table: [NP][2] float4 (a_hi, a_lo, c_hi, c_lo) with a = r or
-// a = 1 - r, then [kMaxNs][2] float2 window weights d_i.
+// Floats of the kernel's table: per pair of node slots (2p, 2p + 1) and state two float4
+// words, (a_hi, a_hi', a_lo, a_lo') and (c_hi, c_hi', c_lo, c_lo') (primes: slot 2p + 1) with
+// a = r or a = 1 - r, then [kMaxNs][2] float2 window weights d_i.
 __host__ __device__ constexpr int df_table_floats(int NP) { return 8 * NP + 4 * kMaxNs; }
 
 // ---- double-float operations (no contraction into FMAs) --------------------
@@ -91,11 +92,66 @@ __device__ __forceinline__ float2 df_of(double x) {
     return make_float2(h, __double2float_rn(x - (double)h));
 }
 
+// ---- the same operations on two independent values at once -----------------
+// Blackwell's packed two-wide FP32 instructions (FADD2 / FMUL2 / FFMA2) round each component
+// as the scalar instruction does, and halve the instructions issued. Component k of every
+// argument belongs to the k-th of two independent double-float computations.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ void tsum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = fadd2(a, b);
+    const float2 bb = fsub2(s, a);
+    e = fadd2(fsub2(a, fsub2(s, bb)), fsub2(b, bb));
+}
+
+__device__ __forceinline__ float2 prod_lo2(float2 ah, float2 al, float2 yh, float2 yl, float2 ph) {
+    float2 pe = ffma2(ah, yh, neg2(ph));
+    pe = ffma2(ah, yl, pe);
+    return ffma2(al, yh, pe);
+}
+
+// node_r / node_u / acc_prod on a pair of nodes
+__device__ __forceinline__ void node_r2(float2 ah, float2 al, float2 gh, float2 gl, float2 &yh, float2 &yl) {
+    const float2 ph = fmul2(ah, yh);
+    const float2 pe = prod_lo2(ah, al, yh, yl, ph);
+    float2 s, e;
+    tsum2(ph, gh, s, e);
+    const float2 t = fadd2(e, fadd2(pe, gl));
+    const float2 nh = fadd2(s, t);
+    yl = fsub2(t, fsub2(nh, s));
+    yh = nh;
+}
+
+__device__ __forceinline__ void node_u2(float2 uh, float2 ul, float2 gh, float2 gl, float2 &yh, float2 &yl) {
+    const float2 ph = fmul2(uh, yh);
+    const float2 pe = prod_lo2(uh, ul, yh, yl, ph);
+    float2 s1, e1, s2, e2;
+    tsum2(yh, neg2(ph), s1, e1);
+    tsum2(s1, gh, s2, e2);
+    const float2 t = fadd2(fadd2(e1, e2), fadd2(fsub2(yl, pe), gl));
+    const float2 nh = fadd2(s2, t);
+    yl = fsub2(t, fsub2(nh, s2));
+    yh = nh;
+}
+
+__device__ __forceinline__ void acc_prod2(float2 ch, float2 cl, float2 yh, float2 yl, float2 &sh, float2 &sl) {
+    const float2 p = fmul2(ch, yh);
+    const float2 pe = prod_lo2(ch, cl, yh, yl, p);
+    float2 s, e;
+    tsum2(sh, p, s, e);
+    sh = s;
+    sl = fadd2(sl, fadd2(e, pe));
+}
+
 // ---------------------------------------------------------------------------
 // Tables: per state the np nodes are ranked by r (ascending, ties by index) and put in
-// the top np of the NP slots; slot t of state s is word 2 t + s: (a_hi, a_lo, c_hi, c_lo)
-// with a = r_j, or a = 1 - r_j in the top df_u_slots(NP) slots; unused slots are zero
-// (Y = G, no contribution). Then the window weights d_i, i < L, as (hi, lo) in word 2 i + s.
+// the top np of the NP slots; slot t = 2 p + e of state s is component e of the pairs in
+// words 4 p + 2 s (a_hi, a_lo) and 4 p + 2 s + 1 (c_hi, c_lo), with a = r_j, or a = 1 - r_j in
+// the top df_u_slots(NP) slots; unused slots are zero (Y = G, no contribution). Then the window weights d_i, i < L, as (hi, lo) in word 2 i + s.
 // Called by every thread of a block (tid, nthr); out is global or shared memory.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void df_tables_fill(int NP, int np, int L, int64_t N, const double *__restrict__ tab1,
@@ -116,9 +172,13 @@ __device__ __forceinline__ void df_tables_fill(int NP, int np, int L, int64_t N,
             const double rk = tq[k];
             rank += (rk < r || (rk == r && k < j)) ? 1 : 0;
         }
-        const int t = NP - np + rank;
+        const int t = NP - np + rank, p = t >> 1, el = t & 1;
         const float2 a = df_of(t >= NP - KU ? 1.0 - r : r), c = df_of(tq[np + j]);
-        tab[2 * t + st] = make_float4(a.x, a.y, c.x, c.y);
+        float *wa = reinterpret_cast<float *>(tab + 4 * p + 2 * st), *wc = wa + 4;
+        wa[el] = a.x;
+        wa[2 + el] = a.y;
+        wc[el] = c.x;
+        wc[2 + el] = c.y;
     }
     for (int e = tid; e < 2 * L; e += nthr) {
         const int st = e & 1, i = e >> 1;
@@ -137,8 +197,11 @@ __device__ __forceinline__ void df_tables_fill(int NP, int np, int L, int64_t N,
 // ---------------------------------------------------------------------------
 // Per lane: state st = (lane >> 4) of mode mode_raw (its partner state on lane ^ 16), over all
 // P.N steps; lanes with mode_raw >= mode_end take part in the shuffles on mode 0 and write
-// nothing. Shared memory (the caller fills the tables and zeroes R and Ys first): tab [NP][2]
-// float4, wdf [kMaxNs][2] float2, R [L][T] and Ys [df_smem_slots(NP)][T] float2, column tid.
+// nothing. Shared memory (the caller fills the tables and zeroes R and Ys first): tab [NP / 2][2][2]
+// float4, wdf [kMaxNs][2] float2, R [L][T] float2 and Ys [df_smem_slots(NP) / 2][T] float4 (the
+// pair (yh, yh', yl, yl') of slots 2p, 2p + 1), column tid. Node slots are updated in pairs with
+// the packed operations (node_r2 / node_u2 / acc_prod2); component 0 of the partial sums collects
+// the even slots and component 1 the odd ones.
 template <int NP, bool BE, int WL>
 __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double *__restrict__ lam,
                                               const double *__restrict__ g0, double *__restrict__ gN,
@@ -149,13 +212,15 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
     constexpr int KR = NP - df_u_slots(NP);       // slots of the r form
     constexpr int KS = df_smem_slots(NP);         // slots in shared memory (all of the r form)
     static_assert(KS <= KR, "shared-memory slots take the r form");
+    static_assert(NP % 2 == 0 && KR % 2 == 0 && KS % 2 == 0, "every slot class holds whole pairs");
     const int L = P.L;
     const int lane = tid & 31, st = lane >> 4;
     const bool active = mode_raw < mode_end;
     const int64_t mode = active ? mode_raw : 0;
-    const float4 *tb = tab + st;
+    const float4 *tb = tab + 2 * st;              // pair p: tb[4 p] (a), tb[4 p + 1] (c)
     const float2 *ws = wdf + st;
-    float2 *Rc = R + tid, *Yc = Ys + tid;
+    float2 *Rc = R + tid;
+    float4 *Yc = reinterpret_cast<float4 *>(Ys) + tid;
     const double *dn = st ? d2 : d1;
 
     // per-mode power-of-two scale from max(|g1^0|, |g2^0|)
@@ -172,9 +237,10 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
     const double mn_oo = st ? mc.Mn.i22 : mc.Mn.i11, mn_ot = st ? mc.Mn.i21 : mc.Mn.i12;
     const double a = P.a, c = mc.c, inv_tau = P.inv_tau;
 
-    float yh[NP - KS], yl[NP - KS];              // slot j >= KS in register j - KS
+    constexpr int PS = KS / 2;                    // pairs in shared memory
+    float2 yh[NP / 2 - PS], yl[NP / 2 - PS];      // pair p >= PS in register p - PS
 #pragma unroll
-    for (int j = 0; j < NP - KS; ++j) yh[j] = yl[j] = 0.0f;
+    for (int j = 0; j < NP / 2 - PS; ++j) yh[j] = yl[j] = make_float2(0.0f, 0.0f);
     double gm1 = gz, gm2 = 0.0;
     const int64_t N = P.N;
     int slot = 1 % L;                            // n % L
@@ -193,30 +259,31 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
         slot = (slot + 1 == L) ? 0 : slot + 1;
         n = 2;
     }
-    // node part of the current step (two double-float partial sums): zero while n <= L
-    float ch0 = 0.0f, cl0 = 0.0f, ch1 = 0.0f, cl1 = 0.0f;
+    // node part of the current step (double-float partial sums of the even / odd slots in
+    // components 0 / 1): zero while n <= L
+    float2 ch = make_float2(0.0f, 0.0f), cl = make_float2(0.0f, 0.0f);
     for (; n <= N; ++n) {
         // node part of step n + 1, from level n + 1 - L (slot (n + 1) % L; zero before level 1)
         const int next = (slot + 1 == L) ? 0 : slot + 1;
-        float nh0 = 0.0f, nl0 = 0.0f, nh1 = 0.0f, nl1 = 0.0f;
+        float2 nh = make_float2(0.0f, 0.0f), nl = make_float2(0.0f, 0.0f);
         const float2 g = Rc[(size_t)next * T];
+        const float2 gh = make_float2(g.x, g.x), gl = make_float2(g.y, g.y);
 #pragma unroll
-        for (int j = 0; j < KS; ++j) {
-            const float4 t = tb[2 * j];
-            float2 y = Yc[(size_t)j * T];
-            node_r(t.x, t.y, g.x, g.y, y.x, y.y);
-            Yc[(size_t)j * T] = y;
-            if (j & 1) acc_prod(t.z, t.w, y.x, y.y, nh1, nl1);
-            else acc_prod(t.z, t.w, y.x, y.y, nh0, nl0);
+        for (int p = 0; p < PS; ++p) {
+            const float4 a = tb[4 * p], c = tb[4 * p + 1];
+            const float4 y = Yc[(size_t)p * T];
+            float2 ya = make_float2(y.x, y.y), yb = make_float2(y.z, y.w);
+            node_r2(make_float2(a.x, a.y), make_float2(a.z, a.w), gh, gl, ya, yb);
+            Yc[(size_t)p * T] = make_float4(ya.x, ya.y, yb.x, yb.y);
+            acc_prod2(make_float2(c.x, c.y), make_float2(c.z, c.w), ya, yb, nh, nl);
         }
 #pragma unroll
-        for (int j = KS; j < NP; ++j) {
-            const float4 t = tb[2 * j];
-            float &ya = yh[j - KS], &yb = yl[j - KS];
-            if (j < KR) node_r(t.x, t.y, g.x, g.y, ya, yb);
-            else node_u(t.x, t.y, g.x, g.y, ya, yb);
-            if (j & 1) acc_prod(t.z, t.w, ya, yb, nh1, nl1);
-            else acc_prod(t.z, t.w, ya, yb, nh0, nl0);
+        for (int p = PS; p < NP / 2; ++p) {
+            const float4 a = tb[4 * p], c = tb[4 * p + 1];
+            float2 &ya = yh[p - PS], &yb = yl[p - PS];
+            if (2 * p < KR) node_r2(make_float2(a.x, a.y), make_float2(a.z, a.w), gh, gl, ya, yb);
+            else node_u2(make_float2(a.x, a.y), make_float2(a.z, a.w), gh, gl, ya, yb);
+            acc_prod2(make_float2(c.x, c.y), make_float2(c.z, c.w), ya, yb, nh, nl);
         }
         // exact window of step n: d_i x^{n-i}, i = 1 .. L - 1 (levels before 1 are zero slots;
         // terms i >= L have zero weights)
@@ -225,12 +292,12 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
         for (int i = 1; i < WL; ++i) {
             sl = (sl == 0) ? L - 1 : sl - 1;
             const float2 w = ws[2 * i], x = Rc[(size_t)sl * T];
-            if (i & 1) acc_prod(w.x, w.y, x.x, x.y, ch1, cl1);
-            else acc_prod(w.x, w.y, x.x, x.y, ch0, cl0);
+            if (i & 1) acc_prod(w.x, w.y, x.x, x.y, ch.y, cl.y);
+            else acc_prod(w.x, w.y, x.x, x.y, ch.x, cl.x);
         }
         float hs, he;
-        tsum(ch0, ch1, hs, he);
-        const double h = (double)hs + (double)fadd(he, fadd(cl0, cl1));
+        tsum(ch.x, ch.y, hs, he);
+        const double h = (double)hs + (double)fadd(he, fadd(cl.x, cl.y));
         // the 2x2 step in FP64 (Eq. 4.1 / 4.7)
         double e, lead;
         if (BE) {
@@ -255,22 +322,20 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
             const float f = ldexpf(1.0f, -k);
             const double fd = ldexp(1.0, -k);
 #pragma unroll
-            for (int j = 0; j < NP - KS; ++j) {
-                yh[j] *= f;
-                yl[j] *= f;
+            for (int j = 0; j < NP / 2 - PS; ++j) {
+                yh[j] = make_float2(yh[j].x * f, yh[j].y * f);
+                yl[j] = make_float2(yl[j].x * f, yl[j].y * f);
             }
-            for (int j = 0; j < KS; ++j) {
-                const float2 v = Yc[(size_t)j * T];
-                Yc[(size_t)j * T] = make_float2(v.x * f, v.y * f);
+            for (int p = 0; p < PS; ++p) {
+                const float4 v = Yc[(size_t)p * T];
+                Yc[(size_t)p * T] = make_float4(v.x * f, v.y * f, v.z * f, v.w * f);
             }
             for (int j = 0; j < L; ++j) {
                 const float2 v = Rc[(size_t)j * T];
                 Rc[(size_t)j * T] = make_float2(v.x * f, v.y * f);
             }
-            nh0 *= f;
-            nl0 *= f;
-            nh1 *= f;
-            nl1 *= f;
+            nh = make_float2(nh.x * f, nh.y * f);
+            nl = make_float2(nl.x * f, nl.y * f);
             x *= fd;
             gm1 *= fd;
             gm2 *= fd;
@@ -281,10 +346,8 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
         Rc[(size_t)slot * T] = xd;
         gm2 = gm1;
         gm1 = x;
-        ch0 = nh0;
-        cl0 = nl0;
-        ch1 = nh1;
-        cl1 = nl1;
+        ch = nh;
+        cl = nl;
         slot = next;
     }
     if (active) {
