@@ -31,7 +31,7 @@ struct Fp2sLayout {
     float *hdf;                   // FP32 fast form: 0.5*d_i of both states as double-float, [4][N+1]
     float *ftab;                  // FP32 fast form: node tables in the fused kernel's order (k_f32_tables)
     double *hist;                 // direct: (N+1) x 2 x nmodes
-    float2 *wz1, *wz2, *hist2;    // direct, CQ_DF64: padded double-float weights; levels [N+1][nmodes][2]
+    float4 *wz, *hist2;           // direct, CQ_DF64: padded double-float weights; levels [N+1][nmodes]
     double *Y, *ring, *glast;     // step API, fast: 2 x np x nm, 2 x L x nm; both: 2 levels x 2 x nm
     void *mixed;                  // direct, CQ_BF16X3 / CQ_TF32X3: region of the mixed-precision solve
     double *wscr;                 // N > kMaxWeights: scratch of the weight builder
@@ -66,9 +66,8 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     if (P.form == CQ_DIRECT && P.prec == CQ_F64)
         l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
     if (P.form == CQ_DIRECT && P.prec == CQ_DF64) {
-        l.wz1 = cv.take<float2>(P.N + 2 * kDirDfBT + 1);
-        l.wz2 = cv.take<float2>(P.N + 2 * kDirDfBT + 1);
-        l.hist2 = cv.take<float2>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
+        l.wz = cv.take<float4>(P.N + 2 * kDirDfBT + 1);
+        l.hist2 = cv.take<float4>((size_t)(P.N + 1) * (hist_modes < 0 ? nm : hist_modes));
     }
     if (P.prec != CQ_F64 && P.prec != CQ_DF64) l.hdf = cv.take<float>((size_t)4 * (P.N + 1));
     if (P.form == CQ_FAST && P.prec == CQ_F32) l.ftab = cv.take<float>(kF32TabFloats);
@@ -1128,7 +1127,7 @@ static int setup_tables(const fp2s_problem_t *p, const Fp2sParams &P, int np1, i
         if ((st = launched())) return st;
     }
     if (P.form == CQ_DIRECT && P.prec == CQ_DF64) {
-        if ((st = direct_df_tables(P, l.d1, l.d2, l.wz1, l.wz2, s))) return st;
+        if ((st = direct_df_tables(P, l.d1, l.d2, l.wz, s))) return st;
     } else if (P.form == CQ_DIRECT && P.prec == CQ_F64) {
         const unsigned g = (unsigned)((P.N + 2 * kDirBT + 256) / 256);
         k_pad<<<g, 256, 0, s>>>(l.d1, P.N, kDirBT, l.dz1);
@@ -1165,7 +1164,7 @@ static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s
     if (P.form == CQ_FAST && P.prec == CQ_DF64)
         return fast_df_solve(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.ftab, s);
     if (P.form == CQ_DIRECT && P.prec == CQ_DF64)
-        return direct_df_solve(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.wz1, l.wz2, l.hist2, s);
+        return direct_df_solve(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.wz, l.hist2, s);
     if (P.form == CQ_FAST && fast_use_split(P.nmodes)) return launch_fast_split(P, l, s);
     if (P.form == CQ_FAST) {
         const int T = fast_block_threads(P.np, P.L, P.nmodes);
@@ -1579,7 +1578,7 @@ __global__ void __launch_bounds__(32, 12) k_adjoint_direct(
 
 struct GradLayout {
     double *tgt, *mu, *gx0, *q1, *q2, *qz1, *qz2, *dza1, *dza2, *acc;
-    float2 *wa1, *wa2, *qa1, *qa2;       // CQ_DF64: d and d' padded for the double-float adjoint
+    float4 *wa, *qa;                     // CQ_DF64: d and d' of both states padded for the double-float adjoint
     double *cg0, *ctgt, *cgx0, *cgN;     // compact [2][ns] copies of a slice (sliced runs only)
     size_t bytes;
 };
@@ -1601,12 +1600,10 @@ static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void 
     g.dza2 = cv.take<double>(P.N + 2 * kAdjBT + 1);
     const bool df = P.prec == CQ_DF64;
     if (df) {
-        g.wa1 = cv.take<float2>(P.N + 4 * kAdjDfBT);
-        g.wa2 = cv.take<float2>(P.N + 4 * kAdjDfBT);
-        g.qa1 = cv.take<float2>(P.N + 4 * kAdjDfBT);
-        g.qa2 = cv.take<float2>(P.N + 4 * kAdjDfBT);
+        g.wa = cv.take<float4>(P.N + 4 * kAdjDfBT);
+        g.qa = cv.take<float4>(P.N + 4 * kAdjDfBT);
     }
-    // FP64: [N + 1][2][ns] doubles; CQ_DF64: [N + 1 + kAdjDfBT][ns][2] pairs (zero levels past N)
+    // FP64: [N + 1][2][ns] doubles; CQ_DF64: [N + 1 + kAdjDfBT][ns] float4 (zero levels past N)
     g.mu = cv.take<double>((size_t)(P.N + 1 + (df ? kAdjDfBT : 0)) * 2 * ns);
     if (ns < nm) {
         g.cg0 = cv.take<double>(2 * ns);
@@ -1803,7 +1800,7 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, gl.tgt, l.tmp, s))) return st;
     if ((st = weight_derivatives(P, p, gl.q1, gl.q2, s))) return st;
     const bool df = P.prec == CQ_DF64;
-    if (df && (st = direct_df_grad_tables(P.N, l.d1, l.d2, gl.q1, gl.q2, gl.wa1, gl.wa2, gl.qa1, gl.qa2, s)))
+    if (df && (st = direct_df_grad_tables(P.N, l.d1, l.d2, gl.q1, gl.q2, gl.wa, gl.qa, s)))
         return st;
     const unsigned pg = (unsigned)((P.N + 2 * kAdjBT + 256) / 256);
     k_pad<<<pg, 256, 0, s>>>(gl.q1, P.N, kAdjBT, gl.qz1);
@@ -1832,9 +1829,9 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
             gx0 = gl.cgx0;
         }
         if (df) {
-            if ((st = direct_df_gradient_slice(Ps, wd, l.lam + m0, g0, gN, l.status, l.d1, l.d2, gl.q1, gl.q2, l.wz1,
-                                               l.wz2, gl.wa1, gl.wa2, gl.qa1, gl.qa2, l.hist2, tgt, vjp,
-                                               reinterpret_cast<float2 *>(gl.mu), gx0, gl.acc, s)))
+            if ((st = direct_df_gradient_slice(Ps, wd, l.lam + m0, g0, gN, l.status, l.d1, l.d2, gl.q1, gl.q2, l.wz,
+                                               gl.wa, gl.qa, l.hist2, tgt, vjp, reinterpret_cast<float4 *>(gl.mu),
+                                               gx0, gl.acc, s)))
                 return st;
             if (ns < nm && (st = copy_slice(gl.gx0 + m0, nm, gl.cgx0, cnt, cnt, s))) return st;
             continue;

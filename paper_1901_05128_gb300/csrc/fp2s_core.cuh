@@ -286,26 +286,25 @@ int fast_df_solve(const Fp2sParams &P, const double *lam, const double *g0, doub
                   const double *d1, const double *d2, const float *dftab, cudaStream_t s);
 
 // Direct solve in double-float (CQ_DIRECT with CQ_DF64, directdf.cu): time block, the padded
-// double-float weights (wz: n + 2 kDirDfBT + 1 pairs per state) and the solve over all N steps
-// (hist: (N + 1) x 2 x nmodes pairs).
+// double-float weights of both states (wz: n + 2 kDirDfBT + 1 entries (d1_hi, d2_hi, d1_lo,
+// d2_lo)) and the solve over all N steps (hist: (N + 1) x nmodes entries (x1_hi, x2_hi, x1_lo,
+// x2_lo)).
 constexpr int kDirDfBT = 8;
-int direct_df_tables(const Fp2sParams &P, const double *d1, const double *d2, float2 *wz1, float2 *wz2,
-                     cudaStream_t s);
+int direct_df_tables(const Fp2sParams &P, const double *d1, const double *d2, float4 *wz, cudaStream_t s);
 int direct_df_solve(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
-                    const double *d1, const double *d2, const float2 *wz1, const float2 *wz2, float2 *hist,
-                    cudaStream_t s);
+                    const double *d1, const double *d2, const float4 *wz, float4 *hist, cudaStream_t s);
 // Its gradient (the discrete adjoint in double-float): time block of the adjoint, the padded
-// weights d and d' (wa, qa: N + 4 kAdjDfBT pairs each), and one slice of modes: forward solve
-// with every level kept (hist), then the adjoint sweep (mu: (N + 1 + kAdjDfBT) x nmodes x 2
-// pairs), adding J, dJ/dbeta_1, dJ/dbeta_2 and a singular-step count to acc[0..3].
+// weights d and d' of both states (wa, qa: N + 4 kAdjDfBT entries each, laid out as wz), and one
+// slice of modes: forward solve with every level kept (hist), then the adjoint sweep (mu:
+// (N + 1 + kAdjDfBT) x nmodes entries, laid out as hist), adding J, dJ/dbeta_1, dJ/dbeta_2 and a
+// singular-step count to acc[0..3].
 constexpr int kAdjDfBT = 4;
 int direct_df_grad_tables(int64_t N, const double *d1, const double *d2, const double *q1, const double *q2,
-                          float2 *wa1, float2 *wa2, float2 *qa1, float2 *qa2, cudaStream_t s);
+                          float4 *wa, float4 *qa, cudaStream_t s);
 int direct_df_gradient_slice(const Fp2sParams &P, double wd, const double *lam, const double *g0, double *gN,
                              int *status, const double *d1, const double *d2, const double *q1, const double *q2,
-                             const float2 *wz1, const float2 *wz2, const float2 *wa1, const float2 *wa2,
-                             const float2 *qa1, const float2 *qa2, float2 *hist, const double *tgt, int vjp,
-                             float2 *mu, double *gx0, double *acc, cudaStream_t s);
+                             const float4 *wz, const float4 *wa, const float4 *qa, float4 *hist,
+                             const double *tgt, int vjp, float4 *mu, double *gx0, double *acc, cudaStream_t s);
 
 // Mixed-precision direct solve (mixed.cu): workspace bytes of its own region, and
 // the run over all N steps (weights, spectrum and the modal G^0 already in place;
