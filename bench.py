@@ -481,6 +481,7 @@ def precision_report(leg, cpu_modes):
                      "achieved": f32_flops / (kms * 1e-3) / 1e12, "peak": alu_peak("fp32")[0] / 1e12,
                      "frac": f32_flops / (kms * 1e-3) / alu_peak("fp32")[0],
                      "peak_source": alu_peak("fp32")[1], "kernel_ms": kms,
+                     "traffic": _recorded_traffic("k_fp2s_fast_f32"),
                      "flops_definition": "(4 np + 2) per DOF-step (node recurrences, history sums, C G^{n-L}); "
                                          "the double-float remainders of the slow nodes and weights are not counted"},
         "error_vs_fp64_oracle_rel_l2_sampled_modes": f32_err, "status": leg["f32_status"],
@@ -1233,7 +1234,7 @@ def run_ours(args, rank, world, dist):
     traffic = _profiled_traffic("k_fp2s_fast_bdf2_2d_m255.md")
     if traffic is not None:
         roofline["traffic"] = traffic
-        roofline["traffic_note"] = "ncu dram bytes per launch (independent of N: state stays on chip)"
+        roofline["traffic_note"] = "ncu dram bytes of one full-size launch (the state stays on chip)"
 
     # oracle legs: bounded samples, which also give the errors of this run
     import numpy as np
@@ -1277,9 +1278,19 @@ def run_ours(args, rank, world, dist):
         out["small_1d"] = small
     if stream is not None:
         out["fast_history_stream"] = stream
+    kms_dir = statistics.mean(d_mains)
+    flops_dir = 2.0 * 2 * (p.ndof // 2) * p.N * (p.N - 1) / 2        # one FMA per history term
+    pk64, pk64_src = alu_peak("fp64")
     out["direct"] = {"value": world * units / (ms_dir * 1e-3), "unit": UNIT, "ms_per_step": ms_dir, "steps": Kd,
-                     "warmup": Wd, "kernel": "k_fp2s_direct<8>", "kernel_ms": statistics.mean(d_mains),
-                     "gpu_launches": int(d_launches), "status": fc.strerror(st_dir), "cpu_baseline": cpu_dir}
+                     "warmup": Wd, "kernel": "k_fp2s_direct<8>", "kernel_ms": kms_dir,
+                     "gpu_launches": int(d_launches), "status": fc.strerror(st_dir), "cpu_baseline": cpu_dir,
+                     "roofline": {"kernel": "k_fp2s_direct<8>", "bound": "alu", "unit": "TFLOP/s",
+                                  "achieved": flops_dir / (kms_dir * 1e-3) / 1e12, "peak": pk64 / 1e12,
+                                  "frac": flops_dir / (kms_dir * 1e-3) / pk64, "peak_source": pk64_src,
+                                  "traffic": _recorded_traffic("k_fp2s_direct"),
+                                  "algorithmic_flops_per_launch": flops_dir,
+                                  "flops_definition": "2 flops per history term, 2 states x nmodes x N (N - 1) / 2 "
+                                                      "terms"}}
     ms_ddf = statistics.mean(dd_steps)
     kms_ddf = statistics.mean(dd_mains)
     ops_ddf = 12.0 * 2 * (p.ndof // 2) * p.N * (p.N - 1) / 2          # double-float history terms
@@ -1344,6 +1355,7 @@ def df64_report(p, units, world, ms, ms_main, ms_fp64, launches, status, error, 
                      "achieved": achieved / 1e12, "peak": pk / 2e12, "frac": achieved / (pk / 2),
                      "peak_source": pk_src + " / 2 (one FMA = 2 flops = 1 FP32-pipe operation)",
                      "fp32_ops_per_dof_step": ops, "kernel_ms": ms_main,
+                     "traffic": _recorded_traffic("k_fp2s_fast_df"),
                      "fp64_equivalent_tflops": flops64 / (ms_main * 1e-3) / 1e12},
         "error_vs_oracle": error,
         "cpu_baseline": "the headline's (the same oracle fast scheme)",
@@ -1470,6 +1482,38 @@ def _kernel_hash():
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+# Source files whose text a recorded traffic figure depends on, per kernel.
+TRAFFIC_SOURCES = {
+    "k_fp2s_fast_df": ("fastdf.cu", "fastdf.cuh", "fp2s_core.cuh", "common.cuh"),
+    "k_fp2s_fast_f32": ("fp2s.cu", "fp2s_core.cuh", "common.cuh"),
+    "k_fp2s_direct": ("fp2s.cu", "fp2s_core.cuh", "common.cuh"),
+}
+TRAFFIC_PROFILE = "dram_traffic_fused_solves_full_size.md"
+
+
+def _files_hash(names):
+    import hashlib
+    h = hashlib.sha256()
+    for f in names:
+        with open(os.path.join(ROOT, "paper_1901_05128_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(kernel):
+    """DRAM bytes per full-size launch of `kernel` recorded in profiles/ (one-pass ncu capture), if
+    it was taken on the current text of the kernel's source files; else None."""
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", TRAFFIC_PROFILE)).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch\[%s\]: (\d+) \(source hash ([0-9a-f]+)\)" % re.escape(kernel), txt)
+    if not m or m.group(2) != _files_hash(TRAFFIC_SOURCES[kernel]):
+        return None
+    return int(m.group(1))
 
 
 def _profiled_traffic(name):
