@@ -25,6 +25,15 @@ and the gradients
              weight derivatives d'_i = d(d_i)/d(beta) (plus the SBD first-step and G^0 terms);
   dJ/dalpha_s = -dJ/dbeta_s (beta_s = 1 - alpha_s).
 The modal gradient is mapped to nodal values with the (orthonormal) sine transform.
+
+The fast schemes (Eqs. 3.9-3.10 and 3.17-3.18 in the steppers of Remarks 4.1 and 4.7) are
+the same schemes with the history weights d_i replaced, for lags i >= L (L = 2 for BE,
+L = Ns for SBD), by the quadrature weights dtilde_i (Eqs. 3.8 and 3.16 without the error
+term); the exact weights stay in the window i < L and in the SBD terms that carry G^0. Their
+gradient (``gradient_fast``) is therefore the recursion above with dtilde in the backward
+history and its beta-derivative in dJ/dbeta; the derivative of the quadrature weights is
+taken by central differences of the quadrature construction, extrapolated (Richardson) from
+the steps delta and delta / 2.
 """
 from __future__ import annotations
 
@@ -32,7 +41,8 @@ import math
 
 import numpy as np
 
-from cq_inputs import BE, BDF2, DIRECT, Problem
+from cq_inputs import BE, BDF2, DIRECT, FAST, Problem
+from .quadrature import be_quadrature_weights, sbd_quadrature_weights
 from .scheme import coupling, solve_modal
 from .spatial import mode_eigenvalues, to_modal, to_physical
 from .weights import weights as cq_weights
@@ -76,7 +86,46 @@ def misfit(p: Problem, GN: np.ndarray, Gt: np.ndarray) -> float:
 def gradient(p: Problem, G0: np.ndarray, Gt: np.ndarray):
     """(J, dJ/dG0 of shape (2, M^dim), dJ/dalpha of shape (2,)) for the direct scheme of ``p``."""
     if p.form != DIRECT:
-        raise ValueError("the oracle adjoint covers the direct schemes")
+        raise ValueError("gradient covers the direct schemes; gradient_fast the fast ones")
+    tau = p.T / p.N
+    betas = (1.0 - p.alpha1, 1.0 - p.alpha2)
+    d = [cq_weights(p.scheme, b, tau, p.N) for b in betas]
+    dd = [weight_derivatives(p.scheme, b, tau, p.N) for b in betas]
+    return _adjoint(p, G0, Gt, d, dd, d, dd)
+
+
+def _quadrature_weights(p: Problem, beta: float, tau: float) -> np.ndarray:
+    if p.scheme == BE:
+        return be_quadrature_weights(beta, tau, p.np1, p.N)
+    return sbd_quadrature_weights(beta, tau, p.np1, p.np2, p.N)
+
+
+def gradient_fast(p: Problem, G0: np.ndarray, Gt: np.ndarray):
+    """(J, dJ/dG0, dJ/dalpha) for the fast scheme of ``p``: the recursion of ``gradient`` with the
+    history weights dtilde (exact below L, quadrature from L on) and their beta-derivatives."""
+    if p.form != FAST:
+        raise ValueError("gradient_fast covers the fast schemes")
+    tau = p.T / p.N
+    L = 2 if p.scheme == BE else p.ns
+    betas = (1.0 - p.alpha1, 1.0 - p.alpha2)
+    d = [cq_weights(p.scheme, b, tau, p.N) for b in betas]
+    dd = [weight_derivatives(p.scheme, b, tau, p.N) for b in betas]
+    dh, ddh = [], []
+    for s, b in enumerate(betas):
+        delta = min(1e-3, 0.25 * b, 0.25 * (1.0 - b))
+        q = [_quadrature_weights(p, b + t, tau) for t in (delta, -delta, 0.5 * delta, -0.5 * delta)]
+        dq = (4.0 * (q[2] - q[3]) / delta - (q[0] - q[1]) / (2.0 * delta)) / 3.0
+        w = _quadrature_weights(p, b, tau)
+        dh.append(np.where(np.arange(p.N + 1) < L, d[s], w))
+        ddh.append(np.where(np.arange(p.N + 1) < L, dd[s], dq))
+    return _adjoint(p, G0, Gt, dh, ddh, d, dd)
+
+
+def _adjoint(p: Problem, G0: np.ndarray, Gt: np.ndarray, dh, ddh, d, dd):
+    """The recursion of the module docstring for the scheme of ``p`` (direct or fast, whose
+    forward levels solve_modal gives): dh / ddh are the history weights of each state and their
+    beta-derivatives, d / dd the exact CQ weights and derivatives (d_0, and the SBD terms that
+    carry G^0)."""
     a = coupling(p.m)
     tau = p.T / p.N
     N = p.N
@@ -84,9 +133,6 @@ def gradient(p: Problem, G0: np.ndarray, Gt: np.ndarray):
     wd = h ** p.dim
     lam_k = mode_eigenvalues(p.M, p.dim)
     c = a + lam_k
-    betas = (1.0 - p.alpha1, 1.0 - p.alpha2)
-    d = [cq_weights(p.scheme, b, tau, N) for b in betas]
-    dd = [weight_derivatives(p.scheme, b, tau, N) for b in betas]
     g0 = to_modal(G0, p.M, p.dim)
     x = solve_modal(p, lam_k, g0)                      # x[n, s, mode]
     t = to_modal(Gt, p.M, p.dim)
@@ -109,8 +155,8 @@ def gradient(p: Problem, G0: np.ndarray, Gt: np.ndarray):
     for m in range(N, 0, -1):
         hr = np.zeros((2, nm))
         for n in range(m + 1, N + 1):
-            hr[0] += d[0][n - m] * mu[n, 0]
-            hr[1] += d[1][n - m] * mu[n, 1]
+            hr[0] += dh[0][n - m] * mu[n, 0]
+            hr[1] += dh[1][n - m] * mu[n, 1]
         rhs = -hr
         if m == N:
             rhs = rhs - r
@@ -146,7 +192,7 @@ def gradient(p: Problem, G0: np.ndarray, Gt: np.ndarray):
             else:
                 hp = np.zeros(nm)
                 for i in range(0, n):              # levels n-i >= 1
-                    hp = hp + dd[s][i] * x[n - i, s]
+                    hp = hp + ddh[s][i] * x[n - i, s]
                 if p.scheme == BDF2:
                     hp = hp + 0.5 * dd[s][n - 1] * x[0, s]
             tot += float(np.sum(mu[n, s] * hp))
