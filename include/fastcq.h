@@ -227,8 +227,8 @@ typedef struct {
     int32_t prec;          /* CQ_F64; in fp2s_solve also CQ_F32 with form == CQ_FAST (np1 + np2 <= 128),
                               CQ_DF64 with either form (fast: np1 + np2 <= 128)
                               and CQ_BF16X3 or CQ_TF32X3 with form == CQ_DIRECT (mixed-precision
-                              direct solve); fp2s_gradient / fp2s_vjp take CQ_F64, CQ_BF16X3 and
-                              CQ_TF32X3 with form == CQ_DIRECT */
+                              direct solve); fp2s_gradient / fp2s_vjp take CQ_F64 with either
+                              form, and CQ_DF64, CQ_BF16X3 and CQ_TF32X3 with form == CQ_DIRECT */
     int32_t flags;
 } fp2s_problem_t;
 
@@ -279,12 +279,21 @@ int fp2s_step(const fp2s_problem_t *p, int64_t n, void *ws_dev, size_t ws_bytes,
 int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, double *g_dev,
                void *stream);
 /* Gradient of the final-time misfit J = 1/2 h^dim sum_{s,dof} (G_s^N - Gt_s)^2
- * through the direct scheme (form == CQ_DIRECT; N <= 13000): the discrete adjoint
- * of Eq. 4.1 / Eq. 4.7, i.e. the transposed 2x2 steps run backwards in time with
- * the CQ convolution reversed in time (same weights), and the beta-derivatives
- * of the weights for dJ/dalpha_i = -dJ/dbeta_i.
- * prec == CQ_F64: FP64 throughout; the workspace holds the forward history and
- * the adjoint variables, two [N+1][2][M^dim] FP64 arrays. Sine modes are
+ * through the scheme of p (N <= 13000): the discrete adjoint of Eq. 4.1 / Eq. 4.7,
+ * i.e. the transposed 2x2 steps run backwards in time with the CQ convolution
+ * reversed in time (same weights), and the beta-derivatives of the weights for
+ * dJ/dalpha_i = -dJ/dbeta_i.
+ * form == CQ_DIRECT, prec == CQ_F64: FP64 throughout; the workspace holds the
+ * forward history and the adjoint variables, two [N+1][2][M^dim] FP64 arrays.
+ * form == CQ_DIRECT, prec == CQ_DF64: the same sweeps with double-float weights,
+ * stored levels and histories (FP64 steps); FP64-class results.
+ * form == CQ_FAST, prec == CQ_F64: the adjoint of the fast scheme (recurrences after
+ * Eqs. 3.10 / 3.18), which is the direct scheme with the quadrature weights for lags
+ * i >= L: the reversed-time history and the weight-derivative history both run as
+ * backward geometric recurrences per quadrature node (O(N (np1 + np2)) per mode);
+ * the derivatives of the quadrature tables in beta are Richardson-extrapolated
+ * central differences of the same table construction (accurate to ~1e-10). The
+ * workspace holds the forward levels ([N+1][2][M^dim] FP64) only. Sine modes are
  * independent, so a smaller workspace is accepted: the forward and adjoint
  * sweeps then run over slices of modes (the largest multiple of 32 modes whose
  * two arrays fit), with the same results up to the summation order of J and
@@ -304,7 +313,7 @@ int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, dou
  * Synchronises `stream`. CQ_EUNSUPPORTED for other forms and precisions. */
 int fp2s_gradient(const fp2s_problem_t *p, const double *G0_dev, const double *Gt_dev, double *J_host,
                   double *dJdG0_dev, double *dJdalpha_host, void *ws_dev, size_t *ws_bytes, void *stream);
-/* Vector-Jacobian product of the direct solve G^N = fp2s_solve(G^0; alpha1, alpha2):
+/* Vector-Jacobian product of the solve G^N = fp2s_solve(G^0; alpha1, alpha2):
  * the backward pass for an arbitrary upstream gradient dL/dG^N (physical
  * [2][M^dim], device). Same adjoint sweep as fp2s_gradient with the terminal
  * condition dL/dx^N = S dL/dG^N (S the orthonormal DST-I) instead of the misfit's.

@@ -1,0 +1,242 @@
+// Gradient of the fast form (fp2s_gradient / fp2s_vjp with CQ_FAST, FP64): the discrete
+// adjoint of the fast scheme.
+//
+// The fast history (recurrences after Eq. 3.10 and Eq. 3.18) is the direct history of
+// Eq. 3.8 with the weights
+//     dt_i = d_i                          for i < L (the exact window),
+//     dt_i = sum_j c_j r_j^(i - L)        for i >= L (the geometric history parts),
+// so its adjoint is the adjoint of the direct scheme with these weights: per mode, the
+// transposed 2x2 steps of Eq. 4.1 / Eq. 4.7 run backward from m = N, the adjoint levels
+// mu^m = K lambda^m (K = [[a + lam_k, -a], [-a, a + lam_k]]) feed the reversed-time history
+//     hr^m = sum_{n > m} dt_{n-m} mu^n,
+// and dJ/dbeta of a state is sum_m x^m hq^m with hq^m = sum_{n >= m} dt'_{n-m} mu^n (dt' the
+// derivative of the weights in beta), plus the terms of the first SBD step and of the
+// 1/2 d_{n-1} G^0 correction (exact weights, as in the direct adjoint).
+// The geometric parts give backward recurrences of O(Np) work per step:
+//     V_j^m = r_j V_j^{m+1} + mu^{m+L},   sum_{n >= m + L} r_j^(n-m-L) mu^n = V_j^m,
+//     W_j^m = r_j W_j^{m+1} + V_j^{m+1},  sum_{n >= m + L} (n-m-L) r_j^(n-m-L-1) mu^n = W_j^m,
+// so that hr^m = window + sum_j c_j V_j^m and, with dt'_i = c'_j r_j^(i-L) + c_j (i-L)
+// r_j^(i-L-1) r'_j, hq^m = d'_0 mu^m + window' + sum_j (c'_j V_j^m + c_j r'_j W_j^m).
+// The derivatives r'_j, c'_j of the Gauss-Jacobi based tables in beta are taken by
+// Richardson-extrapolated central differences of the same table construction (four extra
+// builds per state), which is accurate to ~1e-10 relative; the weights d_i and their
+// derivatives d'_i are exact (the product / Cauchy forms).
+//
+// One lane per mode and state as in the fused fast solve (lanes l < 16: state 1, l + 16: state
+// 2 of the same mode); a lane keeps V_j, W_j and the last L adjoint levels in shared memory
+// (column tid) and reads its forward levels x^m from the history the forward sweep stored.
+#include "common.cuh"
+#include "fp2s_core.cuh"
+
+namespace fastcq {
+
+// der = (c'_j, c_j r'_j), j < np, from the tables t[k] = (r[np], c[np]) built at beta + delta,
+// beta - delta, beta + delta / 2, beta - delta / 2 (k = 0 .. 3) and tab = (r, c) at beta:
+// D(h) = (f(beta + h) - f(beta - h)) / (2 h), f' = (4 D(delta / 2) - D(delta)) / 3.
+__global__ void k_fast_table_derivs(int np, double delta, const double *__restrict__ t, const double *__restrict__ tab,
+                                    double *__restrict__ der) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    auto deriv = [&](int off) {
+        const double dh = (t[off + j] - t[2 * np + off + j]) / (2.0 * delta);
+        const double dh2 = (t[4 * np + off + j] - t[6 * np + off + j]) / delta;
+        return (4.0 * dh2 - dh) / 3.0;
+    };
+    der[j] = deriv(np);
+    der[np + j] = tab[np + j] * deriv(0);
+}
+
+int fast_grad_tables(int scheme, double beta, double tau, int np1, int np2, int L, const double *tab,
+                     double *gj_scratch, double *tmp, double *der, cudaStream_t s) {
+    const int np = scheme == CQ_BE ? np1 : np1 + np2;
+    const double delta = fmin(2e-3, 0.25 * fmin(beta, 1.0 - beta));
+    const double b4[4] = {beta + delta, beta - delta, beta + 0.5 * delta, beta - 0.5 * delta};
+    int st;
+    for (int k = 0; k < 4; ++k) {
+        double *r = tmp + (size_t)2 * np * k;
+        if ((st = build_fast_coeffs(scheme, b4[k], tau, np1, np2, L, gj_scratch, r, r + np, s))) return st;
+    }
+    k_fast_table_derivs<<<(np + 127) / 128, 128, 0, s>>>(np, delta, tmp, tab, der);
+    return launched();
+}
+
+constexpr int kAdjFastMaxT = 64;
+
+// Shared memory: tables interleaved by state (word 2 j + s): r, c, c', c r' ([np][2] each),
+// the window weights d_i and d'_i (i < L, [kMaxNs][2] each), then per lane V [np][T],
+// W [np][T] and the adjoint levels mu^n at slot n % L ([L][T]).
+static size_t adj_fast_smem(int np, int L, int T) {
+    return ((size_t)8 * np + 4 * kMaxNs + (size_t)(2 * np + L) * T) * sizeof(double);
+}
+
+__global__ void __launch_bounds__(kAdjFastMaxT) k_adjoint_fast(
+    Fp2sParams P, double wd, const double *__restrict__ lam, const double *__restrict__ d1,
+    const double *__restrict__ d2, const double *__restrict__ q1, const double *__restrict__ q2,
+    const double *__restrict__ tab1, const double *__restrict__ tab2, const double *__restrict__ der1,
+    const double *__restrict__ der2, const double *__restrict__ hist, const double *__restrict__ tgt, int vjp,
+    double *__restrict__ gx0, double *__restrict__ acc) {
+    extern __shared__ double sm[];
+    const int np = P.np, L = P.L, T = blockDim.x, tid = threadIdx.x;
+    double *rt = sm, *ct = rt + 2 * np, *cpt = ct + 2 * np, *crt = cpt + 2 * np;
+    double *wt = crt + 2 * np, *qt = wt + 2 * kMaxNs;
+    double *V = qt + 2 * kMaxNs, *W = V + (size_t)np * T, *Rm = W + (size_t)np * T;
+    for (int i = tid; i < np; i += T) {
+        rt[2 * i] = tab1[i];
+        rt[2 * i + 1] = tab2[i];
+        ct[2 * i] = tab1[np + i];
+        ct[2 * i + 1] = tab2[np + i];
+        cpt[2 * i] = der1[i];
+        cpt[2 * i + 1] = der2[i];
+        crt[2 * i] = der1[np + i];
+        crt[2 * i + 1] = der2[np + i];
+    }
+    for (int i = tid; i < L; i += T) {                   // d and d' have N + 1 entries
+        const bool in = i <= P.N;
+        wt[2 * i] = in ? d1[i] : 0.0;
+        wt[2 * i + 1] = in ? d2[i] : 0.0;
+        qt[2 * i] = in ? q1[i] : 0.0;
+        qt[2 * i + 1] = in ? q2[i] : 0.0;
+    }
+    for (int j = 0; j < np; ++j) V[(size_t)j * T + tid] = W[(size_t)j * T + tid] = 0.0;
+    for (int j = 0; j < L; ++j) Rm[(size_t)j * T + tid] = 0.0;
+    __syncthreads();
+
+    const int lane = tid & 31, st = lane >> 4;
+    const int64_t nm = P.nmodes, N = P.N;
+    const int64_t mode_raw = ((int64_t)blockIdx.x * (T >> 5) + (tid >> 5)) * kFastModesPerWarp + (lane & 15);
+    const bool active = mode_raw < nm;
+    const int64_t mode = active ? mode_raw : 0;           // idle lanes take part in the shuffles
+    const double a = P.a, c = a + lam[mode], it = P.inv_tau;
+    const double d10 = wt[0], d20 = wt[1];
+    // transposed step matrices and their inverses; the lane's own row, ordered (own, other)
+    Inv2 Mn{}, M1{};
+    bool ok;
+    {
+        const double c0 = (P.scheme == CQ_BE) ? it : 1.5 * it;
+        ok = invert2(c0 + d10 * c, -d10 * a, -d20 * a, c0 + d20 * c, Mn);
+        if (P.scheme == CQ_BDF2)
+            ok &= invert2(it + (2.0 / 3.0) * d10 * c, -(2.0 / 3.0) * d10 * a, -(2.0 / 3.0) * d20 * a,
+                          it + (2.0 / 3.0) * d20 * c, M1);
+    }
+    const double mn_oo = st ? Mn.i22 : Mn.i11, mn_ot = st ? Mn.i21 : Mn.i12;
+    const double m1_oo = st ? M1.i22 : M1.i11, m1_ot = st ? M1.i21 : M1.i12;
+    // terminal condition dJ/dx^N of the lane's state
+    const double xN = hist[(N * 2 + st) * nm + mode];
+    const double e = xN - tgt[st * nm + mode];
+    const double rT = vjp ? tgt[st * nm + mode] : wd * e;
+    double Jpart = (active && !vjp) ? 0.5 * wd * e * e : 0.0;
+    const double *rs = rt + st, *cs = ct + st, *cps = cpt + st, *crs = crt + st, *ws = wt + st, *qs = qt + st;
+    const double *dn = st ? d2 : d1, *qn = st ? q2 : q1;
+    const double dq0 = qs[0];
+    double *Vc = V + tid, *Wc = W + tid, *Rc = Rm + tid;
+    double lp1 = 0.0, lp2 = 0.0, db = 0.0, sg = 0.0, sx = 0.0, lam1 = 0.0, lam2 = 0.0, mu1 = 0.0;
+    int slot = (int)(N % L);                                // slot of level m
+    for (int64_t m = N; m >= 1; --m) {
+        const double in = Rc[(size_t)slot * T];            // mu^{m+L} (zero past N)
+        double h0 = 0.0, h1 = 0.0, k0 = 0.0, k1 = 0.0;
+        int j = 0;
+        for (; j + 2 <= np; j += 2) {
+            const double ra = rs[2 * j], rb = rs[2 * j + 2];
+            const double va = Vc[(size_t)j * T], vb = Vc[(size_t)(j + 1) * T];
+            const double wa = fma(ra, Wc[(size_t)j * T], va), wb = fma(rb, Wc[(size_t)(j + 1) * T], vb);
+            const double na = fma(ra, va, in), nb = fma(rb, vb, in);
+            Wc[(size_t)j * T] = wa;
+            Wc[(size_t)(j + 1) * T] = wb;
+            Vc[(size_t)j * T] = na;
+            Vc[(size_t)(j + 1) * T] = nb;
+            h0 = fma(cs[2 * j], na, h0);
+            h1 = fma(cs[2 * j + 2], nb, h1);
+            k0 = fma(cps[2 * j], na, fma(crs[2 * j], wa, k0));
+            k1 = fma(cps[2 * j + 2], nb, fma(crs[2 * j + 2], wb, k1));
+        }
+        if (j < np) {
+            const double ra = rs[2 * j], va = Vc[(size_t)j * T];
+            const double wa = fma(ra, Wc[(size_t)j * T], va), na = fma(ra, va, in);
+            Wc[(size_t)j * T] = wa;
+            Vc[(size_t)j * T] = na;
+            h0 = fma(cs[2 * j], na, h0);
+            k0 = fma(cps[2 * j], na, fma(crs[2 * j], wa, k0));
+        }
+        // exact window: mu^{m+i}, i = 1 .. L - 1, at slot (m + i) % L
+        int sl = slot;
+        for (int i = 1; i < L; ++i) {
+            sl = (sl + 1 == L) ? 0 : sl + 1;
+            const double u = Rc[(size_t)sl * T];
+            h1 = fma(ws[2 * i], u, h1);
+            k1 = fma(qs[2 * i], u, k1);
+        }
+        double b = -(h0 + h1);
+        if (m == N) b -= rT;
+        const bool first = (P.scheme == CQ_BDF2 && m == 1);
+        if (P.scheme == CQ_BE) {
+            if (m < N) b += lp1 * it;
+        } else {
+            if (m + 1 <= N) b += 2.0 * it * lp1;
+            if (m + 2 <= N) b -= 0.5 * it * lp2;
+        }
+        const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
+        const double l = first ? fma(m1_oo, b, m1_ot * b_o) : fma(mn_oo, b, mn_ot * b_o);
+        const double l_o = __shfl_xor_sync(0xffffffffu, l, 16);
+        const double v = c * l - a * l_o;                  // mu^m of the lane's state
+        Rc[(size_t)slot * T] = v;
+        // hq^m (with the n = m term d'_0 mu^m) against the forward level x^m
+        const double hq = fma(dq0, v, k0 + k1);
+        db = fma(hist[(m * 2 + st) * nm + mode], hq, db);
+        if (m >= 2) {
+            sg = fma(__ldg(dn + m - 1), v, sg);
+            sx = fma(__ldg(qn + m - 1), v, sx);
+        }
+        if (m == 1) {
+            lam1 = l;
+            mu1 = v;
+        } else if (m == 2) {
+            lam2 = l;
+        }
+        lp2 = lp1;
+        lp1 = l;
+        slot = (slot == 0) ? L - 1 : slot - 1;
+    }
+    const double x0 = hist[st * nm + mode];
+    double g;
+    if (P.scheme == CQ_BE) {
+        g = -lam1 * it;
+    } else {
+        g = -lam1 * it + (st ? d20 : d10) * mu1 / 3.0 + 0.5 * it * lam2 + 0.5 * sg;
+        const double x1 = hist[(2 + st) * nm + mode];
+        db += mu1 * dq0 * (x0 - x1) / 3.0 + 0.5 * x0 * sx;
+    }
+    if (active) gx0[st * nm + mode] = g;
+    else db = 0.0;
+    // J over the whole warp; dJ/dbeta per state over each half-warp
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) Jpart += __shfl_xor_sync(0xffffffffu, Jpart, off);
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) db += __shfl_xor_sync(0xffffffffu, db, off);
+    if (lane == 0) {
+        atomicAdd(acc + 0, Jpart);
+        atomicAdd(acc + 1, db);
+    } else if (lane == 16) {
+        atomicAdd(acc + 2, db);
+    }
+    if (active && st == 0 && !ok) atomicAdd(acc + 3, 1.0);
+}
+
+int fast_adjoint_slice(const Fp2sParams &P, double wd, const double *lam, const double *d1, const double *d2,
+                       const double *q1, const double *q2, const double *tab1, const double *tab2,
+                       const double *der1, const double *der2, const double *hist, const double *tgt, int vjp,
+                       double *gx0, double *acc, cudaStream_t s) {
+    int T = kAdjFastMaxT;
+    while (T > 32 && adj_fast_smem(P.np, P.L, T) > 227 * 1024) T /= 2;
+    const size_t smem = adj_fast_smem(P.np, P.L, T);
+    if (smem > 227 * 1024) return CQ_EUNSUPPORTED;
+    static unsigned long long attr = 0;
+    int st;
+    if ((st = smem_attr_once((const void *)k_adjoint_fast, 227 * 1024, &attr))) return st;
+    const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
+    const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
+    k_adjoint_fast<<<blocks, T, smem, s>>>(P, wd, lam, d1, d2, q1, q2, tab1, tab2, der1, der2, hist, tgt, vjp,
+                                           gx0, acc);
+    return launched();
+}
+
+}  // namespace fastcq

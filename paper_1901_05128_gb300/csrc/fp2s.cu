@@ -38,7 +38,8 @@ struct Fp2sLayout {
     size_t bytes;
 };
 
-// hist_modes: modes of the direct FP64 history (all modes unless a gradient runs in slices).
+// hist_modes: modes of the FP64 level history (all modes unless a gradient runs in slices); the
+// direct FP64 solve keeps it, and so does the fast FP64 form inside a gradient (grad).
 // lam_modes: eigenvalues computed (all modes of the grid when the solve covers a range of them).
 static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void *ws, bool stepper,
                               bool grad = false, int64_t hist_modes = -1, int64_t lam_modes = -1) {
@@ -63,7 +64,7 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.tmp = cv.take<double>(2 * nm);
     l.g0 = cv.take<double>(2 * nm);
     l.gN = cv.take<double>(2 * nm);
-    if (P.form == CQ_DIRECT && P.prec == CQ_F64)
+    if ((P.form == CQ_DIRECT || grad) && P.prec == CQ_F64)
         l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
     if (P.form == CQ_DIRECT && P.prec == CQ_DF64) {
         l.wz = cv.take<float4>(P.N + 2 * kDirDfBT + 1);
@@ -129,13 +130,15 @@ static int derive(const fp2s_problem_t *p, Fp2sParams &P, int &np1, int &np2) {
 // swap e = h (+ G^0 correction) and the right-hand side b with one shuffle
 // each to finish the 2x2 step. Tables are interleaved by state (word 2j + s)
 // so the two half-warps read different banks. Four partial sums break the
-// dependency chain of h = sum_j c_j Y_j.
+// dependency chain of h = sum_j c_j Y_j. With HIST (the forward sweep of the fast-form
+// gradient) every level is also stored: hist[(n * 2 + s) * nmodes + mode], n = 0 .. N.
 // ---------------------------------------------------------------------------
+template <bool HIST>
 __global__ void __launch_bounds__(1024) k_fp2s_fast(Fp2sParams P, const double *__restrict__ lam,
                                                     const double *__restrict__ g0, double *__restrict__ gN,
                                                     int *__restrict__ status, const double *__restrict__ d1,
                                                     const double *__restrict__ d2, const double *__restrict__ tab1,
-                                                    const double *__restrict__ tab2) {
+                                                    const double *__restrict__ tab2, double *__restrict__ hist) {
     extern __shared__ double sm[];
     const int np = P.np, L = P.L, T = blockDim.x, tid = threadIdx.x;
     double *rt = sm;                          // rt[2j + s] = r_j of state s
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(1024) k_fp2s_fast(Fp2sParams P, const double *
     double *Yc = Y + tid, *Rc = R + tid;
 
     const double gz = g0[st * P.nmodes + mode];
+    if (HIST && active) hist[st * P.nmodes + mode] = gz;
     const double d_s0 = ws[0], d_o0 = wt[1 - st];
     ModeConst mc;
     const bool ok = mode_setup(P, lam[mode], st ? d_o0 : d_s0, st ? d_s0 : d_o0, mc);
@@ -228,6 +232,7 @@ __global__ void __launch_bounds__(1024) k_fp2s_fast(Fp2sParams P, const double *
         const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
         const double x = m_oo * b + m_ot * b_o;
         Rc[(size_t)slot * T] = x;
+        if (HIST && active) hist[(n * 2 + st) * P.nmodes + mode] = x;
         gm2 = gm1;
         gm1 = x;
     }
@@ -1170,11 +1175,13 @@ static int solve_kernel(const Fp2sParams &P, const Fp2sLayout &l, cudaStream_t s
         const int T = fast_block_threads(P.np, P.L, P.nmodes);
         if (T == 0) return CQ_EUNSUPPORTED;
         const size_t smem = fast_smem_bytes(P.np, P.L, T);
-        if (cudaFuncSetAttribute(k_fp2s_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_fp2s_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
             return CQ_ECUDA;
         const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
         const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
-        k_fp2s_fast<<<blocks, T, smem, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2);
+        k_fp2s_fast<false><<<blocks, T, smem, s>>>(P, l.lam, l.g0, l.gN, l.status, l.d1, l.d2, l.tab1, l.tab2,
+                                                    nullptr);
     } else if (const int lp = direct_lanes_per_mode(P.nmodes); lp > 1) {
         switch (lp) {
             case 2: launch_direct_split<2>(P, l, s); break;
@@ -1578,6 +1585,7 @@ __global__ void __launch_bounds__(32, 12) k_adjoint_direct(
 
 struct GradLayout {
     double *tgt, *mu, *gx0, *q1, *q2, *qz1, *qz2, *dza1, *dza2, *acc;
+    double *fder1, *fder2, *ftmp;        // fast form: (c', c r') of each state's tables; their builds
     float4 *wa, *qa;                     // CQ_DF64: d and d' of both states padded for the double-float adjoint
     double *cg0, *ctgt, *cgx0, *cgN;     // compact [2][ns] copies of a slice (sliced runs only)
     size_t bytes;
@@ -1594,6 +1602,19 @@ static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void 
     g.gx0 = cv.take<double>(2 * nm);
     g.q1 = cv.take<double>(P.N + 1);
     g.q2 = cv.take<double>(P.N + 1);
+    if (P.form == CQ_FAST) {             // the fast adjoint keeps its levels on chip: no mu
+        g.fder1 = cv.take<double>(2 * P.np);
+        g.fder2 = cv.take<double>(2 * P.np);
+        g.ftmp = cv.take<double>(8 * P.np);
+        if (ns < nm) {
+            g.cg0 = cv.take<double>(2 * ns);
+            g.ctgt = cv.take<double>(2 * ns);
+            g.cgx0 = cv.take<double>(2 * ns);
+            g.cgN = cv.take<double>(2 * ns);
+        }
+        g.bytes = cv.bytes();
+        return g;
+    }
     g.qz1 = cv.take<double>(P.N + 2 * kAdjBT + 1);
     g.qz2 = cv.take<double>(P.N + 2 * kAdjBT + 1);
     g.dza1 = cv.take<double>(P.N + 2 * kAdjBT + 1);
@@ -1616,7 +1637,7 @@ static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void 
 }
 
 static size_t grad64_bytes(const fp2s_problem_t *p, const Fp2sParams &P, int64_t ns) {
-    const Fp2sLayout l = fp2s_layout(p, P, nullptr, false, false, ns);
+    const Fp2sLayout l = fp2s_layout(p, P, nullptr, false, true, ns);
     return grad_layout(P, l, nullptr, ns).bytes;
 }
 
@@ -1773,7 +1794,8 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if (st) return st;
     if (!ws_bytes) return CQ_EINVAL;
     const bool mixed = P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3;
-    if (P.form != CQ_DIRECT || !(P.prec == CQ_F64 || P.prec == CQ_DF64 || mixed)) return CQ_EUNSUPPORTED;
+    const bool fast = P.form == CQ_FAST;
+    if (fast ? P.prec != CQ_F64 : !(P.prec == CQ_F64 || P.prec == CQ_DF64 || mixed)) return CQ_EUNSUPPORTED;
     if (P.N > 13000) return CQ_EUNSUPPORTED;            // shared-memory bound of the weight derivatives
     if (mixed)
         return gradient_mixed(p, P, np1, np2, G0_dev, Gt_dev, vjp, J_host, dJdG0_dev, dJdalpha_host, ws_dev,
@@ -1790,7 +1812,7 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     }
     const int64_t ns = grad64_slice(p, P, *ws_bytes);
     if (ns == 0) return CQ_ENOMEM;
-    Fp2sLayout l = fp2s_layout(p, P, ws_dev, false, false, ns);
+    Fp2sLayout l = fp2s_layout(p, P, ws_dev, false, true, ns);
     GradLayout gl = grad_layout(P, l, ws_dev, ns);
     if (!G0_dev || !Gt_dev || (!vjp && !J_host) || !dJdG0_dev || !dJdalpha_host || ((uintptr_t)ws_dev & 255))
         return CQ_EINVAL;
@@ -1802,15 +1824,25 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     const bool df = P.prec == CQ_DF64;
     if (df && (st = direct_df_grad_tables(P.N, l.d1, l.d2, gl.q1, gl.q2, gl.wa, gl.qa, s)))
         return st;
-    const unsigned pg = (unsigned)((P.N + 2 * kAdjBT + 256) / 256);
-    k_pad<<<pg, 256, 0, s>>>(gl.q1, P.N, kAdjBT, gl.qz1);
-    k_pad<<<pg, 256, 0, s>>>(gl.q2, P.N, kAdjBT, gl.qz2);
-    if ((st = launched(2))) return st;
-    // the adjoint needs the weights padded for its own block size
     double *dzA1 = gl.dza1, *dzA2 = gl.dza2;
-    k_pad<<<pg, 256, 0, s>>>(l.d1, P.N, kAdjBT, dzA1);
-    k_pad<<<pg, 256, 0, s>>>(l.d2, P.N, kAdjBT, dzA2);
-    if ((st = launched(2))) return st;
+    if (fast) {
+        // derivatives of the fast tables in beta (the tables at beta are in place)
+        if ((st = fast_grad_tables(P.scheme, 1.0 - p->alpha1, P.tau, np1, np2, P.L, l.tab1, l.scr1, gl.ftmp,
+                                   gl.fder1, s)))
+            return st;
+        if ((st = fast_grad_tables(P.scheme, 1.0 - p->alpha2, P.tau, np1, np2, P.L, l.tab2, l.scr1, gl.ftmp,
+                                   gl.fder2, s)))
+            return st;
+    } else {
+        const unsigned pg = (unsigned)((P.N + 2 * kAdjBT + 256) / 256);
+        k_pad<<<pg, 256, 0, s>>>(gl.q1, P.N, kAdjBT, gl.qz1);
+        k_pad<<<pg, 256, 0, s>>>(gl.q2, P.N, kAdjBT, gl.qz2);
+        if ((st = launched(2))) return st;
+        // the adjoint needs the weights padded for its own block size
+        k_pad<<<pg, 256, 0, s>>>(l.d1, P.N, kAdjBT, dzA1);
+        k_pad<<<pg, 256, 0, s>>>(l.d2, P.N, kAdjBT, dzA2);
+        if ((st = launched(2))) return st;
+    }
     if ((st = cuda_status(cudaMemsetAsync(gl.acc, 0, 8 * sizeof(double), s)))) return st;
     const double wd = grid_weight(p);
     const int64_t nm = P.nmodes;
@@ -1827,6 +1859,24 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
             tgt = gl.ctgt;
             gN = gl.cgN;
             gx0 = gl.cgx0;
+        }
+        if (fast) {
+            // forward fast solve keeping every level, then the backward sweep of the fast adjoint
+            const int T = fast_block_threads(P.np, P.L, cnt);
+            if (T == 0) return CQ_EUNSUPPORTED;
+            const size_t smem = fast_smem_bytes(P.np, P.L, T);
+            if (cudaFuncSetAttribute(k_fp2s_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return CQ_ECUDA;
+            const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
+            k_fp2s_fast<true><<<(unsigned)((cnt + mpb - 1) / mpb), T, smem, s>>>(
+                Ps, l.lam + m0, g0, gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.hist);
+            if ((st = launched())) return st;
+            if ((st = fast_adjoint_slice(Ps, wd, l.lam + m0, l.d1, l.d2, gl.q1, gl.q2, l.tab1, l.tab2, gl.fder1,
+                                         gl.fder2, l.hist, tgt, vjp, gx0, gl.acc, s)))
+                return st;
+            if (ns < nm && (st = copy_slice(gl.gx0 + m0, nm, gl.cgx0, cnt, cnt, s))) return st;
+            continue;
         }
         if (df) {
             if ((st = direct_df_gradient_slice(Ps, wd, l.lam + m0, g0, gN, l.status, l.d1, l.d2, gl.q1, gl.q2, l.wz,

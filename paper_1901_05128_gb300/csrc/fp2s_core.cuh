@@ -306,6 +306,17 @@ int direct_df_gradient_slice(const Fp2sParams &P, double wd, const double *lam, 
                              const float4 *wz, const float4 *wa, const float4 *qa, float4 *hist,
                              const double *tgt, int vjp, float4 *mu, double *gx0, double *acc, cudaStream_t s);
 
+// Gradient of the fast form in FP64 (fastgrad.cu): der = (c'_j, c_j r'_j) of one state's tables
+// tab = (r, c) at beta (tmp: 8 np doubles, gj_scratch: the table builder's 2 np), and the backward
+// sweep over one slice of modes from the forward levels hist ((N + 1) x 2 x nmodes), adding J,
+// dJ/dbeta_1, dJ/dbeta_2 and a singular-step count to acc[0..3] and writing dJ/dx^0 (modal) to gx0.
+int fast_grad_tables(int scheme, double beta, double tau, int np1, int np2, int L, const double *tab,
+                     double *gj_scratch, double *tmp, double *der, cudaStream_t s);
+int fast_adjoint_slice(const Fp2sParams &P, double wd, const double *lam, const double *d1, const double *d2,
+                       const double *q1, const double *q2, const double *tab1, const double *tab2,
+                       const double *der1, const double *der2, const double *hist, const double *tgt, int vjp,
+                       double *gx0, double *acc, cudaStream_t s);
+
 // Mixed-precision direct solve (mixed.cu): workspace bytes of its own region, and
 // the run over all N steps (weights, spectrum and the modal G^0 already in place;
 // hdf: d_i / 2 of both states as double-float, [4][N + 1]).

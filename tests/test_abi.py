@@ -150,7 +150,11 @@ def test_vjp_host_checks(fc):
     sz = C.c_size_t(0)
     da = (C.c_double * 2)()
     pf = fc.problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2)
-    assert fc._lib.fp2s_vjp(C.byref(pf), None, None, None, da, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
+    assert fc.fp2s_vjp(pf, None, None, None, None) > 0                     # fast form: FP64 only
+    for prec in (fc.CQ_F32, fc.CQ_DF64):
+        pq = fc.problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2, prec=prec)
+        sz = C.c_size_t(0)
+        assert fc._lib.fp2s_vjp(C.byref(pq), None, None, None, da, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED
     assert fc._lib.fp2s_vjp(C.byref(p), None, None, None, da, None, None, None) == fc.CQ_EINVAL
     sz = C.c_size_t(n_g)
     assert fc._lib.fp2s_vjp(C.byref(p), None, None, None, da, 1 << 20, C.byref(sz), None) == fc.CQ_EINVAL
