@@ -622,6 +622,7 @@ def gradient_leg(fc, torch, dev, K, flush):
     df = mixed_gradient_run(fc, torch, dev, p, g0, gt, fc.CQ_DF64, "DF64", J, da, dG64, fd, ms, K, flush)
     df["precision"] = ("double-float (FP32 pairs) weights, stored levels and histories of the forward and "
                        "adjoint sweeps; FP64 2x2 steps")
+    fast = fast_gradient_run(fc, torch, dev, p, g0, gt, Gt, K, flush, da, dG64, ms)
     return {
         "workload": "%s: 2D %dx%d (%d DOF), N=%d, BDF2 direct, alpha=(%g,%g), m=%g; target = same scheme with "
                     "alpha + (0.05,-0.05); J = 1/2 h^2 ||G^N - G_target||^2" % (GRAD_WORKLOAD, p.M, p.M, p.ndof, p.N,
@@ -634,6 +635,71 @@ def gradient_leg(fc, torch, dev, K, flush):
         "cpu_baseline": gradient_cpu_baseline(p),
         "mixed_precision": mixed,
         "df64": df,
+        "fast": fast,
+    }
+
+
+def fast_gradient_run(fc, torch, dev, p, g0, gt, Gt, K, flush, da64, dG64, ms64):
+    """The same gradient through the fast scheme (FP64, np1/np2/Ns of the workload): time,
+    dJ/dalpha against central differences of the fast forward solve, and the distance from the
+    direct scheme's gradient (the fast-vs-direct quadrature error)."""
+    import numpy as np
+    import cq_inputs as ci
+
+    def cprob(q):
+        return fc.problem(q.alpha1, q.alpha2, q.m, q.T, q.N, q.dim, q.M, q.scheme, ci.FAST, q.np1, q.np2, q.ns)
+
+    h = 1.0 / (p.M + 1)
+    cp = cprob(p)
+    dg = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_gradient(cp, g0, gt, dg, None), dev)
+    J, da = fc.fp2s_gradient(cp, g0, gt, dg, ws)              # warm-up
+    times, kern = [], []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        J, da = fc.fp2s_gradient(cp, g0, gt, dg, ws)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kern.append(fc.cq_timing_last())
+    del ws
+    wsf = fc.workspace(fc.fp2s_solve(cp, g0, gt, None), dev)
+
+    def J_of(q):
+        gN = torch.empty_like(g0)
+        fc.fp2s_solve(cprob(q), g0, gN, wsf)
+        return 0.5 * h ** p.dim * float(np.sum((gN.cpu().numpy() - Gt) ** 2))
+
+    eps = 1e-5
+    fd = [(J_of(p.replace(**{f: getattr(p, f) + eps})) - J_of(p.replace(**{f: getattr(p, f) - eps}))) / (2 * eps)
+          for f in ("alpha1", "alpha2")]
+    ms = statistics.mean(times)
+    kms = statistics.mean(kern)
+    dG = dg.cpu().numpy()
+    d64 = dG64.cpu().numpy()
+    npts = p.np1 + p.np2
+    # FP64 flops per DOF-step: forward 4 np + 2 (Ns - 1); backward sweep 10 np + 4 (Ns - 1) (per node
+    # the V and W recurrences, the d-history and the two d'-history terms; the window of d and d')
+    flops = (14.0 * npts + 6.0 * (p.ns - 1)) * p.ndof * p.N
+    pk, pk_src = alu_peak("fp64")
+    return {
+        "precision": "FP64, fast form (np1=%d, np2=%d, Ns=%d): forward fast solve keeping every level, then "
+                     "backward geometric recurrences per quadrature node" % (p.np1, p.np2, p.ns),
+        "value": 1e3 / ms, "unit": "grad steps/s (gradient evaluations per second)", "ms_per_gradient": ms,
+        "kernels_ms": kms, "speedup_vs_direct_fp64_gradient": ms64 / ms, "J": J, "dJ_dalpha": list(da),
+        "fd_dJ_dalpha": fd, "rel_err_vs_central_differences": [abs(da[i] - fd[i]) / abs(fd[i]) for i in range(2)],
+        "rel_diff_vs_direct_gradient": {"dJ_dalpha": [abs(da[i] - da64[i]) / abs(da64[i]) for i in range(2)],
+                                        "dJ_dG0_rel_l2": float(np.linalg.norm(dG - d64) / np.linalg.norm(d64))},
+        "roofline": {"kernel": "k_fp2s_fast<true> + k_adjoint_fast", "bound": "alu", "unit": "TFLOP/s",
+                     "achieved": flops / (kms * 1e-3) / 1e12, "peak": pk / 1e12, "frac": flops / (kms * 1e-3) / pk,
+                     "peak_source": pk_src, "algorithmic_flops_per_gradient": flops,
+                     "flops_definition": "(14 np + 6 (Ns - 1)) per DOF-step: forward 4 np + 2 (Ns - 1), backward "
+                                         "10 np + 4 (Ns - 1)"},
+        "cpu_baseline": "the gradient leg's (the oracle's direct adjoint; the fast scheme's oracle gradient runs "
+                        "the same O(N^2) recursion with the quadrature weights)",
     }
 
 
@@ -1456,6 +1522,10 @@ def summary(out):
                               "rel_err_vs_central_differences": g(out, "gradient", "df64",
                                                                   "rel_err_vs_central_differences"),
                               "rel_err_vs_fp64_gradient": g(out, "gradient", "df64", "rel_err_vs_fp64_gradient")},
+                     "fast": {"ms": g(out, "gradient", "fast", "ms_per_gradient"),
+                              "rel_err_vs_central_differences": g(out, "gradient", "fast",
+                                                                  "rel_err_vs_central_differences"),
+                              "frac_fp64": g(out, "gradient", "fast", "roofline", "frac")},
                      "mixed": [{"precision": m.get("precision", "")[:6], "ms": m.get("ms_per_gradient"),
                                 "rel_err_vs_fp64_gradient": m.get("rel_err_vs_fp64_gradient")}
                                for m in g(out, "gradient", "mixed_precision") or []]},

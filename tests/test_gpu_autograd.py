@@ -105,6 +105,19 @@ def test_gradcheck_tiny(pkg):
     assert torch.autograd.gradcheck(f, (G0, alpha), eps=1e-6, atol=1e-8, rtol=1e-6)
 
 
+def test_gradcheck_tiny_fast_form(pkg):
+    """The fast scheme through the binding (fast = (np1, np2, ns)): torch's gradcheck against
+    central differences in G0 and alpha (the quadrature tables rebuilt at every perturbed alpha)."""
+    fc, ag = pkg
+    G0 = torch.tensor(ci.g0_uniform(5, 1, 4), dtype=torch.float64, device="cuda", requires_grad=True)
+    alpha = torch.tensor([0.35, 0.65], dtype=torch.float64, device="cuda", requires_grad=True)
+
+    def f(g, a):
+        return ag.solve(g, a, m=0.3, T=1.0, N=24, dim=1, M=5, scheme=fc.CQ_BDF2, fast=(4, 8, 5))
+
+    assert torch.autograd.gradcheck(f, (G0, alpha), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
 def test_autograd_rejects_bad_input(pkg):
     fc, ag = pkg
     a = torch.tensor([0.3, 0.6], dtype=torch.float64, device="cuda")
@@ -112,6 +125,9 @@ def test_autograd_rejects_bad_input(pkg):
         ag.solve(torch.zeros(2, 7, dtype=torch.float32, device="cuda"), a, m=0.3, T=1.0, N=4, dim=1, M=7)
     with pytest.raises(ValueError):
         ag.solve(torch.zeros(2, 6, dtype=torch.float64, device="cuda"), a, m=0.3, T=1.0, N=4, dim=1, M=7)
+    with pytest.raises(ValueError):               # the fast form's gradient is FP64 only
+        ag.solve(torch.zeros(2, 7, dtype=torch.float64, device="cuda"), a, m=0.3, T=1.0, N=4, dim=1, M=7,
+                 fast=(4, 8, 5), prec=fc.CQ_BF16X3)
 
 
 @pytest.mark.parametrize("p", CASES, ids=["be_1d", "bdf2_1d", "bdf2_2d"])
