@@ -62,13 +62,22 @@ int fast_grad_tables(int scheme, double beta, double tau, int np1, int np2, int 
 
 constexpr int kAdjFastMaxT = 64;
 
-// Shared memory: tables interleaved by state (word 2 j + s): r, c, c', c r' ([np][2] each),
-// the window weights d_i and d'_i (i < L, [kMaxNs][2] each), then per lane V [np][T],
-// W [np][T] and the adjoint levels mu^n at slot n % L ([L][T]).
-static size_t adj_fast_smem(int np, int L, int T) {
-    return ((size_t)8 * np + 4 * kMaxNs + (size_t)(2 * np + L) * T) * sizeof(double);
+// Shared memory: tables interleaved by state (word 2 j + s): r, c, c', c r' ([NP][2] each, zero
+// past np), the window weights d_i and d'_i (i < L, [kMaxNs][2] each), then per lane V [NP][T],
+// W [NP][T] and the adjoint levels mu^n at slot n % L ([L][T]). NP is a compile-time bound of np
+// (the node loop unrolls fully, so the compiler issues the state loads well ahead of their use);
+// the zero-padded slots contribute nothing.
+static size_t adj_fast_smem(int NP, int L, int T) {
+    return ((size_t)8 * NP + 4 * kMaxNs + (size_t)(2 * NP + L) * T) * sizeof(double);
 }
 
+static int adj_np_class(int np) {
+    for (int b : {16, 32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256})
+        if (np <= b) return b;
+    return 0;
+}
+
+template <int NP>
 __global__ void __launch_bounds__(kAdjFastMaxT) k_adjoint_fast(
     Fp2sParams P, double wd, const double *__restrict__ lam, const double *__restrict__ d1,
     const double *__restrict__ d2, const double *__restrict__ q1, const double *__restrict__ q2,
@@ -77,18 +86,19 @@ __global__ void __launch_bounds__(kAdjFastMaxT) k_adjoint_fast(
     double *__restrict__ gx0, double *__restrict__ acc) {
     extern __shared__ double sm[];
     const int np = P.np, L = P.L, T = blockDim.x, tid = threadIdx.x;
-    double *rt = sm, *ct = rt + 2 * np, *cpt = ct + 2 * np, *crt = cpt + 2 * np;
-    double *wt = crt + 2 * np, *qt = wt + 2 * kMaxNs;
-    double *V = qt + 2 * kMaxNs, *W = V + (size_t)np * T, *Rm = W + (size_t)np * T;
-    for (int i = tid; i < np; i += T) {
-        rt[2 * i] = tab1[i];
-        rt[2 * i + 1] = tab2[i];
-        ct[2 * i] = tab1[np + i];
-        ct[2 * i + 1] = tab2[np + i];
-        cpt[2 * i] = der1[i];
-        cpt[2 * i + 1] = der2[i];
-        crt[2 * i] = der1[np + i];
-        crt[2 * i + 1] = der2[np + i];
+    double *rt = sm, *ct = rt + 2 * NP, *cpt = ct + 2 * NP, *crt = cpt + 2 * NP;
+    double *wt = crt + 2 * NP, *qt = wt + 2 * kMaxNs;
+    double *V = qt + 2 * kMaxNs, *W = V + (size_t)NP * T, *Rm = W + (size_t)NP * T;
+    for (int i = tid; i < NP; i += T) {
+        const bool in = i < np;
+        rt[2 * i] = in ? tab1[i] : 0.0;
+        rt[2 * i + 1] = in ? tab2[i] : 0.0;
+        ct[2 * i] = in ? tab1[np + i] : 0.0;
+        ct[2 * i + 1] = in ? tab2[np + i] : 0.0;
+        cpt[2 * i] = in ? der1[i] : 0.0;
+        cpt[2 * i + 1] = in ? der2[i] : 0.0;
+        crt[2 * i] = in ? der1[np + i] : 0.0;
+        crt[2 * i + 1] = in ? der2[np + i] : 0.0;
     }
     for (int i = tid; i < L; i += T) {                   // d and d' have N + 1 entries
         const bool in = i <= P.N;
@@ -97,7 +107,7 @@ __global__ void __launch_bounds__(kAdjFastMaxT) k_adjoint_fast(
         qt[2 * i] = in ? q1[i] : 0.0;
         qt[2 * i + 1] = in ? q2[i] : 0.0;
     }
-    for (int j = 0; j < np; ++j) V[(size_t)j * T + tid] = W[(size_t)j * T + tid] = 0.0;
+    for (int j = 0; j < NP; ++j) V[(size_t)j * T + tid] = W[(size_t)j * T + tid] = 0.0;
     for (int j = 0; j < L; ++j) Rm[(size_t)j * T + tid] = 0.0;
     __syncthreads();
 
@@ -134,8 +144,8 @@ __global__ void __launch_bounds__(kAdjFastMaxT) k_adjoint_fast(
     for (int64_t m = N; m >= 1; --m) {
         const double in = Rc[(size_t)slot * T];            // mu^{m+L} (zero past N)
         double h0 = 0.0, h1 = 0.0, k0 = 0.0, k1 = 0.0;
-        int j = 0;
-        for (; j + 2 <= np; j += 2) {
+#pragma unroll
+        for (int j = 0; j < NP; j += 2) {
             const double ra = rs[2 * j], rb = rs[2 * j + 2];
             const double va = Vc[(size_t)j * T], vb = Vc[(size_t)(j + 1) * T];
             const double wa = fma(ra, Wc[(size_t)j * T], va), wb = fma(rb, Wc[(size_t)(j + 1) * T], vb);
@@ -148,14 +158,6 @@ __global__ void __launch_bounds__(kAdjFastMaxT) k_adjoint_fast(
             h1 = fma(cs[2 * j + 2], nb, h1);
             k0 = fma(cps[2 * j], na, fma(crs[2 * j], wa, k0));
             k1 = fma(cps[2 * j + 2], nb, fma(crs[2 * j + 2], wb, k1));
-        }
-        if (j < np) {
-            const double ra = rs[2 * j], va = Vc[(size_t)j * T];
-            const double wa = fma(ra, Wc[(size_t)j * T], va), na = fma(ra, va, in);
-            Wc[(size_t)j * T] = wa;
-            Vc[(size_t)j * T] = na;
-            h0 = fma(cs[2 * j], na, h0);
-            k0 = fma(cps[2 * j], na, fma(crs[2 * j], wa, k0));
         }
         // exact window: mu^{m+i}, i = 1 .. L - 1, at slot (m + i) % L
         int sl = slot;
@@ -225,18 +227,43 @@ int fast_adjoint_slice(const Fp2sParams &P, double wd, const double *lam, const 
                        const double *q1, const double *q2, const double *tab1, const double *tab2,
                        const double *der1, const double *der2, const double *hist, const double *tgt, int vjp,
                        double *gx0, double *acc, cudaStream_t s) {
+    const int NP = adj_np_class(P.np);
+    if (NP == 0) return CQ_EUNSUPPORTED;
     int T = kAdjFastMaxT;
-    while (T > 32 && adj_fast_smem(P.np, P.L, T) > 227 * 1024) T /= 2;
-    const size_t smem = adj_fast_smem(P.np, P.L, T);
+    while (T > 32 && adj_fast_smem(NP, P.L, T) > 227 * 1024) T /= 2;
+    const size_t smem = adj_fast_smem(NP, P.L, T);
     if (smem > 227 * 1024) return CQ_EUNSUPPORTED;
-    static unsigned long long attr = 0;
-    int st;
-    if ((st = smem_attr_once((const void *)k_adjoint_fast, 227 * 1024, &attr))) return st;
     const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
     const unsigned blocks = (unsigned)((P.nmodes + mpb - 1) / mpb);
-    k_adjoint_fast<<<blocks, T, smem, s>>>(P, wd, lam, d1, d2, q1, q2, tab1, tab2, der1, der2, hist, tgt, vjp,
-                                           gx0, acc);
-    return launched();
+    int st = CQ_OK;
+    auto run = [&](auto kern, unsigned long long *attr) {
+        if ((st = smem_attr_once((const void *)kern, 227 * 1024, attr))) return;
+        kern<<<blocks, T, smem, s>>>(P, wd, lam, d1, d2, q1, q2, tab1, tab2, der1, der2, hist, tgt, vjp, gx0, acc);
+        st = launched();
+    };
+#define CQ_ADJ_FAST(NPV)                        \
+    case NPV: {                                 \
+        static unsigned long long attr = 0;     \
+        run(k_adjoint_fast<NPV>, &attr);        \
+        break;                                  \
+    }
+    switch (NP) {
+        CQ_ADJ_FAST(16)
+        CQ_ADJ_FAST(32)
+        CQ_ADJ_FAST(48)
+        CQ_ADJ_FAST(64)
+        CQ_ADJ_FAST(80)
+        CQ_ADJ_FAST(96)
+        CQ_ADJ_FAST(112)
+        CQ_ADJ_FAST(128)
+        CQ_ADJ_FAST(160)
+        CQ_ADJ_FAST(192)
+        CQ_ADJ_FAST(224)
+        CQ_ADJ_FAST(256)
+        default: return CQ_EUNSUPPORTED;
+    }
+#undef CQ_ADJ_FAST
+    return st;
 }
 
 }  // namespace fastcq
