@@ -69,11 +69,13 @@ CASES = [ci.Problem(0.3, 0.7, 0.4, 1.0, 60, 1, 15, ci.BE, ci.FAST, 16, 0, 2),
          ci.Problem(0.25, 0.8, 0.0, 1.0, 40, 2, 5, ci.BDF2, ci.FAST, 4, 12, 6),
          ci.Problem(0.5, 0.35, 0.45, 1.0, 4, 1, 4, ci.BDF2, ci.FAST, 3, 5, 7),
          ci.Problem(0.6, 0.3, 0.3, 1.0, 1, 1, 3, ci.BE, ci.FAST, 8, 0, 2),
-         ci.Problem(0.35, 0.55, 0.6, 1.0, 50, 2, 9, ci.BDF2, ci.FAST, 7, 25, 17)]
+         ci.Problem(0.35, 0.55, 0.6, 1.0, 50, 2, 9, ci.BDF2, ci.FAST, 7, 25, 17),
+         ci.Problem(0.3, 0.6, 0.4, 1.0, 80, 1, 20, ci.BE, ci.FAST, 200, 0, 2),
+         ci.Problem(0.45, 0.5, 0.35, 1.0, 90, 2, 6, ci.BDF2, ci.FAST, 40, 150, 32)]
 
 
 @pytest.mark.parametrize("p", CASES, ids=["be1d", "be2d", "bdf2_1d", "bdf2_2d_m0", "n_below_L", "one_step",
-                                          "bdf2_ns17_idle_lanes"])
+                                          "bdf2_ns17_idle_lanes", "be_np200", "bdf2_np190_ns32"])
 def test_fast_gradient_against_oracle(fc, p):
     G0 = ci.g0_uniform(p.M, p.dim, 51)
     Gt = 0.5 * ci.g0_uniform(p.M, p.dim, 52)
