@@ -666,6 +666,24 @@ def fast_gradient_run(fc, torch, dev, p, g0, gt, Gt, K, flush, da64, dG64, ms64,
         times.append(e0.elapsed_time(e1))
         kern.append(fc.cq_timing_last())
     del ws
+    # the same with the backward sweep in double-float
+    cpd = fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, ci.FAST, p.np1, p.np2, p.ns,
+                     prec=fc.CQ_DF64)
+    dgd = torch.empty_like(g0)
+    ws = fc.workspace(fc.fp2s_gradient(cpd, g0, gt, dgd, None), dev)
+    Jd, dad = fc.fp2s_gradient(cpd, g0, gt, dgd, ws)          # warm-up
+    dtimes, dkern = [], []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Jd, dad = fc.fp2s_gradient(cpd, g0, gt, dgd, ws)
+        e1.record()
+        e1.synchronize()
+        dtimes.append(e0.elapsed_time(e1))
+        dkern.append(fc.cq_timing_last())
+    del ws
     wsf = fc.workspace(fc.fp2s_solve(cp, g0, gt, None), dev)
 
     def J_of(q):
@@ -705,6 +723,14 @@ def fast_gradient_run(fc, torch, dev, p, g0, gt, Gt, K, flush, da64, dG64, ms64,
                                          "10 np + 4 (Ns - 1)"},
         "cpu_baseline": "the gradient leg's (the oracle's direct adjoint; the fast scheme's oracle gradient runs "
                         "the same O(N^2) recursion with the quadrature weights)",
+        "df64": {"precision": "the backward sweep in double-float (FP32 pairs, packed two-wide; FP64 steps and "
+                              "per-mode sums); forward sweep FP64",
+                 "ms_per_gradient": statistics.mean(dtimes), "kernels_ms": statistics.mean(dkern),
+                 "speedup_vs_fp64_fast_gradient": ms / statistics.mean(dtimes),
+                 "rel_err_vs_central_differences": [abs(dad[i] - fd[i]) / abs(fd[i]) for i in range(2)],
+                 "rel_diff_vs_fp64_fast_gradient": {
+                     "J": abs(Jd - J) / abs(J), "dJ_dalpha": [abs(dad[i] - da[i]) / abs(da[i]) for i in range(2)],
+                     "dJ_dG0_rel_l2": float(np.linalg.norm(dgd.cpu().numpy() - dG) / np.linalg.norm(dG))}},
     }
 
 
@@ -1528,6 +1554,7 @@ def summary(out):
                                                                   "rel_err_vs_central_differences"),
                               "rel_err_vs_fp64_gradient": g(out, "gradient", "df64", "rel_err_vs_fp64_gradient")},
                      "fast": {"ms": g(out, "gradient", "fast", "ms_per_gradient"),
+                              "df64_ms": g(out, "gradient", "fast", "df64", "ms_per_gradient"),
                               "rel_err_vs_central_differences": g(out, "gradient", "fast",
                                                                   "rel_err_vs_central_differences"),
                               "frac_fp64": g(out, "gradient", "fast", "roofline", "frac")},

@@ -16,6 +16,7 @@
 // fp2s_solve runs all N steps of a mode inside one thread of one persistent
 // kernel: modes never interact, so there is no grid-wide synchronisation.
 #include "common.cuh"
+#include "fastgrad.cuh"
 #include "fp2s_core.cuh"
 
 namespace fastcq {
@@ -64,7 +65,7 @@ static Fp2sLayout fp2s_layout(const fp2s_problem_t *p, const Fp2sParams &P, void
     l.tmp = cv.take<double>(2 * nm);
     l.g0 = cv.take<double>(2 * nm);
     l.gN = cv.take<double>(2 * nm);
-    if ((P.form == CQ_DIRECT || grad) && P.prec == CQ_F64)
+    if (((P.form == CQ_DIRECT || grad) && P.prec == CQ_F64) || (grad && P.form == CQ_FAST && P.prec == CQ_DF64))
         l.hist = cv.take<double>((size_t)(P.N + 1) * 2 * (hist_modes < 0 ? nm : hist_modes));
     if (P.form == CQ_DIRECT && P.prec == CQ_DF64) {
         l.wz = cv.take<float4>(P.N + 2 * kDirDfBT + 1);
@@ -1586,6 +1587,7 @@ __global__ void __launch_bounds__(32, 12) k_adjoint_direct(
 struct GradLayout {
     double *tgt, *mu, *gx0, *q1, *q2, *qz1, *qz2, *dza1, *dza2, *acc;
     double *fder1, *fder2, *ftmp;        // fast form: (c', c r') of each state's tables; their builds
+    float *adtab;                        // fast form, CQ_DF64: tables of the double-float backward sweep
     float4 *wa, *qa;                     // CQ_DF64: d and d' of both states padded for the double-float adjoint
     double *cg0, *ctgt, *cgx0, *cgN;     // compact [2][ns] copies of a slice (sliced runs only)
     size_t bytes;
@@ -1606,6 +1608,7 @@ static GradLayout grad_layout(const Fp2sParams &P, const Fp2sLayout &base, void 
         g.fder1 = cv.take<double>(2 * P.np);
         g.fder2 = cv.take<double>(2 * P.np);
         g.ftmp = cv.take<double>(8 * P.np);
+        if (P.prec == CQ_DF64) g.adtab = cv.take<float>(kAdjDfTabFloats);
         if (ns < nm) {
             g.cg0 = cv.take<double>(2 * ns);
             g.ctgt = cv.take<double>(2 * ns);
@@ -1795,7 +1798,8 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if (!ws_bytes) return CQ_EINVAL;
     const bool mixed = P.prec == CQ_BF16X3 || P.prec == CQ_TF32X3;
     const bool fast = P.form == CQ_FAST;
-    if (fast ? P.prec != CQ_F64 : !(P.prec == CQ_F64 || P.prec == CQ_DF64 || mixed)) return CQ_EUNSUPPORTED;
+    if (fast ? (P.prec != CQ_F64 && P.prec != CQ_DF64) : !(P.prec == CQ_F64 || P.prec == CQ_DF64 || mixed))
+        return CQ_EUNSUPPORTED;
     if (P.N > 13000) return CQ_EUNSUPPORTED;            // shared-memory bound of the weight derivatives
     if (mixed)
         return gradient_mixed(p, P, np1, np2, G0_dev, Gt_dev, vjp, J_host, dJdG0_dev, dJdalpha_host, ws_dev,
@@ -1822,7 +1826,7 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
     if ((st = launch_dst_field(p->M, p->dim, l.S, Gt_dev, gl.tgt, l.tmp, s))) return st;
     if ((st = weight_derivatives(P, p, gl.q1, gl.q2, s))) return st;
     const bool df = P.prec == CQ_DF64;
-    if (df && (st = direct_df_grad_tables(P.N, l.d1, l.d2, gl.q1, gl.q2, gl.wa, gl.qa, s)))
+    if (df && !fast && (st = direct_df_grad_tables(P.N, l.d1, l.d2, gl.q1, gl.q2, gl.wa, gl.qa, s)))
         return st;
     double *dzA1 = gl.dza1, *dzA2 = gl.dza2;
     if (fast) {
@@ -1832,6 +1836,9 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
             return st;
         if ((st = fast_grad_tables(P.scheme, 1.0 - p->alpha2, P.tau, np1, np2, P.L, l.tab2, l.scr1, gl.ftmp,
                                    gl.fder2, s)))
+            return st;
+        if (df && (st = fast_adjoint_df_tables(P, l.tab1, l.tab2, gl.fder1, gl.fder2, l.d1, l.d2, gl.q1, gl.q2,
+                                               gl.adtab, s)))
             return st;
     } else {
         const unsigned pg = (unsigned)((P.N + 2 * kAdjBT + 256) / 256);
@@ -1872,9 +1879,11 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
             k_fp2s_fast<true><<<(unsigned)((cnt + mpb - 1) / mpb), T, smem, s>>>(
                 Ps, l.lam + m0, g0, gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.hist);
             if ((st = launched())) return st;
-            if ((st = fast_adjoint_slice(Ps, wd, l.lam + m0, l.d1, l.d2, gl.q1, gl.q2, l.tab1, l.tab2, gl.fder1,
-                                         gl.fder2, l.hist, tgt, vjp, gx0, gl.acc, s)))
-                return st;
+            st = df ? fast_adjoint_df_slice(Ps, wd, l.lam + m0, l.d1, l.d2, gl.q1, gl.q2, gl.adtab, l.hist, tgt, vjp,
+                                            gx0, gl.acc, s)
+                    : fast_adjoint_slice(Ps, wd, l.lam + m0, l.d1, l.d2, gl.q1, gl.q2, l.tab1, l.tab2, gl.fder1,
+                                         gl.fder2, l.hist, tgt, vjp, gx0, gl.acc, s);
+            if (st) return st;
             if (ns < nm && (st = copy_slice(gl.gx0 + m0, nm, gl.cgx0, cnt, cnt, s))) return st;
             continue;
         }

@@ -150,8 +150,10 @@ def test_vjp_host_checks(fc):
     sz = C.c_size_t(0)
     da = (C.c_double * 2)()
     pf = fc.problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2)
-    assert fc.fp2s_vjp(pf, None, None, None, None) > 0                     # fast form: FP64 only
-    for prec in (fc.CQ_F32, fc.CQ_DF64):
+    assert fc.fp2s_vjp(pf, None, None, None, None) > 0                     # fast form: FP64
+    pd = fc.problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2, prec=fc.CQ_DF64)
+    assert fc.fp2s_vjp(pd, None, None, None, None) > 0                     # and its double-float sweep
+    for prec in (fc.CQ_F32,):
         pq = fc.problem(0.3, 0.7, 0.4, 1.0, 40, 1, 15, fc.CQ_BE, fc.CQ_FAST, 16, 0, 2, prec=prec)
         sz = C.c_size_t(0)
         assert fc._lib.fp2s_vjp(C.byref(pq), None, None, None, da, None, C.byref(sz), None) == fc.CQ_EUNSUPPORTED

@@ -1,7 +1,7 @@
-"""GPU gradient of the fast form (fp2s_gradient / fp2s_vjp with CQ_FAST, FP64: the discrete
-adjoint of the fast scheme, with backward geometric recurrences per quadrature node) against
-the oracle's fast-scheme gradient and against central finite differences of the GPU fast
-forward solve (``-m gpu``).
+"""GPU gradient of the fast form (fp2s_gradient / fp2s_vjp with CQ_FAST: the discrete adjoint
+of the fast scheme, with backward geometric recurrences per quadrature node, in FP64 and with the
+backward sweep in double-float, CQ_DF64) against the oracle's fast-scheme gradient and against
+central finite differences of the GPU fast forward solve (``-m gpu``).
 
 Tolerances: J to 1e-12 relative (the fast forward solve, parity-tested at 1e-12); dJ/dG0 to
 1e-10 of its largest entry (sums over modes and steps whose rounding differs between the
@@ -32,12 +32,13 @@ def fc():
     return pkg.load()
 
 
-def _cp(fc, p):
-    return fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, ci.FAST, p.np1, p.np2, p.ns)
+def _cp(fc, p, prec=0):
+    return fc.problem(p.alpha1, p.alpha2, p.m, p.T, p.N, p.dim, p.M, p.scheme, ci.FAST, p.np1, p.np2, p.ns,
+                      prec=prec)
 
 
-def _grad(fc, p, G0, Gt, cap=None):
-    cp = _cp(fc, p)
+def _grad(fc, p, G0, Gt, cap=None, prec=0):
+    cp = _cp(fc, p, prec)
     g0 = torch.tensor(G0, dtype=torch.float64, device="cuda")
     gt = torch.tensor(Gt, dtype=torch.float64, device="cuda")
     dg = torch.empty_like(g0)
@@ -74,12 +75,15 @@ CASES = [ci.Problem(0.3, 0.7, 0.4, 1.0, 60, 1, 15, ci.BE, ci.FAST, 16, 0, 2),
          ci.Problem(0.45, 0.5, 0.35, 1.0, 90, 2, 6, ci.BDF2, ci.FAST, 40, 150, 32)]
 
 
+@pytest.mark.parametrize("prec", [0, 4], ids=["f64", "df64"])
 @pytest.mark.parametrize("p", CASES, ids=["be1d", "be2d", "bdf2_1d", "bdf2_2d_m0", "n_below_L", "one_step",
                                           "bdf2_ns17_idle_lanes", "be_np200", "bdf2_np190_ns32"])
-def test_fast_gradient_against_oracle(fc, p):
+def test_fast_gradient_against_oracle(fc, p, prec):
+    if prec == 4 and p.np1 + p.np2 > 128:
+        pytest.skip("the double-float fast form takes np1 + np2 <= 128")
     G0 = ci.g0_uniform(p.M, p.dim, 51)
     Gt = 0.5 * ci.g0_uniform(p.M, p.dim, 52)
-    J, dG0, da = _grad(fc, p, G0, Gt)
+    J, dG0, da = _grad(fc, p, G0, Gt, prec=prec)
     Jr, dG0r, dar = AD.gradient_fast(p, G0, Gt)
     print("J %.3e vs %.3e; dJ/dalpha rel %.2e %.2e; dJ/dG0 %.2e" % (
         J, Jr, *(np.abs(da - dar) / np.abs(dar)), np.max(np.abs(dG0 - dG0r)) / np.max(np.abs(dG0r))))
@@ -88,8 +92,9 @@ def test_fast_gradient_against_oracle(fc, p):
     assert np.max(np.abs(dG0 - dG0r)) <= 1e-10 * np.max(np.abs(dG0r))
 
 
+@pytest.mark.parametrize("prec", [0, 4], ids=["f64", "df64"])
 @pytest.mark.parametrize("scheme", [ci.BE, ci.BDF2])
-def test_fast_gradient_against_finite_differences(fc, scheme):
+def test_fast_gradient_against_finite_differences(fc, scheme, prec):
     """Misfit against a target made by the same fast scheme with alpha + (0.05, -0.05) on a
     2D grid; central differences of the GPU fast forward solve (tables rebuilt at alpha +- eps)."""
     np1, np2, ns = (32, 0, 2) if scheme == ci.BE else (16, 48, 17)
@@ -100,7 +105,7 @@ def test_fast_gradient_against_finite_differences(fc, scheme):
     gt = torch.empty_like(g0)
     fc.fp2s_solve(cp_t, g0, gt, fc.workspace(fc.fp2s_solve(cp_t, g0, gt, None), "cuda"))
     Gt = gt.cpu().numpy()
-    J, dG0, da = _grad(fc, p, G0, Gt)
+    J, dG0, da = _grad(fc, p, G0, Gt, prec=prec)
     eps = 1e-5
     for s, f in ((0, "alpha1"), (1, "alpha2")):
         v = getattr(p, f)
@@ -136,15 +141,32 @@ def test_fast_vjp_dot_product(fc):
     assert abs(lhs - rhs) <= 1e-12 * float(torch.linalg.norm(dg) * torch.linalg.norm(v))
 
 
-def test_fast_gradient_in_mode_slices(fc):
+@pytest.mark.parametrize("prec", [0, 4], ids=["f64", "df64"])
+def test_fast_gradient_in_mode_slices(fc, prec):
     """A workspace cap below the unsliced size: forward and adjoint sweeps over slices of modes
     give the same dJ/dG0 per mode and J, dJ/dalpha up to the order of their sums."""
     p = ci.Problem(0.35, 0.6, 0.4, 1.0, 300, 2, 31, ci.BDF2, ci.FAST, 8, 24, 9)
     G0 = ci.g0_uniform(p.M, p.dim, 53)
     Gt = 0.5 * ci.g0_uniform(p.M, p.dim, 54)
-    J, dG0, da = _grad(fc, p, G0, Gt)
-    full = fc.fp2s_gradient(_cp(fc, p), None, None, None, None)
-    Js, dGs, das = _grad(fc, p, G0, Gt, cap=full // 5)
+    J, dG0, da = _grad(fc, p, G0, Gt, prec=prec)
+    full = fc.fp2s_gradient(_cp(fc, p, prec), None, None, None, None)
+    Js, dGs, das = _grad(fc, p, G0, Gt, cap=full // 5, prec=prec)
     assert abs(Js - J) <= 1e-13 * abs(J)
     assert np.all(np.abs(das - da) <= 1e-12 * np.abs(da))
     assert np.max(np.abs(dGs - dG0)) <= 1e-13 * np.max(np.abs(dG0))
+
+
+def test_fast_gradient_double_float_against_fp64(fc):
+    """The double-float backward sweep against the FP64 one on the 2D 63x63 grid (BDF2, 16 + 64
+    points, Ns = 17, N = 1024): the same forward levels, so the two differ by the double-float
+    rounding of the recurrences (~2^-48 per operation), far inside 1e-9."""
+    p = ci.Problem(0.4, 0.6, 0.4, 1.0, 1024, 2, 63, ci.BDF2, ci.FAST, 16, 64, 17)
+    G0 = ci.g0_checkerboard_uniform(p.M, ci.SEED_BASE + 11)
+    Gt = 0.5 * ci.g0_uniform(p.M, p.dim, 55)
+    J, dG0, da = _grad(fc, p, G0, Gt)
+    Jd, dGd, dad = _grad(fc, p, G0, Gt, prec=4)
+    print("double-float vs FP64 fast gradient: J %.2e, dJ/dalpha %.2e %.2e, dJ/dG0 %.2e" % (
+        abs(Jd - J) / abs(J), *(np.abs(dad - da) / np.abs(da)), np.max(np.abs(dGd - dG0)) / np.max(np.abs(dG0))))
+    assert abs(Jd - J) <= 1e-13 * abs(J)
+    assert np.all(np.abs(dad - da) <= 1e-9 * np.abs(da))
+    assert np.max(np.abs(dGd - dG0)) <= 1e-10 * np.max(np.abs(dG0))
