@@ -227,8 +227,9 @@ typedef struct {
     int32_t prec;          /* CQ_F64; in fp2s_solve also CQ_F32 with form == CQ_FAST (np1 + np2 <= 128),
                               CQ_DF64 with either form (fast: np1 + np2 <= 128)
                               and CQ_BF16X3 or CQ_TF32X3 with form == CQ_DIRECT (mixed-precision
-                              direct solve); fp2s_gradient / fp2s_vjp take CQ_F64 with either
-                              form, and CQ_DF64, CQ_BF16X3 and CQ_TF32X3 with form == CQ_DIRECT */
+                              direct solve); fp2s_gradient / fp2s_vjp take CQ_F64 and CQ_DF64
+                              with either form (fast, CQ_DF64: np1 + np2 <= 128), and CQ_BF16X3
+                              and CQ_TF32X3 with form == CQ_DIRECT */
     int32_t flags;
 } fp2s_problem_t;
 
@@ -293,7 +294,10 @@ int fp2s_modal(const fp2s_problem_t *p, const void *ws_dev, size_t ws_bytes, dou
  * backward geometric recurrences per quadrature node (O(N (np1 + np2)) per mode);
  * the derivatives of the quadrature tables in beta are Richardson-extrapolated
  * central differences of the same table construction (accurate to ~1e-10). The
- * workspace holds the forward levels ([N+1][2][M^dim] FP64) only. Sine modes are
+ * workspace holds the forward levels ([N+1][2][M^dim] FP64) only.
+ * form == CQ_FAST, prec == CQ_DF64: the same with the backward recurrences in
+ * double-float (the forward sweep and the per-mode sums in FP64); FP64-class
+ * results. Sine modes are
  * independent, so a smaller workspace is accepted: the forward and adjoint
  * sweeps then run over slices of modes (the largest multiple of 32 modes whose
  * two arrays fit), with the same results up to the summation order of J and

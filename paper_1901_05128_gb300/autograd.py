@@ -8,9 +8,9 @@ gradient with respect to alpha_1, alpha_2 (d/dalpha_i = -d/dbeta_i, beta_i = 1 -
 The backward pass recomputes the forward history inside the library call, so nothing
 but G^0 and alpha is kept between forward and backward.
 
-Both passes run on the device in FP64 (direct or fast), in double-float (prec = CQ_DF64,
-direct), or (prec = CQ_BF16X3 / CQ_TF32X3, direct) in the mixed-precision form:
-tensor-core histories on FP32 levels, forward and adjoint alike.
+Both passes run on the device in FP64, in double-float (prec = CQ_DF64), or (prec =
+CQ_BF16X3 / CQ_TF32X3, direct scheme) in the mixed-precision form: tensor-core histories on
+FP32 levels, forward and adjoint alike.
 Arguments are marshalled only.
 """
 from __future__ import annotations
@@ -50,9 +50,9 @@ def solve(G0: torch.Tensor, alpha: torch.Tensor, *, m: float, T: float, N: int, 
           scheme: int = fc.CQ_BDF2, prec: int = fc.CQ_F64, fast=None) -> torch.Tensor:
     """G^N of the direct scheme (or, with fast = (np1, np2, ns), of the fast scheme) for G0
     (float64 CUDA tensor [2, M**dim]) and alpha = (alpha_1, alpha_2) (float64 tensor [2]);
-    differentiable in both. prec: CQ_F64; for the direct scheme also CQ_DF64, or CQ_BF16X3 /
+    differentiable in both. prec: CQ_F64 or CQ_DF64; for the direct scheme also CQ_BF16X3 /
     CQ_TF32X3 for the mixed-precision form."""
-    allowed = (fc.CQ_F64,) if fast is not None else (fc.CQ_F64, fc.CQ_DF64, fc.CQ_BF16X3, fc.CQ_TF32X3)
+    allowed = (fc.CQ_F64, fc.CQ_DF64) if fast is not None else (fc.CQ_F64, fc.CQ_DF64, fc.CQ_BF16X3, fc.CQ_TF32X3)
     if prec not in allowed:
         raise ValueError("prec must be one of %s for this form" % (allowed,))
     if fast is not None and len(fast) != 3:

@@ -125,7 +125,7 @@ def test_autograd_rejects_bad_input(pkg):
         ag.solve(torch.zeros(2, 7, dtype=torch.float32, device="cuda"), a, m=0.3, T=1.0, N=4, dim=1, M=7)
     with pytest.raises(ValueError):
         ag.solve(torch.zeros(2, 6, dtype=torch.float64, device="cuda"), a, m=0.3, T=1.0, N=4, dim=1, M=7)
-    with pytest.raises(ValueError):               # the fast form's gradient is FP64 only
+    with pytest.raises(ValueError):               # no mixed-precision fast-form gradient
         ag.solve(torch.zeros(2, 7, dtype=torch.float64, device="cuda"), a, m=0.3, T=1.0, N=4, dim=1, M=7,
                  fast=(4, 8, 5), prec=fc.CQ_BF16X3)
 
