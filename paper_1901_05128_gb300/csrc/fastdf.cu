@@ -36,6 +36,7 @@
 #include <algorithm>
 
 #include "fastdf.cuh"
+#include "fastgrad.cuh"
 
 namespace fastcq {
 
@@ -48,12 +49,13 @@ __global__ void k_df_tables(int NP, int np, int L, int64_t N, const double *__re
     df_tables_fill(NP, np, L, N, tab1, tab2, d1, d2, out, threadIdx.x, blockDim.x);
 }
 
-// One problem: 16 modes per warp, every block runs all N steps of its 64 modes.
-template <int NP, bool BE, int WL>
+// One problem: 16 modes per warp, every block runs all N steps of its 64 modes (HIST: every level
+// also stored, for the fast-form gradient).
+template <int NP, bool BE, int WL, bool HIST>
 __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
     k_fp2s_fast_df(Fp2sParams P, const double *__restrict__ lam, const double *__restrict__ g0,
                    double *__restrict__ gN, int *__restrict__ status, const double *__restrict__ d1,
-                   const double *__restrict__ d2, const float *__restrict__ dftab) {
+                   const double *__restrict__ d2, const float *__restrict__ dftab, double *__restrict__ hist) {
     constexpr int KS = df_smem_slots(NP);
     extern __shared__ __align__(16) float smd[];
     const int L = P.L, T = blockDim.x, tid = threadIdx.x;
@@ -64,8 +66,9 @@ __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
     for (int j = 0; j < KS; ++j) Ys[(size_t)j * T + tid] = make_float2(0.0f, 0.0f);
     __syncthreads();
     const int64_t mode_raw = ((int64_t)blockIdx.x * (T >> 5) + (tid >> 5)) * kFastModesPerWarp + (tid & 15);
-    df_solve_lane<NP, BE, WL>(P, lam, g0, gN, status, d1, d2, reinterpret_cast<const float4 *>(smd),
-                              reinterpret_cast<const float2 *>(smd + 8 * NP), R, Ys, T, tid, mode_raw, P.nmodes);
+    df_solve_lane<NP, BE, WL, HIST>(P, lam, g0, gN, status, d1, d2, reinterpret_cast<const float4 *>(smd),
+                                    reinterpret_cast<const float2 *>(smd + 8 * NP), R, Ys, T, tid, mode_raw,
+                                    P.nmodes, hist);
 }
 
 static size_t df_smem_bytes(int NP, int L) {
@@ -88,10 +91,10 @@ int fast_df_tables(const Fp2sParams &P, const double *tab1, const double *tab2, 
 // blocks of 96 threads would take 3 rounds of 456 blocks at 3 CTAs per SM (99 % full) against
 // 3 rounds of 608 at 4 (74 %). The rounds' fullness is weighed against the issue rate, modelled
 // as saturating at two warps per scheduler.
-template <int NP, bool BE, int WL>
+template <int NP, bool BE, int WL, bool HIST>
 static int launch_df_kernel(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
-                            const double *d1, const double *d2, const float *dftab, cudaStream_t s) {
-    auto kern = k_fp2s_fast_df<NP, BE, WL>;
+                            const double *d1, const double *d2, const float *dftab, double *hist, cudaStream_t s) {
+    auto kern = k_fp2s_fast_df<NP, BE, WL, HIST>;
     const int64_t mpb = (int64_t)(kDfThreads / 32) * kFastModesPerWarp;
     const int64_t blocks = (P.nmodes + mpb - 1) / mpb;
     const size_t base = df_smem_bytes(NP, P.L);
@@ -125,31 +128,42 @@ static int launch_df_kernel(const Fp2sParams &P, const double *lam, const double
         const size_t pad = (size_t)sm_smem / best - (size_t)reserved;
         smem = std::min<size_t>(std::max(base, pad / 128 * 128), (size_t)max_block);
     }
-    kern<<<(unsigned)blocks, kDfThreads, smem, s>>>(P, lam, g0, gN, status, d1, d2, dftab);
+    kern<<<(unsigned)blocks, kDfThreads, smem, s>>>(P, lam, g0, gN, status, d1, d2, dftab, hist);
     return CQ_OK;
 }
 
-template <int NP>
+template <int NP, bool HIST>
 static int launch_df(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
-                     const double *d1, const double *d2, const float *dftab, cudaStream_t s) {
-    if (P.scheme == CQ_BE) return launch_df_kernel<NP, true, 2>(P, lam, g0, gN, status, d1, d2, dftab, s);
-    if (P.L <= 17) return launch_df_kernel<NP, false, 17>(P, lam, g0, gN, status, d1, d2, dftab, s);
-    return launch_df_kernel<NP, false, kMaxNs>(P, lam, g0, gN, status, d1, d2, dftab, s);
+                     const double *d1, const double *d2, const float *dftab, double *hist, cudaStream_t s) {
+    if (P.scheme == CQ_BE) return launch_df_kernel<NP, true, 2, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+    if (P.L <= 17) return launch_df_kernel<NP, false, 17, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+    return launch_df_kernel<NP, false, kMaxNs, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+}
+
+template <bool HIST>
+static int fast_df_run(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
+                       const double *d1, const double *d2, const float *dftab, double *hist, cudaStream_t s) {
+    switch (df_np_bound(P.np)) {
+        case 16: return launch_df<16, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+        case 32: return launch_df<32, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+        case 48: return launch_df<48, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+        case 64: return launch_df<64, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+        case 80: return launch_df<80, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+        case 96: return launch_df<96, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+        case 112: return launch_df<112, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+        case 128: return launch_df<128, HIST>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
+        default: return CQ_EUNSUPPORTED;
+    }
 }
 
 int fast_df_solve(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
                   const double *d1, const double *d2, const float *dftab, cudaStream_t s) {
-    switch (df_np_bound(P.np)) {
-        case 16: return launch_df<16>(P, lam, g0, gN, status, d1, d2, dftab, s);
-        case 32: return launch_df<32>(P, lam, g0, gN, status, d1, d2, dftab, s);
-        case 48: return launch_df<48>(P, lam, g0, gN, status, d1, d2, dftab, s);
-        case 64: return launch_df<64>(P, lam, g0, gN, status, d1, d2, dftab, s);
-        case 80: return launch_df<80>(P, lam, g0, gN, status, d1, d2, dftab, s);
-        case 96: return launch_df<96>(P, lam, g0, gN, status, d1, d2, dftab, s);
-        case 112: return launch_df<112>(P, lam, g0, gN, status, d1, d2, dftab, s);
-        case 128: return launch_df<128>(P, lam, g0, gN, status, d1, d2, dftab, s);
-        default: return CQ_EUNSUPPORTED;
-    }
+    return fast_df_run<false>(P, lam, g0, gN, status, d1, d2, dftab, nullptr, s);
+}
+
+int fast_df_solve_hist(const Fp2sParams &P, const double *lam, const double *g0, double *gN, int *status,
+                       const double *d1, const double *d2, const float *dftab, double *hist, cudaStream_t s) {
+    return fast_df_run<true>(P, lam, g0, gN, status, d1, d2, dftab, hist, s);
 }
 
 }  // namespace fastcq

@@ -201,14 +201,15 @@ __device__ __forceinline__ void df_tables_fill(int NP, int np, int L, int64_t N,
 // float4, wdf [kMaxNs][2] float2, R [L][T] float2 and Ys [df_smem_slots(NP) / 2][T] float4 (the
 // pair (yh, yh', yl, yl') of slots 2p, 2p + 1), column tid. Node slots are updated in pairs with
 // the packed operations (node_r2 / node_u2 / acc_prod2); component 0 of the partial sums collects
-// the even slots and component 1 the odd ones.
-template <int NP, bool BE, int WL>
+// the even slots and component 1 the odd ones. With HIST every level is also stored in true
+// units (the forward sweep of the fast-form gradient): hist[(n * 2 + s) * nmodes + mode], n = 0 .. N.
+template <int NP, bool BE, int WL, bool HIST = false>
 __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double *__restrict__ lam,
                                               const double *__restrict__ g0, double *__restrict__ gN,
                                               int *__restrict__ status, const double *__restrict__ d1,
                                               const double *__restrict__ d2, const float4 *tab, const float2 *wdf,
                                               float2 *R, float2 *Ys, int T, int tid, int64_t mode_raw,
-                                              int64_t mode_end) {
+                                              int64_t mode_end, double *__restrict__ hist = nullptr) {
     constexpr int KR = NP - df_u_slots(NP);       // slots of the r form
     constexpr int KS = df_smem_slots(NP);         // slots in shared memory (all of the r form)
     static_assert(KS <= KR, "shared-memory slots take the r form");
@@ -229,6 +230,7 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
     int ex = 0;
     if (gmax > 0.0 && isfinite(gmax)) frexp(gmax, &ex);
     double gz = ldexp(gz64, -ex);
+    if (HIST && active) hist[st * P.nmodes + mode] = gz64;
 
     const double d_s0 = dn[0], d_o0 = (st ? d1 : d2)[0];
     ModeConst mc;
@@ -254,6 +256,7 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
         const double b_o = __shfl_xor_sync(0xffffffffu, b, 16);
         const double x = m1_oo * b + m1_ot * b_o;
         Rc[(size_t)slot * T] = df_of(x);
+        if (HIST && active) hist[(2 + st) * P.nmodes + mode] = ldexp(x, ex);
         gm2 = gm1;
         gm1 = x;
         slot = (slot + 1 == L) ? 0 : slot + 1;
@@ -344,6 +347,7 @@ __device__ __forceinline__ void df_solve_lane(const Fp2sParams &P, const double 
             ex += k;
         }
         Rc[(size_t)slot * T] = xd;
+        if (HIST && active) hist[(n * 2 + st) * P.nmodes + mode] = ldexp(x, ex);
         gm2 = gm1;
         gm1 = x;
         ch = nh;

@@ -1868,17 +1868,24 @@ static int gradient_impl(const fp2s_problem_t *p, const double *G0_dev, const do
             gx0 = gl.cgx0;
         }
         if (fast) {
-            // forward fast solve keeping every level, then the backward sweep of the fast adjoint
-            const int T = fast_block_threads(P.np, P.L, cnt);
-            if (T == 0) return CQ_EUNSUPPORTED;
-            const size_t smem = fast_smem_bytes(P.np, P.L, T);
-            if (cudaFuncSetAttribute(k_fp2s_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-                return CQ_ECUDA;
-            const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
-            k_fp2s_fast<true><<<(unsigned)((cnt + mpb - 1) / mpb), T, smem, s>>>(
-                Ps, l.lam + m0, g0, gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.hist);
-            if ((st = launched())) return st;
+            // forward fast solve keeping every level (double-float for CQ_DF64), then the backward
+            // sweep of the fast adjoint
+            if (df) {
+                if ((st = fast_df_solve_hist(Ps, l.lam + m0, g0, gN, l.status, l.d1, l.d2, l.ftab, l.hist, s)))
+                    return st;
+                if ((st = launched())) return st;
+            } else {
+                const int T = fast_block_threads(P.np, P.L, cnt);
+                if (T == 0) return CQ_EUNSUPPORTED;
+                const size_t smem = fast_smem_bytes(P.np, P.L, T);
+                if (cudaFuncSetAttribute(k_fp2s_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem) != cudaSuccess)
+                    return CQ_ECUDA;
+                const int64_t mpb = (int64_t)(T / 32) * kFastModesPerWarp;
+                k_fp2s_fast<true><<<(unsigned)((cnt + mpb - 1) / mpb), T, smem, s>>>(
+                    Ps, l.lam + m0, g0, gN, l.status, l.d1, l.d2, l.tab1, l.tab2, l.hist);
+                if ((st = launched())) return st;
+            }
             st = df ? fast_adjoint_df_slice(Ps, wd, l.lam + m0, l.d1, l.d2, gl.q1, gl.q2, gl.adtab, l.hist, tgt, vjp,
                                             gx0, gl.acc, s)
                     : fast_adjoint_slice(Ps, wd, l.lam + m0, l.d1, l.d2, gl.q1, gl.q2, l.tab1, l.tab2, gl.fder1,
