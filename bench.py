@@ -723,8 +723,8 @@ def fast_gradient_run(fc, torch, dev, p, g0, gt, Gt, K, flush, da64, dG64, ms64,
                                          "10 np + 4 (Ns - 1)"},
         "cpu_baseline": "the gradient leg's (the oracle's direct adjoint; the fast scheme's oracle gradient runs "
                         "the same O(N^2) recursion with the quadrature weights)",
-        "df64": {"precision": "the backward sweep in double-float (FP32 pairs, packed two-wide; FP64 steps and "
-                              "per-mode sums); forward sweep FP64",
+        "df64": {"precision": "forward and backward sweeps in double-float (FP32 pairs, packed two-wide; FP64 "
+                              "steps, stored levels and per-mode sums)",
                  "ms_per_gradient": statistics.mean(dtimes), "kernels_ms": statistics.mean(dkern),
                  "speedup_vs_fp64_fast_gradient": ms / statistics.mean(dtimes),
                  "rel_err_vs_central_differences": [abs(dad[i] - fd[i]) / abs(fd[i]) for i in range(2)],
