@@ -1,5 +1,5 @@
-// Gradient of the fast form (fp2s_gradient / fp2s_vjp with CQ_FAST, FP64): the discrete
-// adjoint of the fast scheme.
+// Gradient of the fast form (fp2s_gradient / fp2s_vjp with CQ_FAST, FP64 or CQ_DF64): the
+// discrete adjoint of the fast scheme.
 //
 // The fast history (recurrences after Eq. 3.10 and Eq. 3.18) is the direct history of
 // Eq. 3.8 with the weights
@@ -24,7 +24,8 @@
 //
 // One lane per mode and state as in the fused fast solve (lanes l < 16: state 1, l + 16: state
 // 2 of the same mode); a lane keeps V_j, W_j and the last L adjoint levels in shared memory
-// (column tid) and reads its forward levels x^m from the history the forward sweep stored.
+// (column tid) and reads its forward levels x^m from the history the forward sweep stored (the
+// FP64 fused fast solve, or for CQ_DF64 the double-float one, with every level kept).
 #include "common.cuh"
 #include "fastdf.cuh"
 #include "fastgrad.cuh"
@@ -277,7 +278,7 @@ int fast_adjoint_slice(const Fp2sParams &P, double wd, const double *lam, const 
 // ranked by r and the slowest quarter takes the u form (a ratio near 1 held as hi + lo loses
 // 2^-49 / (1 - r) relative to 1 - r, and the geometric sums repeat that error); the adjoint
 // variables are scaled by the power of two of the mode's terminal condition. The forward sweep
-// (and its stored levels) is the FP64 fast solve.
+// is the double-float fast solve, which stores its levels in true units (FP64).
 // ---------------------------------------------------------------------------
 
 // Per state s and node pair p (slots 2p, 2p + 1) four float4 words at (p * 2 + s) * 4 + k:
